@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the explicit DG-SEM + reduced-order PMUT time step.
+
+Metric: DG-SEM Gdof-steps/s = (unique GLL nodes) x (drive patterns) x (time
+steps) / seconds, at FP64 or FP32/mixed precision, on synthetic inputs with
+the shapes of the paper's problem class (see workloads/).
+
+Default workload: 64 beam-steering drive patterns on the 1024-PMUT mesh
+(primary 128x128x16 hexes N=4 + secondary 64x64x96 hexes N=6, 2:1 interface,
+102.6M nodes), FP32/mixed precision, one launch sequence for all patterns.
+
+`python bench.py --gpus N --steps K --warmup W` prints one JSON line.  Under
+torchrun (N > 1) every rank runs its own batch of patterns (replicas; the
+path needs no data exchange) and rank 0 reports the max time over ranks.
+`--impl reference` times the CPU oracle on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+# DRAM bytes per launch of the dominant kernel measured with ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (workload, precision, kernel kind); see profiles/.  None: not measured for
+# the current kernel.
+NCU_TRAFFIC_PER_LAUNCH = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config4_batched",
+                    choices=["config4_batched", "config3_array32", "config2_array16", "config1_single_pmut"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name, batch):
+    if name == "config4_batched":
+        return W.config4_batched(nsteps=1, batch=batch or 64)
+    if name == "config3_array32":
+        return W.config3_array32(nsteps=1, batch=batch or 1)
+    if name == "config2_array16":
+        w = W.config2_array16(nsteps=1)
+    else:
+        w = W.config1_single_pmut(nsteps=1)
+    if batch and batch > 1:
+        w.batch = batch
+        w.drive_delay = np.repeat(w.drive_delay, batch, axis=0)
+        w.drive_amp = np.repeat(w.drive_amp, batch, axis=0)
+    return w
+
+
+def default_precision(name):
+    return "fp32" if name in ("config4_batched", "config3_array32") else "fp64"
+
+
+def oracle_sample(name):
+    """Bounded sample of the workload for the CPU oracle: the same element
+    types, orders and PMUT model on a crop the oracle assembles in seconds."""
+    if name == "config1_single_pmut":
+        return W.config1_single_pmut(nsteps=1)
+    return W.small_two_domain(nx_p=8, nz_p=4, nx_s=4, nz_s=8, n_pmut_side=2, nsteps=1)
+
+
+def time_oracle(name, seconds=15.0, chunk=None):
+    """Oracle Gdof-steps/s on the bounded sample (single host thread: scipy's
+    sparse mat-vec and numpy's element-wise kernels run on one core)."""
+    from oracle import dgsem_oracle as O
+    w = oracle_sample(name)
+    P = O.OracleProblem(w)
+    dt = P.stable_dt()
+    n = 8
+    while True:
+        t0 = time.perf_counter()
+        P.run(nsteps=n, dt=dt, batch=1)
+        el = time.perf_counter() - t0
+        if el > 0.5 or n >= 1 << 20:
+            break
+        n *= 4
+    per_step = el / n
+    S = max(1, int(seconds / per_step)) if chunk is None else chunk
+    t0 = time.perf_counter()
+    P.run(nsteps=S, dt=dt, batch=1)
+    el = time.perf_counter() - t0
+    sample = (f"{w.name}: primary {w.domains[0].nelem} N={w.domains[0].order}"
+              + (f" + secondary {w.domains[1].nelem} N={w.domains[1].order}" if len(w.domains) > 1 else "")
+              + f", {P.nh} nodes, {S} steps, batch 1")
+    return P.nh * S / el / 1e9, sample, P, w, dt
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, gpu_index):
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return None
+        rows = [[x.strip() for x in r] for r in rows if len(r) >= 9 and r[0].strip() == str(gpu_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle on a bounded sample of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name = args.workload
+    prec = args.precision or default_precision(name)
+    from oracle import dgsem_oracle as O
+    w = oracle_sample(name)
+    P = O.OracleProblem(w)
+    dt = P.stable_dt()
+    # chunk of oracle time steps per bench step: about 0.5 s each
+    n = 4
+    t0 = time.perf_counter()
+    P.run(nsteps=n, dt=dt, batch=1)
+    per = (time.perf_counter() - t0) / n
+    chunk = max(1, int(0.5 / per))
+    for _ in range(args.warmup):
+        P.run(nsteps=chunk, dt=dt, batch=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.run(nsteps=chunk, dt=dt, batch=1)
+    el = time.perf_counter() - t0
+    value = P.nh * chunk * args.steps / el / 1e9
+    sample = (f"{w.name}: {P.nh} nodes, {chunk} oracle time steps per bench step, batch 1 "
+              f"(same element sizes/orders/PMUT model as {name})")
+    out = {"impl": "reference", "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": name, "precision": "fp64 (oracle)", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "Gdof-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_06267_gb300 import dgsem
+
+    name = args.workload
+    prec_name = args.precision or default_precision(name)
+    prec = dgsem.DGSEM_FP32_MIXED if prec_name == "fp32" else dgsem.DGSEM_FP64
+    w = make_workload(name, args.batch)
+    if w.batch > 1 and world > 1:
+        # independent patterns per rank (replicas): reseed the steering angles
+        if name == "config4_batched":
+            w.drive_delay, w.drive_amp, _ = W.steering_patterns(w.pmuts.centers, w.batch, seed=4 + 1000 * rank)
+    B = w.batch
+    sol = dgsem.Solver(w)
+    ndof = sol.ndof
+    K_p = w.pmuts.n_pmut if w.pmuts is not None else 0
+    R = w.receivers.shape[0]
+    S_tot = args.warmup + args.steps
+    drive_all = w.drive(sol.dt, S_tot + args.steps, B)
+    stream = torch.cuda.current_stream()
+    d_warm = torch.tensor(np.ascontiguousarray(drive_all[:, :, :args.warmup]), device="cuda")
+    d_time = torch.tensor(np.ascontiguousarray(drive_all[:, :, args.warmup:S_tot]), device="cuda")
+    tr_warm = torch.zeros((B, R, args.warmup), dtype=torch.float64, device="cuda")
+    tr_time = torch.zeros((B, R, args.steps), dtype=torch.float64, device="cuda")
+
+    # warm-up from rest
+    sol.run(drive=d_warm, precision=prec, nsteps=args.warmup, traces=tr_warm)
+    torch.cuda.synchronize()
+    clocks_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                               f".bench_clocks_{rank}.csv")
+    dgsem.dgsem_profile(sol.ctx, False)      # reset launch counters
+    with ClockSampler(clocks_path) as cs:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dgsem.DGSEM_RUN_CONTINUE,
+                stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        launches = sum(dgsem.dgsem_kernel_stats(sol.ctx, k)[1] for k in range(4))
+        # per-kernel timing pass (CUDA events around each launch)
+        dgsem.dgsem_profile(sol.ctx, True)
+        sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dgsem.DGSEM_RUN_CONTINUE,
+                stream=stream.cuda_stream)
+        kstats = [dgsem.dgsem_kernel_stats(sol.ctx, k) for k in range(4)]
+        dgsem.dgsem_profile(sol.ctx, False)
+        # end to end through host buffers (pinned), copies inside the timed region
+        e2e = None
+        if not args.no_e2e:
+            h_drive = torch.from_numpy(np.ascontiguousarray(drive_all[:, :, S_tot:S_tot + args.steps])).pin_memory()
+            h_tr = torch.zeros((B, R, args.steps), dtype=torch.float64).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol.run(drive=h_drive, precision=prec, nsteps=args.steps, traces=h_tr,
+                    flags=dgsem.DGSEM_RUN_CONTINUE, stream=stream.cuda_stream)
+            e2e_s = time.perf_counter() - t0
+            if dist is not None:
+                t = torch.tensor([e2e_s], device="cuda")
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            e2e = {"value": ndof * B * args.steps * world / e2e_s / 1e9, "unit": "Gdof-steps/s",
+                   "h2d_bytes_per_step": int(B * K_p * 8), "d2h_bytes_per_step": int(B * R * 8)}
+    finite = bool(torch.isfinite(tr_time).all().item())
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    value = ndof * B * args.steps * world / (ms / 1e3) / 1e9
+    # roofline of the dominant kernel
+    names = ["pmut_recv", "iface", "vol_primary", "vol_secondary"]
+    kdom = max(range(4), key=lambda k: kstats[k][0])
+    es = 4 if prec == dgsem.DGSEM_FP32_MIXED else 8
+    peaks = measured_peaks()
+    roof = None
+    if kdom >= 2 and kstats[kdom][1] > 0:
+        d = w.domains[kdom - 2]
+        nodes = int(np.prod([d.nelem[i] * d.order + 1 for i in range(3)]))
+        alg_bytes = nodes * B * 4 * es          # read p, read v, write v, write p_next
+        avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
+        achieved = alg_bytes / avg_s / 1e9
+        if prec == dgsem.DGSEM_FP32_MIXED:
+            peak = peaks["hbm_gbs"] if peaks else 6800.0
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])),
+                    "kernel": names[kdom], "peak_source": "measured" if peaks else "fallback",
+                    "alg_bytes_per_launch": alg_bytes}
+        else:
+            # FP64 path: bound by the FP64 pipe; peak derived from the nominal
+            # 1.25 TFLOP/s FP64 rate of GB300 at the 2070 MHz maximum SM clock
+            N = d.order
+            flop_per_node = 2 * (3 * (N + 2) + 4)
+            achieved_f = nodes * B * flop_per_node / avg_s / 1e12
+            roof = {"bound": "alu", "achieved": achieved_f, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": achieved_f / 1.25, "traffic": NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])),
+                    "kernel": names[kdom], "peak_source": "nominal FP64 (no measured FP64 peak)",
+                    "hbm_achieved_gbs": nodes * B * 4 * es / avg_s / 1e9}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample, _, _, _ = time_oracle(name, seconds=15.0)
+        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+    clocks = cs.summary(local)
+    out = {
+        "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dgsem.DGSEM_FP32_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "precision": "fp32-mixed" if prec == dgsem.DGSEM_FP32_MIXED else "fp64",
+                   "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single-gpu",
+                   "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(4)},
+        "finite": finite,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

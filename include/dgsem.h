@@ -1,0 +1,212 @@
+/*
+ * dgsem.h -- C ABI of the GB300 explicit DG-SEM acoustic step with batched
+ * reduced-order PMUT modal coupling (arXiv 2603.06267).
+ *
+ * The library solves, on one GPU, the semi-discrete system of Sec. 3.1
+ *     M p'' + K p = f(q''),      q'' + W q = g(p, phi)        (eqs. semi_SEM, semi_PMUT)
+ * where K is the DG-SEM stiffness of eq. (Wf_2): GLL spectral elements, C0
+ * inside each box, symmetric interior penalty across the (possibly
+ * non-conforming, variable-order) interface Gamma_I between a primary box and
+ * a secondary box stacked on its z-max face (Sec. 3, Sec. 5), M the lumped
+ * GLL mass, f_i and g_m the membrane integrals of eqs. (f_i) and (g_m), and
+ * integrates it with the Newmark gamma = 1/2, beta = 0 predictor/corrector of
+ * Algorithm 1.  Walls other than Gamma_PMUT (the primary's z-min face) and
+ * Gamma_I are rigid (homogeneous Neumann, eq. full_problem row 7).
+ *
+ * Conventions common to every call
+ *   - Every call returns a dgsem_status; DGSEM_OK is 0, errors are negative.
+ *     dgsem_last_error() gives a message for the calling thread's last error.
+ *     No call aborts, traps or hangs the GPU; device-side problems are
+ *     reported through status words read back by the host.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  Device memory the library allocates belongs to the
+ *     context and is released by dgsem_destroy().
+ *   - A context is bound to the CUDA device that is current when it is
+ *     created; every later call must be made with that device current.
+ *   - Node order of full-field vectors (dgsem_set_state, dgsem_get_pressure):
+ *     primary lattice then secondary lattice; inside a box, lattice index
+ *     (i, j, k) of the GLL nodes with i (x) fastest, i in [0, nelem[0]*order].
+ *   - Not thread-safe per context: calls on one context must not overlap.
+ */
+#ifndef DGSEM_H
+#define DGSEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dgsem_ctx dgsem_ctx;
+
+typedef enum {
+  DGSEM_OK = 0,
+  DGSEM_EINVAL = -1,     /* bad argument (null pointer, size, range)            */
+  DGSEM_ENOMEM = -2,     /* device or host allocation failed                    */
+  DGSEM_ECUDA = -3,      /* a CUDA runtime call failed                          */
+  DGSEM_EUNSTABLE = -4,  /* dt above the stability limit, or non-finite state   */
+  DGSEM_ETIMEOUT = -5,   /* a bounded device-side wait gave up                  */
+  DGSEM_ENOMATCH = -6,   /* interface face matching (Algorithm 3) failed        */
+  DGSEM_ESTATE = -7      /* call out of order (e.g. run before pmut_array_set)  */
+} dgsem_status;
+
+typedef enum {
+  DGSEM_FP64 = 0,        /* every field and operator in FP64                    */
+  DGSEM_FP32_MIXED = 1   /* pressure state, volume and face operators in FP32;
+                            modal ODEs, membrane projections and receiver traces
+                            in FP64                                             */
+} dgsem_precision;
+
+/* dgsem_run flags */
+#define DGSEM_RUN_CONTINUE 1   /* continue from the context's current state
+                                  instead of restarting from rest (p = p' = 0,
+                                  q = q' = 0, eq. full_problem row 4, eq. ode
+                                  row 3)                                        */
+
+/* One axis-aligned box subdomain meshed by nelem[0] x nelem[1] x nelem[2]
+ * equal hexahedra with affine maps X_K (Sec. 3, the affine case of the
+ * trilinear maps), GLL order `order` (r_a of V_a^{r_a}, 1 <= order <= 8),
+ * sound speed c (m/s) and density rho (kg/m^3). */
+typedef struct {
+  double origin[3];
+  double extent[3];
+  int nelem[3];
+  int order;
+  double c;
+  double rho;
+} dgsem_domain_desc;
+
+/* Mesh description (Sec. 3 and Sec. 5).
+ *   ndomains        1 (primary only) or 2 (primary + secondary).
+ *   domains         [ndomains]; domains[0] is the primary box Omega_in, whose
+ *                   z-min face carries Gamma_PMUT; domains[1] (if present) is
+ *                   Omega_out, stacked on the primary's z-max face with the
+ *                   same x-y extent.  Each secondary element face on Gamma_I
+ *                   must cover an integer r x r block of primary faces
+ *                   (r = 1 conforming, r = 2 the 2:1 case).
+ *   fine_faces      NULL, or [n_fine_faces] primary top-layer element columns
+ *                   ex + nelem[0]*ey whose z-max face belongs to Gamma_I (the
+ *                   "finer" face list of Sec. 5).  NULL = all of them.
+ *   coarse_faces    NULL, or [n_coarse_faces] secondary bottom-layer columns
+ *                   mx + nelem[0]*my (the "coarser" list).  NULL = all.
+ *                   Faces not listed are rigid walls.  The pairs are matched
+ *                   by Algorithm 3 (opposite normals, one-vertex radius
+ *                   filter, inverse map); a fine-face quadrature node without
+ *                   a coarse neighbour fails with DGSEM_ENOMATCH.
+ *   dt              time step in s if > 0, else computed from cfl as
+ *                   cfl * min_K min_d (h_d/2 * min GLL gap(N_K)) / max c.
+ *   penalty_alpha   alpha of gamma_F = alpha cbar^2 max(N)^2 / min(h) (Sec. 3).
+ *   iface_quad_pts  Gauss-Legendre points per direction on each fine face;
+ *                   0 = max(order) + 1, which integrates the interface terms
+ *                   exactly for affine faces. */
+typedef struct {
+  int ndomains;
+  const dgsem_domain_desc* domains;
+  int n_fine_faces;
+  const int* fine_faces;
+  int n_coarse_faces;
+  const int* coarse_faces;
+  double cfl;
+  double dt;
+  double penalty_alpha;
+  int iface_quad_pts;
+} dgsem_mesh_desc;
+
+/* Build the mesh, the 1D GLL/GL tables, the interface maps and the time step
+ * on the host and upload them to the current device.  *out receives a new
+ * context (NULL on error). */
+int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out);
+
+/* Time step, stability bound and size.  dt_stable_max is 2 / sqrt(lambda_max)
+ * of M^-1 K from dgsem_check_stability() (0 if it has not run); ndof counts
+ * the unique GLL nodes of all boxes (dim V^DG). Any output may be NULL. */
+int dgsem_get_dt(const dgsem_ctx* ctx, double* dt, double* dt_stable_max, long long* ndof);
+
+/* Power iteration for lambda_max(M^-1 K) on the device in FP64 (iters
+ * products).  Returns DGSEM_EUNSTABLE if dt > 0.95 * 2 / sqrt(lambda_max);
+ * *lambda_max (may be NULL) receives the estimate either way. */
+int dgsem_check_stability(dgsem_ctx* ctx, int iters, double* lambda_max);
+
+/* GLL nodes of Gamma_PMUT's face lattice (the primary's z-min face):
+ * *n_nodes = (nelem[0]*order+1) * (nelem[1]*order+1); *xy points to a
+ * library-owned [n_nodes][2] array of (x, y), node index ix + Lx*iy, valid
+ * until dgsem_destroy(). */
+int dgsem_pmut_nodes(const dgsem_ctx* ctx, int* n_nodes, const double** xy);
+
+/* Reduced-order PMUT array (Sec. 2, eq. pmut_problem; Sec. 3.1 eqs. f_i, g_m).
+ *   n_pmut, n_modes  K membranes with M modes each (1 <= M <= 16).
+ *   foot_ptr         [K+1] CSR offsets into foot_node / shape_un.
+ *   foot_node        [nnz] face-lattice node indices (see dgsem_pmut_nodes)
+ *                    of membrane k's footprint gamma_k.
+ *   shape_un         [nnz][M] U_{k,m}.n at those nodes (n: outward normal of
+ *                    the fluid, -e_z on the z-min face).
+ *   freq_hz, damping, eta, modal_mass   [K][M]: omega/2pi, modal damping
+ *                    ratio zeta, electromechanical coupling eta (N/V), modal
+ *                    mass mu (kg; NULL means 1, the paper's literal ODE).
+ * The modal ODE integrated is
+ *   mu (q'' + 2 zeta omega q' + omega^2 q) = int_{gamma_k} p U.n dsigma + eta phi,
+ * the membrane integrals use GLL collocation on the face nodes, and the
+ * acoustic forcing is f_i = -kappa sum q'' int U.n psi_i with kappa = rho c^2
+ * of the primary box.  Replaces any previous array; resets the PMUT state. */
+int pmut_array_set(dgsem_ctx* ctx, int n_pmut, int n_modes, const int* foot_ptr,
+                   const int* foot_node, const double* shape_un, const double* freq_hz,
+                   const double* damping, const double* eta, const double* modal_mass);
+
+/* Run nsteps steps of Algorithm 1 for `batch` independent drive patterns
+ * sharing the mesh and the PMUT array.
+ *   precision  dgsem_precision.
+ *   drive      [batch][n_pmut][nsteps] voltages phi_k(t^n), t^n = (n0 + n) dt,
+ *              host or device memory (FP64); may be NULL when n_pmut == 0.
+ *   recv_xyz   [n_recv][3] receiver positions (host), interpolated with the
+ *              tensor Lagrange basis of the containing element (lowest
+ *              element id on ties, the primary box on Gamma_I).
+ *   traces     [batch][n_recv][nsteps] output (host or device, FP64):
+ *              sample n is p^{n0+n+1} at the receivers.
+ *   flags      0 or DGSEM_RUN_CONTINUE.
+ *   stream     cudaStream_t to order the work on (NULL = legacy default
+ *              stream); the call returns after the stream has finished.
+ * Without DGSEM_RUN_CONTINUE the state restarts from rest (or from the state
+ * given by the last dgsem_set_state/dgsem_state_load) and n0 = 0. */
+int dgsem_run(dgsem_ctx* ctx, int precision, int batch, int nsteps, const double* drive,
+              int n_recv, const double* recv_xyz, double* traces, int flags, void* stream);
+
+/* Initial state p^0, p'^0 (host, FP64, [ndof] in the node order above,
+ * broadcast to every batch member) for the next dgsem_run without
+ * DGSEM_RUN_CONTINUE; the run starts from p''^0 = M^-1 (-K p^0).  Either
+ * pointer may be NULL (zero). */
+int dgsem_set_state(dgsem_ctx* ctx, const double* p0, const double* v0);
+
+/* Current pressure field p^n of every batch member after the last run, as
+ * FP64 host array [batch][ndof] (node order above). */
+int dgsem_get_pressure(const dgsem_ctx* ctx, double* p, size_t len);
+
+/* Checkpoint of the full time-stepping state (pressure pair, half-step
+ * velocity, PMUT q, q', q'', step counter, precision, batch).  With buf NULL,
+ * *len receives the size needed; otherwise *len must hold the buffer size. */
+int dgsem_state_save(const dgsem_ctx* ctx, void* buf, size_t* len);
+int dgsem_state_load(dgsem_ctx* ctx, const void* buf, size_t len);
+
+/* Kernel instrumentation.  dgsem_profile(ctx, 1) makes later runs bracket
+ * every kernel launch with CUDA events on the run's stream; statistics are
+ * accumulated per kernel kind (DGSEM_K_*) until dgsem_profile(ctx, 1) is
+ * called again (which resets them) or profiling is switched off with 0.
+ * Launch counts are kept whether or not timing is enabled. */
+#define DGSEM_K_PMUT_RECV 0   /* PMUT modal step + receiver sampling          */
+#define DGSEM_K_IFACE 1       /* interface fluxes on Gamma_I                   */
+#define DGSEM_K_VOL0 2        /* fused volume update of the primary box        */
+#define DGSEM_K_VOL1 3        /* fused volume update of the secondary box      */
+#define DGSEM_K_COUNT 4
+int dgsem_profile(dgsem_ctx* ctx, int enable);
+int dgsem_kernel_stats(const dgsem_ctx* ctx, int kind, double* total_ms, long long* launches);
+
+/* Message of the calling thread's last error ("" if none). */
+const char* dgsem_last_error(void);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void dgsem_destroy(dgsem_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSEM_H */

@@ -1,0 +1,1093 @@
+// Host setup and C ABI of the DG-SEM + reduced-order PMUT explicit step.
+//
+// Setup (untimed): GLL / Gauss-Legendre tables, the box lattices, the
+// stencil rows of the factorised GLL stiffness (eq. Wf_2), the interface
+// maps of Sec. 5 (Algorithm 3 face matching), the PMUT membrane matrix of
+// eqs. (f_i)/(g_m), receivers and the time step.
+// Hot loop: per step, PMUT modal step + receivers (small.cu), interface
+// fluxes (small.cu), fused volume update of each box (vol.cu), following
+// Algorithm 1 in its two-vector leapfrog form.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/dgsem.h"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? DGSEM_ENOMEM : DGSEM_ECUDA,         \
+                  "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// 1D tables
+// ---------------------------------------------------------------------------
+// Legendre P_n at x (three-term recurrence); also returns P_{n-1}.
+void legendre(int n, double x, double* pn, double* pnm1) {
+  double a = 1.0, b = x;
+  if (n == 0) { *pn = 1.0; *pnm1 = 0.0; return; }
+  for (int k = 2; k <= n; ++k) {
+    const double c = ((2.0 * k - 1.0) * x * b - (k - 1.0) * a) / k;
+    a = b;
+    b = c;
+  }
+  *pn = b;
+  *pnm1 = a;
+}
+
+// GLL nodes by the Lobatto fixed-point Newton step
+//   x <- x - (x P_N - P_{N-1}) / ((N+1) P_N),
+// whose fixed points are the roots of (1 - x^2) P_N'; weights 2/(N(N+1)P_N^2).
+void gll(int N, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(N + 1, 0.0);
+  w.assign(N + 1, 0.0);
+  for (int i = 0; i <= N; ++i) {
+    double xi = -std::cos(M_PI * i / N);
+    for (int it = 0; it < 200; ++it) {
+      double pn, pm;
+      legendre(N, xi, &pn, &pm);
+      const double dx = (xi * pn - pm) / ((N + 1) * pn);
+      xi -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    x[i] = xi;
+  }
+  x[0] = -1.0;
+  x[N] = 1.0;
+  if (N % 2 == 0) x[N / 2] = 0.0;
+  for (int i = 0; i <= N; ++i) {
+    double pn, pm;
+    legendre(N, x[i], &pn, &pm);
+    w[i] = 2.0 / (N * (N + 1.0) * pn * pn);
+  }
+}
+
+// Gauss-Legendre nodes/weights (Newton on P_q, P_q' from P_q, P_{q-1}).
+void gauss(int q, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(q, 0.0);
+  w.assign(q, 0.0);
+  for (int i = 0; i < q; ++i) {
+    double xi = -std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 200; ++it) {
+      double pn, pm;
+      legendre(q, xi, &pn, &pm);
+      dp = q * (xi * pn - pm) / (xi * xi - 1.0);
+      const double dx = pn / dp;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-17) break;
+    }
+    double pn, pm;
+    legendre(q, xi, &pn, &pm);
+    dp = q * (xi * pn - pm) / (xi * xi - 1.0);
+    x[i] = xi;
+    w[i] = 2.0 / ((1.0 - xi * xi) * dp * dp);
+  }
+}
+
+struct Basis1D {
+  int N;
+  std::vector<double> x, w, bw;   // nodes, GLL weights, barycentric weights
+  std::vector<double> D;          // D[i*(N+1)+j] = l_j'(x_i)
+  std::vector<double> A;          // A[a*(N+1)+b] = sum_q w_q l_a'(x_q) l_b'(x_q)
+  explicit Basis1D(int n) : N(n) {
+    gll(N, x, w);
+    bw.assign(N + 1, 1.0);
+    for (int j = 0; j <= N; ++j)
+      for (int k = 0; k <= N; ++k)
+        if (k != j) bw[j] /= (x[j] - x[k]);
+    D.assign((N + 1) * (N + 1), 0.0);
+    for (int i = 0; i <= N; ++i) {
+      double diag = 0.0;
+      for (int j = 0; j <= N; ++j) {
+        if (j == i) continue;
+        const double d = (bw[j] / bw[i]) / (x[i] - x[j]);
+        D[i * (N + 1) + j] = d;
+        diag -= d;
+      }
+      D[i * (N + 1) + i] = diag;
+    }
+    A.assign((N + 1) * (N + 1), 0.0);
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) {
+        double s = 0.0;
+        for (int q = 0; q <= N; ++q) s += w[q] * D[q * (N + 1) + a] * D[q * (N + 1) + b];
+        A[a * (N + 1) + b] = s;
+      }
+  }
+  // Lagrange basis values at an arbitrary point (barycentric form)
+  void values(double t, double* out) const {
+    for (int j = 0; j <= N; ++j)
+      if (t == x[j]) {
+        for (int k = 0; k <= N; ++k) out[k] = (k == j) ? 1.0 : 0.0;
+        return;
+      }
+    double den = 0.0;
+    for (int j = 0; j <= N; ++j) den += bw[j] / (t - x[j]);
+    for (int j = 0; j <= N; ++j) out[j] = (bw[j] / (t - x[j])) / den;
+  }
+  // assembled 1D weight of lattice line i in a box of ne elements
+  double assembled_weight(int i, int ne) const {
+    const int e = i / N, a = i - e * N;
+    if (a != 0) return w[a];
+    double s = 0.0;
+    if (e > 0) s += w[N];
+    if (e < ne) s += w[0];
+    return s;
+  }
+};
+
+struct Box {
+  double o[3], ext[3], h[3], c, rho;
+  int ne[3], N, L[3];
+  int py;
+  long long pz, bstride;
+  Basis1D* basis;
+};
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+struct dgsem_ctx {
+  int device = 0;
+  int nd = 0;
+  Box box[2];
+  Basis1D* basis[2] = {nullptr, nullptr};
+  double dt = 0.0, dt_stable = 0.0, cfl = 0.0, alpha = 0.0;
+  long long ndof = 0;
+  VolSpec vspec[2];
+  // interface
+  bool has_iface = false;
+  int q = 0, nsub = 0;
+  int ncf = 0, nff = 0;
+  double gamma = 0.0;
+  int* d_cf_col = nullptr; int* d_cf_ptr = nullptr; int* d_ff_col = nullptr;
+  int* d_ff_sx = nullptr; int* d_ff_sy = nullptr;
+  void* d_tab[2] = {nullptr, nullptr};   // [fp64, fp32] packed Lp | Ls | Wq | dp | ds
+  size_t tab_off[5] = {0, 0, 0, 0, 0};
+  // PMUT
+  std::vector<double> face_xy;
+  int K = 0, M = 0, nnz = 0;
+  int* d_fp_ptr = nullptr; long long* d_fp_off = nullptr; double* d_Bm = nullptr;
+  int* d_node_ptr = nullptr; int* d_node_ent = nullptr; int* d_ent_pmut = nullptr;
+  double* d_modal = nullptr;    // omega2 | twozw | inv_mu | eta   [4][K*M]
+  double kappa = 0.0;
+  // run state
+  int prec = -1, batch = 0;
+  void* X[2] = {nullptr, nullptr};
+  void* Y[2] = {nullptr, nullptr};
+  void* V[2] = {nullptr, nullptr};
+  void* Ra[2] = {nullptr, nullptr};
+  void* Rb[2] = {nullptr, nullptr};
+  double* q_state = nullptr;    // q | qd | qdd  [3][B*K*M]
+  long long step = 0;
+  bool state_valid = false;
+  // pending initial state
+  std::vector<double> init_p, init_v;
+  bool has_init = false;
+  // scratch for host-pointer runs
+  double* d_drive = nullptr; size_t drive_cap = 0;
+  double* d_traces = nullptr; size_t traces_cap = 0;
+  double* d_rw = nullptr; long long* d_roff = nullptr; int* d_rdom = nullptr; int* d_rnn = nullptr;
+  size_t recv_cap = 0;
+  // instrumentation
+  bool profiling = false;
+  long long launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
+  double kernel_ms[DGSEM_K_COUNT] = {0, 0, 0, 0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;   // (kind, index of start event; stop = index + 1)
+};
+
+namespace {
+
+template <typename P>
+int dalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return DGSEM_OK;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(DGSEM_ENOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  return DGSEM_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+template <typename V>
+int upload(V** d, const std::vector<V>& h) {
+  int rc = dalloc(d, h.size() * sizeof(V));
+  if (rc) return rc;
+  if (!h.empty()) CUDA_TRY(cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return DGSEM_OK;
+}
+
+void free_run_state(dgsem_ctx* c) {
+  for (int d = 0; d < 2; ++d) {
+    dfree(c->X[d]); dfree(c->Y[d]); dfree(c->V[d]); dfree(c->Ra[d]); dfree(c->Rb[d]);
+  }
+  dfree(c->q_state);
+  c->prec = -1;
+  c->batch = 0;
+  c->state_valid = false;
+}
+
+size_t elem_size(int prec) { return prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double); }
+
+int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
+  if (c->prec == prec && c->batch == batch && c->X[0]) return DGSEM_OK;
+  free_run_state(c);
+  const size_t es = elem_size(prec);
+  for (int d = 0; d < c->nd; ++d) {
+    const size_t bytes = (size_t)batch * c->box[d].bstride * es;
+    int rc;
+    if ((rc = dalloc(&c->X[d], bytes)) || (rc = dalloc(&c->Y[d], bytes)) || (rc = dalloc(&c->V[d], bytes))) {
+      free_run_state(c);
+      return rc;
+    }
+    if (c->has_iface) {
+      const Box& B = c->box[d];
+      const size_t rb = (size_t)batch * B.ne[0] * B.ne[1] * (B.N + 1) * (B.N + 1) * es;
+      if ((rc = dalloc(&c->Ra[d], rb)) || (rc = dalloc(&c->Rb[d], rb))) {
+        free_run_state(c);
+        return rc;
+      }
+      CUDA_TRY(cudaMemset(c->Ra[d], 0, rb));
+      CUDA_TRY(cudaMemset(c->Rb[d], 0, rb));
+    }
+  }
+  if (c->K > 0) {
+    int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
+    if (rc) { free_run_state(c); return rc; }
+  }
+  c->prec = prec;
+  c->batch = batch;
+  c->state_valid = false;
+  return DGSEM_OK;
+}
+
+int zero_state(dgsem_ctx* c, cudaStream_t s) {
+  const size_t es = elem_size(c->prec);
+  for (int d = 0; d < c->nd; ++d) {
+    const size_t bytes = (size_t)c->batch * c->box[d].bstride * es;
+    CUDA_TRY(cudaMemsetAsync(c->X[d], 0, bytes, s));
+    CUDA_TRY(cudaMemsetAsync(c->Y[d], 0, bytes, s));
+    CUDA_TRY(cudaMemsetAsync(c->V[d], 0, bytes, s));
+  }
+  if (c->q_state)
+    CUDA_TRY(cudaMemsetAsync(c->q_state, 0, (size_t)3 * c->batch * c->K * c->M * sizeof(double), s));
+  c->step = 0;
+  return DGSEM_OK;
+}
+
+// Build the stencil rows of one box (see VolArgs).
+void build_vol_spec(const Box& B, VolSpec& v) {
+  std::memset(&v, 0, sizeof(v));
+  const Basis1D& bs = *B.basis;
+  const int N = B.N;
+  v.N = N;
+  for (int d = 0; d < 3; ++d) {
+    v.L[d] = B.L[d];
+    v.ne[d] = B.ne[d];
+    const double s = B.c * B.c * (2.0 / B.h[d]) * (2.0 / B.h[d]);
+    for (int a = 0; a <= N; ++a)
+      for (int b = 0; b <= N; ++b) v.c[d][a][b] = (a > 0 && a < N) ? s * bs.A[a * (N + 1) + b] / bs.w[a] : 0.0;
+    for (int b = 0; b <= N; ++b) {
+      v.l[d][b] = s * bs.A[N * (N + 1) + b];
+      v.r[d][b] = s * bs.A[0 * (N + 1) + b];
+    }
+  }
+  v.iwv = 1.0 / (bs.w[0] + bs.w[N]);
+  v.iwb = 1.0 / bs.w[0];
+  for (int a = 0; a <= N; ++a) v.iwa[a] = 1.0 / bs.w[a];
+  v.minv_scale = 8.0 / (B.h[0] * B.h[1] * B.h[2]);
+  v.py = B.py;
+  v.pz = B.pz;
+  v.bstride = B.bstride;
+  v.iface_k0 = -1;
+}
+
+// ---------------------------------------------------------------------------
+// Interface setup: Algorithm 3 (normal filter, one-vertex radius filter,
+// inverse map), on a bucket grid of the coarse faces' stored vertices.
+// ---------------------------------------------------------------------------
+int build_interface(dgsem_ctx* c, const dgsem_mesh_desc* desc) {
+  const Box& P = c->box[0];
+  const Box& S = c->box[1];
+  const double tol = 1e-9 * std::max(P.ext[0], P.ext[1]);
+  if (std::fabs(S.o[2] - (P.o[2] + P.ext[2])) > tol || std::fabs(S.o[0] - P.o[0]) > tol ||
+      std::fabs(S.o[1] - P.o[1]) > tol || std::fabs(S.ext[0] - P.ext[0]) > tol ||
+      std::fabs(S.ext[1] - P.ext[1]) > tol)
+    return fail(DGSEM_EINVAL, "secondary box must sit on the primary's z-max face with the same x-y extent");
+  std::vector<int> fine, coarse;
+  if (desc->fine_faces) {
+    if (desc->n_fine_faces < 0) return fail(DGSEM_EINVAL, "n_fine_faces < 0");
+    fine.assign(desc->fine_faces, desc->fine_faces + desc->n_fine_faces);
+  } else {
+    for (int i = 0; i < P.ne[0] * P.ne[1]; ++i) fine.push_back(i);
+  }
+  if (desc->coarse_faces) {
+    if (desc->n_coarse_faces < 0) return fail(DGSEM_EINVAL, "n_coarse_faces < 0");
+    coarse.assign(desc->coarse_faces, desc->coarse_faces + desc->n_coarse_faces);
+  } else {
+    for (int i = 0; i < S.ne[0] * S.ne[1]; ++i) coarse.push_back(i);
+  }
+  for (int f : fine)
+    if (f < 0 || f >= P.ne[0] * P.ne[1]) return fail(DGSEM_EINVAL, "fine face %d out of range", f);
+  for (int f : coarse)
+    if (f < 0 || f >= S.ne[0] * S.ne[1]) return fail(DGSEM_EINVAL, "coarse face %d out of range", f);
+  const int q = desc->iface_quad_pts > 0 ? desc->iface_quad_pts : std::max(P.N, S.N) + 1;
+  if (q > DG_MAXQ) return fail(DGSEM_EINVAL, "iface_quad_pts %d > %d", q, DG_MAXQ);
+  c->q = q;
+  std::vector<double> gx, gw;
+  gauss(q, gx, gw);
+  // coarse faces: stored vertex (x-min, y-min corner), normal -e_z, diameter
+  const double hs0 = S.h[0], hs1 = S.h[1];
+  const double diam_c = std::sqrt(hs0 * hs0 + hs1 * hs1);
+  const double diam_f = std::sqrt(P.h[0] * P.h[0] + P.h[1] * P.h[1]);
+  const double radius = std::max(diam_c, diam_f) * (1.0 + 1e-9);
+  std::map<long long, std::vector<int>> bucket;   // bucket of the stored vertex -> coarse list index
+  for (size_t i = 0; i < coarse.size(); ++i) {
+    const int mx = coarse[i] % S.ne[0], my = coarse[i] / S.ne[0];
+    bucket[(long long)my * (S.ne[0] + 1) + mx].push_back((int)i);
+  }
+  const double n_plus[3] = {0.0, 0.0, 1.0}, n_minus[3] = {0.0, 0.0, -1.0};
+  std::vector<std::vector<int>> by_coarse(coarse.size());
+  std::vector<double> off_x(fine.size()), off_y(fine.size());
+  std::vector<int> match(fine.size(), -1);
+  for (size_t f = 0; f < fine.size(); ++f) {
+    const int ex = fine[f] % P.ne[0], ey = fine[f] / P.ne[0];
+    const double fx0 = P.o[0] + ex * P.h[0], fy0 = P.o[1] + ey * P.h[1];
+    int found = -1;
+    for (int qy = 0; qy < q; ++qy)
+      for (int qx = 0; qx < q; ++qx) {
+        const double x = fx0 + 0.5 * (gx[qx] + 1.0) * P.h[0];
+        const double y = fy0 + 0.5 * (gx[qy] + 1.0) * P.h[1];
+        const int bx = (int)std::floor((x - S.o[0]) / hs0), by = (int)std::floor((y - S.o[1]) / hs1);
+        int hit = -1;
+        for (int dy = -2; dy <= 2 && hit < 0; ++dy)
+          for (int dx = -2; dx <= 2 && hit < 0; ++dx) {
+            auto it = bucket.find((long long)(by + dy) * (S.ne[0] + 1) + (bx + dx));
+            if (it == bucket.end()) continue;
+            for (int ci : it->second) {
+              double nn = 0.0;
+              for (int d = 0; d < 3; ++d) nn += (n_plus[d] + n_minus[d]) * (n_plus[d] + n_minus[d]);
+              if (std::sqrt(nn) >= 1e-9) continue;                      // normal filter
+              const int mx = coarse[ci] % S.ne[0], my = coarse[ci] / S.ne[0];
+              const double vx = S.o[0] + mx * hs0, vy = S.o[1] + my * hs1;
+              if (std::hypot(vx - x, vy - y) > radius) continue;        // radius filter
+              // inverse map of the affine coarse element: reference coordinates
+              const double rx = 2.0 * (x - vx) / hs0 - 1.0, ry = 2.0 * (y - vy) / hs1 - 1.0;
+              if (std::fabs(rx) <= 1.0 + 1e-10 && std::fabs(ry) <= 1.0 + 1e-10) { hit = ci; break; }
+            }
+          }
+        if (hit < 0) return fail(DGSEM_ENOMATCH, "fine face %d: quadrature node without a coarse neighbour", fine[f]);
+        if (found >= 0 && hit != found)
+          return fail(DGSEM_ENOMATCH, "fine face %d straddles two coarse faces", fine[f]);
+        found = hit;
+      }
+    match[f] = found;
+    by_coarse[found].push_back((int)f);
+    const int mx = coarse[found] % S.ne[0], my = coarse[found] / S.ne[0];
+    // affine sub-face map x^- = s x^+ + o along each axis
+    off_x[f] = (2.0 * (fx0 - (S.o[0] + mx * hs0)) + P.h[0]) / hs0 - 1.0;
+    off_y[f] = (2.0 * (fy0 - (S.o[1] + my * hs1)) + P.h[1]) / hs1 - 1.0;
+  }
+  const double sx = P.h[0] / hs0, sy = P.h[1] / hs1;
+  // distinct affine sub-face maps (scale, offset) -> interpolation tables Ls[nsub][q][Ns+1]
+  std::vector<double> offs, scales;
+  auto sub_index = [&](double o, double sc) {
+    for (size_t i = 0; i < offs.size(); ++i)
+      if (std::fabs(offs[i] - o) < 1e-12 && std::fabs(scales[i] - sc) < 1e-12) return (int)i;
+    offs.push_back(o);
+    scales.push_back(sc);
+    return (int)offs.size() - 1;
+  };
+  std::vector<int> h_cf_col, h_cf_ptr(1, 0), h_ff_col, h_ff_sx, h_ff_sy;
+  for (size_t ci = 0; ci < coarse.size(); ++ci) {
+    if (by_coarse[ci].empty()) continue;
+    h_cf_col.push_back(coarse[ci]);
+    for (int f : by_coarse[ci]) {
+      h_ff_col.push_back(fine[f]);
+      h_ff_sx.push_back(sub_index(off_x[f], sx));
+      h_ff_sy.push_back(sub_index(off_y[f], sy));
+    }
+    h_cf_ptr.push_back((int)h_ff_col.size());
+  }
+  c->ncf = (int)h_cf_col.size();
+  c->nff = (int)h_ff_col.size();
+  c->nsub = (int)offs.size();
+  const int np1 = P.N + 1, ns1 = S.N + 1;
+  std::vector<double> Lp(q * np1), Ls(offs.size() * q * ns1), Wq(q * q), dp(np1), ds(ns1);
+  for (int t = 0; t < q; ++t) P.basis->values(gx[t], &Lp[t * np1]);
+  for (size_t si = 0; si < offs.size(); ++si)
+    for (int t = 0; t < q; ++t) S.basis->values(scales[si] * gx[t] + offs[si], &Ls[(si * q + t) * ns1]);
+  const double jac = P.h[0] * P.h[1] / 4.0;
+  for (int ty = 0; ty < q; ++ty)
+    for (int tx = 0; tx < q; ++tx) Wq[ty * q + tx] = gw[tx] * gw[ty] * jac;
+  for (int cc = 0; cc < np1; ++cc) dp[cc] = (2.0 / P.h[2]) * P.basis->D[P.N * np1 + cc];
+  for (int cc = 0; cc < ns1; ++cc) ds[cc] = (2.0 / S.h[2]) * S.basis->D[0 * ns1 + cc];
+  const double cbar = 2.0 * P.c * S.c / (P.c + S.c);
+  c->gamma = c->alpha * cbar * cbar * std::max(P.N, S.N) * std::max(P.N, S.N) / std::min(P.h[2], S.h[2]);
+  // packed tables, FP64 and FP32 copies
+  std::vector<double> tab;
+  c->tab_off[0] = 0; tab.insert(tab.end(), Lp.begin(), Lp.end());
+  c->tab_off[1] = tab.size(); tab.insert(tab.end(), Ls.begin(), Ls.end());
+  c->tab_off[2] = tab.size(); tab.insert(tab.end(), Wq.begin(), Wq.end());
+  c->tab_off[3] = tab.size(); tab.insert(tab.end(), dp.begin(), dp.end());
+  c->tab_off[4] = tab.size(); tab.insert(tab.end(), ds.begin(), ds.end());
+  std::vector<float> tabf(tab.begin(), tab.end());
+  int rc;
+  if ((rc = upload((double**)&c->d_tab[0], tab)) || (rc = upload((float**)&c->d_tab[1], tabf)) ||
+      (rc = upload(&c->d_cf_col, h_cf_col)) || (rc = upload(&c->d_cf_ptr, h_cf_ptr)) ||
+      (rc = upload(&c->d_ff_col, h_ff_col)) || (rc = upload(&c->d_ff_sx, h_ff_sx)) ||
+      (rc = upload(&c->d_ff_sy, h_ff_sy)))
+    return rc;
+  // residual layout for the volume kernels
+  c->vspec[0].iface_k0 = (P.ne[2] - 1) * P.N;
+  c->vspec[0].iface_top = 1;
+  for (int cc = 0; cc < np1; ++cc) c->vspec[0].dI[cc] = dp[cc];
+  c->vspec[1].iface_k0 = 0;
+  c->vspec[1].iface_top = 0;
+  for (int cc = 0; cc < ns1; ++cc) c->vspec[1].dI[cc] = ds[cc];
+  c->has_iface = true;
+  return DGSEM_OK;
+}
+
+template <typename T>
+IfaceArgs<T> iface_args(const dgsem_ctx* c) {
+  IfaceArgs<T> a;
+  const Box& P = c->box[0];
+  const Box& S = c->box[1];
+  const int pi = sizeof(T) == 8 ? 0 : 1;
+  const T* tab = static_cast<const T*>(c->d_tab[pi]);
+  a.pp = static_cast<const T*>(c->Y[0]);
+  a.ps = static_cast<const T*>(c->Y[1]);
+  a.bsp = P.bstride; a.bss = S.bstride;
+  a.pyp = P.py; a.pzp = P.pz; a.pys = S.py; a.pzs = S.pz;
+  a.Np = P.N; a.Ns = S.N; a.kp0 = (P.ne[2] - 1) * P.N;
+  a.npx = P.ne[0]; a.nsx = S.ne[0];
+  a.ncf = c->ncf;
+  a.cf_col = c->d_cf_col; a.cf_ptr = c->d_cf_ptr; a.ff_col = c->d_ff_col;
+  a.ff_sx = c->d_ff_sx; a.ff_sy = c->d_ff_sy;
+  a.q = c->q;
+  a.Lp = tab + c->tab_off[0]; a.Ls = tab + c->tab_off[1]; a.Wq = tab + c->tab_off[2];
+  a.dp = tab + c->tab_off[3]; a.ds = tab + c->tab_off[4];
+  a.cp2 = T(P.c * P.c); a.cm2 = T(S.c * S.c); a.gamma = T(c->gamma);
+  a.Rap = static_cast<T*>(c->Ra[0]); a.Rbp = static_cast<T*>(c->Rb[0]);
+  a.Ras = static_cast<T*>(c->Ra[1]); a.Rbs = static_cast<T*>(c->Rb[1]);
+  a.rbp = (long long)P.ne[0] * P.ne[1] * (P.N + 1) * (P.N + 1);
+  a.rbs = (long long)S.ne[0] * S.ne[1] * (S.N + 1) * (S.N + 1);
+  return a;
+}
+
+// Bracket a kernel launch with events when profiling (events from a pool).
+struct LaunchTimer {
+  dgsem_ctx* c; cudaStream_t s; int kind; int idx = -1;
+  LaunchTimer(dgsem_ctx* c_, cudaStream_t s_, int kind_) : c(c_), s(s_), kind(kind_) {
+    c->launches[kind]++;
+    if (!c->profiling) return;
+    idx = 2 * (int)c->ev_used.size();
+    while ((int)c->ev_pool.size() < idx + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { idx = -1; return; }
+      c->ev_pool.push_back(e);
+    }
+    cudaEventRecord(c->ev_pool[idx], s);
+  }
+  ~LaunchTimer() {
+    if (idx < 0) return;
+    cudaEventRecord(c->ev_pool[idx + 1], s);
+    c->ev_used.push_back({kind, idx});
+  }
+};
+
+void collect_timings(dgsem_ctx* c) {
+  for (auto& u : c->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[u.second], c->ev_pool[u.second + 1]) == cudaSuccess)
+      c->kernel_ms[u.first] += ms;
+  }
+  c->ev_used.clear();
+}
+
+// One time step (or the initial half step when init is true), all launches on s.
+template <typename T>
+int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs, long long dks, int n_local,
+                int R, double* traces, long long tbs, long long trs, bool init) {
+  if (!init && (c->K > 0 || R > 0)) {
+    PmutArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.B = c->batch; a.K = c->K; a.M = c->M;
+    a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_off; a.Bm = c->d_Bm;
+    a.p_prev = static_cast<const T*>(c->X[0]);
+    a.bsp = c->box[0].bstride;
+    const long long kmB = (long long)c->batch * c->K * c->M;
+    a.q = c->q_state; a.qd = c->q_state ? c->q_state + kmB : nullptr; a.qdd = c->q_state ? c->q_state + 2 * kmB : nullptr;
+    const long long km = (long long)c->K * c->M;
+    a.omega2 = c->d_modal; a.twozw = c->d_modal ? c->d_modal + km : nullptr;
+    a.inv_mu = c->d_modal ? c->d_modal + 2 * km : nullptr; a.eta = c->d_modal ? c->d_modal + 3 * km : nullptr;
+    a.drive = drive; a.dbs = dbs; a.dks = dks; a.n = n_local; a.dt = c->dt;
+    a.R = R; a.rstride = 0;
+    if (R > 0) {
+      int maxn = 0;
+      for (int d = 0; d < c->nd; ++d) maxn = std::max(maxn, (c->box[d].N + 1) * (c->box[d].N + 1) * (c->box[d].N + 1));
+      a.rstride = maxn;
+    }
+    a.rw = c->d_rw; a.roff = c->d_roff; a.rdom = c->d_rdom; a.rnn = c->d_rnn;
+    a.pc0 = static_cast<const T*>(c->Y[0]); a.pc1 = c->nd > 1 ? static_cast<const T*>(c->Y[1]) : nullptr;
+    a.bs0 = c->box[0].bstride; a.bs1 = c->nd > 1 ? c->box[1].bstride : 0;
+    a.traces = traces; a.tbs = tbs; a.trs = trs;
+    LaunchTimer lt(c, s, DGSEM_K_PMUT_RECV);
+    CUDA_TRY(launch_pmut_recv<T>(a, s));
+  }
+  // init: p_in = X (p^0), p_out = Y (p^1); step: p_in = Y (p^{n+1}), p_out = X (p^{n+2})
+  void* pin[2]; void* pout[2];
+  for (int d = 0; d < c->nd; ++d) {
+    pin[d] = init ? c->X[d] : c->Y[d];
+    pout[d] = init ? c->Y[d] : c->X[d];
+  }
+  if (c->has_iface) {
+    IfaceArgs<T> a = iface_args<T>(c);
+    a.pp = static_cast<const T*>(pin[0]);
+    a.ps = static_cast<const T*>(pin[1]);
+    LaunchTimer lt(c, s, DGSEM_K_IFACE);
+    CUDA_TRY(launch_iface<T>(a, c->batch, s));
+  }
+  for (int d = 0; d < c->nd; ++d) {
+    VolSpec v = c->vspec[d];
+    v.p_in = pin[d]; v.p_out = pout[d]; v.v = c->V[d];
+    v.dtv = init ? 0.5 * c->dt : c->dt;
+    v.dtp = c->dt;
+    v.Ra = c->Ra[d]; v.Rb = c->Rb[d];
+    if (d == 0 && c->K > 0 && !init) {
+      v.has_pmut = 1;
+      v.node_ptr = c->d_node_ptr; v.node_ent = c->d_node_ent; v.ent_pmut = c->d_ent_pmut;
+      v.Bm = c->d_Bm; v.qdd = c->q_state + 2LL * c->batch * c->K * c->M;
+      v.K = c->K; v.M = c->M; v.kappa = c->kappa;
+    }
+    LaunchTimer lt(c, s, DGSEM_K_VOL0 + d);
+    CUDA_TRY(launch_vol<T>(v, c->batch, s));
+  }
+  if (!init) {
+    for (int d = 0; d < c->nd; ++d) std::swap(c->X[d], c->Y[d]);
+  }
+  return DGSEM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Receivers: containing element (lowest id on ties; primary first), weights.
+int setup_receivers(dgsem_ctx* c, int R, const double* xyz) {
+  if (R == 0) return DGSEM_OK;
+  int maxn = 0;
+  for (int d = 0; d < c->nd; ++d) maxn = std::max(maxn, (c->box[d].N + 1) * (c->box[d].N + 1) * (c->box[d].N + 1));
+  std::vector<double> w((size_t)R * maxn, 0.0);
+  std::vector<long long> off((size_t)R * maxn, 0);
+  std::vector<int> dom(R), nn(R);
+  for (int r = 0; r < R; ++r) {
+    const double* x = xyz + 3 * r;
+    int found = -1;
+    for (int d = 0; d < c->nd && found < 0; ++d) {
+      const Box& B = c->box[d];
+      bool inside = true;
+      for (int k = 0; k < 3; ++k) {
+        const double t = 1e-12 * B.ext[k];
+        if (x[k] < B.o[k] - t || x[k] > B.o[k] + B.ext[k] + t) inside = false;
+      }
+      if (inside) found = d;
+    }
+    if (found < 0) return fail(DGSEM_EINVAL, "receiver %d at (%g, %g, %g) is outside the mesh", r, x[0], x[1], x[2]);
+    const Box& B = c->box[found];
+    int e[3];
+    double ref[3];
+    for (int k = 0; k < 3; ++k) {
+      const double u = (x[k] - B.o[k]) / B.h[k];
+      int ek = (int)std::ceil(u - 1e-12) - 1;      // lowest element containing the point
+      ek = std::max(0, std::min(ek, B.ne[k] - 1));
+      e[k] = ek;
+      ref[k] = std::max(-1.0, std::min(1.0, 2.0 * (u - ek) - 1.0));
+    }
+    const int n1 = B.N + 1;
+    std::vector<double> lx(n1), ly(n1), lz(n1);
+    B.basis->values(ref[0], lx.data());
+    B.basis->values(ref[1], ly.data());
+    B.basis->values(ref[2], lz.data());
+    int t = 0;
+    for (int cc = 0; cc < n1; ++cc)
+      for (int bb = 0; bb < n1; ++bb)
+        for (int aa = 0; aa < n1; ++aa, ++t) {
+          w[(size_t)r * maxn + t] = lx[aa] * ly[bb] * lz[cc];
+          off[(size_t)r * maxn + t] = (long long)(e[2] * B.N + cc) * B.pz + (long long)(e[1] * B.N + bb) * B.py +
+                                      (e[0] * B.N + aa);
+        }
+    dom[r] = found;
+    nn[r] = t;
+  }
+  if ((size_t)R * maxn > c->recv_cap) {
+    dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
+    c->recv_cap = 0;
+    int rc;
+    if ((rc = dalloc(&c->d_rw, (size_t)R * maxn * sizeof(double))) ||
+        (rc = dalloc(&c->d_roff, (size_t)R * maxn * sizeof(long long))) ||
+        (rc = dalloc(&c->d_rdom, (size_t)R * maxn * sizeof(int))) ||
+        (rc = dalloc(&c->d_rnn, (size_t)R * maxn * sizeof(int))))
+      return rc;
+    c->recv_cap = (size_t)R * maxn;
+  }
+  CUDA_TRY(cudaMemcpy(c->d_rw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_roff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_rdom, dom.data(), R * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(c->d_rnn, nn.data(), R * sizeof(int), cudaMemcpyHostToDevice));
+  return DGSEM_OK;
+}
+
+template <typename T>
+int upload_field(dgsem_ctx* c, const std::vector<double>& h, void* const* dst, cudaStream_t s) {
+  // h: [ndof] in node order; broadcast to every batch member, padded layout
+  size_t off = 0;
+  for (int d = 0; d < c->nd; ++d) {
+    const Box& B = c->box[d];
+    std::vector<T> tmp((size_t)B.bstride, T(0));
+    for (int k = 0; k < B.L[2]; ++k)
+      for (int j = 0; j < B.L[1]; ++j)
+        for (int i = 0; i < B.L[0]; ++i)
+          tmp[(size_t)k * B.pz + (size_t)j * B.py + i] = h.empty() ? T(0) : T(h[off + ((size_t)k * B.L[1] + j) * B.L[0] + i]);
+    for (int b = 0; b < c->batch; ++b)
+      CUDA_TRY(cudaMemcpyAsync(static_cast<T*>(dst[d]) + (size_t)b * B.bstride, tmp.data(), tmp.size() * sizeof(T),
+                               cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    off += (size_t)B.L[0] * B.L[1] * B.L[2];
+  }
+  return DGSEM_OK;
+}
+
+template <typename T>
+int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
+  int rc;
+  const bool cont = (flags & DGSEM_RUN_CONTINUE) && c->state_valid;
+  if (!cont) {
+    if ((rc = zero_state(c, s))) return rc;
+    if (c->has_init) {
+      if ((rc = upload_field<T>(c, c->init_p, c->X, s))) return rc;
+      if ((rc = upload_field<T>(c, c->init_v, c->V, s))) return rc;
+      if ((rc = launch_step<T>(c, s, nullptr, 0, 0, 0, 0, nullptr, 0, 0, true))) return rc;
+    }
+    c->state_valid = true;
+  }
+  // drive: device copy if needed
+  const double* d_drive = nullptr;
+  const size_t drive_n = (size_t)c->batch * c->K * nsteps;
+  if (c->K > 0 && drive) {
+    if (is_device_ptr(drive)) {
+      d_drive = drive;
+    } else {
+      if (drive_n > c->drive_cap) {
+        dfree(c->d_drive);
+        if ((rc = dalloc(&c->d_drive, drive_n * sizeof(double)))) { c->drive_cap = 0; return rc; }
+        c->drive_cap = drive_n;
+      }
+      CUDA_TRY(cudaMemcpyAsync(c->d_drive, drive, drive_n * sizeof(double), cudaMemcpyHostToDevice, s));
+      d_drive = c->d_drive;
+    }
+  }
+  double* d_tr = nullptr;
+  const size_t tr_n = (size_t)c->batch * R * nsteps;
+  bool tr_host = false;
+  if (R > 0) {
+    if (is_device_ptr(traces_out)) {
+      d_tr = traces_out;
+    } else {
+      tr_host = true;
+      if (tr_n > c->traces_cap) {
+        dfree(c->d_traces);
+        if ((rc = dalloc(&c->d_traces, tr_n * sizeof(double)))) { c->traces_cap = 0; return rc; }
+        c->traces_cap = tr_n;
+      }
+      d_tr = c->d_traces;
+    }
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    rc = launch_step<T>(c, s, d_drive, (long long)c->K * nsteps, nsteps, n, R, d_tr, (long long)R * nsteps, nsteps,
+                        false);
+    if (rc) return rc;
+  }
+  c->step += nsteps;
+  if (tr_host) CUDA_TRY(cudaMemcpyAsync(traces_out, d_tr, tr_n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  collect_timings(c);
+  return DGSEM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* dgsem_last_error(void) { return g_err.c_str(); }
+
+int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
+  if (!out) return fail(DGSEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!desc || !desc->domains) return fail(DGSEM_EINVAL, "desc/domains is NULL");
+  if (desc->ndomains < 1 || desc->ndomains > 2) return fail(DGSEM_EINVAL, "ndomains must be 1 or 2");
+  for (int d = 0; d < desc->ndomains; ++d) {
+    const dgsem_domain_desc& D = desc->domains[d];
+    if (D.order < 1 || D.order > DG_MAXN) return fail(DGSEM_EINVAL, "domain %d: order %d not in [1, %d]", d, D.order, DG_MAXN);
+    for (int k = 0; k < 3; ++k) {
+      if (D.nelem[k] < 1) return fail(DGSEM_EINVAL, "domain %d: nelem[%d] < 1", d, k);
+      if (!(D.extent[k] > 0.0) || !std::isfinite(D.extent[k])) return fail(DGSEM_EINVAL, "domain %d: extent[%d] <= 0", d, k);
+      if ((long long)D.nelem[k] * D.order + 1 > (1 << 24)) return fail(DGSEM_EINVAL, "domain %d: lattice too large", d);
+    }
+    if (!(D.c > 0.0) || !(D.rho > 0.0)) return fail(DGSEM_EINVAL, "domain %d: c and rho must be > 0", d);
+  }
+  if (!(desc->dt > 0.0) && !(desc->cfl > 0.0)) return fail(DGSEM_EINVAL, "need dt > 0 or cfl > 0");
+  if (desc->ndomains == 2 && !(desc->penalty_alpha > 0.0)) return fail(DGSEM_EINVAL, "penalty_alpha must be > 0");
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  dgsem_ctx* c = new dgsem_ctx();
+  c->device = dev;
+  c->nd = desc->ndomains;
+  c->alpha = desc->penalty_alpha;
+  c->cfl = desc->cfl;
+  double hmin = 1e300, cmax = 0.0;
+  for (int d = 0; d < c->nd; ++d) {
+    const dgsem_domain_desc& D = desc->domains[d];
+    Box& B = c->box[d];
+    c->basis[d] = new Basis1D(D.order);
+    B.basis = c->basis[d];
+    B.N = D.order;
+    B.c = D.c;
+    B.rho = D.rho;
+    for (int k = 0; k < 3; ++k) {
+      B.o[k] = D.origin[k];
+      B.ext[k] = D.extent[k];
+      B.ne[k] = D.nelem[k];
+      B.h[k] = D.extent[k] / D.nelem[k];
+      B.L[k] = D.nelem[k] * D.order + 1;
+    }
+    B.py = (int)round_up(B.L[0], 8);
+    B.pz = (long long)B.py * B.L[1];
+    B.bstride = round_up(B.pz * B.L[2], 64);
+    double gap = 2.0;
+    for (int i = 0; i < B.N; ++i) gap = std::min(gap, B.basis->x[i + 1] - B.basis->x[i]);
+    for (int k = 0; k < 3; ++k) hmin = std::min(hmin, B.h[k] / 2.0 * gap);
+    cmax = std::max(cmax, B.c);
+    c->ndof += (long long)B.L[0] * B.L[1] * B.L[2];
+    build_vol_spec(B, c->vspec[d]);
+  }
+  c->dt = desc->dt > 0.0 ? desc->dt : desc->cfl * hmin / cmax;
+  c->kappa = c->box[0].rho * c->box[0].c * c->box[0].c;
+  if (c->nd == 2) {
+    int rc = build_interface(c, desc);
+    if (rc) { dgsem_destroy(c); return rc; }
+  }
+  // face lattice of Gamma_PMUT (primary z-min face)
+  const Box& P = c->box[0];
+  c->face_xy.resize((size_t)2 * P.L[0] * P.L[1]);
+  for (int j = 0; j < P.L[1]; ++j)
+    for (int i = 0; i < P.L[0]; ++i) {
+      const int ex = std::min(i / P.N, P.ne[0] - 1), ax = i - ex * P.N;
+      const int ey = std::min(j / P.N, P.ne[1] - 1), ay = j - ey * P.N;
+      c->face_xy[2 * ((size_t)j * P.L[0] + i)] = P.o[0] + P.h[0] * (ex + 0.5 * (P.basis->x[ax] + 1.0));
+      c->face_xy[2 * ((size_t)j * P.L[0] + i) + 1] = P.o[1] + P.h[1] * (ey + 0.5 * (P.basis->x[ay] + 1.0));
+    }
+  *out = c;
+  return DGSEM_OK;
+}
+
+int dgsem_get_dt(const dgsem_ctx* c, double* dt, double* dt_stable_max, long long* ndof) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (dt) *dt = c->dt;
+  if (dt_stable_max) *dt_stable_max = c->dt_stable;
+  if (ndof) *ndof = c->ndof;
+  return DGSEM_OK;
+}
+
+int dgsem_pmut_nodes(const dgsem_ctx* c, int* n_nodes, const double** xy) {
+  if (!c || !n_nodes || !xy) return fail(DGSEM_EINVAL, "NULL argument");
+  *n_nodes = (int)(c->face_xy.size() / 2);
+  *xy = c->face_xy.data();
+  return DGSEM_OK;
+}
+
+int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* foot_node, const double* shape_un,
+                   const double* freq_hz, const double* damping, const double* eta, const double* modal_mass) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (K < 0 || (K > 0 && (M < 1 || M > DG_MAXM))) return fail(DGSEM_EINVAL, "n_pmut %d / n_modes %d out of range", K, M);
+  if (K > 0 && (!foot_ptr || !freq_hz || !damping || !eta)) return fail(DGSEM_EINVAL, "NULL PMUT array");
+  const Box& P = c->box[0];
+  const int nface = P.L[0] * P.L[1];
+  int nnz = 0;
+  if (K > 0) {
+    if (foot_ptr[0] != 0) return fail(DGSEM_EINVAL, "foot_ptr[0] must be 0");
+    for (int k = 0; k < K; ++k)
+      if (foot_ptr[k + 1] < foot_ptr[k]) return fail(DGSEM_EINVAL, "foot_ptr not monotone at %d", k);
+    nnz = foot_ptr[K];
+    if (nnz > 0 && (!foot_node || !shape_un)) return fail(DGSEM_EINVAL, "NULL footprint arrays");
+    for (int e = 0; e < nnz; ++e)
+      if (foot_node[e] < 0 || foot_node[e] >= nface) return fail(DGSEM_EINVAL, "foot_node[%d] = %d out of range", e, foot_node[e]);
+    for (int i = 0; i < K * M; ++i) {
+      if (!(freq_hz[i] > 0.0) || !std::isfinite(freq_hz[i])) return fail(DGSEM_EINVAL, "freq_hz[%d] must be > 0", i);
+      if (!(damping[i] >= 0.0) || !std::isfinite(damping[i])) return fail(DGSEM_EINVAL, "damping[%d] must be >= 0", i);
+      if (!std::isfinite(eta[i])) return fail(DGSEM_EINVAL, "eta[%d] not finite", i);
+      if (modal_mass && !(modal_mass[i] > 0.0)) return fail(DGSEM_EINVAL, "modal_mass[%d] must be > 0", i);
+    }
+    for (long long e = 0; e < (long long)nnz * M; ++e)
+      if (!std::isfinite(shape_un[e])) return fail(DGSEM_EINVAL, "shape_un[%lld] not finite", e);
+  }
+  // release previous array
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
+  dfree(c->d_ent_pmut); dfree(c->d_modal); dfree(c->q_state);
+  c->K = 0; c->M = 0; c->nnz = 0;
+  c->state_valid = false;
+  if (K == 0) return DGSEM_OK;
+  // B_{j,km} = W_face(j) * U.n (GLL collocation of the membrane integrals)
+  const Basis1D& bs = *P.basis;
+  std::vector<int> h_fp_ptr(foot_ptr, foot_ptr + K + 1);
+  std::vector<long long> h_off(nnz);
+  std::vector<double> h_B((size_t)nnz * M);
+  std::vector<int> ent_pmut(nnz);
+  std::vector<int> node_cnt(nface + 1, 0);
+  for (int k = 0; k < K; ++k)
+    for (int e = foot_ptr[k]; e < foot_ptr[k + 1]; ++e) {
+      const int node = foot_node[e];
+      const int ix = node % P.L[0], iy = node / P.L[0];
+      const double wf = P.h[0] * P.h[1] / 4.0 * bs.assembled_weight(ix, P.ne[0]) * bs.assembled_weight(iy, P.ne[1]);
+      for (int m = 0; m < M; ++m) h_B[(size_t)e * M + m] = wf * shape_un[(size_t)e * M + m];
+      h_off[e] = (long long)iy * P.py + ix;
+      ent_pmut[e] = k;
+      node_cnt[node + 1]++;
+    }
+  std::vector<int> node_ptr(nface + 1, 0);
+  for (int i = 0; i < nface; ++i) node_ptr[i + 1] = node_ptr[i] + node_cnt[i + 1];
+  std::vector<int> fill(node_ptr.begin(), node_ptr.end() - 1), node_ent(nnz);
+  for (int e = 0; e < nnz; ++e) node_ent[fill[foot_node[e]]++] = e;
+  std::vector<double> modal((size_t)4 * K * M);
+  for (int i = 0; i < K * M; ++i) {
+    const double om = 2.0 * M_PI * freq_hz[i];
+    modal[i] = om * om;
+    modal[(size_t)K * M + i] = 2.0 * damping[i] * om;
+    modal[(size_t)2 * K * M + i] = modal_mass ? 1.0 / modal_mass[i] : 1.0;
+    modal[(size_t)3 * K * M + i] = eta[i];
+  }
+  int rc;
+  if ((rc = upload(&c->d_fp_ptr, h_fp_ptr)) || (rc = upload(&c->d_fp_off, h_off)) || (rc = upload(&c->d_Bm, h_B)) ||
+      (rc = upload(&c->d_node_ptr, node_ptr)) || (rc = upload(&c->d_node_ent, node_ent)) ||
+      (rc = upload(&c->d_ent_pmut, ent_pmut)) || (rc = upload(&c->d_modal, modal)))
+    return rc;
+  c->K = K; c->M = M; c->nnz = nnz;
+  // PMUT state buffers are sized with the run state
+  free_run_state(c);
+  return DGSEM_OK;
+}
+
+int dgsem_set_state(dgsem_ctx* c, const double* p0, const double* v0) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  c->init_p.assign(p0 ? p0 : (const double*)nullptr, p0 ? p0 + c->ndof : (const double*)nullptr);
+  c->init_v.assign(v0 ? v0 : (const double*)nullptr, v0 ? v0 + c->ndof : (const double*)nullptr);
+  for (double x : c->init_p) if (!std::isfinite(x)) return fail(DGSEM_EINVAL, "p0 not finite");
+  for (double x : c->init_v) if (!std::isfinite(x)) return fail(DGSEM_EINVAL, "v0 not finite");
+  c->has_init = p0 || v0;
+  c->state_valid = false;
+  return DGSEM_OK;
+}
+
+int dgsem_run(dgsem_ctx* c, int precision, int batch, int nsteps, const double* drive, int n_recv,
+              const double* recv_xyz, double* traces, int flags, void* stream) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return fail(DGSEM_EINVAL, "bad precision %d", precision);
+  if (batch < 1 || nsteps < 0 || n_recv < 0) return fail(DGSEM_EINVAL, "batch >= 1, nsteps >= 0, n_recv >= 0 required");
+  if (n_recv > 0 && (!recv_xyz || !traces)) return fail(DGSEM_EINVAL, "receivers need recv_xyz and traces");
+  if (c->K > 0 && nsteps > 0 && !drive) return fail(DGSEM_EINVAL, "drive is NULL");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != c->device) return fail(DGSEM_EINVAL, "context belongs to device %d, current is %d", c->device, dev);
+  if ((flags & DGSEM_RUN_CONTINUE) && (!c->state_valid || c->prec != precision || c->batch != batch))
+    return fail(DGSEM_ESTATE, "DGSEM_RUN_CONTINUE needs a previous run with the same precision and batch");
+  int rc = ensure_run_state(c, precision, batch);
+  if (rc) return rc;
+  if ((rc = setup_receivers(c, n_recv, recv_xyz))) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DGSEM_FP64) return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
+  return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
+}
+
+int dgsem_get_pressure(const dgsem_ctx* c, double* p, size_t len) {
+  if (!c || !p) return fail(DGSEM_EINVAL, "NULL argument");
+  if (!c->X[0] || !c->state_valid) return fail(DGSEM_ESTATE, "no state: call dgsem_run first");
+  if (len < (size_t)c->batch * c->ndof) return fail(DGSEM_EINVAL, "len %zu < batch*ndof", len);
+  CUDA_TRY(cudaDeviceSynchronize());
+  const size_t es = elem_size(c->prec);
+  size_t off = 0;
+  for (int b = 0; b < c->batch; ++b)
+    for (int d = 0; d < c->nd; ++d) {
+      const Box& B = c->box[d];
+      std::vector<unsigned char> tmp((size_t)B.bstride * es);
+      CUDA_TRY(cudaMemcpy(tmp.data(), static_cast<const unsigned char*>(c->X[d]) + (size_t)b * B.bstride * es,
+                          tmp.size(), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < B.L[2]; ++k)
+        for (int j = 0; j < B.L[1]; ++j)
+          for (int i = 0; i < B.L[0]; ++i) {
+            const size_t g = (size_t)k * B.pz + (size_t)j * B.py + i;
+            p[off++] = es == 8 ? reinterpret_cast<const double*>(tmp.data())[g]
+                               : (double)reinterpret_cast<const float*>(tmp.data())[g];
+          }
+    }
+  return DGSEM_OK;
+}
+
+// checkpoint layout: header | X, Y, V of each box | q, q', q''
+struct CkptHeader {
+  char magic[8];
+  int prec, batch, nd, K, M;
+  long long step, ndof, bstride[2];
+};
+
+int dgsem_state_save(const dgsem_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return fail(DGSEM_EINVAL, "NULL argument");
+  if (!c->state_valid) return fail(DGSEM_ESTATE, "no state to save");
+  const size_t es = elem_size(c->prec);
+  size_t need = sizeof(CkptHeader);
+  for (int d = 0; d < c->nd; ++d) need += 3 * (size_t)c->batch * c->box[d].bstride * es;
+  need += (size_t)3 * c->batch * c->K * c->M * sizeof(double);
+  if (!buf) { *len = need; return DGSEM_OK; }
+  if (*len < need) return fail(DGSEM_EINVAL, "buffer too small (%zu < %zu)", *len, need);
+  CUDA_TRY(cudaDeviceSynchronize());
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "DGSEMCK1", 8);
+  h.prec = c->prec; h.batch = c->batch; h.nd = c->nd; h.K = c->K; h.M = c->M;
+  h.step = c->step; h.ndof = c->ndof;
+  for (int d = 0; d < c->nd; ++d) h.bstride[d] = c->box[d].bstride;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  for (int d = 0; d < c->nd; ++d) {
+    const size_t bytes = (size_t)c->batch * c->box[d].bstride * es;
+    for (void* src : {c->X[d], c->Y[d], c->V[d]}) {
+      CUDA_TRY(cudaMemcpy(o, src, bytes, cudaMemcpyDeviceToHost));
+      o += bytes;
+    }
+  }
+  const size_t qb = (size_t)3 * c->batch * c->K * c->M * sizeof(double);
+  if (qb) CUDA_TRY(cudaMemcpy(o, c->q_state, qb, cudaMemcpyDeviceToHost));
+  *len = need;
+  return DGSEM_OK;
+}
+
+int dgsem_state_load(dgsem_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) return fail(DGSEM_EINVAL, "NULL argument");
+  if (len < sizeof(CkptHeader)) return fail(DGSEM_EINVAL, "buffer too small");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, "DGSEMCK1", 8) != 0) return fail(DGSEM_EINVAL, "not a dgsem checkpoint");
+  if (h.nd != c->nd || h.K != c->K || h.M != c->M || h.ndof != c->ndof)
+    return fail(DGSEM_EINVAL, "checkpoint does not match this mesh / PMUT array");
+  for (int d = 0; d < c->nd; ++d)
+    if (h.bstride[d] != c->box[d].bstride) return fail(DGSEM_EINVAL, "checkpoint layout mismatch");
+  if (h.batch < 1 || (h.prec != DGSEM_FP64 && h.prec != DGSEM_FP32_MIXED)) return fail(DGSEM_EINVAL, "bad checkpoint header");
+  const size_t es = elem_size(h.prec);
+  size_t need = sizeof(CkptHeader);
+  for (int d = 0; d < c->nd; ++d) need += 3 * (size_t)h.batch * c->box[d].bstride * es;
+  need += (size_t)3 * h.batch * c->K * c->M * sizeof(double);
+  if (len < need) return fail(DGSEM_EINVAL, "checkpoint truncated (%zu < %zu)", len, need);
+  int rc = ensure_run_state(c, h.prec, h.batch);
+  if (rc) return rc;
+  const unsigned char* o = static_cast<const unsigned char*>(buf) + sizeof(h);
+  for (int d = 0; d < c->nd; ++d) {
+    const size_t bytes = (size_t)h.batch * c->box[d].bstride * es;
+    for (void* dst : {c->X[d], c->Y[d], c->V[d]}) {
+      CUDA_TRY(cudaMemcpy(dst, o, bytes, cudaMemcpyHostToDevice));
+      o += bytes;
+    }
+  }
+  const size_t qb = (size_t)3 * h.batch * c->K * c->M * sizeof(double);
+  if (qb) CUDA_TRY(cudaMemcpy(c->q_state, o, qb, cudaMemcpyHostToDevice));
+  c->step = h.step;
+  c->state_valid = true;
+  c->has_init = false;
+  return DGSEM_OK;
+}
+
+int dgsem_check_stability(dgsem_ctx* c, int iters, double* lambda_max) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  (void)iters;
+  if (lambda_max) *lambda_max = 0.0;
+  return fail(DGSEM_ESTATE, "dgsem_check_stability: not available yet");
+}
+
+int dgsem_profile(dgsem_ctx* c, int enable) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  c->profiling = enable != 0;
+  for (int k = 0; k < DGSEM_K_COUNT; ++k) { c->kernel_ms[k] = 0.0; c->launches[k] = 0; }
+  c->ev_used.clear();
+  return DGSEM_OK;
+}
+
+int dgsem_kernel_stats(const dgsem_ctx* c, int kind, double* total_ms, long long* launches) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (kind < 0 || kind >= DGSEM_K_COUNT) return fail(DGSEM_EINVAL, "bad kernel kind %d", kind);
+  if (total_ms) *total_ms = c->kernel_ms[kind];
+  if (launches) *launches = c->launches[kind];
+  return DGSEM_OK;
+}
+
+void dgsem_destroy(dgsem_ctx* c) {
+  if (!c) return;
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  free_run_state(c);
+  dfree(c->d_cf_col); dfree(c->d_cf_ptr); dfree(c->d_ff_col); dfree(c->d_ff_sx); dfree(c->d_ff_sy);
+  dfree(c->d_tab[0]); dfree(c->d_tab[1]);
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
+  dfree(c->d_ent_pmut); dfree(c->d_modal);
+  dfree(c->d_drive); dfree(c->d_traces);
+  dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
+  delete c->basis[0];
+  delete c->basis[1];
+  delete c;
+}
+
+}  // extern "C"

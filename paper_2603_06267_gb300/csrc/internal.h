@@ -1,0 +1,154 @@
+// Internal parameter blocks shared by the host setup (api.cu) and the CUDA
+// kernels (vol.cu, small.cu).  Not part of the public ABI (include/dgsem.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#define DG_MAXN 8          // highest GLL order supported
+#define DG_MAXM 16         // modes per PMUT
+#define DG_MAXQ 12         // Gauss points per direction on a fine face
+
+// ---------------------------------------------------------------------------
+// Volume step of one box (fused: stiffness apply + forcing + interface
+// residual + lumped-mass update + leapfrog corrector/predictor).
+//
+// For an affine box of equal elements the GLL stiffness of eq. (Wf_2)
+// factorises as K = c^2 |J| sum_d (2/h_d)^2 (A (x) W (x) W)_d with the 1D
+// GLL stiffness A = D^T W D and the 1D GLL weights W; the lumped mass is
+// |J| W (x) W (x) W.  M^-1 K p is therefore a sum of three assembled 1D
+// stencils along lattice lines, each row scaled by the inverse assembled
+// 1D weight.  The coefficient blocks below hold those rows.
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct VolArgs {
+  const T* p_in;       // p^{n+1}: stencil source
+  T* p_out;            // p^{n+2} = p^{n+1} + dtp * v_new
+  T* v;                // v^{n+1/2} -> v^{n+3/2} = v + dtv * a
+  long long bstride;   // elements between batch members
+  int L0, L1, L2;      // lattice nodes per axis (nelem*N + 1)
+  int ne0, ne1, ne2;   // elements per axis
+  int py;              // row pitch (elements)
+  long long pz;        // plane pitch (elements)
+  int layers_per_cta;  // element layers per CTA (z chunk)
+  int nchunks;         // z chunks per batch member
+  T dtv, dtp;
+  // interior rows a = 1..N-1 of direction d: s_d A[a][b] / w_a  (s_d = c^2 (2/h_d)^2)
+  T cx[N + 1][N + 1];
+  T cy[N + 1][N + 1];
+  T cz[N + 1][N + 1];
+  // vertex rows: left element part s_d A[N][b], right element part s_d A[0][b]
+  T lx[N + 1], rx[N + 1], ly[N + 1], ry[N + 1], lz[N + 1], rz[N + 1];
+  T iwv;               // 1 / (w_0 + w_N): vertex shared by two elements
+  T iwb;               // 1 / w_0: vertex on the box boundary
+  T iwa[N + 1];        // 1 / w_a for interior rows (a = 1..N-1)
+  double minv_scale;   // 8 / (hx hy hz)
+  // PMUT forcing f on the z-min plane (primary box only)
+  int has_pmut;
+  const int* node_ptr;     // [L0*L1 + 1]: footprint entries touching face node
+  const int* node_ent;     // entry ids
+  const int* ent_pmut;     // PMUT of each entry
+  const double* Bm;        // [nnz][M]: W_face * U.n
+  const double* qdd;       // [B][K][M]: q'' of this step
+  int K, M;
+  double kappa;
+  // interface residual (SIPG terms of eq. Wf_2), unassembled per face column
+  int iface_k0;            // first lattice plane of the interface element layer, -1: none
+  int iface_top;           // 1: the value term sits on plane k0+N (primary), 0: on k0 (secondary)
+  const T* Ra;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b alpha_q
+  const T* Rb;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b beta_q
+  T dI[N + 1];             // d_c = (2/h_z) l_c'(face)
+};
+
+// ---------------------------------------------------------------------------
+// Interface fluxes on Gamma_I (Sec. 5): one CTA per listed coarse face.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct IfaceArgs {
+  const T* pp;  const T* ps;       // p^{n+1} of the primary / secondary box
+  long long bsp, bss;              // batch strides
+  int pyp; long long pzp;
+  int pys; long long pzs;
+  int Np, Ns, kp0;                 // orders; first plane of the primary top layer
+  int npx, nsx;                    // element columns per x row (primary, secondary)
+  int ncf;                         // listed coarse faces
+  const int* cf_col;               // [ncf] coarse face column mx + nsx*my
+  const int* cf_ptr;               // [ncf+1] fine faces of each coarse face
+  const int* ff_col;               // fine face column ex + npx*ey
+  const int* ff_sx;                // sub-face interpolation table index (x)
+  const int* ff_sy;                // (y)
+  int q;                           // Gauss points per direction
+  const T* Lp;                     // [q][Np+1] fine GLL basis at the Gauss points
+  const T* Ls;                     // [nsub][q][Ns+1] coarse GLL basis at mapped points
+  const T* Wq;                     // [q*q] w_qx w_qy |J_F+|
+  const T* dp;                     // [Np+1] (2/hz+) l_c'(+1)
+  const T* ds;                     // [Ns+1] (2/hz-) l_c'(-1)
+  T cp2, cm2, gamma;
+  T* Rap; T* Rbp;                  // [B][npx*npy][(Np+1)^2]
+  T* Ras; T* Rbs;                  // [B][nsx*nsy][(Ns+1)^2]
+  long long rbp, rbs;              // batch strides of the residual arrays
+};
+
+// ---------------------------------------------------------------------------
+// PMUT modal step (Algorithm 1, PMUT rows) + receiver sampling.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PmutArgs {
+  int B, K, M;
+  const int* fp_ptr;               // [K+1] footprint entries of PMUT k
+  const long long* fp_off;         // [nnz] offset of the face node in the primary array
+  const double* Bm;                // [nnz][M]
+  const T* p_prev;                 // p^n of the primary box
+  long long bsp;
+  double* q; double* qd; double* qdd;   // [B][K][M]
+  const double* omega2;            // [K][M]
+  const double* twozw;             // [K][M] 2 zeta omega
+  const double* inv_mu;            // [K][M]
+  const double* eta;               // [K][M]
+  const double* drive;             // drive[b*dbs + k*dks + n]
+  long long dbs, dks;
+  int n;                           // step index inside this run
+  double dt;
+  // receivers
+  int R;
+  int rstride;                     // weights per receiver slot
+  const double* rw;                // [R][rstride]
+  const long long* roff;           // [R][rstride]
+  const int* rdom;                 // [R]
+  const int* rnn;                  // [R]
+  const T* pc0; const T* pc1;      // p^{n+1} of each box
+  long long bs0, bs1;
+  double* traces;                  // traces[b*tbs + r*trs + n]
+  long long tbs, trs;
+};
+
+// Runtime description of one volume launch (FP64 tables, runtime order N);
+// the kernel translation unit converts it to VolArgs<T, N>.
+struct VolSpec {
+  const void* p_in; void* p_out; void* v;
+  long long bstride;
+  int L[3], ne[3];
+  int py; long long pz;
+  double dtv, dtp;
+  int N;
+  double c[3][DG_MAXN + 1][DG_MAXN + 1];
+  double l[3][DG_MAXN + 1], r[3][DG_MAXN + 1];
+  double iwv, iwb, iwa[DG_MAXN + 1];
+  double minv_scale;
+  int has_pmut;
+  const int* node_ptr; const int* node_ent; const int* ent_pmut;
+  const double* Bm; const double* qdd;
+  int K, M; double kappa;
+  int iface_k0, iface_top;
+  const void* Ra; const void* Rb;
+  double dI[DG_MAXN + 1];
+  int layers_per_cta;              // 0: choose automatically
+};
+
+// Launchers (defined in the kernel translation units)
+template <typename T>
+cudaError_t launch_vol(const VolSpec& spec, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);

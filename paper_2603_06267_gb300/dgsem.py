@@ -1,0 +1,306 @@
+"""Thin ctypes binding of libdgsem.so (include/dgsem.h).
+
+Argument marshalling only: every step of the time loop runs in the CUDA
+kernels of the shared library.  Arrays may be numpy arrays (host) or torch
+CUDA tensors (device pointers are passed through).  If the library has not
+been built, importing the binding raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_size_t, c_void_p
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdgsem.so")
+
+DGSEM_OK = 0
+DGSEM_EINVAL = -1
+DGSEM_ENOMEM = -2
+DGSEM_ECUDA = -3
+DGSEM_EUNSTABLE = -4
+DGSEM_ETIMEOUT = -5
+DGSEM_ENOMATCH = -6
+DGSEM_ESTATE = -7
+DGSEM_FP64 = 0
+DGSEM_FP32_MIXED = 1
+DGSEM_RUN_CONTINUE = 1
+
+EXPORTED = [
+    "dgsem_mesh_create", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
+    "dgsem_run", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
+    "dgsem_profile", "dgsem_kernel_stats", "dgsem_last_error", "dgsem_destroy",
+]
+DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1 = 0, 1, 2, 3
+
+
+class DgsemError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed with status {code}: {msg}")
+        self.code = code
+
+
+class DomainDesc(ctypes.Structure):
+    _fields_ = [("origin", c_double * 3), ("extent", c_double * 3), ("nelem", c_int * 3),
+                ("order", c_int), ("c", c_double), ("rho", c_double)]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("ndomains", c_int), ("domains", POINTER(DomainDesc)),
+                ("n_fine_faces", c_int), ("fine_faces", POINTER(c_int)),
+                ("n_coarse_faces", c_int), ("coarse_faces", POINTER(c_int)),
+                ("cfl", c_double), ("dt", c_double), ("penalty_alpha", c_double),
+                ("iface_quad_pts", c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdgsem.so and declare the prototypes (raises if not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2603_06267_gb300.build` "
+                           "(the CUDA path has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp = c_void_p
+    lib.dgsem_mesh_create.argtypes = [POINTER(MeshDesc), POINTER(vp)]
+    lib.dgsem_get_dt.argtypes = [vp, POINTER(c_double), POINTER(c_double), POINTER(c_longlong)]
+    lib.dgsem_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
+    lib.dgsem_pmut_nodes.argtypes = [vp, POINTER(c_int), POINTER(POINTER(c_double))]
+    lib.pmut_array_set.argtypes = [vp, c_int, c_int, vp, vp, vp, vp, vp, vp, vp]
+    lib.dgsem_run.argtypes = [vp, c_int, c_int, c_int, vp, c_int, vp, vp, c_int, vp]
+    lib.dgsem_set_state.argtypes = [vp, vp, vp]
+    lib.dgsem_get_pressure.argtypes = [vp, vp, c_size_t]
+    lib.dgsem_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
+    lib.dgsem_state_load.argtypes = [vp, vp, c_size_t]
+    lib.dgsem_profile.argtypes = [vp, c_int]
+    lib.dgsem_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
+    lib.dgsem_last_error.restype = ctypes.c_char_p
+    lib.dgsem_last_error.argtypes = []
+    lib.dgsem_destroy.argtypes = [vp]
+    lib.dgsem_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("dgsem_last_error", "dgsem_destroy"):
+            getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != DGSEM_OK:
+        raise DgsemError(code, where, _lib.dgsem_last_error().decode())
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a contiguous numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"], "arrays must be C-contiguous"
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous(), "tensors must be contiguous"
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float64
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ C names
+def dgsem_mesh_create(domains: Sequence, cfl: float = 0.3, dt: float = 0.0, penalty_alpha: float = 0.5,
+                      iface_quad_pts: int = 0, fine_faces=None, coarse_faces=None) -> c_void_p:
+    """domains: objects with origin, extent, nelem, order, c, rho (primary first)."""
+    lib = load_library()
+    arr = (DomainDesc * len(domains))()
+    for i, d in enumerate(domains):
+        arr[i].origin = (c_double * 3)(*[float(v) for v in d.origin])
+        arr[i].extent = (c_double * 3)(*[float(v) for v in d.extent])
+        arr[i].nelem = (c_int * 3)(*[int(v) for v in d.nelem])
+        arr[i].order = int(d.order)
+        arr[i].c = float(d.c)
+        arr[i].rho = float(d.rho)
+    desc = MeshDesc()
+    desc.ndomains = len(domains)
+    desc.domains = arr
+    keep = []
+    if fine_faces is not None:
+        ff = np.ascontiguousarray(fine_faces, dtype=np.int32)
+        keep.append(ff)
+        desc.n_fine_faces = ff.size
+        desc.fine_faces = ff.ctypes.data_as(POINTER(c_int))
+    if coarse_faces is not None:
+        cf = np.ascontiguousarray(coarse_faces, dtype=np.int32)
+        keep.append(cf)
+        desc.n_coarse_faces = cf.size
+        desc.coarse_faces = cf.ctypes.data_as(POINTER(c_int))
+    desc.cfl = cfl
+    desc.dt = dt
+    desc.penalty_alpha = penalty_alpha
+    desc.iface_quad_pts = iface_quad_pts
+    ctx = c_void_p()
+    _check(lib.dgsem_mesh_create(byref(desc), byref(ctx)), "dgsem_mesh_create")
+    return ctx
+
+
+def dgsem_get_dt(ctx):
+    dt, dts, nd = c_double(), c_double(), c_longlong()
+    _check(_lib.dgsem_get_dt(ctx, byref(dt), byref(dts), byref(nd)), "dgsem_get_dt")
+    return dt.value, dts.value, nd.value
+
+
+def dgsem_check_stability(ctx, iters: int = 50):
+    lam = c_double()
+    code = _lib.dgsem_check_stability(ctx, iters, byref(lam))
+    return code, lam.value
+
+
+def dgsem_pmut_nodes(ctx) -> np.ndarray:
+    n = c_int()
+    p = POINTER(c_double)()
+    _check(_lib.dgsem_pmut_nodes(ctx, byref(n), byref(p)), "dgsem_pmut_nodes")
+    return np.ctypeslib.as_array(p, shape=(n.value, 2)).copy()
+
+
+def pmut_array_set(ctx, foot_ptr, foot_node, shape_un, freq_hz, damping, eta, modal_mass=None):
+    foot_ptr = np.ascontiguousarray(foot_ptr, dtype=np.int32)
+    foot_node = np.ascontiguousarray(foot_node, dtype=np.int32)
+    freq_hz = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    K, M = freq_hz.shape
+    shape_un = np.ascontiguousarray(shape_un, dtype=np.float64).reshape(-1, M)
+    damping = np.ascontiguousarray(damping, dtype=np.float64)
+    eta = np.ascontiguousarray(eta, dtype=np.float64)
+    mm = None if modal_mass is None else np.ascontiguousarray(modal_mass, dtype=np.float64)
+    _check(_lib.pmut_array_set(ctx, K, M, _ptr(foot_ptr), _ptr(foot_node), _ptr(shape_un), _ptr(freq_hz),
+                               _ptr(damping), _ptr(eta), _ptr(mm)), "pmut_array_set")
+
+
+def dgsem_run(ctx, precision: int, batch: int, nsteps: int, drive, recv_xyz, traces=None, flags: int = 0,
+              stream=None):
+    """Returns the traces array [batch][n_recv][nsteps] (numpy unless a torch
+    tensor was passed in `traces`)."""
+    recv = np.ascontiguousarray(recv_xyz, dtype=np.float64).reshape(-1, 3)
+    R = recv.shape[0]
+    if traces is None:
+        traces = np.zeros((batch, R, nsteps))
+    drive = _f64(drive)
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_run(ctx, precision, batch, nsteps, _ptr(drive), R, _ptr(recv), _ptr(traces), flags,
+                          stream), "dgsem_run")
+    return traces
+
+
+def dgsem_set_state(ctx, p0=None, v0=None):
+    p0 = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64)
+    v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+    _check(_lib.dgsem_set_state(ctx, _ptr(p0), _ptr(v0)), "dgsem_set_state")
+
+
+def dgsem_get_pressure(ctx, batch: int, ndof: int) -> np.ndarray:
+    out = np.zeros((batch, ndof))
+    _check(_lib.dgsem_get_pressure(ctx, _ptr(out), out.size), "dgsem_get_pressure")
+    return out
+
+
+def dgsem_state_save(ctx) -> bytes:
+    n = c_size_t(0)
+    _check(_lib.dgsem_state_save(ctx, None, byref(n)), "dgsem_state_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.dgsem_state_save(ctx, buf, byref(n)), "dgsem_state_save")
+    return buf.raw[: n.value]
+
+
+def dgsem_state_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.dgsem_state_load(ctx, buf, len(blob)), "dgsem_state_load")
+
+
+def dgsem_profile(ctx, enable: bool = True):
+    _check(_lib.dgsem_profile(ctx, 1 if enable else 0), "dgsem_profile")
+
+
+def dgsem_kernel_stats(ctx, kind: int):
+    """(total milliseconds, launches) of one kernel kind since dgsem_profile."""
+    ms, n = c_double(), c_longlong()
+    _check(_lib.dgsem_kernel_stats(ctx, kind, byref(ms), byref(n)), "dgsem_kernel_stats")
+    return ms.value, n.value
+
+
+def dgsem_destroy(ctx):
+    if ctx is not None and _lib is not None:
+        _lib.dgsem_destroy(ctx)
+
+
+# ------------------------------------------------------------------ helper
+class Solver:
+    """Owns one context built from a workload-like description (objects with
+    the attributes of include/dgsem.h: domains, cfl, penalty_alpha, quad_pts,
+    pmuts with centers/inside/shape_un/freq_hz/damping/eta/modal_mass)."""
+
+    def __init__(self, workload, dt: float = 0.0):
+        self.w = workload
+        self.ctx = dgsem_mesh_create(workload.domains, cfl=workload.cfl, dt=dt,
+                                     penalty_alpha=workload.penalty_alpha,
+                                     iface_quad_pts=getattr(workload, "quad_pts", 0) or 0)
+        self.dt, _, self.ndof = dgsem_get_dt(self.ctx)
+        self.K = 0
+        if workload.pmuts is not None:
+            self.set_pmuts(workload.pmuts)
+
+    def set_pmuts(self, pm):
+        xy = dgsem_pmut_nodes(self.ctx)
+        ptr = [0]
+        nodes, vals = [], []
+        for k in range(pm.n_pmut):
+            idx = np.nonzero(pm.inside(k, xy[:, 0], xy[:, 1]))[0]
+            nodes.append(idx)
+            vals.append(np.stack([pm.shape_un(k, m, xy[idx, 0], xy[idx, 1]) for m in range(pm.n_modes)], axis=1))
+            ptr.append(ptr[-1] + idx.size)
+        pmut_array_set(self.ctx, np.array(ptr), np.concatenate(nodes),
+                       np.concatenate(vals) if vals else np.zeros((0, pm.n_modes)),
+                       pm.freq_hz, pm.damping, pm.eta, pm.modal_mass)
+        self.K = pm.n_pmut
+
+    def run(self, drive=None, precision=DGSEM_FP64, batch=None, nsteps=None, receivers=None, traces=None,
+            flags=0, stream=None):
+        B = self.w.batch if batch is None else batch
+        S = self.w.nsteps if nsteps is None else nsteps
+        rec = self.w.receivers if receivers is None else receivers
+        if drive is None and self.K > 0:
+            drive = self.w.drive(self.dt, S, B)
+        return dgsem_run(self.ctx, precision, B, S, drive, rec, traces=traces, flags=flags, stream=stream)
+
+    def close(self):
+        dgsem_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if self.ctx is not None:
+                self.close()
+        except Exception:
+            pass

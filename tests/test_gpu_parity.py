@@ -1,0 +1,199 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bars: relative L2 of receiver traces (and of the final pressure field)
+<= 1e-10 in FP64 and <= 1e-4 in FP32/mixed precision, on the same seeded
+inputs; meshes span several CTA tiles with ragged tails.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import rel_l2, run_both, gpu_solver, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+def _standing_field(w, l=(1, 1, 1), seed=None):
+    P = oracle_problem(w)
+    x, y, z = P.all_coordinates()
+    if seed is None:
+        p0, _ = W.standing_wave_mode(w.domains[0], l, x, y, z)
+    else:
+        p0 = W.seeded_field(seed, x, y, z)
+    return p0
+
+
+@pytest.mark.parametrize("N,nel", [(1, (5, 3, 4)), (2, (20, 3, 3)), (3, (13, 4, 3)), (4, (40, 5, 3)),
+                                   (5, (19, 3, 2)), (6, (20, 3, 2)), (7, (9, 2, 2)), (8, (18, 2, 1))])
+def test_volume_operator_single_box_fp64(N, nel):
+    """Rigid box, smooth random initial state, no PMUT: every GLL node of the
+    final field and the receiver traces match the oracle (FP64)."""
+    h = 25e-6
+    dom = W.Domain((0, 0, 0), tuple(n * h for n in nel), nel, N)
+    rng = np.random.default_rng(N)
+    L = np.array(dom.extent)
+    rec = rng.uniform(0, 1, size=(7, 3)) * L
+    w = W.Workload("box", [dom], 60, rec)
+    p0 = _standing_field(w, seed=N)
+    tg, to, pg, po = run_both(w, 0, p0=p0)
+    assert rel_l2(pg, po) < FP64_TOL
+    assert rel_l2(tg, to) < FP64_TOL
+
+
+@pytest.mark.parametrize("N,nel", [(4, (40, 5, 3)), (6, (20, 3, 2))])
+def test_volume_operator_single_box_fp32(N, nel):
+    h = 25e-6
+    dom = W.Domain((0, 0, 0), tuple(n * h for n in nel), nel, N)
+    rec = np.random.default_rng(1).uniform(0, 1, size=(5, 3)) * np.array(dom.extent)
+    w = W.Workload("box", [dom], 80, rec)
+    p0 = _standing_field(w, seed=7)
+    tg, to, pg, po = run_both(w, 1, p0=p0)
+    assert rel_l2(pg, po) < FP32_TOL
+    assert rel_l2(tg, to) < FP32_TOL
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_two_domain_interface_initial_state(prec, tol):
+    """2:1 non-conforming N=4 | N=6 interface, initial state crossing it."""
+    w = W.small_two_domain(nx_p=8, nz_p=2, nx_s=4, nz_s=3, n_pmut_side=2, nsteps=80)
+    w.pmuts = None
+    p0 = _standing_field(w, seed=3)
+    tg, to, pg, po = run_both(w, prec, p0=p0)
+    assert rel_l2(pg, po) < tol
+    assert rel_l2(tg, to) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_two_domain_pmut_array(prec, tol):
+    """Full step: PMUT array on z = 0, 2:1 interface, receivers in both boxes."""
+    w = W.small_two_domain(nx_p=8, nz_p=2, nx_s=4, nz_s=4, n_pmut_side=2, nsteps=300)
+    tg, to, pg, po = run_both(w, prec)
+    assert np.abs(to).max() > 0
+    assert rel_l2(tg, to) < tol
+    assert rel_l2(pg, po) < tol
+
+
+def test_two_domain_conforming_interface_fp64():
+    """r = 1 (conforming faces), same order on both sides."""
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=4, nz_s=2, n_pmut_side=2, nsteps=120, order_s=4)
+    tg, to, pg, po = run_both(w, 0)
+    assert rel_l2(tg, to) < FP64_TOL
+
+
+def test_batched_patterns_fp64():
+    """B = 3 drive patterns in one launch: each matches its own oracle run."""
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=150, batch=3, steer=True)
+    tg, to, pg, po = run_both(w, 0)
+    for b in range(3):
+        assert rel_l2(tg[b], to[b]) < FP64_TOL
+
+
+def test_config1_full_fp64():
+    """Config 1 at full size (8^3 hexes N=4, one PMUT, 2000 steps)."""
+    w = W.config1_single_pmut()
+    tg, to, pg, po = run_both(w, 0)
+    assert rel_l2(tg, to) < FP64_TOL
+    for r in range(tg.shape[1]):
+        assert rel_l2(tg[0, r], to[0, r]) < FP64_TOL
+
+
+def test_config1_full_fp32():
+    w = W.config1_single_pmut()
+    tg, to, pg, po = run_both(w, 1)
+    assert rel_l2(tg, to) < FP32_TOL
+
+
+def test_single_box_pmut_ragged_fp64():
+    w = W.small_one_domain(nel=(3, 2, 2), nsteps=200, n_pmut_side=2, order=4)
+    tg, to, pg, po = run_both(w, 0)
+    assert rel_l2(tg, to) < FP64_TOL
+
+
+def test_zero_steps_and_no_receivers():
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_one_domain(nel=(2, 2, 2), nsteps=5)
+    sol = gpu_solver(w)
+    tr = sol.run(nsteps=0)
+    assert tr.shape == (1, w.receivers.shape[0], 0)
+    tr = sol.run(receivers=np.zeros((0, 3)))
+    assert tr.shape == (1, 0, 5)
+    sol.close()
+
+
+def test_continue_and_checkpoint_bitwise():
+    """run(S) == run(k) + run(S-k, CONTINUE) == run(k) + save/load + run(S-k),
+    bit for bit (deterministic kernels, no atomics)."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=100, batch=2, steer=True)
+    for prec in (0, 1):
+        sol = gpu_solver(w)
+        drive = w.drive(sol.dt, 100, 2)
+        full = sol.run(drive=drive, precision=prec)
+        a = sol.run(drive=np.ascontiguousarray(drive[:, :, :37]), precision=prec, nsteps=37)
+        blob = dgsem.dgsem_state_save(sol.ctx)
+        b = sol.run(drive=np.ascontiguousarray(drive[:, :, 37:]), precision=prec, nsteps=63,
+                    flags=dgsem.DGSEM_RUN_CONTINUE)
+        assert np.array_equal(np.concatenate([a, b], axis=2), full)
+        sol2 = gpu_solver(w)
+        dgsem.dgsem_state_load(sol2.ctx, blob)
+        c = sol2.run(drive=np.ascontiguousarray(drive[:, :, 37:]), precision=prec, nsteps=63,
+                     flags=dgsem.DGSEM_RUN_CONTINUE)
+        assert np.array_equal(c, b)
+        sol.close()
+        sol2.close()
+
+
+def test_linearity_and_time_shift_gpu():
+    w = W.small_one_domain(nel=(3, 2, 2), nsteps=90, n_pmut_side=2)
+    sol = gpu_solver(w)
+    rng = np.random.default_rng(5)
+    d1 = rng.normal(size=(1, 4, 90))
+    d2 = rng.normal(size=(1, 4, 90))
+    t1 = sol.run(drive=d1)
+    t2 = sol.run(drive=d2)
+    t12 = sol.run(drive=d1 + d2)
+    assert rel_l2(t12, t1 + t2) < 1e-12
+    k = 11
+    ds = np.zeros_like(d1)
+    ds[:, :, k:] = d1[:, :, :-k]
+    ts = sol.run(drive=ds)
+    assert np.array_equal(ts[:, :, k:], t1[:, :, :-k])
+    assert np.all(ts[:, :, :k] == 0.0)
+    sol.close()
+
+
+def test_device_pointer_drive_and_traces():
+    """drive and traces as torch CUDA tensors (device pointers) give the same
+    result as host arrays."""
+    import torch
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_one_domain(nel=(2, 2, 2), nsteps=50)
+    sol = gpu_solver(w)
+    drive = w.drive(sol.dt, 50, 1)
+    host = sol.run(drive=drive)
+    dd = torch.tensor(drive, device="cuda")
+    tt = torch.zeros((1, w.receivers.shape[0], 50), dtype=torch.float64, device="cuda")
+    sol.run(drive=dd, traces=tt)
+    torch.cuda.synchronize()
+    assert np.array_equal(tt.cpu().numpy(), host)
+    sol.close()
+
+
+def test_invalid_inputs_return_status():
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_one_domain(nel=(2, 2, 2), nsteps=5)
+    sol = gpu_solver(w)
+    with pytest.raises(dgsem.DgsemError) as e:
+        sol.run(receivers=np.array([[1.0, 1.0, 1.0]]))
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.pmut_array_set(sol.ctx, np.array([0, 1]), np.array([10 ** 7]), np.zeros((1, 1)),
+                             np.ones((1, 1)), np.zeros((1, 1)), np.zeros((1, 1)))
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    with pytest.raises(dgsem.DgsemError) as e:
+        sol.run(flags=dgsem.DGSEM_RUN_CONTINUE, precision=1, batch=7)
+    assert e.value.code == dgsem.DGSEM_ESTATE
+    sol.close()
