@@ -29,7 +29,8 @@ def run_both(w, precision, drive=None, p0=None, v0=None, nsteps=None, batch=None
     P = oracle_problem(w)
     dt = P.stable_dt()
     sol = gpu_solver(w)
-    assert abs(sol.dt - dt) <= 1e-15 * dt, (sol.dt, dt)
+    # both sides compute dt from the same CFL reading with their own GLL tables
+    assert abs(sol.dt - dt) <= 1e-13 * dt, (sol.dt, dt)
     if drive is None and w.pmuts is not None:
         drive = w.drive(dt, S, B)
     if p0 is not None or v0 is not None:

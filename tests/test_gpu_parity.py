@@ -194,6 +194,6 @@ def test_invalid_inputs_return_status():
                              np.ones((1, 1)), np.zeros((1, 1)), np.zeros((1, 1)))
     assert e.value.code == dgsem.DGSEM_EINVAL
     with pytest.raises(dgsem.DgsemError) as e:
-        sol.run(flags=dgsem.DGSEM_RUN_CONTINUE, precision=1, batch=7)
+        sol.run(drive=np.zeros((7, sol.K, 5)), flags=dgsem.DGSEM_RUN_CONTINUE, precision=1, batch=7)
     assert e.value.code == dgsem.DGSEM_ESTATE
     sol.close()
