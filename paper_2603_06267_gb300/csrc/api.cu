@@ -218,6 +218,10 @@ struct dgsem_ctx {
   double* d_traces = nullptr; size_t traces_cap = 0;
   double* d_rw = nullptr; long long* d_roff = nullptr; int* d_rdom = nullptr; int* d_rnn = nullptr;
   size_t recv_cap = 0;
+  // TMA descriptors of the pressure buffers (X and Y of each box) and the
+  // device status word written by bounded waits
+  CUtensorMap tmap_x[2], tmap_y[2];
+  int* d_err = nullptr;
   // instrumentation
   bool profiling = false;
   long long launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
@@ -266,6 +270,40 @@ void free_run_state(dgsem_ctx* c) {
 
 size_t elem_size(int prec) { return prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double); }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 4D (x, y, z, batch) tiled tensor map of one pressure buffer for the TMA
+// staging loads of the volume kernel (box = one element layer of a tile).
+int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(DGSEM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  const size_t es = elem_size(prec);
+  unsigned box[3];
+  vol_tma_box(B.N, prec == DGSEM_FP32_MIXED, box);
+  if (!box[0]) return fail(DGSEM_EINVAL, "no TMA box for order %d", B.N);
+  const cuuint64_t dims[4] = {(cuuint64_t)B.L[0], (cuuint64_t)B.L[1], (cuuint64_t)B.L[2], (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)B.py * es, (cuuint64_t)B.pz * es, (cuuint64_t)B.bstride * es};
+  for (int i = 0; i < 3; ++i)
+    if (strides[i] % 16) return fail(DGSEM_EINVAL, "TMA stride %d not a multiple of 16 bytes", i);
+  if (reinterpret_cast<uintptr_t>(base) % 16) return fail(DGSEM_EINVAL, "TMA base address not 16-byte aligned");
+  const cuuint32_t boxd[4] = {box[0], box[1], box[2], 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(out, prec == DGSEM_FP32_MIXED ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                      4, base, dims, strides, boxd, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(DGSEM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DGSEM_OK;
+}
+
 int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
   if (c->prec == prec && c->batch == batch && c->X[0]) return DGSEM_OK;
   free_run_state(c);
@@ -291,6 +329,14 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
   if (c->K > 0) {
     int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
     if (rc) { free_run_state(c); return rc; }
+  }
+  for (int d = 0; d < c->nd; ++d) {
+    int rc;
+    if ((rc = make_tmap(&c->tmap_x[d], c->X[d], c->box[d], batch, prec)) ||
+        (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], batch, prec))) {
+      free_run_state(c);
+      return rc;
+    }
   }
   c->prec = prec;
   c->batch = batch;
@@ -588,6 +634,8 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
   }
   for (int d = 0; d < c->nd; ++d) {
     VolSpec v = c->vspec[d];
+    v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
+    v.err = c->d_err;
     v.p_in = pin[d]; v.p_out = pout[d]; v.v = c->V[d];
     v.dtv = init ? 0.5 * c->dt : c->dt;
     v.dtp = c->dt;
@@ -602,7 +650,10 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     CUDA_TRY(launch_vol<T>(v, c->batch, s));
   }
   if (!init) {
-    for (int d = 0; d < c->nd; ++d) std::swap(c->X[d], c->Y[d]);
+    for (int d = 0; d < c->nd; ++d) {
+      std::swap(c->X[d], c->Y[d]);
+      std::swap(c->tmap_x[d], c->tmap_y[d]);
+    }
   }
   return DGSEM_OK;
 }
@@ -705,6 +756,7 @@ int upload_field(dgsem_ctx* c, const std::vector<double>& h, void* const* dst, c
 template <typename T>
 int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
   int rc;
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
   const bool cont = (flags & DGSEM_RUN_CONTINUE) && c->state_valid;
   if (!cont) {
     if ((rc = zero_state(c, s))) return rc;
@@ -756,6 +808,12 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
   if (tr_host) CUDA_TRY(cudaMemcpyAsync(traces_out, d_tr, tr_n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   collect_timings(c);
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    c->state_valid = false;
+    return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up (status %d); the state is invalid", err);
+  }
   return DGSEM_OK;
 }
 
@@ -817,6 +875,11 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
     cmax = std::max(cmax, B.c);
     c->ndof += (long long)B.L[0] * B.L[1] * B.L[2];
     build_vol_spec(B, c->vspec[d]);
+  }
+  {
+    int rc = dalloc(&c->d_err, sizeof(int));
+    if (rc) { dgsem_destroy(c); return rc; }
+    CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
   }
   c->dt = desc->dt > 0.0 ? desc->dt : desc->cfl * hmin / cmax;
   c->kappa = c->box[0].rho * c->box[0].c * c->box[0].c;
@@ -1085,6 +1148,7 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_ent_pmut); dfree(c->d_modal);
   dfree(c->d_drive); dfree(c->d_traces);
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
+  dfree(c->d_err);
   delete c->basis[0];
   delete c->basis[1];
   delete c;

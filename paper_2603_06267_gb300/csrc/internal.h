@@ -2,6 +2,7 @@
 // kernels (vol.cu, small.cu).  Not part of the public ABI (include/dgsem.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -21,7 +22,9 @@
 // 1D weight.  The coefficient blocks below hold those rows.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-struct VolArgs {
+struct alignas(64) VolArgs {
+  CUtensorMap tmap;    // 4D (x, y, z, batch) tiled view of p_in for the TMA staging loads
+  int* err;            // device status word: set to 1 if a bounded wait gives up
   const T* p_in;       // p^{n+1}: stencil source
   T* p_out;            // p^{n+2} = p^{n+1} + dtp * v_new
   T* v;                // v^{n+1/2} -> v^{n+3/2} = v + dtv * a
@@ -125,6 +128,8 @@ struct PmutArgs {
 // Runtime description of one volume launch (FP64 tables, runtime order N);
 // the kernel translation unit converts it to VolArgs<T, N>.
 struct VolSpec {
+  const CUtensorMap* tmap;         // tensor map of p_in (see make_tmap_spec)
+  int* err;
   const void* p_in; void* p_out; void* v;
   long long bstride;
   int L[3], ne[3];
@@ -144,6 +149,10 @@ struct VolSpec {
   double dI[DG_MAXN + 1];
   int layers_per_cta;              // 0: choose automatically
 };
+
+// Box shape (x, y, z) of the TMA staging load of one element layer for a
+// box of order N and the given precision (defined in vol.cu).
+void vol_tma_box(int N, bool fp32, unsigned box[3]);
 
 // Launchers (defined in the kernel translation units)
 template <typename T>

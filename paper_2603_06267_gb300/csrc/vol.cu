@@ -4,23 +4,164 @@
 // leapfrog form of the Newmark gamma=1/2, beta=0 corrector/predictor of
 // Algorithm 1:  v <- v + dtv * a,  p_out <- p_in + dtp * v.
 //
-// Layout: one lattice of GLL nodes per box, x fastest, padded row pitch.
+// Layout: one lattice of GLL nodes per box, x fastest, padded row pitch,
+// batch members one after another.
+//
 // Work decomposition: a CTA owns an element-aligned x-y tile of TXE element
-// columns x (TYE*N) rows and marches over a chunk of element layers in z.
-// Each thread owns the N nodes of one element along x in one row.  For each
-// layer the N+1 planes of the layer are staged in shared memory with a halo
-// of one element on the low x/y side and one node on the high side (vertex
-// rows need the neighbouring element, interior rows only their own); the
-// z-direction coupling to the layer below is carried in registers as a
-// partial sum, so no z halo is loaded.
+// columns x TYE*N rows and marches over a chunk of element layers in z.  Each
+// thread owns the N nodes of one element along x in one row (the thread of
+// the last element column also owns the box's last x node).  The N+1 planes
+// of an element layer are staged in shared memory by one TMA box load
+// (cp.async.bulk.tensor, zero fill outside the box) with a halo of one
+// element on the low x/y side and one node on the high side -- vertex rows
+// need the neighbouring element, interior rows only their own.  Two stages
+// alternate so that the next layer streams in while the current one is
+// computed.  The coupling of a vertex plane to the layer below is a partial
+// sum carried in registers, so no z halo is loaded.
+#include <cstdio>
+#include <type_traits>
+
 #include "internal.h"
 
 namespace {
 
+// ---------------------------------------------------------------------------
+// small PTX helpers: mbarrier + TMA
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 SM clocks (about a second) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// vector loads / stores of runs of consecutive elements
+// ---------------------------------------------------------------------------
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 1> { using t = float; };
+template <> struct Vec<float, 2> { using t = float2; };
+template <> struct Vec<float, 4> { using t = float4; };
+template <> struct Vec<double, 1> { using t = double; };
+template <> struct Vec<double, 2> { using t = double2; };
+
+__device__ __forceinline__ void unpack(const float& v, float* o) { o[0] = v; }
+__device__ __forceinline__ void unpack(const double& v, double* o) { o[0] = v; }
+__device__ __forceinline__ void unpack(const float2& v, float* o) { o[0] = v.x; o[1] = v.y; }
+__device__ __forceinline__ void unpack(const float4& v, float* o) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+__device__ __forceinline__ void unpack(const double2& v, double* o) { o[0] = v.x; o[1] = v.y; }
+
+template <typename T, int V>
+__device__ __forceinline__ typename Vec<T, V>::t packv(const T* o) {
+  typename Vec<T, V>::t v;
+  if constexpr (V == 1) v = o[0];
+  else if constexpr (V == 2) { v.x = o[0]; v.y = o[1]; }
+  else { v.x = o[0]; v.y = o[1]; v.z = o[2]; v.w = o[3]; }
+  return v;
+}
+
+// load CNT consecutive elements (p aligned to V elements)
+template <typename T, int V, int CNT>
+__device__ __forceinline__ void vld(const T* __restrict__ p, T* out) {
+  static_assert(CNT % V == 0, "run length must be a multiple of the vector width");
+  using VT = typename Vec<T, V>::t;
+#pragma unroll
+  for (int k = 0; k < CNT / V; ++k) unpack(reinterpret_cast<const VT*>(p)[k], out + k * V);
+}
+
+template <typename T, int V, int CNT>
+__device__ __forceinline__ void vld_global(const T* __restrict__ p, T* out) {
+  static_assert(CNT % V == 0, "run length must be a multiple of the vector width");
+  using VT = typename Vec<T, V>::t;
+#pragma unroll
+  for (int k = 0; k < CNT / V; ++k) unpack(reinterpret_cast<const VT*>(p)[k], out + k * V);
+}
+
+template <typename T, int V, int CNT>
+__device__ __forceinline__ void vst(T* __restrict__ p, const T* in) {
+  static_assert(CNT % V == 0, "run length must be a multiple of the vector width");
+  using VT = typename Vec<T, V>::t;
+#pragma unroll
+  for (int k = 0; k < CNT / V; ++k) reinterpret_cast<VT*>(p)[k] = packv<T, V>(in + k * V);
+}
+
+constexpr int pow2_div(int n) { return (n % 4 == 0) ? 4 : ((n % 2 == 0) ? 2 : 1); }
+constexpr int cmin(int a, int b) { return a < b ? a : b; }
+constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+
+// ---------------------------------------------------------------------------
+// tile geometry
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+struct TileChoice {
+  static constexpr int TXE = (N <= 4) ? 32 : 16;                                      // element columns
+  static constexpr int TYE = (N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1));  // element rows
+};
+
+template <typename T, int N, int TXE, int TYE>
+struct Geo {
+  static constexpr int AL = 16 / (int)sizeof(T);                // elements per 16 bytes
+  static constexpr int NAL = (N + AL - 1) / AL * AL;            // low x halo rounded up to 16 B
+  static constexpr int PAD = NAL - N;
+  static constexpr int TYR = TYE * N;                           // owned rows
+  static constexpr int BX = (TXE * N + N + 1 + PAD + AL - 1) / AL * AL;   // staged columns
+  static constexpr int BY = TYR + N + 1;                        // staged rows
+  static constexpr int BZ = N + 1;                              // staged planes (one layer)
+  static constexpr int PLANE = BX * BY;
+  static constexpr size_t STAGE_BYTES = sizeof(T) * (size_t)BZ * PLANE;
+  static constexpr size_t STAGE = (STAGE_BYTES + 127) / 128 * 128;
+  static constexpr int STAGES = (2 * STAGE + 64 <= 227 * 1024) ? 2 : 1;
+  static constexpr size_t SMEM = STAGES * STAGE + 64;
+  static constexpr int NT = TXE * TYR;
+  // vector widths: shared-memory runs start at column NAL + tx*N, global runs at ex*N
+  static constexpr int VS = cmin(cmin(AL, pow2_div(N)), pow2_div(gcd_c(N, NAL)));
+  static constexpr int VG = cmin(AL, pow2_div(N));
+  static_assert(NT % 32 == 0, "CTA must be a whole number of warps");
+  // TMA: the x coordinate x0 - NAL (x0 = tile * TXE * N) must be 16-byte aligned
+  static_assert((TXE * N * sizeof(T)) % 16 == 0 && (NAL * sizeof(T)) % 16 == 0, "TMA x coordinate misaligned");
+  static_assert((BX * sizeof(T)) % 16 == 0, "TMA box row must be a multiple of 16 bytes");
+  static_assert(BX <= 256 && BY <= 256 && BZ <= 256, "TMA box dimension above 256");
+  static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
+};
+
+// Sum of the per-face (unassembled) interface residual entries touching face
+// node (i, j), in a fixed order (deterministic, no atomics).
 template <typename T, int N>
 __device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, int ne0, int ne1) {
-  // Sum of the per-face (unassembled) residual entries that touch node (i, j)
-  // of the face lattice, in a fixed order (deterministic).
   int fx = i / N, ax = i - fx * N;
   int fy = j / N, ay = j - fy * N;
   if (fx == ne0) { fx = ne0 - 1; ax = N; }
@@ -29,30 +170,15 @@ __device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, 
   T s = R[(long long)(fy * ne0 + fx) * F + ay * (N + 1) + ax];
   if (ax == 0 && fx > 0) s += R[(long long)(fy * ne0 + fx - 1) * F + ay * (N + 1) + N];
   if (ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx) * F + N * (N + 1) + ax];
-  if (ax == 0 && fx > 0 && ay == 0 && fy > 0)
-    s += R[(long long)((fy - 1) * ne0 + fx - 1) * F + N * (N + 1) + N];
+  if (ax == 0 && fx > 0 && ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx - 1) * F + N * (N + 1) + N];
   return s;
 }
 
-template <typename T, int N, int TXE, int TYE>
-struct VolTile {
-  static constexpr int TYR = TYE * N;              // owned rows
-  static constexpr int COLS = TXE * N + N + 1;     // staged columns
-  static constexpr int CP = (COLS + 3) & ~3;       // smem row pitch
-  static constexpr int ROWS = TYR + N + 1;         // staged rows
-  static constexpr int PLANE = ROWS * CP;
-  static constexpr int NT = TXE * TYR;             // threads
-  static constexpr size_t SMEM = sizeof(T) * (size_t)(N + 1) * PLANE;
-  // the staging loop hands whole rows to whole warps
-  static_assert(NT % 32 == 0, "CTA must be a whole number of warps");
-  static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
-};
-
-// Rare per-node terms: PMUT forcing f (eq. f_i) on the z-min plane and the
-// interface residual of the interface element layer, both times M^-1.
+// Rare per-node terms times M^-1: PMUT forcing f (eq. f_i) on the z-min plane
+// and the interface residual of the interface element layer.
 template <typename T, int N>
-__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, T minv_t, double minv, T ra,
-                                      T rb, bool iface_here) {
+__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, double minv, T ra, T rb,
+                                      bool iface_here) {
   T acc = T(0);
   if (A.has_pmut && k == 0) {
     double f = 0.0;
@@ -70,78 +196,38 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
     if (idx >= 0 && idx <= N) {
       T r = A.dI[idx] * rb;
       if (idx == (A.iface_top ? N : 0)) r += ra;
-      acc -= r * minv_t;
+      acc -= r * T(minv);
     }
   }
   return acc;
 }
 
-// x and y stencils of node (i = ex*N + a, j) in plane P, plus the update.
-template <typename T, int N, int CP>
-__device__ __forceinline__ void node_update(const VolArgs<T, N>& A, const T* __restrict__ P, int a, int i, int j, int k,
-                                            int b, int r0, int cb, bool xl, bool xr, T xiw, bool yvert, bool yl,
-                                            bool yr, T yiw, int yb, const T (&cyi)[N + 1], T iw_y, T zs, T iw_z,
-                                            bool extras_layer, T ra, T rb, bool iface_here, T* __restrict__ pout,
-                                            T* __restrict__ vv) {
-  const int col = cb + a;
-  T xs, iw_x;
-  if (a == 0) {
-    T l = T(0), r = T(0);
-    if (xl) {
+// z stencil of the owned nodes: sum_q coef[q] * (staged plane q, own column)
+template <typename T, int N, int VS, int PLANE>
+__device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, T* zs) {
 #pragma unroll
-      for (int q = 0; q <= N; ++q) l += A.lx[q] * P[r0 * CP + cb - N + q];
-    }
-    if (xr) {
+  for (int a = 0; a <= N; ++a) zs[a] = T(0);
 #pragma unroll
-      for (int q = 0; q <= N; ++q) r += A.rx[q] * P[r0 * CP + cb + q];
-    }
-    xs = (l + r) * xiw;
-    iw_x = xiw;
-  } else {
-    T s = T(0);
+  for (int q = 0; q <= N; ++q) {
+    T t[N + 1];
+    vld<T, VS, N>(S0 + q * PLANE + own, t);
+    t[N] = S0[q * PLANE + own + N];
+    const T cq = coef[q];
 #pragma unroll
-    for (int q = 0; q <= N; ++q) s += A.cx[a][q] * P[r0 * CP + cb + q];
-    xs = s;
-    iw_x = A.iwa[a];
+    for (int a = 0; a <= N; ++a) zs[a] += cq * t[a];
   }
-  T ys;
-  if (yvert) {
-    T l = T(0), r = T(0);
-    if (yl) {
-#pragma unroll
-      for (int q = 0; q <= N; ++q) l += A.ly[q] * P[(r0 - N + q) * CP + col];
-    }
-    if (yr) {
-#pragma unroll
-      for (int q = 0; q <= N; ++q) r += A.ry[q] * P[(r0 + q) * CP + col];
-    }
-    ys = (l + r) * yiw;
-  } else {
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q <= N; ++q) s += cyi[q] * P[(r0 - yb + q) * CP + col];
-    ys = s;
-  }
-  T acc = -(xs + ys + zs);
-  if (extras_layer) {
-    const T minv_t = T(A.minv_scale) * iw_x * iw_y * iw_z;
-    const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
-    acc += node_extras<T, N>(A, i, j, k, b, minv_t, minv, ra, rb, iface_here);
-  }
-  const long long g = (long long)k * A.pz + (long long)j * A.py + i;
-  const T vn = vv[g] + A.dtv * acc;
-  vv[g] = vn;
-  pout[g] = P[r0 * CP + col] + A.dtp * vn;
 }
 
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
 template <typename T, int N, int TXE, int TYE>
-__global__ void __launch_bounds__(TXE * TYE * N)
-vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
-  using Tile = VolTile<T, N, TXE, TYE>;
-  constexpr int TYR = Tile::TYR, COLS = Tile::COLS, CP = Tile::CP, ROWS = Tile::ROWS;
-  constexpr int PLANE = Tile::PLANE;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);
+__global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
+  using G = Geo<T, N, TXE, TYE>;
+  constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
+  constexpr int STAGES = G::STAGES;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TXE + tx;
@@ -152,15 +238,17 @@ vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
   const int b = blockIdx.z / A.nchunks;
   const int ez0 = chunk * A.layers_per_cta;
   const int ez1 = min(ez0 + A.layers_per_cta, A.ne2);
-  const T* __restrict__ pin = A.p_in + (long long)b * A.bstride;
-  T* __restrict__ pout = A.p_out + (long long)b * A.bstride;
-  T* __restrict__ vv = A.v + (long long)b * A.bstride;
+  const long long boff = (long long)b * A.bstride;
+  const T* __restrict__ pin = A.p_in + boff;
+  T* __restrict__ pout = A.p_out + boff;
+  T* __restrict__ vv = A.v + boff;
 
-  const int ex = ex0 + tx;          // element column of this thread (ex == ne0: lone last vertex)
-  const int j = y0 + ty;            // lattice row
-  const bool row_ok = j < A.L1;
+  const int ex = ex0 + tx;                 // element column
+  const int j = y0 + ty;                   // lattice row
+  const bool active = ex < A.ne0 && j < A.L1;
+  const bool xlast = ex == A.ne0 - 1;      // also owns node ne0*N
   const int ey = j / N;
-  const int yb = j - ey * N;        // local row index in its element
+  const int yb = j - ey * N;
   const bool yvert = (yb == 0);
   const bool yl = ey > 0, yr = ey < A.ne1;
   const T yiw = (yl && yr) ? A.iwv : A.iwb;
@@ -168,123 +256,225 @@ vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
 #pragma unroll
   for (int q = 0; q <= N; ++q) cyi[q] = yvert ? T(0) : A.cy[yb][q];
   const T iw_y = yvert ? yiw : A.iwa[yb];
-  const bool xl = ex > 0, xr = ex < A.ne0;
-  const T xiw = (xl && xr) ? A.iwv : A.iwb;
+  const bool xl = ex > 0;
+  const T xiw = xl ? A.iwv : A.iwb;        // vertex node ex*N (an element always lies to its right)
 
-  // smem coordinates of this thread's first node (node ex*N)
-  const int r0 = ty + N;            // staged row of row j
-  const int cb = N + tx * N;        // staged column of node ex*N
+  const int r0 = ty + N;                   // staged row of lattice row j
+  const int cb = NAL + tx * N;             // staged column of node ex*N
+  const int own = r0 * BX + cb;            // staged offset of node ex*N in a plane
+  const long long grow = (long long)j * A.py + (long long)ex * N;   // node ex*N in a plane
 
   // interface residual of this column (gathered once)
-  T ra[N], rb[N];
+  T ra[N + 1], rb[N + 1];
+#pragma unroll
+  for (int a = 0; a <= N; ++a) { ra[a] = T(0); rb[a] = T(0); }
   const bool iface_here = A.iface_k0 >= 0 && A.iface_k0 <= ez1 * N && A.iface_k0 + N >= ez0 * N;
+  if (iface_here && active) {
+    const long long fs = (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
 #pragma unroll
-  for (int a = 0; a < N; ++a) { ra[a] = T(0); rb[a] = T(0); }
-  if (iface_here && row_ok) {
-    const T* Rab = A.Ra + (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
-    const T* Rbb = A.Rb + (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const int i = ex * N + a;
-      if (i < A.L0) {
-        ra[a] = face_gather<T, N>(Rab, i, j, A.ne0, A.ne1);
-        rb[a] = face_gather<T, N>(Rbb, i, j, A.ne0, A.ne1);
+    for (int a = 0; a <= N; ++a) {
+      if (a < N || xlast) {
+        ra[a] = face_gather<T, N>(A.Ra + fs, ex * N + a, j, A.ne0, A.ne1);
+        rb[a] = face_gather<T, N>(A.Rb + fs, ex * N + a, j, A.ne0, A.ne1);
       }
     }
   }
 
-  // z carry: sum_b lz[b] p[(ez-1)N + b] of each owned node
-  T carry[N];
+  // z carry: sum_q lz[q] p[(ez-1)N + q] of each owned node
+  T carry[N + 1];
 #pragma unroll
-  for (int a = 0; a < N; ++a) carry[a] = T(0);
-  if (ez0 > 0 && row_ok) {
+  for (int a = 0; a <= N; ++a) carry[a] = T(0);
+  if (ez0 > 0 && active) {
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-      const int i = ex * N + a;
-      if (i < A.L0) {
-        T s = T(0);
+    for (int q = 0; q <= N; ++q) {
+      T t[N];
+      const T* src = pin + (long long)((ez0 - 1) * N + q) * A.pz + grow;
+      vld_global<T, VG, N>(src, t);
 #pragma unroll
-        for (int q = 0; q <= N; ++q)
-          s += A.lz[q] * pin[(long long)((ez0 - 1) * N + q) * A.pz + (long long)j * A.py + i];
-        carry[a] = s;
-      }
+      for (int a = 0; a < N; ++a) carry[a] += A.lz[q] * t[a];
+      if (xlast) carry[N] += A.lz[q] * src[N];
     }
   }
 
-  const int warp = tid >> 5, lane = tid & 31;
-  constexpr int NWARP = (Tile::NT + 31) / 32;
-
-  for (int ez = ez0; ez < ez1; ++ez) {
-    __syncthreads();
-    // stage planes ez*N .. ez*N+N, rows y0-N .. y0+TYR, columns x0-N .. x0+TXE*N
-    for (int rr = warp; rr < (N + 1) * ROWS; rr += NWARP) {
-      const int c = rr / ROWS, r = rr - c * ROWS;
-      const int gk = ez * N + c, gj = y0 - N + r;
-      const bool ok = gj >= 0 && gj < A.L1;
-      const T* src = pin + (long long)gk * A.pz + (long long)gj * A.py;
-      T* dst = S + c * PLANE + r * CP;
-      for (int col = lane; col < COLS; col += 32) {
-        const int gi = x0 - N + col;
-        dst[col] = (ok && gi >= 0 && gi < A.L0) ? src[gi] : T(0);
-      }
+  // the TMA destination must be 128-byte aligned
+  if (smem_u32(smem_raw) % 128 != 0) {
+    if (tid == 0) atomicExch(A.err, 2);
+    return;
+  }
+  // pipeline set-up
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap)) : "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < STAGES && ez0 + s < ez1; ++s) {
+      mbar_expect_tx(&bar[s], (uint32_t)G::STAGE_BYTES);
+      tma_load_4d(smem_raw + s * G::STAGE, &A.tmap, &bar[s], x0 - NAL, y0 - N, (ez0 + s) * N, b);
     }
-    __syncthreads();
-    if (!row_ok) continue;
-    const bool extras_layer = (A.has_pmut && ez == 0) ||
-                              (iface_here && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
-    // vertex plane c = 0: left part carried from the layer below
-    {
-      const int k = ez * N;
-      const T iw_z = (ez > 0) ? A.iwv : A.iwb;
+  }
+
+  int it = 0;
+  for (int ez = ez0; ez < ez1; ++ez, ++it) {
+    const int s = it % STAGES;
+    const uint32_t parity = (uint32_t)((it / STAGES) & 1);
+    const T* S0 = reinterpret_cast<const T*>(smem_raw + s * G::STAGE);
+    const bool last_layer = (ez == A.ne2 - 1);
+    const int nplanes = last_layer ? N + 1 : N;
+    // v of the first plane of the layer, loaded before the wait for the staged p
+    T vcur[N + 1];
 #pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int i = ex * N + a;
-        if (i < A.L0) {
-          T zr = T(0);
+    for (int a = 0; a <= N; ++a) vcur[a] = T(0);
+    if (active) {
+      const T* src = vv + (long long)(ez * N) * A.pz + grow;
+      vld_global<T, VG, N>(src, vcur);
+      if (xlast) vcur[N] = src[N];
+    }
+    if (!mbar_wait_bounded(&bar[s], parity)) {
+      if (tid == 0) atomicExch(A.err, 1);
+      // give the copies in flight a bounded chance to land before leaving
+      for (int q = 0; q < STAGES; ++q) (void)mbar_wait_bounded(&bar[q], parity);
+      return;
+    }
+    if (active) {
+      const bool extras_layer = (A.has_pmut && ez == 0) ||
+                                (iface_here && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
+      // one plane of the layer; ZM selects the z rows: 0 vertex plane (carried
+      // lower part + own layer), 1 interior plane c, 2 top boundary plane
+      auto plane = [&](auto zm, int c) {
+        constexpr int ZM = decltype(zm)::value;
+        const T* P = S0 + c * PLANE;
+        const int k = ez * N + c;
+        // v of the next plane, one plane ahead
+        T vnext[N + 1];
 #pragma unroll
-          for (int q = 0; q <= N; ++q) zr += A.rz[q] * S[q * PLANE + r0 * CP + cb + a];
-          const T zs = (carry[a] + zr) * iw_z;
-          node_update<T, N, CP>(A, S, a, i, j, k, b, r0, cb, xl, xr, xiw, yvert, yl, yr, yiw, yb, cyi, iw_y, zs, iw_z,
-                                extras_layer, ra[a], rb[a], iface_here, pout, vv);
+        for (int a = 0; a <= N; ++a) vnext[a] = T(0);
+        if (c + 1 < nplanes) {
+          const T* src = vv + (long long)(k + 1) * A.pz + grow;
+          vld_global<T, VG, N>(src, vnext);
+          if (xlast) vnext[N] = src[N];
         }
-      }
-    }
-    // interior planes c = 1 .. N-1
+        // staged row of lattice row j: columns cb-N .. cb+N
+        T xr[2 * N + 1];
+        vld<T, VS, N>(P + own - N, xr);
+        vld<T, VS, N>(P + own, xr + N);
+        xr[2 * N] = P[own + N];
+        T acc[N + 1];
+        // x stencil
+        {
+          T l = T(0), r = T(0);
+          if (xl) {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) l += A.lx[q] * xr[q];
+          }
+#pragma unroll
+          for (int q = 0; q <= N; ++q) r += A.rx[q] * xr[N + q];
+          acc[0] = (l + r) * xiw;
+        }
+#pragma unroll
+        for (int a = 1; a < N; ++a) {
+          T s2 = T(0);
+#pragma unroll
+          for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * xr[N + q];
+          acc[a] = s2;
+        }
+        {
+          T l = T(0);
+#pragma unroll
+          for (int q = 0; q <= N; ++q) l += A.lx[q] * xr[N + q];
+          acc[N] = l * A.iwb;                 // last x node of the box (kept only if xlast)
+        }
+        // y stencil
+        if (yvert) {
+          T ylv[N + 1], yrv[N + 1];
+#pragma unroll
+          for (int a = 0; a <= N; ++a) { ylv[a] = T(0); yrv[a] = T(0); }
+          if (yl) {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) {
+              T t[N + 1];
+              vld<T, VS, N>(P + own + (q - N) * BX, t);
+              t[N] = P[own + (q - N) * BX + N];
+#pragma unroll
+              for (int a = 0; a <= N; ++a) ylv[a] += A.ly[q] * t[a];
+            }
+          }
+          if (yr) {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) {
+              T t[N + 1];
+              vld<T, VS, N>(P + own + q * BX, t);
+              t[N] = P[own + q * BX + N];
+#pragma unroll
+              for (int a = 0; a <= N; ++a) yrv[a] += A.ry[q] * t[a];
+            }
+          }
+#pragma unroll
+          for (int a = 0; a <= N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
+        } else {
+#pragma unroll
+          for (int q = 0; q <= N; ++q) {
+            T t[N + 1];
+            vld<T, VS, N>(P + own + (q - yb) * BX, t);
+            t[N] = P[own + (q - yb) * BX + N];
+#pragma unroll
+            for (int a = 0; a <= N; ++a) acc[a] += cyi[q] * t[a];
+          }
+        }
+        // z stencil: own column over the staged planes of the layer
+        T zs[N + 1];
+        T iw_z;
+        if constexpr (ZM == 0) {
+          zsum<T, N, VS, PLANE>(S0, own, A.rz, zs);
+          iw_z = (ez > 0) ? A.iwv : A.iwb;
+#pragma unroll
+          for (int a = 0; a <= N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
+        } else if constexpr (ZM == 1) {
+          zsum<T, N, VS, PLANE>(S0, own, A.cz[c], zs);
+          iw_z = A.iwa[c];
+        } else {
+          zsum<T, N, VS, PLANE>(S0, own, A.lz, zs);
+          iw_z = A.iwb;
+#pragma unroll
+          for (int a = 0; a <= N; ++a) zs[a] *= iw_z;
+        }
+        // update: a = -(M^-1 K p) (+ extras), v += dtv a, p_out = p + dtp v
+        T vn[N + 1], pn[N + 1];
+#pragma unroll
+        for (int a = 0; a <= N; ++a) {
+          T accum = -(acc[a] + zs[a]);
+          if (extras_layer && (a < N || xlast)) {
+            const T iw_x = (a == 0) ? xiw : (a < N ? A.iwa[a] : A.iwb);
+            const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
+            accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv, ra[a], rb[a], iface_here);
+          }
+          vn[a] = vcur[a] + A.dtv * accum;
+          pn[a] = xr[N + a] + A.dtp * vn[a];
+        }
+        T* vdst = vv + (long long)k * A.pz + grow;
+        T* pdst = pout + (long long)k * A.pz + grow;
+        vst<T, VG, N>(vdst, vn);
+        vst<T, VG, N>(pdst, pn);
+        if (xlast) {
+          vdst[N] = vn[N];
+          pdst[N] = pn[N];
+        }
+#pragma unroll
+        for (int a = 0; a <= N; ++a) vcur[a] = vnext[a];
+      };
+      plane(std::integral_constant<int, 0>(), 0);
 #pragma unroll 1
-    for (int c = 1; c < N; ++c) {
-      const int k = ez * N + c;
-      const T iw_z = A.iwa[c];
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int i = ex * N + a;
-        if (i < A.L0) {
-          T zs = T(0);
-#pragma unroll
-          for (int q = 0; q <= N; ++q) zs += A.cz[c][q] * S[q * PLANE + r0 * CP + cb + a];
-          node_update<T, N, CP>(A, S + c * PLANE, a, i, j, k, b, r0, cb, xl, xr, xiw, yvert, yl, yr, yiw, yb, cyi, iw_y,
-                                zs, iw_z, extras_layer, ra[a], rb[a], iface_here, pout, vv);
-        }
-      }
+      for (int c = 1; c < N; ++c) plane(std::integral_constant<int, 1>(), c);
+      if (last_layer) plane(std::integral_constant<int, 2>(), N);
+      // carry for the vertex plane (ez+1)*N
+      zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
     }
-    // carry for the vertex plane (ez+1)*N
-#pragma unroll
-    for (int a = 0; a < N; ++a) {
-      T s = T(0);
-#pragma unroll
-      for (int q = 0; q <= N; ++q) s += A.lz[q] * S[q * PLANE + r0 * CP + cb + a];
-      carry[a] = s;
-    }
-    // top boundary plane of the box (only the layer below exists)
-    if (ez == A.ne2 - 1) {
-      const int k = A.ne2 * N;
-#pragma unroll
-      for (int a = 0; a < N; ++a) {
-        const int i = ex * N + a;
-        if (i < A.L0) {
-          node_update<T, N, CP>(A, S + N * PLANE, a, i, j, k, b, r0, cb, xl, xr, xiw, yvert, yl, yr, yiw, yb, cyi, iw_y,
-                                carry[a] * A.iwb, A.iwb, extras_layer, ra[a], rb[a], iface_here, pout, vv);
-        }
-      }
+    __syncthreads();   // every thread is done with stage s
+    if (tid == 0 && ez + STAGES < ez1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&bar[s], (uint32_t)G::STAGE_BYTES);
+      tma_load_4d(smem_raw + s * G::STAGE, &A.tmap, &bar[s], x0 - NAL, y0 - N, (ez + STAGES) * N, b);
     }
   }
 }
@@ -292,6 +482,8 @@ vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
 template <typename T, int N>
 VolArgs<T, N> make_args(const VolSpec& s) {
   VolArgs<T, N> a;
+  a.tmap = *s.tmap;
+  a.err = s.err;
   a.p_in = static_cast<const T*>(s.p_in);
   a.p_out = static_cast<T*>(s.p_out);
   a.v = static_cast<T*>(s.v);
@@ -323,22 +515,16 @@ VolArgs<T, N> make_args(const VolSpec& s) {
 }
 
 template <typename T, int N>
-struct TileChoice {
-  // element columns per CTA along x and element rows along y
-  static constexpr int TXE = (N <= 4) ? 32 : 16;
-  static constexpr int TYE = (N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1));
-};
-
-template <typename T, int N>
 cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
   constexpr int TXE = TileChoice<T, N>::TXE, TYE = TileChoice<T, N>::TYE;
-  using Tile = VolTile<T, N, TXE, TYE>;
+  using G = Geo<T, N, TXE, TYE>;
+  if (!s.tmap || !s.err) return cudaErrorInvalidValue;
   VolArgs<T, N> a = make_args<T, N>(s);
   int layers = s.layers_per_cta;
-  const int gx = (s.L[0] + TXE * N - 1) / (TXE * N);
-  const int gy = (s.L[1] + Tile::TYR - 1) / Tile::TYR;
+  const int gx = (s.ne[0] + TXE - 1) / TXE;
+  const int gy = (s.L[1] + G::TYR - 1) / G::TYR;
   if (layers <= 0) {
-    // enough CTAs to cover the GPU several times over
+    // enough CTAs to fill every SM a few times over
     const long long cols = (long long)gx * gy * batch;
     layers = s.ne[2];
     while (layers > 1 && cols * ((s.ne[2] + layers - 1) / layers) < 4 * 152) layers = (layers + 1) / 2;
@@ -346,15 +532,38 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
   auto kern = vol_kernel<T, N, TXE, TYE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
-  dim3 block(TXE, Tile::TYR, 1);
-  kern<<<grid, block, Tile::SMEM, st>>>(a);
+  dim3 block(TXE, G::TYR, 1);
+  kern<<<grid, block, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
+template <typename T, int N>
+void box_n(unsigned box[3]) {
+  constexpr int TXE = TileChoice<T, N>::TXE, TYE = TileChoice<T, N>::TYE;
+  using G = Geo<T, N, TXE, TYE>;
+  box[0] = G::BX;
+  box[1] = G::BY;
+  box[2] = G::BZ;
+}
+
 }  // namespace
+
+void vol_tma_box(int N, bool fp32, unsigned box[3]) {
+  box[0] = box[1] = box[2] = 0;
+  switch (N) {
+#define DG_BOX(n)                       \
+  case n:                               \
+    if (fp32) box_n<float, n>(box);     \
+    else box_n<double, n>(box);         \
+    break;
+    DG_BOX(1) DG_BOX(2) DG_BOX(3) DG_BOX(4) DG_BOX(5) DG_BOX(6) DG_BOX(7) DG_BOX(8)
+#undef DG_BOX
+    default: break;
+  }
+}
 
 template <typename T>
 cudaError_t launch_vol(const VolSpec& s, int batch, cudaStream_t st) {
