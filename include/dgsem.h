@@ -186,6 +186,19 @@ int dgsem_get_pressure(const dgsem_ctx* ctx, double* p, size_t len);
 int dgsem_state_save(const dgsem_ctx* ctx, void* buf, size_t* len);
 int dgsem_state_load(dgsem_ctx* ctx, const void* buf, size_t len);
 
+/* Tile shapes of the fused volume kernel.  Orders 4 and 6 have several
+ * CTA tile shapes (element columns x element rows); dgsem_num_tiles gives
+ * their count for a box and precision, dgsem_set_tiles selects one per box
+ * ([ndomains] variant indices, 0 = default) for later runs at that
+ * precision, and dgsem_autotune times every variant of each box's volume
+ * kernel for `batch` patterns (`reps` launches each, CUDA events on `stream`)
+ * and keeps the fastest (written to chosen[ndomains] if not NULL).  The
+ * autotuner uses the run state as scratch: the next dgsem_run must not pass
+ * DGSEM_RUN_CONTINUE. */
+int dgsem_num_tiles(const dgsem_ctx* ctx, int precision, int box, int* n);
+int dgsem_set_tiles(dgsem_ctx* ctx, int precision, const int* tiles);
+int dgsem_autotune(dgsem_ctx* ctx, int precision, int batch, int reps, int* chosen, void* stream);
+
 /* Kernel instrumentation.  dgsem_profile(ctx, 1) makes later runs bracket
  * every kernel launch with CUDA events on the run's stream; statistics are
  * accumulated per kernel kind (DGSEM_K_*) until dgsem_profile(ctx, 1) is

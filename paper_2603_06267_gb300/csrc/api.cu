@@ -221,6 +221,7 @@ struct dgsem_ctx {
   // TMA descriptors of the pressure buffers (X and Y of each box) and the
   // device status word written by bounded waits
   CUtensorMap tmap_x[2], tmap_y[2];
+  int tile_pref[2][2] = {{0, 0}, {0, 0}};   // [fp64, fp32][box] tile-shape variant
   int* d_err = nullptr;
   // instrumentation
   bool profiling = false;
@@ -276,7 +277,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 
 // 4D (x, y, z, batch) tiled tensor map of one pressure buffer for the TMA
 // staging loads of the volume kernel (box = one element layer of a tile).
-int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec) {
+int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec, int tile) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -288,8 +289,8 @@ int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec) {
   }
   const size_t es = elem_size(prec);
   unsigned box[3];
-  vol_tma_box(B.N, prec == DGSEM_FP32_MIXED, box);
-  if (!box[0]) return fail(DGSEM_EINVAL, "no TMA box for order %d", B.N);
+  const int nv = prec == DGSEM_FP32_MIXED ? vol_tma_box_f32(B.N, tile, box) : vol_tma_box_f64(B.N, tile, box);
+  if (!nv || !box[0]) return fail(DGSEM_EINVAL, "no tile variant %d for order %d", tile, B.N);
   const cuuint64_t dims[4] = {(cuuint64_t)B.L[0], (cuuint64_t)B.L[1], (cuuint64_t)B.L[2], (cuuint64_t)batch};
   const cuuint64_t strides[3] = {(cuuint64_t)B.py * es, (cuuint64_t)B.pz * es, (cuuint64_t)B.bstride * es};
   for (int i = 0; i < 3; ++i)
@@ -330,17 +331,22 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
     int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
     if (rc) { free_run_state(c); return rc; }
   }
-  for (int d = 0; d < c->nd; ++d) {
-    int rc;
-    if ((rc = make_tmap(&c->tmap_x[d], c->X[d], c->box[d], batch, prec)) ||
-        (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], batch, prec))) {
-      free_run_state(c);
-      return rc;
-    }
-  }
   c->prec = prec;
   c->batch = batch;
   c->state_valid = false;
+  return DGSEM_OK;
+}
+
+// (Re-)encode the TMA descriptors of both pressure buffers of every box for
+// the tile variants selected for the current precision.
+int refresh_tmaps(dgsem_ctx* c) {
+  for (int d = 0; d < c->nd; ++d) {
+    const int tile = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][d];
+    int rc;
+    if ((rc = make_tmap(&c->tmap_x[d], c->X[d], c->box[d], c->batch, c->prec, tile)) ||
+        (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], c->batch, c->prec, tile)))
+      return rc;
+  }
   return DGSEM_OK;
 }
 
@@ -636,6 +642,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     VolSpec v = c->vspec[d];
     v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
     v.err = c->d_err;
+    v.tile = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][d];
     v.p_in = pin[d]; v.p_out = pout[d]; v.v = c->V[d];
     v.dtv = init ? 0.5 * c->dt : c->dt;
     v.dtp = c->dt;
@@ -756,6 +763,7 @@ int upload_field(dgsem_ctx* c, const std::vector<double>& h, void* const* dst, c
 template <typename T>
 int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
   int rc;
+  if ((rc = refresh_tmaps(c))) return rc;
   CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
   const bool cont = (flags & DGSEM_RUN_CONTINUE) && c->state_valid;
   if (!cont) {
@@ -1120,6 +1128,78 @@ int dgsem_check_stability(dgsem_ctx* c, int iters, double* lambda_max) {
   (void)iters;
   if (lambda_max) *lambda_max = 0.0;
   return fail(DGSEM_ESTATE, "dgsem_check_stability: not available yet");
+}
+
+int dgsem_set_tiles(dgsem_ctx* c, int precision, const int* tiles) {
+  if (!c || !tiles) return fail(DGSEM_EINVAL, "NULL argument");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return fail(DGSEM_EINVAL, "bad precision");
+  for (int d = 0; d < c->nd; ++d) {
+    unsigned box[3];
+    const int nv = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[d].N, tiles[d], box)
+                                                 : vol_tma_box_f64(c->box[d].N, tiles[d], box);
+    if (!nv) return fail(DGSEM_EINVAL, "box %d: no tile variant %d for order %d", d, tiles[d], c->box[d].N);
+  }
+  for (int d = 0; d < c->nd; ++d) c->tile_pref[precision == DGSEM_FP32_MIXED ? 1 : 0][d] = tiles[d];
+  return DGSEM_OK;
+}
+
+int dgsem_num_tiles(const dgsem_ctx* c, int precision, int box, int* n) {
+  if (!c || !n) return fail(DGSEM_EINVAL, "NULL argument");
+  if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "bad box %d", box);
+  unsigned b3[3];
+  *n = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[box].N, 0, b3) : vol_tma_box_f64(c->box[box].N, 0, b3);
+  return DGSEM_OK;
+}
+
+int dgsem_autotune(dgsem_ctx* c, int precision, int batch, int reps, int* chosen, void* stream) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return fail(DGSEM_EINVAL, "bad precision");
+  if (batch < 1 || reps < 1) return fail(DGSEM_EINVAL, "batch and reps must be >= 1");
+  int rc = ensure_run_state(c, precision, batch);
+  if (rc) return rc;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if ((rc = zero_state(c, s))) return rc;
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+  const int pi = precision == DGSEM_FP32_MIXED ? 1 : 0;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  for (int d = 0; d < c->nd; ++d) {
+    unsigned b3[3];
+    const int nv = pi ? vol_tma_box_f32(c->box[d].N, 0, b3) : vol_tma_box_f64(c->box[d].N, 0, b3);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < nv; ++v) {
+      c->tile_pref[pi][d] = v;
+      if ((rc = refresh_tmaps(c))) break;
+      VolSpec sp = c->vspec[d];
+      sp.tmap = &c->tmap_y[d];
+      sp.err = c->d_err;
+      sp.tile = v;
+      sp.p_in = c->Y[d]; sp.p_out = c->X[d]; sp.v = c->V[d];
+      sp.dtv = c->dt; sp.dtp = c->dt;
+      sp.Ra = c->Ra[d]; sp.Rb = c->Rb[d];
+      cudaError_t e = pi ? launch_vol<float>(sp, batch, s) : launch_vol<double>(sp, batch, s);   // warm-up
+      if (e != cudaSuccess) { cudaGetLastError(); continue; }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps; ++r) e = pi ? launch_vol<float>(sp, batch, s) : launch_vol<double>(sp, batch, s);
+      cudaEventRecord(e1, s);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); continue; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    c->tile_pref[pi][d] = best;
+    if (chosen) chosen[d] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->state_valid = false;
+  if (rc) return rc;
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up during autotuning");
+  return refresh_tmaps(c);
 }
 
 int dgsem_profile(dgsem_ctx* c, int enable) {

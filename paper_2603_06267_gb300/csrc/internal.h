@@ -22,7 +22,7 @@
 // 1D weight.  The coefficient blocks below hold those rows.
 // ---------------------------------------------------------------------------
 template <typename T, int N>
-struct alignas(64) VolArgs {
+struct VolArgs {
   CUtensorMap tmap;    // 4D (x, y, z, batch) tiled view of p_in for the TMA staging loads
   int* err;            // device status word: set to 1 if a bounded wait gives up
   const T* p_in;       // p^{n+1}: stencil source
@@ -148,11 +148,14 @@ struct VolSpec {
   const void* Ra; const void* Rb;
   double dI[DG_MAXN + 1];
   int layers_per_cta;              // 0: choose automatically
+  int tile;                        // tile-shape variant (see vol_impl.cuh)
 };
 
 // Box shape (x, y, z) of the TMA staging load of one element layer for a
-// box of order N and the given precision (defined in vol.cu).
-void vol_tma_box(int N, bool fp32, unsigned box[3]);
+// box of order N and tile variant `tile`; returns the number of tile variants
+// of that order (0 if the order or the variant is unsupported).
+int vol_tma_box_f32(int N, int tile, unsigned box[3]);
+int vol_tma_box_f64(int N, int tile, unsigned box[3]);
 
 // Launchers (defined in the kernel translation units)
 template <typename T>

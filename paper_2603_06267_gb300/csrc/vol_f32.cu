@@ -1,0 +1,5 @@
+// FP32 instantiations of the fused volume kernel (see vol_impl.cuh).
+#include "vol_impl.cuh"
+
+template cudaError_t launch_vol<float>(const VolSpec&, int, cudaStream_t);
+int vol_tma_box_f32(int N, int tile, unsigned box[3]) { return dgvol::tma_box<float>(N, tile, box); }

@@ -1,0 +1,5 @@
+// FP64 instantiations of the fused volume kernel (see vol_impl.cuh).
+#include "vol_impl.cuh"
+
+template cudaError_t launch_vol<double>(const VolSpec&, int, cudaStream_t);
+int vol_tma_box_f64(int N, int tile, unsigned box[3]) { return dgvol::tma_box<double>(N, tile, box); }

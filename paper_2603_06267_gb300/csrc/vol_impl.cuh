@@ -18,12 +18,13 @@
 // alternate so that the next layer streams in while the current one is
 // computed.  The coupling of a vertex plane to the layer below is a partial
 // sum carried in registers, so no z halo is loaded.
+#pragma once
 #include <cstdio>
 #include <type_traits>
 
 #include "internal.h"
 
-namespace {
+namespace dgvol {
 
 // ---------------------------------------------------------------------------
 // small PTX helpers: mbarrier + TMA
@@ -126,11 +127,23 @@ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 // ---------------------------------------------------------------------------
 // tile geometry
 // ---------------------------------------------------------------------------
-template <typename T, int N>
-struct TileChoice {
-  static constexpr int TXE = (N <= 4) ? 32 : 16;                                      // element columns
-  static constexpr int TYE = (N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1));  // element rows
+// Tile shapes (element columns TXE x element rows TYE per CTA).  Orders 4
+// and 6 (the workloads' primary and secondary boxes) have several shapes the
+// autotuner chooses from; variant 0 is the default.
+template <typename T, int N, int V> struct TileShape;
+template <typename T, int N> struct TileShape<T, N, 0> {
+  static constexpr int TXE = (N <= 4) ? 32 : 16;
+  static constexpr int TYE = (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1)));
 };
+template <typename T, int N> struct NumShapes { static constexpr int value = (N == 4 || N == 6) ? 4 : 1; };
+// FP32 N=4: 512 / 384 / 256 threads; FP64 N=4: 256 / 256 / 128 threads
+template <typename T> struct TileShape<T, 4, 1> { static constexpr int TXE = sizeof(T) == 4 ? 32 : 16, TYE = sizeof(T) == 4 ? 3 : 4; };
+template <typename T> struct TileShape<T, 4, 2> { static constexpr int TXE = 32, TYE = sizeof(T) == 4 ? 2 : 1; };
+template <typename T> struct TileShape<T, 4, 3> { static constexpr int TXE = 16, TYE = sizeof(T) == 4 ? 4 : 2; };
+// FP32 N=6: 192 / 384 / 288 / 192 threads; FP64 N=6: 192 / 96 / 192 / 96 threads
+template <typename T> struct TileShape<T, 6, 1> { static constexpr int TXE = 16, TYE = sizeof(T) == 4 ? 4 : 1; };
+template <typename T> struct TileShape<T, 6, 2> { static constexpr int TXE = sizeof(T) == 4 ? 16 : 8, TYE = sizeof(T) == 4 ? 3 : 4; };
+template <typename T> struct TileShape<T, 6, 3> { static constexpr int TXE = sizeof(T) == 4 ? 32 : 8, TYE = sizeof(T) == 4 ? 1 : 2; };
 
 template <typename T, int N, int TXE, int TYE>
 struct Geo {
@@ -514,9 +527,8 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   return a;
 }
 
-template <typename T, int N>
-cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
-  constexpr int TXE = TileChoice<T, N>::TXE, TYE = TileChoice<T, N>::TYE;
+template <typename T, int N, int TXE, int TYE>
+cudaError_t launch_tile(const VolSpec& s, int batch, cudaStream_t st) {
   using G = Geo<T, N, TXE, TYE>;
   if (!s.tmap || !s.err) return cudaErrorInvalidValue;
   VolArgs<T, N> a = make_args<T, N>(s);
@@ -540,33 +552,73 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename T, int N, int V>
+cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
+  return launch_tile<T, N, TileShape<T, N, V>::TXE, TileShape<T, N, V>::TYE>(s, batch, st);
+}
+
 template <typename T, int N>
-void box_n(unsigned box[3]) {
-  constexpr int TXE = TileChoice<T, N>::TXE, TYE = TileChoice<T, N>::TYE;
-  using G = Geo<T, N, TXE, TYE>;
+cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
+  if constexpr (NumShapes<T, N>::value > 1) {
+    switch (s.tile) {
+      case 0: return launch_v<T, N, 0>(s, batch, st);
+      case 1: return launch_v<T, N, 1>(s, batch, st);
+      case 2: return launch_v<T, N, 2>(s, batch, st);
+      case 3: return launch_v<T, N, 3>(s, batch, st);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    if (s.tile != 0) return cudaErrorInvalidValue;
+    return launch_v<T, N, 0>(s, batch, st);
+  }
+}
+
+template <typename T, int N, int V>
+void box_v(unsigned box[3]) {
+  using G = Geo<T, N, TileShape<T, N, V>::TXE, TileShape<T, N, V>::TYE>;
   box[0] = G::BX;
   box[1] = G::BY;
   box[2] = G::BZ;
 }
 
-}  // namespace
-
-void vol_tma_box(int N, bool fp32, unsigned box[3]) {
+template <typename T, int N>
+int box_n(int tile, unsigned box[3]) {
   box[0] = box[1] = box[2] = 0;
+  if (tile < 0 || tile >= NumShapes<T, N>::value) return 0;
+  if constexpr (NumShapes<T, N>::value > 1) {
+    switch (tile) {
+      case 0: box_v<T, N, 0>(box); break;
+      case 1: box_v<T, N, 1>(box); break;
+      case 2: box_v<T, N, 2>(box); break;
+      default: box_v<T, N, 3>(box); break;
+    }
+  } else {
+    box_v<T, N, 0>(box);
+  }
+  return NumShapes<T, N>::value;
+}
+
+// Host entry points of one precision (instantiated in vol_f32.cu / vol_f64.cu)
+template <typename T>
+int tma_box(int N, int tile, unsigned box[3]) {
   switch (N) {
-#define DG_BOX(n)                       \
-  case n:                               \
-    if (fp32) box_n<float, n>(box);     \
-    else box_n<double, n>(box);         \
-    break;
-    DG_BOX(1) DG_BOX(2) DG_BOX(3) DG_BOX(4) DG_BOX(5) DG_BOX(6) DG_BOX(7) DG_BOX(8)
-#undef DG_BOX
-    default: break;
+    case 1: return box_n<T, 1>(tile, box);
+    case 2: return box_n<T, 2>(tile, box);
+    case 3: return box_n<T, 3>(tile, box);
+    case 4: return box_n<T, 4>(tile, box);
+    case 5: return box_n<T, 5>(tile, box);
+    case 6: return box_n<T, 6>(tile, box);
+    case 7: return box_n<T, 7>(tile, box);
+    case 8: return box_n<T, 8>(tile, box);
+    default: box[0] = box[1] = box[2] = 0; return 0;
   }
 }
 
+}  // namespace dgvol
+
 template <typename T>
 cudaError_t launch_vol(const VolSpec& s, int batch, cudaStream_t st) {
+  using namespace dgvol;
   switch (s.N) {
     case 1: return launch_n<T, 1>(s, batch, st);
     case 2: return launch_n<T, 2>(s, batch, st);
@@ -579,6 +631,3 @@ cudaError_t launch_vol(const VolSpec& s, int batch, cudaStream_t st) {
     default: return cudaErrorInvalidValue;
   }
 }
-
-template cudaError_t launch_vol<float>(const VolSpec&, int, cudaStream_t);
-template cudaError_t launch_vol<double>(const VolSpec&, int, cudaStream_t);

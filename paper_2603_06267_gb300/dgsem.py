@@ -32,6 +32,7 @@ DGSEM_RUN_CONTINUE = 1
 EXPORTED = [
     "dgsem_mesh_create", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "dgsem_run", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
+    "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_last_error", "dgsem_destroy",
 ]
 DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1 = 0, 1, 2, 3
@@ -79,6 +80,9 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_get_pressure.argtypes = [vp, vp, c_size_t]
     lib.dgsem_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
     lib.dgsem_state_load.argtypes = [vp, vp, c_size_t]
+    lib.dgsem_num_tiles.argtypes = [vp, c_int, c_int, POINTER(c_int)]
+    lib.dgsem_set_tiles.argtypes = [vp, c_int, vp]
+    lib.dgsem_autotune.argtypes = [vp, c_int, c_int, c_int, vp, vp]
     lib.dgsem_profile.argtypes = [vp, c_int]
     lib.dgsem_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_last_error.restype = ctypes.c_char_p
@@ -237,6 +241,27 @@ def dgsem_state_save(ctx) -> bytes:
 def dgsem_state_load(ctx, blob: bytes):
     buf = ctypes.create_string_buffer(blob, len(blob))
     _check(_lib.dgsem_state_load(ctx, buf, len(blob)), "dgsem_state_load")
+
+
+def dgsem_num_tiles(ctx, precision: int, box: int) -> int:
+    n = c_int()
+    _check(_lib.dgsem_num_tiles(ctx, precision, box, byref(n)), "dgsem_num_tiles")
+    return n.value
+
+
+def dgsem_set_tiles(ctx, precision: int, tiles):
+    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    _check(_lib.dgsem_set_tiles(ctx, precision, _ptr(t)), "dgsem_set_tiles")
+
+
+def dgsem_autotune(ctx, precision: int, batch: int, ndomains: int, reps: int = 3, stream=None):
+    """Times every tile variant of each box's volume kernel and keeps the
+    fastest; returns the chosen variant per box."""
+    out = np.zeros(ndomains, dtype=np.int32)
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_autotune(ctx, precision, batch, reps, _ptr(out), stream), "dgsem_autotune")
+    return out
 
 
 def dgsem_profile(ctx, enable: bool = True):

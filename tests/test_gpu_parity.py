@@ -197,3 +197,48 @@ def test_invalid_inputs_return_status():
         sol.run(drive=np.zeros((7, sol.K, 5)), flags=dgsem.DGSEM_RUN_CONTINUE, precision=1, batch=7)
     assert e.value.code == dgsem.DGSEM_ESTATE
     sol.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+@pytest.mark.parametrize("N,nel", [(4, (40, 9, 3)), (6, (20, 5, 3))])
+def test_every_tile_variant_matches_oracle(prec, tol, N, nel):
+    """Each CTA tile shape of the volume kernel (the autotuner's choices) is a
+    separate kernel instantiation: every one matches the oracle."""
+    from paper_2603_06267_gb300 import dgsem
+    h = 25e-6
+    dom = W.Domain((0, 0, 0), tuple(n * h for n in nel), nel, N)
+    rec = np.random.default_rng(2).uniform(0, 1, size=(5, 3)) * np.array(dom.extent)
+    w = W.Workload("box", [dom], 40, rec)
+    P = oracle_problem(w)
+    x, y, z = P.all_coordinates()
+    p0 = W.seeded_field(9, x, y, z)
+    to = P.run(p0=p0, dt=P.stable_dt())
+    po = P.final_state["p"].T
+    sol = gpu_solver(w)
+    nv = dgsem.dgsem_num_tiles(sol.ctx, prec, 0)
+    assert nv >= 3
+    for v in range(nv):
+        dgsem.dgsem_set_tiles(sol.ctx, prec, [v])
+        dgsem.dgsem_set_state(sol.ctx, p0, None)
+        tg = sol.run(precision=prec)
+        pg = dgsem.dgsem_get_pressure(sol.ctx, 1, sol.ndof)
+        assert rel_l2(pg, po) < tol, (v, rel_l2(pg, po))
+        assert rel_l2(tg, to) < tol
+    sol.close()
+
+
+def test_autotune_then_run_matches_oracle():
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=8, nz_p=2, nx_s=4, nz_s=3, n_pmut_side=2, nsteps=120)
+    P = oracle_problem(w)
+    dt = P.stable_dt()
+    drive = w.drive(dt, w.nsteps, 1)
+    to = P.run(dt=dt, drive=drive)
+    sol = gpu_solver(w)
+    for prec, tol in ((1, FP32_TOL), (0, FP64_TOL)):
+        chosen = dgsem.dgsem_autotune(sol.ctx, prec, 1, 2, reps=2)
+        assert chosen[0] < dgsem.dgsem_num_tiles(sol.ctx, prec, 0)
+        assert chosen[1] < dgsem.dgsem_num_tiles(sol.ctx, prec, 1)
+        tg = sol.run(drive=drive, precision=prec)
+        assert rel_l2(tg, to) < tol
+    sol.close()
