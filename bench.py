@@ -225,6 +225,8 @@ def main():
     B = w.batch
     sol = dgsem.Solver(w)
     ndof = sol.ndof
+    # untimed setup: pick the volume-kernel tile shape per box for this batch
+    tiles = dgsem.dgsem_autotune(sol.ctx, prec, B, len(w.domains), reps=2)
     K_p = w.pmuts.n_pmut if w.pmuts is not None else 0
     R = w.receivers.shape[0]
     S_tot = args.warmup + args.steps
@@ -329,6 +331,7 @@ def main():
         "config": {"workload": name, "precision": "fp32-mixed" if prec == dgsem.DGSEM_FP32_MIXED else "fp64",
                    "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
                    "parallelism": f"replicas x{world}" if world > 1 else "single-gpu",
+                   "tiles": [int(t) for t in tiles],
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(4)},

@@ -220,9 +220,17 @@ struct dgsem_ctx {
   size_t recv_cap = 0;
   // TMA descriptors of the pressure buffers (X and Y of each box) and the
   // device status word written by bounded waits
-  CUtensorMap tmap_x[2], tmap_y[2];
+  CUtensorMap tmap_x[2], tmap_y[2], tmap_v[2];
+  bool has_tmap_v[2] = {false, false};
   int tile_pref[2][2] = {{0, 0}, {0, 0}};   // [fp64, fp32][box] tile-shape variant
   int* d_err = nullptr;
+  int* d_step = nullptr;                      // step counter of the current run
+  // CUDA graph of a block of steps, replayed by dgsem_run
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  long long graph_launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
+  std::vector<unsigned char> graph_key;
   // instrumentation
   bool profiling = false;
   long long launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
@@ -259,7 +267,14 @@ int upload(V** d, const std::vector<V>& h) {
   return DGSEM_OK;
 }
 
+void drop_graph(dgsem_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+  c->graph_key.clear();
+}
+
 void free_run_state(dgsem_ctx* c) {
+  drop_graph(c);
   for (int d = 0; d < 2; ++d) {
     dfree(c->X[d]); dfree(c->Y[d]); dfree(c->V[d]); dfree(c->Ra[d]); dfree(c->Rb[d]);
   }
@@ -275,9 +290,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// 4D (x, y, z, batch) tiled tensor map of one pressure buffer for the TMA
-// staging loads of the volume kernel (box = one element layer of a tile).
-int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec, int tile) {
+// 4D (x, y, z, batch) tiled tensor map of one state buffer of a box for the
+// TMA staging loads of the volume kernel (box = one element layer of a tile).
+int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec, const unsigned box[3]) {
   static EncodeTiledFn encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -288,9 +303,8 @@ int make_tmap(CUtensorMap* out, void* base, const Box& B, int batch, int prec, i
     encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
   const size_t es = elem_size(prec);
-  unsigned box[3];
-  const int nv = prec == DGSEM_FP32_MIXED ? vol_tma_box_f32(B.N, tile, box) : vol_tma_box_f64(B.N, tile, box);
-  if (!nv || !box[0]) return fail(DGSEM_EINVAL, "no tile variant %d for order %d", tile, B.N);
+  if (!box[0] || !box[1] || !box[2]) return fail(DGSEM_EINVAL, "empty TMA box");
+  if ((box[0] * es) % 16) return fail(DGSEM_EINVAL, "TMA box row not a multiple of 16 bytes");
   const cuuint64_t dims[4] = {(cuuint64_t)B.L[0], (cuuint64_t)B.L[1], (cuuint64_t)B.L[2], (cuuint64_t)batch};
   const cuuint64_t strides[3] = {(cuuint64_t)B.py * es, (cuuint64_t)B.pz * es, (cuuint64_t)B.bstride * es};
   for (int i = 0; i < 3; ++i)
@@ -342,10 +356,16 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
 int refresh_tmaps(dgsem_ctx* c) {
   for (int d = 0; d < c->nd; ++d) {
     const int tile = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][d];
+    unsigned box[3], vbox[3];
+    const int nv = c->prec == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[d].N, tile, box, vbox)
+                                               : vol_tma_box_f64(c->box[d].N, tile, box, vbox);
+    if (!nv) return fail(DGSEM_EINVAL, "no tile variant %d for order %d", tile, c->box[d].N);
     int rc;
-    if ((rc = make_tmap(&c->tmap_x[d], c->X[d], c->box[d], c->batch, c->prec, tile)) ||
-        (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], c->batch, c->prec, tile)))
+    if ((rc = make_tmap(&c->tmap_x[d], c->X[d], c->box[d], c->batch, c->prec, box)) ||
+        (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], c->batch, c->prec, box)))
       return rc;
+    c->has_tmap_v[d] = vbox[0] != 0;
+    if (c->has_tmap_v[d] && (rc = make_tmap(&c->tmap_v[d], c->V[d], c->box[d], c->batch, c->prec, vbox))) return rc;
   }
   return DGSEM_OK;
 }
@@ -611,7 +631,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     const long long km = (long long)c->K * c->M;
     a.omega2 = c->d_modal; a.twozw = c->d_modal ? c->d_modal + km : nullptr;
     a.inv_mu = c->d_modal ? c->d_modal + 2 * km : nullptr; a.eta = c->d_modal ? c->d_modal + 3 * km : nullptr;
-    a.drive = drive; a.dbs = dbs; a.dks = dks; a.n = n_local; a.dt = c->dt;
+    a.drive = drive; a.dbs = dbs; a.dks = dks; a.n = n_local; a.step = c->d_step; a.dt = c->dt;
     a.R = R; a.rstride = 0;
     if (R > 0) {
       int maxn = 0;
@@ -641,8 +661,10 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
   for (int d = 0; d < c->nd; ++d) {
     VolSpec v = c->vspec[d];
     v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
+    v.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
     v.err = c->d_err;
     v.tile = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][d];
+    v.step = (!init && d == c->nd - 1) ? c->d_step : nullptr;
     v.p_in = pin[d]; v.p_out = pout[d]; v.v = c->V[d];
     v.dtv = init ? 0.5 * c->dt : c->dt;
     v.dtp = c->dt;
@@ -723,6 +745,7 @@ int setup_receivers(dgsem_ctx* c, int R, const double* xyz) {
     nn[r] = t;
   }
   if ((size_t)R * maxn > c->recv_cap) {
+    drop_graph(c);   // the captured kernels hold the old receiver buffers
     dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
     c->recv_cap = 0;
     int rc;
@@ -783,6 +806,7 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
       d_drive = drive;
     } else {
       if (drive_n > c->drive_cap) {
+        drop_graph(c);
         dfree(c->d_drive);
         if ((rc = dalloc(&c->d_drive, drive_n * sizeof(double)))) { c->drive_cap = 0; return rc; }
         c->drive_cap = drive_n;
@@ -800,6 +824,7 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     } else {
       tr_host = true;
       if (tr_n > c->traces_cap) {
+        drop_graph(c);
         dfree(c->d_traces);
         if ((rc = dalloc(&c->d_traces, tr_n * sizeof(double)))) { c->traces_cap = 0; return rc; }
         c->traces_cap = tr_n;
@@ -807,9 +832,49 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
       d_tr = c->d_traces;
     }
   }
-  for (int n = 0; n < nsteps; ++n) {
-    rc = launch_step<T>(c, s, d_drive, (long long)c->K * nsteps, nsteps, n, R, d_tr, (long long)R * nsteps, nsteps,
-                        false);
+  CUDA_TRY(cudaMemsetAsync(c->d_step, 0, sizeof(int), s));
+  const long long dbs = (long long)c->K * nsteps, dks = nsteps, tbs = (long long)R * nsteps, trs = nsteps;
+  int done = 0;
+  if (!c->profiling && nsteps >= 4) {
+    // replay a captured block of G (even) steps; the kernels read the step
+    // index from the device counter, so the same graph serves every block
+    const int G = std::min(32, nsteps - (nsteps % 2));
+    struct Key { int prec, batch, R, G; const void* dr; const void* tr; long long dbs, tbs; const void* x0; const void* y0; int t0, t1; } key;
+    std::memset(&key, 0, sizeof(key));
+    key.prec = c->prec; key.batch = c->batch; key.R = R; key.G = G; key.dr = d_drive; key.tr = d_tr;
+    key.dbs = dbs; key.tbs = tbs; key.x0 = c->X[0]; key.y0 = c->Y[0];
+    key.t0 = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][0]; key.t1 = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][1];
+    std::vector<unsigned char> kb(reinterpret_cast<unsigned char*>(&key), reinterpret_cast<unsigned char*>(&key) + sizeof(key));
+    if (!c->graph || c->graph_key != kb) {
+      if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+      if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      long long before[DGSEM_K_COUNT];
+      for (int k = 0; k < DGSEM_K_COUNT; ++k) before[k] = c->launches[k];
+      CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int crc = DGSEM_OK;
+      for (int n = 0; n < G && crc == DGSEM_OK; ++n)
+        crc = launch_step<T>(c, c->cap_stream, d_drive, dbs, dks, 0, R, d_tr, tbs, trs, false);
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+      if (crc) { if (g) cudaGraphDestroy(g); return crc; }
+      if (ce != cudaSuccess) return fail(DGSEM_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) { c->graph = nullptr; return fail(DGSEM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce)); }
+      for (int k = 0; k < DGSEM_K_COUNT; ++k) {
+        c->graph_launches[k] = c->launches[k] - before[k];
+        c->launches[k] = before[k];
+      }
+      c->graph_steps = G;
+      c->graph_key = kb;
+    }
+    for (; done + G <= nsteps; done += G) {
+      CUDA_TRY(cudaGraphLaunch(c->graph, s));
+      for (int k = 0; k < DGSEM_K_COUNT; ++k) c->launches[k] += c->graph_launches[k];
+    }
+  }
+  for (int n = done; n < nsteps; ++n) {
+    rc = launch_step<T>(c, s, d_drive, dbs, dks, 0, R, d_tr, tbs, trs, false);
     if (rc) return rc;
   }
   c->step += nsteps;
@@ -886,8 +951,10 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
   }
   {
     int rc = dalloc(&c->d_err, sizeof(int));
+    if (!rc) rc = dalloc(&c->d_step, sizeof(int));
     if (rc) { dgsem_destroy(c); return rc; }
     CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+    CUDA_TRY(cudaMemset(c->d_step, 0, sizeof(int)));
   }
   c->dt = desc->dt > 0.0 ? desc->dt : desc->cfl * hmin / cmax;
   c->kappa = c->box[0].rho * c->box[0].c * c->box[0].c;
@@ -949,7 +1016,8 @@ int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* f
     for (long long e = 0; e < (long long)nnz * M; ++e)
       if (!std::isfinite(shape_un[e])) return fail(DGSEM_EINVAL, "shape_un[%lld] not finite", e);
   }
-  // release previous array
+  // release previous array (and any captured graph using it)
+  drop_graph(c);
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
   dfree(c->d_ent_pmut); dfree(c->d_modal); dfree(c->q_state);
   c->K = 0; c->M = 0; c->nnz = 0;
@@ -1125,18 +1193,104 @@ int dgsem_state_load(dgsem_ctx* c, const void* buf, size_t len) {
 
 int dgsem_check_stability(dgsem_ctx* c, int iters, double* lambda_max) {
   if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
-  (void)iters;
+  if (iters < 1) return fail(DGSEM_EINVAL, "iters must be >= 1");
   if (lambda_max) *lambda_max = 0.0;
-  return fail(DGSEM_ESTATE, "dgsem_check_stability: not available yet");
+  int rc = ensure_run_state(c, DGSEM_FP64, 1);
+  if (rc) return rc;
+  if ((rc = refresh_tmaps(c))) return rc;
+  cudaStream_t s = 0;
+  if ((rc = zero_state(c, s))) return rc;
+  c->state_valid = false;
+  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+  // assembled 1D GLL weights of every box (the lumped mass is their product)
+  std::vector<double*> dw;
+  auto cleanup = [&]() { for (double* p : dw) cudaFree(p); };
+  double* d_red = nullptr;
+  if ((rc = dalloc(&d_red, 2 * sizeof(double)))) return rc;
+  dw.push_back(d_red);
+  double* w1[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  for (int d = 0; d < c->nd; ++d)
+    for (int k = 0; k < 3; ++k) {
+      std::vector<double> w(c->box[d].L[k]);
+      for (int i = 0; i < c->box[d].L[k]; ++i) w[i] = c->box[d].basis->assembled_weight(i, c->box[d].ne[k]);
+      if ((rc = upload(&w1[d][k], w))) { cleanup(); return rc; }
+      dw.push_back(w1[d][k]);
+    }
+  // deterministic pseudo-random start vector (LCG)
+  std::vector<double> x0(c->ndof);
+  unsigned long long st = 0x9E3779B97F4A7C15ull;
+  for (auto& v : x0) { st = st * 6364136223846793005ull + 1442695040888963407ull; v = (double)(st >> 11) / 9007199254740992.0 - 0.5; }
+  if ((rc = upload_field<double>(c, x0, c->X, s))) { cleanup(); return rc; }
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    // V = -M^-1 K X  (volume kernel with v = 0, dtv = 1, dtp = 0, no PMUT forcing)
+    for (int d = 0; d < c->nd; ++d) CUDA_TRY(cudaMemsetAsync(c->V[d], 0, c->box[d].bstride * sizeof(double), s));
+    if (c->has_iface) {
+      IfaceArgs<double> a = iface_args<double>(c);
+      a.pp = static_cast<const double*>(c->X[0]);
+      a.ps = static_cast<const double*>(c->X[1]);
+      CUDA_TRY(launch_iface<double>(a, 1, s));
+    }
+    for (int d = 0; d < c->nd; ++d) {
+      VolSpec v = c->vspec[d];
+      v.tmap = &c->tmap_x[d];
+      v.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
+      v.err = c->d_err;
+      v.tile = c->tile_pref[0][d];
+      v.p_in = c->X[d]; v.p_out = c->Y[d]; v.v = c->V[d];
+      v.dtv = 1.0; v.dtp = 0.0;
+      v.Ra = c->Ra[d]; v.Rb = c->Rb[d];
+      CUDA_TRY(launch_vol<double>(v, 1, s));
+    }
+    // Rayleigh quotient x.K x / x.M x = -(x.M v)/(x.M x), and the norm of v
+    CUDA_TRY(cudaMemsetAsync(d_red, 0, 2 * sizeof(double), s));
+    for (int d = 0; d < c->nd; ++d) {
+      const Box& B = c->box[d];
+      const double scale = B.h[0] * B.h[1] * B.h[2] / 8.0;
+      CUDA_TRY(launch_mdot((const double*)c->X[d], (const double*)c->V[d], w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1],
+                           B.L[2], B.py, B.pz, scale, d_red, s));
+      CUDA_TRY(launch_mdot((const double*)c->V[d], (const double*)c->V[d], w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1],
+                           B.L[2], B.py, B.pz, scale, d_red + 1, s));
+    }
+    double red[2];
+    CUDA_TRY(cudaMemcpy(red, d_red, sizeof(red), cudaMemcpyDeviceToHost));
+    // x is M-normalised (x.M x = 1) after the first iteration
+    double xmx = 1.0;
+    if (it == 0) {
+      CUDA_TRY(cudaMemsetAsync(d_red, 0, sizeof(double), s));
+      for (int d = 0; d < c->nd; ++d) {
+        const Box& B = c->box[d];
+        CUDA_TRY(launch_mdot((const double*)c->X[d], (const double*)c->X[d], w1[d][0], w1[d][1], w1[d][2], B.L[0],
+                             B.L[1], B.L[2], B.py, B.pz, B.h[0] * B.h[1] * B.h[2] / 8.0, d_red, s));
+      }
+      CUDA_TRY(cudaMemcpy(&xmx, d_red, sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    lam = -red[0] / xmx;
+    if (!(red[1] > 0.0) || !std::isfinite(red[1])) break;
+    const double inv = 1.0 / std::sqrt(red[1]);
+    for (int d = 0; d < c->nd; ++d)
+      CUDA_TRY(launch_scale((double*)c->X[d], (const double*)c->V[d], inv, c->box[d].bstride, s));
+  }
+  CUDA_TRY(cudaDeviceSynchronize());
+  cleanup();
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up during the stability check");
+  if (lambda_max) *lambda_max = lam;
+  if (!(lam > 0.0)) return fail(DGSEM_EUNSTABLE, "lambda_max estimate %g is not positive", lam);
+  c->dt_stable = 2.0 / std::sqrt(lam);
+  if (c->dt > 0.95 * c->dt_stable)
+    return fail(DGSEM_EUNSTABLE, "dt = %.4e s exceeds 0.95 * 2/sqrt(lambda_max) = %.4e s", c->dt, 0.95 * c->dt_stable);
+  return DGSEM_OK;
 }
 
 int dgsem_set_tiles(dgsem_ctx* c, int precision, const int* tiles) {
   if (!c || !tiles) return fail(DGSEM_EINVAL, "NULL argument");
   if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return fail(DGSEM_EINVAL, "bad precision");
   for (int d = 0; d < c->nd; ++d) {
-    unsigned box[3];
-    const int nv = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[d].N, tiles[d], box)
-                                                 : vol_tma_box_f64(c->box[d].N, tiles[d], box);
+    unsigned box[3], vbox[3];
+    const int nv = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[d].N, tiles[d], box, vbox)
+                                                 : vol_tma_box_f64(c->box[d].N, tiles[d], box, vbox);
     if (!nv) return fail(DGSEM_EINVAL, "box %d: no tile variant %d for order %d", d, tiles[d], c->box[d].N);
   }
   for (int d = 0; d < c->nd; ++d) c->tile_pref[precision == DGSEM_FP32_MIXED ? 1 : 0][d] = tiles[d];
@@ -1146,8 +1300,9 @@ int dgsem_set_tiles(dgsem_ctx* c, int precision, const int* tiles) {
 int dgsem_num_tiles(const dgsem_ctx* c, int precision, int box, int* n) {
   if (!c || !n) return fail(DGSEM_EINVAL, "NULL argument");
   if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "bad box %d", box);
-  unsigned b3[3];
-  *n = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[box].N, 0, b3) : vol_tma_box_f64(c->box[box].N, 0, b3);
+  unsigned b3[3], v3[3];
+  *n = precision == DGSEM_FP32_MIXED ? vol_tma_box_f32(c->box[box].N, 0, b3, v3)
+                                     : vol_tma_box_f64(c->box[box].N, 0, b3, v3);
   return DGSEM_OK;
 }
 
@@ -1165,8 +1320,8 @@ int dgsem_autotune(dgsem_ctx* c, int precision, int batch, int reps, int* chosen
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
   for (int d = 0; d < c->nd; ++d) {
-    unsigned b3[3];
-    const int nv = pi ? vol_tma_box_f32(c->box[d].N, 0, b3) : vol_tma_box_f64(c->box[d].N, 0, b3);
+    unsigned b3[3], v3[3];
+    const int nv = pi ? vol_tma_box_f32(c->box[d].N, 0, b3, v3) : vol_tma_box_f64(c->box[d].N, 0, b3, v3);
     int best = 0;
     float best_ms = 1e30f;
     for (int v = 0; v < nv; ++v) {
@@ -1174,6 +1329,7 @@ int dgsem_autotune(dgsem_ctx* c, int precision, int batch, int reps, int* chosen
       if ((rc = refresh_tmaps(c))) break;
       VolSpec sp = c->vspec[d];
       sp.tmap = &c->tmap_y[d];
+      sp.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
       sp.err = c->d_err;
       sp.tile = v;
       sp.p_in = c->Y[d]; sp.p_out = c->X[d]; sp.v = c->V[d];
@@ -1229,6 +1385,8 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_drive); dfree(c->d_traces);
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
   dfree(c->d_err);
+  dfree(c->d_step);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c->basis[0];
   delete c->basis[1];
   delete c;

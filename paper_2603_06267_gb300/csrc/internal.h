@@ -24,7 +24,9 @@
 template <typename T, int N>
 struct VolArgs {
   CUtensorMap tmap;    // 4D (x, y, z, batch) tiled view of p_in for the TMA staging loads
+  CUtensorMap tmap_v;  // same view of v (used when v is staged too)
   int* err;            // device status word: set to 1 if a bounded wait gives up
+  int* step;           // if not NULL, block (0,0,0) advances the run's step counter
   const T* p_in;       // p^{n+1}: stencil source
   T* p_out;            // p^{n+2} = p^{n+1} + dtp * v_new
   T* v;                // v^{n+1/2} -> v^{n+3/2} = v + dtv * a
@@ -110,7 +112,8 @@ struct PmutArgs {
   const double* eta;               // [K][M]
   const double* drive;             // drive[b*dbs + k*dks + n]
   long long dbs, dks;
-  int n;                           // step index inside this run
+  int n;                           // step offset inside this run
+  const int* step;                 // device step counter of the run (added to n)
   double dt;
   // receivers
   int R;
@@ -128,8 +131,10 @@ struct PmutArgs {
 // Runtime description of one volume launch (FP64 tables, runtime order N);
 // the kernel translation unit converts it to VolArgs<T, N>.
 struct VolSpec {
-  const CUtensorMap* tmap;         // tensor map of p_in (see make_tmap_spec)
+  const CUtensorMap* tmap;         // tensor map of p_in
+  const CUtensorMap* tmap_v;       // tensor map of v (NULL when the variant does not stage v)
   int* err;
+  int* step;                       // step counter to advance (last launch of a step), or NULL
   const void* p_in; void* p_out; void* v;
   long long bstride;
   int L[3], ne[3];
@@ -151,11 +156,12 @@ struct VolSpec {
   int tile;                        // tile-shape variant (see vol_impl.cuh)
 };
 
-// Box shape (x, y, z) of the TMA staging load of one element layer for a
-// box of order N and tile variant `tile`; returns the number of tile variants
-// of that order (0 if the order or the variant is unsupported).
-int vol_tma_box_f32(int N, int tile, unsigned box[3]);
-int vol_tma_box_f64(int N, int tile, unsigned box[3]);
+// Box shapes (x, y, z) of the TMA staging loads of one element layer (p)
+// and of its v planes (vbox, all zero when v is not staged) for a box of
+// order N and tile variant `tile`; returns the number of tile variants of
+// that order (0 if the order or the variant is unsupported).
+int vol_tma_box_f32(int N, int tile, unsigned box[3], unsigned vbox[3]);
+int vol_tma_box_f64(int N, int tile, unsigned box[3], unsigned vbox[3]);
 
 // Launchers (defined in the kernel translation units)
 template <typename T>
@@ -164,3 +170,7 @@ template <typename T>
 cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);
+// power-iteration helpers (FP64)
+cudaError_t launch_mdot(const double* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
+                        int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s);
+cudaError_t launch_scale(double* x, const double* y, double a, long long n, cudaStream_t s);

@@ -2,4 +2,6 @@
 #include "vol_impl.cuh"
 
 template cudaError_t launch_vol<float>(const VolSpec&, int, cudaStream_t);
-int vol_tma_box_f32(int N, int tile, unsigned box[3]) { return dgvol::tma_box<float>(N, tile, box); }
+int vol_tma_box_f32(int N, int tile, unsigned box[3], unsigned vbox[3]) {
+  return dgvol::tma_box<float>(N, tile, box, vbox);
+}

@@ -2,4 +2,6 @@
 #include "vol_impl.cuh"
 
 template cudaError_t launch_vol<double>(const VolSpec&, int, cudaStream_t);
-int vol_tma_box_f64(int N, int tile, unsigned box[3]) { return dgvol::tma_box<double>(N, tile, box); }
+int vol_tma_box_f64(int N, int tile, unsigned box[3], unsigned vbox[3]) {
+  return dgvol::tma_box<double>(N, tile, box, vbox);
+}

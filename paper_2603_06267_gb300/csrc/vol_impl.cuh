@@ -8,16 +8,19 @@
 // batch members one after another.
 //
 // Work decomposition: a CTA owns an element-aligned x-y tile of TXE element
-// columns x TYE*N rows and marches over a chunk of element layers in z.  Each
-// thread owns the N nodes of one element along x in one row (the thread of
-// the last element column also owns the box's last x node).  The N+1 planes
-// of an element layer are staged in shared memory by one TMA box load
-// (cp.async.bulk.tensor, zero fill outside the box) with a halo of one
-// element on the low x/y side and one node on the high side -- vertex rows
-// need the neighbouring element, interior rows only their own.  Two stages
-// alternate so that the next layer streams in while the current one is
-// computed.  The coupling of a vertex plane to the layer below is a partial
-// sum carried in registers, so no z halo is loaded.
+// columns x TYE*N rows and marches over a chunk of element layers in z.  A
+// thread owns the N nodes of one element along x in one row; PG thread
+// groups split the planes of each layer between them (plane c goes to group
+// c mod PG), so more warps share one staged tile.  The thread of the last
+// element column also owns the box's last x node (a separate, rarely taken
+// path).  The N+1 planes of an element layer are staged in shared memory by
+// one TMA box load (cp.async.bulk.tensor, zero fill outside the box) with a
+// halo of one element on the low x/y side and one node on the high side --
+// vertex rows need the neighbouring element, interior rows only their own.
+// In FP32 the N planes of v of the layer arrive by a second TMA box into
+// the same stage.  Two stages alternate so that the next layer streams in
+// while the current one is computed.  The coupling of a vertex plane to the
+// layer below is a partial sum carried in registers, so no z halo is loaded.
 #pragma once
 #include <cstdio>
 #include <type_traits>
@@ -105,14 +108,6 @@ __device__ __forceinline__ void vld(const T* __restrict__ p, T* out) {
 }
 
 template <typename T, int V, int CNT>
-__device__ __forceinline__ void vld_global(const T* __restrict__ p, T* out) {
-  static_assert(CNT % V == 0, "run length must be a multiple of the vector width");
-  using VT = typename Vec<T, V>::t;
-#pragma unroll
-  for (int k = 0; k < CNT / V; ++k) unpack(reinterpret_cast<const VT*>(p)[k], out + k * V);
-}
-
-template <typename T, int V, int CNT>
 __device__ __forceinline__ void vst(T* __restrict__ p, const T* in) {
   static_assert(CNT % V == 0, "run length must be a multiple of the vector width");
   using VT = typename Vec<T, V>::t;
@@ -123,51 +118,69 @@ __device__ __forceinline__ void vst(T* __restrict__ p, const T* in) {
 constexpr int pow2_div(int n) { return (n % 4 == 0) ? 4 : ((n % 2 == 0) ? 2 : 1); }
 constexpr int cmin(int a, int b) { return a < b ? a : b; }
 constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
 
 // ---------------------------------------------------------------------------
-// tile geometry
+// tile shapes: element columns TXE x element rows TYE per CTA, PG plane
+// groups.  Orders 4 and 6 (the workloads' primary and secondary boxes) have
+// several shapes the autotuner chooses from; variant 0 is the default.
 // ---------------------------------------------------------------------------
-// Tile shapes (element columns TXE x element rows TYE per CTA).  Orders 4
-// and 6 (the workloads' primary and secondary boxes) have several shapes the
-// autotuner chooses from; variant 0 is the default.
-template <typename T, int N, int V> struct TileShape;
-template <typename T, int N> struct TileShape<T, N, 0> {
-  static constexpr int TXE = (N <= 4) ? 32 : 16;
-  static constexpr int TYE = (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1)));
+template <int A, int B, int C> struct Shape { static constexpr int TXE = A, TYE = B, PG = C; };
+template <typename T, int N, int V> struct TileShape {
+  using S = Shape<(N <= 4) ? 32 : 16,
+                  (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1))), 1>;
 };
 template <typename T, int N> struct NumShapes { static constexpr int value = (N == 4 || N == 6) ? 4 : 1; };
-// FP32 N=4: 512 / 384 / 256 threads; FP64 N=4: 256 / 256 / 128 threads
-template <typename T> struct TileShape<T, 4, 1> { static constexpr int TXE = sizeof(T) == 4 ? 32 : 16, TYE = sizeof(T) == 4 ? 3 : 4; };
-template <typename T> struct TileShape<T, 4, 2> { static constexpr int TXE = 32, TYE = sizeof(T) == 4 ? 2 : 1; };
-template <typename T> struct TileShape<T, 4, 3> { static constexpr int TXE = 16, TYE = sizeof(T) == 4 ? 4 : 2; };
-// FP32 N=6: 192 / 384 / 288 / 192 threads; FP64 N=6: 192 / 96 / 192 / 96 threads
-template <typename T> struct TileShape<T, 6, 1> { static constexpr int TXE = 16, TYE = sizeof(T) == 4 ? 4 : 1; };
-template <typename T> struct TileShape<T, 6, 2> { static constexpr int TXE = sizeof(T) == 4 ? 16 : 8, TYE = sizeof(T) == 4 ? 3 : 4; };
-template <typename T> struct TileShape<T, 6, 3> { static constexpr int TXE = sizeof(T) == 4 ? 32 : 8, TYE = sizeof(T) == 4 ? 1 : 2; };
+// FP32 N=4: 512 threads in each, FP64 N=4: 256 / 256 / 128 / 512
+template <> struct TileShape<float, 4, 0> { using S = Shape<32, 2, 2>; };
+template <> struct TileShape<float, 4, 1> { using S = Shape<32, 4, 1>; };
+template <> struct TileShape<float, 4, 2> { using S = Shape<16, 4, 2>; };
+template <> struct TileShape<float, 4, 3> { using S = Shape<32, 2, 1>; };
+template <> struct TileShape<double, 4, 0> { using S = Shape<32, 2, 1>; };
+template <> struct TileShape<double, 4, 1> { using S = Shape<16, 4, 1>; };
+template <> struct TileShape<double, 4, 2> { using S = Shape<32, 1, 1>; };
+template <> struct TileShape<double, 4, 3> { using S = Shape<32, 2, 2>; };
+// FP32 N=6: 384 / 576 / 192 / 384 threads, FP64 N=6: 192 / 96 / 192 / 384
+template <> struct TileShape<float, 6, 0> { using S = Shape<16, 2, 2>; };
+template <> struct TileShape<float, 6, 1> { using S = Shape<16, 2, 3>; };
+template <> struct TileShape<float, 6, 2> { using S = Shape<16, 2, 1>; };
+template <> struct TileShape<float, 6, 3> { using S = Shape<32, 1, 2>; };
+template <> struct TileShape<double, 6, 0> { using S = Shape<16, 2, 1>; };
+template <> struct TileShape<double, 6, 1> { using S = Shape<16, 1, 1>; };
+template <> struct TileShape<double, 6, 2> { using S = Shape<8, 4, 1>; };
+template <> struct TileShape<double, 6, 3> { using S = Shape<16, 2, 2>; };
 
-template <typename T, int N, int TXE, int TYE>
+template <typename T, int N, int TXE, int TYE, int PG>
 struct Geo {
   static constexpr int AL = 16 / (int)sizeof(T);                // elements per 16 bytes
   static constexpr int NAL = (N + AL - 1) / AL * AL;            // low x halo rounded up to 16 B
   static constexpr int PAD = NAL - N;
   static constexpr int TYR = TYE * N;                           // owned rows
-  static constexpr int BX = (TXE * N + N + 1 + PAD + AL - 1) / AL * AL;   // staged columns
-  static constexpr int BY = TYR + N + 1;                        // staged rows
-  static constexpr int BZ = N + 1;                              // staged planes (one layer)
+  static constexpr int BX = (TXE * N + N + 1 + PAD + AL - 1) / AL * AL;   // staged p columns
+  static constexpr int BY = TYR + N + 1;                        // staged p rows
+  static constexpr int BZ = N + 1;                              // staged p planes (one layer)
   static constexpr int PLANE = BX * BY;
-  static constexpr size_t STAGE_BYTES = sizeof(T) * (size_t)BZ * PLANE;
-  static constexpr size_t STAGE = (STAGE_BYTES + 127) / 128 * 128;
+  static constexpr size_t P_BYTES = sizeof(T) * (size_t)BZ * PLANE;
+  // v of the owned nodes (+ the box's last x column), N planes, staged in FP32
+  static constexpr int BXV = (TXE * N + 1 + AL - 1) / AL * AL;
+  static constexpr int VPLANE = BXV * TYR;
+  static constexpr size_t V_BYTES_RAW = sizeof(T) * (size_t)N * VPLANE;
+  static constexpr bool VTMA = sizeof(T) == 4 && 2 * (r128(P_BYTES) + r128(V_BYTES_RAW)) + 64 <= 227 * 1024;
+  static constexpr size_t V_BYTES = VTMA ? V_BYTES_RAW : 0;
+  static constexpr size_t STAGE = r128(P_BYTES) + r128(V_BYTES);
   static constexpr int STAGES = (2 * STAGE + 64 <= 227 * 1024) ? 2 : 1;
   static constexpr size_t SMEM = STAGES * STAGE + 64;
-  static constexpr int NT = TXE * TYR;
+  static constexpr int NT = TXE * TYR * PG;
   // vector widths: shared-memory runs start at column NAL + tx*N, global runs at ex*N
   static constexpr int VS = cmin(cmin(AL, pow2_div(N)), pow2_div(gcd_c(N, NAL)));
   static constexpr int VG = cmin(AL, pow2_div(N));
-  static_assert(NT % 32 == 0, "CTA must be a whole number of warps");
-  // TMA: the x coordinate x0 - NAL (x0 = tile * TXE * N) must be 16-byte aligned
+  static constexpr int VV = cmin(AL, pow2_div(gcd_c(N, BXV)));   // v runs start at tx*N in a BXV row
+  static_assert(NT % 32 == 0 && NT <= 1024, "CTA must be a whole number of warps, at most 1024 threads");
+  static_assert(PG >= 1 && PG <= N, "plane groups");
+  // TMA: the x coordinates x0 - NAL and x0 (x0 = tile * TXE * N) must be 16-byte aligned
   static_assert((TXE * N * sizeof(T)) % 16 == 0 && (NAL * sizeof(T)) % 16 == 0, "TMA x coordinate misaligned");
-  static_assert((BX * sizeof(T)) % 16 == 0, "TMA box row must be a multiple of 16 bytes");
-  static_assert(BX <= 256 && BY <= 256 && BZ <= 256, "TMA box dimension above 256");
+  static_assert((BX * sizeof(T)) % 16 == 0 && (BXV * sizeof(T)) % 16 == 0, "TMA box row not a multiple of 16 B");
+  static_assert(BX <= 256 && BY <= 256 && BZ <= 256 && BXV <= 256 && TYR <= 256, "TMA box dimension above 256");
   static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
 };
 
@@ -190,8 +203,7 @@ __device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, 
 // Rare per-node terms times M^-1: PMUT forcing f (eq. f_i) on the z-min plane
 // and the interface residual of the interface element layer.
 template <typename T, int N>
-__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, double minv, T ra, T rb,
-                                      bool iface_here) {
+__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, double minv) {
   T acc = T(0);
   if (A.has_pmut && k == 0) {
     double f = 0.0;
@@ -204,46 +216,48 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
     }
     acc += T(-A.kappa * f * minv);
   }
-  if (iface_here) {
+  if (A.iface_k0 >= 0) {
     const int idx = k - A.iface_k0;
     if (idx >= 0 && idx <= N) {
-      T r = A.dI[idx] * rb;
-      if (idx == (A.iface_top ? N : 0)) r += ra;
+      const long long fs = (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
+      T r = A.dI[idx] * face_gather<T, N>(A.Rb + fs, i, j, A.ne0, A.ne1);
+      if (idx == (A.iface_top ? N : 0)) r += face_gather<T, N>(A.Ra + fs, i, j, A.ne0, A.ne1);
       acc -= r * T(minv);
     }
   }
   return acc;
 }
 
-// z stencil of the owned nodes: sum_q coef[q] * (staged plane q, own column)
+// z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column)
 template <typename T, int N, int VS, int PLANE>
 __device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, T* zs) {
 #pragma unroll
-  for (int a = 0; a <= N; ++a) zs[a] = T(0);
+  for (int a = 0; a < N; ++a) zs[a] = T(0);
 #pragma unroll
   for (int q = 0; q <= N; ++q) {
-    T t[N + 1];
+    T t[N];
     vld<T, VS, N>(S0 + q * PLANE + own, t);
-    t[N] = S0[q * PLANE + own + N];
     const T cq = coef[q];
 #pragma unroll
-    for (int a = 0; a <= N; ++a) zs[a] += cq * t[a];
+    for (int a = 0; a < N; ++a) zs[a] += cq * t[a];
   }
 }
 
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE>
-__global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
-  using G = Geo<T, N, TXE, TYE>;
+template <typename T, int N, int TXE, int TYE, int PG>
+__global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
+  using G = Geo<T, N, TXE, TYE, PG>;
   constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
+  constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
   constexpr int STAGES = G::STAGES;
+  constexpr bool VTMA = G::VTMA;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
 
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TXE + tx;
+  const int tx = threadIdx.x, ty = threadIdx.y, pg = threadIdx.z;
+  const int tid = (pg * TYR + ty) * TXE + tx;
   const int ex0 = blockIdx.x * TXE;
   const int x0 = ex0 * N;
   const int y0 = blockIdx.y * TYR;
@@ -255,6 +269,15 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
   const T* __restrict__ pin = A.p_in + boff;
   T* __restrict__ pout = A.p_out + boff;
   T* __restrict__ vv = A.v + boff;
+
+  // the last launch of a step advances the run's step counter (read by the
+  // PMUT/receiver kernel of the next step, which starts after this one ends)
+  if (A.step && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) atomicAdd(A.step, 1);
+  // the TMA destination must be 128-byte aligned
+  if (smem_u32(smem_raw) % 128 != 0) {
+    if (tid == 0) atomicExch(A.err, 2);
+    return;
+  }
 
   const int ex = ex0 + tx;                 // element column
   const int j = y0 + ty;                   // lattice row
@@ -274,58 +297,43 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
 
   const int r0 = ty + N;                   // staged row of lattice row j
   const int cb = NAL + tx * N;             // staged column of node ex*N
-  const int own = r0 * BX + cb;            // staged offset of node ex*N in a plane
+  const int own = r0 * BX + cb;            // staged offset of node ex*N in a p plane
+  const int vown = ty * BXV + tx * N;      // staged offset of node ex*N in a v plane
   const long long grow = (long long)j * A.py + (long long)ex * N;   // node ex*N in a plane
 
-  // interface residual of this column (gathered once)
-  T ra[N + 1], rb[N + 1];
+  // z carry: sum_q lz[q] p[(ez-1)N + q] of each owned node (plane group 0 owns the vertex planes)
+  T carry[N];
+  T carryX = T(0);
 #pragma unroll
-  for (int a = 0; a <= N; ++a) { ra[a] = T(0); rb[a] = T(0); }
-  const bool iface_here = A.iface_k0 >= 0 && A.iface_k0 <= ez1 * N && A.iface_k0 + N >= ez0 * N;
-  if (iface_here && active) {
-    const long long fs = (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
-#pragma unroll
-    for (int a = 0; a <= N; ++a) {
-      if (a < N || xlast) {
-        ra[a] = face_gather<T, N>(A.Ra + fs, ex * N + a, j, A.ne0, A.ne1);
-        rb[a] = face_gather<T, N>(A.Rb + fs, ex * N + a, j, A.ne0, A.ne1);
-      }
-    }
-  }
-
-  // z carry: sum_q lz[q] p[(ez-1)N + q] of each owned node
-  T carry[N + 1];
-#pragma unroll
-  for (int a = 0; a <= N; ++a) carry[a] = T(0);
-  if (ez0 > 0 && active) {
+  for (int a = 0; a < N; ++a) carry[a] = T(0);
+  if (ez0 > 0 && active && pg == 0) {
 #pragma unroll
     for (int q = 0; q <= N; ++q) {
       T t[N];
       const T* src = pin + (long long)((ez0 - 1) * N + q) * A.pz + grow;
-      vld_global<T, VG, N>(src, t);
+      vld<T, VG, N>(src, t);
 #pragma unroll
       for (int a = 0; a < N; ++a) carry[a] += A.lz[q] * t[a];
-      if (xlast) carry[N] += A.lz[q] * src[N];
+      if (xlast) carryX += A.lz[q] * src[N];
     }
   }
 
-  // the TMA destination must be 128-byte aligned
-  if (smem_u32(smem_raw) % 128 != 0) {
-    if (tid == 0) atomicExch(A.err, 2);
-    return;
-  }
   // pipeline set-up
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap)) : "memory");
+    if constexpr (VTMA) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap_v)) : "memory");
   }
   __syncthreads();
+  auto issue = [&](int ez, int s) {
+    unsigned char* st = smem_raw + s * G::STAGE;
+    mbar_expect_tx(&bar[s], (uint32_t)(G::P_BYTES + G::V_BYTES));
+    tma_load_4d(st, &A.tmap, &bar[s], x0 - NAL, y0 - N, ez * N, b);
+    if constexpr (VTMA) tma_load_4d(st + r128(G::P_BYTES), &A.tmap_v, &bar[s], x0, y0, ez * N, b);
+  };
   if (tid == 0) {
-    for (int s = 0; s < STAGES && ez0 + s < ez1; ++s) {
-      mbar_expect_tx(&bar[s], (uint32_t)G::STAGE_BYTES);
-      tma_load_4d(smem_raw + s * G::STAGE, &A.tmap, &bar[s], x0 - NAL, y0 - N, (ez0 + s) * N, b);
-    }
+    for (int s = 0; s < STAGES && ez0 + s < ez1; ++s) issue(ez0 + s, s);
   }
 
   int it = 0;
@@ -333,17 +341,9 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
     const int s = it % STAGES;
     const uint32_t parity = (uint32_t)((it / STAGES) & 1);
     const T* S0 = reinterpret_cast<const T*>(smem_raw + s * G::STAGE);
+    const T* V0 = reinterpret_cast<const T*>(smem_raw + s * G::STAGE + r128(G::P_BYTES));
     const bool last_layer = (ez == A.ne2 - 1);
     const int nplanes = last_layer ? N + 1 : N;
-    // v of the first plane of the layer, loaded before the wait for the staged p
-    T vcur[N + 1];
-#pragma unroll
-    for (int a = 0; a <= N; ++a) vcur[a] = T(0);
-    if (active) {
-      const T* src = vv + (long long)(ez * N) * A.pz + grow;
-      vld_global<T, VG, N>(src, vcur);
-      if (xlast) vcur[N] = src[N];
-    }
     if (!mbar_wait_bounded(&bar[s], parity)) {
       if (tid == 0) atomicExch(A.err, 1);
       // give the copies in flight a bounded chance to land before leaving
@@ -352,28 +352,26 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
     }
     if (active) {
       const bool extras_layer = (A.has_pmut && ez == 0) ||
-                                (iface_here && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
-      // one plane of the layer; ZM selects the z rows: 0 vertex plane (carried
-      // lower part + own layer), 1 interior plane c, 2 top boundary plane
+                                (A.iface_k0 >= 0 && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
+      // one plane of the layer for the N owned nodes; ZM selects the z rows:
+      // 0 vertex plane (carried lower part + own layer), 1 interior plane c,
+      // 2 top boundary plane of the box
       auto plane = [&](auto zm, int c) {
         constexpr int ZM = decltype(zm)::value;
         const T* P = S0 + c * PLANE;
         const int k = ez * N + c;
-        // v of the next plane, one plane ahead
-        T vnext[N + 1];
-#pragma unroll
-        for (int a = 0; a <= N; ++a) vnext[a] = T(0);
-        if (c + 1 < nplanes) {
-          const T* src = vv + (long long)(k + 1) * A.pz + grow;
-          vld_global<T, VG, N>(src, vnext);
-          if (xlast) vnext[N] = src[N];
+        T vcur[N];
+        if constexpr (VTMA && ZM != 2) {
+          vld<T, VV, N>(V0 + c * VPLANE + vown, vcur);
+        } else {
+          vld<T, VG, N>(vv + (long long)k * A.pz + grow, vcur);
         }
-        // staged row of lattice row j: columns cb-N .. cb+N
+        // staged row of lattice row j: columns cb-N .. cb+N-1
         T xr[2 * N + 1];
         vld<T, VS, N>(P + own - N, xr);
         vld<T, VS, N>(P + own, xr + N);
         xr[2 * N] = P[own + N];
-        T acc[N + 1];
+        T acc[N];
         // x stencil
         {
           T l = T(0), r = T(0);
@@ -392,57 +390,48 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
           for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * xr[N + q];
           acc[a] = s2;
         }
-        {
-          T l = T(0);
-#pragma unroll
-          for (int q = 0; q <= N; ++q) l += A.lx[q] * xr[N + q];
-          acc[N] = l * A.iwb;                 // last x node of the box (kept only if xlast)
-        }
         // y stencil
         if (yvert) {
-          T ylv[N + 1], yrv[N + 1];
+          T ylv[N], yrv[N];
 #pragma unroll
-          for (int a = 0; a <= N; ++a) { ylv[a] = T(0); yrv[a] = T(0); }
+          for (int a = 0; a < N; ++a) { ylv[a] = T(0); yrv[a] = T(0); }
           if (yl) {
 #pragma unroll
             for (int q = 0; q <= N; ++q) {
-              T t[N + 1];
+              T t[N];
               vld<T, VS, N>(P + own + (q - N) * BX, t);
-              t[N] = P[own + (q - N) * BX + N];
 #pragma unroll
-              for (int a = 0; a <= N; ++a) ylv[a] += A.ly[q] * t[a];
+              for (int a = 0; a < N; ++a) ylv[a] += A.ly[q] * t[a];
             }
           }
           if (yr) {
 #pragma unroll
             for (int q = 0; q <= N; ++q) {
-              T t[N + 1];
+              T t[N];
               vld<T, VS, N>(P + own + q * BX, t);
-              t[N] = P[own + q * BX + N];
 #pragma unroll
-              for (int a = 0; a <= N; ++a) yrv[a] += A.ry[q] * t[a];
+              for (int a = 0; a < N; ++a) yrv[a] += A.ry[q] * t[a];
             }
           }
 #pragma unroll
-          for (int a = 0; a <= N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
+          for (int a = 0; a < N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
         } else {
 #pragma unroll
           for (int q = 0; q <= N; ++q) {
-            T t[N + 1];
+            T t[N];
             vld<T, VS, N>(P + own + (q - yb) * BX, t);
-            t[N] = P[own + (q - yb) * BX + N];
 #pragma unroll
-            for (int a = 0; a <= N; ++a) acc[a] += cyi[q] * t[a];
+            for (int a = 0; a < N; ++a) acc[a] += cyi[q] * t[a];
           }
         }
         // z stencil: own column over the staged planes of the layer
-        T zs[N + 1];
+        T zs[N];
         T iw_z;
         if constexpr (ZM == 0) {
           zsum<T, N, VS, PLANE>(S0, own, A.rz, zs);
           iw_z = (ez > 0) ? A.iwv : A.iwb;
 #pragma unroll
-          for (int a = 0; a <= N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
+          for (int a = 0; a < N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
         } else if constexpr (ZM == 1) {
           zsum<T, N, VS, PLANE>(S0, own, A.cz[c], zs);
           iw_z = A.iwa[c];
@@ -450,44 +439,99 @@ __global__ void __launch_bounds__(TXE * TYE * N, 1) vol_kernel(const __grid_cons
           zsum<T, N, VS, PLANE>(S0, own, A.lz, zs);
           iw_z = A.iwb;
 #pragma unroll
-          for (int a = 0; a <= N; ++a) zs[a] *= iw_z;
+          for (int a = 0; a < N; ++a) zs[a] *= iw_z;
         }
         // update: a = -(M^-1 K p) (+ extras), v += dtv a, p_out = p + dtp v
-        T vn[N + 1], pn[N + 1];
+        T vn[N], pn[N];
 #pragma unroll
-        for (int a = 0; a <= N; ++a) {
+        for (int a = 0; a < N; ++a) {
           T accum = -(acc[a] + zs[a]);
-          if (extras_layer && (a < N || xlast)) {
-            const T iw_x = (a == 0) ? xiw : (a < N ? A.iwa[a] : A.iwb);
+          if (extras_layer) {
+            const T iw_x = (a == 0) ? xiw : A.iwa[a];
             const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
-            accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv, ra[a], rb[a], iface_here);
+            accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
           }
           vn[a] = vcur[a] + A.dtv * accum;
           pn[a] = xr[N + a] + A.dtp * vn[a];
         }
-        T* vdst = vv + (long long)k * A.pz + grow;
-        T* pdst = pout + (long long)k * A.pz + grow;
-        vst<T, VG, N>(vdst, vn);
-        vst<T, VG, N>(pdst, pn);
-        if (xlast) {
-          vdst[N] = vn[N];
-          pdst[N] = pn[N];
-        }
-#pragma unroll
-        for (int a = 0; a <= N; ++a) vcur[a] = vnext[a];
+        vst<T, VG, N>(vv + (long long)k * A.pz + grow, vn);
+        vst<T, VG, N>(pout + (long long)k * A.pz + grow, pn);
       };
-      plane(std::integral_constant<int, 0>(), 0);
-#pragma unroll 1
-      for (int c = 1; c < N; ++c) plane(std::integral_constant<int, 1>(), c);
-      if (last_layer) plane(std::integral_constant<int, 2>(), N);
+      // the box's last x node (column cb+N), owned by the last element column
+      auto plane_last_x = [&](int c) {
+        const T* P = S0 + c * PLANE;
+        const int k = ez * N + c;
+        const int col = own + N;
+        T x = T(0);
+#pragma unroll
+        for (int q = 0; q <= N; ++q) x += A.lx[q] * P[own + q];
+        x *= A.iwb;
+        T y;
+        if (yvert) {
+          T l = T(0), r = T(0);
+          if (yl) {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) l += A.ly[q] * P[col + (q - N) * BX];
+          }
+          if (yr) {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) r += A.ry[q] * P[col + q * BX];
+          }
+          y = (l + r) * yiw;
+        } else {
+          y = T(0);
+#pragma unroll
+          for (int q = 0; q <= N; ++q) y += cyi[q] * P[col + (q - yb) * BX];
+        }
+        T z = T(0), iw_z;
+        if (c == 0) {
+#pragma unroll
+          for (int q = 0; q <= N; ++q) z += A.rz[q] * S0[q * PLANE + col];
+          iw_z = (ez > 0) ? A.iwv : A.iwb;
+          z = (carryX + z) * iw_z;
+        } else if (c < N) {
+#pragma unroll
+          for (int q = 0; q <= N; ++q) z += A.cz[c][q] * S0[q * PLANE + col];
+          iw_z = A.iwa[c];
+        } else {
+#pragma unroll
+          for (int q = 0; q <= N; ++q) z += A.lz[q] * S0[q * PLANE + col];
+          iw_z = A.iwb;
+          z *= iw_z;
+        }
+        T accum = -(x + y + z);
+        if (extras_layer) {
+          const double minv = A.minv_scale * (double)A.iwb * (double)iw_y * (double)iw_z;
+          accum += node_extras<T, N>(A, ex * N + N, j, k, b, minv);
+        }
+        T* vp = vv + (long long)k * A.pz + grow + N;
+        T vo;
+        if constexpr (VTMA) vo = (c < N) ? V0[c * VPLANE + vown + N] : *vp;
+        else vo = *vp;
+        const T vn = vo + A.dtv * accum;
+        *vp = vn;
+        pout[(long long)k * A.pz + grow + N] = P[col] + A.dtp * vn;
+      };
+      for (int c = pg; c < nplanes; c += PG) {
+        if (c == 0) plane(std::integral_constant<int, 0>(), 0);
+        else if (c < N) plane(std::integral_constant<int, 1>(), c);
+        else plane(std::integral_constant<int, 2>(), N);
+        if (xlast) plane_last_x(c);
+      }
       // carry for the vertex plane (ez+1)*N
-      zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
+      if (pg == 0) {
+        zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
+        if (xlast) {
+          carryX = T(0);
+#pragma unroll
+          for (int q = 0; q <= N; ++q) carryX += A.lz[q] * S0[q * PLANE + own + N];
+        }
+      }
     }
     __syncthreads();   // every thread is done with stage s
     if (tid == 0 && ez + STAGES < ez1) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bar[s], (uint32_t)G::STAGE_BYTES);
-      tma_load_4d(smem_raw + s * G::STAGE, &A.tmap, &bar[s], x0 - NAL, y0 - N, (ez + STAGES) * N, b);
+      issue(ez + STAGES, s);
     }
   }
 }
@@ -496,7 +540,9 @@ template <typename T, int N>
 VolArgs<T, N> make_args(const VolSpec& s) {
   VolArgs<T, N> a;
   a.tmap = *s.tmap;
+  if (s.tmap_v) a.tmap_v = *s.tmap_v;
   a.err = s.err;
+  a.step = s.step;
   a.p_in = static_cast<const T*>(s.p_in);
   a.p_out = static_cast<T*>(s.p_out);
   a.v = static_cast<T*>(s.v);
@@ -527,10 +573,13 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   return a;
 }
 
-template <typename T, int N, int TXE, int TYE>
-cudaError_t launch_tile(const VolSpec& s, int batch, cudaStream_t st) {
-  using G = Geo<T, N, TXE, TYE>;
+template <typename T, int N, int V>
+cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
+  using SH = typename TileShape<T, N, V>::S;
+  constexpr int TXE = SH::TXE, TYE = SH::TYE, PG = SH::PG;
+  using G = Geo<T, N, TXE, TYE, PG>;
   if (!s.tmap || !s.err) return cudaErrorInvalidValue;
+  if (G::VTMA && !s.tmap_v) return cudaErrorInvalidValue;
   VolArgs<T, N> a = make_args<T, N>(s);
   int layers = s.layers_per_cta;
   const int gx = (s.ne[0] + TXE - 1) / TXE;
@@ -543,18 +592,13 @@ cudaError_t launch_tile(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
-  dim3 block(TXE, G::TYR, 1);
+  dim3 block(TXE, G::TYR, PG);
   kern<<<grid, block, G::SMEM, st>>>(a);
   return cudaGetLastError();
-}
-
-template <typename T, int N, int V>
-cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
-  return launch_tile<T, N, TileShape<T, N, V>::TXE, TileShape<T, N, V>::TYE>(s, batch, st);
 }
 
 template <typename T, int N>
@@ -574,43 +618,48 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
 }
 
 template <typename T, int N, int V>
-void box_v(unsigned box[3]) {
-  using G = Geo<T, N, TileShape<T, N, V>::TXE, TileShape<T, N, V>::TYE>;
+void box_v(unsigned box[3], unsigned vbox[3]) {
+  using SH = typename TileShape<T, N, V>::S;
+  using G = Geo<T, N, SH::TXE, SH::TYE, SH::PG>;
   box[0] = G::BX;
   box[1] = G::BY;
   box[2] = G::BZ;
+  vbox[0] = G::VTMA ? G::BXV : 0;
+  vbox[1] = G::VTMA ? G::TYR : 0;
+  vbox[2] = G::VTMA ? N : 0;
 }
 
 template <typename T, int N>
-int box_n(int tile, unsigned box[3]) {
+int box_n(int tile, unsigned box[3], unsigned vbox[3]) {
   box[0] = box[1] = box[2] = 0;
+  vbox[0] = vbox[1] = vbox[2] = 0;
   if (tile < 0 || tile >= NumShapes<T, N>::value) return 0;
   if constexpr (NumShapes<T, N>::value > 1) {
     switch (tile) {
-      case 0: box_v<T, N, 0>(box); break;
-      case 1: box_v<T, N, 1>(box); break;
-      case 2: box_v<T, N, 2>(box); break;
-      default: box_v<T, N, 3>(box); break;
+      case 0: box_v<T, N, 0>(box, vbox); break;
+      case 1: box_v<T, N, 1>(box, vbox); break;
+      case 2: box_v<T, N, 2>(box, vbox); break;
+      default: box_v<T, N, 3>(box, vbox); break;
     }
   } else {
-    box_v<T, N, 0>(box);
+    box_v<T, N, 0>(box, vbox);
   }
   return NumShapes<T, N>::value;
 }
 
 // Host entry points of one precision (instantiated in vol_f32.cu / vol_f64.cu)
 template <typename T>
-int tma_box(int N, int tile, unsigned box[3]) {
+int tma_box(int N, int tile, unsigned box[3], unsigned vbox[3]) {
   switch (N) {
-    case 1: return box_n<T, 1>(tile, box);
-    case 2: return box_n<T, 2>(tile, box);
-    case 3: return box_n<T, 3>(tile, box);
-    case 4: return box_n<T, 4>(tile, box);
-    case 5: return box_n<T, 5>(tile, box);
-    case 6: return box_n<T, 6>(tile, box);
-    case 7: return box_n<T, 7>(tile, box);
-    case 8: return box_n<T, 8>(tile, box);
-    default: box[0] = box[1] = box[2] = 0; return 0;
+    case 1: return box_n<T, 1>(tile, box, vbox);
+    case 2: return box_n<T, 2>(tile, box, vbox);
+    case 3: return box_n<T, 3>(tile, box, vbox);
+    case 4: return box_n<T, 4>(tile, box, vbox);
+    case 5: return box_n<T, 5>(tile, box, vbox);
+    case 6: return box_n<T, 6>(tile, box, vbox);
+    case 7: return box_n<T, 7>(tile, box, vbox);
+    case 8: return box_n<T, 8>(tile, box, vbox);
+    default: box[0] = box[1] = box[2] = 0; vbox[0] = vbox[1] = vbox[2] = 0; return 0;
   }
 }
 

@@ -242,3 +242,25 @@ def test_autotune_then_run_matches_oracle():
         tg = sol.run(drive=drive, precision=prec)
         assert rel_l2(tg, to) < tol
     sol.close()
+
+
+def test_stability_check_matches_oracle_eigenvalue():
+    """dgsem_check_stability's power iteration (M-weighted Rayleigh quotient)
+    approaches the largest eigenvalue of M^-1 K from below; a time step above
+    the bound is reported as DGSEM_EUNSTABLE (no GPU fault involved)."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2)
+    P = oracle_problem(w)
+    D = np.diag(1 / np.sqrt(P.M))
+    lmax = np.linalg.eigvalsh(D @ P.K.toarray() @ D)[-1]
+    sol = gpu_solver(w)
+    code, lam = dgsem.dgsem_check_stability(sol.ctx, 400)
+    assert code == dgsem.DGSEM_OK
+    assert lam <= lmax * (1 + 1e-9) and lam >= 0.97 * lmax, (lam, lmax)
+    _, dts, _ = dgsem.dgsem_get_dt(sol.ctx)
+    assert abs(dts - 2 / np.sqrt(lam)) < 1e-12 * dts
+    sol.close()
+    big = gpu_solver(w, dt=3.0 * 2 / np.sqrt(lmax))
+    code, _ = dgsem.dgsem_check_stability(big.ctx, 200)
+    assert code == dgsem.DGSEM_EUNSTABLE
+    big.close()
