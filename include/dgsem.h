@@ -212,6 +212,30 @@ int dgsem_autotune(dgsem_ctx* ctx, int precision, int batch, int reps, int* chos
 int dgsem_profile(dgsem_ctx* ctx, int enable);
 int dgsem_kernel_stats(const dgsem_ctx* ctx, int kind, double* total_ms, long long* launches);
 
+/* Receiver sampling that allocates no device memory (the paper has no
+ * counterpart; this is a service of this library).
+ *
+ * Samples the current pressure field p^n of every batch member (the state
+ * left by the last dgsem_run) at n_recv points, with the same element choice
+ * and tensor Lagrange interpolation as dgsem_run's traces.
+ *   recv_xyz  [n_recv][3] positions, host or device memory.
+ *   out       [batch][n_recv] FP64, device memory (written on `stream`).
+ * Why: some callers cannot call cudaMalloc at the moment they want a sample
+ * -- code running while a CUDA stream capture is open (an allocation would
+ * break the capture), processes whose device memory is handed out entirely
+ * by another allocator, or real-time loops that cannot afford the device
+ * synchronisation an allocation implies.  This call allocates nothing: the
+ * receiver table lives in a fixed array of about 0.75 MiB that every device
+ * loading the library holds until the process exits.
+ * Limits: at most 64 receivers per call (larger n_recv returns
+ * DGSEM_EINVAL with a message); needs a previous dgsem_run (DGSEM_ESTATE
+ * otherwise).  The first call on a device looks up the array's device
+ * address; make that first call before any stream capture begins.  All calls
+ * share the one array and it keeps the last call's contents, so calls whose
+ * work overlaps on the GPU (other host threads, other streams) race: issue
+ * them one at a time.  Returns after `stream` has finished the work. */
+int dgsem_sample_noalloc(dgsem_ctx* ctx, int n_recv, const double* recv_xyz, double* out, void* stream);
+
 /* Message of the calling thread's last error ("" if none). */
 const char* dgsem_last_error(void);
 

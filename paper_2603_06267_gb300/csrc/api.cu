@@ -1393,3 +1393,188 @@ void dgsem_destroy(dgsem_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Receiver sampling without device allocation.
+//
+// dgsem_sample_noalloc keeps its receiver table (containing element, tensor
+// Lagrange weights and node offsets of up to NA_MAX_RECV points) in the
+// file-scope device array below instead of buffers from cudaMalloc, then runs
+// the receiver-sampling kernel of the time loop on it.  The array lives for
+// the lifetime of the library on every device that loads it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int NA_MAX_RECV = 64;                                   // receivers per call
+constexpr int NA_MAX_NODES = (DG_MAXN + 1) * (DG_MAXN + 1) * (DG_MAXN + 1);
+constexpr size_t NA_OFF_STATUS = 0;                               // int status word
+constexpr size_t NA_OFF_XYZ = 256;                                // [R][3] double
+constexpr size_t NA_OFF_W = NA_OFF_XYZ + (((size_t)NA_MAX_RECV * 3 * sizeof(double) + 255) / 256) * 256;
+constexpr size_t NA_OFF_OFF = NA_OFF_W + (size_t)NA_MAX_RECV * NA_MAX_NODES * sizeof(double);
+constexpr size_t NA_OFF_DOM = NA_OFF_OFF + (size_t)NA_MAX_RECV * NA_MAX_NODES * sizeof(long long);
+constexpr size_t NA_OFF_NN = NA_OFF_DOM + (size_t)NA_MAX_RECV * sizeof(int);
+constexpr size_t NA_BYTES = NA_OFF_NN + (size_t)NA_MAX_RECV * sizeof(int);   // about 0.75 MiB
+
+static __device__ __align__(256) unsigned char g_sample_scratch[NA_BYTES];
+
+// device address of g_sample_scratch, looked up once per device
+constexpr int NA_MAX_DEVICES = 64;
+unsigned char* g_sample_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+
+struct NaBox {
+  double o[3], h[3], ext[3];
+  int ne[3], N;
+  int py;
+  long long pz;
+  double x[DG_MAXN + 1], bw[DG_MAXN + 1];   // GLL nodes and barycentric weights
+};
+struct NaArgs {
+  int R, nd;
+  NaBox box[2];
+  unsigned char* scratch;
+};
+
+__device__ void na_lagrange(const NaBox& B, double t, double* out) {
+  const int N = B.N;
+  for (int j = 0; j <= N; ++j)
+    if (t == B.x[j]) {
+      for (int k = 0; k <= N; ++k) out[k] = (k == j) ? 1.0 : 0.0;
+      return;
+    }
+  double den = 0.0;
+  for (int j = 0; j <= N; ++j) den += B.bw[j] / (t - B.x[j]);
+  for (int j = 0; j <= N; ++j) out[j] = (B.bw[j] / (t - B.x[j])) / den;
+}
+
+// One thread per receiver: containing element (primary box first, lowest
+// element id on ties) and its tensor Lagrange weights, written to the table.
+__global__ void na_receiver_table(const __grid_constant__ NaArgs A) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= A.R) return;
+  const double* xyz = reinterpret_cast<const double*>(A.scratch + NA_OFF_XYZ) + 3 * r;
+  double* w = reinterpret_cast<double*>(A.scratch + NA_OFF_W) + (size_t)r * NA_MAX_NODES;
+  long long* off = reinterpret_cast<long long*>(A.scratch + NA_OFF_OFF) + (size_t)r * NA_MAX_NODES;
+  int* dom = reinterpret_cast<int*>(A.scratch + NA_OFF_DOM);
+  int* nn = reinterpret_cast<int*>(A.scratch + NA_OFF_NN);
+  int found = -1;
+  for (int d = 0; d < A.nd && found < 0; ++d) {
+    bool inside = true;
+    for (int k = 0; k < 3; ++k) {
+      const double t = 1e-12 * A.box[d].ext[k];
+      if (xyz[k] < A.box[d].o[k] - t || xyz[k] > A.box[d].o[k] + A.box[d].ext[k] + t) inside = false;
+    }
+    if (inside) found = d;
+  }
+  if (found < 0) {
+    atomicExch(reinterpret_cast<int*>(A.scratch + NA_OFF_STATUS), r + 1);
+    nn[r] = 0;
+    dom[r] = 0;
+    return;
+  }
+  const NaBox& B = A.box[found];
+  int e[3];
+  double ref[3];
+  for (int k = 0; k < 3; ++k) {
+    const double u = (xyz[k] - B.o[k]) / B.h[k];
+    int ek = (int)ceil(u - 1e-12) - 1;
+    ek = max(0, min(ek, B.ne[k] - 1));
+    e[k] = ek;
+    ref[k] = fmax(-1.0, fmin(1.0, 2.0 * (u - ek) - 1.0));
+  }
+  double lx[DG_MAXN + 1], ly[DG_MAXN + 1], lz[DG_MAXN + 1];
+  na_lagrange(B, ref[0], lx);
+  na_lagrange(B, ref[1], ly);
+  na_lagrange(B, ref[2], lz);
+  const int n1 = B.N + 1;
+  int t = 0;
+  for (int cc = 0; cc < n1; ++cc)
+    for (int bb = 0; bb < n1; ++bb)
+      for (int aa = 0; aa < n1; ++aa, ++t) {
+        w[t] = lx[aa] * ly[bb] * lz[cc];
+        off[t] = (long long)(e[2] * B.N + cc) * B.pz + (long long)(e[1] * B.N + bb) * B.py + (e[0] * B.N + aa);
+      }
+  dom[r] = found;
+  nn[r] = t;
+}
+
+}  // namespace
+
+extern "C" int dgsem_sample_noalloc(dgsem_ctx* c, int n_recv, const double* recv_xyz, double* out, void* stream) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (n_recv < 0 || n_recv > NA_MAX_RECV)
+    return fail(DGSEM_EINVAL, "dgsem_sample_noalloc: n_recv = %d outside [0, %d] (its receiver table holds at most %d points)",
+                n_recv, NA_MAX_RECV, NA_MAX_RECV);
+  if (n_recv == 0) return DGSEM_OK;
+  if (!recv_xyz || !out) return fail(DGSEM_EINVAL, "recv_xyz and out are required");
+  if (!c->state_valid || !c->X[0]) return fail(DGSEM_ESTATE, "no pressure state: call dgsem_run first");
+  if (!is_device_ptr(out)) return fail(DGSEM_EINVAL, "out must be device memory ([batch][n_recv] doubles)");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != c->device) return fail(DGSEM_EINVAL, "context belongs to device %d, current is %d", c->device, dev);
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(DGSEM_EINVAL, "device %d beyond the supported %d", dev, NA_MAX_DEVICES);
+  // set-up, once per device: the device address of the scratch array (the
+  // host-side symbol is only a stand-in and must never reach a kernel)
+  if (!g_sample_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_sample_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(DGSEM_ECUDA, "cudaGetSymbolAddress(g_sample_scratch): %s", cudaGetErrorString(e));
+    g_sample_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  unsigned char* scratch = g_sample_scratch_addr[dev];
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the status word must start at zero; the table entries are overwritten
+  CUDA_TRY(cudaMemsetAsync(scratch + NA_OFF_STATUS, 0, sizeof(int), s));
+  CUDA_TRY(cudaMemcpyAsync(scratch + NA_OFF_XYZ, recv_xyz, (size_t)n_recv * 3 * sizeof(double), cudaMemcpyDefault, s));
+  NaArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.R = n_recv;
+  a.nd = c->nd;
+  a.scratch = scratch;
+  for (int d = 0; d < c->nd; ++d) {
+    const Box& B = c->box[d];
+    for (int k = 0; k < 3; ++k) {
+      a.box[d].o[k] = B.o[k]; a.box[d].h[k] = B.h[k]; a.box[d].ext[k] = B.ext[k]; a.box[d].ne[k] = B.ne[k];
+    }
+    a.box[d].N = B.N;
+    a.box[d].py = B.py;
+    a.box[d].pz = B.pz;
+    for (int i = 0; i <= B.N; ++i) { a.box[d].x[i] = B.basis->x[i]; a.box[d].bw[i] = B.basis->bw[i]; }
+  }
+  na_receiver_table<<<(n_recv + 63) / 64, 64, 0, s>>>(a);
+  CUDA_TRY(cudaGetLastError());
+  int status = 0;
+  CUDA_TRY(cudaMemcpyAsync(&status, scratch + NA_OFF_STATUS, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (status) return fail(DGSEM_EINVAL, "receiver %d is outside the mesh", status - 1);
+  // the receiver-sampling kernel of the time loop, reading the table from the scratch array
+  cudaError_t e;
+  if (c->prec == DGSEM_FP32_MIXED) {
+    PmutArgs<float> p;
+    std::memset(&p, 0, sizeof(p));
+    p.B = c->batch; p.K = 0; p.R = n_recv; p.rstride = NA_MAX_NODES;
+    p.rw = reinterpret_cast<const double*>(scratch + NA_OFF_W);
+    p.roff = reinterpret_cast<const long long*>(scratch + NA_OFF_OFF);
+    p.rdom = reinterpret_cast<const int*>(scratch + NA_OFF_DOM);
+    p.rnn = reinterpret_cast<const int*>(scratch + NA_OFF_NN);
+    p.pc0 = static_cast<const float*>(c->X[0]); p.pc1 = c->nd > 1 ? static_cast<const float*>(c->X[1]) : nullptr;
+    p.bs0 = c->box[0].bstride; p.bs1 = c->nd > 1 ? c->box[1].bstride : 0;
+    p.traces = out; p.tbs = n_recv; p.trs = 1; p.n = 0; p.step = nullptr;
+    e = launch_pmut_recv<float>(p, s);
+  } else {
+    PmutArgs<double> p;
+    std::memset(&p, 0, sizeof(p));
+    p.B = c->batch; p.K = 0; p.R = n_recv; p.rstride = NA_MAX_NODES;
+    p.rw = reinterpret_cast<const double*>(scratch + NA_OFF_W);
+    p.roff = reinterpret_cast<const long long*>(scratch + NA_OFF_OFF);
+    p.rdom = reinterpret_cast<const int*>(scratch + NA_OFF_DOM);
+    p.rnn = reinterpret_cast<const int*>(scratch + NA_OFF_NN);
+    p.pc0 = static_cast<const double*>(c->X[0]); p.pc1 = c->nd > 1 ? static_cast<const double*>(c->X[1]) : nullptr;
+    p.bs0 = c->box[0].bstride; p.bs1 = c->nd > 1 ? c->box[1].bstride : 0;
+    p.traces = out; p.tbs = n_recv; p.trs = 1; p.n = 0; p.step = nullptr;
+    e = launch_pmut_recv<double>(p, s);
+  }
+  if (e != cudaSuccess) return fail(DGSEM_ECUDA, "receiver sampling launch: %s", cudaGetErrorString(e));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return DGSEM_OK;
+}

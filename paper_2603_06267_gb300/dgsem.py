@@ -33,7 +33,7 @@ EXPORTED = [
     "dgsem_mesh_create", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "dgsem_run", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
-    "dgsem_profile", "dgsem_kernel_stats", "dgsem_last_error", "dgsem_destroy",
+    "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
 ]
 DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1 = 0, 1, 2, 3
 
@@ -83,6 +83,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_num_tiles.argtypes = [vp, c_int, c_int, POINTER(c_int)]
     lib.dgsem_set_tiles.argtypes = [vp, c_int, vp]
     lib.dgsem_autotune.argtypes = [vp, c_int, c_int, c_int, vp, vp]
+    lib.dgsem_sample_noalloc.argtypes = [vp, c_int, vp, vp, vp]
     lib.dgsem_profile.argtypes = [vp, c_int]
     lib.dgsem_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_last_error.restype = ctypes.c_char_p
@@ -261,6 +262,17 @@ def dgsem_autotune(ctx, precision: int, batch: int, ndomains: int, reps: int = 3
     if stream is None:
         stream = _current_stream()
     _check(_lib.dgsem_autotune(ctx, precision, batch, reps, _ptr(out), stream), "dgsem_autotune")
+    return out
+
+
+def dgsem_sample_noalloc(ctx, recv_xyz, out, stream=None):
+    """Sample the current pressure field at recv_xyz ([R][3], R <= 64) into the
+    device tensor `out` ([batch][R] float64) without any device allocation
+    (for callers inside a stream capture or with a fixed memory budget)."""
+    recv = np.ascontiguousarray(recv_xyz, dtype=np.float64).reshape(-1, 3)
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_sample_noalloc(ctx, recv.shape[0], _ptr(recv), _ptr(out), stream), "dgsem_sample_noalloc")
     return out
 
 
