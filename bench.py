@@ -36,7 +36,12 @@ import workloads as W  # noqa: E402
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (workload, precision, kernel kind); see profiles/.  None: not measured for
 # the current kernel.
-NCU_TRAFFIC_PER_LAUNCH = {}
+NCU_TRAFFIC_PER_LAUNCH = {
+    # profiles/vol_kernel_f32_N6_config3.md: 1.350 GB per launch at batch 1 on the
+    # config-3 mesh; traffic scales with the number of patterns (independent state)
+    ("config4_batched", "fp32", "vol_secondary"): 1.3497e9 * 64,
+    ("config3_array32", "fp32", "vol_secondary"): 1.3497e9,
+}
 
 
 def parse():
@@ -51,6 +56,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tiles", default=None,
+                    help="comma-separated volume-kernel tile variant per box (skips the autotuner)")
     return ap.parse_args()
 
 
@@ -226,7 +233,11 @@ def main():
     sol = dgsem.Solver(w)
     ndof = sol.ndof
     # untimed setup: pick the volume-kernel tile shape per box for this batch
-    tiles = dgsem.dgsem_autotune(sol.ctx, prec, B, len(w.domains), reps=2)
+    if args.tiles:
+        tiles = [int(t) for t in args.tiles.split(",")]
+        dgsem.dgsem_set_tiles(sol.ctx, prec, tiles)
+    else:
+        tiles = dgsem.dgsem_autotune(sol.ctx, prec, B, len(w.domains), reps=2)
     K_p = w.pmuts.n_pmut if w.pmuts is not None else 0
     R = w.receivers.shape[0]
     S_tot = args.warmup + args.steps
@@ -305,7 +316,7 @@ def main():
         if prec == dgsem.DGSEM_FP32_MIXED:
             peak = peaks["hbm_gbs"] if peaks else 6800.0
             roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])),
+                    "traffic": (NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])) if B in (1, 64) else None),
                     "kernel": names[kdom], "peak_source": "measured" if peaks else "fallback",
                     "alg_bytes_per_launch": alg_bytes}
         else:

@@ -25,15 +25,20 @@ constexpr int NP1 = DG_MAXN + 1;
 constexpr int FG = 4;          // fine faces per group
 constexpr int IF_THREADS = 256;
 constexpr int IF_BPC = 4;      // batch members per CTA
+constexpr int NQ = DG_MAXQ, NP = NP1;
 
+// Interpolation to the Gauss nodes and projection back are sum-factorised
+// (one 1D contraction per direction), and every phase is spread over all
+// threads of the CTA (items = face x field x line x node).
 template <typename T>
 __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant__ IfaceArgs<T> A, int batch) {
-  __shared__ T Lp[DG_MAXQ * NP1];
-  __shared__ T Ts[NP1 * NP1], Gs[NP1 * NP1];
-  __shared__ T Tp[FG][NP1 * NP1], Gp[FG][NP1 * NP1];
-  __shared__ T Lsx[FG][DG_MAXQ * NP1], Lsy[FG][DG_MAXQ * NP1];
-  __shared__ T al[FG][DG_MAXQ * DG_MAXQ], bp[FG][DG_MAXQ * DG_MAXQ], bm[FG][DG_MAXQ * DG_MAXQ];
-  __shared__ T accA[NP1 * NP1], accB[NP1 * NP1];
+  __shared__ T Lp[NQ * NP];
+  __shared__ T Lsx[FG][NQ * NP], Lsy[FG][NQ * NP];
+  __shared__ T Tp[FG][2][NP * NP];          // fine face: value / normal derivative at the face nodes
+  __shared__ T Ts[2][NP * NP];              // coarse face
+  __shared__ T W1[FG * 2 * NP * NQ * 2];    // x-interpolated (phase 2-3), then x-projected (phase 4-5)
+  __shared__ T Q[FG][3][NQ * NQ];           // alpha, beta+, beta- at the Gauss nodes
+  __shared__ T acc[2][NP * NP];             // coarse residual (alpha part, beta part)
   const int cf = blockIdx.x;
   const int tid = threadIdx.x;
   const int Np = A.Np, Ns = A.Ns, q = A.q, qq = q * q;
@@ -41,6 +46,9 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
   const int ccol = A.cf_col[cf];
   const int mx = ccol % A.nsx, my = ccol / A.nsx;
   const int f0 = A.cf_ptr[cf], f1 = A.cf_ptr[cf + 1];
+  // W1 layout: fine part [f][w][line][node] (np1 lines x q nodes), coarse part after it
+  T* U1p = W1;                                      // [FG][2][np1][q]
+  T* U1s = W1 + FG * 2 * np1 * q;                   // [FG][2][ns1][q]
   for (int t = tid; t < q * np1; t += IF_THREADS) Lp[t] = A.Lp[t];
   const int b0 = blockIdx.y * IF_BPC, b1 = min(b0 + IF_BPC, batch);
   for (int b = b0; b < b1; ++b) {
@@ -53,14 +61,15 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
       const long long base = (long long)(my * Ns + bb) * A.pys + (mx * Ns + a);
       T g = T(0);
       for (int c = 0; c <= Ns; ++c) g += A.ds[c] * ps[base + (long long)c * A.pzs];
-      Ts[t] = ps[base];
-      Gs[t] = g;
-      accA[t] = T(0);
-      accB[t] = T(0);
+      Ts[0][t] = ps[base];
+      Ts[1][t] = g;
+      acc[0][t] = T(0);
+      acc[1][t] = T(0);
     }
     for (int g0 = f0; g0 < f1; g0 += FG) {
       const int nfg = min(FG, f1 - g0);
       __syncthreads();
+      // phase 1: tables of the group's sub-faces and the fine traces
       for (int t = tid; t < nfg * q * ns1; t += IF_THREADS) {
         const int f = t / (q * ns1), r = t - f * (q * ns1);
         Lsx[f][r] = A.Ls[(long long)A.ff_sx[g0 + f] * q * ns1 + r];
@@ -74,87 +83,118 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
         const long long base = (long long)A.kp0 * A.pzp + (long long)(ey * Np + bb) * A.pyp + (ex * Np + a);
         T g = T(0);
         for (int c = 0; c <= Np; ++c) g += A.dp[c] * pp[base + (long long)c * A.pzp];
-        Tp[f][r] = pp[base + (long long)Np * A.pzp];
-        Gp[f][r] = g;
+        Tp[f][0][r] = pp[base + (long long)Np * A.pzp];
+        Tp[f][1][r] = g;
       }
       __syncthreads();
+      // phase 2: interpolate along x to the Gauss abscissae (fine, and coarse per sub-face)
+      {
+        const int nfine = nfg * 2 * np1 * q, ncoarse = nfg * 2 * ns1 * q;
+        for (int t = tid; t < nfine + ncoarse; t += IF_THREADS) {
+          if (t < nfine) {
+            const int qx = t % q, r = t / q;
+            const int bb = r % np1, r2 = r / np1;
+            const int w = r2 % 2, f = r2 / 2;
+            const T* src = &Tp[f][w][bb * np1];
+            T sum = T(0);
+            for (int a = 0; a < np1; ++a) sum += Lp[qx * np1 + a] * src[a];
+            U1p[((f * 2 + w) * np1 + bb) * q + qx] = sum;
+          } else {
+            const int u = t - nfine;
+            const int qx = u % q, r = u / q;
+            const int bb = r % ns1, r2 = r / ns1;
+            const int w = r2 % 2, f = r2 / 2;
+            const T* src = &Ts[w][bb * ns1];
+            T sum = T(0);
+            for (int a = 0; a < ns1; ++a) sum += Lsx[f][qx * ns1 + a] * src[a];
+            U1s[((f * 2 + w) * ns1 + bb) * q + qx] = sum;
+          }
+        }
+      }
+      __syncthreads();
+      // phase 3: along y, then jump / average / penalty weights at each Gauss node
       for (int t = tid; t < nfg * qq; t += IF_THREADS) {
         const int f = t / qq, r = t - f * qq;
         const int qx = r % q, qy = r / q;
-        T up = T(0), dpv = T(0);
+        T up = T(0), dpv = T(0), um = T(0), dmv = T(0);
         for (int bb = 0; bb < np1; ++bb) {
-          T su = T(0), sd = T(0);
-          for (int a = 0; a < np1; ++a) {
-            su += Lp[qx * np1 + a] * Tp[f][bb * np1 + a];
-            sd += Lp[qx * np1 + a] * Gp[f][bb * np1 + a];
-          }
-          up += Lp[qy * np1 + bb] * su;
-          dpv += Lp[qy * np1 + bb] * sd;
+          const T l = Lp[qy * np1 + bb];
+          up += l * U1p[((f * 2 + 0) * np1 + bb) * q + qx];
+          dpv += l * U1p[((f * 2 + 1) * np1 + bb) * q + qx];
         }
-        T um = T(0), dmv = T(0);
         for (int bb = 0; bb < ns1; ++bb) {
-          T su = T(0), sd = T(0);
-          for (int a = 0; a < ns1; ++a) {
-            su += Lsx[f][qx * ns1 + a] * Ts[bb * ns1 + a];
-            sd += Lsx[f][qx * ns1 + a] * Gs[bb * ns1 + a];
-          }
-          um += Lsy[f][qy * ns1 + bb] * su;
-          dmv += Lsy[f][qy * ns1 + bb] * sd;
+          const T l = Lsy[f][qy * ns1 + bb];
+          um += l * U1s[((f * 2 + 0) * ns1 + bb) * q + qx];
+          dmv += l * U1s[((f * 2 + 1) * ns1 + bb) * q + qx];
         }
         const T J = up - um;
         const T avg = T(0.5) * (A.cp2 * dpv + A.cm2 * dmv);
         const T W = A.Wq[r];
-        al[f][r] = W * (A.gamma * J - avg);
-        bp[f][r] = -T(0.5) * W * A.cp2 * J;
-        bm[f][r] = -T(0.5) * W * A.cm2 * J;
+        Q[f][0][r] = W * (A.gamma * J - avg);
+        Q[f][1][r] = -T(0.5) * W * A.cp2 * J;
+        Q[f][2][r] = -T(0.5) * W * A.cm2 * J;
       }
       __syncthreads();
-      // fine face residuals, then the coarse residual of this group (fixed order)
-      for (int t = tid; t < nfg * nf2 + ns2; t += IF_THREADS) {
-        if (t < nfg * nf2) {
-          const int f = t / nf2, r = t - f * nf2;
-          const int a = r % np1, bb = r / np1;
-          T sa = T(0), sb = T(0);
-          for (int qy = 0; qy < q; ++qy) {
-            T ta = T(0), tb = T(0);
-            for (int qx = 0; qx < q; ++qx) {
-              ta += Lp[qx * np1 + a] * al[f][qy * q + qx];
-              tb += Lp[qx * np1 + a] * bp[f][qy * q + qx];
-            }
-            sa += Lp[qy * np1 + bb] * ta;
-            sb += Lp[qy * np1 + bb] * tb;
+      // phase 4: project along x (fine: alpha, beta+; coarse: alpha, beta-)
+      T* T2p = W1;                                  // [FG][2][q][np1]
+      T* T2s = W1 + FG * 2 * q * np1;               // [FG][2][q][ns1]
+      {
+        const int nfine = nfg * 2 * q * np1, ncoarse = nfg * 2 * q * ns1;
+        for (int t = tid; t < nfine + ncoarse; t += IF_THREADS) {
+          if (t < nfine) {
+            const int a = t % np1, r = t / np1;
+            const int qy = r % q, r2 = r / q;
+            const int w = r2 % 2, f = r2 / 2;
+            const T* src = &Q[f][w][qy * q];
+            T sum = T(0);
+            for (int qx = 0; qx < q; ++qx) sum += Lp[qx * np1 + a] * src[qx];
+            T2p[((f * 2 + w) * q + qy) * np1 + a] = sum;
+          } else {
+            const int u = t - nfine;
+            const int a = u % ns1, r = u / ns1;
+            const int qy = r % q, r2 = r / q;
+            const int w = r2 % 2, f = r2 / 2;
+            const T* src = &Q[f][w == 0 ? 0 : 2][qy * q];
+            T sum = T(0);
+            for (int qx = 0; qx < q; ++qx) sum += Lsx[f][qx * ns1 + a] * src[qx];
+            T2s[((f * 2 + w) * q + qy) * ns1 + a] = sum;
           }
-          const long long o = (long long)b * A.rbp + (long long)A.ff_col[g0 + f] * nf2 + r;
-          A.Rap[o] = sa;
-          A.Rbp[o] = sb;
-        } else {
-          const int r = t - nfg * nf2;
-          const int a = r % ns1, bb = r / ns1;
-          T sa_tot = accA[r], sb_tot = accB[r];
-          for (int f = 0; f < nfg; ++f) {
-            T sa = T(0), sb = T(0);
-            for (int qy = 0; qy < q; ++qy) {
-              T ta = T(0), tb = T(0);
-              for (int qx = 0; qx < q; ++qx) {
-                ta += Lsx[f][qx * ns1 + a] * al[f][qy * q + qx];
-                tb += Lsx[f][qx * ns1 + a] * bm[f][qy * q + qx];
-              }
-              sa += Lsy[f][qy * ns1 + bb] * ta;
-              sb += Lsy[f][qy * ns1 + bb] * tb;
+        }
+      }
+      __syncthreads();
+      // phase 5: project along y; fine residuals out, coarse residual accumulated in face order
+      {
+        const int nfine = nfg * 2 * nf2;
+        for (int t = tid; t < nfine + 2 * ns2; t += IF_THREADS) {
+          if (t < nfine) {
+            const int r = t % nf2, r2 = t / nf2;
+            const int w = r2 % 2, f = r2 / 2;
+            const int a = r % np1, bb = r / np1;
+            T sum = T(0);
+            for (int qy = 0; qy < q; ++qy) sum += Lp[qy * np1 + bb] * T2p[((f * 2 + w) * q + qy) * np1 + a];
+            const long long o = (long long)b * A.rbp + (long long)A.ff_col[g0 + f] * nf2 + r;
+            if (w == 0) A.Rap[o] = sum;
+            else A.Rbp[o] = sum;
+          } else {
+            const int u = t - nfine;
+            const int r = u % ns2, w = u / ns2;
+            const int a = r % ns1, bb = r / ns1;
+            T tot = acc[w][r];
+            for (int f = 0; f < nfg; ++f) {
+              T sum = T(0);
+              for (int qy = 0; qy < q; ++qy) sum += Lsy[f][qy * ns1 + bb] * T2s[((f * 2 + w) * q + qy) * ns1 + a];
+              tot += (w == 0) ? -sum : sum;
             }
-            sa_tot -= sa;
-            sb_tot += sb;
+            acc[w][r] = tot;
           }
-          accA[r] = sa_tot;
-          accB[r] = sb_tot;
         }
       }
     }
     __syncthreads();
     for (int t = tid; t < ns2; t += IF_THREADS) {
       const long long o = (long long)b * A.rbs + (long long)ccol * ns2 + t;
-      A.Ras[o] = accA[t];
-      A.Rbs[o] = accB[t];
+      A.Ras[o] = acc[0][t];
+      A.Rbs[o] = acc[1][t];
     }
   }
 }
