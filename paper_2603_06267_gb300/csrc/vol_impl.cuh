@@ -228,9 +228,17 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
   return acc;
 }
 
-// z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column)
-template <typename T, int N, int VS, int PLANE>
-__device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, T* zs) {
+// z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column).
+// With DIFF the values are taken relative to plane `ref` (the node itself):
+// the rows of the 1D stiffness sum to zero, so this is the same sum, but its
+// terms are small and FP32 rounding scales with the local variation of p
+// instead of with p itself.
+template <typename T, int N, int VS, int PLANE, bool DIFF>
+__device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, int ref, T* zs) {
+  T r[N];
+#pragma unroll
+  for (int a = 0; a < N; ++a) r[a] = T(0);
+  if constexpr (DIFF) vld<T, VS, N>(S0 + ref * PLANE + own, r);
 #pragma unroll
   for (int a = 0; a < N; ++a) zs[a] = T(0);
 #pragma unroll
@@ -239,7 +247,7 @@ __device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T*
     vld<T, VS, N>(S0 + q * PLANE + own, t);
     const T cq = coef[q];
 #pragma unroll
-    for (int a = 0; a < N; ++a) zs[a] += cq * t[a];
+    for (int a = 0; a < N; ++a) zs[a] += cq * (t[a] - r[a]);
   }
 }
 
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
   constexpr int STAGES = G::STAGES;
   constexpr bool VTMA = G::VTMA;
+  constexpr bool DIFF = sizeof(T) == 4;    // difference form of the stencils in FP32
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
 
@@ -307,14 +316,23 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
 #pragma unroll
   for (int a = 0; a < N; ++a) carry[a] = T(0);
   if (ez0 > 0 && active && pg == 0) {
+    T r[N];
+    T rX = T(0);
+#pragma unroll
+    for (int a = 0; a < N; ++a) r[a] = T(0);
+    if constexpr (DIFF) {
+      const T* src = pin + (long long)(ez0 * N) * A.pz + grow;     // the vertex plane itself
+      vld<T, VG, N>(src, r);
+      if (xlast) rX = src[N];
+    }
 #pragma unroll
     for (int q = 0; q <= N; ++q) {
       T t[N];
       const T* src = pin + (long long)((ez0 - 1) * N + q) * A.pz + grow;
       vld<T, VG, N>(src, t);
 #pragma unroll
-      for (int a = 0; a < N; ++a) carry[a] += A.lz[q] * t[a];
-      if (xlast) carryX += A.lz[q] * src[N];
+      for (int a = 0; a < N; ++a) carry[a] += A.lz[q] * (t[a] - r[a]);
+      if (xlast) carryX += A.lz[q] * (src[N] - rX);
     }
   }
 
@@ -374,20 +392,22 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         T acc[N];
         // x stencil
         {
+          const T ref = DIFF ? xr[N] : T(0);
           T l = T(0), r = T(0);
           if (xl) {
 #pragma unroll
-            for (int q = 0; q <= N; ++q) l += A.lx[q] * xr[q];
+            for (int q = 0; q <= N; ++q) l += A.lx[q] * (xr[q] - ref);
           }
 #pragma unroll
-          for (int q = 0; q <= N; ++q) r += A.rx[q] * xr[N + q];
+          for (int q = 0; q <= N; ++q) r += A.rx[q] * (xr[N + q] - ref);
           acc[0] = (l + r) * xiw;
         }
 #pragma unroll
         for (int a = 1; a < N; ++a) {
+          const T ref = DIFF ? xr[N + a] : T(0);
           T s2 = T(0);
 #pragma unroll
-          for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * xr[N + q];
+          for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * (xr[N + q] - ref);
           acc[a] = s2;
         }
         // y stencil
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
               T t[N];
               vld<T, VS, N>(P + own + (q - N) * BX, t);
 #pragma unroll
-              for (int a = 0; a < N; ++a) ylv[a] += A.ly[q] * t[a];
+              for (int a = 0; a < N; ++a) ylv[a] += A.ly[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
             }
           }
           if (yr) {
@@ -410,33 +430,38 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
               T t[N];
               vld<T, VS, N>(P + own + q * BX, t);
 #pragma unroll
-              for (int a = 0; a < N; ++a) yrv[a] += A.ry[q] * t[a];
+              for (int a = 0; a < N; ++a) yrv[a] += A.ry[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
             }
           }
 #pragma unroll
           for (int a = 0; a < N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
         } else {
+          T ys[N];
+#pragma unroll
+          for (int a = 0; a < N; ++a) ys[a] = T(0);
 #pragma unroll
           for (int q = 0; q <= N; ++q) {
             T t[N];
             vld<T, VS, N>(P + own + (q - yb) * BX, t);
 #pragma unroll
-            for (int a = 0; a < N; ++a) acc[a] += cyi[q] * t[a];
+            for (int a = 0; a < N; ++a) ys[a] += cyi[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
           }
+#pragma unroll
+          for (int a = 0; a < N; ++a) acc[a] += ys[a];
         }
         // z stencil: own column over the staged planes of the layer
         T zs[N];
         T iw_z;
         if constexpr (ZM == 0) {
-          zsum<T, N, VS, PLANE>(S0, own, A.rz, zs);
+          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.rz, 0, zs);
           iw_z = (ez > 0) ? A.iwv : A.iwb;
 #pragma unroll
           for (int a = 0; a < N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
         } else if constexpr (ZM == 1) {
-          zsum<T, N, VS, PLANE>(S0, own, A.cz[c], zs);
+          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.cz[c], c, zs);
           iw_z = A.iwa[c];
         } else {
-          zsum<T, N, VS, PLANE>(S0, own, A.lz, zs);
+          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.lz, N, zs);
           iw_z = A.iwb;
 #pragma unroll
           for (int a = 0; a < N; ++a) zs[a] *= iw_z;
@@ -462,40 +487,41 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         const T* P = S0 + c * PLANE;
         const int k = ez * N + c;
         const int col = own + N;
+        const T self = DIFF ? P[col] : T(0);
         T x = T(0);
 #pragma unroll
-        for (int q = 0; q <= N; ++q) x += A.lx[q] * P[own + q];
+        for (int q = 0; q <= N; ++q) x += A.lx[q] * (P[own + q] - self);
         x *= A.iwb;
         T y;
         if (yvert) {
           T l = T(0), r = T(0);
           if (yl) {
 #pragma unroll
-            for (int q = 0; q <= N; ++q) l += A.ly[q] * P[col + (q - N) * BX];
+            for (int q = 0; q <= N; ++q) l += A.ly[q] * (P[col + (q - N) * BX] - self);
           }
           if (yr) {
 #pragma unroll
-            for (int q = 0; q <= N; ++q) r += A.ry[q] * P[col + q * BX];
+            for (int q = 0; q <= N; ++q) r += A.ry[q] * (P[col + q * BX] - self);
           }
           y = (l + r) * yiw;
         } else {
           y = T(0);
 #pragma unroll
-          for (int q = 0; q <= N; ++q) y += cyi[q] * P[col + (q - yb) * BX];
+          for (int q = 0; q <= N; ++q) y += cyi[q] * (P[col + (q - yb) * BX] - self);
         }
         T z = T(0), iw_z;
         if (c == 0) {
 #pragma unroll
-          for (int q = 0; q <= N; ++q) z += A.rz[q] * S0[q * PLANE + col];
+          for (int q = 0; q <= N; ++q) z += A.rz[q] * (S0[q * PLANE + col] - self);
           iw_z = (ez > 0) ? A.iwv : A.iwb;
           z = (carryX + z) * iw_z;
         } else if (c < N) {
 #pragma unroll
-          for (int q = 0; q <= N; ++q) z += A.cz[c][q] * S0[q * PLANE + col];
+          for (int q = 0; q <= N; ++q) z += A.cz[c][q] * (S0[q * PLANE + col] - self);
           iw_z = A.iwa[c];
         } else {
 #pragma unroll
-          for (int q = 0; q <= N; ++q) z += A.lz[q] * S0[q * PLANE + col];
+          for (int q = 0; q <= N; ++q) z += A.lz[q] * (S0[q * PLANE + col] - self);
           iw_z = A.iwb;
           z *= iw_z;
         }
@@ -520,11 +546,12 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
       }
       // carry for the vertex plane (ez+1)*N
       if (pg == 0) {
-        zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
+        zsum<T, N, VS, PLANE, DIFF>(S0, own, A.lz, N, carry);
         if (xlast) {
+          const T self = DIFF ? S0[N * PLANE + own + N] : T(0);
           carryX = T(0);
 #pragma unroll
-          for (int q = 0; q <= N; ++q) carryX += A.lz[q] * S0[q * PLANE + own + N];
+          for (int q = 0; q <= N; ++q) carryX += A.lz[q] * (S0[q * PLANE + own + N] - self);
         }
       }
     }
