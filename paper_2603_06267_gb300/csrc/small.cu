@@ -30,7 +30,9 @@ constexpr int NQ = DG_MAXQ, NP = NP1;
 // Interpolation to the Gauss nodes and projection back are sum-factorised
 // (one 1D contraction per direction), and every phase is spread over all
 // threads of the CTA (items = face x field x line x node).
-template <typename T>
+// CNP, CNS, CQ: compile-time (N+1) of both sides and Gauss points, or 0 for
+// the runtime sizes of A (index arithmetic is the kernel's main cost).
+template <typename T, int CNP, int CNS, int CQ>
 __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant__ IfaceArgs<T> A, int batch) {
   __shared__ T Lp[NQ * NP];
   __shared__ T Lsx[FG][NQ * NP], Lsy[FG][NQ * NP];
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
   __shared__ T acc[2][NP * NP];             // coarse residual (alpha part, beta part)
   const int cf = blockIdx.x;
   const int tid = threadIdx.x;
-  const int Np = A.Np, Ns = A.Ns, q = A.q, qq = q * q;
+  const int Np = CNP ? CNP - 1 : A.Np, Ns = CNS ? CNS - 1 : A.Ns, q = CQ ? CQ : A.q, qq = q * q;
   const int np1 = Np + 1, ns1 = Ns + 1, nf2 = np1 * np1, ns2 = ns1 * ns1;
   const int ccol = A.cf_col[cf];
   const int mx = ccol % A.nsx, my = ccol / A.nsx;
@@ -319,7 +321,8 @@ template <typename T>
 cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s) {
   if (a.ncf <= 0) return cudaSuccess;
   dim3 grid(a.ncf, (batch + IF_BPC - 1) / IF_BPC);
-  iface_kernel<T><<<grid, IF_THREADS, 0, s>>>(a, batch);
+  if (a.Np == 4 && a.Ns == 6 && a.q == 7) iface_kernel<T, 5, 7, 7><<<grid, IF_THREADS, 0, s>>>(a, batch);
+  else iface_kernel<T, 0, 0, 0><<<grid, IF_THREADS, 0, s>>>(a, batch);
   return cudaGetLastError();
 }
 
