@@ -170,6 +170,18 @@ int pmut_array_set(dgsem_ctx* ctx, int n_pmut, int n_modes, const int* foot_ptr,
 int dgsem_run(dgsem_ctx* ctx, int precision, int batch, int nsteps, const double* drive,
               int n_recv, const double* recv_xyz, double* traces, int flags, void* stream);
 
+/* Several meshes in one launch: dgsem_run on each of the n contexts with the
+ * same precision, nsteps and flags, their time steps captured as parallel
+ * branches of one CUDA graph so that meshes of different sizes and orders
+ * (e.g. PMUT arrays of different sizes) share the GPU in one launch.  All
+ * contexts must belong to the current device and be distinct.  Per-context
+ * arrays: batch[n], drive[n] (as in dgsem_run), n_recv[n], recv_xyz[n],
+ * traces[n]; n_recv, recv_xyz and traces may be NULL when no context has
+ * receivers.  Results equal n separate dgsem_run calls. */
+int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* batch, int nsteps,
+                    const double* const* drive, const int* n_recv, const double* const* recv_xyz,
+                    double* const* traces, int flags, void* stream);
+
 /* Initial state p^0, p'^0 (host, FP64, [ndof] in the node order above,
  * broadcast to every batch member) for the next dgsem_run without
  * DGSEM_RUN_CONTINUE; the run starts from p''^0 = M^-1 (-K p^0).  Either

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -783,8 +784,21 @@ int upload_field(dgsem_ctx* c, const std::vector<double>& h, void* const* dst, c
   return DGSEM_OK;
 }
 
+// Per-run device views of the drive and trace buffers.
+struct RunIO {
+  const double* d_drive = nullptr;
+  double* d_tr = nullptr;
+  double* host_tr = nullptr;     // caller's host trace buffer (copied back at the end), or NULL
+  size_t tr_n = 0;
+  int R = 0;
+  long long dbs = 0, dks = 0, tbs = 0, trs = 0;
+};
+
+// Everything a run does before its time steps: tensor maps, status words,
+// state reset or initial state, device copies of the drive, trace buffers.
 template <typename T>
-int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
+int run_prepare(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s,
+                RunIO& io) {
   int rc;
   if ((rc = refresh_tmaps(c))) return rc;
   CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
@@ -799,11 +813,11 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     c->state_valid = true;
   }
   // drive: device copy if needed
-  const double* d_drive = nullptr;
   const size_t drive_n = (size_t)c->batch * c->K * nsteps;
+  io.d_drive = nullptr;
   if (c->K > 0 && drive) {
     if (is_device_ptr(drive)) {
-      d_drive = drive;
+      io.d_drive = drive;
     } else {
       if (drive_n > c->drive_cap) {
         drop_graph(c);
@@ -812,28 +826,55 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
         c->drive_cap = drive_n;
       }
       CUDA_TRY(cudaMemcpyAsync(c->d_drive, drive, drive_n * sizeof(double), cudaMemcpyHostToDevice, s));
-      d_drive = c->d_drive;
+      io.d_drive = c->d_drive;
     }
   }
-  double* d_tr = nullptr;
-  const size_t tr_n = (size_t)c->batch * R * nsteps;
-  bool tr_host = false;
+  io.R = R;
+  io.tr_n = (size_t)c->batch * R * nsteps;
+  io.host_tr = nullptr;
+  io.d_tr = nullptr;
   if (R > 0) {
     if (is_device_ptr(traces_out)) {
-      d_tr = traces_out;
+      io.d_tr = traces_out;
     } else {
-      tr_host = true;
-      if (tr_n > c->traces_cap) {
+      io.host_tr = traces_out;
+      if (io.tr_n > c->traces_cap) {
         drop_graph(c);
         dfree(c->d_traces);
-        if ((rc = dalloc(&c->d_traces, tr_n * sizeof(double)))) { c->traces_cap = 0; return rc; }
-        c->traces_cap = tr_n;
+        if ((rc = dalloc(&c->d_traces, io.tr_n * sizeof(double)))) { c->traces_cap = 0; return rc; }
+        c->traces_cap = io.tr_n;
       }
-      d_tr = c->d_traces;
+      io.d_tr = c->d_traces;
     }
   }
   CUDA_TRY(cudaMemsetAsync(c->d_step, 0, sizeof(int), s));
-  const long long dbs = (long long)c->K * nsteps, dks = nsteps, tbs = (long long)R * nsteps, trs = nsteps;
+  io.dbs = (long long)c->K * nsteps;
+  io.dks = nsteps;
+  io.tbs = (long long)R * nsteps;
+  io.trs = nsteps;
+  return DGSEM_OK;
+}
+
+// Traces back to the host if needed, timings, device status word.
+int run_finish(dgsem_ctx* c, int nsteps, const RunIO& io, cudaStream_t s) {
+  c->step += nsteps;
+  if (io.host_tr) CUDA_TRY(cudaMemcpyAsync(io.host_tr, io.d_tr, io.tr_n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  collect_timings(c);
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    c->state_valid = false;
+    return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up (status %d); the state is invalid", err);
+  }
+  return DGSEM_OK;
+}
+
+template <typename T>
+int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
+  RunIO io;
+  int rc = run_prepare<T>(c, nsteps, drive, R, traces_out, flags, s, io);
+  if (rc) return rc;
   int done = 0;
   if (!c->profiling && nsteps >= 4) {
     // replay a captured block of G (even) steps; the kernels read the step
@@ -841,8 +882,8 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     const int G = std::min(32, nsteps - (nsteps % 2));
     struct Key { int prec, batch, R, G; const void* dr; const void* tr; long long dbs, tbs; const void* x0; const void* y0; int t0, t1; } key;
     std::memset(&key, 0, sizeof(key));
-    key.prec = c->prec; key.batch = c->batch; key.R = R; key.G = G; key.dr = d_drive; key.tr = d_tr;
-    key.dbs = dbs; key.tbs = tbs; key.x0 = c->X[0]; key.y0 = c->Y[0];
+    key.prec = c->prec; key.batch = c->batch; key.R = R; key.G = G; key.dr = io.d_drive; key.tr = io.d_tr;
+    key.dbs = io.dbs; key.tbs = io.tbs; key.x0 = c->X[0]; key.y0 = c->Y[0];
     key.t0 = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][0]; key.t1 = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][1];
     std::vector<unsigned char> kb(reinterpret_cast<unsigned char*>(&key), reinterpret_cast<unsigned char*>(&key) + sizeof(key));
     if (!c->graph || c->graph_key != kb) {
@@ -853,7 +894,7 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
       CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       int crc = DGSEM_OK;
       for (int n = 0; n < G && crc == DGSEM_OK; ++n)
-        crc = launch_step<T>(c, c->cap_stream, d_drive, dbs, dks, 0, R, d_tr, tbs, trs, false);
+        crc = launch_step<T>(c, c->cap_stream, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false);
       cudaGraph_t g = nullptr;
       cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
       if (crc) { if (g) cudaGraphDestroy(g); return crc; }
@@ -874,18 +915,89 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     }
   }
   for (int n = done; n < nsteps; ++n) {
-    rc = launch_step<T>(c, s, d_drive, dbs, dks, 0, R, d_tr, tbs, trs, false);
+    rc = launch_step<T>(c, s, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false);
     if (rc) return rc;
   }
-  c->step += nsteps;
-  if (tr_host) CUDA_TRY(cudaMemcpyAsync(traces_out, d_tr, tr_n * sizeof(double), cudaMemcpyDeviceToHost, s));
-  CUDA_TRY(cudaStreamSynchronize(s));
-  collect_timings(c);
-  int err = 0;
-  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (err) {
-    c->state_valid = false;
-    return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up (status %d); the state is invalid", err);
+  return run_finish(c, nsteps, io, s);
+}
+
+// Several meshes in one launch: each context's block of G steps is captured
+// on its own stream as a parallel branch of one CUDA graph, so uneven
+// meshes (different sizes and orders) run concurrently.
+template <typename T>
+int run_multi_impl(int n, dgsem_ctx* const* ctxs, int nsteps, const double* const* drive, const int* n_recv,
+                   double* const* traces, int flags, cudaStream_t s) {
+  std::vector<RunIO> io(n);
+  for (int i = 0; i < n; ++i) {
+    int rc = run_prepare<T>(ctxs[i], nsteps, drive ? drive[i] : nullptr, n_recv ? n_recv[i] : 0,
+                            traces ? traces[i] : nullptr, flags, s, io[i]);
+    if (rc) return rc;
+  }
+  const int G = std::min(32, nsteps - (nsteps % 2));
+  int done = 0;
+  if (G >= 2) {
+    cudaStream_t main = nullptr;
+    std::vector<cudaEvent_t> ev(n + 1, nullptr);
+    auto cleanup = [&]() {
+      for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+      if (main) cudaStreamDestroy(main);
+    };
+    CUDA_TRY(cudaStreamCreateWithFlags(&main, cudaStreamNonBlocking));
+    for (auto& e : ev) {
+      cudaError_t ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      if (ce != cudaSuccess) { cleanup(); return fail(DGSEM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)); }
+    }
+    for (int i = 0; i < n; ++i)
+      if (!ctxs[i]->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctxs[i]->cap_stream, cudaStreamNonBlocking));
+    std::vector<std::array<long long, DGSEM_K_COUNT>> before(n), per(n);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < DGSEM_K_COUNT; ++k) before[i][k] = ctxs[i]->launches[k];
+    cudaError_t ce = cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) { cleanup(); return fail(DGSEM_ECUDA, "graph capture: %s", cudaGetErrorString(ce)); }
+    cudaEventRecord(ev[n], main);
+    int crc = DGSEM_OK;
+    for (int i = 0; i < n && crc == DGSEM_OK; ++i) {
+      dgsem_ctx* c = ctxs[i];
+      cudaStreamWaitEvent(c->cap_stream, ev[n], 0);
+      for (int st = 0; st < G && crc == DGSEM_OK; ++st)
+        crc = launch_step<T>(c, c->cap_stream, io[i].d_drive, io[i].dbs, io[i].dks, 0, io[i].R, io[i].d_tr, io[i].tbs,
+                             io[i].trs, false);
+      cudaEventRecord(ev[i], c->cap_stream);
+      cudaStreamWaitEvent(main, ev[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    ce = cudaStreamEndCapture(main, &g);
+    if (crc) { if (g) cudaGraphDestroy(g); cleanup(); return crc; }
+    if (ce != cudaSuccess) { cleanup(); return fail(DGSEM_ECUDA, "graph capture: %s", cudaGetErrorString(ce)); }
+    cudaGraphExec_t exec = nullptr;
+    ce = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) { cleanup(); return fail(DGSEM_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce)); }
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < DGSEM_K_COUNT; ++k) {
+        per[i][k] = ctxs[i]->launches[k] - before[i][k];
+        ctxs[i]->launches[k] = before[i][k];
+      }
+    for (; done + G <= nsteps; done += G) {
+      ce = cudaGraphLaunch(exec, s);
+      if (ce != cudaSuccess) break;
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < DGSEM_K_COUNT; ++k) ctxs[i]->launches[k] += per[i][k];
+    }
+    cudaStreamSynchronize(s);
+    cudaGraphExecDestroy(exec);
+    cleanup();
+    if (ce != cudaSuccess) return fail(DGSEM_ECUDA, "graph launch: %s", cudaGetErrorString(ce));
+  }
+  for (int st = done; st < nsteps; ++st)
+    for (int i = 0; i < n; ++i) {
+      int rc = launch_step<T>(ctxs[i], s, io[i].d_drive, io[i].dbs, io[i].dks, 0, io[i].R, io[i].d_tr, io[i].tbs,
+                              io[i].trs, false);
+      if (rc) return rc;
+    }
+  for (int i = 0; i < n; ++i) {
+    int rc = run_finish(ctxs[i], nsteps, io[i], s);
+    if (rc) return rc;
   }
   return DGSEM_OK;
 }
@@ -1092,6 +1204,36 @@ int dgsem_run(dgsem_ctx* c, int precision, int batch, int nsteps, const double* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (precision == DGSEM_FP64) return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
   return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
+}
+
+int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* batch, int nsteps,
+                    const double* const* drive, const int* n_recv, const double* const* recv_xyz,
+                    double* const* traces, int flags, void* stream) {
+  if (n < 1 || !ctxs || !batch) return fail(DGSEM_EINVAL, "n >= 1, ctxs and batch are required");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return fail(DGSEM_EINVAL, "bad precision %d", precision);
+  if (nsteps < 0) return fail(DGSEM_EINVAL, "nsteps < 0");
+  int dev = -1;
+  CUDA_TRY(cudaGetDevice(&dev));
+  for (int i = 0; i < n; ++i) {
+    dgsem_ctx* c = ctxs[i];
+    if (!c) return fail(DGSEM_EINVAL, "ctxs[%d] is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return fail(DGSEM_EINVAL, "context %d appears twice", i);
+    if (c->device != dev) return fail(DGSEM_EINVAL, "context %d belongs to device %d, current is %d", i, c->device, dev);
+    if (batch[i] < 1) return fail(DGSEM_EINVAL, "batch[%d] < 1", i);
+    const int R = n_recv ? n_recv[i] : 0;
+    if (R < 0 || (R > 0 && (!recv_xyz || !recv_xyz[i] || !traces || !traces[i])))
+      return fail(DGSEM_EINVAL, "context %d: receivers need recv_xyz and traces", i);
+    if (c->K > 0 && nsteps > 0 && (!drive || !drive[i])) return fail(DGSEM_EINVAL, "context %d: drive is NULL", i);
+    if ((flags & DGSEM_RUN_CONTINUE) && (!c->state_valid || c->prec != precision || c->batch != batch[i]))
+      return fail(DGSEM_ESTATE, "context %d: DGSEM_RUN_CONTINUE needs a previous run with the same precision and batch", i);
+    int rc = ensure_run_state(c, precision, batch[i]);
+    if (rc) return rc;
+    if ((rc = setup_receivers(c, R, R > 0 ? recv_xyz[i] : nullptr))) return rc;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == DGSEM_FP64) return run_multi_impl<double>(n, ctxs, nsteps, drive, n_recv, traces, flags, s);
+  return run_multi_impl<float>(n, ctxs, nsteps, drive, n_recv, traces, flags, s);
 }
 
 int dgsem_get_pressure(const dgsem_ctx* c, double* p, size_t len) {

@@ -31,7 +31,7 @@ DGSEM_RUN_CONTINUE = 1
 
 EXPORTED = [
     "dgsem_mesh_create", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
-    "dgsem_run", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
+    "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
 ]
@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_pmut_nodes.argtypes = [vp, POINTER(c_int), POINTER(POINTER(c_double))]
     lib.pmut_array_set.argtypes = [vp, c_int, c_int, vp, vp, vp, vp, vp, vp, vp]
     lib.dgsem_run.argtypes = [vp, c_int, c_int, c_int, vp, c_int, vp, vp, c_int, vp]
+    lib.dgsem_run_multi.argtypes = [c_int, vp, c_int, vp, c_int, vp, vp, vp, vp, c_int, vp]
     lib.dgsem_set_state.argtypes = [vp, vp, vp]
     lib.dgsem_get_pressure.argtypes = [vp, vp, c_size_t]
     lib.dgsem_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
@@ -216,6 +217,28 @@ def dgsem_run(ctx, precision: int, batch: int, nsteps: int, drive, recv_xyz, tra
         stream = _current_stream()
     _check(_lib.dgsem_run(ctx, precision, batch, nsteps, _ptr(drive), R, _ptr(recv), _ptr(traces), flags,
                           stream), "dgsem_run")
+    return traces
+
+
+def dgsem_run_multi(ctxs, precision: int, batch, nsteps: int, drives, recv_xyz, traces=None, flags: int = 0,
+                    stream=None):
+    """dgsem_run on several contexts in one launch (parallel graph branches).
+    drives / recv_xyz: per-context arrays; returns the per-context traces."""
+    n = len(ctxs)
+    carr = (c_void_p * n)(*[c.value if isinstance(c, c_void_p) else c for c in ctxs])
+    barr = np.ascontiguousarray(batch, dtype=np.int32)
+    recvs = [np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3) for r in recv_xyz]
+    nr = np.array([r.shape[0] for r in recvs], dtype=np.int32)
+    if traces is None:
+        traces = [np.zeros((int(barr[i]), int(nr[i]), nsteps)) for i in range(n)]
+    drives = [_f64(d) for d in drives]
+    darr = (c_void_p * n)(*[_ptr(d) for d in drives])
+    rarr = (c_void_p * n)(*[_ptr(r) for r in recvs])
+    tarr = (c_void_p * n)(*[_ptr(t) for t in traces])
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_run_multi(n, carr, precision, _ptr(barr), nsteps, darr, _ptr(nr), rarr, tarr, flags, stream),
+           "dgsem_run_multi")
     return traces
 
 

@@ -264,3 +264,76 @@ def test_stability_check_matches_oracle_eigenvalue():
     code, _ = dgsem.dgsem_check_stability(big.ctx, 200)
     assert code == dgsem.DGSEM_EUNSTABLE
     big.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_run_multi_uneven_meshes_equals_separate_runs(prec):
+    """Uneven PMUT arrays (different sizes, orders, batches) in one
+    graph-captured launch give exactly the traces of separate runs."""
+    from paper_2603_06267_gb300 import dgsem
+    ws = [W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=70, batch=2, steer=True),
+          W.small_two_domain(nx_p=8, nz_p=2, nx_s=4, nz_s=2, n_pmut_side=4, nsteps=70, batch=1, seed=21),
+          W.small_one_domain(nel=(3, 2, 2), nsteps=70, n_pmut_side=2, order=6)]
+    sols = [gpu_solver(w) for w in ws]
+    drives = [w.drive(s.dt, 70, w.batch) for w, s in zip(ws, sols)]
+    sep = [s.run(drive=d, precision=prec) for s, d in zip(sols, drives)]
+    multi = dgsem.dgsem_run_multi([s.ctx for s in sols], prec, [w.batch for w in ws], 70, drives,
+                                  [w.receivers for w in ws])
+    for a, b in zip(sep, multi):
+        assert np.array_equal(a, b)
+    # the oracle agrees with the multi-mesh run too (FP64)
+    if prec == 0:
+        P = oracle_problem(ws[1])
+        to = P.run(dt=P.stable_dt(), drive=drives[1])
+        assert rel_l2(multi[1], to) < FP64_TOL
+    for s in sols:
+        s.close()
+
+
+def test_fp32_long_horizon_8000_steps():
+    """FP32-mixed stays within 1e-4 of the FP64 oracle over 8000 steps (the
+    config-3/4 horizon) on a 2:1 mesh with a PMUT array."""
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=8000)
+    tg, to, pg, po = run_both(w, 1)
+    assert rel_l2(tg, to) < FP32_TOL
+
+
+def test_config2_full_size_fp32_vs_fp64():
+    """Config 2 at full size (18.6M nodes, 256 PMUTs, 64 receivers, 4000 steps):
+    FP32-mixed traces within 1e-4 of the FP64 path, receiver by receiver."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.config2_array16()
+    sol = gpu_solver(w)
+    t64 = sol.run(precision=dgsem.DGSEM_FP64)
+    t32 = sol.run(precision=dgsem.DGSEM_FP32_MIXED)
+    assert np.abs(t64).max() > 0 and np.all(np.isfinite(t32))
+    assert rel_l2(t32, t64) < FP32_TOL
+    worst = max(rel_l2(t32[0, r], t64[0, r]) for r in range(t64.shape[1]))
+    assert worst < 1e-3
+    sol.close()
+
+
+def test_config3_full_size_linearity_and_shift():
+    """Config 3 mesh at full size with 64 patterns (the bench's launch
+    configuration): linear in the drive and exactly time-shift invariant."""
+    import torch
+    from paper_2603_06267_gb300 import dgsem
+    S = 120
+    w = W.config4_batched(nsteps=S, batch=64)
+    sol = gpu_solver(w)
+    dgsem.dgsem_autotune(sol.ctx, 1, 64, 2, reps=1)
+    d = w.drive(sol.dt, S, 64)
+    # compress the bursts into the window: shift every pattern to start at t = 0
+    rng = np.random.default_rng(9)
+    d1 = rng.normal(size=d.shape) * 5.0
+    d2 = rng.normal(size=d.shape) * 5.0
+    t1 = sol.run(drive=d1, precision=1)
+    t2 = sol.run(drive=d2, precision=1)
+    t12 = sol.run(drive=d1 + d2, precision=1)
+    assert rel_l2(t12, t1 + t2) < 1e-5
+    k = 7
+    ds = np.zeros_like(d1)
+    ds[:, :, k:] = d1[:, :, :-k]
+    ts = sol.run(drive=ds, precision=1)
+    assert np.array_equal(ts[:, :, k:], t1[:, :, :-k])
+    sol.close()
