@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgsem.so")
-SOURCES = ["api.cu", "vol_f32.cu", "vol_f64.cu", "small.cu"]
+SOURCES = ["api.cu", "vol_f32.cu", "vol_f64.cu", "small.cu", "surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +37,8 @@ def _stale(obj: str, deps) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "vol_impl.cuh"), os.path.join(INCLUDE, "dgsem.h")]
+    headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "vol_impl.cuh"), os.path.join(INCLUDE, "dgsem.h"),
+               os.path.join(INCLUDE, "surrogate.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                     "-I", CSRC, "-I", INCLUDE]
     if verbose:

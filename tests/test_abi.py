@@ -73,3 +73,13 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.dgsem_get_dt(None, None, None, None) == dgsem.DGSEM_EINVAL
     lib.dgsem_destroy(None)
     assert b"NULL" in lib.dgsem_last_error()
+
+
+def test_surrogate_symbols_exported(lib):
+    src = open(os.path.join(ROOT, "include", "surrogate.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"^\s*(?:int|void|size_t|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+    from paper_2603_06267_gb300 import surrogate
+    assert sorted(surrogate.SRG_EXPORTED) == names
+    for n in names:
+        assert hasattr(lib, n), n

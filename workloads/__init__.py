@@ -354,3 +354,21 @@ def seeded_field(rng_seed: int, x, y, z, scale=1.0):
         a = rng.normal()
         out = out + a * np.cos(k[0] * x + ph[0]) * np.cos(k[1] * y + ph[1]) * np.cos(k[2] * z + ph[2])
     return scale * out
+
+
+def surrogate_array(batch: int = 64, seed: int = 5, nsteps: int = 2950) -> Workload:
+    """Training/evaluation workload of the learned surrogate: an 8x8 PMUT array
+    (pitch 100 um, 5 modes, +-3 % spread) on a 32x32x8 N=4 primary box
+    (0.8 x 0.8 x 0.2 mm) under a 16x16x24 N=6 secondary box (0.8 x 0.8 x 1.2 mm),
+    64 receivers on an 8x8 grid at z = 0.8 mm, beam-steering drive patterns.
+    The config-4 mesh would cost ~0.8 TDoF-steps per pattern; this one ~5.6 G."""
+    rng = np.random.default_rng(seed)
+    doms = _stacked(32, 8, 0.8e-3, 0.2e-3, 16, 24, 1.2e-3)
+    centers = _grid_centers(8, 100e-6)
+    pm = make_pmut_array(centers, 60e-6, MODE_FREQS_5, 0.01,
+                         freq_scale=rng.uniform(0.97, 1.03, size=centers.shape[0]))
+    g = 50e-6 + 100e-6 * np.arange(8)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(64, 0.8e-3)], axis=1)
+    d, a, _ = steering_patterns(centers, batch, seed=seed + 1000)
+    return Workload("surrogate_array", doms, nsteps, rec, pm, batch=batch, drive_delay=d, drive_amp=a)
