@@ -63,6 +63,12 @@ struct VolArgs {
   const T* Ra;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b alpha_q
   const T* Rb;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b beta_q
   T dI[N + 1];             // d_c = (2/h_z) l_c'(face)
+  // FP32 tables for packed f32x2 arithmetic: x rows with their taps in pairs
+  // (q = 2k, 2k+1), y and z coefficients repeated in both lanes
+  float2 cxq[N + 1][(N + 1) / 2];
+  float2 lxq[(N + 1) / 2], rxq[(N + 1) / 2];
+  float2 ly2[N + 1], ry2[N + 1], lz2[N + 1], rz2[N + 1];
+  float2 cz2[N + 1][N + 1];
 };
 
 // ---------------------------------------------------------------------------

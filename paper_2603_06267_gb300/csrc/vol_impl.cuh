@@ -228,17 +228,9 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
   return acc;
 }
 
-// z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column).
-// With DIFF the values are taken relative to plane `ref` (the node itself):
-// the rows of the 1D stiffness sum to zero, so this is the same sum, but its
-// terms are small and FP32 rounding scales with the local variation of p
-// instead of with p itself.
-template <typename T, int N, int VS, int PLANE, bool DIFF>
-__device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, int ref, T* zs) {
-  T r[N];
-#pragma unroll
-  for (int a = 0; a < N; ++a) r[a] = T(0);
-  if constexpr (DIFF) vld<T, VS, N>(S0 + ref * PLANE + own, r);
+// z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column)
+template <typename T, int N, int VS, int PLANE>
+__device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, T* zs) {
 #pragma unroll
   for (int a = 0; a < N; ++a) zs[a] = T(0);
 #pragma unroll
@@ -247,7 +239,169 @@ __device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T*
     vld<T, VS, N>(S0 + q * PLANE + own, t);
     const T cq = coef[q];
 #pragma unroll
-    for (int a = 0; a < N; ++a) zs[a] += cq * (t[a] - r[a]);
+    for (int a = 0; a < N; ++a) zs[a] += cq * t[a];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 stencils.  Every row of the 1D stiffness sums to zero, so
+// sum_q c_q p_q = sum_q c_q (p_q - p_ref) for any p_ref.  The FP32 path takes
+// p_ref close to the nodes involved (the node itself along y and z, the
+// element's first node along x): the summands then have the size of the local
+// variation of p rather than of p, and FP32 rounding no longer accumulates
+// into a coherent drift over thousands of steps.  The arithmetic is packed
+// two lanes wide (f32x2): y and z pair neighbouring owned nodes, x pairs the
+// taps of a row.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+// a - b, exactly as a subtraction (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// acc[i] += c2 * (t - self) over the owned run (pairs, then a lone last node for odd N)
+template <int N, int VS>
+__device__ __forceinline__ void run_term(const float* __restrict__ src, float2 c2, const float* self, float2* acc,
+                                         float& accT) {
+  float t[N];
+  vld<float, VS, N>(src, t);
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) acc[i] = __ffma2_rn(c2, sub2(f2(t[2 * i], t[2 * i + 1]), f2(self[2 * i], self[2 * i + 1])), acc[i]);
+  if constexpr (N % 2 == 1) accT = fmaf(c2.x, t[N - 1] - self[N - 1], accT);
+}
+
+// x row: sum_q cq[q] d[q] over q = 0..N with taps in pairs (cq2) and, for even
+// N, a lone last tap
+template <int N>
+__device__ __forceinline__ float row_dot(const float2* cq2, float clast, const float2* d2, float dlast) {
+  constexpr int K2 = (N + 1) / 2;
+  float2 s = __fmul2_rn(cq2[0], d2[0]);
+#pragma unroll
+  for (int k = 1; k < K2; ++k) s = __ffma2_rn(cq2[k], d2[k], s);
+  float r = s.x + s.y;
+  if constexpr (N % 2 == 0) r = fmaf(clast, dlast, r);
+  return r;
+}
+
+// M^-1 K p of the N owned nodes of one staged plane (FP32, difference form).
+// ZM: 0 vertex plane (carry = lower layer's part), 1 interior plane c,
+// 2 top boundary plane of the box.  xr: staged row (left element, own
+// element, next vertex); cyi2: this row's interior y coefficients.
+template <int N, int ZM, int VS, int PLANE, int BX>
+__device__ __forceinline__ void stencil_f32(const VolArgs<float, N>& A, const float* __restrict__ S0, int own,
+                                            int c, const float* xr, bool xl, float xiw, bool yvert, bool yl,
+                                            bool yr, float yiw, int yb, const float2* cyi2, const float* carry,
+                                            float iw_z, float* out) {
+  constexpr int K2 = (N + 1) / 2;
+  constexpr int NP = N / 2;
+  const float* P = S0 + c * PLANE;
+  const float* self = xr + N;
+  // x: differences to the element's first node
+  const float ref = xr[N];
+  const float2 ref2 = f2(ref, ref);
+  float2 d2[K2];
+#pragma unroll
+  for (int k = 0; k < K2; ++k) d2[k] = sub2(f2(xr[N + 2 * k], xr[N + 2 * k + 1]), ref2);
+  const float dlast = (N % 2 == 0) ? xr[2 * N] - ref : 0.f;
+  float acc[N];
+  {
+    float r = row_dot<N>(A.rxq, A.rx[N], d2, dlast);
+    if (xl) {
+      float2 dl[K2];
+#pragma unroll
+      for (int k = 0; k < K2; ++k) dl[k] = sub2(f2(xr[2 * k], xr[2 * k + 1]), ref2);
+      // for even N the pairs cover q = 0..N-1; the tap q = N is the node itself
+      float2 sl = __fmul2_rn(A.lxq[0], dl[0]);
+#pragma unroll
+      for (int k = 1; k < K2; ++k) sl = __ffma2_rn(A.lxq[k], dl[k], sl);
+      r += sl.x + sl.y;
+    }
+    acc[0] = r * xiw;
+  }
+#pragma unroll
+  for (int a = 1; a < N; ++a) acc[a] = row_dot<N>(A.cxq[a], A.cx[a][N], d2, dlast);
+  // y: differences to the node itself
+  float2 ys[NP > 0 ? NP : 1];
+  float ysT = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) ys[i] = f2(0.f, 0.f);
+  if (yvert) {
+    if (yl) {
+#pragma unroll
+      for (int q = 0; q < N; ++q) run_term<N, VS>(P + own + (q - N) * BX, A.ly2[q], self, ys, ysT);
+    }
+    if (yr) {
+#pragma unroll
+      for (int q = 1; q <= N; ++q) run_term<N, VS>(P + own + q * BX, A.ry2[q], self, ys, ysT);
+    }
+    const float2 w2 = f2(yiw, yiw);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) ys[i] = __fmul2_rn(ys[i], w2);
+    ysT *= yiw;
+  } else {
+#pragma unroll
+    for (int q = 0; q <= N; ++q) run_term<N, VS>(P + own + (q - yb) * BX, cyi2[q], self, ys, ysT);
+  }
+  // z: differences to the node itself, over the staged planes of the layer
+  float2 zs[NP > 0 ? NP : 1];
+  float zsT = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) zs[i] = f2(0.f, 0.f);
+  if constexpr (ZM == 0) {
+#pragma unroll
+    for (int q = 1; q <= N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.rz2[q], self, zs, zsT);
+    const float2 w2 = f2(iw_z, iw_z);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) zs[i] = __fmul2_rn(__fadd2_rn(f2(carry[2 * i], carry[2 * i + 1]), zs[i]), w2);
+    if constexpr (N % 2 == 1) zsT = (carry[N - 1] + zsT) * iw_z;
+  } else if constexpr (ZM == 1) {
+#pragma unroll
+    for (int q = 0; q <= N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.cz2[c][q], self, zs, zsT);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.lz2[q], self, zs, zsT);
+    const float2 w2 = f2(iw_z, iw_z);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) zs[i] = __fmul2_rn(zs[i], w2);
+    zsT *= iw_z;
+  }
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const float2 sm = __fadd2_rn(__fadd2_rn(f2(acc[2 * i], acc[2 * i + 1]), ys[i]), zs[i]);
+    out[2 * i] = sm.x;
+    out[2 * i + 1] = sm.y;
+  }
+  if constexpr (N % 2 == 1) out[N - 1] = (acc[N - 1] + ysT) + zsT;
+}
+
+// z carry of the next vertex plane (plane N of the layer):
+// sum_{q<N} lz[q] (p_q - p_N) of each owned node (FP32 difference form)
+template <int N, int VS, int PLANE>
+__device__ __forceinline__ void carry_f32(const VolArgs<float, N>& A, const float* __restrict__ S0, int own,
+                                          float* carry) {
+  constexpr int NP = N / 2;
+  float self[N];
+  vld<float, VS, N>(S0 + N * PLANE + own, self);
+  float2 cs[NP > 0 ? NP : 1];
+  float cT = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) cs[i] = f2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.lz2[q], self, cs, cT);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) { carry[2 * i] = cs[i].x; carry[2 * i + 1] = cs[i].y; }
+  if constexpr (N % 2 == 1) carry[N - 1] = cT;
+}
+
+// Row of the tile handled by thread row ty: the TYE vertex rows (element
+// boundaries, two-element y stencil) come first so that they fill their own
+// warps and the y stencil does not diverge inside a warp.
+template <int N, int TYE>
+__device__ __forceinline__ int tile_row(int ty) {
+  if constexpr (N == 1) {
+    return ty;
+  } else {
+    if (ty < TYE) return ty * N;
+    const int i = ty - TYE;
+    return (i / (N - 1)) * N + 1 + i % (N - 1);
   }
 }
 
@@ -261,7 +415,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
   constexpr int STAGES = G::STAGES;
   constexpr bool VTMA = G::VTMA;
-  constexpr bool DIFF = sizeof(T) == 4;    // difference form of the stencils in FP32
+  constexpr bool DIFF = sizeof(T) == 4;    // FP32: difference form, packed arithmetic
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
 
@@ -289,7 +443,8 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   }
 
   const int ex = ex0 + tx;                 // element column
-  const int j = y0 + ty;                   // lattice row
+  const int rt = tile_row<N, TYE>(ty);     // row in the tile
+  const int j = y0 + rt;                   // lattice row
   const bool active = ex < A.ne0 && j < A.L1;
   const bool xlast = ex == A.ne0 - 1;      // also owns node ne0*N
   const int ey = j / N;
@@ -298,16 +453,20 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   const bool yl = ey > 0, yr = ey < A.ne1;
   const T yiw = (yl && yr) ? A.iwv : A.iwb;
   T cyi[N + 1];
+  float2 cyi2[DIFF ? N + 1 : 1];
 #pragma unroll
-  for (int q = 0; q <= N; ++q) cyi[q] = yvert ? T(0) : A.cy[yb][q];
+  for (int q = 0; q <= N; ++q) {
+    cyi[q] = yvert ? T(0) : A.cy[yb][q];
+    if constexpr (DIFF) cyi2[q] = f2((float)cyi[q], (float)cyi[q]);
+  }
   const T iw_y = yvert ? yiw : A.iwa[yb];
   const bool xl = ex > 0;
   const T xiw = xl ? A.iwv : A.iwb;        // vertex node ex*N (an element always lies to its right)
 
-  const int r0 = ty + N;                   // staged row of lattice row j
+  const int r0 = rt + N;                   // staged row of lattice row j
   const int cb = NAL + tx * N;             // staged column of node ex*N
   const int own = r0 * BX + cb;            // staged offset of node ex*N in a p plane
-  const int vown = ty * BXV + tx * N;      // staged offset of node ex*N in a v plane
+  const int vown = rt * BXV + tx * N;      // staged offset of node ex*N in a v plane
   const long long grow = (long long)j * A.py + (long long)ex * N;   // node ex*N in a plane
 
   // z carry: sum_q lz[q] p[(ez-1)N + q] of each owned node (plane group 0 owns the vertex planes)
@@ -389,95 +548,118 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         vld<T, VS, N>(P + own - N, xr);
         vld<T, VS, N>(P + own, xr + N);
         xr[2 * N] = P[own + N];
-        T acc[N];
-        // x stencil
-        {
-          const T ref = DIFF ? xr[N] : T(0);
-          T l = T(0), r = T(0);
-          if (xl) {
-#pragma unroll
-            for (int q = 0; q <= N; ++q) l += A.lx[q] * (xr[q] - ref);
-          }
-#pragma unroll
-          for (int q = 0; q <= N; ++q) r += A.rx[q] * (xr[N + q] - ref);
-          acc[0] = (l + r) * xiw;
-        }
-#pragma unroll
-        for (int a = 1; a < N; ++a) {
-          const T ref = DIFF ? xr[N + a] : T(0);
-          T s2 = T(0);
-#pragma unroll
-          for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * (xr[N + q] - ref);
-          acc[a] = s2;
-        }
-        // y stencil
-        if (yvert) {
-          T ylv[N], yrv[N];
-#pragma unroll
-          for (int a = 0; a < N; ++a) { ylv[a] = T(0); yrv[a] = T(0); }
-          if (yl) {
-#pragma unroll
-            for (int q = 0; q <= N; ++q) {
-              T t[N];
-              vld<T, VS, N>(P + own + (q - N) * BX, t);
-#pragma unroll
-              for (int a = 0; a < N; ++a) ylv[a] += A.ly[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
-            }
-          }
-          if (yr) {
-#pragma unroll
-            for (int q = 0; q <= N; ++q) {
-              T t[N];
-              vld<T, VS, N>(P + own + q * BX, t);
-#pragma unroll
-              for (int a = 0; a < N; ++a) yrv[a] += A.ry[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
-            }
-          }
-#pragma unroll
-          for (int a = 0; a < N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
-        } else {
-          T ys[N];
-#pragma unroll
-          for (int a = 0; a < N; ++a) ys[a] = T(0);
-#pragma unroll
-          for (int q = 0; q <= N; ++q) {
-            T t[N];
-            vld<T, VS, N>(P + own + (q - yb) * BX, t);
-#pragma unroll
-            for (int a = 0; a < N; ++a) ys[a] += cyi[q] * (t[a] - (DIFF ? xr[N + a] : T(0)));
-          }
-#pragma unroll
-          for (int a = 0; a < N; ++a) acc[a] += ys[a];
-        }
-        // z stencil: own column over the staged planes of the layer
-        T zs[N];
-        T iw_z;
-        if constexpr (ZM == 0) {
-          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.rz, 0, zs);
-          iw_z = (ez > 0) ? A.iwv : A.iwb;
-#pragma unroll
-          for (int a = 0; a < N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
-        } else if constexpr (ZM == 1) {
-          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.cz[c], c, zs);
-          iw_z = A.iwa[c];
-        } else {
-          zsum<T, N, VS, PLANE, DIFF>(S0, own, A.lz, N, zs);
-          iw_z = A.iwb;
-#pragma unroll
-          for (int a = 0; a < N; ++a) zs[a] *= iw_z;
-        }
-        // update: a = -(M^-1 K p) (+ extras), v += dtv a, p_out = p + dtp v
         T vn[N], pn[N];
-#pragma unroll
-        for (int a = 0; a < N; ++a) {
-          T accum = -(acc[a] + zs[a]);
+        T iw_z;
+        if constexpr (ZM == 0) iw_z = (ez > 0) ? A.iwv : A.iwb;
+        else if constexpr (ZM == 1) iw_z = A.iwa[c];
+        else iw_z = A.iwb;
+        if constexpr (DIFF) {
+          float sm[N];
+          stencil_f32<N, ZM, VS, PLANE, BX>(A, S0, own, c, xr, xl, xiw, yvert, yl, yr, yiw, yb, cyi2, carry, iw_z,
+                                            sm);
           if (extras_layer) {
-            const T iw_x = (a == 0) ? xiw : A.iwa[a];
-            const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
-            accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
+#pragma unroll
+            for (int a = 0; a < N; ++a) {
+              const T iw_x = (a == 0) ? xiw : A.iwa[a];
+              const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
+              const T accum = node_extras<T, N>(A, ex * N + a, j, k, b, minv) - sm[a];
+              vn[a] = vcur[a] + A.dtv * accum;
+              pn[a] = xr[N + a] + A.dtp * vn[a];
+            }
+          } else {
+            // v += dtv (-M^-1 K p), p_out = p + dtp v
+            const float2 ndtv = f2(-A.dtv, -A.dtv), dtp = f2(A.dtp, A.dtp);
+#pragma unroll
+            for (int i = 0; i < N / 2; ++i) {
+              const float2 v2 = __ffma2_rn(ndtv, f2(sm[2 * i], sm[2 * i + 1]), f2(vcur[2 * i], vcur[2 * i + 1]));
+              const float2 p2 = __ffma2_rn(dtp, v2, f2(xr[N + 2 * i], xr[N + 2 * i + 1]));
+              vn[2 * i] = v2.x; vn[2 * i + 1] = v2.y;
+              pn[2 * i] = p2.x; pn[2 * i + 1] = p2.y;
+            }
+            if constexpr (N % 2 == 1) {
+              vn[N - 1] = vcur[N - 1] - A.dtv * sm[N - 1];
+              pn[N - 1] = xr[2 * N - 1] + A.dtp * vn[N - 1];
+            }
           }
-          vn[a] = vcur[a] + A.dtv * accum;
-          pn[a] = xr[N + a] + A.dtp * vn[a];
+        } else {
+          T acc[N];
+          // x stencil
+          {
+            T l = T(0), r = T(0);
+            if (xl) {
+#pragma unroll
+              for (int q = 0; q <= N; ++q) l += A.lx[q] * xr[q];
+            }
+#pragma unroll
+            for (int q = 0; q <= N; ++q) r += A.rx[q] * xr[N + q];
+            acc[0] = (l + r) * xiw;
+          }
+#pragma unroll
+          for (int a = 1; a < N; ++a) {
+            T s2 = T(0);
+#pragma unroll
+            for (int q = 0; q <= N; ++q) s2 += A.cx[a][q] * xr[N + q];
+            acc[a] = s2;
+          }
+          // y stencil
+          if (yvert) {
+            T ylv[N], yrv[N];
+#pragma unroll
+            for (int a = 0; a < N; ++a) { ylv[a] = T(0); yrv[a] = T(0); }
+            if (yl) {
+#pragma unroll
+              for (int q = 0; q <= N; ++q) {
+                T t[N];
+                vld<T, VS, N>(P + own + (q - N) * BX, t);
+#pragma unroll
+                for (int a = 0; a < N; ++a) ylv[a] += A.ly[q] * t[a];
+              }
+            }
+            if (yr) {
+#pragma unroll
+              for (int q = 0; q <= N; ++q) {
+                T t[N];
+                vld<T, VS, N>(P + own + q * BX, t);
+#pragma unroll
+                for (int a = 0; a < N; ++a) yrv[a] += A.ry[q] * t[a];
+              }
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a) acc[a] += (ylv[a] + yrv[a]) * yiw;
+          } else {
+#pragma unroll
+            for (int q = 0; q <= N; ++q) {
+              T t[N];
+              vld<T, VS, N>(P + own + (q - yb) * BX, t);
+#pragma unroll
+              for (int a = 0; a < N; ++a) acc[a] += cyi[q] * t[a];
+            }
+          }
+          // z stencil: own column over the staged planes of the layer
+          T zs[N];
+          if constexpr (ZM == 0) {
+            zsum<T, N, VS, PLANE>(S0, own, A.rz, zs);
+#pragma unroll
+            for (int a = 0; a < N; ++a) zs[a] = (carry[a] + zs[a]) * iw_z;
+          } else if constexpr (ZM == 1) {
+            zsum<T, N, VS, PLANE>(S0, own, A.cz[c], zs);
+          } else {
+            zsum<T, N, VS, PLANE>(S0, own, A.lz, zs);
+#pragma unroll
+            for (int a = 0; a < N; ++a) zs[a] *= iw_z;
+          }
+          // update: a = -(M^-1 K p) (+ extras), v += dtv a, p_out = p + dtp v
+#pragma unroll
+          for (int a = 0; a < N; ++a) {
+            T accum = -(acc[a] + zs[a]);
+            if (extras_layer) {
+              const T iw_x = (a == 0) ? xiw : A.iwa[a];
+              const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
+              accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
+            }
+            vn[a] = vcur[a] + A.dtv * accum;
+            pn[a] = xr[N + a] + A.dtp * vn[a];
+          }
         }
         vst<T, VG, N>(vv + (long long)k * A.pz + grow, vn);
         vst<T, VG, N>(pout + (long long)k * A.pz + grow, pn);
@@ -546,7 +728,8 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
       }
       // carry for the vertex plane (ez+1)*N
       if (pg == 0) {
-        zsum<T, N, VS, PLANE, DIFF>(S0, own, A.lz, N, carry);
+        if constexpr (DIFF) carry_f32<N, VS, PLANE>(A, S0, own, carry);
+        else zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
         if (xlast) {
           const T self = DIFF ? S0[N * PLANE + own + N] : T(0);
           carryX = T(0);
@@ -589,6 +772,21 @@ VolArgs<T, N> make_args(const VolSpec& s) {
     a.lz[p] = T(s.l[2][p]); a.rz[p] = T(s.r[2][p]);
     a.iwa[p] = T(s.iwa[p]);
     a.dI[p] = T(s.dI[p]);
+  }
+  for (int p = 0; p <= N; ++p) {
+    for (int k = 0; k < (N + 1) / 2; ++k) {
+      // taps past q = N (odd N) do not occur: the pairs end at q = N
+      a.cxq[p][k] = make_float2((float)s.c[0][p][2 * k], (float)s.c[0][p][2 * k + 1]);
+    }
+    for (int q = 0; q <= N; ++q) a.cz2[p][q] = make_float2((float)s.c[2][p][q], (float)s.c[2][p][q]);
+    a.ly2[p] = make_float2((float)s.l[1][p], (float)s.l[1][p]);
+    a.ry2[p] = make_float2((float)s.r[1][p], (float)s.r[1][p]);
+    a.lz2[p] = make_float2((float)s.l[2][p], (float)s.l[2][p]);
+    a.rz2[p] = make_float2((float)s.r[2][p], (float)s.r[2][p]);
+  }
+  for (int k = 0; k < (N + 1) / 2; ++k) {
+    a.lxq[k] = make_float2((float)s.l[0][2 * k], (float)s.l[0][2 * k + 1]);
+    a.rxq[k] = make_float2((float)s.r[0][2 * k], (float)s.r[0][2 * k + 1]);
   }
   a.iwv = T(s.iwv); a.iwb = T(s.iwb);
   a.minv_scale = s.minv_scale;
