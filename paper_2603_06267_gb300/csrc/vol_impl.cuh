@@ -203,7 +203,7 @@ __device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, 
 // Rare per-node terms times M^-1: PMUT forcing f (eq. f_i) on the z-min plane
 // and the interface residual of the interface element layer.
 template <typename T, int N>
-__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, double minv) {
+__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, T minv) {
   T acc = T(0);
   if (A.has_pmut && k == 0) {
     double f = 0.0;
@@ -214,7 +214,7 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
       const double* Bv = A.Bm + (long long)ent * A.M;
       for (int m = 0; m < A.M; ++m) f += qd[m] * Bv[m];
     }
-    acc += T(-A.kappa * f * minv);
+    acc += T(-A.kappa * f) * minv;
   }
   if (A.iface_k0 >= 0) {
     const int idx = k - A.iface_k0;
@@ -222,7 +222,7 @@ __device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int 
       const long long fs = (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
       T r = A.dI[idx] * face_gather<T, N>(A.Rb + fs, i, j, A.ne0, A.ne1);
       if (idx == (A.iface_top ? N : 0)) r += face_gather<T, N>(A.Ra + fs, i, j, A.ne0, A.ne1);
-      acc -= r * T(minv);
+      acc -= r * minv;
     }
   }
   return acc;
@@ -417,7 +417,9 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   constexpr bool VTMA = G::VTMA;
   constexpr bool DIFF = sizeof(T) == 4;    // FP32: difference form, packed arithmetic
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NW = G::NT / 32;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
+  int* cnt = reinterpret_cast<int*>(bar + 4);   // warps done with each stage
 
   const int tx = threadIdx.x, ty = threadIdx.y, pg = threadIdx.z;
   const int tid = (pg * TYR + ty) * TXE + tx;
@@ -461,6 +463,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
   }
   const T iw_y = yvert ? yiw : A.iwa[yb];
   const bool xl = ex > 0;
+  const T mscale = T(A.minv_scale);        // 8 / (hx hy hz): M^-1 = mscale / (w_a w_b w_c)
   const T xiw = xl ? A.iwv : A.iwb;        // vertex node ex*N (an element always lies to its right)
 
   const int r0 = rt + N;                   // staged row of lattice row j
@@ -497,7 +500,10 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
 
   // pipeline set-up
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&bar[s], 1);
+      cnt[s] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap)) : "memory");
     if constexpr (VTMA) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap_v)) : "memory");
@@ -561,7 +567,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
 #pragma unroll
             for (int a = 0; a < N; ++a) {
               const T iw_x = (a == 0) ? xiw : A.iwa[a];
-              const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
+              const T minv = mscale * iw_x * iw_y * iw_z;
               const T accum = node_extras<T, N>(A, ex * N + a, j, k, b, minv) - sm[a];
               vn[a] = vcur[a] + A.dtv * accum;
               pn[a] = xr[N + a] + A.dtp * vn[a];
@@ -654,7 +660,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
             T accum = -(acc[a] + zs[a]);
             if (extras_layer) {
               const T iw_x = (a == 0) ? xiw : A.iwa[a];
-              const double minv = A.minv_scale * (double)iw_x * (double)iw_y * (double)iw_z;
+              const T minv = mscale * iw_x * iw_y * iw_z;
               accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
             }
             vn[a] = vcur[a] + A.dtv * accum;
@@ -709,7 +715,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         }
         T accum = -(x + y + z);
         if (extras_layer) {
-          const double minv = A.minv_scale * (double)A.iwb * (double)iw_y * (double)iw_z;
+          const T minv = mscale * A.iwb * iw_y * iw_z;
           accum += node_extras<T, N>(A, ex * N + N, j, k, b, minv);
         }
         T* vp = vv + (long long)k * A.pz + grow + N;
@@ -738,10 +744,20 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         }
       }
     }
-    __syncthreads();   // every thread is done with stage s
-    if (tid == 0 && ez + STAGES < ez1) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(ez + STAGES, s);
+    // release stage s: the last warp to finish reading it issues its next
+    // load, so warps with more work in this layer (vertex rows, the z carry)
+    // hold up the others only when the ring runs dry
+    __syncwarp();
+    if ((tid & 31) == 0) {
+      __threadfence_block();
+      if (atomicAdd(&cnt[s], 1) == NW - 1) {
+        cnt[s] = 0;
+        __threadfence_block();
+        if (ez + STAGES < ez1) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(ez + STAGES, s);
+        }
+      }
     }
   }
 }
