@@ -228,6 +228,8 @@ struct dgsem_ctx {
   int* d_step = nullptr;                      // step counter of the current run
   // CUDA graph of a block of steps, replayed by dgsem_run
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;      // second branch of a captured step
+  cudaEvent_t fork_ev[2] = {nullptr, nullptr};
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   long long graph_launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
@@ -616,10 +618,22 @@ void collect_timings(dgsem_ctx* c) {
   c->ev_used.clear();
 }
 
-// One time step (or the initial half step when init is true), all launches on s.
+// One time step (or the initial half step when init is true).  With a side
+// stream (graph capture of a two-box mesh) the PMUT/receiver launch runs on
+// the side stream, concurrently with the interface launch on s; both volume
+// launches follow on s (the primary needs q'' of this step, both need the
+// interface residual).  Running the two volume launches concurrently as well
+// was measured slower: their CTAs compete for shared memory and bandwidth.
+// Without a side stream everything runs on s in that order.
 template <typename T>
 int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs, long long dks, int n_local,
-                int R, double* traces, long long tbs, long long trs, bool init) {
+                int R, double* traces, long long tbs, long long trs, bool init, cudaStream_t side = nullptr) {
+  const bool fork = side && c->nd == 2 && c->has_iface && !init;
+  cudaStream_t sp = fork ? side : s;       // stream of the PMUT launch
+  if (fork) {
+    CUDA_TRY(cudaEventRecord(c->fork_ev[0], s));
+    CUDA_TRY(cudaStreamWaitEvent(side, c->fork_ev[0], 0));
+  }
   if (!init && (c->K > 0 || R > 0)) {
     PmutArgs<T> a;
     std::memset(&a, 0, sizeof(a));
@@ -643,9 +657,10 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     a.pc0 = static_cast<const T*>(c->Y[0]); a.pc1 = c->nd > 1 ? static_cast<const T*>(c->Y[1]) : nullptr;
     a.bs0 = c->box[0].bstride; a.bs1 = c->nd > 1 ? c->box[1].bstride : 0;
     a.traces = traces; a.tbs = tbs; a.trs = trs;
-    LaunchTimer lt(c, s, DGSEM_K_PMUT_RECV);
-    CUDA_TRY(launch_pmut_recv<T>(a, s));
+    LaunchTimer lt(c, sp, DGSEM_K_PMUT_RECV);
+    CUDA_TRY(launch_pmut_recv<T>(a, sp));
   }
+  if (fork) CUDA_TRY(cudaEventRecord(c->fork_ev[1], side));
   // init: p_in = X (p^0), p_out = Y (p^1); step: p_in = Y (p^{n+1}), p_out = X (p^{n+2})
   void* pin[2]; void* pout[2];
   for (int d = 0; d < c->nd; ++d) {
@@ -659,6 +674,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     LaunchTimer lt(c, s, DGSEM_K_IFACE);
     CUDA_TRY(launch_iface<T>(a, c->batch, s));
   }
+  if (fork) CUDA_TRY(cudaStreamWaitEvent(s, c->fork_ev[1], 0));
   for (int d = 0; d < c->nd; ++d) {
     VolSpec v = c->vspec[d];
     v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
@@ -870,6 +886,14 @@ int run_finish(dgsem_ctx* c, int nsteps, const RunIO& io, cudaStream_t s) {
   return DGSEM_OK;
 }
 
+// Stream and events of the second branch of a captured step.
+int ensure_side(dgsem_ctx* c) {
+  if (!c->side_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : c->fork_ev)
+    if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  return DGSEM_OK;
+}
+
 template <typename T>
 int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
   RunIO io;
@@ -889,12 +913,14 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     if (!c->graph || c->graph_key != kb) {
       if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
       if (!c->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      if ((rc = ensure_side(c))) return rc;
       long long before[DGSEM_K_COUNT];
       for (int k = 0; k < DGSEM_K_COUNT; ++k) before[k] = c->launches[k];
       CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
       int crc = DGSEM_OK;
       for (int n = 0; n < G && crc == DGSEM_OK; ++n)
-        crc = launch_step<T>(c, c->cap_stream, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false);
+        crc = launch_step<T>(c, c->cap_stream, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false,
+                             c->side_stream);
       cudaGraph_t g = nullptr;
       cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
       if (crc) { if (g) cudaGraphDestroy(g); return crc; }
@@ -947,8 +973,11 @@ int run_multi_impl(int n, dgsem_ctx* const* ctxs, int nsteps, const double* cons
       cudaError_t ce = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
       if (ce != cudaSuccess) { cleanup(); return fail(DGSEM_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(ce)); }
     }
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
       if (!ctxs[i]->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&ctxs[i]->cap_stream, cudaStreamNonBlocking));
+      int rc = ensure_side(ctxs[i]);
+      if (rc) { cleanup(); return rc; }
+    }
     std::vector<std::array<long long, DGSEM_K_COUNT>> before(n), per(n);
     for (int i = 0; i < n; ++i)
       for (int k = 0; k < DGSEM_K_COUNT; ++k) before[i][k] = ctxs[i]->launches[k];
@@ -961,7 +990,7 @@ int run_multi_impl(int n, dgsem_ctx* const* ctxs, int nsteps, const double* cons
       cudaStreamWaitEvent(c->cap_stream, ev[n], 0);
       for (int st = 0; st < G && crc == DGSEM_OK; ++st)
         crc = launch_step<T>(c, c->cap_stream, io[i].d_drive, io[i].dbs, io[i].dks, 0, io[i].R, io[i].d_tr, io[i].tbs,
-                             io[i].trs, false);
+                             io[i].trs, false, c->side_stream);
       cudaEventRecord(ev[i], c->cap_stream);
       cudaStreamWaitEvent(main, ev[i], 0);
     }
@@ -1529,6 +1558,9 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_err);
   dfree(c->d_step);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  for (cudaEvent_t e : c->fork_ev)
+    if (e) cudaEventDestroy(e);
   delete c->basis[0];
   delete c->basis[1];
   delete c;

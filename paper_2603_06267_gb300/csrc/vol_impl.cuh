@@ -125,17 +125,27 @@ constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
 // groups.  Orders 4 and 6 (the workloads' primary and secondary boxes) have
 // several shapes the autotuner chooses from; variant 0 is the default.
 // ---------------------------------------------------------------------------
-template <int A, int B, int C> struct Shape { static constexpr int TXE = A, TYE = B, PG = C; };
+// ZR: each thread copies its column of the staged element layer into
+// registers once per layer, and the z stencils of its planes and the z carry
+// read that copy instead of shared memory (FP32 only); MINB: CTAs per SM
+template <int A, int B, int C, int Z = 0, int M = 1> struct Shape {
+  static constexpr int TXE = A, TYE = B, PG = C, MINB = M;
+  static constexpr bool ZR = Z != 0;
+};
 template <typename T, int N, int V> struct TileShape {
   using S = Shape<(N <= 4) ? 32 : 16,
                   (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1))), 1>;
 };
-template <typename T, int N> struct NumShapes { static constexpr int value = (N == 4 || N == 6) ? 4 : 1; };
+template <typename T, int N> struct NumShapes {
+  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? 6 : 4) : 1;
+};
 // FP32 N=4: 512 threads in each, FP64 N=4: 256 / 256 / 128 / 512
 template <> struct TileShape<float, 4, 0> { using S = Shape<32, 2, 2>; };
 template <> struct TileShape<float, 4, 1> { using S = Shape<32, 4, 1>; };
 template <> struct TileShape<float, 4, 2> { using S = Shape<16, 4, 2>; };
 template <> struct TileShape<float, 4, 3> { using S = Shape<32, 2, 1>; };
+template <> struct TileShape<float, 4, 4> { using S = Shape<32, 4, 1, 1>; };
+template <> struct TileShape<float, 4, 5> { using S = Shape<32, 2, 1, 1, 2>; };
 template <> struct TileShape<double, 4, 0> { using S = Shape<32, 2, 1>; };
 template <> struct TileShape<double, 4, 1> { using S = Shape<16, 4, 1>; };
 template <> struct TileShape<double, 4, 2> { using S = Shape<32, 1, 1>; };
@@ -145,6 +155,8 @@ template <> struct TileShape<float, 6, 0> { using S = Shape<16, 2, 2>; };
 template <> struct TileShape<float, 6, 1> { using S = Shape<16, 2, 3>; };
 template <> struct TileShape<float, 6, 2> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<float, 6, 3> { using S = Shape<32, 1, 2>; };
+template <> struct TileShape<float, 6, 4> { using S = Shape<16, 2, 2, 1>; };
+template <> struct TileShape<float, 6, 5> { using S = Shape<16, 2, 1, 1>; };
 template <> struct TileShape<double, 6, 0> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<double, 6, 1> { using S = Shape<16, 1, 1>; };
 template <> struct TileShape<double, 6, 2> { using S = Shape<8, 4, 1>; };
@@ -281,46 +293,38 @@ __device__ __forceinline__ float row_dot(const float2* cq2, float clast, const f
   return r;
 }
 
-// M^-1 K p of the N owned nodes of one staged plane (FP32, difference form).
-// ZM: 0 vertex plane (carry = lower layer's part), 1 interior plane c,
-// 2 top boundary plane of the box.  xr: staged row (left element, own
-// element, next vertex); cyi2: this row's interior y coefficients.
-template <int N, int ZM, int VS, int PLANE, int BX>
-__device__ __forceinline__ void stencil_f32(const VolArgs<float, N>& A, const float* __restrict__ S0, int own,
-                                            int c, const float* xr, bool xl, float xiw, bool yvert, bool yl,
-                                            bool yr, float yiw, int yb, const float2* cyi2, const float* carry,
-                                            float iw_z, float* out) {
+// x part of M^-1 K p of the N owned nodes: xr holds the staged row (left
+// element, own element, next vertex); differences to the element's first node
+template <int N>
+__device__ __forceinline__ void xstencil_f32(const VolArgs<float, N>& A, const float* xr, bool xl, float xiw,
+                                             float* acc) {
   constexpr int K2 = (N + 1) / 2;
-  constexpr int NP = N / 2;
-  const float* P = S0 + c * PLANE;
-  const float* self = xr + N;
-  // x: differences to the element's first node
   const float ref = xr[N];
   const float2 ref2 = f2(ref, ref);
   float2 d2[K2];
 #pragma unroll
   for (int k = 0; k < K2; ++k) d2[k] = sub2(f2(xr[N + 2 * k], xr[N + 2 * k + 1]), ref2);
   const float dlast = (N % 2 == 0) ? xr[2 * N] - ref : 0.f;
-  float acc[N];
-  {
-    float r = row_dot<N>(A.rxq, A.rx[N], d2, dlast);
-    if (xl) {
-      float2 dl[K2];
+  float r = row_dot<N>(A.rxq, A.rx[N], d2, dlast);
+  if (xl) {
+    // for even N the pairs cover q = 0..N-1; the tap q = N is the node itself
+    float2 sl = __fmul2_rn(A.lxq[0], sub2(f2(xr[0], xr[1]), ref2));
 #pragma unroll
-      for (int k = 0; k < K2; ++k) dl[k] = sub2(f2(xr[2 * k], xr[2 * k + 1]), ref2);
-      // for even N the pairs cover q = 0..N-1; the tap q = N is the node itself
-      float2 sl = __fmul2_rn(A.lxq[0], dl[0]);
-#pragma unroll
-      for (int k = 1; k < K2; ++k) sl = __ffma2_rn(A.lxq[k], dl[k], sl);
-      r += sl.x + sl.y;
-    }
-    acc[0] = r * xiw;
+    for (int k = 1; k < K2; ++k) sl = __ffma2_rn(A.lxq[k], sub2(f2(xr[2 * k], xr[2 * k + 1]), ref2), sl);
+    r += sl.x + sl.y;
   }
+  acc[0] = r * xiw;
 #pragma unroll
   for (int a = 1; a < N; ++a) acc[a] = row_dot<N>(A.cxq[a], A.cx[a][N], d2, dlast);
-  // y: differences to the node itself
-  float2 ys[NP > 0 ? NP : 1];
-  float ysT = 0.f;
+}
+
+// y part: differences to the node itself (self = the owned run of this plane)
+template <int N, int VS, int BX>
+__device__ __forceinline__ void ystencil_f32(const VolArgs<float, N>& A, const float* __restrict__ P, int own,
+                                             const float* self, bool yvert, bool yl, bool yr, float yiw, int yb,
+                                             const float2* cyi2, float2* ys, float& ysT) {
+  constexpr int NP = N / 2;
+  ysT = 0.f;
 #pragma unroll
   for (int i = 0; i < NP; ++i) ys[i] = f2(0.f, 0.f);
   if (yvert) {
@@ -340,31 +344,84 @@ __device__ __forceinline__ void stencil_f32(const VolArgs<float, N>& A, const fl
 #pragma unroll
     for (int q = 0; q <= N; ++q) run_term<N, VS>(P + own + (q - yb) * BX, cyi2[q], self, ys, ysT);
   }
-  // z: differences to the node itself, over the staged planes of the layer
-  float2 zs[NP > 0 ? NP : 1];
-  float zsT = 0.f;
+}
+
+// z part from the staged planes (runtime plane c).  ZM: 0 vertex plane
+// (carry = lower layer's part), 1 interior plane, 2 top boundary plane.
+template <int N, int ZM, int VS, int PLANE>
+__device__ __forceinline__ void zstencil_smem_f32(const VolArgs<float, N>& A, const float* __restrict__ S0, int own,
+                                                  int c, const float* self, const float* carry, float iw_z,
+                                                  float2* zs, float& zsT) {
+  constexpr int NP = N / 2;
+  zsT = 0.f;
 #pragma unroll
   for (int i = 0; i < NP; ++i) zs[i] = f2(0.f, 0.f);
   if constexpr (ZM == 0) {
 #pragma unroll
     for (int q = 1; q <= N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.rz2[q], self, zs, zsT);
-    const float2 w2 = f2(iw_z, iw_z);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) zs[i] = __fmul2_rn(__fadd2_rn(f2(carry[2 * i], carry[2 * i + 1]), zs[i]), w2);
-    if constexpr (N % 2 == 1) zsT = (carry[N - 1] + zsT) * iw_z;
   } else if constexpr (ZM == 1) {
 #pragma unroll
     for (int q = 0; q <= N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.cz2[c][q], self, zs, zsT);
   } else {
 #pragma unroll
     for (int q = 0; q < N; ++q) run_term<N, VS>(S0 + q * PLANE + own, A.lz2[q], self, zs, zsT);
+  }
+  if constexpr (ZM != 1) {
     const float2 w2 = f2(iw_z, iw_z);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) zs[i] = __fmul2_rn(zs[i], w2);
-    zsT *= iw_z;
+    for (int i = 0; i < NP; ++i) {
+      const float2 t = (ZM == 0) ? __fadd2_rn(f2(carry[2 * i], carry[2 * i + 1]), zs[i]) : zs[i];
+      zs[i] = __fmul2_rn(t, w2);
+    }
+    if constexpr (N % 2 == 1) zsT = ((ZM == 0 ? carry[N - 1] : 0.f) + zsT) * iw_z;
   }
+}
+
+// acc += c2 * (col - self) over the owned run, all in registers
+template <int N>
+__device__ __forceinline__ void reg_term(const float* col, float2 c2, const float* self, float2* acc, float& accT) {
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
+  for (int i = 0; i < N / 2; ++i)
+    acc[i] = __ffma2_rn(c2, sub2(f2(col[2 * i], col[2 * i + 1]), f2(self[2 * i], self[2 * i + 1])), acc[i]);
+  if constexpr (N % 2 == 1) accT = fmaf(c2.x, col[N - 1] - self[N - 1], accT);
+}
+
+// z part from the thread's column of the layer in registers, runtime plane c
+// (the term q = c is zero)
+template <int N, int ZM>
+__device__ __forceinline__ void zstencil_col_f32(const VolArgs<float, N>& A, const float (*col)[N], int c,
+                                                 const float* self, const float* carry, float iw_z, float2* zs,
+                                                 float& zsT) {
+  constexpr int NP = N / 2;
+  zsT = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) zs[i] = f2(0.f, 0.f);
+  if constexpr (ZM == 0) {
+#pragma unroll
+    for (int q = 1; q <= N; ++q) reg_term<N>(col[q], A.rz2[q], self, zs, zsT);
+  } else if constexpr (ZM == 1) {
+#pragma unroll
+    for (int q = 0; q <= N; ++q) reg_term<N>(col[q], A.cz2[c][q], self, zs, zsT);
+  } else {
+#pragma unroll
+    for (int q = 0; q < N; ++q) reg_term<N>(col[q], A.lz2[q], self, zs, zsT);
+  }
+  if constexpr (ZM != 1) {
+    const float2 w2 = f2(iw_z, iw_z);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const float2 t = (ZM == 0) ? __fadd2_rn(f2(carry[2 * i], carry[2 * i + 1]), zs[i]) : zs[i];
+      zs[i] = __fmul2_rn(t, w2);
+    }
+    if constexpr (N % 2 == 1) zsT = ((ZM == 0 ? carry[N - 1] : 0.f) + zsT) * iw_z;
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void combine_f32(const float* acc, const float2* ys, float ysT, const float2* zs, float zsT,
+                                            float* out) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) {
     const float2 sm = __fadd2_rn(__fadd2_rn(f2(acc[2 * i], acc[2 * i + 1]), ys[i]), zs[i]);
     out[2 * i] = sm.x;
     out[2 * i + 1] = sm.y;
@@ -391,6 +448,21 @@ __device__ __forceinline__ void carry_f32(const VolArgs<float, N>& A, const floa
   if constexpr (N % 2 == 1) carry[N - 1] = cT;
 }
 
+// the same from the column in registers
+template <int N>
+__device__ __forceinline__ void carry_reg_f32(const VolArgs<float, N>& A, const float (*col)[N], float* carry) {
+  constexpr int NP = N / 2;
+  float2 cs[NP > 0 ? NP : 1];
+  float cT = 0.f;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) cs[i] = f2(0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < N; ++q) reg_term<N>(col[q], A.lz2[q], col[N], cs, cT);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) { carry[2 * i] = cs[i].x; carry[2 * i + 1] = cs[i].y; }
+  if constexpr (N % 2 == 1) carry[N - 1] = cT;
+}
+
 // Row of the tile handled by thread row ty: the TYE vertex rows (element
 // boundaries, two-element y stencil) come first so that they fill their own
 // warps and the y stencil does not diverge inside a warp.
@@ -408,9 +480,10 @@ __device__ __forceinline__ int tile_row(int ty) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE, int PG>
-__global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
+template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB>
+__global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
   using G = Geo<T, N, TXE, TYE, PG>;
+  static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
   constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
   constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
   constexpr int STAGES = G::STAGES;
@@ -534,8 +607,46 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
       return;
     }
     if (active) {
+      // planes carrying PMUT forcing (z = 0) or interface terms
+      auto plane_extras = [&](int k) {
+        return (A.has_pmut && k == 0) || (A.iface_k0 >= 0 && k >= A.iface_k0 && k <= A.iface_k0 + N);
+      };
       const bool extras_layer = (A.has_pmut && ez == 0) ||
                                 (A.iface_k0 >= 0 && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
+      // ZR: the thread's column of every staged plane of the layer, in
+      // registers (the z stencil of all planes and the carry read it)
+      T col[ZR ? N + 1 : 1][N];
+      if constexpr (ZR) {
+#pragma unroll
+        for (int q = 0; q <= N; ++q) vld<T, VS, N>(S0 + q * PLANE + own, col[q]);
+      }
+      // FP32 update of the N owned nodes of plane k from sm = M^-1 K p:
+      // a = -sm (+ PMUT / interface terms), v += dtv a, p_out = p + dtp v
+      auto commit_f32 = [&](int k, const T* vcur, const T* self, const float* sm, T iw_z, T* vn, T* pn) {
+        if (extras_layer && plane_extras(k)) {
+#pragma unroll
+          for (int a = 0; a < N; ++a) {
+            const T iw_x = (a == 0) ? xiw : A.iwa[a];
+            const T minv = mscale * iw_x * iw_y * iw_z;
+            const T accum = node_extras<T, N>(A, ex * N + a, j, k, b, minv) - sm[a];
+            vn[a] = vcur[a] + A.dtv * accum;
+            pn[a] = self[a] + A.dtp * vn[a];
+          }
+        } else {
+          const float2 ndtv = f2(-A.dtv, -A.dtv), dtp = f2(A.dtp, A.dtp);
+#pragma unroll
+          for (int i = 0; i < N / 2; ++i) {
+            const float2 v2 = __ffma2_rn(ndtv, f2(sm[2 * i], sm[2 * i + 1]), f2(vcur[2 * i], vcur[2 * i + 1]));
+            const float2 p2 = __ffma2_rn(dtp, v2, f2(self[2 * i], self[2 * i + 1]));
+            vn[2 * i] = v2.x; vn[2 * i + 1] = v2.y;
+            pn[2 * i] = p2.x; pn[2 * i + 1] = p2.y;
+          }
+          if constexpr (N % 2 == 1) {
+            vn[N - 1] = vcur[N - 1] - A.dtv * sm[N - 1];
+            pn[N - 1] = self[N - 1] + A.dtp * vn[N - 1];
+          }
+        }
+      };
       // one plane of the layer for the N owned nodes; ZM selects the z rows:
       // 0 vertex plane (carried lower part + own layer), 1 interior plane c,
       // 2 top boundary plane of the box
@@ -560,33 +671,15 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
         else if constexpr (ZM == 1) iw_z = A.iwa[c];
         else iw_z = A.iwb;
         if constexpr (DIFF) {
-          float sm[N];
-          stencil_f32<N, ZM, VS, PLANE, BX>(A, S0, own, c, xr, xl, xiw, yvert, yl, yr, yiw, yb, cyi2, carry, iw_z,
-                                            sm);
-          if (extras_layer) {
-#pragma unroll
-            for (int a = 0; a < N; ++a) {
-              const T iw_x = (a == 0) ? xiw : A.iwa[a];
-              const T minv = mscale * iw_x * iw_y * iw_z;
-              const T accum = node_extras<T, N>(A, ex * N + a, j, k, b, minv) - sm[a];
-              vn[a] = vcur[a] + A.dtv * accum;
-              pn[a] = xr[N + a] + A.dtp * vn[a];
-            }
-          } else {
-            // v += dtv (-M^-1 K p), p_out = p + dtp v
-            const float2 ndtv = f2(-A.dtv, -A.dtv), dtp = f2(A.dtp, A.dtp);
-#pragma unroll
-            for (int i = 0; i < N / 2; ++i) {
-              const float2 v2 = __ffma2_rn(ndtv, f2(sm[2 * i], sm[2 * i + 1]), f2(vcur[2 * i], vcur[2 * i + 1]));
-              const float2 p2 = __ffma2_rn(dtp, v2, f2(xr[N + 2 * i], xr[N + 2 * i + 1]));
-              vn[2 * i] = v2.x; vn[2 * i + 1] = v2.y;
-              pn[2 * i] = p2.x; pn[2 * i + 1] = p2.y;
-            }
-            if constexpr (N % 2 == 1) {
-              vn[N - 1] = vcur[N - 1] - A.dtv * sm[N - 1];
-              pn[N - 1] = xr[2 * N - 1] + A.dtp * vn[N - 1];
-            }
-          }
+          float acc[N], sm[N];
+          float2 ys[N / 2 > 0 ? N / 2 : 1], zs[N / 2 > 0 ? N / 2 : 1];
+          float ysT, zsT;
+          xstencil_f32<N>(A, xr, xl, xiw, acc);
+          ystencil_f32<N, VS, BX>(A, P, own, xr + N, yvert, yl, yr, yiw, yb, cyi2, ys, ysT);
+          if constexpr (ZR) zstencil_col_f32<N, ZM>(A, col, c, xr + N, carry, iw_z, zs, zsT);
+          else zstencil_smem_f32<N, ZM, VS, PLANE>(A, S0, own, c, xr + N, carry, iw_z, zs, zsT);
+          combine_f32<N>(acc, ys, ysT, zs, zsT, sm);
+          commit_f32(k, vcur, xr + N, sm, iw_z, vn, pn);
         } else {
           T acc[N];
           // x stencil
@@ -658,7 +751,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             T accum = -(acc[a] + zs[a]);
-            if (extras_layer) {
+            if (extras_layer && plane_extras(k)) {
               const T iw_x = (a == 0) ? xiw : A.iwa[a];
               const T minv = mscale * iw_x * iw_y * iw_z;
               accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
@@ -714,7 +807,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
           z *= iw_z;
         }
         T accum = -(x + y + z);
-        if (extras_layer) {
+        if (extras_layer && plane_extras(k)) {
           const T minv = mscale * A.iwb * iw_y * iw_z;
           accum += node_extras<T, N>(A, ex * N + N, j, k, b, minv);
         }
@@ -734,7 +827,8 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, 1) vol_kernel(const __grid
       }
       // carry for the vertex plane (ez+1)*N
       if (pg == 0) {
-        if constexpr (DIFF) carry_f32<N, VS, PLANE>(A, S0, own, carry);
+        if constexpr (ZR) carry_reg_f32<N>(A, col, carry);
+        else if constexpr (DIFF) carry_f32<N, VS, PLANE>(A, S0, own, carry);
         else zsum<T, N, VS, PLANE>(S0, own, A.lz, carry);
         if (xlast) {
           const T self = DIFF ? S0[N * PLANE + own + N] : T(0);
@@ -833,7 +927,7 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE, PG>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
@@ -850,8 +944,11 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
       case 1: return launch_v<T, N, 1>(s, batch, st);
       case 2: return launch_v<T, N, 2>(s, batch, st);
       case 3: return launch_v<T, N, 3>(s, batch, st);
-      default: return cudaErrorInvalidValue;
+      case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4>(s, batch, st); break;
+      case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5>(s, batch, st); break;
+      default: break;
     }
+    return cudaErrorInvalidValue;
   } else {
     if (s.tile != 0) return cudaErrorInvalidValue;
     return launch_v<T, N, 0>(s, batch, st);
@@ -880,7 +977,9 @@ int box_n(int tile, unsigned box[3], unsigned vbox[3]) {
       case 0: box_v<T, N, 0>(box, vbox); break;
       case 1: box_v<T, N, 1>(box, vbox); break;
       case 2: box_v<T, N, 2>(box, vbox); break;
-      default: box_v<T, N, 3>(box, vbox); break;
+      case 3: box_v<T, N, 3>(box, vbox); break;
+      case 4: if constexpr (NumShapes<T, N>::value > 4) box_v<T, N, 4>(box, vbox); break;
+      default: if constexpr (NumShapes<T, N>::value > 5) box_v<T, N, 5>(box, vbox); break;
     }
   } else {
     box_v<T, N, 0>(box, vbox);

@@ -76,6 +76,30 @@ def test_two_domain_pmut_array(prec, tol):
     assert rel_l2(pg, po) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_two_domain_pmut_every_tile_variant(prec, tol):
+    """PMUT forcing and interface terms (the volume kernel's extras planes)
+    under every tile variant of each box, the other box at variant 0."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=8, nz_p=2, nx_s=4, nz_s=3, n_pmut_side=2, nsteps=160)
+    P = oracle_problem(w)
+    dt = P.stable_dt()
+    drive = w.drive(dt, w.nsteps, 1)
+    to = P.run(nsteps=w.nsteps, dt=dt, drive=drive)
+    po = P.final_state["p"].T
+    sol = gpu_solver(w)
+    for box in range(2):
+        for v in range(dgsem.dgsem_num_tiles(sol.ctx, prec, box)):
+            tiles = [0, 0]
+            tiles[box] = v
+            dgsem.dgsem_set_tiles(sol.ctx, prec, tiles)
+            tg = sol.run(drive=drive, precision=prec)
+            pg = dgsem.dgsem_get_pressure(sol.ctx, 1, sol.ndof)
+            assert rel_l2(tg, to) < tol, (box, v, rel_l2(tg, to))
+            assert rel_l2(pg, po) < tol, (box, v, rel_l2(pg, po))
+    sol.close()
+
+
 def test_two_domain_conforming_interface_fp64():
     """r = 1 (conforming faces), same order on both sides."""
     w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=4, nz_s=2, n_pmut_side=2, nsteps=120, order_s=4)
