@@ -190,6 +190,7 @@ struct dgsem_ctx {
   int q = 0, nsub = 0;
   int ncf = 0, nff = 0;
   double gamma = 0.0;
+  int max_ff = 0;                          // most fine faces on one coarse face
   int* d_cf_col = nullptr; int* d_cf_ptr = nullptr; int* d_ff_col = nullptr;
   int* d_ff_sx = nullptr; int* d_ff_sy = nullptr;
   void* d_tab[2] = {nullptr, nullptr};   // [fp64, fp32] packed Lp | Ls | Wq | dp | ds
@@ -523,6 +524,8 @@ int build_interface(dgsem_ctx* c, const dgsem_mesh_desc* desc) {
   }
   c->ncf = (int)h_cf_col.size();
   c->nff = (int)h_ff_col.size();
+  c->max_ff = 0;
+  for (size_t i = 0; i + 1 < h_cf_ptr.size(); ++i) c->max_ff = std::max(c->max_ff, h_cf_ptr[i + 1] - h_cf_ptr[i]);
   c->nsub = (int)offs.size();
   const int np1 = P.N + 1, ns1 = S.N + 1;
   std::vector<double> Lp(q * np1), Ls(offs.size() * q * ns1), Wq(q * q), dp(np1), ds(ns1);
@@ -575,6 +578,7 @@ IfaceArgs<T> iface_args(const dgsem_ctx* c) {
   a.Np = P.N; a.Ns = S.N; a.kp0 = (P.ne[2] - 1) * P.N;
   a.npx = P.ne[0]; a.nsx = S.ne[0];
   a.ncf = c->ncf;
+  a.max_ff = c->max_ff;
   a.cf_col = c->d_cf_col; a.cf_ptr = c->d_cf_ptr; a.ff_col = c->d_ff_col;
   a.ff_sx = c->d_ff_sx; a.ff_sy = c->d_ff_sy;
   a.q = c->q;

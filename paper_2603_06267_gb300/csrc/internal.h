@@ -83,6 +83,7 @@ struct IfaceArgs {
   int Np, Ns, kp0;                 // orders; first plane of the primary top layer
   int npx, nsx;                    // element columns per x row (primary, secondary)
   int ncf;                         // listed coarse faces
+  int max_ff;                      // most fine faces on one coarse face
   const int* cf_col;               // [ncf] coarse face column mx + nsx*my
   const int* cf_ptr;               // [ncf+1] fine faces of each coarse face
   const int* ff_col;               // fine face column ex + npx*ey

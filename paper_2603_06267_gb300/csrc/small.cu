@@ -202,6 +202,188 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
 }
 
 // ---------------------------------------------------------------------------
+// The same interface terms, organised for the production orders (compile-time
+// NP1 = Np+1, NS1 = Ns+1, Q Gauss points, at most FS fine faces per coarse
+// face).  One CTA takes one coarse face for BPC batch members at once.  A
+// worker thread per (member, fine face, Gauss abscissa qx) contracts the
+// face traces along x at its abscissa, then walks the Gauss rows qy: it
+// interpolates along y, forms the jump / average / penalty weights at
+// (qx, qy) and accumulates their projection along y onto the face GLL rows
+// -- all in registers, with the 1D tables read from shared memory as
+// broadcasts.  A last phase projects along x and writes the fine residuals
+// and the coarse residual (summed over the fine faces in list order, so the
+// result is deterministic).  Same arithmetic as iface_kernel, reordered.
+// ---------------------------------------------------------------------------
+constexpr int RB_THREADS = 256;
+
+template <typename T, int NP1, int NS1, int Q, int FS, int BPC>
+__global__ void __launch_bounds__(RB_THREADS) iface_rows_kernel(const __grid_constant__ IfaceArgs<T> A, int batch) {
+  static_assert(BPC * FS * Q <= RB_THREADS, "one worker per (member, fine face, qx)");
+  __shared__ T sLp[Q][NP1];
+  __shared__ T sLsx[FS][Q][NS1], sLsy[FS][Q][NS1];
+  __shared__ T sW[Q * Q];
+  __shared__ T TF[BPC][FS][2][NP1 * NP1];      // fine traces: value, normal derivative
+  __shared__ T TC[BPC][2][NS1 * NS1];          // coarse traces
+  __shared__ T PF[BPC][FS][2][NP1][Q];         // y-projected fine weights (alpha, beta+) at (row, qx)
+  __shared__ T PC[BPC][FS][2][NS1][Q];         // y-projected coarse weights (alpha, beta-)
+  constexpr int NF2 = NP1 * NP1, NS2 = NS1 * NS1;
+  const int cf = blockIdx.x;
+  const int tid = threadIdx.x;
+  const int b0 = blockIdx.y * BPC;
+  const int nb = min(BPC, batch - b0);
+  const int ccol = A.cf_col[cf];
+  const int mx = ccol % A.nsx, my = ccol / A.nsx;
+  const int f0 = A.cf_ptr[cf];
+  const int nf = A.cf_ptr[cf + 1] - f0;
+  const int Np = NP1 - 1, Ns = NS1 - 1;
+  // tables
+  for (int t = tid; t < Q * NP1; t += RB_THREADS) sLp[t / NP1][t % NP1] = A.Lp[t];
+  for (int t = tid; t < nf * Q * NS1; t += RB_THREADS) {
+    const int f = t / (Q * NS1), r = t - f * (Q * NS1);
+    sLsx[f][r / NS1][r % NS1] = A.Ls[(long long)A.ff_sx[f0 + f] * Q * NS1 + r];
+    sLsy[f][r / NS1][r % NS1] = A.Ls[(long long)A.ff_sy[f0 + f] * Q * NS1 + r];
+  }
+  for (int t = tid; t < Q * Q; t += RB_THREADS) sW[t] = A.Wq[t];
+  // traces: coarse face (secondary bottom layer), then the fine faces (primary top layer)
+  for (int t = tid; t < nb * NS2; t += RB_THREADS) {
+    const int bl = t / NS2, r = t - bl * NS2;
+    const int a = r % NS1, bb = r / NS1;
+    const T* ps = A.ps + (long long)(b0 + bl) * A.bss;
+    const long long base = (long long)(my * Ns + bb) * A.pys + (mx * Ns + a);
+    T g = T(0);
+#pragma unroll
+    for (int c = 0; c < NS1; ++c) g += A.ds[c] * ps[base + (long long)c * A.pzs];
+    TC[bl][0][r] = ps[base];
+    TC[bl][1][r] = g;
+  }
+  for (int t = tid; t < nb * nf * NF2; t += RB_THREADS) {
+    const int bl = t / (nf * NF2), r2 = t - bl * (nf * NF2);
+    const int f = r2 / NF2, r = r2 - f * NF2;
+    const int fcol = A.ff_col[f0 + f];
+    const int ex = fcol % A.npx, ey = fcol / A.npx;
+    const int a = r % NP1, bb = r / NP1;
+    const T* pp = A.pp + (long long)(b0 + bl) * A.bsp;
+    const long long base = (long long)A.kp0 * A.pzp + (long long)(ey * Np + bb) * A.pyp + (ex * Np + a);
+    T g = T(0);
+#pragma unroll
+    for (int c = 0; c < NP1; ++c) g += A.dp[c] * pp[base + (long long)c * A.pzp];
+    TF[bl][f][0][r] = pp[base + (long long)Np * A.pzp];
+    TF[bl][f][1][r] = g;
+  }
+  __syncthreads();
+  // workers: (member, fine face, qx)
+  {
+    const int bl = tid / (FS * Q);
+    const int f = (tid / Q) % FS;
+    const int qx = tid % Q;
+    if (tid < BPC * FS * Q && bl < nb && f < nf) {
+      T VF[2][NP1], VC[2][NS1];
+      {
+        T lx[NP1];
+#pragma unroll
+        for (int i = 0; i < NP1; ++i) lx[i] = sLp[qx][i];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+          for (int j = 0; j < NP1; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < NP1; ++i) s += lx[i] * TF[bl][f][w][j * NP1 + i];
+            VF[w][j] = s;
+          }
+      }
+      {
+        T lx[NS1];
+#pragma unroll
+        for (int i = 0; i < NS1; ++i) lx[i] = sLsx[f][qx][i];
+#pragma unroll
+        for (int w = 0; w < 2; ++w)
+#pragma unroll
+          for (int j = 0; j < NS1; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i < NS1; ++i) s += lx[i] * TC[bl][w][j * NS1 + i];
+            VC[w][j] = s;
+          }
+      }
+      T pa[NP1], pb[NP1], ca[NS1], cb[NS1];
+#pragma unroll
+      for (int j = 0; j < NP1; ++j) { pa[j] = T(0); pb[j] = T(0); }
+#pragma unroll
+      for (int j = 0; j < NS1; ++j) { ca[j] = T(0); cb[j] = T(0); }
+#pragma unroll
+      for (int qy = 0; qy < Q; ++qy) {
+        T up = T(0), dup = T(0), um = T(0), dum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP1; ++j) {
+          const T l = sLp[qy][j];
+          up += l * VF[0][j];
+          dup += l * VF[1][j];
+        }
+#pragma unroll
+        for (int j = 0; j < NS1; ++j) {
+          const T l = sLsy[f][qy][j];
+          um += l * VC[0][j];
+          dum += l * VC[1][j];
+        }
+        const T J = up - um;
+        const T avg = T(0.5) * (A.cp2 * dup + A.cm2 * dum);
+        const T W = sW[qy * Q + qx];
+        const T alpha = W * (A.gamma * J - avg);
+        const T bp = -T(0.5) * W * A.cp2 * J;
+        const T bm = -T(0.5) * W * A.cm2 * J;
+#pragma unroll
+        for (int j = 0; j < NP1; ++j) {
+          const T l = sLp[qy][j];
+          pa[j] += l * alpha;
+          pb[j] += l * bp;
+        }
+#pragma unroll
+        for (int j = 0; j < NS1; ++j) {
+          const T l = sLsy[f][qy][j];
+          ca[j] += l * alpha;
+          cb[j] += l * bm;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NP1; ++j) { PF[bl][f][0][j][qx] = pa[j]; PF[bl][f][1][j][qx] = pb[j]; }
+#pragma unroll
+      for (int j = 0; j < NS1; ++j) { PC[bl][f][0][j][qx] = ca[j]; PC[bl][f][1][j][qx] = cb[j]; }
+    }
+  }
+  __syncthreads();
+  // projection along x: fine residuals (alpha -> Rap, beta+ -> Rbp) ...
+  for (int t = tid; t < nb * nf * 2 * NF2; t += RB_THREADS) {
+    const int r = t % NF2, r2 = t / NF2;
+    const int w = r2 % 2, r3 = r2 / 2;
+    const int f = r3 % nf, bl = r3 / nf;
+    const int i = r % NP1, j = r / NP1;
+    T s = T(0);
+#pragma unroll
+    for (int qx = 0; qx < Q; ++qx) s += sLp[qx][i] * PF[bl][f][w][j][qx];
+    const long long o = (long long)(b0 + bl) * A.rbp + (long long)A.ff_col[f0 + f] * NF2 + r;
+    if (w == 0) A.Rap[o] = s;
+    else A.Rbp[o] = s;
+  }
+  // ... and the coarse residual (-alpha -> Ras, beta- -> Rbs), fine faces in list order
+  for (int t = tid; t < nb * 2 * NS2; t += RB_THREADS) {
+    const int r = t % NS2, r2 = t / NS2;
+    const int w = r2 % 2, bl = r2 / 2;
+    const int i = r % NS1, j = r / NS1;
+    T tot = T(0);
+    for (int f = 0; f < nf; ++f) {
+      T s = T(0);
+#pragma unroll
+      for (int qx = 0; qx < Q; ++qx) s += sLsx[f][qx][i] * PC[bl][f][w][j][qx];
+      tot += s;
+    }
+    const long long o = (long long)(b0 + bl) * A.rbs + (long long)ccol * NS2 + r;
+    if (w == 0) A.Ras[o] = -tot;
+    else A.Rbs[o] = tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Warps [0, B*K): PMUT (b, k).  g_{k,m} = sum_j B_{j,km} p^n_j (warp-shuffle
 // reduction in FP64), then the Newmark predictor / solve / corrector of the
 // modal ODE mu (q'' + 2 zeta w q' + w^2 q) = g + eta phi^n on lanes m < M.
@@ -320,9 +502,15 @@ cudaError_t launch_scale(double* x, const double* y, double a, long long n, cuda
 template <typename T>
 cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s) {
   if (a.ncf <= 0) return cudaSuccess;
-  dim3 grid(a.ncf, (batch + IF_BPC - 1) / IF_BPC);
-  if (a.Np == 4 && a.Ns == 6 && a.q == 7) iface_kernel<T, 5, 7, 7><<<grid, IF_THREADS, 0, s>>>(a, batch);
-  else iface_kernel<T, 0, 0, 0><<<grid, IF_THREADS, 0, s>>>(a, batch);
+  constexpr int BPC = sizeof(T) == 4 ? 8 : 4;   // static shared memory stays under 48 KB
+  if (a.max_ff <= 4 && a.Np == 4 && a.Ns == 6 && a.q == 7) {
+    iface_rows_kernel<T, 5, 7, 7, 4, BPC><<<dim3(a.ncf, (batch + BPC - 1) / BPC), RB_THREADS, 0, s>>>(a, batch);
+  } else if (a.max_ff <= 4 && a.Np == 4 && a.Ns == 4 && a.q == 5) {
+    iface_rows_kernel<T, 5, 5, 5, 4, BPC><<<dim3(a.ncf, (batch + BPC - 1) / BPC), RB_THREADS, 0, s>>>(a, batch);
+  } else {
+    dim3 grid(a.ncf, (batch + IF_BPC - 1) / IF_BPC);
+    iface_kernel<T, 0, 0, 0><<<grid, IF_THREADS, 0, s>>>(a, batch);
+  }
   return cudaGetLastError();
 }
 
