@@ -7,8 +7,11 @@ by quadrature, its own interface matrix by brute-force face matching, and
 integrates with the paper's three-vector Newmark scheme literally.
 
 Paper passages followed (arXiv 2603.06267):
-  * problem: Sec. 2, eq. (full_problem) rows 1, 7-10 without PML/ABC;
+  * problem: Sec. 2, eq. (full_problem) rows 1, 6-10 without PML;
     PMUT modal ODEs eq. (ode)/(pmut_problem).
+  * first-order absorbing boundary on Gamma_ABC: the damping form d of
+    eq. (Wf_4), d(w, v) = sum_F int_F c w v, giving C of eq. (semi_SEM),
+    applied to the predicted velocity as in Algorithm 1.
   * DG-SEM space V^DG (C0 Q_r inside each box, discontinuous across Gamma_I),
     bilinear forms m and a (SIPG), penalty gamma_F: Sec. 3, eqs. (Wf_1)-(Wf_2).
   * algebraic form M p'' + K p = f(q''), q'' + W q = g(p, phi), lumped GLL
@@ -30,7 +33,13 @@ Readings where the paper is silent (each also listed in the design doc):
     on each finer face; h in gamma_F is the element length normal to the
     face; c-bar is the harmonic mean.
   * time loop runs S steps (n = 0..S-1); trace sample n is p^{n+1}.
-  * a non-zero initial state (p0, p'0) starts from p''0 = M^-1(-K p0).
+  * a non-zero initial state (p0, p'0) starts from p''0 = M^-1(-K p0 - C p'0).
+  * the integral of d uses GLL collocation on the face nodes (like the
+    lumped mass), so C is diagonal.  With absorbing sides dt is also held
+    to 1 / max_j (C_jj / M_jj): the explicit damping of Algorithm 1 loses
+    stability at a few times that (corner nodes of three absorbing sides).  The strong form's row 6 has the
+    opposite sign convention to d; d is taken as written (it dissipates
+    energy, which is what an absorbing condition does).
 """
 from __future__ import annotations
 
@@ -375,6 +384,7 @@ class OracleProblem:
             KI, self.gamma = interface_matrix(self.meshes[0], self.meshes[1], self.nh, alpha, nq)
             self.K = (self.K + KI).tocsr()
         self.Minv = 1.0 / self.M
+        self._absorbing_matrix()
         self._pmut_matrix()
 
     def _assemble_volume(self):
@@ -394,6 +404,31 @@ class OracleProblem:
         self.K = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                shape=(self.nh, self.nh)).tocsr()
         self.M = M
+
+    def _absorbing_matrix(self):
+        """Diagonal C of the damping form d (eq. Wf_4): for every element face
+        F on an absorbing box side, C_jj += c w_a w_b |J_F| at its GLL nodes."""
+        C = np.zeros(self.nh)
+        for dom, m in zip(self.w.domains, self.meshes):
+            sides = getattr(dom, "absorbing", (0,) * 6)
+            N = m.N
+            for side in range(6):
+                if not sides[side]:
+                    continue
+                d = side // 2                      # normal direction
+                t1, t2 = [e for e in range(3) if e != d]
+                jac = m.h[t1] * m.h[t2] / 4.0      # face Jacobian of the affine face
+                fixed = 0 if side % 2 == 0 else m.L[d] - 1
+                for e2 in range(m.ne[t2]):
+                    for e1 in range(m.ne[t1]):
+                        for b in range(N + 1):
+                            for a in range(N + 1):
+                                idx = [0, 0, 0]
+                                idx[d] = fixed
+                                idx[t1] = e1 * N + a
+                                idx[t2] = e2 * N + b
+                                C[m.node_id(*idx)] += dom.c * m.w[a] * m.w[b] * jac
+        self.C = C
 
     def face_nodes(self):
         """Ids and (x, y) of the GLL nodes on the z = origin face of the
@@ -477,11 +512,17 @@ class OracleProblem:
     # ---------------------------------------------------------------- time step
     def stable_dt(self, cfl: Optional[float] = None):
         """dt = CFL * min_K min_d (h_d / 2 * min GLL gap) / c_max  (reading of
-        the CFL bound dt <~ h_min, Sec. 3.1)."""
+        the CFL bound dt <~ h_min, Sec. 3.1).  With absorbing sides the
+        damping term of Algorithm 1 is explicit (C acts on the predicted
+        velocity), so dt is also held to 1 / max_j (C_jj / M_jj)."""
         cfl = self.w.cfl if cfl is None else cfl
         cmax = max(m.c for m in self.meshes)
         hmin = min(min(m.h) / 2.0 * float(np.min(np.diff(m.xi))) for m in self.meshes)
-        return cfl * hmin / cmax
+        dt = cfl * hmin / cmax
+        sigma = float(np.max(self.C * self.Minv))
+        if sigma > 0.0:
+            dt = min(dt, 1.0 / sigma)
+        return dt
 
     def all_coordinates(self):
         xs, ys, zs = [], [], []
@@ -518,7 +559,7 @@ class OracleProblem:
             p = np.array(p0, dtype=np.float64).reshape(self.nh, -1) * np.ones((1, B))
             if v0 is not None:
                 pd = np.array(v0, dtype=np.float64).reshape(self.nh, -1) * np.ones((1, B))
-            pdd = self.Minv[:, None] * (-(self.K @ p))
+            pdd = self.Minv[:, None] * (-(self.K @ p) - self.C[:, None] * pd)
         traces = np.zeros((B, len(rec), S))
         energies = [] if energy else None
         Minv = self.Minv[:, None]
@@ -536,8 +577,8 @@ class OracleProblem:
             # acoustic predictor
             p_new = p + dt * pd + 0.5 * dt * dt * pdd
             pd_new = pd + 0.5 * dt * pdd
-            # acoustic solve: p'' = M^-1 (f(q'') - K p)
-            rhs = -(self.K @ p_new)
+            # acoustic solve: p'' = M^-1 (f(q'') - K p - C p'_pred)
+            rhs = -(self.K @ p_new) - self.C[:, None] * pd_new
             if pm is not None:
                 rhs = rhs - self.kappa * (self.B @ qdd_new)
             pdd_new = Minv * rhs

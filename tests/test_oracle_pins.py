@@ -383,3 +383,82 @@ def test_face_matching_finds_coarse_quadrant(two_domain):
             assert abs(rm[2] + 1.0) < 1e-12
             expect_x = -1 + ((ex % 2) + (ref[q, 0] + 1) / 2)
             assert abs(rm[0] - expect_x) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# First-order absorbing boundary (damping form d of eq. Wf_4)
+# ---------------------------------------------------------------------------
+def _abc_box(absorbing, nel=(3, 2, 2), order=4, h=75e-6):
+    dom = W.Domain((0, 0, 0), tuple(n * h for n in nel), nel, order, absorbing=absorbing)
+    return W.Workload("abc_box", [dom], 10, np.array([[h, h, h]]))
+
+
+def test_abc_matrix_is_face_quadrature_of_c():
+    """C sums to c x (area of the absorbing sides); zero off those sides."""
+    w = _abc_box((1, 0, 0, 1, 0, 1))
+    P = O.OracleProblem(w)
+    d = w.domains[0]
+    Lx, Ly, Lz = d.extent
+    assert abs(P.C.sum() - d.c * (Ly * Lz + Lx * Lz + Lx * Ly)) < 1e-12 * d.c * Lx * Ly
+    x, y, z = P.all_coordinates()
+    on = (np.isclose(x, 0) | np.isclose(y, Ly) | np.isclose(z, Lz))
+    assert np.all(P.C[~on] == 0) and np.all(P.C[on] > 0)
+
+
+def test_abc_discrete_energy_balance():
+    """Algorithm 1 with C acting on the predicted velocity v^{n+1/2}:
+    E^{n+1} - E^n = -(dt/2) v^{n+1/2}.C (v^{n+1/2} + v^{n+3/2}) exactly, with
+    E the leapfrog energy 1/2 v.M v + 1/2 p^{n+1}.K p^{n+2}."""
+    w = _abc_box((1, 1, 0, 1, 1, 0))
+    P = O.OracleProblem(w)
+    x, y, z = P.all_coordinates()
+    p0 = W.seeded_field(4, x, y, z)
+    v0 = 1e3 * W.seeded_field(5, x, y, z)
+    dt = P.stable_dt()
+    vs = []
+    _, E = P.run(nsteps=40, dt=dt, p0=p0, v0=v0, energy=True, batch=1,
+                 callback=lambda n, p, pd, pdd, **k: vs.append((pd + 0.5 * dt * pdd)[:, 0].copy()))
+    e = E[:, 0, 0]
+    for n in range(1, 40):
+        pred = -0.5 * dt * np.dot(vs[n - 1] * P.C, vs[n - 1] + vs[n])
+        assert abs((e[n] - e[n - 1]) - pred) <= 1e-9 * abs(e[n]), n
+    assert e[-1] < e[0]
+
+
+def test_abc_absorbs_a_normally_incident_plane_wave():
+    """A plane pulse running along +x leaves through an absorbing x+ side
+    (rigid walls normal to y and z keep it an exact plane wave): almost no
+    energy remains, while a rigid x+ side reflects all of it."""
+    h, N = 75e-6, 4
+    nel = (24, 1, 1)
+    out = {}
+    for sides in [(0, 1, 0, 0, 0, 0), (0, 0, 0, 0, 0, 0)]:
+        dom = W.Domain((0, 0, 0), tuple(n * h for n in nel), nel, N, absorbing=sides)
+        w = W.Workload("pulse", [dom], 10, np.array([[h, h / 2, h / 2]]))
+        P = O.OracleProblem(w)
+        x, y, z = P.all_coordinates()
+        Lx = dom.extent[0]
+        p0, v0 = W.gaussian_pulse_x(dom, x, 0.6 * Lx, 2 * h, +1)
+        dt = P.stable_dt()
+        S = int((0.4 * Lx + 8 * h) / dom.c / dt)
+        _, E = P.run(nsteps=S, dt=dt, p0=p0, v0=v0, energy=True, batch=1)
+        out[sides[1]] = E[-1, 1, 0] / E[0, 1, 0]
+    assert out[1] < 1e-3, out
+    assert out[0] > 0.99, out
+
+
+def test_abc_step_map_is_stable_at_the_chosen_dt():
+    """Spectral radius of the damped leapfrog map (p^{n+1}, v^{n+1/2}) ->
+    (p^{n+2}, v^{n+3/2}) with every side absorbing, at stable_dt(): <= 1."""
+    for order, nel in [(2, (3, 2, 2)), (4, (2, 2, 2))]:
+        w = _abc_box((1, 1, 1, 1, 1, 1), nel=nel, order=order)
+        P = O.OracleProblem(w)
+        dt = P.stable_dt()
+        n = P.nh
+        A = P.Minv[:, None] * P.K.toarray()
+        s = P.Minv * P.C
+        Vp, Vv = -dt * A, np.eye(n) - dt * np.diag(s)
+        T = np.block([[np.eye(n) + dt * Vp, dt * Vv], [Vp, Vv]])
+        assert np.max(np.abs(np.linalg.eigvals(T))) <= 1.0 + 1e-9
+        # and the limit is the damping one here (three absorbing sides meet at the corners)
+        assert abs(dt * np.max(s) - 1.0) < 1e-12

@@ -77,13 +77,16 @@ def _shape_integrals(m: int):
 
 @dataclass
 class Domain:
-    """Axis-aligned box meshed by nelem hexahedra of GLL order `order`."""
+    """Axis-aligned box meshed by nelem hexahedra of GLL order `order`.
+    absorbing: per box side (x-, x+, y-, y+, z-, z+) 1 = first-order
+    absorbing boundary (Gamma_ABC), 0 = rigid wall (Gamma_N)."""
     origin: tuple
     extent: tuple
     nelem: tuple
     order: int
     c: float = WATER_C
     rho: float = WATER_RHO
+    absorbing: tuple = (0, 0, 0, 0, 0, 0)
 
 
 @dataclass
@@ -372,3 +375,14 @@ def surrogate_array(batch: int = 64, seed: int = 5, nsteps: int = 2950) -> Workl
     rec = np.stack([X.ravel(), Y.ravel(), np.full(64, 0.8e-3)], axis=1)
     d, a, _ = steering_patterns(centers, batch, seed=seed + 1000)
     return Workload("surrogate_array", doms, nsteps, rec, pm, batch=batch, drive_delay=d, drive_amp=a)
+
+
+def gaussian_pulse_x(domain: Domain, x, center: float, width: float, direction: int = 1):
+    """Plane pulse g(x) = exp(-((x - center)/width)^2) travelling along
+    direction * e_x at the domain's sound speed: p0 = g, p'0 = -direction c g'.
+    With rigid walls normal to y and z this is an exact solution of the wave
+    equation until it reaches an x side."""
+    s = (np.asarray(x) - center) / width
+    g = np.exp(-s * s)
+    dg = -2.0 * s / width * g
+    return g, -direction * domain.c * dg
