@@ -117,6 +117,21 @@ typedef struct {
  * context (NULL on error). */
 int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out);
 
+/* First-order absorbing boundary (Sec. 2, eq. full_problem row 6, as the
+ * damping form d(w, v) = sum_F int_F c w v of eq. Wf_4; matrix C of eq.
+ * semi_SEM, diagonal by GLL collocation on the face nodes).
+ *   box    0 = primary, 1 = secondary.
+ *   sides  [6] for the box sides x-, x+, y-, y+, z-, z+: non-zero = absorbing
+ *          (Gamma_ABC), 0 = rigid wall (Gamma_N, the default).  The primary
+ *          z-min side (Gamma_PMUT) and the interface sides cannot absorb
+ *          (DGSEM_EINVAL).
+ * Algorithm 1 applies C to the predicted velocity, explicitly, so dt is held
+ * to min(cfl dt, 1 / max_i C_ii/M_ii); a dt the caller fixed in
+ * dgsem_mesh_desc above that limit is rejected (DGSEM_EUNSTABLE, nothing
+ * changed).  The context's state is invalidated: the next dgsem_run starts
+ * from rest. */
+int dgsem_set_absorbing(dgsem_ctx* ctx, int box, const int* sides);
+
 /* Time step, stability bound and size.  dt_stable_max is 2 / sqrt(lambda_max)
  * of M^-1 K from dgsem_check_stability() (0 if it has not run); ndof counts
  * the unique GLL nodes of all boxes (dim V^DG). Any output may be NULL. */

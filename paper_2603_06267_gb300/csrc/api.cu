@@ -183,6 +183,8 @@ struct dgsem_ctx {
   Box box[2];
   Basis1D* basis[2] = {nullptr, nullptr};
   double dt = 0.0, dt_stable = 0.0, cfl = 0.0, alpha = 0.0;
+  double dt_cfl = 0.0;                     // dt before the absorbing-boundary limit
+  bool dt_fixed = false;                   // dt given by the caller (not from cfl)
   long long ndof = 0;
   VolSpec vspec[2];
   // interface
@@ -1102,6 +1104,8 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
     CUDA_TRY(cudaMemset(c->d_step, 0, sizeof(int)));
   }
   c->dt = desc->dt > 0.0 ? desc->dt : desc->cfl * hmin / cmax;
+  c->dt_cfl = c->dt;
+  c->dt_fixed = desc->dt > 0.0;
   c->kappa = c->box[0].rho * c->box[0].c * c->box[0].c;
   if (c->nd == 2) {
     int rc = build_interface(c, desc);
@@ -1118,6 +1122,45 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
       c->face_xy[2 * ((size_t)j * P.L[0] + i) + 1] = P.o[1] + P.h[1] * (ey + 0.5 * (P.basis->x[ay] + 1.0));
     }
   *out = c;
+  return DGSEM_OK;
+}
+
+int dgsem_set_absorbing(dgsem_ctx* c, int box, const int* sides) {
+  if (!c || !sides) return fail(DGSEM_EINVAL, "NULL argument");
+  if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "bad box %d", box);
+  const Box& B = c->box[box];
+  for (int s = 0; s < 6; ++s) {
+    if (!sides[s]) continue;
+    if (box == 0 && s == 4) return fail(DGSEM_EINVAL, "the primary z-min side carries Gamma_PMUT");
+    if (c->nd == 2 && ((box == 0 && s == 5) || (box == 1 && s == 4)))
+      return fail(DGSEM_EINVAL, "box %d side %d is the interface Gamma_I", box, s);
+  }
+  double abc[6];
+  for (int s = 0; s < 6; ++s) abc[s] = sides[s] ? B.c * (2.0 / B.h[s / 2]) / B.basis->w[0] : 0.0;
+  // largest C_ii / M_ii of any node: the corner where the most absorbing sides meet
+  double sigma = 0.0;
+  for (int d = 0; d < c->nd; ++d) {
+    double sd = 0.0;
+    for (int ax = 0; ax < 3; ++ax) {
+      const double lo = d == box ? abc[2 * ax] : c->vspec[d].abc[2 * ax];
+      const double hi = d == box ? abc[2 * ax + 1] : c->vspec[d].abc[2 * ax + 1];
+      sd += std::max(lo, hi);
+    }
+    sigma = std::max(sigma, sd);
+  }
+  double dt = c->dt_cfl;
+  if (sigma > 0.0) dt = std::min(dt, 1.0 / sigma);
+  if (c->dt_fixed && dt < c->dt_cfl)
+    return fail(DGSEM_EUNSTABLE, "dt = %.4e s exceeds 1 / max(C/M) = %.4e s of the absorbing sides", c->dt_cfl, dt);
+  for (int s = 0; s < 6; ++s) c->vspec[box].abc[s] = abc[s];
+  c->vspec[box].has_abc = 0;
+  for (int s = 0; s < 6; ++s) c->vspec[box].has_abc |= sides[s] ? 1 : 0;
+  c->dt = dt;
+  // the captured step graph holds the old parameters, and the state's half-step
+  // velocity belongs to the old dt
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  c->graph_key.clear();
+  c->state_valid = false;
   return DGSEM_OK;
 }
 

@@ -63,6 +63,10 @@ struct VolArgs {
   const T* Ra;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b alpha_q
   const T* Rb;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b beta_q
   T dI[N + 1];             // d_c = (2/h_z) l_c'(face)
+  // absorbing sides (eq. Wf_4): sigma = C_ii / M_ii = c (2/h_d) / w_0 per box
+  // side (x-, x+, y-, y+, z-, z+), 0 = rigid; a -= sigma v on those nodes
+  T abc[6];
+  int has_abc;
   // FP32 tables for packed f32x2 arithmetic: x rows with their taps in pairs
   // (q = 2k, 2k+1), y and z coefficients repeated in both lanes
   float2 cxq[N + 1][(N + 1) / 2];
@@ -159,6 +163,10 @@ struct VolSpec {
   int iface_k0, iface_top;
   const void* Ra; const void* Rb;
   double dI[DG_MAXN + 1];
+  // first-order absorbing sides (x-, x+, y-, y+, z-, z+): C_ii / M_ii of a
+  // node on that side, c (2/h_d) / w_0; 0 = rigid wall
+  double abc[6];
+  int has_abc;
   int layers_per_cta;              // 0: choose automatically
   int tile;                        // tile-shape variant (see vol_impl.cuh)
 };
@@ -171,8 +179,14 @@ int vol_tma_box_f32(int N, int tile, unsigned box[3], unsigned vbox[3]);
 int vol_tma_box_f64(int N, int tile, unsigned box[3], unsigned vbox[3]);
 
 // Launchers (defined in the kernel translation units)
+// (one instantiation per precision and absorbing-side flag, each in its own
+// translation unit; the flag removes the absorbing term from boxes without one)
+template <typename T, bool ABC>
+cudaError_t launch_vol_flag(const VolSpec& spec, int batch, cudaStream_t s);
 template <typename T>
-cudaError_t launch_vol(const VolSpec& spec, int batch, cudaStream_t s);
+inline cudaError_t launch_vol(const VolSpec& spec, int batch, cudaStream_t s) {
+  return spec.has_abc ? launch_vol_flag<T, true>(spec, batch, s) : launch_vol_flag<T, false>(spec, batch, s);
+}
 template <typename T>
 cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s);
 template <typename T>

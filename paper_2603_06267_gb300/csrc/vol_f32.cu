@@ -1,7 +1,8 @@
-// FP32 instantiations of the fused volume kernel (see vol_impl.cuh).
+// FP32 instantiations of the fused volume kernel (see vol_impl.cuh), boxes
+// without absorbing sides.
 #include "vol_impl.cuh"
 
-template cudaError_t launch_vol<float>(const VolSpec&, int, cudaStream_t);
+template cudaError_t launch_vol_flag<float, false>(const VolSpec&, int, cudaStream_t);
 int vol_tma_box_f32(int N, int tile, unsigned box[3], unsigned vbox[3]) {
   return dgvol::tma_box<float>(N, tile, box, vbox);
 }

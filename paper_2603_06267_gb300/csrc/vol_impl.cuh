@@ -480,7 +480,7 @@ __device__ __forceinline__ int tile_row(int ty) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB>
+template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool ABC>
 __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
   using G = Geo<T, N, TXE, TYE, PG>;
   static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
@@ -537,6 +537,12 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
   const T iw_y = yvert ? yiw : A.iwa[yb];
   const bool xl = ex > 0;
   const T mscale = T(A.minv_scale);        // 8 / (hx hy hz): M^-1 = mscale / (w_a w_b w_c)
+  // absorbing sides: C_ii / M_ii of this row's y sides and of the box's x-min node
+  const T abc_y = ABC ? ((j == 0 ? A.abc[2] : T(0)) + (j == A.L1 - 1 ? A.abc[3] : T(0))) : T(0);
+  const T abc_x0 = (ABC && ex == 0) ? A.abc[0] : T(0);
+  auto abc_plane = [&](int k) {   // y and z sides of the nodes of plane k
+    return abc_y + (k == 0 ? A.abc[4] : T(0)) + (k == A.L2 - 1 ? A.abc[5] : T(0));
+  };
   const T xiw = xl ? A.iwv : A.iwb;        // vertex node ex*N (an element always lies to its right)
 
   const int r0 = rt + N;                   // staged row of lattice row j
@@ -622,7 +628,16 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       }
       // FP32 update of the N owned nodes of plane k from sm = M^-1 K p:
       // a = -sm (+ PMUT / interface terms), v += dtv a, p_out = p + dtp v
-      auto commit_f32 = [&](int k, const T* vcur, const T* self, const float* sm, T iw_z, T* vn, T* pn) {
+      auto commit_f32 = [&](int k, const T* vcur, const T* self, float* sm, T iw_z, T* vn, T* pn) {
+        if constexpr (ABC) {
+          // absorbing sides (eq. Wf_4): a -= C/M v with v the predicted velocity v^{n+1/2}
+          const T sg = abc_plane(k);
+          if (sg != T(0) || abc_x0 != T(0)) {
+            sm[0] += (sg + abc_x0) * vcur[0];
+#pragma unroll
+            for (int a = 1; a < N; ++a) sm[a] += sg * vcur[a];
+          }
+        }
         if (extras_layer && plane_extras(k)) {
 #pragma unroll
           for (int a = 0; a < N; ++a) {
@@ -747,10 +762,12 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
 #pragma unroll
             for (int a = 0; a < N; ++a) zs[a] *= iw_z;
           }
-          // update: a = -(M^-1 K p) (+ extras), v += dtv a, p_out = p + dtp v
+          // update: a = -(M^-1 K p) - C/M v (+ extras), v += dtv a, p_out = p + dtp v
+          const T sg = ABC ? abc_plane(k) : T(0);
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             T accum = -(acc[a] + zs[a]);
+            if constexpr (ABC) accum -= (sg + (a == 0 ? abc_x0 : T(0))) * vcur[a];
             if (extras_layer && plane_extras(k)) {
               const T iw_x = (a == 0) ? xiw : A.iwa[a];
               const T minv = mscale * iw_x * iw_y * iw_z;
@@ -815,6 +832,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
         T vo;
         if constexpr (VTMA) vo = (c < N) ? V0[c * VPLANE + vown + N] : *vp;
         else vo = *vp;
+        if constexpr (ABC) accum -= (abc_plane(k) + A.abc[1]) * vo;
         const T vn = vo + A.dtv * accum;
         *vp = vn;
         pout[(long long)k * A.pz + grow + N] = P[col] + A.dtp * vn;
@@ -898,6 +916,8 @@ VolArgs<T, N> make_args(const VolSpec& s) {
     a.lxq[k] = make_float2((float)s.l[0][2 * k], (float)s.l[0][2 * k + 1]);
     a.rxq[k] = make_float2((float)s.r[0][2 * k], (float)s.r[0][2 * k + 1]);
   }
+  for (int q = 0; q < 6; ++q) a.abc[q] = T(s.abc[q]);
+  a.has_abc = s.has_abc;
   a.iwv = T(s.iwv); a.iwb = T(s.iwb);
   a.minv_scale = s.minv_scale;
   a.has_pmut = s.has_pmut;
@@ -908,7 +928,7 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   return a;
 }
 
-template <typename T, int N, int V>
+template <typename T, int N, int V, bool ABC>
 cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   using SH = typename TileShape<T, N, V>::S;
   constexpr int TXE = SH::TXE, TYE = SH::TYE, PG = SH::PG;
@@ -927,7 +947,7 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, ABC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
@@ -936,22 +956,22 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+template <typename T, int N, bool ABC>
 cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
   if constexpr (NumShapes<T, N>::value > 1) {
     switch (s.tile) {
-      case 0: return launch_v<T, N, 0>(s, batch, st);
-      case 1: return launch_v<T, N, 1>(s, batch, st);
-      case 2: return launch_v<T, N, 2>(s, batch, st);
-      case 3: return launch_v<T, N, 3>(s, batch, st);
-      case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4>(s, batch, st); break;
-      case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5>(s, batch, st); break;
+      case 0: return launch_v<T, N, 0, ABC>(s, batch, st);
+      case 1: return launch_v<T, N, 1, ABC>(s, batch, st);
+      case 2: return launch_v<T, N, 2, ABC>(s, batch, st);
+      case 3: return launch_v<T, N, 3, ABC>(s, batch, st);
+      case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4, ABC>(s, batch, st); break;
+      case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5, ABC>(s, batch, st); break;
       default: break;
     }
     return cudaErrorInvalidValue;
   } else {
     if (s.tile != 0) return cudaErrorInvalidValue;
-    return launch_v<T, N, 0>(s, batch, st);
+    return launch_v<T, N, 0, ABC>(s, batch, st);
   }
 }
 
@@ -1005,18 +1025,18 @@ int tma_box(int N, int tile, unsigned box[3], unsigned vbox[3]) {
 
 }  // namespace dgvol
 
-template <typename T>
-cudaError_t launch_vol(const VolSpec& s, int batch, cudaStream_t st) {
+template <typename T, bool ABC>
+cudaError_t launch_vol_flag(const VolSpec& s, int batch, cudaStream_t st) {
   using namespace dgvol;
   switch (s.N) {
-    case 1: return launch_n<T, 1>(s, batch, st);
-    case 2: return launch_n<T, 2>(s, batch, st);
-    case 3: return launch_n<T, 3>(s, batch, st);
-    case 4: return launch_n<T, 4>(s, batch, st);
-    case 5: return launch_n<T, 5>(s, batch, st);
-    case 6: return launch_n<T, 6>(s, batch, st);
-    case 7: return launch_n<T, 7>(s, batch, st);
-    case 8: return launch_n<T, 8>(s, batch, st);
+    case 1: return launch_n<T, 1, ABC>(s, batch, st);
+    case 2: return launch_n<T, 2, ABC>(s, batch, st);
+    case 3: return launch_n<T, 3, ABC>(s, batch, st);
+    case 4: return launch_n<T, 4, ABC>(s, batch, st);
+    case 5: return launch_n<T, 5, ABC>(s, batch, st);
+    case 6: return launch_n<T, 6, ABC>(s, batch, st);
+    case 7: return launch_n<T, 7, ABC>(s, batch, st);
+    case 8: return launch_n<T, 8, ABC>(s, batch, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -30,7 +30,7 @@ DGSEM_FP32_MIXED = 1
 DGSEM_RUN_CONTINUE = 1
 
 EXPORTED = [
-    "dgsem_mesh_create", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
+    "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
     vp = c_void_p
     lib.dgsem_mesh_create.argtypes = [POINTER(MeshDesc), POINTER(vp)]
     lib.dgsem_get_dt.argtypes = [vp, POINTER(c_double), POINTER(c_double), POINTER(c_longlong)]
+    lib.dgsem_set_absorbing.argtypes = [vp, c_int, vp]
     lib.dgsem_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
     lib.dgsem_pmut_nodes.argtypes = [vp, POINTER(c_int), POINTER(POINTER(c_double))]
     lib.pmut_array_set.argtypes = [vp, c_int, c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -170,6 +171,13 @@ def dgsem_mesh_create(domains: Sequence, cfl: float = 0.3, dt: float = 0.0, pena
     ctx = c_void_p()
     _check(lib.dgsem_mesh_create(byref(desc), byref(ctx)), "dgsem_mesh_create")
     return ctx
+
+
+def dgsem_set_absorbing(ctx, box: int, sides):
+    """First-order absorbing box sides (x-, x+, y-, y+, z-, z+), eq. Wf_4."""
+    arr = np.ascontiguousarray([1 if v else 0 for v in sides], dtype=np.int32)
+    assert arr.shape == (6,)
+    _check(_lib.dgsem_set_absorbing(ctx, box, _ptr(arr)), "dgsem_set_absorbing")
 
 
 def dgsem_get_dt(ctx):
@@ -326,6 +334,10 @@ class Solver:
         self.ctx = dgsem_mesh_create(workload.domains, cfl=workload.cfl, dt=dt,
                                      penalty_alpha=workload.penalty_alpha,
                                      iface_quad_pts=getattr(workload, "quad_pts", 0) or 0)
+        for d, dom in enumerate(workload.domains):
+            sides = getattr(dom, "absorbing", None)
+            if sides is not None and any(sides):
+                dgsem_set_absorbing(self.ctx, d, sides)
         self.dt, _, self.ndof = dgsem_get_dt(self.ctx)
         self.K = 0
         if workload.pmuts is not None:
