@@ -9,6 +9,10 @@ integrates with the paper's three-vector Newmark scheme literally.
 Paper passages followed (arXiv 2603.06267):
   * problem: Sec. 2, eq. (full_problem) rows 1, 6-10 without PML;
     PMUT modal ODEs eq. (ode)/(pmut_problem).
+  * TX -> RX switch (eq. ode row 2, eq. pmut_problem row 2): from step
+    rx_switch on, phi_k^n = s / C_k sum_m eta_km q_km^n with the modal
+    coordinates of step n (the q that Algorithm 1's PMUT solve pairs with
+    p^n); s = +1 is the literal equation, s = -1 the stiffening reading.
   * first-order absorbing boundary on Gamma_ABC: the damping form d of
     eq. (Wf_4), d(w, v) = sum_F int_F c w v, giving C of eq. (semi_SEM),
     applied to the predicted velocity as in Algorithm 1.
@@ -554,6 +558,10 @@ class OracleProblem:
                 drive = self.w.drive(dt, S, B)
             drive = np.asarray(drive, dtype=np.float64)
             q = np.zeros((K * Mm, B)); qd = np.zeros_like(q); qdd = np.zeros_like(q)
+            rx_on = self.w.rx_switch is not None
+            if rx_on:
+                cap = np.broadcast_to(np.asarray(self.w.rx_capacitance, dtype=np.float64), (K,))
+            volts = np.zeros((B, K, S))
         p = np.zeros((self.nh, B)); pd = np.zeros_like(p); pdd = np.zeros_like(p)
         if p0 is not None:
             p = np.array(p0, dtype=np.float64).reshape(self.nh, -1) * np.ones((1, B))
@@ -569,7 +577,14 @@ class OracleProblem:
                 q_new = q + dt * qd + 0.5 * dt * dt * qdd
                 qd_new = qd + 0.5 * dt * qdd
                 # PMUT solve: q'' = -W q - 2 zeta w q'_pred + g(p^n, phi^n) / mu
-                phi = np.repeat(drive[:, :, n].T, Mm, axis=0)          # [(k,m), B]
+                if rx_on and n >= self.w.rx_switch:
+                    # open circuit: phi_k = s / C_k sum_m eta_km q_km^n
+                    vk = (eta[:, None] * q).reshape(K, Mm, B).sum(axis=1)   # [K, B]
+                    vk = (self.w.rx_sign / cap)[:, None] * vk
+                else:
+                    vk = drive[:, :, n].T                                   # [K, B]
+                volts[:, :, n] = vk.T
+                phi = np.repeat(vk, Mm, axis=0)                           # [(k,m), B]
                 g = (self.B.T @ p) + eta[:, None] * phi
                 qdd_new = -omega2[:, None] * q_new - twozw[:, None] * qd_new + g / mu[:, None]
                 # PMUT corrector
@@ -599,6 +614,7 @@ class OracleProblem:
         self.final_state = dict(p=p, pd=pd, pdd=pdd)
         if pm is not None:
             self.final_state.update(q=q, qd=qd, qdd=qdd)
+            self.voltages = volts
         if energy:
             return traces, np.array(energies)
         return traces

@@ -462,3 +462,47 @@ def test_abc_step_map_is_stable_at_the_chosen_dt():
         assert np.max(np.abs(np.linalg.eigvals(T))) <= 1.0 + 1e-9
         # and the limit is the damping one here (three absorbing sides meet at the corners)
         assert abs(dt * np.max(s) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# TX -> RX switch of the PMUT voltage (eq. ode row 2, eq. pmut_problem row 2)
+# ---------------------------------------------------------------------------
+def _rx_workload(sign, rho=1.0e-12, nsteps=900, rx_switch=650):
+    L = 0.3e-3
+    dom = W.Domain((0.0, 0.0, 0.0), (L, L, L), (4, 4, 4), 4, rho=rho)
+    pm = W.make_pmut_array([[0.15e-3, 0.15e-3]], 60e-6, W.MODE_FREQS_5[:3], 0.0)
+    d, a = W._uniform_drive(1)
+    w = W.Workload("rx", [dom], nsteps, np.array([[0.15e-3, 0.15e-3, 0.15e-3]]), pm, drive_delay=d, drive_amp=a)
+    w.rx_switch, w.rx_capacitance, w.rx_sign = rx_switch, np.array([1.0e-12]), sign
+    return w
+
+
+@pytest.mark.parametrize("sign", [-1, +1])
+def test_rx_open_circuit_modal_recurrence(sign):
+    """With a negligible fluid density the membrane is decoupled, and after the
+    switch Algorithm 1 (phi^n from q^n, stiffness on q^{n+1}) gives exactly
+      q^{n+2} - 2 q^{n+1} + q^n = dt^2 (-W q^{n+1} + (s/C) mu^-1 eta eta^T q^n),
+    and the recorded voltage is phi^n = (s/C) eta . q^n."""
+    w = _rx_workload(sign)
+    P = O.OracleProblem(w)
+    dt = P.stable_dt()
+    Q = []
+    P.run(dt=dt, batch=1, callback=lambda n, q=None, **k: Q.append(q[:, 0].copy()))
+    a = np.array([np.zeros(3)] + Q)                       # a[n] = q^n
+    pm = w.pmuts
+    eta, mu = pm.eta[0], pm.modal_mass[0]
+    om2 = (2 * np.pi * pm.freq_hz[0]) ** 2
+    Lam = (sign / 1.0e-12) * np.outer(eta / mu, eta)
+    n0 = w.rx_switch
+    scale = np.abs(a).max()
+    assert scale > 0
+    for n in range(n0, w.nsteps - 1):
+        lhs = a[n + 2] - 2 * a[n + 1] + a[n]
+        rhs = dt * dt * (-om2 * a[n + 1] + Lam @ a[n])
+        assert np.abs(lhs - rhs).max() <= 1e-9 * scale, n
+    volts = P.voltages[0, 0]
+    for n in range(n0, w.nsteps):
+        assert abs(volts[n] - (sign / 1.0e-12) * np.dot(eta, a[n])) <= 1e-12 * abs(volts).max()
+    # before the switch the recorded voltage is the drive
+    np.testing.assert_array_equal(volts[:n0], w.drive(dt, w.nsteps, 1)[0, 0, :n0])
+

@@ -143,6 +143,11 @@ class Workload:
     drive_amp: Optional[np.ndarray] = None        # [B, K]
     burst_freq: float = 2.0e6
     burst_cycles: float = 3.0
+    # TX -> RX switch: from step rx_switch on, membrane k's voltage is the
+    # open-circuit value rx_sign / C_k sum_m eta_km q_km (None: transmit only)
+    rx_switch: Optional[int] = None
+    rx_capacitance: Optional[np.ndarray] = None   # [K] farads
+    rx_sign: int = -1
 
     def drive(self, dt: float, nsteps: Optional[int] = None, batch: Optional[int] = None) -> np.ndarray:
         """phi_k(t^n) for t^n = n dt, n = 0..S-1, shape [B, K, S] (volts).
