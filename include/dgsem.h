@@ -167,6 +167,30 @@ int pmut_array_set(dgsem_ctx* ctx, int n_pmut, int n_modes, const int* foot_ptr,
                    const int* foot_node, const double* shape_un, const double* freq_hz,
                    const double* damping, const double* eta, const double* modal_mass);
 
+/* TX -> RX switch of the PMUT array (Sec. 2, eq. ode row 2 / eq.
+ * pmut_problem row 2): steps n < n_switch take the drive voltage phi_k,0
+ * passed to dgsem_run (transmission); from step n_switch on, membrane k's
+ * voltage is the open-circuit value
+ *     phi_k^n = sign / C_k * sum_m eta_km q_km^n
+ * with the modal coordinates of step n (reception).  n counts steps since
+ * the state was at rest or set by dgsem_set_state (dgsem_run flag
+ * DGSEM_RUN_CONTINUE keeps counting; checkpoints store the count).
+ *   n_switch     first receiving step; < 0 switches reception off (default).
+ *   capacitance  [n_pmut] C_k in farads (> 0), copied.
+ *   sign         +1: the equation as printed; -1: the convention in which the
+ *                open circuit stiffens the membrane (open-circuit frequency
+ *                above short-circuit).
+ * While reception is configured every dgsem_run records the voltage used in
+ * each step, [batch][n_pmut][nsteps] on the device, read with
+ * dgsem_get_voltages.  DGSEM_ESTATE without a PMUT array. */
+int pmut_set_receive(dgsem_ctx* ctx, long long n_switch, const double* capacitance, int sign);
+
+/* Copy the voltages of the last dgsem_run ([batch][n_pmut][nsteps] doubles,
+ * drive before the switch, open circuit after it) to the host array out of n
+ * doubles.  DGSEM_ESTATE if that run recorded none, DGSEM_EINVAL if n is too
+ * small. */
+int dgsem_get_voltages(const dgsem_ctx* ctx, double* out, size_t n);
+
 /* Run nsteps steps of Algorithm 1 for `batch` independent drive patterns
  * sharing the mesh and the PMUT array.
  *   precision  dgsem_precision.

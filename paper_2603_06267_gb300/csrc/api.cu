@@ -213,6 +213,13 @@ struct dgsem_ctx {
   void* Rb[2] = {nullptr, nullptr};
   double* q_state = nullptr;    // q | qd | qdd  [3][B*K*M]
   long long step = 0;
+  // TX -> RX switch of the PMUT array (off: rx_switch < 0)
+  long long rx_switch = -1;
+  double* d_rx_gain = nullptr;             // [K] s / C_k
+  long long* d_step_base = nullptr;        // steps done before the current run
+  double* d_volt = nullptr;                // [B][K][S] voltages of the last run
+  size_t volt_cap = 0;
+  long long volt_n = 0;                    // doubles recorded by the last run
   bool state_valid = false;
   // pending initial state
   std::vector<double> init_p, init_v;
@@ -633,7 +640,8 @@ void collect_timings(dgsem_ctx* c) {
 // Without a side stream everything runs on s in that order.
 template <typename T>
 int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs, long long dks, int n_local,
-                int R, double* traces, long long tbs, long long trs, bool init, cudaStream_t side = nullptr) {
+                int R, double* traces, long long tbs, long long trs, bool init, cudaStream_t side = nullptr,
+                double* volt = nullptr) {
   const bool fork = side && c->nd == 2 && c->has_iface && !init;
   cudaStream_t sp = fork ? side : s;       // stream of the PMUT launch
   if (fork) {
@@ -663,6 +671,10 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     a.pc0 = static_cast<const T*>(c->Y[0]); a.pc1 = c->nd > 1 ? static_cast<const T*>(c->Y[1]) : nullptr;
     a.bs0 = c->box[0].bstride; a.bs1 = c->nd > 1 ? c->box[1].bstride : 0;
     a.traces = traces; a.tbs = tbs; a.trs = trs;
+    if (c->rx_switch >= 0) {
+      a.rx_gain = c->d_rx_gain; a.rx_switch = c->rx_switch; a.step_base = c->d_step_base;
+    }
+    a.volt = volt; a.vbs = (long long)c->K * dks; a.vks = dks;
     LaunchTimer lt(c, sp, DGSEM_K_PMUT_RECV);
     CUDA_TRY(launch_pmut_recv<T>(a, sp));
   }
@@ -814,6 +826,7 @@ struct RunIO {
   size_t tr_n = 0;
   int R = 0;
   long long dbs = 0, dks = 0, tbs = 0, trs = 0;
+  double* d_volt = nullptr;      // voltage record of this run (RX configured), or NULL
 };
 
 // Everything a run does before its time steps: tensor maps, status words,
@@ -870,6 +883,21 @@ int run_prepare(dgsem_ctx* c, int nsteps, const double* drive, int R, double* tr
     }
   }
   CUDA_TRY(cudaMemsetAsync(c->d_step, 0, sizeof(int), s));
+  if (c->rx_switch >= 0 && c->K > 0) {
+    if (!c->d_step_base && (rc = dalloc(&c->d_step_base, sizeof(long long)))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(c->d_step_base, &c->step, sizeof(long long), cudaMemcpyHostToDevice, s));
+    const size_t vn = (size_t)c->batch * c->K * nsteps;
+    if (vn > c->volt_cap) {
+      drop_graph(c);   // the captured kernels hold the old buffer
+      dfree(c->d_volt);
+      if ((rc = dalloc(&c->d_volt, vn * sizeof(double)))) { c->volt_cap = 0; return rc; }
+      c->volt_cap = vn;
+    }
+    io.d_volt = c->d_volt;
+    c->volt_n = (long long)vn;
+  } else {
+    c->volt_n = 0;
+  }
   io.dbs = (long long)c->K * nsteps;
   io.dks = nsteps;
   io.tbs = (long long)R * nsteps;
@@ -926,7 +954,7 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
       int crc = DGSEM_OK;
       for (int n = 0; n < G && crc == DGSEM_OK; ++n)
         crc = launch_step<T>(c, c->cap_stream, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false,
-                             c->side_stream);
+                             c->side_stream, io.d_volt);
       cudaGraph_t g = nullptr;
       cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
       if (crc) { if (g) cudaGraphDestroy(g); return crc; }
@@ -947,7 +975,7 @@ int run_impl(dgsem_ctx* c, int nsteps, const double* drive, int R, double* trace
     }
   }
   for (int n = done; n < nsteps; ++n) {
-    rc = launch_step<T>(c, s, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false);
+    rc = launch_step<T>(c, s, io.d_drive, io.dbs, io.dks, 0, R, io.d_tr, io.tbs, io.trs, false, nullptr, io.d_volt);
     if (rc) return rc;
   }
   return run_finish(c, nsteps, io, s);
@@ -996,7 +1024,7 @@ int run_multi_impl(int n, dgsem_ctx* const* ctxs, int nsteps, const double* cons
       cudaStreamWaitEvent(c->cap_stream, ev[n], 0);
       for (int st = 0; st < G && crc == DGSEM_OK; ++st)
         crc = launch_step<T>(c, c->cap_stream, io[i].d_drive, io[i].dbs, io[i].dks, 0, io[i].R, io[i].d_tr, io[i].tbs,
-                             io[i].trs, false, c->side_stream);
+                             io[i].trs, false, c->side_stream, io[i].d_volt);
       cudaEventRecord(ev[i], c->cap_stream);
       cudaStreamWaitEvent(main, ev[i], 0);
     }
@@ -1027,7 +1055,7 @@ int run_multi_impl(int n, dgsem_ctx* const* ctxs, int nsteps, const double* cons
   for (int st = done; st < nsteps; ++st)
     for (int i = 0; i < n; ++i) {
       int rc = launch_step<T>(ctxs[i], s, io[i].d_drive, io[i].dbs, io[i].dks, 0, io[i].R, io[i].d_tr, io[i].tbs,
-                              io[i].trs, false);
+                              io[i].trs, false, nullptr, io[i].d_volt);
       if (rc) return rc;
     }
   for (int i = 0; i < n; ++i) {
@@ -1208,6 +1236,8 @@ int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* f
   drop_graph(c);
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
   dfree(c->d_ent_pmut); dfree(c->d_modal); dfree(c->q_state);
+  dfree(c->d_rx_gain);
+  c->rx_switch = -1;
   c->K = 0; c->M = 0; c->nnz = 0;
   c->state_valid = false;
   if (K == 0) return DGSEM_OK;
@@ -1248,6 +1278,37 @@ int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* f
   c->K = K; c->M = M; c->nnz = nnz;
   // PMUT state buffers are sized with the run state
   free_run_state(c);
+  return DGSEM_OK;
+}
+
+int pmut_set_receive(dgsem_ctx* c, long long n_switch, const double* capacitance, int sign) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  drop_graph(c);   // the captured PMUT launches hold the old switch
+  if (n_switch < 0) {
+    c->rx_switch = -1;
+    return DGSEM_OK;
+  }
+  if (c->K == 0) return fail(DGSEM_ESTATE, "no PMUT array: call pmut_array_set first");
+  if (!capacitance) return fail(DGSEM_EINVAL, "NULL capacitance");
+  if (sign != 1 && sign != -1) return fail(DGSEM_EINVAL, "sign must be +1 or -1");
+  std::vector<double> gain(c->K);
+  for (int k = 0; k < c->K; ++k) {
+    if (!(capacitance[k] > 0.0) || !std::isfinite(capacitance[k]))
+      return fail(DGSEM_EINVAL, "capacitance[%d] must be > 0", k);
+    gain[k] = sign / capacitance[k];
+  }
+  dfree(c->d_rx_gain);
+  int rc = upload(&c->d_rx_gain, gain);
+  if (rc) { c->rx_switch = -1; return rc; }
+  c->rx_switch = n_switch;
+  return DGSEM_OK;
+}
+
+int dgsem_get_voltages(const dgsem_ctx* c, double* out, size_t n) {
+  if (!c || !out) return fail(DGSEM_EINVAL, "NULL argument");
+  if (c->volt_n == 0 || !c->d_volt) return fail(DGSEM_ESTATE, "no voltage record: configure pmut_set_receive and run");
+  if (n < (size_t)c->volt_n) return fail(DGSEM_EINVAL, "buffer of %zu doubles is smaller than %lld", n, c->volt_n);
+  CUDA_TRY(cudaMemcpy(out, c->d_volt, (size_t)c->volt_n * sizeof(double), cudaMemcpyDeviceToHost));
   return DGSEM_OK;
 }
 
@@ -1604,6 +1665,7 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
   dfree(c->d_err);
   dfree(c->d_step);
+  dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   for (cudaEvent_t e : c->fork_ev)

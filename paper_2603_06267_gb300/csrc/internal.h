@@ -125,6 +125,13 @@ struct PmutArgs {
   long long dbs, dks;
   int n;                           // step offset inside this run
   const int* step;                 // device step counter of the run (added to n)
+  // TX -> RX switch (eq. ode row 2): from absolute step rx_switch on, the
+  // voltage is rx_gain[k] sum_m eta_km q_km^n (rx_gain = s / C_k) instead of the drive
+  const double* rx_gain;           // [K], or NULL: transmit only
+  long long rx_switch;
+  const long long* step_base;      // steps done before this run (since rest)
+  double* volt;                    // volt[b*vbs + k*vks + n]: voltage used in step n, or NULL
+  long long vbs, vks;
   double dt;
   // receivers
   int R;

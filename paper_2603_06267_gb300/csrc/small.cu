@@ -404,6 +404,18 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
   if (warp < npw) {
     const int b = warp / A.K, k = warp - b * A.K;
     const int M = A.M;
+    // loads that do not depend on the projection go first, so their latency
+    // overlaps the footprint gather below
+    const int n = A.n + (A.step ? *A.step : 0);
+    const long long kb = ((long long)b * A.K + k) * M;
+    const bool rx = A.rx_gain && (A.step_base ? *A.step_base : 0) + n >= A.rx_switch;
+    const double drv = (!rx && A.drive) ? A.drive[b * A.dbs + k * A.dks + n] : 0.0;
+    double q = 0.0, qd = 0.0, qdd = 0.0;
+    if (lane < M) {
+      q = A.q[kb + lane];
+      qd = A.qd[kb + lane];
+      qdd = A.qdd[kb + lane];
+    }
     double g[DG_MAXM];
 #pragma unroll
     for (int m = 0; m < DG_MAXM; ++m) g[m] = 0.0;
@@ -424,13 +436,14 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
         if (lane == m) gm = s;
       }
     }
+    // voltage of membrane k at t^n: the drive (TX) or, from step rx_switch on,
+    // the open-circuit value s / C_k sum_m eta_km q_km^n (RX, eq. ode row 2)
+    double phi = drv;
+    if (rx) phi = warp_sum((lane < M) ? A.eta[k * M + lane] * q : 0.0) * A.rx_gain[k];
     if (lane < M) {
       const int km = k * M + lane;
-      const long long idx = ((long long)b * A.K + k) * M + lane;
+      const long long idx = kb + lane;
       const double dt = A.dt;
-      const double q = A.q[idx], qd = A.qd[idx], qdd = A.qdd[idx];
-      const int n = A.n + (A.step ? *A.step : 0);
-      const double phi = A.drive ? A.drive[b * A.dbs + k * A.dks + n] : 0.0;
       const double qn = q + dt * qd + 0.5 * dt * dt * qdd;          // predictor
       const double qdp = qd + 0.5 * dt * qdd;
       const double qddn = -A.omega2[km] * qn - A.twozw[km] * qdp + (gm + A.eta[km] * phi) * A.inv_mu[km];
@@ -438,6 +451,7 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
       A.qd[idx] = qdp + 0.5 * dt * qddn;                                // corrector
       A.qdd[idx] = qddn;
     }
+    if (A.volt && lane == 0) A.volt[b * A.vbs + k * A.vks + n] = phi;
     return;
   }
   const int rw = warp - npw;

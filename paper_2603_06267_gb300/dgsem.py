@@ -31,6 +31,7 @@ DGSEM_RUN_CONTINUE = 1
 
 EXPORTED = [
     "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
+    "pmut_set_receive", "dgsem_get_voltages",
     "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
@@ -73,6 +74,8 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_mesh_create.argtypes = [POINTER(MeshDesc), POINTER(vp)]
     lib.dgsem_get_dt.argtypes = [vp, POINTER(c_double), POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_set_absorbing.argtypes = [vp, c_int, vp]
+    lib.pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
+    lib.dgsem_get_voltages.argtypes = [vp, vp, c_size_t]
     lib.dgsem_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
     lib.dgsem_pmut_nodes.argtypes = [vp, POINTER(c_int), POINTER(POINTER(c_double))]
     lib.pmut_array_set.argtypes = [vp, c_int, c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -178,6 +181,20 @@ def dgsem_set_absorbing(ctx, box: int, sides):
     arr = np.ascontiguousarray([1 if v else 0 for v in sides], dtype=np.int32)
     assert arr.shape == (6,)
     _check(_lib.dgsem_set_absorbing(ctx, box, _ptr(arr)), "dgsem_set_absorbing")
+
+
+def pmut_set_receive(ctx, n_switch: int, capacitance=None, sign: int = -1):
+    """TX -> RX switch: from step n_switch on, phi_k = sign / C_k sum_m eta_km q_km
+    (n_switch < 0: transmit only)."""
+    cap = None if capacitance is None else np.ascontiguousarray(capacitance, dtype=np.float64)
+    _check(_lib.pmut_set_receive(ctx, int(n_switch), _ptr(cap), int(sign)), "pmut_set_receive")
+
+
+def dgsem_get_voltages(ctx, batch: int, n_pmut: int, nsteps: int):
+    """[batch, n_pmut, nsteps] voltages used by the last dgsem_run."""
+    out = np.zeros((batch, n_pmut, nsteps))
+    _check(_lib.dgsem_get_voltages(ctx, _ptr(out), out.size), "dgsem_get_voltages")
+    return out
 
 
 def dgsem_get_dt(ctx):
@@ -342,6 +359,9 @@ class Solver:
         self.K = 0
         if workload.pmuts is not None:
             self.set_pmuts(workload.pmuts)
+            if getattr(workload, "rx_switch", None) is not None:
+                cap = np.broadcast_to(np.asarray(workload.rx_capacitance, dtype=np.float64), (self.K,))
+                pmut_set_receive(self.ctx, workload.rx_switch, cap, workload.rx_sign)
 
     def set_pmuts(self, pm):
         xy = dgsem_pmut_nodes(self.ctx)
