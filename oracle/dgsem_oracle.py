@@ -13,6 +13,22 @@ Paper passages followed (arXiv 2603.06267):
     rx_switch on, phi_k^n = s / C_k sum_m eta_km q_km^n with the modal
     coordinates of step n (the q that Algorithm 1's PMUT solve pairs with
     p^n); s = +1 is the literal equation, s = -1 the stiffening reading.
+  * perfectly matched layer, eq. (full_problem) rows 1-3 with the damping
+    profile zeta_i of Sec. 2 (zeta~ = c / l log(1/R), the layer measured
+    from its inner face).  Readings (the paper only says the scheme is
+    similar to Algorithm 1): psi in the nodal space of p; Phi element-local
+    at the GLL nodes; int (div Phi) v integrated by parts to -int Phi.grad v
+    (the natural condition is on the total flux); psi and Phi at half steps
+    like the velocity, the Phi damping by Crank-Nicolson, the alpha p' term on
+    the predicted velocity like C p'_pred:
+        psi^{n+1} = psi^{n+1/2} + dt/2 p^{n+1}
+        Phi^{n+3/2} = [(1 - dt z/2) Phi^{n+1/2}
+                       + dt c^2 ((alpha - 2 z) grad p^{n+1} + Z3 grad psi^{n+1})] / (1 + dt z/2)
+        M p''^{n+1} = f - K p^{n+1} - C p'_pred - M (beta p^{n+1} + alpha p'_pred
+                      + gamma psi^{n+1}) - G (Phi^{n+1/2} + Phi^{n+3/2}) / 2
+        psi^{n+3/2} = psi^{n+1/2} + dt p^{n+1}
+    with (G Phi)_j = sum_K sum_q w_q |J| Phi(x_q).grad psi_j(x_q); at rest
+    (or at a set initial state) psi^{1/2} = 0, Phi^{1/2} = 0.
   * first-order absorbing boundary on Gamma_ABC: the damping form d of
     eq. (Wf_4), d(w, v) = sum_F int_F c w v, giving C of eq. (semi_SEM),
     applied to the predicted velocity as in Algorithm 1.
@@ -389,6 +405,7 @@ class OracleProblem:
             self.K = (self.K + KI).tocsr()
         self.Minv = 1.0 / self.M
         self._absorbing_matrix()
+        self._pml_setup()
         self._pmut_matrix()
 
     def _assemble_volume(self):
@@ -433,6 +450,73 @@ class OracleProblem:
                                 idx[t2] = e2 * N + b
                                 C[m.node_id(*idx)] += dom.c * m.w[a] * m.w[b] * jac
         self.C = C
+
+    def _pml_setup(self):
+        """Damping profiles zeta_d at every node, the node coefficients
+        alpha, beta, gamma, and per PML element its node ids, GLL gradient
+        matrix, quadrature weights and zeta at its nodes."""
+        self.pml = None
+        zeta = np.zeros((3, self.nh))
+        elems = []
+        for dom, m in zip(self.w.domains, self.meshes):
+            th = getattr(dom, "pml", (0.0,) * 6)
+            if not any(t > 0 for t in th):
+                continue
+            R = float(getattr(dom, "pml_R", 1e-4))
+            x = m.all_coordinates()
+            ids_all = np.arange(m.offset, m.offset + m.nnode)
+            for d in range(3):
+                lo = m.origin[d]
+                hi = lo + m.ne[d] * m.h[d]
+                for side, t in ((0, th[2 * d]), (1, th[2 * d + 1])):
+                    if t <= 0:
+                        continue
+                    zt = m.c / t * math.log(1.0 / R)
+                    s = (lo + t - x[d]) / t if side == 0 else (x[d] - (hi - t)) / t
+                    s = np.clip(s, 0.0, 1.0)
+                    zeta[d, ids_all] += zt * (s - np.sin(2 * math.pi * s) / (2 * math.pi))
+            # GLL gradient matrix of the reference element at its own nodes
+            N = m.N
+            xi, w = m.xi, m.w
+            P, Q, Rr = np.meshgrid(xi, xi, xi, indexing="ij")
+            pts = np.stack([P.transpose(2, 1, 0).ravel(), Q.transpose(2, 1, 0).ravel(),
+                            Rr.transpose(2, 1, 0).ravel()], axis=1)
+            WP, WQ, WR = np.meshgrid(w, w, w, indexing="ij")
+            wq = (WP * WQ * WR).transpose(2, 1, 0).ravel() * (m.h[0] * m.h[1] * m.h[2] / 8.0)
+            _, gref = reference_basis(N, xi, pts)
+            grad = gref * np.array([2.0 / m.h[d] for d in range(3)])[None, None, :]
+            for ez in range(m.ne[2]):
+                for ey in range(m.ne[1]):
+                    for ex in range(m.ne[0]):
+                        ids = m.element_nodes(ex, ey, ez)
+                        if np.any(zeta[:, ids] != 0.0):
+                            elems.append((ids, grad, wq, m.c ** 2))
+        if not elems:
+            return
+        z1, z2, z3 = zeta
+        self.pml = dict(zeta=zeta, alpha=z1 + z2 + z3, beta=z1 * z2 + z2 * z3 + z3 * z1, gamma=z1 * z2 * z3,
+                        elems=elems)
+
+    def _pml_step(self, Phi, psi_half, p_new, dt):
+        """Phi^{n+1/2} -> Phi^{n+3/2} on every PML element and the residual
+        G (Phi^{n+1/2} + Phi^{n+3/2}) / 2; psi^{n+1} = psi^{n+1/2} + dt/2 p^{n+1}."""
+        zeta = self.pml["zeta"]
+        psi_int = psi_half + 0.5 * dt * p_new
+        r = np.zeros_like(p_new)
+        new = []
+        for (ids, grad, wq, c2), F in zip(self.pml["elems"], Phi):
+            z = zeta[:, ids]                                   # [3, nq]
+            al = z.sum(axis=0)
+            Z3 = np.stack([z[1] * z[2], z[2] * z[0], z[0] * z[1]])
+            gp = np.einsum("qid,ib->dqb", grad, p_new[ids])
+            gs = np.einsum("qid,ib->dqb", grad, psi_int[ids])
+            Fn = ((1.0 - 0.5 * dt * z)[:, :, None] * F
+                  + dt * c2 * ((al[None, :] - 2.0 * z)[:, :, None] * gp + Z3[:, :, None] * gs)) \
+                / (1.0 + 0.5 * dt * z)[:, :, None]
+            Fm = 0.5 * (F + Fn)
+            np.add.at(r, ids, np.einsum("q,qid,dqb->ib", wq, grad, Fm))
+            new.append(Fn)
+        return new, psi_int, r
 
     def face_nodes(self):
         """Ids and (x, y) of the GLL nodes on the z = origin face of the
@@ -523,7 +607,10 @@ class OracleProblem:
         cmax = max(m.c for m in self.meshes)
         hmin = min(min(m.h) / 2.0 * float(np.min(np.diff(m.xi))) for m in self.meshes)
         dt = cfl * hmin / cmax
-        sigma = float(np.max(self.C * self.Minv))
+        damp = self.C * self.Minv
+        if self.pml is not None:
+            damp = damp + self.pml["alpha"]
+        sigma = float(np.max(damp))
         if sigma > 0.0:
             dt = min(dt, 1.0 / sigma)
         return dt
@@ -568,6 +655,11 @@ class OracleProblem:
             if v0 is not None:
                 pd = np.array(v0, dtype=np.float64).reshape(self.nh, -1) * np.ones((1, B))
             pdd = self.Minv[:, None] * (-(self.K @ p) - self.C[:, None] * pd)
+            if self.pml is not None:
+                pdd = pdd - self.pml["beta"][:, None] * p - self.pml["alpha"][:, None] * pd
+        if self.pml is not None:
+            psi_half = np.zeros((self.nh, B))
+            Phi = [np.zeros((3, len(e[0]), B)) for e in self.pml["elems"]]
         traces = np.zeros((B, len(rec), S))
         energies = [] if energy else None
         Minv = self.Minv[:, None]
@@ -596,6 +688,11 @@ class OracleProblem:
             rhs = -(self.K @ p_new) - self.C[:, None] * pd_new
             if pm is not None:
                 rhs = rhs - self.kappa * (self.B @ qdd_new)
+            if self.pml is not None:
+                Phi, psi_int, r = self._pml_step(Phi, psi_half, p_new, dt)
+                rhs = rhs - self.M[:, None] * (self.pml["beta"][:, None] * p_new + self.pml["alpha"][:, None] * pd_new
+                                               + self.pml["gamma"][:, None] * psi_int) - r
+                psi_half = psi_half + dt * p_new
             pdd_new = Minv * rhs
             # acoustic corrector
             pd_new = pd_new + 0.5 * dt * pdd_new

@@ -79,7 +79,9 @@ def _shape_integrals(m: int):
 class Domain:
     """Axis-aligned box meshed by nelem hexahedra of GLL order `order`.
     absorbing: per box side (x-, x+, y-, y+, z-, z+) 1 = first-order
-    absorbing boundary (Gamma_ABC), 0 = rigid wall (Gamma_N)."""
+    absorbing boundary (Gamma_ABC), 0 = rigid wall (Gamma_N).
+    pml: per box side the thickness of a perfectly matched layer inside the
+    box along that side (0 = none), pml_R its design reflection."""
     origin: tuple
     extent: tuple
     nelem: tuple
@@ -87,6 +89,10 @@ class Domain:
     c: float = WATER_C
     rho: float = WATER_RHO
     absorbing: tuple = (0, 0, 0, 0, 0, 0)
+    # perfectly matched layer: thickness (m) per box side, 0 = none, and the
+    # design reflection coefficient R of the damping profile
+    pml: tuple = (0.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+    pml_R: float = 1.0e-4
 
 
 @dataclass
