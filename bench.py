@@ -269,12 +269,12 @@ def main():
         if dist is not None:
             dist.barrier()
         ms = e0.elapsed_time(e1)
-        launches = sum(dgsem.dgsem_kernel_stats(sol.ctx, k)[1] for k in range(4))
+        launches = sum(dgsem.dgsem_kernel_stats(sol.ctx, k)[1] for k in range(5))
         # per-kernel timing pass (CUDA events around each launch)
         dgsem.dgsem_profile(sol.ctx, True)
         sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dgsem.DGSEM_RUN_CONTINUE,
                 stream=stream.cuda_stream)
-        kstats = [dgsem.dgsem_kernel_stats(sol.ctx, k) for k in range(4)]
+        kstats = [dgsem.dgsem_kernel_stats(sol.ctx, k) for k in range(5)]
         dgsem.dgsem_profile(sol.ctx, False)
         # end to end through host buffers (pinned), copies inside the timed region
         e2e = None
@@ -303,7 +303,7 @@ def main():
         return
     value = ndof * B * args.steps * world / (ms / 1e3) / 1e9
     # roofline of the dominant kernel
-    names = ["pmut_recv", "iface", "vol_primary", "vol_secondary"]
+    names = ["pmut_recv", "iface", "vol_primary", "vol_secondary", "pml"]
     kdom = max(range(4), key=lambda k: kstats[k][0])
     es = 4 if prec == dgsem.DGSEM_FP32_MIXED else 8
     peaks = measured_peaks()
@@ -346,7 +346,7 @@ def main():
                    "tiles": [int(t) for t in tiles],
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(4)},
+        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(5) if kstats[k][1]},
         "finite": finite,
     }
     print(json.dumps(out), flush=True)

@@ -132,6 +132,29 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out);
  * from rest. */
 int dgsem_set_absorbing(dgsem_ctx* ctx, int box, const int* sides);
 
+/* Perfectly matched layer (Sec. 2, eq. full_problem rows 1-3) inside a box
+ * along its sides, with the damping profile of Sec. 2:
+ *     zeta_i(x) = zeta~ (s - sin(2 pi s) / (2 pi)),  zeta~ = c / l log(1 / R),
+ * s in [0, 1] the depth into a layer of thickness l (0 at its inner face).
+ *   box        0 = primary, 1 = secondary.
+ *   thickness  [6] layer thickness in m for the sides x-, x+, y-, y+, z-, z+
+ *              (0 = none); a layer takes the elements it overlaps.  The
+ *              primary z-min side (Gamma_PMUT) and the interface sides
+ *              cannot carry one (DGSEM_EINVAL), nor may two layers of an axis
+ *              overlap.
+ *   R          design reflection coefficient, 0 < R < 1 (the paper uses
+ *              1e-5 .. 1e-4).
+ * The auxiliary fields Phi (element-local at the GLL nodes of the layer's
+ * elements) and psi (nodal) live at half steps like the velocity; Phi's own
+ * damping is integrated by Crank-Nicolson, alpha p' acts on the predicted
+ * velocity like C p'_pred in Algorithm 1.  dt is held to
+ * min(cfl dt, 1 / max_i (C_ii/M_ii + alpha_i)) (the damping terms are
+ * explicit); a dt the caller fixed above it is refused (DGSEM_EUNSTABLE).
+ * All-zero thickness removes the layer.  The run state is re-allocated and
+ * invalidated; checkpoints (dgsem_state_save) of a box with a layer are not
+ * supported (DGSEM_ESTATE). */
+int dgsem_set_pml(dgsem_ctx* ctx, int box, const double* thickness, double R);
+
 /* Time step, stability bound and size.  dt_stable_max is 2 / sqrt(lambda_max)
  * of M^-1 K from dgsem_check_stability() (0 if it has not run); ndof counts
  * the unique GLL nodes of all boxes (dim V^DG). Any output may be NULL. */
@@ -259,7 +282,8 @@ int dgsem_autotune(dgsem_ctx* ctx, int precision, int batch, int reps, int* chos
 #define DGSEM_K_IFACE 1       /* interface fluxes on Gamma_I                   */
 #define DGSEM_K_VOL0 2        /* fused volume update of the primary box        */
 #define DGSEM_K_VOL1 3        /* fused volume update of the secondary box      */
-#define DGSEM_K_COUNT 4
+#define DGSEM_K_PML 4         /* perfectly matched layer elements (both boxes) */
+#define DGSEM_K_COUNT 5
 int dgsem_profile(dgsem_ctx* ctx, int enable);
 int dgsem_kernel_stats(const dgsem_ctx* ctx, int kind, double* total_ms, long long* launches);
 

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dgsem.h"
@@ -213,6 +214,17 @@ struct dgsem_ctx {
   void* Rb[2] = {nullptr, nullptr};
   double* q_state = nullptr;    // q | qd | qdd  [3][B*K*M]
   long long step = 0;
+  // perfectly matched layer per box
+  bool has_pml[2] = {false, false};
+  std::vector<double> zeta_h[2][3];        // host profiles zeta_d[L_d]
+  void* d_zeta[2][2][3] = {};              // [box][fp64, fp32][axis]
+  int* d_pml_slot[2] = {nullptr, nullptr}; // [ne2][ne1][ne0] slot or -1
+  int* d_pml_elem[2] = {nullptr, nullptr}; // [npml] element index
+  int npml[2] = {0, 0};
+  int pml_lo[2][3] = {}, pml_hi[2][3] = {};
+  void* Psi[2] = {nullptr, nullptr};       // psi, lattice layout (run state)
+  void* Phi[2] = {nullptr, nullptr};       // [B][npml][3][(N+1)^3] (run state)
+  void* Rpml[2] = {nullptr, nullptr};      // [B][npml][(N+1)^3] (run state)
   // TX -> RX switch of the PMUT array (off: rx_switch < 0)
   long long rx_switch = -1;
   double* d_rx_gain = nullptr;             // [K] s / C_k
@@ -242,12 +254,12 @@ struct dgsem_ctx {
   cudaEvent_t fork_ev[2] = {nullptr, nullptr};
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
-  long long graph_launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
+  long long graph_launches[DGSEM_K_COUNT] = {};
   std::vector<unsigned char> graph_key;
   // instrumentation
   bool profiling = false;
-  long long launches[DGSEM_K_COUNT] = {0, 0, 0, 0};
-  double kernel_ms[DGSEM_K_COUNT] = {0, 0, 0, 0};
+  long long launches[DGSEM_K_COUNT] = {};
+  double kernel_ms[DGSEM_K_COUNT] = {};
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, int>> ev_used;   // (kind, index of start event; stop = index + 1)
 };
@@ -290,6 +302,7 @@ void free_run_state(dgsem_ctx* c) {
   drop_graph(c);
   for (int d = 0; d < 2; ++d) {
     dfree(c->X[d]); dfree(c->Y[d]); dfree(c->V[d]); dfree(c->Ra[d]); dfree(c->Rb[d]);
+    dfree(c->Psi[d]); dfree(c->Phi[d]); dfree(c->Rpml[d]);
   }
   dfree(c->q_state);
   c->prec = -1;
@@ -353,6 +366,15 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
       CUDA_TRY(cudaMemset(c->Ra[d], 0, rb));
       CUDA_TRY(cudaMemset(c->Rb[d], 0, rb));
     }
+    if (c->has_pml[d]) {
+      const Box& B = c->box[d];
+      const size_t nl = (size_t)(B.N + 1) * (B.N + 1) * (B.N + 1);
+      const size_t fb = (size_t)batch * c->npml[d] * 3 * nl * es, rb = (size_t)batch * c->npml[d] * nl * es;
+      if ((rc = dalloc(&c->Psi[d], bytes)) || (rc = dalloc(&c->Phi[d], fb)) || (rc = dalloc(&c->Rpml[d], rb))) {
+        free_run_state(c);
+        return rc;
+      }
+    }
   }
   if (c->K > 0) {
     int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
@@ -393,6 +415,13 @@ int zero_state(dgsem_ctx* c, cudaStream_t s) {
   }
   if (c->q_state)
     CUDA_TRY(cudaMemsetAsync(c->q_state, 0, (size_t)3 * c->batch * c->K * c->M * sizeof(double), s));
+  for (int d = 0; d < c->nd; ++d) {
+    if (!c->has_pml[d]) continue;
+    const Box& B = c->box[d];
+    const size_t nl = (size_t)(B.N + 1) * (B.N + 1) * (B.N + 1);
+    CUDA_TRY(cudaMemsetAsync(c->Psi[d], 0, (size_t)c->batch * B.bstride * es, s));
+    CUDA_TRY(cudaMemsetAsync(c->Phi[d], 0, (size_t)c->batch * c->npml[d] * 3 * nl * es, s));
+  }
   c->step = 0;
   return DGSEM_OK;
 }
@@ -693,6 +722,36 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     CUDA_TRY(launch_iface<T>(a, c->batch, s));
   }
   if (fork) CUDA_TRY(cudaStreamWaitEvent(s, c->fork_ev[1], 0));
+  // perfectly matched layers: Phi update and element residuals (read p^{n+1}, psi^{n+1/2})
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  for (int d = 0; d < c->nd && !init; ++d) {
+    if (!c->has_pml[d]) continue;
+    const Box& B = c->box[d];
+    const int nl = (B.N + 1) * (B.N + 1) * (B.N + 1);
+    PmlArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = static_cast<const T*>(pin[d]);
+    a.psi = static_cast<const T*>(c->Psi[d]);
+    a.phi = static_cast<T*>(c->Phi[d]);
+    a.r = static_cast<T*>(c->Rpml[d]);
+    a.elem = c->d_pml_elem[d];
+    a.npml = c->npml[d]; a.N = B.N; a.ne0 = B.ne[0]; a.ne1 = B.ne[1];
+    a.py = B.py; a.pz = B.pz; a.bstride = B.bstride;
+    a.phi_bs = (long long)c->npml[d] * 3 * nl; a.r_bs = (long long)c->npml[d] * nl;
+    for (int ax = 0; ax < 3; ++ax) {
+      a.zeta[ax] = static_cast<const T*>(c->d_zeta[d][pi][ax]);
+      a.g[ax] = T(2.0 / B.h[ax]);
+    }
+    for (int i = 0; i <= B.N; ++i) {
+      a.w[i] = T(B.basis->w[i]);
+      for (int j = 0; j <= B.N; ++j) a.D[i][j] = T(B.basis->D[i * (B.N + 1) + j]);
+    }
+    a.detJ = T(B.h[0] * B.h[1] * B.h[2] / 8.0);
+    a.c2 = T(B.c * B.c);
+    a.dt = T(c->dt);
+    LaunchTimer lt(c, s, DGSEM_K_PML);
+    CUDA_TRY(launch_pml<T>(a, c->batch, s));
+  }
   for (int d = 0; d < c->nd; ++d) {
     VolSpec v = c->vspec[d];
     v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
@@ -704,6 +763,20 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     v.dtv = init ? 0.5 * c->dt : c->dt;
     v.dtp = c->dt;
     v.Ra = c->Ra[d]; v.Rb = c->Rb[d];
+    if (c->has_pml[d]) {
+      const Box& B = c->box[d];
+      v.has_pml = 1;
+      v.pml_init = init ? 1 : 0;
+      for (int ax = 0; ax < 3; ++ax) {
+        v.zeta[ax] = c->d_zeta[d][pi][ax];
+        v.pml_lo[ax] = c->pml_lo[d][ax];
+        v.pml_hi[ax] = c->pml_hi[d][ax];
+      }
+      v.psi = c->Psi[d];
+      v.rpml = c->Rpml[d];
+      v.pml_slot = c->d_pml_slot[d];
+      v.rpml_bs = (long long)c->npml[d] * (B.N + 1) * (B.N + 1) * (B.N + 1);
+    }
     if (d == 0 && c->K > 0 && !init) {
       v.has_pmut = 1;
       v.node_ptr = c->d_node_ptr; v.node_ent = c->d_node_ent; v.ent_pmut = c->d_ent_pmut;
@@ -1153,6 +1226,48 @@ int dgsem_mesh_create(const dgsem_mesh_desc* desc, dgsem_ctx** out) {
   return DGSEM_OK;
 }
 
+namespace {
+
+// Largest damping rate C_ii/M_ii + alpha_i over the nodes of a box: the sum
+// is separable (one term per axis), so its maximum is the sum of the axis
+// maxima.
+double box_damping_max(const Box& B, const double* abc, const std::vector<double>* zeta) {
+  double tot = 0.0;
+  for (int ax = 0; ax < 3; ++ax) {
+    double m = 0.0;
+    for (int i = 0; i < B.L[ax]; ++i) {
+      double v = (zeta && !zeta[ax].empty()) ? zeta[ax][i] : 0.0;
+      if (i == 0) v += abc[2 * ax];
+      if (i == B.L[ax] - 1) v += abc[2 * ax + 1];
+      m = std::max(m, v);
+    }
+    tot += m;
+  }
+  return tot;
+}
+
+// dt limit of the explicit damping terms: dt <= 1 / sigma over all boxes;
+// box `box` takes the candidate abc / zeta.  Returns the new dt, or -1 if the
+// caller fixed a dt above it.
+double damped_dt(const dgsem_ctx* c, int box, const double* abc, const std::vector<double>* zeta) {
+  double sigma = 0.0;
+  for (int d = 0; d < c->nd; ++d)
+    sigma = std::max(sigma, d == box ? box_damping_max(c->box[d], abc, zeta)
+                                     : box_damping_max(c->box[d], c->vspec[d].abc, c->has_pml[d] ? c->zeta_h[d] : nullptr));
+  double dt = c->dt_cfl;
+  if (sigma > 0.0) dt = std::min(dt, 1.0 / sigma);
+  if (c->dt_fixed && dt < c->dt_cfl) return -1.0;
+  return dt;
+}
+
+// physical coordinate of lattice line i along axis ax of box B
+double lattice_coord(const Box& B, int ax, int i) {
+  const int e = std::min(i / B.N, B.ne[ax] - 1), a = i - e * B.N;
+  return B.o[ax] + B.h[ax] * (e + 0.5 * (B.basis->x[a] + 1.0));
+}
+
+}  // namespace
+
 int dgsem_set_absorbing(dgsem_ctx* c, int box, const int* sides) {
   if (!c || !sides) return fail(DGSEM_EINVAL, "NULL argument");
   if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "bad box %d", box);
@@ -1165,30 +1280,95 @@ int dgsem_set_absorbing(dgsem_ctx* c, int box, const int* sides) {
   }
   double abc[6];
   for (int s = 0; s < 6; ++s) abc[s] = sides[s] ? B.c * (2.0 / B.h[s / 2]) / B.basis->w[0] : 0.0;
-  // largest C_ii / M_ii of any node: the corner where the most absorbing sides meet
-  double sigma = 0.0;
-  for (int d = 0; d < c->nd; ++d) {
-    double sd = 0.0;
-    for (int ax = 0; ax < 3; ++ax) {
-      const double lo = d == box ? abc[2 * ax] : c->vspec[d].abc[2 * ax];
-      const double hi = d == box ? abc[2 * ax + 1] : c->vspec[d].abc[2 * ax + 1];
-      sd += std::max(lo, hi);
-    }
-    sigma = std::max(sigma, sd);
-  }
-  double dt = c->dt_cfl;
-  if (sigma > 0.0) dt = std::min(dt, 1.0 / sigma);
-  if (c->dt_fixed && dt < c->dt_cfl)
-    return fail(DGSEM_EUNSTABLE, "dt = %.4e s exceeds 1 / max(C/M) = %.4e s of the absorbing sides", c->dt_cfl, dt);
+  const double dt = damped_dt(c, box, abc, c->has_pml[box] ? c->zeta_h[box] : nullptr);
+  if (dt < 0.0)
+    return fail(DGSEM_EUNSTABLE, "dt = %.4e s exceeds the limit 1 / max(C/M + alpha) of the damping terms", c->dt_cfl);
   for (int s = 0; s < 6; ++s) c->vspec[box].abc[s] = abc[s];
   c->vspec[box].has_abc = 0;
   for (int s = 0; s < 6; ++s) c->vspec[box].has_abc |= sides[s] ? 1 : 0;
   c->dt = dt;
   // the captured step graph holds the old parameters, and the state's half-step
   // velocity belongs to the old dt
-  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
-  c->graph_key.clear();
+  drop_graph(c);
   c->state_valid = false;
+  return DGSEM_OK;
+}
+
+int dgsem_set_pml(dgsem_ctx* c, int box, const double* thickness, double R) {
+  if (!c || !thickness) return fail(DGSEM_EINVAL, "NULL argument");
+  if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "bad box %d", box);
+  const Box& B = c->box[box];
+  bool any = false;
+  for (int s = 0; s < 6; ++s) {
+    if (!(thickness[s] >= 0.0) || !std::isfinite(thickness[s])) return fail(DGSEM_EINVAL, "thickness[%d] must be >= 0", s);
+    if (thickness[s] == 0.0) continue;
+    any = true;
+    if (box == 0 && s == 4) return fail(DGSEM_EINVAL, "the primary z-min side carries Gamma_PMUT");
+    if (c->nd == 2 && ((box == 0 && s == 5) || (box == 1 && s == 4)))
+      return fail(DGSEM_EINVAL, "box %d side %d is the interface Gamma_I", box, s);
+  }
+  if (any && !(R > 0.0 && R < 1.0)) return fail(DGSEM_EINVAL, "R must lie in (0, 1)");
+  int lo[3], hi[3];
+  std::vector<double> zeta[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    const double tl = thickness[2 * ax], th = thickness[2 * ax + 1];
+    if (tl + th > B.ext[ax] * (1.0 + 1e-12)) return fail(DGSEM_EINVAL, "the layers of axis %d overlap", ax);
+    lo[ax] = tl > 0.0 ? (int)std::ceil(tl / B.h[ax] - 1e-9) : 0;
+    hi[ax] = th > 0.0 ? (int)std::ceil(th / B.h[ax] - 1e-9) : 0;
+    zeta[ax].assign(B.L[ax], 0.0);
+    const double x0 = B.o[ax], x1 = B.o[ax] + B.ext[ax];
+    for (int i = 0; i < B.L[ax]; ++i) {
+      const double x = lattice_coord(B, ax, i);
+      for (int side = 0; side < 2; ++side) {
+        const double t = side == 0 ? tl : th;
+        if (t <= 0.0) continue;
+        const double zt = B.c / t * std::log(1.0 / R);
+        double sd = side == 0 ? (x0 + t - x) / t : (x - (x1 - t)) / t;
+        sd = std::min(1.0, std::max(0.0, sd));
+        zeta[ax][i] += zt * (sd - std::sin(2.0 * M_PI * sd) / (2.0 * M_PI));
+      }
+    }
+  }
+  const double dt = damped_dt(c, box, c->vspec[box].abc, any ? zeta : nullptr);
+  if (dt < 0.0)
+    return fail(DGSEM_EUNSTABLE, "dt = %.4e s exceeds the limit 1 / max(C/M + alpha) of the damping terms", c->dt_cfl);
+  // layer elements: any axis index inside that axis' layers
+  std::vector<int> slot((size_t)B.ne[0] * B.ne[1] * B.ne[2], -1), elem;
+  if (any) {
+    for (int ez = 0; ez < B.ne[2]; ++ez)
+      for (int ey = 0; ey < B.ne[1]; ++ey)
+        for (int ex = 0; ex < B.ne[0]; ++ex) {
+          const bool in = ex < lo[0] || ex >= B.ne[0] - hi[0] || ey < lo[1] || ey >= B.ne[1] - hi[1] ||
+                          ez < lo[2] || ez >= B.ne[2] - hi[2];
+          if (!in) continue;
+          const int el = ex + B.ne[0] * (ey + B.ne[1] * ez);
+          slot[el] = (int)elem.size();
+          elem.push_back(el);
+        }
+  }
+  // replace the layer of this box
+  free_run_state(c);
+  dfree(c->d_pml_slot[box]); dfree(c->d_pml_elem[box]);
+  for (int p = 0; p < 2; ++p)
+    for (int ax = 0; ax < 3; ++ax) dfree(c->d_zeta[box][p][ax]);
+  c->has_pml[box] = false;
+  c->npml[box] = 0;
+  for (int ax = 0; ax < 3; ++ax) c->zeta_h[box][ax].clear();
+  c->dt = dt;
+  c->state_valid = false;
+  if (!any) return DGSEM_OK;
+  int rc;
+  if ((rc = upload(&c->d_pml_slot[box], slot)) || (rc = upload(&c->d_pml_elem[box], elem))) return rc;
+  for (int ax = 0; ax < 3; ++ax) {
+    std::vector<float> zf(zeta[ax].begin(), zeta[ax].end());
+    if ((rc = upload((double**)&c->d_zeta[box][0][ax], zeta[ax])) || (rc = upload((float**)&c->d_zeta[box][1][ax], zf)))
+      return rc;
+    c->zeta_h[box][ax] = zeta[ax];
+    c->pml_lo[box][ax] = lo[ax];
+    c->pml_hi[box][ax] = hi[ax];
+  }
+  c->npml[box] = (int)elem.size();
+  c->has_pml[box] = true;
   return DGSEM_OK;
 }
 
@@ -1407,6 +1587,7 @@ struct CkptHeader {
 int dgsem_state_save(const dgsem_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return fail(DGSEM_EINVAL, "NULL argument");
   if (!c->state_valid) return fail(DGSEM_ESTATE, "no state to save");
+  if (c->has_pml[0] || c->has_pml[1]) return fail(DGSEM_ESTATE, "checkpoints of a state with a PML are not supported");
   const size_t es = elem_size(c->prec);
   size_t need = sizeof(CkptHeader);
   for (int d = 0; d < c->nd; ++d) need += 3 * (size_t)c->batch * c->box[d].bstride * es;
@@ -1666,6 +1847,11 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_err);
   dfree(c->d_step);
   dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
+  for (int d = 0; d < 2; ++d) {
+    dfree(c->d_pml_slot[d]); dfree(c->d_pml_elem[d]);
+    for (int p = 0; p < 2; ++p)
+      for (int ax = 0; ax < 3; ++ax) dfree(c->d_zeta[d][p][ax]);
+  }
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   for (cudaEvent_t e : c->fork_ev)

@@ -67,6 +67,16 @@ struct VolArgs {
   // side (x-, x+, y-, y+, z-, z+), 0 = rigid; a -= sigma v on those nodes
   T abc[6];
   int has_abc;
+  // perfectly matched layer (eq. full_problem rows 1-3): on the nodes of the
+  // layer's elements a -= beta p + alpha v + gamma psi^{n+1} + M^-1 (G Phi)
+  // and psi^{n+3/2} = psi^{n+1/2} + dt p^{n+1}
+  int has_pml, pml_init;           // pml_init: initial half step (no psi, no G Phi)
+  const T* zeta[3];                // per-axis profiles zeta_d[L_d]
+  T* psi;                          // psi at half steps, lattice layout
+  const T* rpml;                   // [B][npml][(N+1)^3] G Phi^{n+1} per layer element
+  const int* pml_slot;             // [ne2][ne1][ne0] slot in rpml, -1 outside the layer
+  long long rpml_bs;               // batch stride of rpml
+  int pml_lo[3], pml_hi[3];        // layer elements per axis at the low / high side
   // FP32 tables for packed f32x2 arithmetic: x rows with their taps in pairs
   // (q = 2k, 2k+1), y and z coefficients repeated in both lanes
   float2 cxq[N + 1][(N + 1) / 2];
@@ -103,6 +113,27 @@ struct IfaceArgs {
   T* Rap; T* Rbp;                  // [B][npx*npy][(Np+1)^2]
   T* Ras; T* Rbs;                  // [B][nsx*nsy][(Ns+1)^2]
   long long rbp, rbs;              // batch strides of the residual arrays
+};
+
+// ---------------------------------------------------------------------------
+// Perfectly matched layer, one CTA per (layer element, batch member): Phi
+// update at the element's GLL nodes and the element residual G Phi^{n+1}.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PmlArgs {
+  const T* p;                      // p^{n+1}, lattice layout
+  const T* psi;                    // psi^{n+1/2}, lattice layout
+  T* phi;                          // [B][npml][3][(N+1)^3] Phi at half steps, updated in place
+  T* r;                            // [B][npml][(N+1)^3] G (Phi^{n+1/2} + Phi^{n+3/2}) / 2
+  const int* elem;                 // [npml] element ex + ne0 * (ey + ne1 * ez)
+  int npml, N, ne0, ne1;
+  int py; long long pz, bstride;
+  long long phi_bs, r_bs;
+  const T* zeta[3];
+  T D[DG_MAXN + 1][DG_MAXN + 1];   // D[i][j] = l_j'(xi_i) of the GLL basis
+  T w[DG_MAXN + 1];                // GLL weights
+  T g[3];                          // 2 / h_d
+  T detJ, c2, dt;
 };
 
 // ---------------------------------------------------------------------------
@@ -174,6 +205,14 @@ struct VolSpec {
   // node on that side, c (2/h_d) / w_0; 0 = rigid wall
   double abc[6];
   int has_abc;
+  // perfectly matched layer (see VolArgs); pointers in the state precision
+  int has_pml, pml_init;
+  const void* zeta[3];
+  void* psi;
+  const void* rpml;
+  const int* pml_slot;
+  long long rpml_bs;
+  int pml_lo[3], pml_hi[3];
   int layers_per_cta;              // 0: choose automatically
   int tile;                        // tile-shape variant (see vol_impl.cuh)
 };
@@ -186,18 +225,22 @@ int vol_tma_box_f32(int N, int tile, unsigned box[3], unsigned vbox[3]);
 int vol_tma_box_f64(int N, int tile, unsigned box[3], unsigned vbox[3]);
 
 // Launchers (defined in the kernel translation units)
-// (one instantiation per precision and absorbing-side flag, each in its own
-// translation unit; the flag removes the absorbing term from boxes without one)
+// (one instantiation per precision and open-boundary flag, each in its own
+// translation unit; the flag removes the absorbing-side and PML terms from
+// boxes without them)
 template <typename T, bool ABC>
 cudaError_t launch_vol_flag(const VolSpec& spec, int batch, cudaStream_t s);
 template <typename T>
 inline cudaError_t launch_vol(const VolSpec& spec, int batch, cudaStream_t s) {
-  return spec.has_abc ? launch_vol_flag<T, true>(spec, batch, s) : launch_vol_flag<T, false>(spec, batch, s);
+  return (spec.has_abc || spec.has_pml) ? launch_vol_flag<T, true>(spec, batch, s)
+                                         : launch_vol_flag<T, false>(spec, batch, s);
 }
 template <typename T>
 cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pml(const PmlArgs<T>& a, int batch, cudaStream_t s);
 // power-iteration helpers (FP64)
 cudaError_t launch_mdot(const double* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
                         int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s);

@@ -463,6 +463,55 @@ __device__ __forceinline__ void carry_reg_f32(const VolArgs<float, N>& A, const 
   if constexpr (N % 2 == 1) carry[N - 1] = cT;
 }
 
+// Perfectly matched layer.  Does lattice index i (along an axis of ne
+// elements) belong to an element of the layer (lo elements at the low side,
+// hi at the high side)?
+template <int N>
+__device__ __forceinline__ bool pml_axis(int i, int ne, int lo, int hi) {
+  const int e1 = min(i / N, ne - 1);
+  const int e0 = (i % N == 0 && i > 0) ? i / N - 1 : e1;
+  return e0 < lo || e1 >= ne - hi;
+}
+
+// PML part of the acceleration at node (i, j, k) of batch member b (a node of
+// a layer element): beta p + alpha v + gamma psi^{n+1} + M^-1 sum_K (G Phi)_K,
+// with psi^{n+1} = psi^{n+1/2} + dt/2 p, and psi^{n+3/2} = psi^{n+1/2} + dt p
+// written back.  The initial half step has psi^{1/2} = 0 and Phi^{1/2} = 0:
+// only beta p + alpha v.
+template <typename T, int N>
+__device__ __noinline__ T pml_terms(const VolArgs<T, N>& A, int i, int j, int k, int b, T p, T v, T minv) {
+  constexpr int NP = N + 1, NL = NP * NP * NP;
+  const T zx = A.zeta[0][i], zy = A.zeta[1][j], zz = A.zeta[2][k];
+  T acc = (zx * zy + zy * zz + zz * zx) * p + (zx + zy + zz) * v;
+  if (A.pml_init) return acc;
+  const long long g = (long long)b * A.bstride + (long long)k * A.pz + (long long)j * A.py + i;
+  const T ph = A.psi[g];
+  acc += zx * zy * zz * (ph + T(0.5) * A.dtp * p);
+  A.psi[g] = ph + A.dtp * p;
+  // the node's elements along each axis (two at an element boundary)
+  int ex[2], ax[2], ey[2], ay[2], ez[2], az[2];
+  auto split = [](int idx, int ne, int* e, int* a) {
+    int n = 0;
+    if (idx % N == 0) {
+      if (idx / N - 1 >= 0) { e[n] = idx / N - 1; a[n] = N; ++n; }
+      if (idx / N < ne) { e[n] = idx / N; a[n] = 0; ++n; }
+    } else {
+      e[n] = idx / N; a[n] = idx % N; ++n;
+    }
+    return n;
+  };
+  const int nx = split(i, A.ne0, ex, ax), ny = split(j, A.ne1, ey, ay), nz = split(k, A.ne2, ez, az);
+  const T* R = A.rpml + (long long)b * A.rpml_bs;
+  T r = T(0);
+  for (int c = 0; c < nz; ++c)
+    for (int q = 0; q < ny; ++q)
+      for (int t = 0; t < nx; ++t) {
+        const int slot = A.pml_slot[((long long)ez[c] * A.ne1 + ey[q]) * A.ne0 + ex[t]];
+        if (slot >= 0) r += R[(long long)slot * NL + (az[c] * NP + ay[q]) * NP + ax[t]];
+      }
+  return acc + minv * r;
+}
+
 // Row of the tile handled by thread row ty: the TYE vertex rows (element
 // boundaries, two-element y stencil) come first so that they fill their own
 // warps and the y stencil does not diverge inside a warp.
@@ -480,7 +529,7 @@ __device__ __forceinline__ int tile_row(int ty) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool ABC>
+template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN>
 __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
   using G = Geo<T, N, TXE, TYE, PG>;
   static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
@@ -538,8 +587,9 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
   const bool xl = ex > 0;
   const T mscale = T(A.minv_scale);        // 8 / (hx hy hz): M^-1 = mscale / (w_a w_b w_c)
   // absorbing sides: C_ii / M_ii of this row's y sides and of the box's x-min node
-  const T abc_y = ABC ? ((j == 0 ? A.abc[2] : T(0)) + (j == A.L1 - 1 ? A.abc[3] : T(0))) : T(0);
-  const T abc_x0 = (ABC && ex == 0) ? A.abc[0] : T(0);
+  const T abc_y = OPEN ? ((j == 0 ? A.abc[2] : T(0)) + (j == A.L1 - 1 ? A.abc[3] : T(0))) : T(0);
+  const T abc_x0 = (OPEN && ex == 0) ? A.abc[0] : T(0);
+  const bool pml_y = OPEN && A.has_pml && pml_axis<N>(j, A.ne1, A.pml_lo[1], A.pml_hi[1]);
   auto abc_plane = [&](int k) {   // y and z sides of the nodes of plane k
     return abc_y + (k == 0 ? A.abc[4] : T(0)) + (k == A.L2 - 1 ? A.abc[5] : T(0));
   };
@@ -629,13 +679,23 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       // FP32 update of the N owned nodes of plane k from sm = M^-1 K p:
       // a = -sm (+ PMUT / interface terms), v += dtv a, p_out = p + dtp v
       auto commit_f32 = [&](int k, const T* vcur, const T* self, float* sm, T iw_z, T* vn, T* pn) {
-        if constexpr (ABC) {
+        if constexpr (OPEN) {
           // absorbing sides (eq. Wf_4): a -= C/M v with v the predicted velocity v^{n+1/2}
           const T sg = abc_plane(k);
           if (sg != T(0) || abc_x0 != T(0)) {
             sm[0] += (sg + abc_x0) * vcur[0];
 #pragma unroll
             for (int a = 1; a < N; ++a) sm[a] += sg * vcur[a];
+          }
+          if (A.has_pml) {
+            const bool yz = pml_y || pml_axis<N>(k, A.ne2, A.pml_lo[2], A.pml_hi[2]);
+            for (int a = 0; a < N; ++a) {
+              const int i = ex * N + a;
+              if (yz || pml_axis<N>(i, A.ne0, A.pml_lo[0], A.pml_hi[0])) {
+                const T minv = mscale * ((a == 0) ? xiw : A.iwa[a]) * iw_y * iw_z;
+                sm[a] += pml_terms<T, N>(A, i, j, k, b, self[a], vcur[a], minv);
+              }
+            }
           }
         }
         if (extras_layer && plane_extras(k)) {
@@ -763,11 +823,18 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
             for (int a = 0; a < N; ++a) zs[a] *= iw_z;
           }
           // update: a = -(M^-1 K p) - C/M v (+ extras), v += dtv a, p_out = p + dtp v
-          const T sg = ABC ? abc_plane(k) : T(0);
+          const T sg = OPEN ? abc_plane(k) : T(0);
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             T accum = -(acc[a] + zs[a]);
-            if constexpr (ABC) accum -= (sg + (a == 0 ? abc_x0 : T(0))) * vcur[a];
+            if constexpr (OPEN) {
+              accum -= (sg + (a == 0 ? abc_x0 : T(0))) * vcur[a];
+              if (A.has_pml && (pml_y || pml_axis<N>(k, A.ne2, A.pml_lo[2], A.pml_hi[2]) ||
+                                pml_axis<N>(ex * N + a, A.ne0, A.pml_lo[0], A.pml_hi[0]))) {
+                const T minv = mscale * ((a == 0) ? xiw : A.iwa[a]) * iw_y * iw_z;
+                accum -= pml_terms<T, N>(A, ex * N + a, j, k, b, xr[N + a], vcur[a], minv);
+              }
+            }
             if (extras_layer && plane_extras(k)) {
               const T iw_x = (a == 0) ? xiw : A.iwa[a];
               const T minv = mscale * iw_x * iw_y * iw_z;
@@ -832,7 +899,10 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
         T vo;
         if constexpr (VTMA) vo = (c < N) ? V0[c * VPLANE + vown + N] : *vp;
         else vo = *vp;
-        if constexpr (ABC) accum -= (abc_plane(k) + A.abc[1]) * vo;
+        if constexpr (OPEN) {
+          accum -= (abc_plane(k) + A.abc[1]) * vo;
+          if (A.has_pml) accum -= pml_terms<T, N>(A, ex * N + N, j, k, b, P[col], vo, mscale * A.iwb * iw_y * iw_z);
+        }
         const T vn = vo + A.dtv * accum;
         *vp = vn;
         pout[(long long)k * A.pz + grow + N] = P[col] + A.dtp * vn;
@@ -918,6 +988,17 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   }
   for (int q = 0; q < 6; ++q) a.abc[q] = T(s.abc[q]);
   a.has_abc = s.has_abc;
+  a.has_pml = s.has_pml;
+  a.pml_init = s.pml_init;
+  for (int d = 0; d < 3; ++d) {
+    a.zeta[d] = static_cast<const T*>(s.zeta[d]);
+    a.pml_lo[d] = s.pml_lo[d];
+    a.pml_hi[d] = s.pml_hi[d];
+  }
+  a.psi = static_cast<T*>(s.psi);
+  a.rpml = static_cast<const T*>(s.rpml);
+  a.pml_slot = s.pml_slot;
+  a.rpml_bs = s.rpml_bs;
   a.iwv = T(s.iwv); a.iwb = T(s.iwb);
   a.minv_scale = s.minv_scale;
   a.has_pmut = s.has_pmut;
@@ -928,7 +1009,7 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   return a;
 }
 
-template <typename T, int N, int V, bool ABC>
+template <typename T, int N, int V, bool OPEN>
 cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   using SH = typename TileShape<T, N, V>::S;
   constexpr int TXE = SH::TXE, TYE = SH::TYE, PG = SH::PG;
@@ -947,7 +1028,7 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, ABC>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, OPEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
@@ -956,22 +1037,22 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int N, bool ABC>
+template <typename T, int N, bool OPEN>
 cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
   if constexpr (NumShapes<T, N>::value > 1) {
     switch (s.tile) {
-      case 0: return launch_v<T, N, 0, ABC>(s, batch, st);
-      case 1: return launch_v<T, N, 1, ABC>(s, batch, st);
-      case 2: return launch_v<T, N, 2, ABC>(s, batch, st);
-      case 3: return launch_v<T, N, 3, ABC>(s, batch, st);
-      case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4, ABC>(s, batch, st); break;
-      case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5, ABC>(s, batch, st); break;
+      case 0: return launch_v<T, N, 0, OPEN>(s, batch, st);
+      case 1: return launch_v<T, N, 1, OPEN>(s, batch, st);
+      case 2: return launch_v<T, N, 2, OPEN>(s, batch, st);
+      case 3: return launch_v<T, N, 3, OPEN>(s, batch, st);
+      case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4, OPEN>(s, batch, st); break;
+      case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5, OPEN>(s, batch, st); break;
       default: break;
     }
     return cudaErrorInvalidValue;
   } else {
     if (s.tile != 0) return cudaErrorInvalidValue;
-    return launch_v<T, N, 0, ABC>(s, batch, st);
+    return launch_v<T, N, 0, OPEN>(s, batch, st);
   }
 }
 
@@ -1025,18 +1106,18 @@ int tma_box(int N, int tile, unsigned box[3], unsigned vbox[3]) {
 
 }  // namespace dgvol
 
-template <typename T, bool ABC>
+template <typename T, bool OPEN>
 cudaError_t launch_vol_flag(const VolSpec& s, int batch, cudaStream_t st) {
   using namespace dgvol;
   switch (s.N) {
-    case 1: return launch_n<T, 1, ABC>(s, batch, st);
-    case 2: return launch_n<T, 2, ABC>(s, batch, st);
-    case 3: return launch_n<T, 3, ABC>(s, batch, st);
-    case 4: return launch_n<T, 4, ABC>(s, batch, st);
-    case 5: return launch_n<T, 5, ABC>(s, batch, st);
-    case 6: return launch_n<T, 6, ABC>(s, batch, st);
-    case 7: return launch_n<T, 7, ABC>(s, batch, st);
-    case 8: return launch_n<T, 8, ABC>(s, batch, st);
+    case 1: return launch_n<T, 1, OPEN>(s, batch, st);
+    case 2: return launch_n<T, 2, OPEN>(s, batch, st);
+    case 3: return launch_n<T, 3, OPEN>(s, batch, st);
+    case 4: return launch_n<T, 4, OPEN>(s, batch, st);
+    case 5: return launch_n<T, 5, OPEN>(s, batch, st);
+    case 6: return launch_n<T, 6, OPEN>(s, batch, st);
+    case 7: return launch_n<T, 7, OPEN>(s, batch, st);
+    case 8: return launch_n<T, 8, OPEN>(s, batch, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -30,13 +30,13 @@ DGSEM_FP32_MIXED = 1
 DGSEM_RUN_CONTINUE = 1
 
 EXPORTED = [
-    "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
+    "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_set_pml", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "pmut_set_receive", "dgsem_get_voltages",
     "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
 ]
-DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1 = 0, 1, 2, 3
+DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1, DGSEM_K_PML = 0, 1, 2, 3, 4
 
 
 class DgsemError(RuntimeError):
@@ -74,6 +74,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_mesh_create.argtypes = [POINTER(MeshDesc), POINTER(vp)]
     lib.dgsem_get_dt.argtypes = [vp, POINTER(c_double), POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_set_absorbing.argtypes = [vp, c_int, vp]
+    lib.dgsem_set_pml.argtypes = [vp, c_int, vp, c_double]
     lib.pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
     lib.dgsem_get_voltages.argtypes = [vp, vp, c_size_t]
     lib.dgsem_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
@@ -181,6 +182,14 @@ def dgsem_set_absorbing(ctx, box: int, sides):
     arr = np.ascontiguousarray([1 if v else 0 for v in sides], dtype=np.int32)
     assert arr.shape == (6,)
     _check(_lib.dgsem_set_absorbing(ctx, box, _ptr(arr)), "dgsem_set_absorbing")
+
+
+def dgsem_set_pml(ctx, box: int, thickness, R: float = 1e-4):
+    """Perfectly matched layer of the given thickness (m) along the sides
+    x-, x+, y-, y+, z-, z+ of a box (0 = none), design reflection R."""
+    arr = np.ascontiguousarray(thickness, dtype=np.float64)
+    assert arr.shape == (6,)
+    _check(_lib.dgsem_set_pml(ctx, box, _ptr(arr), float(R)), "dgsem_set_pml")
 
 
 def pmut_set_receive(ctx, n_switch: int, capacitance=None, sign: int = -1):
@@ -355,6 +364,9 @@ class Solver:
             sides = getattr(dom, "absorbing", None)
             if sides is not None and any(sides):
                 dgsem_set_absorbing(self.ctx, d, sides)
+            th = getattr(dom, "pml", None)
+            if th is not None and any(t > 0 for t in th):
+                dgsem_set_pml(self.ctx, d, th, getattr(dom, "pml_R", 1e-4))
         self.dt, _, self.ndof = dgsem_get_dt(self.ctx)
         self.K = 0
         if workload.pmuts is not None:
