@@ -139,7 +139,8 @@ template <typename T, int N, int V> struct TileShape {
 template <typename T, int N> struct NumShapes {
   static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? 6 : 4) : 1;
 };
-// FP32 N=4: 512 threads in each, FP64 N=4: 256 / 256 / 128 / 512
+// FP32 N=4: 512 / 512 / 512 / 256 threads, register-column 512 / 256 (two CTAs
+// per SM); FP64 N=4: 256 / 256 / 128 / 512
 template <> struct TileShape<float, 4, 0> { using S = Shape<32, 2, 2>; };
 template <> struct TileShape<float, 4, 1> { using S = Shape<32, 4, 1>; };
 template <> struct TileShape<float, 4, 2> { using S = Shape<16, 4, 2>; };
@@ -150,7 +151,9 @@ template <> struct TileShape<double, 4, 0> { using S = Shape<32, 2, 1>; };
 template <> struct TileShape<double, 4, 1> { using S = Shape<16, 4, 1>; };
 template <> struct TileShape<double, 4, 2> { using S = Shape<32, 1, 1>; };
 template <> struct TileShape<double, 4, 3> { using S = Shape<32, 2, 2>; };
-// FP32 N=6: 384 / 576 / 192 / 384 threads, FP64 N=6: 192 / 96 / 192 / 384
+// FP32 N=6: 384 / 576 / 192 / 384 threads, register-column 384 / 192; FP64 N=6:
+// 192 / 96 / 192 / 384.  (Two CTAs of half the rows per SM were measured slower
+// than one CTA of full rows for both orders.)
 template <> struct TileShape<float, 6, 0> { using S = Shape<16, 2, 2>; };
 template <> struct TileShape<float, 6, 1> { using S = Shape<16, 2, 3>; };
 template <> struct TileShape<float, 6, 2> { using S = Shape<16, 2, 1>; };
