@@ -222,6 +222,11 @@ struct dgsem_ctx {
   int* d_pml_elem[2] = {nullptr, nullptr}; // [npml] element index
   int npml[2] = {0, 0};
   int pml_lo[2][3] = {}, pml_hi[2][3] = {};
+  // face arrays assembled each step (run state): interface residual per face
+  // node of each box, PMUT forcing per node of the primary's z-min face
+  void* Ga[2] = {nullptr, nullptr};
+  void* Gb[2] = {nullptr, nullptr};
+  void* Fpm = nullptr;
   void* Psi[2] = {nullptr, nullptr};       // psi, lattice layout (run state)
   void* Phi[2] = {nullptr, nullptr};       // [B][npml][3][(N+1)^3] (run state)
   void* Rpml[2] = {nullptr, nullptr};      // [B][npml][(N+1)^3] (run state)
@@ -303,7 +308,9 @@ void free_run_state(dgsem_ctx* c) {
   for (int d = 0; d < 2; ++d) {
     dfree(c->X[d]); dfree(c->Y[d]); dfree(c->V[d]); dfree(c->Ra[d]); dfree(c->Rb[d]);
     dfree(c->Psi[d]); dfree(c->Phi[d]); dfree(c->Rpml[d]);
+    dfree(c->Ga[d]); dfree(c->Gb[d]);
   }
+  dfree(c->Fpm);
   dfree(c->q_state);
   c->prec = -1;
   c->batch = 0;
@@ -365,6 +372,13 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
       }
       CUDA_TRY(cudaMemset(c->Ra[d], 0, rb));
       CUDA_TRY(cudaMemset(c->Rb[d], 0, rb));
+      const size_t gb = (size_t)batch * B.L[1] * B.py * es;
+      if ((rc = dalloc(&c->Ga[d], gb)) || (rc = dalloc(&c->Gb[d], gb))) {
+        free_run_state(c);
+        return rc;
+      }
+      CUDA_TRY(cudaMemset(c->Ga[d], 0, gb));
+      CUDA_TRY(cudaMemset(c->Gb[d], 0, gb));
     }
     if (c->has_pml[d]) {
       const Box& B = c->box[d];
@@ -378,7 +392,10 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
   }
   if (c->K > 0) {
     int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
+    const size_t fb = (size_t)batch * c->box[0].L[1] * c->box[0].py * es;
+    if (!rc) rc = dalloc(&c->Fpm, fb);
     if (rc) { free_run_state(c); return rc; }
+    CUDA_TRY(cudaMemset(c->Fpm, 0, fb));
   }
   c->prec = prec;
   c->batch = batch;
@@ -660,6 +677,38 @@ void collect_timings(dgsem_ctx* c) {
   c->ev_used.clear();
 }
 
+// Assemble the face arrays the volume launches read: the interface residual
+// of every face node of each box (after the interface launch) and, when
+// pmut, the PMUT forcing of the primary's z-min face (after the PMUT launch).
+template <typename T>
+int launch_face_assembly(dgsem_ctx* c, cudaStream_t s, int batch, bool pmut) {
+  if (c->has_iface) {
+    for (int d = 0; d < c->nd; ++d) {
+      const Box& B = c->box[d];
+      FaceAsmArgs<T> a;
+      a.Ra = static_cast<const T*>(c->Ra[d]); a.Rb = static_cast<const T*>(c->Rb[d]);
+      a.ga = static_cast<T*>(c->Ga[d]); a.gb = static_cast<T*>(c->Gb[d]);
+      a.N = B.N; a.ne0 = B.ne[0]; a.ne1 = B.ne[1]; a.L0 = B.L[0]; a.L1 = B.L[1]; a.py = B.py;
+      a.rbs = (long long)B.ne[0] * B.ne[1] * (B.N + 1) * (B.N + 1);
+      a.gbs = (long long)B.L[1] * B.py;
+      LaunchTimer lt(c, s, DGSEM_K_IFACE);
+      CUDA_TRY(launch_face_asm<T>(a, batch, s));
+    }
+  }
+  if (pmut && c->K > 0) {
+    const Box& P = c->box[0];
+    PmutForceArgs a;
+    a.node_ptr = c->d_node_ptr; a.node_ent = c->d_node_ent; a.ent_pmut = c->d_ent_pmut;
+    a.Bm = c->d_Bm; a.qdd = c->q_state + 2LL * batch * c->K * c->M;
+    a.K = c->K; a.M = c->M; a.L0 = P.L[0]; a.L1 = P.L[1]; a.py = P.py;
+    a.kappa = c->kappa;
+    a.f = c->Fpm; a.fbs = (long long)P.L[1] * P.py;
+    LaunchTimer lt(c, s, DGSEM_K_PMUT_RECV);
+    CUDA_TRY(launch_pmut_force<T>(a, batch, s));
+  }
+  return DGSEM_OK;
+}
+
 // One time step (or the initial half step when init is true).  With a side
 // stream (graph capture of a two-box mesh) the PMUT/receiver launch runs on
 // the side stream, concurrently with the interface launch on s; both volume
@@ -722,6 +771,10 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     CUDA_TRY(launch_iface<T>(a, c->batch, s));
   }
   if (fork) CUDA_TRY(cudaStreamWaitEvent(s, c->fork_ev[1], 0));
+  {
+    const int rc = launch_face_assembly<T>(c, s, c->batch, !init);
+    if (rc) return rc;
+  }
   // perfectly matched layers: Phi update and element residuals (read p^{n+1}, psi^{n+1/2})
   const int pi = std::is_same<T, float>::value ? 1 : 0;
   for (int d = 0; d < c->nd && !init; ++d) {
@@ -762,7 +815,8 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     v.p_in = pin[d]; v.p_out = pout[d]; v.v = c->V[d];
     v.dtv = init ? 0.5 * c->dt : c->dt;
     v.dtp = c->dt;
-    v.Ra = c->Ra[d]; v.Rb = c->Rb[d];
+    v.ga = c->Ga[d]; v.gb = c->Gb[d];
+    v.gbs = (long long)c->box[d].L[1] * c->box[d].py;
     if (c->has_pml[d]) {
       const Box& B = c->box[d];
       v.has_pml = 1;
@@ -779,9 +833,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     }
     if (d == 0 && c->K > 0 && !init) {
       v.has_pmut = 1;
-      v.node_ptr = c->d_node_ptr; v.node_ent = c->d_node_ent; v.ent_pmut = c->d_ent_pmut;
-      v.Bm = c->d_Bm; v.qdd = c->q_state + 2LL * c->batch * c->K * c->M;
-      v.K = c->K; v.M = c->M; v.kappa = c->kappa;
+      v.fpm = c->Fpm;
     }
     LaunchTimer lt(c, s, DGSEM_K_VOL0 + d);
     CUDA_TRY(launch_vol<T>(v, c->batch, s));
@@ -1690,16 +1742,20 @@ int dgsem_check_stability(dgsem_ctx* c, int iters, double* lambda_max) {
       a.pp = static_cast<const double*>(c->X[0]);
       a.ps = static_cast<const double*>(c->X[1]);
       CUDA_TRY(launch_iface<double>(a, 1, s));
+      if ((rc = launch_face_assembly<double>(c, s, 1, false))) { cleanup(); return rc; }
     }
     for (int d = 0; d < c->nd; ++d) {
       VolSpec v = c->vspec[d];
+      v.has_abc = 0;     // M^-1 K only (v = 0 makes the damping terms vanish anyway)
+      v.has_pml = 0;
       v.tmap = &c->tmap_x[d];
       v.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
       v.err = c->d_err;
       v.tile = c->tile_pref[0][d];
       v.p_in = c->X[d]; v.p_out = c->Y[d]; v.v = c->V[d];
       v.dtv = 1.0; v.dtp = 0.0;
-      v.Ra = c->Ra[d]; v.Rb = c->Rb[d];
+      v.ga = c->Ga[d]; v.gb = c->Gb[d];
+      v.gbs = (long long)c->box[d].L[1] * c->box[d].py;
       CUDA_TRY(launch_vol<double>(v, 1, s));
     }
     // Rayleigh quotient x.K x / x.M x = -(x.M v)/(x.M x), and the norm of v
@@ -1794,7 +1850,10 @@ int dgsem_autotune(dgsem_ctx* c, int precision, int batch, int reps, int* chosen
       sp.tile = v;
       sp.p_in = c->Y[d]; sp.p_out = c->X[d]; sp.v = c->V[d];
       sp.dtv = c->dt; sp.dtp = c->dt;
-      sp.Ra = c->Ra[d]; sp.Rb = c->Rb[d];
+      sp.ga = c->Ga[d]; sp.gb = c->Gb[d];
+      sp.gbs = (long long)c->box[d].L[1] * c->box[d].py;
+      sp.has_abc = 0;
+      sp.has_pml = 0;
       cudaError_t e = pi ? launch_vol<float>(sp, batch, s) : launch_vol<double>(sp, batch, s);   // warm-up
       if (e != cudaSuccess) { cudaGetLastError(); continue; }
       cudaEventRecord(e0, s);

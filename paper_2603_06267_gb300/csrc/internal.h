@@ -48,20 +48,17 @@ struct VolArgs {
   T iwb;               // 1 / w_0: vertex on the box boundary
   T iwa[N + 1];        // 1 / w_a for interior rows (a = 1..N-1)
   double minv_scale;   // 8 / (hx hy hz)
-  // PMUT forcing f on the z-min plane (primary box only)
+  // PMUT forcing f on the z-min plane (primary box only), assembled per face
+  // node for this step: fpm[b][j][i] = -kappa sum_entries sum_m q'' B  (eq. f_i)
   int has_pmut;
-  const int* node_ptr;     // [L0*L1 + 1]: footprint entries touching face node
-  const int* node_ent;     // entry ids
-  const int* ent_pmut;     // PMUT of each entry
-  const double* Bm;        // [nnz][M]: W_face * U.n
-  const double* qdd;       // [B][K][M]: q'' of this step
-  int K, M;
-  double kappa;
-  // interface residual (SIPG terms of eq. Wf_2), unassembled per face column
+  const T* fpm;
+  // interface residual (SIPG terms of eq. Wf_2), assembled per face node:
+  // the nodes of the interface element layer get -(d_c gb + [c = top] ga)
   int iface_k0;            // first lattice plane of the interface element layer, -1: none
   int iface_top;           // 1: the value term sits on plane k0+N (primary), 0: on k0 (secondary)
-  const T* Ra;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b alpha_q
-  const T* Rb;             // [B][ne0*ne1][(N+1)^2]: sum_q l_a l_b beta_q
+  const T* ga;             // [B][L1][py]: sum over faces of sum_q l_a l_b alpha_q
+  const T* gb;             // [B][L1][py]: sum over faces of sum_q l_a l_b beta_q
+  long long gbs;           // batch stride of fpm / ga / gb
   T dI[N + 1];             // d_c = (2/h_z) l_c'(face)
   // absorbing sides (eq. Wf_4): sigma = C_ii / M_ii = c (2/h_d) / w_0 per box
   // side (x-, x+, y-, y+, z-, z+), 0 = rigid; a -= sigma v on those nodes
@@ -114,6 +111,48 @@ struct IfaceArgs {
   T* Ras; T* Rbs;                  // [B][nsx*nsy][(Ns+1)^2]
   long long rbp, rbs;              // batch strides of the residual arrays
 };
+
+// ---------------------------------------------------------------------------
+// Face assembly, once per step before the volume launches: the per-face
+// interface residuals summed at each face node in a fixed order, and the
+// PMUT forcing summed at each node of Gamma_PMUT's face lattice.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct FaceAsmArgs {
+  const T* Ra; const T* Rb;        // [B][ne0*ne1][(N+1)^2] per face column
+  T* ga; T* gb;                    // [B][L1][py] per face node
+  int N, ne0, ne1, L0, L1, py;
+  long long rbs, gbs;
+};
+struct PmutForceArgs {
+  const int* node_ptr;             // [L0*L1 + 1] footprint entries of each face node
+  const int* node_ent;             // entry ids
+  const int* ent_pmut;             // PMUT of each entry
+  const double* Bm;                // [nnz][M]: W_face * U.n
+  const double* qdd;               // [B][K][M]: q'' of this step
+  int K, M, L0, L1, py;
+  double kappa;
+  void* f;                         // [B][L1][py] -kappa sum q'' B, state precision
+  long long fbs;
+};
+
+#ifdef __CUDACC__
+// Sum of the per-face (unassembled) interface residual entries touching face
+// node (i, j), in a fixed order (deterministic, no atomics).
+template <typename T, int N>
+__device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, int ne0, int ne1) {
+  int fx = i / N, ax = i - fx * N;
+  int fy = j / N, ay = j - fy * N;
+  if (fx == ne0) { fx = ne0 - 1; ax = N; }
+  if (fy == ne1) { fy = ne1 - 1; ay = N; }
+  constexpr int F = (N + 1) * (N + 1);
+  T s = R[(long long)(fy * ne0 + fx) * F + ay * (N + 1) + ax];
+  if (ax == 0 && fx > 0) s += R[(long long)(fy * ne0 + fx - 1) * F + ay * (N + 1) + N];
+  if (ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx) * F + N * (N + 1) + ax];
+  if (ax == 0 && fx > 0 && ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx - 1) * F + N * (N + 1) + N];
+  return s;
+}
+#endif
 
 // ---------------------------------------------------------------------------
 // Perfectly matched layer, one CTA per (layer element, batch member): Phi
@@ -195,11 +234,10 @@ struct VolSpec {
   double iwv, iwb, iwa[DG_MAXN + 1];
   double minv_scale;
   int has_pmut;
-  const int* node_ptr; const int* node_ent; const int* ent_pmut;
-  const double* Bm; const double* qdd;
-  int K, M; double kappa;
+  const void* fpm;
   int iface_k0, iface_top;
-  const void* Ra; const void* Rb;
+  const void* ga; const void* gb;
+  long long gbs;
   double dI[DG_MAXN + 1];
   // first-order absorbing sides (x-, x+, y-, y+, z-, z+): C_ii / M_ii of a
   // node on that side, c (2/h_d) / w_0; 0 = rigid wall
@@ -241,6 +279,10 @@ template <typename T>
 cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pml(const PmlArgs<T>& a, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_face_asm(const FaceAsmArgs<T>& a, int batch, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pmut_force(const PmutForceArgs& a, int batch, cudaStream_t s);
 // power-iteration helpers (FP64)
 cudaError_t launch_mdot(const double* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
                         int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s);

@@ -468,6 +468,74 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------
+// Face assembly (once per step): the interface residual of every face node,
+// summed over the faces that touch it in a fixed order, and the PMUT forcing
+// f_j = -kappa sum_{entries of j} sum_m q''_m B_{j,m} (eq. f_i) of every node
+// of the primary's z-min face, accumulated in FP64.  The volume kernels read
+// both as contiguous rows.
+// ---------------------------------------------------------------------------
+// A thread takes one face node for AB batch members, so the index work and
+// the CSR walk are shared by them.
+constexpr int AB = 8;
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) face_asm_kernel(const __grid_constant__ FaceAsmArgs<T> A, int batch) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)A.L0 * A.L1) return;
+  const int i = (int)(t % A.L0), j = (int)(t / A.L0);
+  const int b0 = blockIdx.y * AB, b1 = min(batch, b0 + AB);
+  // face entries touching node (i, j), in the order of face_gather
+  int fx = i / N, ax = i - fx * N, fy = j / N, ay = j - fy * N;
+  if (fx == A.ne0) { fx = A.ne0 - 1; ax = N; }
+  if (fy == A.ne1) { fy = A.ne1 - 1; ay = N; }
+  constexpr int F = (N + 1) * (N + 1);
+  long long off[4];
+  int n = 0;
+  off[n++] = (long long)(fy * A.ne0 + fx) * F + ay * (N + 1) + ax;
+  if (ax == 0 && fx > 0) off[n++] = (long long)(fy * A.ne0 + fx - 1) * F + ay * (N + 1) + N;
+  if (ay == 0 && fy > 0) off[n++] = (long long)((fy - 1) * A.ne0 + fx) * F + N * (N + 1) + ax;
+  if (ax == 0 && fx > 0 && ay == 0 && fy > 0) off[n++] = (long long)((fy - 1) * A.ne0 + fx - 1) * F + N * (N + 1) + N;
+  for (int b = b0; b < b1; ++b) {
+    const T* Ra = A.Ra + (long long)b * A.rbs;
+    const T* Rb = A.Rb + (long long)b * A.rbs;
+    T sa = Ra[off[0]], sb = Rb[off[0]];
+    for (int q = 1; q < n; ++q) {
+      sa += Ra[off[q]];
+      sb += Rb[off[q]];
+    }
+    const long long o = (long long)b * A.gbs + (long long)j * A.py + i;
+    A.ga[o] = sa;
+    A.gb[o] = sb;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) pmut_force_kernel(const __grid_constant__ PmutForceArgs A, int batch) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)A.L0 * A.L1) return;
+  const int i = (int)(t % A.L0), j = (int)(t / A.L0);
+  const int b0 = blockIdx.y * AB, nb = min(batch - b0, AB);
+  double f[AB];
+#pragma unroll
+  for (int q = 0; q < AB; ++q) f[q] = 0.0;
+  const int e1 = A.node_ptr[t + 1];
+  for (int e = A.node_ptr[t]; e < e1; ++e) {
+    const int ent = A.node_ent[e];
+    const int k = A.ent_pmut[ent];
+    const double* Bv = A.Bm + (long long)ent * A.M;
+    for (int m = 0; m < A.M; ++m) {
+      const double bm = Bv[m];
+#pragma unroll
+      for (int q = 0; q < AB; ++q)
+        if (q < nb) f[q] += A.qdd[((long long)(b0 + q) * A.K + k) * A.M + m] * bm;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < AB; ++q)
+    if (q < nb) static_cast<T*>(A.f)[(long long)(b0 + q) * A.fbs + (long long)j * A.py + i] = T(-A.kappa * f[q]);
+}
+
+// ---------------------------------------------------------------------------
 // Power-iteration helpers (setup only): M-weighted dot product over a box
 // lattice with the lumped mass M = scale * w_x(i) w_y(j) w_z(k), and scaling.
 // ---------------------------------------------------------------------------
@@ -537,6 +605,37 @@ cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_face_asm(const FaceAsmArgs<T>& a, int batch, cudaStream_t s) {
+  const long long n = (long long)a.L0 * a.L1;
+  if (n == 0 || batch <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)((n + 255) / 256), (batch + AB - 1) / AB);
+  switch (a.N) {
+    case 1: face_asm_kernel<T, 1><<<grid, 256, 0, s>>>(a, batch); break;
+    case 2: face_asm_kernel<T, 2><<<grid, 256, 0, s>>>(a, batch); break;
+    case 3: face_asm_kernel<T, 3><<<grid, 256, 0, s>>>(a, batch); break;
+    case 4: face_asm_kernel<T, 4><<<grid, 256, 0, s>>>(a, batch); break;
+    case 5: face_asm_kernel<T, 5><<<grid, 256, 0, s>>>(a, batch); break;
+    case 6: face_asm_kernel<T, 6><<<grid, 256, 0, s>>>(a, batch); break;
+    case 7: face_asm_kernel<T, 7><<<grid, 256, 0, s>>>(a, batch); break;
+    case 8: face_asm_kernel<T, 8><<<grid, 256, 0, s>>>(a, batch); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pmut_force(const PmutForceArgs& a, int batch, cudaStream_t s) {
+  const long long n = (long long)a.L0 * a.L1;
+  if (n == 0 || batch <= 0) return cudaSuccess;
+  pmut_force_kernel<T><<<dim3((unsigned)((n + 255) / 256), (batch + AB - 1) / AB), 256, 0, s>>>(a, batch);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_face_asm<float>(const FaceAsmArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_face_asm<double>(const FaceAsmArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_pmut_force<float>(const PmutForceArgs&, int, cudaStream_t);
+template cudaError_t launch_pmut_force<double>(const PmutForceArgs&, int, cudaStream_t);
 template cudaError_t launch_iface<float>(const IfaceArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_iface<double>(const IfaceArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_pmut_recv<float>(const PmutArgs<float>&, cudaStream_t);

@@ -199,50 +199,6 @@ struct Geo {
   static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
 };
 
-// Sum of the per-face (unassembled) interface residual entries touching face
-// node (i, j), in a fixed order (deterministic, no atomics).
-template <typename T, int N>
-__device__ __forceinline__ T face_gather(const T* __restrict__ R, int i, int j, int ne0, int ne1) {
-  int fx = i / N, ax = i - fx * N;
-  int fy = j / N, ay = j - fy * N;
-  if (fx == ne0) { fx = ne0 - 1; ax = N; }
-  if (fy == ne1) { fy = ne1 - 1; ay = N; }
-  constexpr int F = (N + 1) * (N + 1);
-  T s = R[(long long)(fy * ne0 + fx) * F + ay * (N + 1) + ax];
-  if (ax == 0 && fx > 0) s += R[(long long)(fy * ne0 + fx - 1) * F + ay * (N + 1) + N];
-  if (ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx) * F + N * (N + 1) + ax];
-  if (ax == 0 && fx > 0 && ay == 0 && fy > 0) s += R[(long long)((fy - 1) * ne0 + fx - 1) * F + N * (N + 1) + N];
-  return s;
-}
-
-// Rare per-node terms times M^-1: PMUT forcing f (eq. f_i) on the z-min plane
-// and the interface residual of the interface element layer.
-template <typename T, int N>
-__device__ __noinline__ T node_extras(const VolArgs<T, N>& A, int i, int j, int k, int b, T minv) {
-  T acc = T(0);
-  if (A.has_pmut && k == 0) {
-    double f = 0.0;
-    const int e0 = A.node_ptr[j * A.L0 + i], e1 = A.node_ptr[j * A.L0 + i + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int ent = A.node_ent[e];
-      const double* qd = A.qdd + ((long long)b * A.K + A.ent_pmut[ent]) * A.M;
-      const double* Bv = A.Bm + (long long)ent * A.M;
-      for (int m = 0; m < A.M; ++m) f += qd[m] * Bv[m];
-    }
-    acc += T(-A.kappa * f) * minv;
-  }
-  if (A.iface_k0 >= 0) {
-    const int idx = k - A.iface_k0;
-    if (idx >= 0 && idx <= N) {
-      const long long fs = (long long)b * (A.ne0 * A.ne1) * (N + 1) * (N + 1);
-      T r = A.dI[idx] * face_gather<T, N>(A.Rb + fs, i, j, A.ne0, A.ne1);
-      if (idx == (A.iface_top ? N : 0)) r += face_gather<T, N>(A.Ra + fs, i, j, A.ne0, A.ne1);
-      acc -= r * minv;
-    }
-  }
-  return acc;
-}
-
 // z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column)
 template <typename T, int N, int VS, int PLANE>
 __device__ __forceinline__ void zsum(const T* __restrict__ S0, int own, const T* coef, T* zs) {
@@ -670,6 +626,46 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       auto plane_extras = [&](int k) {
         return (A.has_pmut && k == 0) || (A.iface_k0 >= 0 && k >= A.iface_k0 && k <= A.iface_k0 + N);
       };
+      // M^-1 times the extra terms of plane k's owned nodes, from the face arrays
+      // assembled for this step: PMUT forcing f (eq. f_i) on z = 0, and
+      // -(d_c Rb + [c = top] Ra) of the interface residual on its element layer
+      auto plane_extra_vals = [&](int k, T iw_z, T* e) {
+        const long long o = (long long)b * A.gbs + (long long)j * A.py + (long long)ex * N;
+        T t[N];
+#pragma unroll
+        for (int a = 0; a < N; ++a) e[a] = T(0);
+        if (A.has_pmut && k == 0) {
+          vld<T, VG, N>(A.fpm + o, t);
+#pragma unroll
+          for (int a = 0; a < N; ++a) e[a] += t[a];
+        }
+        const int idx = k - A.iface_k0;
+        if (A.iface_k0 >= 0 && idx >= 0 && idx <= N) {
+          vld<T, VG, N>(A.gb + o, t);
+          const T d = A.dI[idx];
+#pragma unroll
+          for (int a = 0; a < N; ++a) e[a] -= d * t[a];
+          if (idx == (A.iface_top ? N : 0)) {
+            vld<T, VG, N>(A.ga + o, t);
+#pragma unroll
+            for (int a = 0; a < N; ++a) e[a] -= t[a];
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < N; ++a) e[a] *= mscale * ((a == 0) ? xiw : A.iwa[a]) * iw_y * iw_z;
+      };
+      // the same for the box's last x node (column ex*N + N)
+      auto last_extra_val = [&](int k, T iw_z) {
+        const long long o = (long long)b * A.gbs + (long long)j * A.py + (long long)ex * N + N;
+        T e = T(0);
+        if (A.has_pmut && k == 0) e += A.fpm[o];
+        const int idx = k - A.iface_k0;
+        if (A.iface_k0 >= 0 && idx >= 0 && idx <= N) {
+          e -= A.dI[idx] * A.gb[o];
+          if (idx == (A.iface_top ? N : 0)) e -= A.ga[o];
+        }
+        return e * mscale * A.iwb * iw_y * iw_z;
+      };
       const bool extras_layer = (A.has_pmut && ez == 0) ||
                                 (A.iface_k0 >= 0 && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
       // ZR: the thread's column of every staged plane of the layer, in
@@ -702,27 +698,22 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
           }
         }
         if (extras_layer && plane_extras(k)) {
+          T e[N];
+          plane_extra_vals(k, iw_z, e);
 #pragma unroll
-          for (int a = 0; a < N; ++a) {
-            const T iw_x = (a == 0) ? xiw : A.iwa[a];
-            const T minv = mscale * iw_x * iw_y * iw_z;
-            const T accum = node_extras<T, N>(A, ex * N + a, j, k, b, minv) - sm[a];
-            vn[a] = vcur[a] + A.dtv * accum;
-            pn[a] = self[a] + A.dtp * vn[a];
-          }
-        } else {
-          const float2 ndtv = f2(-A.dtv, -A.dtv), dtp = f2(A.dtp, A.dtp);
+          for (int a = 0; a < N; ++a) sm[a] -= e[a];
+        }
+        const float2 ndtv = f2(-A.dtv, -A.dtv), dtp = f2(A.dtp, A.dtp);
 #pragma unroll
-          for (int i = 0; i < N / 2; ++i) {
-            const float2 v2 = __ffma2_rn(ndtv, f2(sm[2 * i], sm[2 * i + 1]), f2(vcur[2 * i], vcur[2 * i + 1]));
-            const float2 p2 = __ffma2_rn(dtp, v2, f2(self[2 * i], self[2 * i + 1]));
-            vn[2 * i] = v2.x; vn[2 * i + 1] = v2.y;
-            pn[2 * i] = p2.x; pn[2 * i + 1] = p2.y;
-          }
-          if constexpr (N % 2 == 1) {
-            vn[N - 1] = vcur[N - 1] - A.dtv * sm[N - 1];
-            pn[N - 1] = self[N - 1] + A.dtp * vn[N - 1];
-          }
+        for (int i = 0; i < N / 2; ++i) {
+          const float2 v2 = __ffma2_rn(ndtv, f2(sm[2 * i], sm[2 * i + 1]), f2(vcur[2 * i], vcur[2 * i + 1]));
+          const float2 p2 = __ffma2_rn(dtp, v2, f2(self[2 * i], self[2 * i + 1]));
+          vn[2 * i] = v2.x; vn[2 * i + 1] = v2.y;
+          pn[2 * i] = p2.x; pn[2 * i + 1] = p2.y;
+        }
+        if constexpr (N % 2 == 1) {
+          vn[N - 1] = vcur[N - 1] - A.dtv * sm[N - 1];
+          pn[N - 1] = self[N - 1] + A.dtp * vn[N - 1];
         }
       };
       // one plane of the layer for the N owned nodes; ZM selects the z rows:
@@ -827,6 +818,10 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
           }
           // update: a = -(M^-1 K p) - C/M v (+ extras), v += dtv a, p_out = p + dtp v
           const T sg = OPEN ? abc_plane(k) : T(0);
+          T ext[N];
+#pragma unroll
+          for (int a = 0; a < N; ++a) ext[a] = T(0);
+          if (extras_layer && plane_extras(k)) plane_extra_vals(k, iw_z, ext);
 #pragma unroll
           for (int a = 0; a < N; ++a) {
             T accum = -(acc[a] + zs[a]);
@@ -838,11 +833,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
                 accum -= pml_terms<T, N>(A, ex * N + a, j, k, b, xr[N + a], vcur[a], minv);
               }
             }
-            if (extras_layer && plane_extras(k)) {
-              const T iw_x = (a == 0) ? xiw : A.iwa[a];
-              const T minv = mscale * iw_x * iw_y * iw_z;
-              accum += node_extras<T, N>(A, ex * N + a, j, k, b, minv);
-            }
+            accum += ext[a];
             vn[a] = vcur[a] + A.dtv * accum;
             pn[a] = xr[N + a] + A.dtp * vn[a];
           }
@@ -894,10 +885,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
           z *= iw_z;
         }
         T accum = -(x + y + z);
-        if (extras_layer && plane_extras(k)) {
-          const T minv = mscale * A.iwb * iw_y * iw_z;
-          accum += node_extras<T, N>(A, ex * N + N, j, k, b, minv);
-        }
+        if (extras_layer && plane_extras(k)) accum += last_extra_val(k, iw_z);
         T* vp = vv + (long long)k * A.pz + grow + N;
         T vo;
         if constexpr (VTMA) vo = (c < N) ? V0[c * VPLANE + vown + N] : *vp;
@@ -1005,10 +993,10 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   a.iwv = T(s.iwv); a.iwb = T(s.iwb);
   a.minv_scale = s.minv_scale;
   a.has_pmut = s.has_pmut;
-  a.node_ptr = s.node_ptr; a.node_ent = s.node_ent; a.ent_pmut = s.ent_pmut;
-  a.Bm = s.Bm; a.qdd = s.qdd; a.K = s.K; a.M = s.M; a.kappa = s.kappa;
+  a.fpm = static_cast<const T*>(s.fpm);
   a.iface_k0 = s.iface_k0; a.iface_top = s.iface_top;
-  a.Ra = static_cast<const T*>(s.Ra); a.Rb = static_cast<const T*>(s.Rb);
+  a.ga = static_cast<const T*>(s.ga); a.gb = static_cast<const T*>(s.gb);
+  a.gbs = s.gbs;
   return a;
 }
 

@@ -339,7 +339,8 @@ def test_config2_full_size_fp32_vs_fp64():
 
 def test_config3_full_size_linearity_and_shift():
     """Config 3 mesh at full size with 64 patterns (the bench's launch
-    configuration): linear in the drive and exactly time-shift invariant."""
+    configuration): linear in the drive, exactly time-shift invariant, and
+    each pattern independent of the others in the batch."""
     import torch
     from paper_2603_06267_gb300 import dgsem
     S = 120
@@ -360,4 +361,7 @@ def test_config3_full_size_linearity_and_shift():
     ds[:, :, k:] = d1[:, :, :-k]
     ts = sol.run(drive=ds, precision=1)
     assert np.array_equal(ts[:, :, k:], t1[:, :, :-k])
+    # batch independence: pattern 5 of the 64 equals the same drive run alone
+    t5 = sol.run(drive=np.ascontiguousarray(d1[5:6]), precision=1, batch=1)
+    assert rel_l2(t5[0], t1[5]) < 1e-6
     sol.close()
