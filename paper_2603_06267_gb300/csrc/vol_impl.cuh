@@ -64,6 +64,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return true;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
                                             int w) {
   asm volatile(
@@ -668,6 +672,16 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       };
       const bool extras_layer = (A.has_pmut && ez == 0) ||
                                 (A.iface_k0 >= 0 && A.iface_k0 <= ez * N + N && A.iface_k0 + N >= ez * N);
+      if (extras_layer) {
+        // the face rows this thread reads on the layer's planes: start them
+        // towards L1 now, so the planes do not wait on DRAM
+        const long long o = (long long)b * A.gbs + (long long)j * A.py + (long long)ex * N;
+        if (A.has_pmut && ez == 0) { prefetch_l1(A.fpm + o); prefetch_l1(A.fpm + o + N); }
+        if (A.iface_k0 >= 0) {
+          prefetch_l1(A.gb + o); prefetch_l1(A.gb + o + N);
+          prefetch_l1(A.ga + o); prefetch_l1(A.ga + o + N);
+        }
+      }
       // ZR: the thread's column of every staged plane of the layer, in
       // registers (the z stencil of all planes and the carry read it)
       T col[ZR ? N + 1 : 1][N];
