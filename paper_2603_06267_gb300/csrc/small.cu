@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(IF_THREADS) iface_kernel(const __grid_constant
 constexpr int RB_THREADS = 256;
 
 template <typename T, int NP1, int NS1, int Q, int FS, int BPC>
-__global__ void __launch_bounds__(RB_THREADS) iface_rows_kernel(const __grid_constant__ IfaceArgs<T> A, int batch) {
+__global__ void __launch_bounds__(RB_THREADS, sizeof(T) == 4 ? 3 : 1) iface_rows_kernel(const __grid_constant__ IfaceArgs<T> A, int batch) {
   static_assert(BPC * FS * Q <= RB_THREADS, "one worker per (member, fine face, qx)");
   __shared__ T sLp[Q][NP1];
   __shared__ T sLsx[FS][Q][NS1], sLsy[FS][Q][NS1];
