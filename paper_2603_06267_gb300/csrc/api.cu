@@ -202,6 +202,8 @@ struct dgsem_ctx {
   std::vector<double> face_xy;
   int K = 0, M = 0, nnz = 0;
   int* d_fp_ptr = nullptr; long long* d_fp_off = nullptr; double* d_Bm = nullptr;
+  float* d_Bm32 = nullptr;                 // FP32 copy of d_Bm (FP32 forcing assembly)
+  float* d_qdd32 = nullptr;                // FP32 copy of q'' (run state, FP32 runs)
   int* d_node_ptr = nullptr; int* d_node_ent = nullptr; int* d_ent_pmut = nullptr;
   double* d_modal = nullptr;    // omega2 | twozw | inv_mu | eta   [4][K*M]
   double kappa = 0.0;
@@ -311,6 +313,7 @@ void free_run_state(dgsem_ctx* c) {
     dfree(c->Ga[d]); dfree(c->Gb[d]);
   }
   dfree(c->Fpm);
+  dfree(c->d_qdd32);
   dfree(c->q_state);
   c->prec = -1;
   c->batch = 0;
@@ -392,6 +395,7 @@ int ensure_run_state(dgsem_ctx* c, int prec, int batch) {
   }
   if (c->K > 0) {
     int rc = dalloc(&c->q_state, (size_t)3 * batch * c->K * c->M * sizeof(double));
+    if (!rc && prec == DGSEM_FP32_MIXED) rc = dalloc(&c->d_qdd32, (size_t)batch * c->K * c->M * sizeof(float));
     const size_t fb = (size_t)batch * c->box[0].L[1] * c->box[0].py * es;
     if (!rc) rc = dalloc(&c->Fpm, fb);
     if (rc) { free_run_state(c); return rc; }
@@ -700,6 +704,7 @@ int launch_face_assembly(dgsem_ctx* c, cudaStream_t s, int batch, bool pmut) {
     PmutForceArgs a;
     a.node_ptr = c->d_node_ptr; a.node_ent = c->d_node_ent; a.ent_pmut = c->d_ent_pmut;
     a.Bm = c->d_Bm; a.qdd = c->q_state + 2LL * batch * c->K * c->M;
+    a.Bm32 = c->d_Bm32; a.qdd32 = c->d_qdd32;
     a.K = c->K; a.M = c->M; a.L0 = P.L[0]; a.L1 = P.L[1]; a.py = P.py;
     a.kappa = c->kappa;
     a.f = c->Fpm; a.fbs = (long long)P.L[1] * P.py;
@@ -731,6 +736,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     std::memset(&a, 0, sizeof(a));
     a.B = c->batch; a.K = c->K; a.M = c->M;
     a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_off; a.Bm = c->d_Bm;
+    a.qdd32 = std::is_same<T, float>::value ? c->d_qdd32 : nullptr;
     a.p_prev = static_cast<const T*>(c->X[0]);
     a.bsp = c->box[0].bstride;
     const long long kmB = (long long)c->batch * c->K * c->M;
@@ -1466,7 +1472,7 @@ int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* f
   }
   // release previous array (and any captured graph using it)
   drop_graph(c);
-  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_Bm32); dfree(c->d_node_ptr); dfree(c->d_node_ent);
   dfree(c->d_ent_pmut); dfree(c->d_modal); dfree(c->q_state);
   dfree(c->d_rx_gain);
   c->rx_switch = -1;
@@ -1503,7 +1509,9 @@ int pmut_array_set(dgsem_ctx* c, int K, int M, const int* foot_ptr, const int* f
     modal[(size_t)3 * K * M + i] = eta[i];
   }
   int rc;
+  std::vector<float> h_B32(h_B.begin(), h_B.end());
   if ((rc = upload(&c->d_fp_ptr, h_fp_ptr)) || (rc = upload(&c->d_fp_off, h_off)) || (rc = upload(&c->d_Bm, h_B)) ||
+      (rc = upload(&c->d_Bm32, h_B32)) ||
       (rc = upload(&c->d_node_ptr, node_ptr)) || (rc = upload(&c->d_node_ent, node_ent)) ||
       (rc = upload(&c->d_ent_pmut, ent_pmut)) || (rc = upload(&c->d_modal, modal)))
     return rc;
@@ -1899,7 +1907,7 @@ void dgsem_destroy(dgsem_ctx* c) {
   free_run_state(c);
   dfree(c->d_cf_col); dfree(c->d_cf_ptr); dfree(c->d_ff_col); dfree(c->d_ff_sx); dfree(c->d_ff_sy);
   dfree(c->d_tab[0]); dfree(c->d_tab[1]);
-  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_node_ptr); dfree(c->d_node_ent);
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_Bm32); dfree(c->d_node_ptr); dfree(c->d_node_ent);
   dfree(c->d_ent_pmut); dfree(c->d_modal);
   dfree(c->d_drive); dfree(c->d_traces);
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);

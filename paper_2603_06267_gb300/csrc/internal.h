@@ -130,6 +130,8 @@ struct PmutForceArgs {
   const int* ent_pmut;             // PMUT of each entry
   const double* Bm;                // [nnz][M]: W_face * U.n
   const double* qdd;               // [B][K][M]: q'' of this step
+  const float* Bm32;               // FP32 copies (the FP32 state sums f in FP32)
+  const float* qdd32;
   int K, M, L0, L1, py;
   double kappa;
   void* f;                         // [B][L1][py] -kappa sum q'' B, state precision
@@ -187,6 +189,7 @@ struct PmutArgs {
   const T* p_prev;                 // p^n of the primary box
   long long bsp;
   double* q; double* qd; double* qdd;   // [B][K][M]
+  float* qdd32;                    // FP32 copy of q'' for the forcing assembly, or NULL
   const double* omega2;            // [K][M]
   const double* twozw;             // [K][M] 2 zeta omega
   const double* inv_mu;            // [K][M]

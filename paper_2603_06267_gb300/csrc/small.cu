@@ -450,6 +450,7 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
       A.q[idx] = qn;
       A.qd[idx] = qdp + 0.5 * dt * qddn;                                // corrector
       A.qdd[idx] = qddn;
+      if (A.qdd32) A.qdd32[idx] = (float)qddn;
     }
     if (A.volt && lane == 0) A.volt[b * A.vbs + k * A.vks + n] = phi;
     return;
@@ -509,30 +510,38 @@ __global__ void __launch_bounds__(256) face_asm_kernel(const __grid_constant__ F
   }
 }
 
+// FP64 state: q'' and B in FP64.  FP32 state: their FP32 copies, summed in
+// FP32 (a node sums one or two footprint entries of a few modes; the result
+// joins an FP32 state update, and GB300's FP64 pipe is narrow).
 template <typename T>
 __global__ void __launch_bounds__(256) pmut_force_kernel(const __grid_constant__ PmutForceArgs A, int batch) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)A.L0 * A.L1) return;
   const int i = (int)(t % A.L0), j = (int)(t / A.L0);
   const int b0 = blockIdx.y * AB, nb = min(batch - b0, AB);
-  double f[AB];
+  const T* qdd;
+  const T* Bm;
+  if constexpr (sizeof(T) == 4) { qdd = reinterpret_cast<const T*>(A.qdd32); Bm = reinterpret_cast<const T*>(A.Bm32); }
+  else { qdd = reinterpret_cast<const T*>(A.qdd); Bm = reinterpret_cast<const T*>(A.Bm); }
+  T f[AB];
 #pragma unroll
-  for (int q = 0; q < AB; ++q) f[q] = 0.0;
+  for (int q = 0; q < AB; ++q) f[q] = T(0);
   const int e1 = A.node_ptr[t + 1];
   for (int e = A.node_ptr[t]; e < e1; ++e) {
     const int ent = A.node_ent[e];
     const int k = A.ent_pmut[ent];
-    const double* Bv = A.Bm + (long long)ent * A.M;
+    const T* Bv = Bm + (long long)ent * A.M;
     for (int m = 0; m < A.M; ++m) {
-      const double bm = Bv[m];
+      const T bm = Bv[m];
 #pragma unroll
       for (int q = 0; q < AB; ++q)
-        if (q < nb) f[q] += A.qdd[((long long)(b0 + q) * A.K + k) * A.M + m] * bm;
+        if (q < nb) f[q] += qdd[((long long)(b0 + q) * A.K + k) * A.M + m] * bm;
     }
   }
+  const T kap = T(-A.kappa);
 #pragma unroll
   for (int q = 0; q < AB; ++q)
-    if (q < nb) static_cast<T*>(A.f)[(long long)(b0 + q) * A.fbs + (long long)j * A.py + i] = T(-A.kappa * f[q]);
+    if (q < nb) static_cast<T*>(A.f)[(long long)(b0 + q) * A.fbs + (long long)j * A.py + i] = kap * f[q];
 }
 
 // ---------------------------------------------------------------------------
