@@ -131,9 +131,11 @@ constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
 // ---------------------------------------------------------------------------
 // ZR: each thread copies its column of the staged element layer into
 // registers once per layer, and the z stencils of its planes and the z carry
-// read that copy instead of shared memory (FP32 only); MINB: CTAs per SM
-template <int A, int B, int C, int Z = 0, int M = 1> struct Shape {
-  static constexpr int TXE = A, TYE = B, PG = C, MINB = M;
+// read that copy instead of shared memory (FP32 only); MINB: CTAs per SM;
+// RING 3: the p layers in a three-deep ring (v stays two deep), so a p load
+// has two layers of work to hide behind
+template <int A, int B, int C, int Z = 0, int M = 1, int R = 0> struct Shape {
+  static constexpr int TXE = A, TYE = B, PG = C, MINB = M, RING = R;
   static constexpr bool ZR = Z != 0;
 };
 template <typename T, int N, int V> struct TileShape {
@@ -141,7 +143,7 @@ template <typename T, int N, int V> struct TileShape {
                   (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1))), 1>;
 };
 template <typename T, int N> struct NumShapes {
-  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? 6 : 4) : 1;
+  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? (N == 6 ? 7 : 6) : 4) : 1;
 };
 // FP32 N=4: 512 / 512 / 512 / 256 threads, register-column 512 / 256 (two CTAs
 // per SM); FP64 N=4: 256 / 256 / 128 / 512
@@ -164,12 +166,13 @@ template <> struct TileShape<float, 6, 2> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<float, 6, 3> { using S = Shape<32, 1, 2>; };
 template <> struct TileShape<float, 6, 4> { using S = Shape<16, 2, 2, 1>; };
 template <> struct TileShape<float, 6, 5> { using S = Shape<16, 2, 1, 1>; };
+template <> struct TileShape<float, 6, 6> { using S = Shape<16, 2, 2, 1, 1, 3>; };
 template <> struct TileShape<double, 6, 0> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<double, 6, 1> { using S = Shape<16, 1, 1>; };
 template <> struct TileShape<double, 6, 2> { using S = Shape<8, 4, 1>; };
 template <> struct TileShape<double, 6, 3> { using S = Shape<16, 2, 2>; };
 
-template <typename T, int N, int TXE, int TYE, int PG>
+template <typename T, int N, int TXE, int TYE, int PG, int RING = 0>
 struct Geo {
   static constexpr int AL = 16 / (int)sizeof(T);                // elements per 16 bytes
   static constexpr int NAL = (N + AL - 1) / AL * AL;            // low x halo rounded up to 16 B
@@ -184,11 +187,16 @@ struct Geo {
   static constexpr int BXV = (TXE * N + 1 + AL - 1) / AL * AL;
   static constexpr int VPLANE = BXV * TYR;
   static constexpr size_t V_BYTES_RAW = sizeof(T) * (size_t)N * VPLANE;
-  static constexpr bool VTMA = sizeof(T) == 4 && 2 * (r128(P_BYTES) + r128(V_BYTES_RAW)) + 64 <= 227 * 1024;
+  static constexpr size_t PB = r128(P_BYTES), VBR = r128(V_BYTES_RAW);
+  static constexpr int PDEPTH = RING == 3 ? 3 : 2;
+  static constexpr bool VTMA = sizeof(T) == 4 && PDEPTH * PB + 2 * VBR + 128 <= 227 * 1024;
   static constexpr size_t V_BYTES = VTMA ? V_BYTES_RAW : 0;
-  static constexpr size_t STAGE = r128(P_BYTES) + r128(V_BYTES);
-  static constexpr int STAGES = (2 * STAGE + 64 <= 227 * 1024) ? 2 : 1;
-  static constexpr size_t SMEM = STAGES * STAGE + 64;
+  static constexpr size_t VB = r128(V_BYTES);
+  // ring depths: p layers (PST) and v planes (VST, 0 when v is not staged)
+  static constexpr int PST = (PDEPTH * PB + (VTMA ? 2 * VB : 0) + 128 <= 227 * 1024) ? PDEPTH : 1;
+  static constexpr int VST = VTMA ? 2 : 0;
+  static constexpr size_t VBASE = PST * PB;
+  static constexpr size_t SMEM = PST * PB + VST * VB + 128;   // + barriers and counters
   static constexpr int NT = TXE * TYR * PG;
   // vector widths: shared-memory runs start at column NAL + tx*N, global runs at ex*N
   static constexpr int VS = cmin(cmin(AL, pow2_div(N)), pow2_div(gcd_c(N, NAL)));
@@ -492,19 +500,21 @@ __device__ __forceinline__ int tile_row(int ty) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN>
+template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN, int RING>
 __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
-  using G = Geo<T, N, TXE, TYE, PG>;
+  using G = Geo<T, N, TXE, TYE, PG, RING>;
+  static_assert(RING == 0 || G::VTMA, "the three-deep p ring is for kernels that stage v");
   static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
   constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
   constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
-  constexpr int STAGES = G::STAGES;
+  constexpr int PST = G::PST, VST = G::VST;
   constexpr bool VTMA = G::VTMA;
   constexpr bool DIFF = sizeof(T) == 4;    // FP32: difference form, packed arithmetic
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NW = G::NT / 32;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + STAGES * G::STAGE);
-  int* cnt = reinterpret_cast<int*>(bar + 4);   // warps done with each stage
+  uint64_t* pbar = reinterpret_cast<uint64_t*>(smem_raw + G::SMEM - 128);   // p stage full
+  uint64_t* vbar = pbar + PST;                                                // v stage full
+  int* cnt = reinterpret_cast<int*>(pbar + 8);   // warps done with each p stage
 
   const int tx = threadIdx.x, ty = threadIdx.y, pg = threadIdx.z;
   const int tid = (pg * TYR + ty) * TXE + tx;
@@ -592,37 +602,45 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
 
   // pipeline set-up
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&bar[s], 1);
+    for (int s = 0; s < PST; ++s) {
+      mbar_init(&pbar[s], 1);
       cnt[s] = 0;
     }
+    for (int s = 0; s < VST; ++s) mbar_init(&vbar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap)) : "memory");
     if constexpr (VTMA) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&A.tmap_v)) : "memory");
   }
   __syncthreads();
-  auto issue = [&](int ez, int s) {
-    unsigned char* st = smem_raw + s * G::STAGE;
-    mbar_expect_tx(&bar[s], (uint32_t)(G::P_BYTES + G::V_BYTES));
-    tma_load_4d(st, &A.tmap, &bar[s], x0 - NAL, y0 - N, ez * N, b);
-    if constexpr (VTMA) tma_load_4d(st + r128(G::P_BYTES), &A.tmap_v, &bar[s], x0, y0, ez * N, b);
+  auto issue_p = [&](int ez, int s) {
+    mbar_expect_tx(&pbar[s], (uint32_t)G::P_BYTES);
+    tma_load_4d(smem_raw + s * G::PB, &A.tmap, &pbar[s], x0 - NAL, y0 - N, ez * N, b);
+  };
+  auto issue_v = [&](int ez, int s) {
+    if constexpr (VTMA) {
+      mbar_expect_tx(&vbar[s], (uint32_t)G::V_BYTES);
+      tma_load_4d(smem_raw + G::VBASE + s * G::VB, &A.tmap_v, &vbar[s], x0, y0, ez * N, b);
+    }
   };
   if (tid == 0) {
-    for (int s = 0; s < STAGES && ez0 + s < ez1; ++s) issue(ez0 + s, s);
+    for (int s = 0; s < PST && ez0 + s < ez1; ++s) issue_p(ez0 + s, s);
+    for (int s = 0; s < VST && ez0 + s < ez1; ++s) issue_v(ez0 + s, s);
   }
 
   int it = 0;
   for (int ez = ez0; ez < ez1; ++ez, ++it) {
-    const int s = it % STAGES;
-    const uint32_t parity = (uint32_t)((it / STAGES) & 1);
-    const T* S0 = reinterpret_cast<const T*>(smem_raw + s * G::STAGE);
-    const T* V0 = reinterpret_cast<const T*>(smem_raw + s * G::STAGE + r128(G::P_BYTES));
+    const int sp = it % PST, sv = VST ? it % VST : 0;
+    const T* S0 = reinterpret_cast<const T*>(smem_raw + sp * G::PB);
+    const T* V0 = reinterpret_cast<const T*>(smem_raw + G::VBASE + sv * G::VB);
     const bool last_layer = (ez == A.ne2 - 1);
     const int nplanes = last_layer ? N + 1 : N;
-    if (!mbar_wait_bounded(&bar[s], parity)) {
+    bool ok = mbar_wait_bounded(&pbar[sp], (uint32_t)((it / PST) & 1));
+    if constexpr (VST > 0) ok = ok && mbar_wait_bounded(&vbar[sv], (uint32_t)((it / VST) & 1));
+    if (!ok) {
       if (tid == 0) atomicExch(A.err, 1);
       // give the copies in flight a bounded chance to land before leaving
-      for (int q = 0; q < STAGES; ++q) (void)mbar_wait_bounded(&bar[q], parity);
+      for (int q = 0; q < PST; ++q) (void)mbar_wait_bounded(&pbar[q], (uint32_t)((it / PST) & 1));
+      for (int q = 0; q < VST; ++q) (void)mbar_wait_bounded(&vbar[q], (uint32_t)((it / VST) & 1));
       return;
     }
     if (active) {
@@ -931,19 +949,18 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
         }
       }
     }
-    // release stage s: the last warp to finish reading it issues its next
+    // release the layer's stages: the last warp to finish reading them issues their next
     // load, so warps with more work in this layer (vertex rows, the z carry)
     // hold up the others only when the ring runs dry
     __syncwarp();
     if ((tid & 31) == 0) {
       __threadfence_block();
-      if (atomicAdd(&cnt[s], 1) == NW - 1) {
-        cnt[s] = 0;
+      if (atomicAdd(&cnt[sp], 1) == NW - 1) {
+        cnt[sp] = 0;
         __threadfence_block();
-        if (ez + STAGES < ez1) {
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue(ez + STAGES, s);
-        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (ez + PST < ez1) issue_p(ez + PST, sp);
+        if (ez + VST < ez1) issue_v(ez + VST, sv);
       }
     }
   }
@@ -1018,7 +1035,7 @@ template <typename T, int N, int V, bool OPEN>
 cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   using SH = typename TileShape<T, N, V>::S;
   constexpr int TXE = SH::TXE, TYE = SH::TYE, PG = SH::PG;
-  using G = Geo<T, N, TXE, TYE, PG>;
+  using G = Geo<T, N, TXE, TYE, PG, SH::RING>;
   if (!s.tmap || !s.err) return cudaErrorInvalidValue;
   if (G::VTMA && !s.tmap_v) return cudaErrorInvalidValue;
   VolArgs<T, N> a = make_args<T, N>(s);
@@ -1033,7 +1050,7 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, OPEN>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, OPEN, SH::RING>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
@@ -1052,6 +1069,7 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
       case 3: return launch_v<T, N, 3, OPEN>(s, batch, st);
       case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4, OPEN>(s, batch, st); break;
       case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5, OPEN>(s, batch, st); break;
+      case 6: if constexpr (NumShapes<T, N>::value > 6) return launch_v<T, N, 6, OPEN>(s, batch, st); break;
       default: break;
     }
     return cudaErrorInvalidValue;
@@ -1064,7 +1082,7 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
 template <typename T, int N, int V>
 void box_v(unsigned box[3], unsigned vbox[3]) {
   using SH = typename TileShape<T, N, V>::S;
-  using G = Geo<T, N, SH::TXE, SH::TYE, SH::PG>;
+  using G = Geo<T, N, SH::TXE, SH::TYE, SH::PG, SH::RING>;
   box[0] = G::BX;
   box[1] = G::BY;
   box[2] = G::BZ;
@@ -1085,7 +1103,8 @@ int box_n(int tile, unsigned box[3], unsigned vbox[3]) {
       case 2: box_v<T, N, 2>(box, vbox); break;
       case 3: box_v<T, N, 3>(box, vbox); break;
       case 4: if constexpr (NumShapes<T, N>::value > 4) box_v<T, N, 4>(box, vbox); break;
-      default: if constexpr (NumShapes<T, N>::value > 5) box_v<T, N, 5>(box, vbox); break;
+      case 5: if constexpr (NumShapes<T, N>::value > 5) box_v<T, N, 5>(box, vbox); break;
+      default: if constexpr (NumShapes<T, N>::value > 6) box_v<T, N, 6>(box, vbox); break;
     }
   } else {
     box_v<T, N, 0>(box, vbox);
