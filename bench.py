@@ -45,7 +45,7 @@ NCU_TRAFFIC_PER_LAUNCH = {
 }
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiles", default=None,
                     help="comma-separated volume-kernel tile variant per box (skips the autotuner)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def make_workload(name, batch):
@@ -76,6 +76,32 @@ def make_workload(name, batch):
         w.drive_delay = np.repeat(w.drive_delay, batch, axis=0)
         w.drive_amp = np.repeat(w.drive_amp, batch, axis=0)
     return w
+
+
+def replica_workload(name, batch, rank, world):
+    """The workload rank `rank` of `world` runs.  The path shards as replicas:
+    every rank advances its own batch of independent drive patterns and no
+    data moves between ranks (config 4: its own seeded steering angles)."""
+    w = make_workload(name, batch)
+    if w.batch > 1 and world > 1 and name == "config4_batched":
+        w.drive_delay, w.drive_amp, _ = W.steering_patterns(w.pmuts.centers, w.batch, seed=4 + 1000 * rank)
+    return w
+
+
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest value of x over all ranks (x itself on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ndof, batch, steps, world, seconds):
+    """Gdof-steps/s of the whole job: every rank advanced batch patterns of
+    ndof nodes by steps steps within `seconds` (the slowest rank's time)."""
+    return ndof * batch * steps * world / seconds / 1e9
 
 
 def default_precision(name):
@@ -225,11 +251,7 @@ def main():
     name = args.workload
     prec_name = args.precision or default_precision(name)
     prec = dgsem.DGSEM_FP32_MIXED if prec_name == "fp32" else dgsem.DGSEM_FP64
-    w = make_workload(name, args.batch)
-    if w.batch > 1 and world > 1:
-        # independent patterns per rank (replicas): reseed the steering angles
-        if name == "config4_batched":
-            w.drive_delay, w.drive_amp, _ = W.steering_patterns(w.pmuts.centers, w.batch, seed=4 + 1000 * rank)
+    w = replica_workload(name, args.batch, rank, world)
     B = w.batch
     sol = dgsem.Solver(w)
     ndof = sol.ndof
@@ -285,23 +307,16 @@ def main():
             t0 = time.perf_counter()
             sol.run(drive=h_drive, precision=prec, nsteps=args.steps, traces=h_tr,
                     flags=dgsem.DGSEM_RUN_CONTINUE, stream=stream.cuda_stream)
-            e2e_s = time.perf_counter() - t0
-            if dist is not None:
-                t = torch.tensor([e2e_s], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                e2e_s = float(t.item())
-            e2e = {"value": ndof * B * args.steps * world / e2e_s / 1e9, "unit": "Gdof-steps/s",
+            e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+            e2e = {"value": whole_job_rate(ndof, B, args.steps, world, e2e_s), "unit": "Gdof-steps/s",
                    "h2d_bytes_per_step": int(B * K_p * 8), "d2h_bytes_per_step": int(B * R * 8)}
     finite = bool(torch.isfinite(tr_time).all().item())
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    value = ndof * B * args.steps * world / (ms / 1e3) / 1e9
+    value = whole_job_rate(ndof, B, args.steps, world, ms / 1e3)
     # roofline of the dominant kernel
     names = ["pmut_recv", "iface", "vol_primary", "vol_secondary", "pml"]
     kdom = max(range(4), key=lambda k: kstats[k][0])
