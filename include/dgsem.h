@@ -155,6 +155,15 @@ int dgsem_set_absorbing(dgsem_ctx* ctx, int box, const int* sides);
  * supported (DGSEM_ESTATE). */
 int dgsem_set_pml(dgsem_ctx* ctx, int box, const double* thickness, double R);
 
+/* Failure-path self test (no counterpart in the paper): one warp waits, with
+ * the bounded mbarrier wait the TMA pipeline of the volume kernels uses, on a
+ * barrier nothing arrives at; the wait gives up after 2^24 SM clocks and
+ * records it in the context's device status word, which this call reads back
+ * and clears.  DGSEM_OK when the give-up was reported (a stalled stage in a
+ * run is reported the same way, as DGSEM_ETIMEOUT from dgsem_run), DGSEM_ECUDA
+ * otherwise.  The context stays usable. */
+int dgsem_selftest_wait(dgsem_ctx* ctx, void* stream);
+
 /* Time step, stability bound and size.  dt_stable_max is 2 / sqrt(lambda_max)
  * of M^-1 K from dgsem_check_stability() (0 if it has not run); ndof counts
  * the unique GLL nodes of all boxes (dim V^DG). Any output may be NULL. */

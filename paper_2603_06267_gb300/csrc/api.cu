@@ -1430,6 +1430,19 @@ int dgsem_set_pml(dgsem_ctx* c, int box, const double* thickness, double R) {
   return DGSEM_OK;
 }
 
+int dgsem_selftest_wait(dgsem_ctx* c, void* stream) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), s));
+  CUDA_TRY(launch_wait_probe(c->d_err, 1LL << 24, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+  if (err != 3) return fail(DGSEM_ECUDA, "the bounded wait did not report its give-up (status %d)", err);
+  return DGSEM_OK;
+}
+
 int dgsem_get_dt(const dgsem_ctx* c, double* dt, double* dt_stable_max, long long* ndof) {
   if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
   if (dt) *dt = c->dt;

@@ -282,6 +282,8 @@ template <typename T>
 cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pml(const PmlArgs<T>& a, int batch, cudaStream_t s);
+// one warp waiting on an mbarrier nothing arrives at (bounded; sets *err = 3)
+cudaError_t launch_wait_probe(int* err, long long budget, cudaStream_t s);
 template <typename T>
 cudaError_t launch_face_asm(const FaceAsmArgs<T>& a, int batch, cudaStream_t s);
 template <typename T>

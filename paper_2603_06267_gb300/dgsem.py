@@ -30,7 +30,7 @@ DGSEM_FP32_MIXED = 1
 DGSEM_RUN_CONTINUE = 1
 
 EXPORTED = [
-    "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_set_pml", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
+    "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_set_pml", "dgsem_selftest_wait", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "pmut_set_receive", "dgsem_get_voltages",
     "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
@@ -75,6 +75,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_get_dt.argtypes = [vp, POINTER(c_double), POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_set_absorbing.argtypes = [vp, c_int, vp]
     lib.dgsem_set_pml.argtypes = [vp, c_int, vp, c_double]
+    lib.dgsem_selftest_wait.argtypes = [vp, vp]
     lib.pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
     lib.dgsem_get_voltages.argtypes = [vp, vp, c_size_t]
     lib.dgsem_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
@@ -182,6 +183,13 @@ def dgsem_set_absorbing(ctx, box: int, sides):
     arr = np.ascontiguousarray([1 if v else 0 for v in sides], dtype=np.int32)
     assert arr.shape == (6,)
     _check(_lib.dgsem_set_absorbing(ctx, box, _ptr(arr)), "dgsem_set_absorbing")
+
+
+def dgsem_selftest_wait(ctx, stream=None):
+    """Run the failure-path self test (a bounded device wait that must give up)."""
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_selftest_wait(ctx, stream), "dgsem_selftest_wait")
 
 
 def dgsem_set_pml(ctx, box: int, thickness, R: float = 1e-4):

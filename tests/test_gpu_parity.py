@@ -365,3 +365,19 @@ def test_config3_full_size_linearity_and_shift():
     t5 = sol.run(drive=np.ascontiguousarray(d1[5:6]), precision=1, batch=1)
     assert rel_l2(t5[0], t1[5]) < 1e-6
     sol.close()
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    """A device wait that nothing satisfies gives up within its budget and is
+    reported through the status word; the same context then runs normally."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40)
+    P = oracle_problem(w)
+    dt = P.stable_dt()
+    drive = w.drive(dt, w.nsteps, 1)
+    to = P.run(dt=dt, drive=drive)
+    sol = gpu_solver(w)
+    dgsem.dgsem_selftest_wait(sol.ctx)
+    tg = sol.run(drive=drive, precision=0)
+    sol.close()
+    assert rel_l2(tg, to) < FP64_TOL
