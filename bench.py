@@ -23,6 +23,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -274,8 +275,8 @@ def main():
     # warm-up from rest
     sol.run(drive=d_warm, precision=prec, nsteps=args.warmup, traces=tr_warm)
     torch.cuda.synchronize()
-    clocks_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
-                               f".bench_clocks_{rank}.csv")
+    clocks_dir = os.environ.get("DGSEM_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+    clocks_path = os.path.join(clocks_dir, f".bench_clocks_{rank}.csv")
     dgsem.dgsem_profile(sol.ctx, False)      # reset launch counters
     with ClockSampler(clocks_path) as cs:
         if dist is not None:

@@ -41,7 +41,7 @@ Paper passages followed (arXiv 2603.06267):
     one-vertex radius filter, Newton inverse map): Sec. 5, eq. (integral_DG),
     Algorithm 3.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * modal ODE carries a modal mass and damping:
       mu (q'' + 2 zeta w q' + w^2 q) = int p U.n + eta phi,
     damping evaluated at the predicted velocity like C p'_pred in Alg. 1;

@@ -32,7 +32,7 @@ def _declared_functions():
     return sorted(set(names))
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_core_entry_points():
     names = _declared_functions()
     for n in ("dgsem_mesh_create", "pmut_array_set", "dgsem_run", "dgsem_destroy", "dgsem_last_error"):
         assert n in names
