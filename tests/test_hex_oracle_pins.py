@@ -1,0 +1,233 @@
+"""Pins of the general-hexahedron oracle against facts the mathematics fixes:
+exact volumes and areas of trilinear elements under GLL quadrature, the
+linear patch test across a bent 2:1 interface, invariance under rigid motions
+and under re-listing elements in rotated local frames, the affine special case
+(the pinned box oracle), spectral convergence of a rigid-box eigenvalue, and
+the leapfrog energy invariant."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import hex as H
+from oracle import dgsem_oracle as O
+from oracle import hex_oracle as HO
+
+
+def _map_nodes(pa, pb, tol):
+    """index into pb's node array of every node of pa (same positions, per
+    domain: the two sides of the interface share positions but not nodes)."""
+    from scipy.spatial import cKDTree
+    out = []
+    for ma, mb in zip(pa.meshes, pb.meshes):
+        xa = np.column_stack(ma.all_coordinates()) if hasattr(ma, "all_coordinates") else ma.coords
+        xb = np.column_stack(mb.all_coordinates()) if hasattr(mb, "all_coordinates") else mb.coords
+        d, idx = cKDTree(xb).query(xa)
+        assert np.max(d) < tol
+        assert np.unique(idx).size == idx.size == xb.shape[0]
+        out.append(idx + mb.offset)
+    return np.concatenate(out)
+
+
+def _coords(prob):
+    return np.column_stack(prob.all_coordinates())
+
+
+@pytest.fixture(scope="module")
+def two_dom():
+    w = H.distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40)
+    return w, HO.HexOracleProblem(w)
+
+
+def test_trilinear_map_of_corners_and_jacobian():
+    rng = np.random.default_rng(0)
+    V = rng.normal(size=(8, 3))
+    X, J = HO.trilinear(V, HO.CORNERS)
+    np.testing.assert_allclose(X, V, atol=1e-15)
+    # finite differences of the map
+    ref = rng.uniform(-1, 1, size=(4, 3))
+    _, J = HO.trilinear(V, ref)
+    for d in range(3):
+        e = np.zeros(3); e[d] = 1e-6
+        Xp, _ = HO.trilinear(V, ref + e)
+        Xm, _ = HO.trilinear(V, ref - e)
+        np.testing.assert_allclose((Xp - Xm) / 2e-6, J[:, :, d], rtol=1e-8, atol=1e-9)
+    x = HO.trilinear(V * 0.1 + HO.CORNERS, np.array([[0.3, -0.2, 0.5]]))[0][0]
+    ref = HO.newton_reference(V * 0.1 + HO.CORNERS, x)
+    np.testing.assert_allclose(ref, [0.3, -0.2, 0.5], atol=1e-13)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_mass_sums_to_box_volume(order):
+    """sum_i M_ii = |Omega| exactly: |J| of a trilinear map has degree <= 2
+    per direction, integrated exactly by N+1 GLL points for N >= 2."""
+    w = H.distorted_one_domain(nel=(3, 2, 2), order=order)
+    p = HO.HexOracleProblem(w)
+    ext = w.box_extent
+    assert abs(p.M.sum() - ext[0] * ext[1] * ext[2]) < 1e-12 * ext[0] * ext[1] * ext[2]
+    assert np.min(p.meshes[0].detJ) > 0
+
+
+def test_two_domain_mass_fills_the_box(two_dom):
+    w, p = two_dom
+    ext = w.box_extent
+    vol = ext[0] * ext[1] * ext[2]
+    assert abs(p.M.sum() - vol) < 1e-12 * vol
+
+
+def test_pmut_face_weights_sum_to_plane_area(two_dom):
+    """The z = 0 plane is flat and its elements' faces tile it, so the
+    assembled face weights sum to its area exactly (planar bilinear faces
+    have a polynomial surface Jacobian)."""
+    w, p = two_dom
+    _, xyz, Wf = p.pmut_face_nodes()
+    assert np.all(np.abs(xyz[:, 2]) < 1e-18)
+    area = w.box_extent[0] * w.box_extent[1]
+    assert abs(Wf.sum() - area) < 1e-12 * area
+
+
+def test_linear_patch_across_bent_interface(two_dom):
+    """For u linear in x, (K u)_i = 0 at every node off the outer walls,
+    including the curved non-conforming interface: the GLL volume rule is
+    exact for the integrand (degree N+1 per direction), the GL face rule for
+    the Nanson-weighted interface terms, and the jump of u vanishes."""
+    w, p = two_dom
+    X = _coords(p)
+    rng = np.random.default_rng(1)
+    a = rng.normal(size=3)
+    u = X @ a + 0.7
+    r = p.K @ u
+    ext = np.array(w.box_extent)
+    tol = 1e-9 * ext.max()
+    inner = np.all((X > tol) & (X < ext[None, :] - tol), axis=1)
+    scale = abs(p.K).sum(axis=1).max() * np.abs(u).max()
+    assert inner.sum() > 100
+    assert np.max(np.abs(r[inner])) < 1e-12 * scale
+    # the wall rows carry the boundary flux c^2 int psi_i a.n: the test is not vacuous
+    assert np.max(np.abs(r[~inner])) > 1e4 * np.max(np.abs(r[inner]))
+
+
+def test_interface_nodes_are_inside_patch(two_dom):
+    """The patch-test nodes include the interface nodes of both sides."""
+    w, p = two_dom
+    m0 = p.meshes[0]
+    ids = m0.conn[w.fine_faces[:, 0]].ravel()
+    X = _coords(p)[ids]
+    assert np.any(np.abs(X[:, 2] - 2 * 25e-6) > 1e-7)   # the interface is bent
+
+
+def test_matching_finds_the_parent_coarse_element(two_dom):
+    """Algorithm 3 on the 2:1 lattice: every fine-face node lies in the coarse
+    element above its parent position, and its reference position maps back
+    to it."""
+    w, p = two_dom
+    nx_s = p.meshes[1].dom.lattice[0]
+    nx_p = p.meshes[0].dom.lattice[0]
+    for F, refp, xq, per in p.matches:
+        e = F.elem
+        i, j = e % nx_p, (e // nx_p) % nx_p
+        parent = (j // 2) * nx_s + (i // 2)
+        for q, (gi, refm) in enumerate(per):
+            G = p.coarse_faces[gi]
+            assert G.elem == parent
+            x, _ = HO.trilinear(p.meshes[1].elem_verts(G.elem), refm[None, :])
+            assert np.linalg.norm(x[0] - xq[q]) < 1e-12 * 50e-6
+            assert abs(abs(refm[2]) - 1.0) < 1e-9          # on the coarse face
+
+
+def test_rigid_motion_invariance():
+    """K and M do not change when the whole mesh is rotated and moved (a
+    transposed Jacobian or a normal in the wrong frame would change them)."""
+    w = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=3, order_s=4)
+    p0 = HO.HexOracleProblem(w)
+    rng = np.random.default_rng(5)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(Q) < 0:
+        Q[:, 0] = -Q[:, 0]
+    for d in w.domains:
+        d.vertices = d.vertices @ Q.T + np.array([1e-4, -2e-4, 3e-4])
+    w.pmuts = None
+    p1 = HO.HexOracleProblem(w)
+    assert abs(p1.K - p0.K).max() < 1e-11 * abs(p0.K).max()
+    np.testing.assert_allclose(p1.M, p0.M, rtol=1e-12)
+
+
+def test_rotated_local_frames_give_the_same_operator():
+    """Re-listing every element in a rotated local frame (and renumbering
+    its faces) is the same physical mesh: same M, K up to node order."""
+    wa = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=3, order_s=4)
+    wb = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=3, order_s=4, scramble=7)
+    assert not np.array_equal(wa.domains[0].elements, wb.domains[0].elements)
+    pa, pb = HO.HexOracleProblem(wa), HO.HexOracleProblem(wb)
+    idx = _map_nodes(pa, pb, 1e-12 * 50e-6)
+    np.testing.assert_allclose(pb.M[idx], pa.M, rtol=1e-12)
+    Kb = pb.K[idx][:, idx]
+    assert abs(Kb - pa.K).max() < 1e-11 * abs(pa.K).max()
+    Bb = pb.B[idx]
+    assert abs(Bb - pa.B).max() < 1e-12 * abs(pa.B).max()
+
+
+def test_affine_case_is_the_box_oracle():
+    """On undistorted lattices the general oracle reproduces the (pinned)
+    box oracle: mass, stiffness with the 2:1 interface, PMUT matrix, dt."""
+    wb = W.small_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=2, n_pmut_side=1, nsteps=10)
+    wh = H.hex_workload_from_box(wb)
+    pb, ph = O.OracleProblem(wb), HO.HexOracleProblem(wh)
+    idx = _map_nodes(pb, ph, 1e-15)
+    np.testing.assert_allclose(ph.M[idx], pb.M, rtol=1e-13)
+    Kh = ph.K[idx][:, idx]
+    assert abs(Kh - pb.K).max() < 1e-12 * abs(pb.K).max()
+    assert abs(ph.B[idx] - pb.B).max() < 1e-13 * abs(pb.B).max()
+    assert abs(ph.stable_dt() - pb.stable_dt()) < 1e-15 * pb.stable_dt()
+
+
+def test_rigid_box_eigenvalue_converges_spectrally():
+    """Rayleigh quotient of the interpolated rigid-box mode cos(pi x / L) on
+    the distorted mesh tends to (c pi / L)^2, faster than algebraically."""
+    errs = []
+    for N in (2, 3, 4, 5, 6):
+        w = H.distorted_one_domain(nel=(2, 2, 2), order=N, amp=0.12)
+        p = HO.HexOracleProblem(w)
+        X = _coords(p)
+        L = w.box_extent[0]
+        u = np.cos(math.pi * X[:, 0] / L)
+        rq = (u @ (p.K @ u)) / (u @ (p.M * u))
+        exact = (p.meshes[0].c * math.pi / L) ** 2
+        errs.append(abs(rq / exact - 1.0))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-6 and errs[-1] < 1e-3 * errs[0], errs
+
+
+def test_operator_symmetric_with_constant_kernel(two_dom):
+    w, p = two_dom
+    assert abs(p.K - p.K.T).max() < 1e-12 * abs(p.K).max()
+    one = np.ones(p.nh)
+    assert np.max(np.abs(p.K @ one)) < 1e-12 * abs(p.K).sum(axis=1).max()
+
+
+def test_leapfrog_energy_is_conserved_on_curved_mesh(two_dom):
+    """Acoustic part alone (no PMUT): Algorithm 1 keeps the leapfrog energy
+    1/2 v.M v + 1/2 p.K p_next constant on the distorted two-domain mesh."""
+    w, p = two_dom
+    X = _coords(p)
+    p0 = W.seeded_field(3, X[:, 0], X[:, 1], X[:, 2])
+    pm = w.pmuts
+    w.pmuts = None
+    try:
+        _, e = p.run(nsteps=30, p0=p0, energy=True, receivers=w.receivers[:2])
+    finally:
+        w.pmuts = pm
+    lf = e[:, 0, 0]
+    assert np.max(np.abs(lf - lf[0])) < 1e-11 * abs(lf[0])
+
+
+def test_unmatched_interface_node_is_an_error():
+    """A coarse face list missing a face leaves fine nodes without a
+    neighbour: the matching raises instead of dropping them."""
+    w = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=2, order_s=2)
+    w2 = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=1, n_pmut_side=1, order_p=2, order_s=2)
+    w2.coarse_faces = w2.coarse_faces[:3]
+    with pytest.raises(ValueError):
+        HO.HexOracleProblem(w2)
+    HO.HexOracleProblem(w)
