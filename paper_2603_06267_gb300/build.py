@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgsem.so")
-SOURCES = ["api.cu", "vol_f32.cu", "vol_f32_abc.cu", "vol_f64.cu", "vol_f64_abc.cu", "small.cu", "pml.cu", "surrogate.cu"]
+SOURCES = ["api.cu", "vol_f32.cu", "vol_f32_abc.cu", "vol_f64.cu", "vol_f64_abc.cu", "small.cu", "pml.cu", "surrogate.cu",
+           "hex_api.cu", "hex_kernels.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +38,8 @@ def _stale(obj: str, deps) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "vol_impl.cuh"), os.path.join(INCLUDE, "dgsem.h"),
+    headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "vol_impl.cuh"), os.path.join(CSRC, "tables.h"),
+               os.path.join(CSRC, "hex_geom.h"), os.path.join(INCLUDE, "dgsem.h"), os.path.join(INCLUDE, "dghex.h"),
                os.path.join(INCLUDE, "surrogate.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                     "-I", CSRC, "-I", INCLUDE]

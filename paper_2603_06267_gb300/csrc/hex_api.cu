@@ -1,0 +1,1031 @@
+// Host setup and C ABI of the DG-SEM step on general hexahedral meshes
+// (include/dghex.h).
+//
+// Setup (untimed): topological C0 numbering of the GLL nodes of each domain
+// (shared vertices, edges and faces matched by vertex ids, any element
+// orientation), geometric factors and lumped mass on the GPU, Algorithm 3 on
+// the GPU, the slot layout of the element-local residuals, PMUT face weights,
+// receivers and the time step.
+// Step: PMUT modal step (the box path's kernel), element stiffness of each
+// domain, interface terms, residual gather + leapfrog update, tail (forcing
+// slots, receivers, step counter) -- Algorithm 1 in two-vector leapfrog form
+// with the state (p^n, v^{n-1/2}).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <type_traits>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dghex.h"
+#include "hex_geom.h"
+#include "internal.h"
+#include "tables.h"
+
+namespace {
+
+int hfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  return dg_fail_msg(code, buf);
+}
+
+#define HCUDA(expr)                                                                      \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return hfail(e_ == cudaErrorMemoryAllocation ? DGSEM_ENOMEM : DGSEM_ECUDA,         \
+                   "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+template <typename P>
+int dmalloc(P** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return DGSEM_OK;
+  HCUDA(cudaMalloc(reinterpret_cast<void**>(p), bytes));
+  return DGSEM_OK;
+}
+
+template <typename P>
+void dfree(P*& p) {
+  if (p) cudaFree(const_cast<void*>(reinterpret_cast<const void*>(p)));
+  p = nullptr;
+}
+
+template <typename V>
+int upload(V** d, const std::vector<V>& h) {
+  int rc = dmalloc(d, h.size() * sizeof(V));
+  if (rc) return rc;
+  if (!h.empty()) HCUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return DGSEM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct HexDom {
+  int N = 0, n = 0, nl = 0, ne = 0, nv = 0;
+  double c = 0.0, rho = 0.0;
+  std::vector<double> vert;
+  std::vector<int> elem;
+  std::vector<int> conn;          // [ne][nl] global node ids
+  long long node0 = 0, nnode = 0;
+  long long vslot0 = 0;           // first volume slot
+  dgtab::Basis1D* basis = nullptr;
+  double* d_vert = nullptr;
+  int* d_elem = nullptr;
+  int* d_conn = nullptr;
+  double* d_G64 = nullptr;
+  float* d_G32 = nullptr;
+};
+
+// corner list position of the corner with bits (i, j, k)
+inline int corner(int i, int j, int k) { return i + 2 * j + 4 * k; }
+
+// C0 numbering of one domain's GLL nodes: vertices, edges (keyed by their two
+// vertex ids, counted from the smaller), faces (keyed by the smallest vertex
+// and its two face neighbours, counted from the smallest towards the smaller
+// neighbour first) and element interiors.  Ids are assigned in order of first
+// appearance of the entity over the elements.
+int number_nodes(HexDom& D, long long node0, std::map<std::array<int, 4>, int>& face_count) {
+  const int N = D.N, n = D.n, nl = D.nl;
+  D.conn.assign((size_t)D.ne * nl, -1);
+  std::vector<long long> vnode(D.nv, -1);
+  std::unordered_map<unsigned long long, long long> edge_base;
+  std::map<std::array<int, 3>, long long> face_base;
+  long long next = 0;
+  const long long nv = D.nv;
+  for (int e = 0; e < D.ne; ++e) {
+    const int* V = &D.elem[(size_t)e * 8];
+    for (int f = 0; f < 6; ++f) {
+      const int ax = f >> 1, side = f & 1;
+      std::array<int, 4> key;
+      int k = 0;
+      for (int c = 0; c < 8; ++c)
+        if (((c >> ax) & 1) == side) key[k++] = V[c];
+      std::sort(key.begin(), key.end());
+      face_count[key] += 1;
+    }
+    long long ibase = -1;
+    for (int i = 0; i < nl; ++i) {
+      const int l[3] = {i % n, (i / n) % n, i / (n * n)};
+      bool ext[3];
+      int next_ax = 0;
+      for (int d = 0; d < 3; ++d) {
+        ext[d] = l[d] == 0 || l[d] == N;
+        next_ax += ext[d];
+      }
+      long long id;
+      if (next_ax == 3) {
+        const int v = V[corner(l[0] == N, l[1] == N, l[2] == N)];
+        if (vnode[v] < 0) vnode[v] = next++;
+        id = vnode[v];
+      } else if (next_ax == 2) {
+        const int fa = !ext[0] ? 0 : (!ext[1] ? 1 : 2);
+        int bits[3] = {l[0] == N, l[1] == N, l[2] == N};
+        bits[fa] = 0;
+        const int vA = V[corner(bits[0], bits[1], bits[2])];
+        bits[fa] = 1;
+        const int vB = V[corner(bits[0], bits[1], bits[2])];
+        const unsigned long long key = (unsigned long long)std::min(vA, vB) * (unsigned long long)nv + std::max(vA, vB);
+        auto it = edge_base.find(key);
+        long long base;
+        if (it == edge_base.end()) {
+          base = next;
+          next += N - 1;
+          edge_base.emplace(key, base);
+        } else {
+          base = it->second;
+        }
+        const int t = l[fa];
+        id = base + (vA < vB ? t - 1 : N - 1 - t);
+      } else if (next_ax == 1) {
+        const int xa = ext[0] ? 0 : (ext[1] ? 1 : 2);
+        const int f1 = xa == 0 ? 1 : 0, f2 = xa == 2 ? 1 : 2;
+        const int s = l[xa] == N;
+        auto C = [&](int i1, int i2) {
+          int bits[3];
+          bits[xa] = s;
+          bits[f1] = i1;
+          bits[f2] = i2;
+          return V[corner(bits[0], bits[1], bits[2])];
+        };
+        int oi = 0, oj = 0;
+        for (int i1 = 0; i1 < 2; ++i1)
+          for (int i2 = 0; i2 < 2; ++i2)
+            if (C(i1, i2) < C(oi, oj)) {
+              oi = i1;
+              oj = i2;
+            }
+        const int n1 = C(1 - oi, oj), n2 = C(oi, 1 - oj);
+        const int u = oi == 0 ? l[f1] : N - l[f1];
+        const int w = oj == 0 ? l[f2] : N - l[f2];
+        int first, second;
+        std::array<int, 3> key;
+        if (n1 < n2) {
+          first = u; second = w; key = {C(oi, oj), n1, n2};
+        } else {
+          first = w; second = u; key = {C(oi, oj), n2, n1};
+        }
+        auto it = face_base.find(key);
+        long long base;
+        if (it == face_base.end()) {
+          base = next;
+          next += (long long)(N - 1) * (N - 1);
+          face_base.emplace(key, base);
+        } else {
+          base = it->second;
+        }
+        id = base + (first - 1) + (long long)(N - 1) * (second - 1);
+      } else {
+        if (ibase < 0) {
+          ibase = next;
+          next += (long long)(N - 1) * (N - 1) * (N - 1);
+        }
+        id = ibase + (l[0] - 1) + (long long)(N - 1) * ((l[1] - 1) + (long long)(N - 1) * (l[2] - 1));
+      }
+      D.conn[(size_t)e * nl + i] = (int)(node0 + id);
+    }
+  }
+  D.node0 = node0;
+  D.nnode = next;
+  return DGSEM_OK;
+}
+
+void elem_verts(const HexDom& D, int e, double* V) {
+  for (int c = 0; c < 8; ++c)
+    for (int k = 0; k < 3; ++k) V[3 * c + k] = D.vert[3 * (size_t)D.elem[(size_t)e * 8 + c] + k];
+}
+
+}  // namespace
+
+struct dghex_ctx {
+  int device = 0;
+  int nd = 0;
+  HexDom dom[2];
+  long long ndof = 0, nvol = 0;
+  std::vector<double> xyz;
+  double dt = 0.0;
+  // interface (Algorithm 3)
+  int q = 0, nff = 0, ncf = 0;
+  std::vector<int> ff, cf, match;
+  std::vector<double> refm;
+  int ng = 0, max_pts = 0;
+  long long islot0 = 0, nislot = 0;
+  std::vector<int> g_fe, g_ce, g_pt, pt_idx;
+  std::vector<long long> g_slot;
+  int *d_g_fe = nullptr, *d_g_ce = nullptr, *d_g_pt = nullptr, *d_pt_idx = nullptr;
+  long long* d_g_slot = nullptr;
+  double* d_pdat = nullptr;
+  // Gamma_PMUT
+  std::vector<long long> pn_id;
+  std::vector<double> pn_xyz, pn_w;
+  int K = 0, M = 0, nnz = 0;
+  long long fslot0 = 0;
+  std::vector<long long> ent_node;
+  int* d_fp_ptr = nullptr; long long* d_fp_off = nullptr; double* d_Bm = nullptr; int* d_ent_k = nullptr;
+  double* d_modal = nullptr;
+  double kappa = 0.0;
+  // slots and their per-node lists
+  long long nslot = 0;
+  int* d_node_ptr = nullptr; int* d_node_slot = nullptr;
+  double* d_Mloc = nullptr; double* d_M = nullptr; double* d_Minv64 = nullptr; float* d_Minv32 = nullptr;
+  // run state
+  int prec = -1, batch = 0;
+  void* P = nullptr; void* V = nullptr; void* S = nullptr;
+  double* q_state = nullptr;
+  bool state_valid = false;
+  int* d_step = nullptr; unsigned* d_done = nullptr;
+  std::vector<double> init_p, init_v;
+  bool has_init = false;
+  // receivers and scratch for host-pointer runs
+  double* d_rw = nullptr; long long* d_roff = nullptr; int* d_rnn = nullptr;
+  size_t recv_cap = 0; int rstride = 0;
+  double* d_drive = nullptr; size_t drive_cap = 0;
+  double* d_traces = nullptr; size_t traces_cap = 0;
+  // instrumentation
+  bool profiling = false;
+  long long launches[DGHEX_K_COUNT] = {};
+  double kernel_ms[DGHEX_K_COUNT] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;
+};
+
+namespace {
+
+struct HexTimer {
+  dghex_ctx* c; cudaStream_t s; int kind; int idx = -1;
+  HexTimer(dghex_ctx* c_, cudaStream_t s_, int k) : c(c_), s(s_), kind(k) {
+    c->launches[kind] += 1;
+    if (!c->profiling) return;
+    idx = (int)c->ev_used.size() * 2;
+    while ((int)c->ev_pool.size() < idx + 2) {
+      cudaEvent_t ev;
+      if (cudaEventCreate(&ev) != cudaSuccess) { idx = -1; return; }
+      c->ev_pool.push_back(ev);
+    }
+    cudaEventRecord(c->ev_pool[idx], s);
+  }
+  ~HexTimer() {
+    if (idx < 0) return;
+    cudaEventRecord(c->ev_pool[idx + 1], s);
+    c->ev_used.emplace_back(kind, idx);
+  }
+};
+
+void collect_timings(dghex_ctx* c) {
+  for (auto& u : c->ev_used) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev_pool[u.second], c->ev_pool[u.second + 1]) == cudaSuccess)
+      c->kernel_ms[u.first] += ms;
+  }
+  c->ev_used.clear();
+}
+
+void free_run_state(dghex_ctx* c) {
+  dfree(c->P); dfree(c->V); dfree(c->S); dfree(c->q_state);
+  c->prec = -1;
+  c->batch = 0;
+  c->state_valid = false;
+}
+
+int ensure_run_state(dghex_ctx* c, int prec, int batch) {
+  if (c->prec == prec && c->batch == batch && c->P) return DGSEM_OK;
+  free_run_state(c);
+  const size_t es = prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
+  int rc;
+  if ((rc = dmalloc(&c->P, es * batch * c->ndof)) || (rc = dmalloc(&c->V, es * batch * c->ndof)) ||
+      (rc = dmalloc(&c->S, es * batch * c->nslot)))
+    return rc;
+  if (c->K > 0 && (rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
+  c->prec = prec;
+  c->batch = batch;
+  return DGSEM_OK;
+}
+
+// Slot layout: volume slots of domain 0 then 1 (element-major), the interface
+// groups' blocks, then one forcing slot per PMUT footprint entry; each node
+// lists its slots in ascending order.
+int build_slots(dghex_ctx* c) {
+  c->islot0 = c->nvol;
+  c->fslot0 = c->islot0 + c->nislot;
+  c->nslot = c->fslot0 + c->nnz;
+  if (c->nslot >= (1LL << 31)) return hfail(DGSEM_EINVAL, "mesh too large: %lld residual slots", c->nslot);
+  std::vector<int> node_of((size_t)c->nslot);
+  for (int d = 0; d < c->nd; ++d) {
+    const HexDom& D = c->dom[d];
+    for (size_t k = 0; k < D.conn.size(); ++k) node_of[(size_t)D.vslot0 + k] = D.conn[k];
+  }
+  if (c->nd == 2) {
+    const HexDom &Dp = c->dom[0], &Dm = c->dom[1];
+    for (int g = 0; g < c->ng; ++g) {
+      const long long s0 = c->g_slot[g];
+      for (int i = 0; i < Dp.nl; ++i) node_of[s0 + i] = Dp.conn[(size_t)c->g_fe[g] * Dp.nl + i];
+      for (int i = 0; i < Dm.nl; ++i) node_of[s0 + Dp.nl + i] = Dm.conn[(size_t)c->g_ce[g] * Dm.nl + i];
+    }
+  }
+  for (int e = 0; e < c->nnz; ++e) node_of[(size_t)c->fslot0 + e] = (int)c->ent_node[e];
+  std::vector<int> ptr((size_t)c->ndof + 1, 0), slot((size_t)c->nslot);
+  for (long long s = 0; s < c->nslot; ++s) ptr[node_of[s] + 1] += 1;
+  for (long long j = 0; j < c->ndof; ++j) ptr[j + 1] += ptr[j];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  for (long long s = 0; s < c->nslot; ++s) slot[fill[node_of[s]]++] = (int)s;
+  dfree(c->d_node_ptr);
+  dfree(c->d_node_slot);
+  int rc;
+  if ((rc = upload(&c->d_node_ptr, ptr)) || (rc = upload(&c->d_node_slot, slot))) return rc;
+  free_run_state(c);
+  return DGSEM_OK;
+}
+
+int setup_interface(dghex_ctx* c, const dghex_mesh_desc* d) {
+  HexDom &Dp = c->dom[0], &Dm = c->dom[1];
+  c->nff = d->n_fine_faces;
+  c->ncf = d->n_coarse_faces;
+  c->ff.assign(d->fine_faces, d->fine_faces + 2 * (size_t)c->nff);
+  c->cf.assign(d->coarse_faces, d->coarse_faces + 2 * (size_t)c->ncf);
+  const int q = d->iface_quad_pts > 0 ? d->iface_quad_pts : std::max(Dp.N, Dm.N) + 1;
+  if (q > hex::MAXQ) return hfail(DGSEM_EINVAL, "iface_quad_pts %d > %d", q, hex::MAXQ);
+  c->q = q;
+  std::vector<double> gx, gw;
+  dgtab::gauss(q, gx, gw);
+  int* d_ff = nullptr; int* d_cf = nullptr;
+  double *d_fdat = nullptr, *d_cdat = nullptr, *d_refm = nullptr;
+  int* d_match = nullptr;
+  const long long npt = (long long)c->nff * q * q;
+  int rc;
+  auto cleanup = [&]() { dfree(d_ff); dfree(d_cf); dfree(d_fdat); dfree(d_cdat); dfree(d_refm); dfree(d_match); };
+  if ((rc = upload(&d_ff, c->ff)) || (rc = upload(&d_cf, c->cf)) || (rc = dmalloc(&d_fdat, 8 * sizeof(double) * c->nff)) ||
+      (rc = dmalloc(&d_cdat, 8 * sizeof(double) * c->ncf)) || (rc = dmalloc(&d_refm, 3 * sizeof(double) * npt)) ||
+      (rc = dmalloc(&d_match, sizeof(int) * npt)) || (rc = dmalloc(&c->d_pdat, hex::PDAT * sizeof(double) * npt))) {
+    cleanup();
+    return rc;
+  }
+  for (int side = 0; side < 2; ++side) {
+    HexDom& D = side == 0 ? Dp : Dm;
+    hex::FaceArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vert = D.d_vert; a.elem = D.d_elem;
+    a.faces = side == 0 ? d_ff : d_cf;
+    a.nf = side == 0 ? c->nff : c->ncf;
+    a.n = D.n;
+    for (int i = 0; i < D.n; ++i) { a.xi[i] = D.basis->x[i]; a.w[i] = D.basis->w[i]; }
+    a.Mloc = c->d_Mloc + D.vslot0;
+    a.out = side == 0 ? d_fdat : d_cdat;
+    cudaError_t e = hex::launch_faces(a, 0);
+    if (e != cudaSuccess) { cleanup(); return hfail(DGSEM_ECUDA, "face kernel: %s", cudaGetErrorString(e)); }
+  }
+  hex::MatchArgs m;
+  std::memset(&m, 0, sizeof(m));
+  m.vert_p = Dp.d_vert; m.elem_p = Dp.d_elem; m.ff = d_ff; m.fdat = d_fdat;
+  m.vert_m = Dm.d_vert; m.elem_m = Dm.d_elem; m.cf = d_cf; m.cdat = d_cdat;
+  m.nff = c->nff; m.ncf = c->ncf; m.q = q;
+  for (int i = 0; i < q; ++i) { m.g[i] = gx[i]; m.gw[i] = gw[i]; }
+  m.tol = d->normal_tol > 0.0 ? d->normal_tol : 0.5;
+  m.eps = 1e-12;
+  m.match = d_match; m.refm = d_refm;
+  const double cbar = 2.0 * Dp.c * Dm.c / (Dp.c + Dm.c);
+  const int Nmax = std::max(Dp.N, Dm.N);
+  m.alpha_cbar2_n2 = d->penalty_alpha * cbar * cbar * Nmax * Nmax;
+  m.pdat = c->d_pdat;
+  cudaError_t e = hex::launch_match(m, 0);
+  if (e == cudaSuccess) e = hex::launch_ipoints(m, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) { cleanup(); return hfail(DGSEM_ECUDA, "interface matching: %s", cudaGetErrorString(e)); }
+  c->match.resize(npt);
+  c->refm.resize(3 * npt);
+  e = cudaMemcpy(c->match.data(), d_match, sizeof(int) * npt, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(c->refm.data(), d_refm, 3 * sizeof(double) * npt, cudaMemcpyDeviceToHost);
+  cleanup();
+  if (e != cudaSuccess) return hfail(DGSEM_ECUDA, "interface matching: %s", cudaGetErrorString(e));
+  for (long long t = 0; t < npt; ++t)
+    if (c->match[t] < 0)
+      return hfail(DGSEM_ENOMATCH, "fine face %lld, Gauss node %lld has no coarse neighbour (Algorithm 3)",
+                   t / (q * q), t % (q * q));
+  // groups: per fine face, its nodes split by coarse element (first appearance)
+  c->g_fe.clear(); c->g_ce.clear(); c->g_pt.assign(1, 0); c->pt_idx.clear(); c->g_slot.clear();
+  long long slot = c->nvol;
+  c->max_pts = 0;
+  for (int f = 0; f < c->nff; ++f) {
+    std::vector<int> ces;
+    for (int j = 0; j < q * q; ++j) {
+      const int ce = c->cf[2 * c->match[(size_t)f * q * q + j]];
+      if (std::find(ces.begin(), ces.end(), ce) == ces.end()) ces.push_back(ce);
+    }
+    for (int ce : ces) {
+      int cnt = 0;
+      for (int j = 0; j < q * q; ++j)
+        if (c->cf[2 * c->match[(size_t)f * q * q + j]] == ce) {
+          c->pt_idx.push_back(f * q * q + j);
+          ++cnt;
+        }
+      c->g_fe.push_back(c->ff[2 * f]);
+      c->g_ce.push_back(ce);
+      c->g_pt.push_back((int)c->pt_idx.size());
+      c->g_slot.push_back(slot);
+      slot += Dp.nl + Dm.nl;
+      c->max_pts = std::max(c->max_pts, cnt);
+    }
+  }
+  c->ng = (int)c->g_fe.size();
+  c->nislot = slot - c->nvol;
+  if ((rc = upload(&c->d_g_fe, c->g_fe)) || (rc = upload(&c->d_g_ce, c->g_ce)) || (rc = upload(&c->d_g_pt, c->g_pt)) ||
+      (rc = upload(&c->d_pt_idx, c->pt_idx)) || (rc = upload(&c->d_g_slot, c->g_slot)))
+    return rc;
+  return DGSEM_OK;
+}
+
+// Unique nodes of the PMUT faces with W_j = sum_F w_a w_b |J_F| (host, FP64).
+void setup_pmut_nodes(dghex_ctx* c, const std::vector<int>& faces) {
+  const HexDom& D = c->dom[0];
+  std::map<long long, double> W;
+  std::map<long long, std::array<double, 3>> X;
+  for (size_t k = 0; k < faces.size() / 2; ++k) {
+    const int e = faces[2 * k], f = faces[2 * k + 1];
+    double V[24];
+    elem_verts(D, e, V);
+    const int ax = f >> 1, fixed = (f & 1) ? D.N : 0;
+    const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+    for (int i = 0; i < D.nl; ++i) {
+      const int l[3] = {i % D.n, (i / D.n) % D.n, i / (D.n * D.n)};
+      if (l[ax] != fixed) continue;
+      const double r[3] = {D.basis->x[l[0]], D.basis->x[l[1]], D.basis->x[l[2]]};
+      double x[3], J[3][3], nrm[3];
+      hex::tri_map(V, r, x, J);
+      const double dS = hex::face_normal(f, J, nrm);
+      const long long id = D.conn[(size_t)e * D.nl + i];
+      W[id] += D.basis->w[l[t0]] * D.basis->w[l[t1]] * dS;
+      X[id] = {x[0], x[1], x[2]};
+    }
+  }
+  c->pn_id.clear(); c->pn_xyz.clear(); c->pn_w.clear();
+  for (auto& kv : W) {
+    c->pn_id.push_back(kv.first);
+    c->pn_w.push_back(kv.second);
+    const auto& x = X[kv.first];
+    c->pn_xyz.insert(c->pn_xyz.end(), x.begin(), x.end());
+  }
+}
+
+// Receivers: lowest-id containing element (primary first), tensor Lagrange
+// weights at the Newton reference position.
+int setup_receivers(dghex_ctx* c, int R, const double* xyz) {
+  if (R == 0) return DGSEM_OK;
+  int maxn = 0;
+  for (int d = 0; d < c->nd; ++d) maxn = std::max(maxn, c->dom[d].nl);
+  std::vector<double> w((size_t)R * maxn, 0.0);
+  std::vector<long long> off((size_t)R * maxn, 0);
+  std::vector<int> nn(R, 0);
+  for (int r = 0; r < R; ++r) {
+    const double* x = xyz + 3 * (size_t)r;
+    bool done = false;
+    for (int d = 0; d < c->nd && !done; ++d) {
+      const HexDom& D = c->dom[d];
+      for (int e = 0; e < D.ne && !done; ++e) {
+        double V[24];
+        elem_verts(D, e, V);
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int k = 0; k < 8; ++k)
+          for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], V[3 * k + a]);
+            hi[a] = std::max(hi[a], V[3 * k + a]);
+          }
+        const double pad = 1e-9 * std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        bool out = false;
+        for (int a = 0; a < 3; ++a) out = out || x[a] < lo[a] - pad || x[a] > hi[a] + pad;
+        if (out) continue;
+        double ref[3];
+        if (!hex::newton_ref(V, x, ref) || !hex::inside_ref(ref)) continue;
+        double l[3][hex::MAXN1], dl[hex::MAXN1];
+        for (int a = 0; a < 3; ++a) hex::lagrange(D.n, D.basis->x.data(), std::min(1.0, std::max(-1.0, ref[a])), l[a], dl);
+        for (int i = 0; i < D.nl; ++i) {
+          w[(size_t)r * maxn + i] = l[0][i % D.n] * l[1][(i / D.n) % D.n] * l[2][i / (D.n * D.n)];
+          off[(size_t)r * maxn + i] = D.conn[(size_t)e * D.nl + i];
+        }
+        nn[r] = D.nl;
+        done = true;
+      }
+    }
+    if (!done) return hfail(DGSEM_EINVAL, "receiver %d (%g, %g, %g) is outside the mesh", r, x[0], x[1], x[2]);
+  }
+  if ((size_t)R > c->recv_cap || maxn != c->rstride) {
+    dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rnn);
+    int rc;
+    if ((rc = dmalloc(&c->d_rw, sizeof(double) * R * maxn)) || (rc = dmalloc(&c->d_roff, sizeof(long long) * R * maxn)) ||
+        (rc = dmalloc(&c->d_rnn, sizeof(int) * R)))
+      return rc;
+    c->recv_cap = R;
+  }
+  c->rstride = maxn;
+  HCUDA(cudaMemcpy(c->d_rw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  HCUDA(cudaMemcpy(c->d_roff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  HCUDA(cudaMemcpy(c->d_rnn, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return DGSEM_OK;
+}
+
+template <typename T>
+int launch_residual(dghex_ctx* c, cudaStream_t s) {
+  const T* p = static_cast<const T*>(c->P);
+  T* S = static_cast<T*>(c->S);
+  for (int d = 0; d < c->nd; ++d) {
+    const HexDom& D = c->dom[d];
+    hex::HexVolArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = p; a.S = S; a.p_bs = c->ndof; a.s_bs = c->nslot;
+    a.conn = D.d_conn;
+    a.G = std::is_same<T, float>::value ? reinterpret_cast<const T*>(D.d_G32) : reinterpret_cast<const T*>(D.d_G64);
+    a.slot_base = D.vslot0;
+    a.ne = D.ne; a.batch = c->batch;
+    for (int i = 0; i < D.n; ++i)
+      for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
+    HexTimer t(c, s, DGHEX_K_VOL);
+    HCUDA(hex::launch_hex_vol<T>(a, D.n, s));
+  }
+  if (c->nd == 2 && c->ng > 0) {
+    const HexDom &Dp = c->dom[0], &Dm = c->dom[1];
+    hex::HexIfaceArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = p; a.S = S; a.p_bs = c->ndof; a.s_bs = c->nslot;
+    a.conn_p = Dp.d_conn; a.conn_m = Dm.d_conn;
+    a.g_fe = c->d_g_fe; a.g_ce = c->d_g_ce; a.g_pt = c->d_g_pt; a.pt_idx = c->d_pt_idx; a.g_slot = c->d_g_slot;
+    a.pdat = c->d_pdat;
+    for (int i = 0; i < Dp.n; ++i) a.xip[i] = Dp.basis->x[i];
+    for (int i = 0; i < Dm.n; ++i) a.xim[i] = Dm.basis->x[i];
+    a.np = Dp.n; a.nm = Dm.n;
+    a.c2p = Dp.c * Dp.c; a.c2m = Dm.c * Dm.c;
+    a.ng = c->ng; a.batch = c->batch; a.max_pts = c->max_pts;
+    HexTimer t(c, s, DGHEX_K_IFACE);
+    HCUDA(hex::launch_hex_iface<T>(a, s));
+  }
+  return DGSEM_OK;
+}
+
+template <typename T>
+int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp) {
+  hex::HexUpdateArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.p = static_cast<T*>(c->P); a.v = static_cast<T*>(c->V); a.S = static_cast<const T*>(c->S);
+  a.p_bs = c->ndof; a.s_bs = c->nslot;
+  a.node_ptr = c->d_node_ptr; a.node_slot = c->d_node_slot;
+  a.Minv = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_Minv32) : reinterpret_cast<const T*>(c->d_Minv64);
+  a.ndof = c->ndof; a.cv = T(cv); a.cp = T(cp); a.batch = c->batch;
+  HexTimer t(c, s, DGHEX_K_UPDATE);
+  HCUDA(hex::launch_hex_update<T>(a, s));
+  return DGSEM_OK;
+}
+
+template <typename T>
+int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs, long long dks, int R, double* traces,
+                long long tbs, long long trs) {
+  if (c->K > 0) {
+    PmutArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.B = c->batch; a.K = c->K; a.M = c->M;
+    a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_off; a.Bm = c->d_Bm;
+    a.p_prev = static_cast<const T*>(c->P);
+    a.bsp = c->ndof;
+    const long long kmB = (long long)c->batch * c->K * c->M;
+    a.q = c->q_state; a.qd = c->q_state + kmB; a.qdd = c->q_state + 2 * kmB;
+    const long long km = (long long)c->K * c->M;
+    a.omega2 = c->d_modal; a.twozw = c->d_modal + km; a.inv_mu = c->d_modal + 2 * km; a.eta = c->d_modal + 3 * km;
+    a.drive = drive; a.dbs = dbs; a.dks = dks; a.n = 0; a.step = c->d_step; a.dt = c->dt;
+    HexTimer t(c, s, DGHEX_K_PMUT);
+    HCUDA(launch_pmut_recv<T>(a, s));
+  }
+  int rc = launch_residual<T>(c, s);
+  if (rc) return rc;
+  if ((rc = launch_update<T>(c, s, -c->dt, c->dt))) return rc;
+  hex::HexTailArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.nnz = c->nnz; a.M = c->M; a.K = c->K;
+  a.ent_k = c->d_ent_k; a.Bm = c->d_Bm;
+  a.qdd = c->q_state ? c->q_state + 2 * (long long)c->batch * c->K * c->M : nullptr;
+  a.kappa = c->kappa;
+  a.S = static_cast<T*>(c->S); a.s_bs = c->nslot; a.fslot = c->fslot0;
+  a.R = R; a.rstride = c->rstride; a.rw = c->d_rw; a.roff = c->d_roff; a.rnn = c->d_rnn;
+  a.p = static_cast<const T*>(c->P); a.p_bs = c->ndof;
+  a.traces = traces; a.tbs = tbs; a.trs = trs;
+  a.n = 0; a.step = c->d_step; a.done = c->d_done;
+  a.batch = c->batch;
+  a.fblocks = (int)(((long long)c->nnz * c->batch + 255) / 256);
+  HexTimer t(c, s, DGHEX_K_TAIL);
+  HCUDA(hex::launch_hex_tail<T>(a, s));
+  return DGSEM_OK;
+}
+
+template <typename T>
+int upload_field(const std::vector<double>& h, void* dst, int batch, long long ndof, cudaStream_t s) {
+  std::vector<T> t(h.begin(), h.end());
+  for (int b = 0; b < batch; ++b)
+    HCUDA(cudaMemcpyAsync(static_cast<T*>(dst) + (size_t)b * ndof, t.data(), t.size() * sizeof(T),
+                          cudaMemcpyHostToDevice, s));
+  HCUDA(cudaStreamSynchronize(s));
+  return DGSEM_OK;
+}
+
+template <typename T>
+int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
+  const bool fresh = !(flags & DGSEM_RUN_CONTINUE) || !c->state_valid;
+  const size_t es = sizeof(T);
+  if (fresh) {
+    HCUDA(cudaMemsetAsync(c->P, 0, es * c->batch * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->V, 0, es * c->batch * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->S, 0, es * c->batch * c->nslot, s));
+    if (c->q_state) HCUDA(cudaMemsetAsync(c->q_state, 0, sizeof(double) * 3 * (size_t)c->batch * c->K * c->M, s));
+    if (c->has_init) {
+      int rc;
+      if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->P, c->batch, c->ndof, s))) return rc;
+      if (!c->init_v.empty() && (rc = upload_field<T>(c->init_v, c->V, c->batch, c->ndof, s))) return rc;
+      // v^{-1/2} = p'^0 - dt/2 p''^0 with p''^0 = -M^-1 K p^0 (the forcing slots are zero at rest)
+      if ((rc = launch_residual<T>(c, s)) || (rc = launch_update<T>(c, s, 0.5 * c->dt, 0.0))) return rc;
+    }
+  }
+  const double* d_drive = drive;
+  const size_t dn = (size_t)c->batch * c->K * nsteps;
+  if (c->K > 0) {
+    if (!drive) return hfail(DGSEM_EINVAL, "drive is NULL with %d PMUTs", c->K);
+    if (!is_device_ptr(drive)) {
+      if (dn > c->drive_cap) {
+        dfree(c->d_drive);
+        int rc = dmalloc(&c->d_drive, dn * sizeof(double));
+        if (rc) return rc;
+        c->drive_cap = dn;
+      }
+      HCUDA(cudaMemcpyAsync(c->d_drive, drive, dn * sizeof(double), cudaMemcpyHostToDevice, s));
+      d_drive = c->d_drive;
+    }
+  }
+  double* d_traces = traces_out;
+  const size_t tn = (size_t)c->batch * R * nsteps;
+  const bool host_traces = R > 0 && !is_device_ptr(traces_out);
+  if (host_traces) {
+    if (tn > c->traces_cap) {
+      dfree(c->d_traces);
+      int rc = dmalloc(&c->d_traces, tn * sizeof(double));
+      if (rc) return rc;
+      c->traces_cap = tn;
+    }
+    d_traces = c->d_traces;
+  }
+  HCUDA(cudaMemsetAsync(c->d_step, 0, sizeof(int), s));
+  HCUDA(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), s));
+  if (c->profiling) {
+    for (int k = 0; k < DGHEX_K_COUNT; ++k) c->kernel_ms[k] += 0.0;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    int rc = launch_step<T>(c, s, d_drive, (long long)c->K * nsteps, nsteps, R, d_traces, (long long)R * nsteps, nsteps);
+    if (rc) return rc;
+  }
+  if (host_traces) HCUDA(cudaMemcpyAsync(traces_out, d_traces, tn * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HCUDA(cudaStreamSynchronize(s));
+  if (c->profiling) collect_timings(c);
+  else c->ev_used.clear();
+  c->state_valid = true;
+  return DGSEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
+  if (!out) return hfail(DGSEM_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d || !d->domains) return hfail(DGSEM_EINVAL, "desc or domains is NULL");
+  if (d->ndomains < 1 || d->ndomains > 2) return hfail(DGSEM_EINVAL, "ndomains must be 1 or 2");
+  for (int k = 0; k < d->ndomains; ++k) {
+    const dghex_domain_desc& D = d->domains[k];
+    if (D.order < 1 || D.order > 8) return hfail(DGSEM_EINVAL, "domain %d: order must be 1..8", k);
+    if (!(D.c > 0.0) || !(D.rho > 0.0)) return hfail(DGSEM_EINVAL, "domain %d: c and rho must be > 0", k);
+    if (D.n_vert < 8 || D.n_elem < 1 || !D.vert || !D.elem) return hfail(DGSEM_EINVAL, "domain %d: empty mesh", k);
+    for (long long i = 0; i < 8LL * D.n_elem; ++i)
+      if (D.elem[i] < 0 || D.elem[i] >= D.n_vert)
+        return hfail(DGSEM_EINVAL, "domain %d: element %lld lists vertex %d out of range", k, i / 8, D.elem[i]);
+  }
+  if (!(d->penalty_alpha > 0.0) && d->ndomains == 2) return hfail(DGSEM_EINVAL, "penalty_alpha must be > 0");
+  if (d->dt <= 0.0 && !(d->cfl > 0.0)) return hfail(DGSEM_EINVAL, "cfl must be > 0 when dt is not given");
+  auto check_faces = [&](int nf, const int* f, int dom, const char* what) -> int {
+    if (nf < 0 || (nf > 0 && !f)) return hfail(DGSEM_EINVAL, "%s: bad list", what);
+    for (int i = 0; i < nf; ++i)
+      if (f[2 * i] < 0 || f[2 * i] >= d->domains[dom].n_elem || f[2 * i + 1] < 0 || f[2 * i + 1] > 5)
+        return hfail(DGSEM_EINVAL, "%s: entry %d out of range", what, i);
+    return DGSEM_OK;
+  };
+  int rc;
+  if (d->ndomains == 2) {
+    if (d->n_fine_faces < 1 || d->n_coarse_faces < 1) return hfail(DGSEM_EINVAL, "two domains need the interface face lists");
+    if ((rc = check_faces(d->n_fine_faces, d->fine_faces, 0, "fine_faces")) ||
+        (rc = check_faces(d->n_coarse_faces, d->coarse_faces, 1, "coarse_faces")))
+      return rc;
+  }
+  if ((rc = check_faces(d->n_pmut_faces, d->pmut_faces, 0, "pmut_faces"))) return rc;
+  dghex_ctx* c = new dghex_ctx();
+  cudaGetDevice(&c->device);
+  c->nd = d->ndomains;
+  std::vector<std::map<std::array<int, 4>, int>> fcount(c->nd);
+  long long node0 = 0, vslot = 0;
+  for (int k = 0; k < c->nd; ++k) {
+    const dghex_domain_desc& S = d->domains[k];
+    HexDom& D = c->dom[k];
+    D.N = S.order; D.n = S.order + 1; D.nl = D.n * D.n * D.n;
+    D.ne = S.n_elem; D.nv = S.n_vert; D.c = S.c; D.rho = S.rho;
+    D.vert.assign(S.vert, S.vert + 3 * (size_t)S.n_vert);
+    D.elem.assign(S.elem, S.elem + 8 * (size_t)S.n_elem);
+    D.basis = new dgtab::Basis1D(D.N);
+    number_nodes(D, node0, fcount[k]);
+    node0 += D.nnode;
+    D.vslot0 = vslot;
+    vslot += (long long)D.ne * D.nl;
+  }
+  c->ndof = node0;
+  c->nvol = vslot;
+  if (c->ndof >= (1LL << 31) || c->nvol >= (1LL << 31)) {
+    dghex_destroy(c);
+    return hfail(DGSEM_EINVAL, "mesh too large (%lld nodes, %lld element nodes)", node0, vslot);
+  }
+  // listed faces must be boundary faces of their domain
+  auto boundary = [&](int dom, int nf, const int* f, const char* what) -> int {
+    const HexDom& D = c->dom[dom];
+    for (int i = 0; i < nf; ++i) {
+      const int e = f[2 * i], lf = f[2 * i + 1], ax = lf >> 1, side = lf & 1;
+      std::array<int, 4> key;
+      int k = 0;
+      for (int cc = 0; cc < 8; ++cc)
+        if (((cc >> ax) & 1) == side) key[k++] = D.elem[(size_t)e * 8 + cc];
+      std::sort(key.begin(), key.end());
+      if (fcount[dom][key] != 1) return hfail(DGSEM_EINVAL, "%s: entry %d is not a boundary face", what, i);
+    }
+    return DGSEM_OK;
+  };
+  if ((c->nd == 2 && ((rc = boundary(0, d->n_fine_faces, d->fine_faces, "fine_faces")) ||
+                      (rc = boundary(1, d->n_coarse_faces, d->coarse_faces, "coarse_faces")))) ||
+      (rc = boundary(0, d->n_pmut_faces, d->pmut_faces, "pmut_faces"))) {
+    dghex_destroy(c);
+    return rc;
+  }
+  // node positions (host)
+  c->xyz.assign(3 * (size_t)c->ndof, 0.0);
+  for (int k = 0; k < c->nd; ++k) {
+    const HexDom& D = c->dom[k];
+    for (int e = 0; e < D.ne; ++e) {
+      double V[24];
+      elem_verts(D, e, V);
+      for (int i = 0; i < D.nl; ++i) {
+        const double r[3] = {D.basis->x[i % D.n], D.basis->x[(i / D.n) % D.n], D.basis->x[i / (D.n * D.n)]};
+        double x[3], J[3][3];
+        hex::tri_map(V, r, x, J);
+        const long long id = D.conn[(size_t)e * D.nl + i];
+        for (int a = 0; a < 3; ++a) c->xyz[3 * id + a] = x[a];
+      }
+    }
+  }
+  // geometry on the device
+  int* d_bad = nullptr;
+  rc = dmalloc(&c->d_Mloc, sizeof(double) * c->nvol);
+  if (!rc) rc = dmalloc(&d_bad, sizeof(int));
+  if (!rc && cudaMemset(d_bad, 0, sizeof(int)) != cudaSuccess) rc = hfail(DGSEM_ECUDA, "memset");
+  for (int k = 0; k < c->nd && !rc; ++k) {
+    HexDom& D = c->dom[k];
+    if ((rc = upload(&D.d_vert, D.vert)) || (rc = upload(&D.d_elem, D.elem)) || (rc = upload(&D.d_conn, D.conn)) ||
+        (rc = dmalloc(&D.d_G64, sizeof(double) * 6 * (size_t)D.ne * D.nl)) ||
+        (rc = dmalloc(&D.d_G32, sizeof(float) * 6 * (size_t)D.ne * D.nl)))
+      break;
+    hex::GeomArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.vert = D.d_vert; a.elem = D.d_elem; a.ne = D.ne; a.n = D.n;
+    for (int i = 0; i < D.n; ++i) { a.xi[i] = D.basis->x[i]; a.w[i] = D.basis->w[i]; }
+    a.c2 = D.c * D.c;
+    a.G64 = D.d_G64; a.G32 = D.d_G32; a.Mloc = c->d_Mloc + D.vslot0; a.bad = d_bad;
+    const cudaError_t e = hex::launch_geom(a, 0);
+    if (e != cudaSuccess) rc = hfail(DGSEM_ECUDA, "geometry kernel: %s", cudaGetErrorString(e));
+  }
+  int bad = 0;
+  if (!rc && cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = hfail(DGSEM_ECUDA, "geometry kernel failed");
+  dfree(d_bad);
+  if (!rc && bad > 0) rc = hfail(DGSEM_EINVAL, "%d GLL nodes with a non-positive Jacobian", bad);
+  if (rc) {
+    dghex_destroy(c);
+    return rc;
+  }
+  // time step: CFL on the shortest element edge
+  double hmin_t = 1e300, cmax = 0.0;
+  static const int edges[12][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6}, {5, 7}, {0, 4}, {1, 5}, {2, 6}, {3, 7}};
+  for (int k = 0; k < c->nd; ++k) {
+    const HexDom& D = c->dom[k];
+    double gap = 1e300;
+    for (int i = 0; i < D.N; ++i) gap = std::min(gap, D.basis->x[i + 1] - D.basis->x[i]);
+    for (int e = 0; e < D.ne; ++e) {
+      double V[24];
+      elem_verts(D, e, V);
+      double h = 1e300;
+      for (auto& ed : edges) {
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a) s += (V[3 * ed[0] + a] - V[3 * ed[1] + a]) * (V[3 * ed[0] + a] - V[3 * ed[1] + a]);
+        h = std::min(h, std::sqrt(s));
+      }
+      hmin_t = std::min(hmin_t, h / 2.0 * gap);
+    }
+    cmax = std::max(cmax, D.c);
+  }
+  c->dt = d->dt > 0.0 ? d->dt : d->cfl * hmin_t / cmax;
+  if (c->nd == 2 && (rc = setup_interface(c, d))) {
+    dghex_destroy(c);
+    return rc;
+  }
+  std::vector<int> pf(d->pmut_faces, d->pmut_faces + 2 * (size_t)std::max(0, d->n_pmut_faces));
+  setup_pmut_nodes(c, pf);
+  if ((rc = build_slots(c)) || (rc = dmalloc(&c->d_M, sizeof(double) * c->ndof)) ||
+      (rc = dmalloc(&c->d_Minv64, sizeof(double) * c->ndof)) || (rc = dmalloc(&c->d_Minv32, sizeof(float) * c->ndof)) ||
+      (rc = dmalloc(&c->d_step, sizeof(int))) || (rc = dmalloc(&c->d_done, sizeof(unsigned)))) {
+    dghex_destroy(c);
+    return rc;
+  }
+  cudaError_t e = hex::launch_mass(c->d_Mloc, c->d_node_ptr, c->d_node_slot, c->nvol, c->ndof, c->d_Minv64, c->d_Minv32,
+                                   c->d_M, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    dghex_destroy(c);
+    return hfail(DGSEM_ECUDA, "mass kernel: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return DGSEM_OK;
+}
+
+int dghex_get_dt(const dghex_ctx* c, double* dt, long long* ndof) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (dt) *dt = c->dt;
+  if (ndof) *ndof = c->ndof;
+  return DGSEM_OK;
+}
+
+int dghex_nodes(const dghex_ctx* c, long long* ndof, long long* first_secondary, const double** xyz) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (ndof) *ndof = c->ndof;
+  if (first_secondary) *first_secondary = c->nd == 2 ? c->dom[1].node0 : c->ndof;
+  if (xyz) *xyz = c->xyz.data();
+  return DGSEM_OK;
+}
+
+int dghex_pmut_nodes(const dghex_ctx* c, int* n, const double** xyz, const double** weight) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (n) *n = (int)c->pn_id.size();
+  if (xyz) *xyz = c->pn_xyz.data();
+  if (weight) *weight = c->pn_w.data();
+  return DGSEM_OK;
+}
+
+int dghex_pmut_set(dghex_ctx* c, int K, int M, const int* foot_ptr, const int* foot_node, const double* shape_un,
+                   const double* freq_hz, const double* damping, const double* eta, const double* modal_mass) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (K < 0 || M < 1 || M > DG_MAXM) return hfail(DGSEM_EINVAL, "n_pmut >= 0 and 1 <= n_modes <= %d", DG_MAXM);
+  if (K > 0 && (!foot_ptr || !freq_hz || !damping || !eta)) return hfail(DGSEM_EINVAL, "NULL PMUT array");
+  const int npn = (int)c->pn_id.size();
+  std::vector<int> fp_ptr(foot_ptr, foot_ptr + (K > 0 ? K + 1 : 0));
+  if (K > 0 && fp_ptr[0] != 0) return hfail(DGSEM_EINVAL, "foot_ptr[0] must be 0");
+  for (int k = 0; k < K; ++k)
+    if (fp_ptr[k + 1] < fp_ptr[k]) return hfail(DGSEM_EINVAL, "foot_ptr must be non-decreasing");
+  const int nnz = K > 0 ? fp_ptr[K] : 0;
+  if (nnz > 0 && (!foot_node || !shape_un)) return hfail(DGSEM_EINVAL, "NULL footprint");
+  std::vector<long long> off(nnz);
+  std::vector<double> B((size_t)nnz * M);
+  std::vector<int> entk(nnz);
+  for (int k = 0; k < K; ++k)
+    for (int e = fp_ptr[k]; e < fp_ptr[k + 1]; ++e) {
+      const int j = foot_node[e];
+      if (j < 0 || j >= npn) return hfail(DGSEM_EINVAL, "foot_node[%d] = %d out of range", e, j);
+      off[e] = c->pn_id[j];
+      entk[e] = k;
+      for (int m = 0; m < M; ++m) B[(size_t)e * M + m] = c->pn_w[j] * shape_un[(size_t)e * M + m];
+    }
+  std::vector<double> modal(4 * (size_t)K * M);
+  const size_t km = (size_t)K * M;
+  for (size_t i = 0; i < km; ++i) {
+    const double w = 2.0 * M_PI * freq_hz[i];
+    const double mu = modal_mass ? modal_mass[i] : 1.0;
+    if (!(mu > 0.0)) return hfail(DGSEM_EINVAL, "modal_mass must be > 0");
+    modal[i] = w * w;
+    modal[km + i] = 2.0 * damping[i] * w;
+    modal[2 * km + i] = 1.0 / mu;
+    modal[3 * km + i] = eta[i];
+  }
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
+  c->K = K; c->M = M; c->nnz = nnz;
+  c->ent_node = off;
+  c->kappa = c->dom[0].rho * c->dom[0].c * c->dom[0].c;
+  int rc;
+  if ((rc = upload(&c->d_fp_ptr, fp_ptr)) || (rc = upload(&c->d_fp_off, off)) || (rc = upload(&c->d_Bm, B)) ||
+      (rc = upload(&c->d_ent_k, entk)) || (rc = upload(&c->d_modal, modal)))
+    return rc;
+  return build_slots(c);
+}
+
+int dghex_get_matches(const dghex_ctx* c, int* q, int* coarse_face, double* ref, long long n) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (q) *q = c->q;
+  const long long have = (long long)c->match.size();
+  if ((coarse_face || ref) && n < have) return hfail(DGSEM_EINVAL, "arrays hold %lld points, %lld needed", n, have);
+  if (coarse_face) std::copy(c->match.begin(), c->match.end(), coarse_face);
+  if (ref) std::copy(c->refm.begin(), c->refm.end(), ref);
+  return DGSEM_OK;
+}
+
+int dghex_set_state(dghex_ctx* c, const double* p0, const double* v0) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  c->init_p.clear();
+  c->init_v.clear();
+  if (p0) c->init_p.assign(p0, p0 + c->ndof);
+  if (v0) c->init_v.assign(v0, v0 + c->ndof);
+  c->has_init = p0 || v0;
+  c->state_valid = false;
+  return DGSEM_OK;
+}
+
+int dghex_run(dghex_ctx* c, int precision, int batch, int nsteps, const double* drive, int n_recv, const double* recv_xyz,
+              double* traces, int flags, void* stream) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return hfail(DGSEM_EINVAL, "bad precision");
+  if (batch < 1 || nsteps < 0 || n_recv < 0) return hfail(DGSEM_EINVAL, "batch >= 1, nsteps >= 0, n_recv >= 0");
+  if (n_recv > 0 && (!recv_xyz || !traces)) return hfail(DGSEM_EINVAL, "receivers without positions or traces");
+  if ((flags & DGSEM_RUN_CONTINUE) && c->state_valid && (c->prec != precision || c->batch != batch))
+    return hfail(DGSEM_ESTATE, "continuing run with a different precision or batch");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_run_state(c, precision, batch);
+  if (rc) return rc;
+  if (c->K > 0 && !c->q_state && (rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
+  if ((rc = setup_receivers(c, n_recv, recv_xyz))) return rc;
+  if (precision == DGSEM_FP32_MIXED) return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
+  return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
+}
+
+int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
+  if (!c || !p) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (!c->state_valid) return hfail(DGSEM_ESTATE, "no run yet");
+  const size_t n = (size_t)c->batch * c->ndof;
+  if (len < n) return hfail(DGSEM_EINVAL, "p holds %zu values, %zu needed", len, n);
+  if (c->prec == DGSEM_FP32_MIXED) {
+    std::vector<float> t(n);
+    HCUDA(cudaMemcpy(t.data(), c->P, n * sizeof(float), cudaMemcpyDeviceToHost));
+    std::copy(t.begin(), t.end(), p);
+  } else {
+    HCUDA(cudaMemcpy(p, c->P, n * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  return DGSEM_OK;
+}
+
+int dghex_profile(dghex_ctx* c, int enable) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  c->profiling = enable != 0;
+  for (int k = 0; k < DGHEX_K_COUNT; ++k) {
+    c->kernel_ms[k] = 0.0;
+    c->launches[k] = 0;
+  }
+  c->ev_used.clear();
+  return DGSEM_OK;
+}
+
+int dghex_kernel_stats(const dghex_ctx* c, int kind, double* total_ms, long long* launches) {
+  if (!c || kind < 0 || kind >= DGHEX_K_COUNT) return hfail(DGSEM_EINVAL, "bad argument");
+  if (total_ms) *total_ms = c->kernel_ms[kind];
+  if (launches) *launches = c->launches[kind];
+  return DGSEM_OK;
+}
+
+void dghex_destroy(dghex_ctx* c) {
+  if (!c) return;
+  free_run_state(c);
+  for (int k = 0; k < 2; ++k) {
+    HexDom& D = c->dom[k];
+    dfree(D.d_vert); dfree(D.d_elem); dfree(D.d_conn); dfree(D.d_G64); dfree(D.d_G32);
+    delete D.basis;
+    D.basis = nullptr;
+  }
+  dfree(c->d_g_fe); dfree(c->d_g_ce); dfree(c->d_g_pt); dfree(c->d_pt_idx); dfree(c->d_g_slot); dfree(c->d_pdat);
+  dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
+  dfree(c->d_node_ptr); dfree(c->d_node_slot);
+  dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);
+  dfree(c->d_step); dfree(c->d_done);
+  dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rnn);
+  dfree(c->d_drive); dfree(c->d_traces);
+  for (auto ev : c->ev_pool) cudaEventDestroy(ev);
+  delete c;
+}
+
+}  // extern "C"

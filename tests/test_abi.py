@@ -83,3 +83,45 @@ def test_surrogate_symbols_exported(lib):
     assert sorted(surrogate.SRG_EXPORTED) == names
     for n in names:
         assert hasattr(lib, n), n
+
+
+def _declared_hex_functions():
+    src = open(os.path.join(ROOT, "include", "dghex.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_general_hexahedron_symbol(lib):
+    names = _declared_hex_functions()
+    assert "dghex_mesh_create" in names and "dghex_run" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_hex_binding_lists_every_declared_symbol():
+    from paper_2603_06267_gb300 import dghex
+    assert sorted(dghex.EXPORTED) == _declared_hex_functions()
+
+
+def test_invalid_hex_mesh_rejected_without_gpu(lib):
+    """Bad orders, vertex ids and face lists are refused on the host."""
+    from paper_2603_06267_gb300 import dghex, dgsem
+    from workloads import hex as H
+    w = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=2, order_s=2)
+    prim, sec = w.domains
+    bad = H.HexDomain(prim.vertices, prim.elements, 9)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create([bad])
+    assert e.value.code == dgsem.DGSEM_EINVAL and "order" in str(e.value)
+    els = prim.elements.copy()
+    els[0, 3] = prim.vertices.shape[0]
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create([H.HexDomain(prim.vertices, els, 2)])
+    assert e.value.code == dgsem.DGSEM_EINVAL and "vertex" in str(e.value)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create([prim, sec])          # two domains without the interface lists
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    inner = np.array([[0, 1]])                        # the face shared by elements 0 and 1
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create([prim], pmut_faces=inner)
+    assert e.value.code == dgsem.DGSEM_EINVAL and "boundary" in str(e.value)

@@ -1,0 +1,180 @@
+"""General hexahedra on the GPU (C ABI include/dghex.h) against the
+trilinear-element oracle: Algorithm 3 matches, node positions and PMUT face
+weights, receiver traces and full fields in FP64 (rel-L2 <= 1e-10) and FP32
+(<= 1e-4), element orientation, batching, continued runs, the affine case
+against the box path, and the error paths."""
+import numpy as np
+import pytest
+
+import workloads as W
+from workloads import hex as H
+from oracle import hex_oracle as HO
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _node_map(prob, xyz, first_sec):
+    """index into the library's node array of every oracle node (per domain)."""
+    from scipy.spatial import cKDTree
+    out = []
+    bounds = [(0, first_sec), (first_sec, xyz.shape[0])]
+    for m, (lo, hi) in zip(prob.meshes, bounds):
+        d, idx = cKDTree(xyz[lo:hi]).query(m.coords)
+        assert np.max(d) < 1e-12 * 1e-3
+        assert np.unique(idx).size == idx.size == hi - lo
+        out.append(idx + lo)
+    return np.concatenate(out)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2603_06267_gb300 import dghex
+    return dghex.load_library()
+
+
+@pytest.fixture(scope="module")
+def two_dom():
+    w = H.distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=120, scramble=3)
+    return w, HO.HexOracleProblem(w)
+
+
+def test_matching_equals_oracle(lib, two_dom):
+    from paper_2603_06267_gb300 import dghex
+    w, prob = two_dom
+    s = dghex.HexSolver(w)
+    q, cf, ref = dghex.dghex_get_matches(s.ctx, len(w.fine_faces))
+    assert q == prob.nq
+    for f, (F, refp, xq, per) in enumerate(prob.matches):
+        for j, (gi, refm) in enumerate(per):
+            assert cf[f, j] == gi
+            assert np.max(np.abs(ref[f, j] - refm)) < 1e-12
+    s.close()
+
+
+def test_nodes_mass_layout_and_pmut_weights(lib, two_dom):
+    from paper_2603_06267_gb300 import dghex
+    w, prob = two_dom
+    s = dghex.HexSolver(w)
+    xyz, first = dghex.dghex_nodes(s.ctx)
+    assert xyz.shape[0] == prob.nh and first == prob.meshes[1].offset
+    _node_map(prob, xyz, first)
+    ids, pxyz, Wf = prob.pmut_face_nodes()
+    gx, gw = dghex.dghex_pmut_nodes(s.ctx)
+    from scipy.spatial import cKDTree
+    d, idx = cKDTree(gx).query(pxyz)
+    assert np.max(d) < 1e-15 and gx.shape[0] == pxyz.shape[0]
+    np.testing.assert_allclose(gw[idx], Wf, rtol=1e-13)
+    dt, ndof = dghex.dghex_get_dt(s.ctx)
+    assert ndof == prob.nh and abs(dt - prob.stable_dt()) < 1e-15 * dt
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_two_domain_pmut_parity(lib, two_dom, prec, tol):
+    """Distorted fine/coarse pair with a bent 2:1 interface, rotated element
+    frames and a driven PMUT array: traces and the final field."""
+    from paper_2603_06267_gb300 import dghex
+    w, prob = two_dom
+    s = dghex.HexSolver(w)
+    tr = s.run(precision=prec)
+    ref = prob.run(dt=s.dt)
+    assert np.max(np.abs(ref)) > 0
+    assert _rel(tr, ref) < tol, _rel(tr, ref)
+    xyz, first = dghex.dghex_nodes(s.ctx)
+    idx = _node_map(prob, xyz, first)
+    p = dghex.dghex_get_pressure(s.ctx, 1, s.ndof)[0]
+    assert _rel(p[idx], prob.final_state["p"][:, 0]) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_one_domain_initial_state_parity(lib, prec, tol):
+    """Distorted single box, orders 3 and 5, a smooth initial state and no
+    PMUT (the set-state start p''0 = -M^-1 K p0)."""
+    from paper_2603_06267_gb300 import dghex
+    for order, scr in ((3, None), (5, 9)):
+        w = H.distorted_one_domain(nel=(3, 2, 2), order=order, nsteps=60, scramble=scr)
+        w.pmuts = None
+        prob = HO.HexOracleProblem(w)
+        s = dghex.HexSolver(w)
+        xyz, first = dghex.dghex_nodes(s.ctx)
+        idx = _node_map(prob, xyz, first)
+        X = prob.meshes[0].coords
+        p0 = W.seeded_field(5, X[:, 0], X[:, 1], X[:, 2])
+        v0 = 1e6 * W.seeded_field(6, X[:, 0], X[:, 1], X[:, 2])
+        g0 = np.zeros(s.ndof); g0[idx] = p0
+        gv = np.zeros(s.ndof); gv[idx] = v0
+        dghex.dghex_set_state(s.ctx, g0, gv)
+        tr = s.run(precision=prec)
+        ref = prob.run(dt=s.dt, p0=p0, v0=v0)
+        assert _rel(tr, ref) < tol, (order, _rel(tr, ref))
+        s.close()
+
+
+def test_batch_members_are_independent(lib):
+    """Three drive patterns in one run equal three single runs bit for bit."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40, batch=3, steer=True)
+    s = dghex.HexSolver(w)
+    drive = w.drive(s.dt, w.nsteps, 3)
+    for prec in (0, 1):
+        tr = s.run(drive=drive, precision=prec, batch=3)
+        for b in range(3):
+            one = s.run(drive=np.ascontiguousarray(drive[b:b + 1]), precision=prec, batch=1)
+            assert np.array_equal(one[0], tr[b])
+    s.close()
+
+
+def test_continued_run_equals_single_run(lib):
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=50)
+    s = dghex.HexSolver(w)
+    drive = w.drive(s.dt, 50, 1)
+    full = s.run(drive=drive, nsteps=50)
+    a = s.run(drive=np.ascontiguousarray(drive[:, :, :30]), nsteps=30)
+    b = s.run(drive=np.ascontiguousarray(drive[:, :, 30:]), nsteps=20, flags=1)
+    assert np.array_equal(np.concatenate([a, b], axis=2), full)
+    s.close()
+
+
+def test_affine_mesh_matches_box_path(lib):
+    """The lattice of a box workload given as general hexahedra gives the
+    box path's traces (two different GPU implementations of one operator)."""
+    from paper_2603_06267_gb300 import dghex, dgsem
+    wb = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, nsteps=80)
+    wh = H.hex_workload_from_box(wb)
+    sb = dgsem.Solver(wb)
+    sh = dghex.HexSolver(wh)
+    assert abs(sb.dt - sh.dt) < 1e-15 * sb.dt
+    drive = wb.drive(sb.dt, wb.nsteps, 1)
+    tb = sb.run(drive=drive)
+    th = sh.run(drive=drive)
+    assert _rel(th, tb) < 1e-11, _rel(th, tb)
+    sb.close()
+    sh.close()
+
+
+def test_errors_inverted_element_and_unmatched_interface(lib):
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w = H.distorted_two_domain(nx_p=2, nz_p=1, nx_s=1, nz_s=1, n_pmut_side=1, order_p=2, order_s=2)
+    prim, sec = w.domains
+    inv = prim.elements.copy()
+    inv[0] = inv[0][[1, 0, 3, 2, 5, 4, 7, 6]]         # mirrored: negative Jacobian
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create([H.HexDomain(prim.vertices, inv, 2)])
+    assert e.value.code == dgsem.DGSEM_EINVAL and "Jacobian" in str(e.value)
+    w4 = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=1, n_pmut_side=1, order_p=2, order_s=2)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_mesh_create(w4.domains, w4.fine_faces, w4.coarse_faces[:3], w4.pmut_faces)
+    assert e.value.code == dgsem.DGSEM_ENOMATCH
+    # the library stays usable
+    s = dghex.HexSolver(w)
+    s.run(nsteps=3)
+    s.close()
