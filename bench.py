@@ -53,7 +53,8 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config4_batched",
-                    choices=["config4_batched", "config3_array32", "config2_array16", "config1_single_pmut"])
+                    choices=["config4_batched", "config3_array32", "config2_array16", "config1_single_pmut",
+                             "hex_c3_like", "hex_c2_like"])
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -106,12 +107,26 @@ def whole_job_rate(ndof, batch, steps, world, seconds):
 
 
 def default_precision(name):
-    return "fp32" if name in ("config4_batched", "config3_array32") else "fp64"
+    return "fp32" if name in ("config4_batched", "config3_array32", "hex_c3_like", "hex_c2_like") else "fp64"
+
+
+def is_hex(name):
+    return name.startswith("hex_")
+
+
+def make_hex_workload(name, batch):
+    from workloads import hex as H
+    if name == "hex_c3_like":
+        return H.hex_c3_like(nsteps=1, batch=batch or 64)
+    return H.hex_c2_like(nsteps=1, batch=batch or 8)
 
 
 def oracle_sample(name):
     """Bounded sample of the workload for the CPU oracle: the same element
     types, orders and PMUT model on a crop the oracle assembles in seconds."""
+    if is_hex(name):
+        from workloads import hex as H
+        return H.distorted_two_domain(nx_p=8, nz_p=4, nx_s=4, nz_s=6, n_pmut_side=2, nsteps=1)
     if name == "config1_single_pmut":
         return W.config1_single_pmut(nsteps=1)
     return W.small_two_domain(nx_p=8, nz_p=4, nx_s=4, nz_s=8, n_pmut_side=2, nsteps=1)
@@ -120,9 +135,8 @@ def oracle_sample(name):
 def time_oracle(name, seconds=15.0, chunk=None):
     """Oracle Gdof-steps/s on the bounded sample (single host thread: scipy's
     sparse mat-vec and numpy's element-wise kernels run on one core)."""
-    from oracle import dgsem_oracle as O
     w = oracle_sample(name)
-    P = O.OracleProblem(w)
+    P = _oracle_problem(w)
     dt = P.stable_dt()
     n = 8
     while True:
@@ -137,10 +151,22 @@ def time_oracle(name, seconds=15.0, chunk=None):
     t0 = time.perf_counter()
     P.run(nsteps=S, dt=dt, batch=1)
     el = time.perf_counter() - t0
-    sample = (f"{w.name}: primary {w.domains[0].nelem} N={w.domains[0].order}"
-              + (f" + secondary {w.domains[1].nelem} N={w.domains[1].order}" if len(w.domains) > 1 else "")
+    sample = (f"{w.name}: primary {_nelem(w.domains[0])} N={w.domains[0].order}"
+              + (f" + secondary {_nelem(w.domains[1])} N={w.domains[1].order}" if len(w.domains) > 1 else "")
               + f", {P.nh} nodes, {S} steps, batch 1")
     return P.nh * S / el / 1e9, sample, P, w, dt
+
+
+def _oracle_problem(w):
+    if hasattr(w, "pmut_faces"):
+        from oracle import hex_oracle as HO
+        return HO.HexOracleProblem(w)
+    from oracle import dgsem_oracle as O
+    return O.OracleProblem(w)
+
+
+def _nelem(d):
+    return tuple(d.nelem) if hasattr(d, "nelem") else tuple(d.lattice)
 
 
 class ClockSampler:
@@ -205,9 +231,8 @@ def run_reference(args):
         return
     name = args.workload
     prec = args.precision or default_precision(name)
-    from oracle import dgsem_oracle as O
     w = oracle_sample(name)
-    P = O.OracleProblem(w)
+    P = _oracle_problem(w)
     dt = P.stable_dt()
     # chunk of oracle time steps per bench step: about 0.5 s each
     n = 4
@@ -250,6 +275,9 @@ def main():
     from paper_2603_06267_gb300 import dgsem
 
     name = args.workload
+    if is_hex(name):
+        main_hex(args, torch, dist, rank, world, local)
+        return
     prec_name = args.precision or default_precision(name)
     prec = dgsem.DGSEM_FP32_MIXED if prec_name == "fp32" else dgsem.DGSEM_FP64
     w = replica_workload(name, args.batch, rank, world)
@@ -368,6 +396,102 @@ def main():
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def main_hex(args, torch, dist, rank, world, local):
+    """General hexahedra (include/dghex.h): the same step on distorted
+    trilinear meshes with a bent 2:1 interface."""
+    from paper_2603_06267_gb300 import dghex
+    name = args.workload
+    prec_name = args.precision or default_precision(name)
+    prec = dghex.DGSEM_FP32_MIXED if prec_name == "fp32" else dghex.DGSEM_FP64
+    w = make_hex_workload(name, args.batch)
+    B = w.batch
+    t0 = time.perf_counter()
+    sol = dghex.HexSolver(w)
+    setup_s = time.perf_counter() - t0
+    ndof = sol.ndof
+    K_p = w.pmuts.n_pmut
+    R = w.receivers.shape[0]
+    S_tot = args.warmup + args.steps
+    drive_all = w.drive(sol.dt, S_tot + args.steps, B)
+    stream = torch.cuda.current_stream()
+    d_warm = torch.tensor(np.ascontiguousarray(drive_all[:, :, :args.warmup]), device="cuda")
+    d_time = torch.tensor(np.ascontiguousarray(drive_all[:, :, args.warmup:S_tot]), device="cuda")
+    tr_warm = torch.zeros((B, R, args.warmup), dtype=torch.float64, device="cuda")
+    tr_time = torch.zeros((B, R, args.steps), dtype=torch.float64, device="cuda")
+    sol.run(drive=d_warm, precision=prec, nsteps=args.warmup, traces=tr_warm)
+    torch.cuda.synchronize()
+    clocks_dir = os.environ.get("DGSEM_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+    clocks_path = os.path.join(clocks_dir, f".bench_clocks_{rank}.csv")
+    dghex.dghex_profile(sol.ctx, False)
+    with ClockSampler(clocks_path) as cs:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dghex._dg.DGSEM_RUN_CONTINUE,
+                stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = sum(dghex.dghex_kernel_stats(sol.ctx, k)[1] for k in range(5))
+        dghex.dghex_profile(sol.ctx, True)
+        sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dghex._dg.DGSEM_RUN_CONTINUE,
+                stream=stream.cuda_stream)
+        kstats = [dghex.dghex_kernel_stats(sol.ctx, k) for k in range(5)]
+        dghex.dghex_profile(sol.ctx, False)
+        e2e = None
+        if not args.no_e2e:
+            h_drive = torch.from_numpy(np.ascontiguousarray(drive_all[:, :, S_tot:S_tot + args.steps])).pin_memory()
+            h_tr = torch.zeros((B, R, args.steps), dtype=torch.float64).pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sol.run(drive=h_drive, precision=prec, nsteps=args.steps, traces=h_tr,
+                    flags=dghex._dg.DGSEM_RUN_CONTINUE, stream=stream.cuda_stream)
+            e2e_s = time.perf_counter() - t0
+            e2e = {"value": whole_job_rate(ndof, B, args.steps, 1, e2e_s), "unit": "Gdof-steps/s",
+                   "h2d_bytes_per_step": int(B * K_p * 8), "d2h_bytes_per_step": int(B * R * 8)}
+    finite = bool(torch.isfinite(tr_time).all().item())
+    value = whole_job_rate(ndof, B, args.steps, 1, ms / 1e3)
+    names = ["pmut", "vol", "iface", "update", "tail"]
+    es = 4 if prec == dghex.DGSEM_FP32_MIXED else 8
+    # algorithmic bytes per launch (DRAM, the work each kernel must move)
+    nl = [(d.order + 1) ** 3 for d in w.domains]
+    ne = [d.elements.shape[0] for d in w.domains]
+    ploc = sum(a * b for a, b in zip(nl, ne))                 # element-local nodes = volume slots
+    # vol (both domains, per launch averaged over the two launches): p read once per node,
+    # the element-local residual written, geometric factors and node ids read once
+    vol_bytes = (ndof * B * es + ploc * B * es + ploc * (6 * es + 4)) / len(w.domains)
+    upd_bytes = ndof * B * 4 * es + ploc * B * es + ndof * (es + 4) + ploc * 4
+    alg = {"vol": vol_bytes, "update": upd_bytes}
+    kdom = max((1, 3), key=lambda k: kstats[k][0])
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
+    achieved = alg[names[kdom]] / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": names[kdom], "peak_source": "measured" if peaks else "fallback",
+            "alg_bytes_per_launch": alg[names[kdom]]}
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, sample, _, _, _ = time_oracle(name, seconds=15.0)
+        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+    out = {
+        "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dghex.DGSEM_FP32_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "precision": "fp32-mixed" if prec == dghex.DGSEM_FP32_MIXED else "fp64",
+                   "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
+                   "elements": ne, "orders": [d.order for d in w.domains], "setup_s": setup_s,
+                   "parallelism": "single-gpu",
+                   "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cs.summary(local),
+        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(5) if kstats[k][1]},
+        "finite": finite,
+    }
+    print(json.dumps(out), flush=True)
 
 
 if __name__ == "__main__":

@@ -247,9 +247,11 @@ struct dghex_ctx {
   long long nslot = 0;
   int* d_node_ptr = nullptr; int* d_node_slot = nullptr;
   double* d_Mloc = nullptr; double* d_M = nullptr; double* d_Minv64 = nullptr; float* d_Minv32 = nullptr;
-  // run state
-  int prec = -1, batch = 0;
+  // run state: fields batch-innermost, row length Bp (the batch padded to a
+  // multiple of the 32-byte vector width when it is at least that wide)
+  int prec = -1, batch = 0, Bp = 0;
   void* P = nullptr; void* V = nullptr; void* S = nullptr;
+  long long* d_fp_offB = nullptr;          // footprint node offsets j * Bp for the PMUT kernel
   double* q_state = nullptr;
   bool state_valid = false;
   int* d_step = nullptr; unsigned* d_done = nullptr;
@@ -258,6 +260,7 @@ struct dghex_ctx {
   // receivers and scratch for host-pointer runs
   double* d_rw = nullptr; long long* d_roff = nullptr; int* d_rnn = nullptr;
   size_t recv_cap = 0; int rstride = 0;
+  std::vector<double> recv_xyz;            // positions the receiver tables were built for
   double* d_drive = nullptr; size_t drive_cap = 0;
   double* d_traces = nullptr; size_t traces_cap = 0;
   // instrumentation
@@ -300,9 +303,10 @@ void collect_timings(dghex_ctx* c) {
 }
 
 void free_run_state(dghex_ctx* c) {
-  dfree(c->P); dfree(c->V); dfree(c->S); dfree(c->q_state);
+  dfree(c->P); dfree(c->V); dfree(c->S); dfree(c->q_state); dfree(c->d_fp_offB);
   c->prec = -1;
   c->batch = 0;
+  c->Bp = 0;
   c->state_valid = false;
 }
 
@@ -310,13 +314,21 @@ int ensure_run_state(dghex_ctx* c, int prec, int batch) {
   if (c->prec == prec && c->batch == batch && c->P) return DGSEM_OK;
   free_run_state(c);
   const size_t es = prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
+  const int vw = (int)(32 / es);
+  const int Bp = batch < vw ? batch : (batch + vw - 1) / vw * vw;
   int rc;
-  if ((rc = dmalloc(&c->P, es * batch * c->ndof)) || (rc = dmalloc(&c->V, es * batch * c->ndof)) ||
-      (rc = dmalloc(&c->S, es * batch * c->nslot)))
+  if ((rc = dmalloc(&c->P, es * Bp * c->ndof)) || (rc = dmalloc(&c->V, es * Bp * c->ndof)) ||
+      (rc = dmalloc(&c->S, es * Bp * c->nslot)))
     return rc;
-  if (c->K > 0 && (rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
+  if (c->K > 0) {
+    if ((rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
+    std::vector<long long> off(c->ent_node);
+    for (auto& o : off) o *= Bp;
+    if ((rc = upload(&c->d_fp_offB, off))) return rc;
+  }
   c->prec = prec;
   c->batch = batch;
+  c->Bp = Bp;
   return DGSEM_OK;
 }
 
@@ -488,6 +500,9 @@ void setup_pmut_nodes(dghex_ctx* c, const std::vector<int>& faces) {
 // weights at the Newton reference position.
 int setup_receivers(dghex_ctx* c, int R, const double* xyz) {
   if (R == 0) return DGSEM_OK;
+  if (c->recv_xyz.size() == 3 * (size_t)R && std::equal(c->recv_xyz.begin(), c->recv_xyz.end(), xyz))
+    return DGSEM_OK;
+  c->recv_xyz.clear();
   int maxn = 0;
   for (int d = 0; d < c->nd; ++d) maxn = std::max(maxn, c->dom[d].nl);
   std::vector<double> w((size_t)R * maxn, 0.0);
@@ -537,6 +552,7 @@ int setup_receivers(dghex_ctx* c, int R, const double* xyz) {
   HCUDA(cudaMemcpy(c->d_rw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
   HCUDA(cudaMemcpy(c->d_roff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
   HCUDA(cudaMemcpy(c->d_rnn, nn.data(), nn.size() * sizeof(int), cudaMemcpyHostToDevice));
+  c->recv_xyz.assign(xyz, xyz + 3 * (size_t)R);
   return DGSEM_OK;
 }
 
@@ -548,11 +564,11 @@ int launch_residual(dghex_ctx* c, cudaStream_t s) {
     const HexDom& D = c->dom[d];
     hex::HexVolArgs<T> a;
     std::memset(&a, 0, sizeof(a));
-    a.p = p; a.S = S; a.p_bs = c->ndof; a.s_bs = c->nslot;
+    a.p = p; a.S = S; a.Bp = c->Bp;
     a.conn = D.d_conn;
     a.G = std::is_same<T, float>::value ? reinterpret_cast<const T*>(D.d_G32) : reinterpret_cast<const T*>(D.d_G64);
     a.slot_base = D.vslot0;
-    a.ne = D.ne; a.batch = c->batch;
+    a.ne = D.ne;
     for (int i = 0; i < D.n; ++i)
       for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
     HexTimer t(c, s, DGHEX_K_VOL);
@@ -562,7 +578,7 @@ int launch_residual(dghex_ctx* c, cudaStream_t s) {
     const HexDom &Dp = c->dom[0], &Dm = c->dom[1];
     hex::HexIfaceArgs<T> a;
     std::memset(&a, 0, sizeof(a));
-    a.p = p; a.S = S; a.p_bs = c->ndof; a.s_bs = c->nslot;
+    a.p = p; a.S = S; a.Bp = c->Bp;
     a.conn_p = Dp.d_conn; a.conn_m = Dm.d_conn;
     a.g_fe = c->d_g_fe; a.g_ce = c->d_g_ce; a.g_pt = c->d_g_pt; a.pt_idx = c->d_pt_idx; a.g_slot = c->d_g_slot;
     a.pdat = c->d_pdat;
@@ -570,7 +586,7 @@ int launch_residual(dghex_ctx* c, cudaStream_t s) {
     for (int i = 0; i < Dm.n; ++i) a.xim[i] = Dm.basis->x[i];
     a.np = Dp.n; a.nm = Dm.n;
     a.c2p = Dp.c * Dp.c; a.c2m = Dm.c * Dm.c;
-    a.ng = c->ng; a.batch = c->batch; a.max_pts = c->max_pts;
+    a.ng = c->ng; a.max_pts = c->max_pts;
     HexTimer t(c, s, DGHEX_K_IFACE);
     HCUDA(hex::launch_hex_iface<T>(a, s));
   }
@@ -582,10 +598,10 @@ int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp) {
   hex::HexUpdateArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.p = static_cast<T*>(c->P); a.v = static_cast<T*>(c->V); a.S = static_cast<const T*>(c->S);
-  a.p_bs = c->ndof; a.s_bs = c->nslot;
+  a.Bp = c->Bp;
   a.node_ptr = c->d_node_ptr; a.node_slot = c->d_node_slot;
   a.Minv = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_Minv32) : reinterpret_cast<const T*>(c->d_Minv64);
-  a.ndof = c->ndof; a.cv = T(cv); a.cp = T(cp); a.batch = c->batch;
+  a.ndof = c->ndof; a.cv = T(cv); a.cp = T(cp);
   HexTimer t(c, s, DGHEX_K_UPDATE);
   HCUDA(hex::launch_hex_update<T>(a, s));
   return DGSEM_OK;
@@ -598,9 +614,9 @@ int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs
     PmutArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.B = c->batch; a.K = c->K; a.M = c->M;
-    a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_off; a.Bm = c->d_Bm;
+    a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_offB; a.Bm = c->d_Bm;
     a.p_prev = static_cast<const T*>(c->P);
-    a.bsp = c->ndof;
+    a.bsp = 1;
     const long long kmB = (long long)c->batch * c->K * c->M;
     a.q = c->q_state; a.qd = c->q_state + kmB; a.qdd = c->q_state + 2 * kmB;
     const long long km = (long long)c->K * c->M;
@@ -614,28 +630,28 @@ int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs
   if ((rc = launch_update<T>(c, s, -c->dt, c->dt))) return rc;
   hex::HexTailArgs<T> a;
   std::memset(&a, 0, sizeof(a));
-  a.nnz = c->nnz; a.M = c->M; a.K = c->K;
+  a.nnz = c->nnz; a.M = c->M; a.K = c->K; a.B = c->batch; a.Bp = c->Bp;
   a.ent_k = c->d_ent_k; a.Bm = c->d_Bm;
   a.qdd = c->q_state ? c->q_state + 2 * (long long)c->batch * c->K * c->M : nullptr;
   a.kappa = c->kappa;
-  a.S = static_cast<T*>(c->S); a.s_bs = c->nslot; a.fslot = c->fslot0;
+  a.S = static_cast<T*>(c->S); a.fslot = c->fslot0;
   a.R = R; a.rstride = c->rstride; a.rw = c->d_rw; a.roff = c->d_roff; a.rnn = c->d_rnn;
-  a.p = static_cast<const T*>(c->P); a.p_bs = c->ndof;
+  a.p = static_cast<const T*>(c->P);
   a.traces = traces; a.tbs = tbs; a.trs = trs;
   a.n = 0; a.step = c->d_step; a.done = c->d_done;
-  a.batch = c->batch;
   a.fblocks = (int)(((long long)c->nnz * c->batch + 255) / 256);
   HexTimer t(c, s, DGHEX_K_TAIL);
   HCUDA(hex::launch_hex_tail<T>(a, s));
   return DGSEM_OK;
 }
 
+// one FP64 field broadcast to every batch member (padding members stay 0)
 template <typename T>
-int upload_field(const std::vector<double>& h, void* dst, int batch, long long ndof, cudaStream_t s) {
-  std::vector<T> t(h.begin(), h.end());
-  for (int b = 0; b < batch; ++b)
-    HCUDA(cudaMemcpyAsync(static_cast<T*>(dst) + (size_t)b * ndof, t.data(), t.size() * sizeof(T),
-                          cudaMemcpyHostToDevice, s));
+int upload_field(const std::vector<double>& h, void* dst, int batch, int Bp, long long ndof, cudaStream_t s) {
+  std::vector<T> t((size_t)ndof * Bp, T(0));
+  for (long long j = 0; j < ndof; ++j)
+    for (int b = 0; b < batch; ++b) t[(size_t)j * Bp + b] = T(h[j]);
+  HCUDA(cudaMemcpyAsync(dst, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   HCUDA(cudaStreamSynchronize(s));
   return DGSEM_OK;
 }
@@ -645,14 +661,14 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
   const bool fresh = !(flags & DGSEM_RUN_CONTINUE) || !c->state_valid;
   const size_t es = sizeof(T);
   if (fresh) {
-    HCUDA(cudaMemsetAsync(c->P, 0, es * c->batch * c->ndof, s));
-    HCUDA(cudaMemsetAsync(c->V, 0, es * c->batch * c->ndof, s));
-    HCUDA(cudaMemsetAsync(c->S, 0, es * c->batch * c->nslot, s));
+    HCUDA(cudaMemsetAsync(c->P, 0, es * c->Bp * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->V, 0, es * c->Bp * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->S, 0, es * c->Bp * c->nslot, s));
     if (c->q_state) HCUDA(cudaMemsetAsync(c->q_state, 0, sizeof(double) * 3 * (size_t)c->batch * c->K * c->M, s));
     if (c->has_init) {
       int rc;
-      if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->P, c->batch, c->ndof, s))) return rc;
-      if (!c->init_v.empty() && (rc = upload_field<T>(c->init_v, c->V, c->batch, c->ndof, s))) return rc;
+      if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->P, c->batch, c->Bp, c->ndof, s))) return rc;
+      if (!c->init_v.empty() && (rc = upload_field<T>(c->init_v, c->V, c->batch, c->Bp, c->ndof, s))) return rc;
       // v^{-1/2} = p'^0 - dt/2 p''^0 with p''^0 = -M^-1 K p^0 (the forcing slots are zero at rest)
       if ((rc = launch_residual<T>(c, s)) || (rc = launch_update<T>(c, s, 0.5 * c->dt, 0.0))) return rc;
     }
@@ -804,8 +820,8 @@ int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
   for (int k = 0; k < c->nd && !rc; ++k) {
     HexDom& D = c->dom[k];
     if ((rc = upload(&D.d_vert, D.vert)) || (rc = upload(&D.d_elem, D.elem)) || (rc = upload(&D.d_conn, D.conn)) ||
-        (rc = dmalloc(&D.d_G64, sizeof(double) * 6 * (size_t)D.ne * D.nl)) ||
-        (rc = dmalloc(&D.d_G32, sizeof(float) * 6 * (size_t)D.ne * D.nl)))
+        (rc = dmalloc(&D.d_G64, sizeof(double) * 6 * (size_t)D.ne * hex::gstride(D.n))) ||
+        (rc = dmalloc(&D.d_G32, sizeof(float) * 6 * (size_t)D.ne * hex::gstride(D.n))))
       break;
     hex::GeomArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -969,7 +985,6 @@ int dghex_run(dghex_ctx* c, int precision, int batch, int nsteps, const double* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = ensure_run_state(c, precision, batch);
   if (rc) return rc;
-  if (c->K > 0 && !c->q_state && (rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
   if ((rc = setup_receivers(c, n_recv, recv_xyz))) return rc;
   if (precision == DGSEM_FP32_MIXED) return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
   return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
@@ -978,15 +993,18 @@ int dghex_run(dghex_ctx* c, int precision, int batch, int nsteps, const double* 
 int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
   if (!c || !p) return hfail(DGSEM_EINVAL, "NULL argument");
   if (!c->state_valid) return hfail(DGSEM_ESTATE, "no run yet");
-  const size_t n = (size_t)c->batch * c->ndof;
+  const size_t n = (size_t)c->batch * c->ndof, nb = (size_t)c->Bp * c->ndof;
   if (len < n) return hfail(DGSEM_EINVAL, "p holds %zu values, %zu needed", len, n);
+  std::vector<double> t(nb);
   if (c->prec == DGSEM_FP32_MIXED) {
-    std::vector<float> t(n);
-    HCUDA(cudaMemcpy(t.data(), c->P, n * sizeof(float), cudaMemcpyDeviceToHost));
-    std::copy(t.begin(), t.end(), p);
+    std::vector<float> f(nb);
+    HCUDA(cudaMemcpy(f.data(), c->P, nb * sizeof(float), cudaMemcpyDeviceToHost));
+    std::copy(f.begin(), f.end(), t.begin());
   } else {
-    HCUDA(cudaMemcpy(p, c->P, n * sizeof(double), cudaMemcpyDeviceToHost));
+    HCUDA(cudaMemcpy(t.data(), c->P, nb * sizeof(double), cudaMemcpyDeviceToHost));
   }
+  for (int b = 0; b < c->batch; ++b)
+    for (long long j = 0; j < c->ndof; ++j) p[(size_t)b * c->ndof + j] = t[(size_t)j * c->Bp + b];
   return DGSEM_OK;
 }
 

@@ -138,14 +138,17 @@ HXD void lagrange(int n, const double* xi, double t, double* l, double* dl) {
 // Kernel parameter blocks
 // ---------------------------------------------------------------------------
 // Setup: geometric factors c^2 w_abc |J| J^-1 J^-T (6 symmetric entries, order
-// 00 11 22 01 02 12) and w_abc |J| at every GLL node of every element.
+// 00 11 22 01 02 12) and w_abc |J| at every GLL node of every element.  The
+// factors are stored [element][entry][gstride(n)] with the row padded to a
+// multiple of 4 values, so every row starts on a 16-byte boundary.
+HXD int gstride(int n) { return (n * n * n + 3) / 4 * 4; }
 struct GeomArgs {
   const double* vert;   // [nv][3]
   const int* elem;      // [ne][8]
   int ne, n;            // elements, nodes per direction
   double xi[MAXN1], w[MAXN1];
   double c2;
-  double* G64;          // [ne][6][n^3]
+  double* G64;          // [ne][6][gstride(n)]
   float* G32;
   double* Mloc;         // [ne][n^3] (volume slots of this domain)
   int* bad;             // count of nodes with |J| <= 0
@@ -177,15 +180,19 @@ struct MatchArgs {
   double* pdat;         // [nff q^2][PDAT]: refp(3) refm(3) a+(3) a-(3) W gamma
 };
 
+// Step kernels keep every field batch-innermost: value (node j, member b) at
+// j * Bp + b, Bp the batch padded to a multiple of the vector width (8 FP32 or
+// 4 FP64 members = 32 bytes) when the batch is at least that wide.
+//
 // Step: element stiffness of one domain into its volume slots.
 template <typename T>
 struct HexVolArgs {
   const T* p; T* S;
-  long long p_bs, s_bs;      // batch strides
+  int Bp;                    // padded batch (row length of p and S)
   const int* conn;           // [ne][n^3] node ids
-  const T* G;                // [ne][6][n^3]
+  const T* G;                // [ne][6][gstride(n)]
   long long slot_base;       // first volume slot of this domain
-  int ne, batch;
+  int ne;
   T D[MAXN1][MAXN1];         // D[i][j] = l_j'(xi_i)
 };
 
@@ -194,7 +201,7 @@ struct HexVolArgs {
 template <typename T>
 struct HexIfaceArgs {
   const T* p; T* S;
-  long long p_bs, s_bs;
+  int Bp;
   const int* conn_p; const int* conn_m;
   const int* g_fe; const int* g_ce;   // [ng] element ids
   const int* g_pt;                    // [ng+1] CSR into pt_idx
@@ -204,7 +211,7 @@ struct HexIfaceArgs {
   double xip[MAXN1], xim[MAXN1];
   int np, nm;                         // GLL nodes per direction, fine / coarse
   double c2p, c2m;
-  int ng, batch, max_pts;
+  int ng, max_pts;
 };
 
 // Step: residual assembly (sum of a node's slots in ascending slot order)
@@ -212,28 +219,27 @@ struct HexIfaceArgs {
 template <typename T>
 struct HexUpdateArgs {
   T* p; T* v; const T* S;
-  long long p_bs, s_bs;
+  int Bp;
   const int* node_ptr; const int* node_slot;
   const T* Minv;
   long long ndof;
   T cv, cp;
-  int batch;
 };
 
 // Step tail: PMUT forcing slots kappa sum_m q''_km B_jm of every footprint
 // entry, receiver samples of p^{n+1}, then the step counter advances.
 template <typename T>
 struct HexTailArgs {
-  int nnz, M, K;
+  int nnz, M, K, B, Bp;
   const int* ent_k; const double* Bm; const double* qdd;
   double kappa;
-  T* S; long long s_bs; long long fslot;
+  T* S; long long fslot;
   int R, rstride;
-  const double* rw; const long long* roff; const int* rnn;
-  const T* p; long long p_bs;
+  const double* rw; const long long* roff; const int* rnn;   // roff: node ids
+  const T* p;
   double* traces; long long tbs, trs;
   int n; int* step; unsigned* done;
-  int batch, fblocks;
+  int fblocks;
 };
 
 cudaError_t launch_geom(const GeomArgs& a, cudaStream_t s);

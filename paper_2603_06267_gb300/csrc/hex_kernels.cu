@@ -10,7 +10,47 @@
 // Algorithm 1, and the tail (PMUT forcing slots, receivers, step counter).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "hex_geom.h"
+
+namespace {
+
+// cp.async (sm_80+): asynchronous global -> shared copies, completed by
+// commit/wait groups; they keep no registers busy while in flight.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int K>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
+
+// copy of `bytes` (4, 8, 16 or 32; both addresses aligned to it)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  if constexpr (BYTES == 32) {
+    cp_async16(smem, gmem);
+    cp_async16(static_cast<char*>(smem) + 16, static_cast<const char*>(gmem) + 16);
+  } else if constexpr (BYTES == 16) {
+    cp_async16(smem, gmem);
+  } else if constexpr (BYTES == 8) {
+    cp_async8(smem, gmem);
+  } else {
+    static_assert(BYTES == 4, "cp.async size");
+    cp_async4(smem, gmem);
+  }
+}
+
+}  // namespace
 
 namespace hex {
 
@@ -41,7 +81,7 @@ __global__ void geom_kernel(const __grid_constant__ GeomArgs a) {
   for (int k = 0; k < 6; ++k) {
     const int d = comp[k][0], f = comp[k][1];
     const double g = s * (Ji[d][0] * Ji[f][0] + Ji[d][1] * Ji[f][1] + Ji[d][2] * Ji[f][2]);
-    const long long o = (6LL * e + k) * nl + i;
+    const long long o = (6LL * e + k) * gstride(n) + i;
     a.G64[o] = g;
     a.G32[o] = (float)g;
   }
@@ -200,57 +240,296 @@ __global__ void ipoint_kernel(const __grid_constant__ MatchArgs a) {
 // ---------------------------------------------------------------------------
 // Step kernels
 // ---------------------------------------------------------------------------
-// Element stiffness of eq. (Wf_2) on one element per CTA, for every batch
-// member: grad^ u by the GLL derivative matrix (difference form
-// sum_m D_am (u_m - u_a), exact for constants in any precision), the
-// geometric factors, then the transposed derivative; the element-local
-// residual goes to the element's slots.
-template <typename T, int N>
-__global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
-    hex_vol_kernel(const __grid_constant__ HexVolArgs<T> A) {
-  constexpr int n = N + 1, nl = n * n * n;
-  __shared__ T u[nl];
-  __shared__ T F[3][nl];
-  __shared__ T D[n][n];
-  const int e = blockIdx.x;
-  const int i = threadIdx.x;
-  if (i < n * n) D[i / n][i % n] = A.D[i / n][i % n];
-  const bool act = i < nl;
-  const int ia = i % n, ib = (i / n) % n, ic = i / (n * n);
-  int node = 0;
-  T g[6];
-  if (act) {
-    node = A.conn[(long long)e * nl + i];
+// BB consecutive batch members of one node, moved as one vector.
+template <typename T, int BB>
+struct alignas(sizeof(T) * BB) Pack {
+  T v[BB];
+};
+
+// Explicitly rounded arithmetic: the compiler may not contract or reorder
+// these, so a batch member's result is the same for every vector width BB.
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+
+// Member-wise operations on a Pack.  FP32 packs of an even width use the
+// packed f32x2 instructions (two members per instruction); each lane rounds
+// exactly like the scalar form, so results do not depend on the width.
+template <typename T, int BB>
+constexpr bool packed2() { return std::is_same<T, float>::value && BB % 2 == 0; }
+
+__device__ __forceinline__ float2 sub2_(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// acc += d * (x - y)
+template <typename T, int BB>
+__device__ __forceinline__ void vfma_diff(Pack<T, BB>& acc, T d, const Pack<T, BB>& x, const Pack<T, BB>& y) {
+  if constexpr (packed2<T, BB>()) {
+    const float2 d2 = make_float2(d, d);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g[k] = A.G[(6LL * e + k) * nl + i];
+    for (int b = 0; b < BB; b += 2) {
+      float2& a = *reinterpret_cast<float2*>(&acc.v[b]);
+      a = __ffma2_rn(d2, sub2_(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b])), a);
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BB; ++b) acc.v[b] = fma_(d, sub_(x.v[b], y.v[b]), acc.v[b]);
   }
-  const long long slot = A.slot_base + (long long)e * nl + i;
-  for (int b = 0; b < A.batch; ++b) {
-    if (act) u[i] = A.p[b * A.p_bs + node];
+}
+
+// acc += d * x
+template <typename T, int BB>
+__device__ __forceinline__ void vfma(Pack<T, BB>& acc, T d, const Pack<T, BB>& x) {
+  if constexpr (packed2<T, BB>()) {
+    const float2 d2 = make_float2(d, d);
+#pragma unroll
+    for (int b = 0; b < BB; b += 2) {
+      float2& a = *reinterpret_cast<float2*>(&acc.v[b]);
+      a = __ffma2_rn(d2, *reinterpret_cast<const float2*>(&x.v[b]), a);
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BB; ++b) acc.v[b] = fma_(d, x.v[b], acc.v[b]);
+  }
+}
+
+// d * x
+template <typename T, int BB>
+__device__ __forceinline__ Pack<T, BB> vmul(T d, const Pack<T, BB>& x) {
+  Pack<T, BB> o;
+  if constexpr (packed2<T, BB>()) {
+    const float2 d2 = make_float2(d, d);
+#pragma unroll
+    for (int b = 0; b < BB; b += 2)
+      *reinterpret_cast<float2*>(&o.v[b]) = __fmul2_rn(d2, *reinterpret_cast<const float2*>(&x.v[b]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < BB; ++b) o.v[b] = mul_(d, x.v[b]);
+  }
+  return o;
+}
+
+// x + y
+template <typename T, int BB>
+__device__ __forceinline__ Pack<T, BB> vadd(const Pack<T, BB>& x, const Pack<T, BB>& y) {
+  Pack<T, BB> o;
+  if constexpr (packed2<T, BB>()) {
+#pragma unroll
+    for (int b = 0; b < BB; b += 2)
+      *reinterpret_cast<float2*>(&o.v[b]) =
+          __fadd2_rn(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < BB; ++b) o.v[b] = add_(x.v[b], y.v[b]);
+  }
+  return o;
+}
+
+template <typename T, int BB>
+__device__ __forceinline__ Pack<T, BB> vzero() {
+  Pack<T, BB> o;
+#pragma unroll
+  for (int b = 0; b < BB; ++b) o.v[b] = T(0);
+  return o;
+}
+
+// Element stiffness of eq. (Wf_2), sum-factorised along element lines.
+// A CTA takes E elements and BB batch members at a time; each element has
+// n^2 threads, and thread q of an element owns the x-line (b, c), the y-line
+// (a, c) and the z-line (a, b) with (., .) = (q mod n, q div n):
+//   A: x- and y-lines: grad^_x u, grad^_y u of their line (difference form
+//      sum_m D_am (u_m - u_a), exact for constants in any precision) -> smem
+//   B: z-line: grad^_z u in registers, then F = G grad^ u at its nodes with
+//      the geometric factors G; F_x, F_y -> smem, F_z stays in registers
+//   C: x-lines: D^T F_x -> R_x; y-lines: D^T F_y -> R_y (in place)
+//   D: z-line: r = R_x + R_y + D^T F_z -> the element's residual slots.
+// The derivative matrix is indexed by compile-time indices only (uniform
+// across the warp), and the per-member arithmetic is the same for every BB.
+template <int N>
+struct VolTeam {
+  static constexpr int n = N + 1, nl = n * n * n, line = n * n;
+  static constexpr int E = line >= 128 ? 1 : 128 / line;          // elements per CTA
+  static constexpr int threads = (E * line + 31) / 32 * 32;
+};
+
+// shared memory: u double buffer (the current one then holds R_x), the
+// x/y gradients (then F_x, F_y, R_y), and the CTA's geometric factors
+template <typename T, int BB, int N>
+constexpr size_t vol_smem() {
+  return 4 * sizeof(T) * BB * (size_t)VolTeam<N>::nl * VolTeam<N>::E +
+         sizeof(T) * 6 * (size_t)((VolTeam<N>::nl + 3) / 4 * 4) * VolTeam<N>::E;
+}
+
+// A shared array of packs stored as planes of 16-byte entries (members
+// [0, H), [H, 2H), ...): a warp's 16-byte accesses to consecutive entries are
+// then contiguous and free of bank conflicts.
+template <typename T, int BB>
+struct SPlanes {
+  static constexpr int H = (int)(sizeof(T) * BB > 16 ? 16 / sizeof(T) : BB);   // members per entry
+  static constexpr int NPL = BB / H;                                           // planes
+  using P = Pack<T, BB>;
+  using Half = Pack<T, H>;
+  T* base;
+  int count;
+  __device__ __forceinline__ T* ptr(int pl, int k) const { return base + ((long long)pl * count + k) * H; }
+  __device__ __forceinline__ P ld(int k) const {
+    P o;
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl) *reinterpret_cast<Half*>(&o.v[pl * H]) = *reinterpret_cast<const Half*>(ptr(pl, k));
+    return o;
+  }
+  __device__ __forceinline__ void st(int k, const P& x) const {
+#pragma unroll
+    for (int pl = 0; pl < NPL; ++pl) *reinterpret_cast<Half*>(ptr(pl, k)) = *reinterpret_cast<const Half*>(&x.v[pl * H]);
+  }
+};
+
+template <typename T, int N, int BB>
+__global__ void __launch_bounds__(VolTeam<N>::threads) hex_vol_kernel(const __grid_constant__ HexVolArgs<T> A) {
+  using TM = VolTeam<N>;
+  constexpr int n = TM::n, nl = TM::nl, E = TM::E, gs = (nl + 3) / 4 * 4;
+  constexpr int GPER = (E * nl + TM::threads - 1) / TM::threads;   // gather entries per thread
+  using P = Pack<T, BB>;
+  using SP = SPlanes<T, BB>;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const SP Ub[2] = {{sm, E * nl}, {sm + (long long)E * nl * BB, E * nl}};   // u, then R_x
+  const SP G0 = {sm + 2LL * E * nl * BB, E * nl};   // grad^_x u, then F_x
+  const SP G1 = {sm + 3LL * E * nl * BB, E * nl};   // grad^_y u, then F_y, then R_y
+  T* Gs = sm + 4LL * E * nl * BB;                   // [E][6][gs] geometric factors
+  const int t = threadIdx.x;
+  const int el = t / TM::line, q = t - el * TM::line;
+  const int e0 = blockIdx.x * E;
+  const int e = e0 + el;
+  const int ne_cta = min(E, A.ne - e0);
+  const bool act = el < E && e < A.ne;
+  const int qa = q % n, qb = q / n;          // the two line coordinates
+  const int o = el * nl;                     // this element's entries in the shared arrays
+  const T* gsm = Gs + el * 6 * gs;
+  const int nch = A.Bp / BB;
+  // node ids of this thread's gather entries, reused by every chunk
+  int nd[GPER];
+#pragma unroll
+  for (int g = 0; g < GPER; ++g) {
+    const int i = t + g * TM::threads;
+    nd[g] = i < ne_cta * nl ? A.conn[(long long)e0 * nl + i] : 0;
+  }
+  auto gather = [&](int ch, const SP& dst) {
+#pragma unroll
+    for (int g = 0; g < GPER; ++g) {
+      const int i = t + g * TM::threads;
+      if (i < ne_cta * nl) {
+        const T* src = A.p + (long long)nd[g] * A.Bp + ch * BB;
+#pragma unroll
+        for (int pl = 0; pl < SP::NPL; ++pl)
+          cp_async<(int)(SP::H * sizeof(T))>(dst.ptr(pl, i), src + pl * SP::H);
+      }
+    }
+  };
+  {
+    constexpr int per16 = 16 / (int)sizeof(T);
+    const T* gsrc = A.G + 6LL * e0 * gs;
+    for (int i = t * per16; i < ne_cta * 6 * gs; i += blockDim.x * per16) cp_async16(Gs + i, gsrc + i);
+  }
+  gather(0, Ub[0]);
+  cp_commit();
+  for (int ch = 0; ch < nch; ++ch) {
+    const SP& U = Ub[ch & 1];
+    if (ch + 1 < nch) gather(ch + 1, Ub[(ch + 1) & 1]);
+    cp_commit();
+    cp_wait<1>();
     __syncthreads();
     if (act) {
-      const T ui = u[i];
-      T g0 = T(0), g1 = T(0), g2 = T(0);
+      // A: x-line (b, c) = (qa, qb) and y-line (a, c) = (qa, qb)
+      P lx[n], ly[n];
 #pragma unroll
       for (int m = 0; m < n; ++m) {
-        g0 += D[ia][m] * (u[ic * n * n + ib * n + m] - ui);
-        g1 += D[ib][m] * (u[ic * n * n + m * n + ia] - ui);
-        g2 += D[ic][m] * (u[m * n * n + ib * n + ia] - ui);
+        lx[m] = U.ld(o + m + n * qa + n * n * qb);
+        ly[m] = U.ld(o + qa + n * m + n * n * qb);
       }
-      F[0][i] = g[0] * g0 + g[3] * g1 + g[4] * g2;
-      F[1][i] = g[3] * g0 + g[1] * g1 + g[5] * g2;
-      F[2][i] = g[4] * g0 + g[5] * g1 + g[2] * g2;
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        P ox = vzero<T, BB>(), oy = vzero<T, BB>();
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          if (m == a) continue;
+          const T d = A.D[a][m];
+          vfma_diff(ox, d, lx[m], lx[a]);
+          vfma_diff(oy, d, ly[m], ly[a]);
+        }
+        G0.st(o + a + n * qa + n * n * qb, ox);
+        G1.st(o + qa + n * a + n * n * qb, oy);
+      }
+    }
+    __syncthreads();
+    P fz[n];
+    if (act) {
+      // B: z-line (a, b) = (qa, qb): grad^_z u, then F = G grad^ u at its nodes
+      P lz[n];
+#pragma unroll
+      for (int m = 0; m < n; ++m) lz[m] = U.ld(o + qa + n * qb + n * n * m);
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        P gz = vzero<T, BB>();
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          if (m == c) continue;
+          vfma_diff(gz, T(A.D[c][m]), lz[m], lz[c]);
+        }
+        const int k = qa + n * qb + n * n * c;
+        const T* gp = gsm + k;
+        const T G00 = gp[0], G11 = gp[gs], G22 = gp[2 * gs], G01 = gp[3 * gs], G02 = gp[4 * gs], G12 = gp[5 * gs];
+        const P gx = G0.ld(o + k), gy = G1.ld(o + k);
+        P fx = vmul(G00, gx), fy = vmul(G01, gx);
+        fz[c] = vmul(G02, gx);
+        vfma(fx, G01, gy);
+        vfma(fy, G11, gy);
+        vfma(fz[c], G12, gy);
+        vfma(fx, G02, gz);
+        vfma(fy, G12, gz);
+        vfma(fz[c], G22, gz);
+        G0.st(o + k, fx);
+        G1.st(o + k, fy);
+      }
     }
     __syncthreads();
     if (act) {
-      T r = T(0);
+      // C: x-line: R_x = D^T F_x -> U; y-line: R_y = D^T F_y -> G1 (in place)
+      P lx[n], ly[n];
 #pragma unroll
       for (int m = 0; m < n; ++m) {
-        r += D[m][ia] * F[0][ic * n * n + ib * n + m];
-        r += D[m][ib] * F[1][ic * n * n + m * n + ia];
-        r += D[m][ic] * F[2][m * n * n + ib * n + ia];
+        lx[m] = G0.ld(o + m + n * qa + n * n * qb);
+        ly[m] = G1.ld(o + qa + n * m + n * n * qb);
       }
-      A.S[b * A.s_bs + slot] = r;
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        P ox = vzero<T, BB>(), oy = vzero<T, BB>();
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          const T d = A.D[m][a];
+          vfma(ox, d, lx[m]);
+          vfma(oy, d, ly[m]);
+        }
+        U.st(o + a + n * qa + n * n * qb, ox);
+        G1.st(o + qa + n * a + n * n * qb, oy);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      // D: z-line: r = R_x + R_y + D^T F_z
+      P* sout = reinterpret_cast<P*>(A.S + (A.slot_base + (long long)e * nl) * A.Bp) + ch;
+#pragma unroll
+      for (int c = 0; c < n; ++c) {
+        const int k = qa + n * qb + n * n * c;
+        P rz = vzero<T, BB>();
+#pragma unroll
+        for (int m = 0; m < n; ++m) vfma(rz, T(A.D[m][c]), fz[m]);
+        sout[(long long)k * (A.Bp / BB)] = vadd(vadd(U.ld(o + k), G1.ld(o + k)), rz);
+      }
     }
     __syncthreads();
   }
@@ -261,21 +540,22 @@ __global__ void __launch_bounds__(((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32)
 // and A = 1/2 (c+^2 dp+/dn+ + c-^2 dp-/dn+):
 //   r_i(K+) += W (gamma J - A) psi_i - 1/2 W J c+^2 d psi_i / d n+
 //   r_i(K-) -= W (gamma J - A) psi_i + 1/2 W J c-^2 d psi_i / d n+
-template <typename T>
+template <typename T, int BB>
 __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ HexIfaceArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using P = Pack<T, BB>;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
   const int g = blockIdx.x;
   const int np = A.np, nm = A.nm;
   const int nlp = np * np * np, nlm = nm * nm * nm;
   const int p0 = A.g_pt[g], npts = A.g_pt[g + 1] - p0;
-  const int P = A.max_pts;
-  T* up = reinterpret_cast<T*>(smem_raw);
-  T* um = up + nlp;
-  T* tp = um + nlm;                 // [P][3][2][np]: l, l' per axis, fine side
-  T* tm = tp + (long long)P * 6 * np;   // [P][3][2][nm]
-  T* av = tm + (long long)P * 6 * nm;   // [P][8]: a+(3) a-(3) W gamma
-  T* sv = av + 8 * P;               // [P]
-  T* sd = sv + P;                   // [P]
+  const int Q = A.max_pts;
+  P* up = reinterpret_cast<P*>(smem_raw);
+  P* um = up + nlp;
+  P* sv = um + nlm;                 // [Q]
+  P* sd = sv + Q;                   // [Q]
+  T* tp = reinterpret_cast<T*>(sd + Q);   // [Q][3][2][np]: l, l' per axis, fine side
+  T* tm = tp + (long long)Q * 6 * np;     // [Q][3][2][nm]
+  T* av = tm + (long long)Q * 6 * nm;     // [Q][8]: a+(3) a-(3) W gamma
   const int tid = threadIdx.x;
   for (int j = tid; j < npts; j += blockDim.x) {
     const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
@@ -297,57 +577,86 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
   const int fe = A.g_fe[g], ce = A.g_ce[g];
   const long long slot = A.g_slot[g];
   const T c2p = T(A.c2p), c2m = T(A.c2m);
-  for (int b = 0; b < A.batch; ++b) {
-    for (int i = tid; i < nlp; i += blockDim.x) up[i] = A.p[b * A.p_bs + A.conn_p[(long long)fe * nlp + i]];
-    for (int i = tid; i < nlm; i += blockDim.x) um[i] = A.p[b * A.p_bs + A.conn_m[(long long)ce * nlm + i]];
+  const int nch = A.Bp / BB;
+  for (int ch = 0; ch < nch; ++ch) {
+    for (int i = tid; i < nlp; i += blockDim.x)
+      up[i] = reinterpret_cast<const P*>(A.p + (long long)A.conn_p[(long long)fe * nlp + i] * A.Bp)[ch];
+    for (int i = tid; i < nlm; i += blockDim.x)
+      um[i] = reinterpret_cast<const P*>(A.p + (long long)A.conn_m[(long long)ce * nlm + i] * A.Bp)[ch];
     __syncthreads();
     for (int j = tid; j < npts; j += blockDim.x) {
-      T vp = 0, dp0 = 0, dp1 = 0, dp2 = 0;
+      T vp[BB], dp0[BB], dp1[BB], dp2[BB], vm[BB], dm0[BB], dm1[BB], dm2[BB];
+#pragma unroll
+      for (int b = 0; b < BB; ++b) vp[b] = dp0[b] = dp1[b] = dp2[b] = vm[b] = dm0[b] = dm1[b] = dm2[b] = T(0);
       {
         const T* lx = tp + (j * 3 + 0) * 2 * np;
         const T* ly = tp + (j * 3 + 1) * 2 * np;
         const T* lz = tp + (j * 3 + 2) * 2 * np;
         for (int c = 0; c < np; ++c)
           for (int bb = 0; bb < np; ++bb) {
-            T s0 = 0, s1 = 0;
+            T s0[BB], s1[BB];
+#pragma unroll
+            for (int b = 0; b < BB; ++b) s0[b] = s1[b] = T(0);
             for (int a = 0; a < np; ++a) {
-              const T uv = up[(c * np + bb) * np + a];
-              s0 += lx[a] * uv;
-              s1 += lx[np + a] * uv;
+              const P uv = up[(c * np + bb) * np + a];
+              const T la = lx[a], da = lx[np + a];
+#pragma unroll
+              for (int b = 0; b < BB; ++b) {
+                s0[b] = fma_(la, uv.v[b], s0[b]);
+                s1[b] = fma_(da, uv.v[b], s1[b]);
+              }
             }
-            const T yz = ly[bb] * lz[c];
-            vp += yz * s0;
-            dp0 += yz * s1;
-            dp1 += ly[np + bb] * lz[c] * s0;
-            dp2 += ly[bb] * lz[np + c] * s0;
+            const T yz = mul_(ly[bb], lz[c]), dyz = mul_(ly[np + bb], lz[c]), ydz = mul_(ly[bb], lz[np + c]);
+#pragma unroll
+            for (int b = 0; b < BB; ++b) {
+              vp[b] = fma_(yz, s0[b], vp[b]);
+              dp0[b] = fma_(yz, s1[b], dp0[b]);
+              dp1[b] = fma_(dyz, s0[b], dp1[b]);
+              dp2[b] = fma_(ydz, s0[b], dp2[b]);
+            }
           }
       }
-      T vm = 0, dm0 = 0, dm1 = 0, dm2 = 0;
       {
         const T* lx = tm + (j * 3 + 0) * 2 * nm;
         const T* ly = tm + (j * 3 + 1) * 2 * nm;
         const T* lz = tm + (j * 3 + 2) * 2 * nm;
         for (int c = 0; c < nm; ++c)
           for (int bb = 0; bb < nm; ++bb) {
-            T s0 = 0, s1 = 0;
+            T s0[BB], s1[BB];
+#pragma unroll
+            for (int b = 0; b < BB; ++b) s0[b] = s1[b] = T(0);
             for (int a = 0; a < nm; ++a) {
-              const T uv = um[(c * nm + bb) * nm + a];
-              s0 += lx[a] * uv;
-              s1 += lx[nm + a] * uv;
+              const P uv = um[(c * nm + bb) * nm + a];
+              const T la = lx[a], da = lx[nm + a];
+#pragma unroll
+              for (int b = 0; b < BB; ++b) {
+                s0[b] = fma_(la, uv.v[b], s0[b]);
+                s1[b] = fma_(da, uv.v[b], s1[b]);
+              }
             }
-            const T yz = ly[bb] * lz[c];
-            vm += yz * s0;
-            dm0 += yz * s1;
-            dm1 += ly[nm + bb] * lz[c] * s0;
-            dm2 += ly[bb] * lz[nm + c] * s0;
+            const T yz = mul_(ly[bb], lz[c]), dyz = mul_(ly[nm + bb], lz[c]), ydz = mul_(ly[bb], lz[nm + c]);
+#pragma unroll
+            for (int b = 0; b < BB; ++b) {
+              vm[b] = fma_(yz, s0[b], vm[b]);
+              dm0[b] = fma_(yz, s1[b], dm0[b]);
+              dm1[b] = fma_(dyz, s0[b], dm1[b]);
+              dm2[b] = fma_(ydz, s0[b], dm2[b]);
+            }
           }
       }
       const T* a8 = av + 8 * j;
-      const T jump = vp - vm;
-      const T avg = T(0.5) * (c2p * (dp0 * a8[0] + dp1 * a8[1] + dp2 * a8[2]) +
-                              c2m * (dm0 * a8[3] + dm1 * a8[4] + dm2 * a8[5]));
-      sv[j] = a8[6] * (a8[7] * jump - avg);
-      sd[j] = T(-0.5) * a8[6] * jump;
+      P s, dd;
+#pragma unroll
+      for (int b = 0; b < BB; ++b) {
+        const T jump = sub_(vp[b], vm[b]);
+        const T dnp = fma_(dp2[b], a8[2], fma_(dp1[b], a8[1], mul_(dp0[b], a8[0])));
+        const T dnm = fma_(dm2[b], a8[5], fma_(dm1[b], a8[4], mul_(dm0[b], a8[3])));
+        const T avg = mul_(T(0.5), add_(mul_(c2p, dnp), mul_(c2m, dnm)));
+        s.v[b] = mul_(a8[6], sub_(mul_(a8[7], jump), avg));
+        dd.v[b] = mul_(mul_(T(-0.5), a8[6]), jump);
+      }
+      sv[j] = s;
+      sd[j] = dd;
     }
     __syncthreads();
     for (int i = tid; i < nlp + nlm; i += blockDim.x) {
@@ -358,44 +667,54 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
       const T* tb = plus ? tp : tm;
       const T c2 = plus ? c2p : c2m;
       const T sgn = plus ? T(1) : T(-1);
-      T r = 0;
+      T r[BB];
+#pragma unroll
+      for (int b = 0; b < BB; ++b) r[b] = T(0);
       for (int j = 0; j < npts; ++j) {
         const T* lx = tb + (j * 3 + 0) * 2 * n;
         const T* ly = tb + (j * 3 + 1) * 2 * n;
         const T* lz = tb + (j * 3 + 2) * 2 * n;
         const T* a8 = av + 8 * j + (plus ? 0 : 3);
-        const T psi = lx[ia] * ly[ib] * lz[ic];
-        const T dn = a8[0] * lx[n + ia] * ly[ib] * lz[ic] + a8[1] * lx[ia] * ly[n + ib] * lz[ic] +
-                     a8[2] * lx[ia] * ly[ib] * lz[n + ic];
-        r += sgn * sv[j] * psi + sd[j] * c2 * dn;
+        const T psi = mul_(sgn, mul_(mul_(lx[ia], ly[ib]), lz[ic]));
+        const T t0 = mul_(mul_(lx[n + ia], ly[ib]), lz[ic]);
+        const T t1 = mul_(mul_(lx[ia], ly[n + ib]), lz[ic]);
+        const T t2 = mul_(mul_(lx[ia], ly[ib]), lz[n + ic]);
+        const T dn = mul_(c2, fma_(a8[2], t2, fma_(a8[1], t1, mul_(a8[0], t0))));
+        const P s = sv[j], dd = sd[j];
+#pragma unroll
+        for (int b = 0; b < BB; ++b) r[b] = fma_(dd.v[b], dn, fma_(s.v[b], psi, r[b]));
       }
-      A.S[b * A.s_bs + slot + i] = r;
+      P o;
+#pragma unroll
+      for (int b = 0; b < BB; ++b) o.v[b] = r[b];
+      reinterpret_cast<P*>(A.S + (slot + i) * A.Bp)[ch] = o;
     }
     __syncthreads();
   }
 }
 
-// Residual assembly and leapfrog update, one thread per node and up to
-// UB batch members: r = sum of the node's slots (ascending slot order, so
-// the sum is the same in every run), v += cv M^-1 r, p += cp v.
-constexpr int UB = 8;
-
-template <typename T>
+// Residual assembly and leapfrog update, one thread per (node, BB members):
+// r = sum of the node's slots (ascending slot order, so the sum is the same
+// in every run and for every batch width), v += cv M^-1 r, p += cp v.
+template <typename T, int BB>
 __global__ void __launch_bounds__(256) hex_update_kernel(const __grid_constant__ HexUpdateArgs<T> A) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  using P = Pack<T, BB>;
+  const int nch = A.Bp / BB;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long j = t / nch;
   if (j >= A.ndof) return;
+  const int ch = (int)(t - j * nch);
   const int k0 = A.node_ptr[j], k1 = A.node_ptr[j + 1];
   const T mi = A.Minv[j];
-  const int b0 = blockIdx.y * UB, b1 = min(A.batch, b0 + UB);
-  for (int b = b0; b < b1; ++b) {
-    const T* S = A.S + b * A.s_bs;
-    T r = 0;
-    for (int k = k0; k < k1; ++k) r += S[A.node_slot[k]];
-    const long long o = b * A.p_bs + j;
-    const T v = A.v[o] + A.cv * mi * r;
-    A.v[o] = v;
-    A.p[o] = A.p[o] + A.cp * v;
-  }
+  P r = vzero<T, BB>();
+  for (int k = k0; k < k1; ++k) r = vadd(r, reinterpret_cast<const P*>(A.S + (long long)A.node_slot[k] * A.Bp)[ch]);
+  P* pp = reinterpret_cast<P*>(A.p + j * A.Bp) + ch;
+  P* vp = reinterpret_cast<P*>(A.v + j * A.Bp) + ch;
+  P pv = *pp, vv = *vp;
+  vfma(vv, mul_(A.cv, mi), r);
+  vfma(pv, A.cp, vv);
+  *vp = vv;
+  *pp = pv;
 }
 
 __device__ __forceinline__ double hex_warp_sum(double v) {
@@ -409,25 +728,24 @@ __global__ void __launch_bounds__(256) hex_tail_kernel(const __grid_constant__ H
   if ((int)blockIdx.x < A.fblocks) {
     // forcing slot of footprint entry e: kappa sum_m q''_km B_em (= -f, eq. f_i)
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < (long long)A.nnz * A.batch) {
-      const int b = (int)(t / A.nnz), e = (int)(t - (long long)b * A.nnz);
+    if (t < (long long)A.nnz * A.B) {
+      const int e = (int)(t / A.B), b = (int)(t - (long long)e * A.B);
       const int k = A.ent_k[e];
       const double* q = A.qdd + ((long long)b * A.K + k) * A.M;
       const double* Bv = A.Bm + (long long)e * A.M;
       double s = 0.0;
       for (int m = 0; m < A.M; ++m) s += q[m] * Bv[m];
-      A.S[b * A.s_bs + A.fslot + e] = T(A.kappa * s);
+      A.S[(A.fslot + e) * A.Bp + b] = T(A.kappa * s);
     }
   } else {
     const int warp = (int)(((blockIdx.x - A.fblocks) * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (warp < A.batch * A.R) {
+    if (warp < A.B * A.R) {
       const int b = warp / A.R, r = warp - b * A.R;
-      const T* p = A.p + b * A.p_bs;
       const double* w = A.rw + (long long)r * A.rstride;
       const long long* off = A.roff + (long long)r * A.rstride;
       double s = 0.0;
-      for (int t = lane; t < A.rnn[r]; t += 32) s += w[t] * (double)p[off[t]];
+      for (int t = lane; t < A.rnn[r]; t += 32) s += w[t] * (double)A.p[off[t] * A.Bp + b];
       s = hex_warp_sum(s);
       if (lane == 0) A.traces[b * A.tbs + r * A.trs + n] = s;
     }
@@ -484,59 +802,87 @@ cudaError_t launch_ipoints(const MatchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <typename T, int N>
+// vector width: 32 bytes of batch members when the padded batch allows it
+template <typename T>
+constexpr int vec_width() { return 32 / (int)sizeof(T); }
+
+template <typename T, int N, int BB>
 cudaError_t vol_n(const HexVolArgs<T>& a, cudaStream_t s) {
-  constexpr int threads = ((N + 1) * (N + 1) * (N + 1) + 31) / 32 * 32;
-  hex_vol_kernel<T, N><<<a.ne, threads, 0, s>>>(a);
+  using TM = VolTeam<N>;
+  constexpr size_t sm = vol_smem<T, BB, N>();
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(hex_vol_kernel<T, N, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  hex_vol_kernel<T, N, BB><<<(a.ne + TM::E - 1) / TM::E, TM::threads, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s) {
-  if (a.ne == 0 || a.batch == 0) return cudaSuccess;
+template <typename T, int BB>
+cudaError_t vol_bb(const HexVolArgs<T>& a, int n, cudaStream_t s) {
   switch (n - 1) {
-    case 1: return vol_n<T, 1>(a, s);
-    case 2: return vol_n<T, 2>(a, s);
-    case 3: return vol_n<T, 3>(a, s);
-    case 4: return vol_n<T, 4>(a, s);
-    case 5: return vol_n<T, 5>(a, s);
-    case 6: return vol_n<T, 6>(a, s);
-    case 7: return vol_n<T, 7>(a, s);
-    case 8: return vol_n<T, 8>(a, s);
+    case 1: return vol_n<T, 1, BB>(a, s);
+    case 2: return vol_n<T, 2, BB>(a, s);
+    case 3: return vol_n<T, 3, BB>(a, s);
+    case 4: return vol_n<T, 4, BB>(a, s);
+    case 5: return vol_n<T, 5, BB>(a, s);
+    case 6: return vol_n<T, 6, BB>(a, s);
+    case 7: return vol_n<T, 7, BB>(a, s);
+    case 8: return vol_n<T, 8, BB>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
+cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s) {
+  if (a.ne == 0 || a.Bp == 0) return cudaSuccess;
+  constexpr int V = vec_width<T>();
+  return (a.Bp % V == 0) ? vol_bb<T, V>(a, n, s) : vol_bb<T, 1>(a, n, s);
+}
+
+template <typename T, int BB>
 size_t iface_smem(const HexIfaceArgs<T>& a) {
-  const long long P = a.max_pts;
+  const long long Q = a.max_pts;
   const long long nlp = (long long)a.np * a.np * a.np, nlm = (long long)a.nm * a.nm * a.nm;
-  return sizeof(T) * (size_t)(nlp + nlm + P * 6 * a.np + P * 6 * a.nm + 8 * P + 2 * P);
+  return sizeof(T) * BB * (size_t)(nlp + nlm + 2 * Q) + sizeof(T) * (size_t)(Q * 6 * a.np + Q * 6 * a.nm + 8 * Q);
+}
+
+template <typename T, int BB>
+cudaError_t iface_bb(const HexIfaceArgs<T>& a, cudaStream_t s) {
+  const size_t sm = iface_smem<T, BB>(a);
+  if (sm > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(hex_iface_kernel<T, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  hex_iface_kernel<T, BB><<<a.ng, 128, sm, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s) {
-  if (a.ng == 0 || a.batch == 0) return cudaSuccess;
-  const size_t sm = iface_smem(a);
-  if (sm > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(hex_iface_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  hex_iface_kernel<T><<<a.ng, 128, sm, s>>>(a);
+  if (a.ng == 0 || a.Bp == 0) return cudaSuccess;
+  constexpr int V = vec_width<T>();
+  return (a.Bp % V == 0) ? iface_bb<T, V>(a, s) : iface_bb<T, 1>(a, s);
+}
+
+template <typename T, int BB>
+cudaError_t update_bb(const HexUpdateArgs<T>& a, cudaStream_t s) {
+  const long long n = a.ndof * (a.Bp / BB);
+  hex_update_kernel<T, BB><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_hex_update(const HexUpdateArgs<T>& a, cudaStream_t s) {
-  if (a.ndof == 0 || a.batch == 0) return cudaSuccess;
-  const dim3 grid((unsigned)((a.ndof + 255) / 256), (a.batch + UB - 1) / UB);
-  hex_update_kernel<T><<<grid, 256, 0, s>>>(a);
-  return cudaGetLastError();
+  if (a.ndof == 0 || a.Bp == 0) return cudaSuccess;
+  constexpr int V = vec_width<T>();
+  return (a.Bp % V == 0) ? update_bb<T, V>(a, s) : update_bb<T, 1>(a, s);
 }
 
 template <typename T>
 cudaError_t launch_hex_tail(const HexTailArgs<T>& a, cudaStream_t s) {
-  const long long rth = (long long)a.batch * a.R * 32;
+  const long long rth = (long long)a.B * a.R * 32;
   const long long blocks = a.fblocks + (rth + 255) / 256;
   hex_tail_kernel<T><<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, s>>>(a);
   return cudaGetLastError();

@@ -119,16 +119,18 @@ def test_one_domain_initial_state_parity(lib, prec, tol):
 
 
 def test_batch_members_are_independent(lib):
-    """Three drive patterns in one run equal three single runs bit for bit."""
+    """Drive patterns in one run equal single runs bit for bit, whatever the
+    batch width (3: scalar path; 9 FP32 / 5 FP64: padded to the 32-byte
+    vector width)."""
     from paper_2603_06267_gb300 import dghex
-    w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40, batch=3, steer=True)
+    w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40, batch=9, steer=True)
     s = dghex.HexSolver(w)
-    drive = w.drive(s.dt, w.nsteps, 3)
-    for prec in (0, 1):
-        tr = s.run(drive=drive, precision=prec, batch=3)
-        for b in range(3):
+    drive = w.drive(s.dt, w.nsteps, 9)
+    for prec, B in ((0, 3), (1, 3), (1, 9), (0, 5)):
+        tr = s.run(drive=np.ascontiguousarray(drive[:B]), precision=prec, batch=B)
+        for b in range(B):
             one = s.run(drive=np.ascontiguousarray(drive[b:b + 1]), precision=prec, batch=1)
-            assert np.array_equal(one[0], tr[b])
+            assert np.array_equal(one[0], tr[b]), (prec, B, b)
     s.close()
 
 

@@ -116,15 +116,11 @@ def scramble_orientation(elements: np.ndarray, faces_lists, seed: int):
 
 
 def _lattice_elements(nx, ny, nz, offset=0):
-    vid = lambda i, j, k: offset + (k * (ny + 1) + j) * (nx + 1) + i
-    el = np.zeros((nx * ny * nz, 8), dtype=np.int64)
-    e = 0
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                for c in range(8):
-                    el[e, c] = vid(i + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1))
-                e += 1
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    i, j, k = i.ravel(), j.ravel(), k.ravel()
+    el = np.zeros((i.size, 8), dtype=np.int64)
+    for c in range(8):
+        el[:, c] = offset + ((k + ((c >> 2) & 1)) * (ny + 1) + (j + ((c >> 1) & 1))) * (nx + 1) + (i + (c & 1))
     return el
 
 
@@ -295,4 +291,15 @@ def hex_c2_like(nsteps=400, batch=1, amp=0.1, bump=0.3, seed=51, steer=True) -> 
     w = distorted_two_domain(nx_p=64, nz_p=16, nx_s=32, nz_s=64, h_p=25e-6, amp=amp, bump=bump, seed=seed,
                              n_pmut_side=16, n_modes=5, nsteps=nsteps, batch=batch, n_recv=64, steer=steer)
     w.name = "hex_c2_like"
+    return w
+
+
+def hex_c3_like(nsteps=400, batch=64, amp=0.1, bump=0.3, seed=61) -> HexWorkload:
+    """The 1024-PMUT mesh class as distorted hexahedra: fine primary 128 x 128 x
+    16 (h = 25 um, N = 4) under a coarse secondary 64 x 64 x 96 (N = 6) with a
+    bent interface, 32 x 32 PMUTs at 100 um pitch, 64 receivers, beam-steering
+    drive patterns."""
+    w = distorted_two_domain(nx_p=128, nz_p=16, nx_s=64, nz_s=96, h_p=25e-6, amp=amp, bump=bump, seed=seed,
+                             n_pmut_side=32, n_modes=5, nsteps=nsteps, batch=batch, n_recv=64, steer=True)
+    w.name = "hex_c3_like"
     return w
