@@ -13,7 +13,9 @@ Default workload: 64 beam-steering drive patterns on the 1024-PMUT mesh
 torchrun (N > 1) every rank runs its own batch of patterns (replicas; the
 path needs no data exchange) and rank 0 reports the max time over ranks.
 `--impl reference` times the CPU oracle on a bounded sample of the same
-workload instead.
+workload instead.  `--workload hex_c3_like` (or hex_c2_like) measures the
+general-hexahedron path (include/dghex.h) on the same mesh class with
+displaced vertices and a bent interface.
 """
 from __future__ import annotations
 
