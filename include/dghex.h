@@ -35,9 +35,10 @@
  * faces topologically.
  *
  * Node order of full-field vectors: every node of domain 0 then every node
- * of domain 1; inside a domain, nodes are numbered in order of first
- * appearance over the elements (element order, then local GLL index
- * a + (N+1) b + (N+1)^2 c).  dghex_nodes gives their positions.
+ * of domain 1; inside a domain, the nodes of each mesh entity (vertex, edge,
+ * face, element interior) get consecutive numbers when the entity first
+ * appears, scanning the elements in order and each element's nodes by local
+ * GLL index a + (N+1) b + (N+1)^2 c.  dghex_nodes gives their positions.
  */
 #ifndef DGHEX_H
 #define DGHEX_H
@@ -141,6 +142,15 @@ int dghex_set_state(dghex_ctx* ctx, const double* p0, const double* v0);
 
 /* Pressure p^n of every batch member after the last run, [batch][ndof]. */
 int dghex_get_pressure(const dghex_ctx* ctx, double* p, size_t len);
+
+/* Interface kernel.  When every Gauss node of a (fine face, coarse element)
+ * group lies on one face of each side's element (a geometrically conforming
+ * interface; checked at mesh creation to 1e-12 in the coarse reference
+ * coordinate), the interface terms are evaluated on collapsed face arrays;
+ * otherwise by full tensor evaluation at each node.  general = 1 forces the
+ * full evaluation (0 restores the automatic choice).  Both give the same
+ * operator up to rounding. */
+int dghex_set_interface_kernel(dghex_ctx* ctx, int general);
 
 /* Kernel instrumentation as dgsem_profile / dgsem_kernel_stats. */
 #define DGHEX_K_PMUT 0       /* PMUT modal step                                   */

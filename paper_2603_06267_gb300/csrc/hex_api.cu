@@ -229,7 +229,10 @@ struct dghex_ctx {
   std::vector<double> refm;
   int ng = 0, max_pts = 0;
   long long islot0 = 0, nislot = 0;
-  std::vector<int> g_fe, g_ce, g_pt, pt_idx;
+  std::vector<int> g_fe, g_ce, g_pt, pt_idx, g_face;
+  bool onface = false;                      // every group's Gauss nodes lie on one face per side
+  bool force_general_iface = false;         // use the general interface kernel even when onface
+  int* d_g_face = nullptr;
   std::vector<long long> g_slot;
   int *d_g_fe = nullptr, *d_g_ce = nullptr, *d_g_pt = nullptr, *d_pt_idx = nullptr;
   long long* d_g_slot = nullptr;
@@ -433,6 +436,8 @@ int setup_interface(dghex_ctx* c, const dghex_mesh_desc* d) {
                    t / (q * q), t % (q * q));
   // groups: per fine face, its nodes split by coarse element (first appearance)
   c->g_fe.clear(); c->g_ce.clear(); c->g_pt.assign(1, 0); c->pt_idx.clear(); c->g_slot.clear();
+  c->g_face.clear();
+  c->onface = true;
   long long slot = c->nvol;
   c->max_pts = 0;
   for (int f = 0; f < c->nff; ++f) {
@@ -442,14 +447,23 @@ int setup_interface(dghex_ctx* c, const dghex_mesh_desc* d) {
       if (std::find(ces.begin(), ces.end(), ce) == ces.end()) ces.push_back(ce);
     }
     for (int ce : ces) {
-      int cnt = 0;
-      for (int j = 0; j < q * q; ++j)
-        if (c->cf[2 * c->match[(size_t)f * q * q + j]] == ce) {
-          c->pt_idx.push_back(f * q * q + j);
-          ++cnt;
-        }
+      int cnt = 0, cface = -1;
+      for (int j = 0; j < q * q; ++j) {
+        const size_t t = (size_t)f * q * q + j;
+        if (c->cf[2 * c->match[t]] != ce) continue;
+        c->pt_idx.push_back((int)t);
+        ++cnt;
+        // on the matched coarse face: one face for the whole group, and the
+        // Newton reference position on it to rounding
+        const int lf = c->cf[2 * c->match[t] + 1];
+        if (cface < 0) cface = lf;
+        const double want = (lf & 1) ? 1.0 : -1.0;
+        if (lf != cface || std::fabs(c->refm[3 * t + (lf >> 1)] - want) > 1e-12) c->onface = false;
+      }
       c->g_fe.push_back(c->ff[2 * f]);
       c->g_ce.push_back(ce);
+      c->g_face.push_back(c->ff[2 * f + 1]);
+      c->g_face.push_back(cface);
       c->g_pt.push_back((int)c->pt_idx.size());
       c->g_slot.push_back(slot);
       slot += Dp.nl + Dm.nl;
@@ -459,7 +473,8 @@ int setup_interface(dghex_ctx* c, const dghex_mesh_desc* d) {
   c->ng = (int)c->g_fe.size();
   c->nislot = slot - c->nvol;
   if ((rc = upload(&c->d_g_fe, c->g_fe)) || (rc = upload(&c->d_g_ce, c->g_ce)) || (rc = upload(&c->d_g_pt, c->g_pt)) ||
-      (rc = upload(&c->d_pt_idx, c->pt_idx)) || (rc = upload(&c->d_g_slot, c->g_slot)))
+      (rc = upload(&c->d_pt_idx, c->pt_idx)) || (rc = upload(&c->d_g_slot, c->g_slot)) ||
+      (rc = upload(&c->d_g_face, c->g_face)))
     return rc;
   return DGSEM_OK;
 }
@@ -581,6 +596,12 @@ int launch_residual(dghex_ctx* c, cudaStream_t s) {
     a.p = p; a.S = S; a.Bp = c->Bp;
     a.conn_p = Dp.d_conn; a.conn_m = Dm.d_conn;
     a.g_fe = c->d_g_fe; a.g_ce = c->d_g_ce; a.g_pt = c->d_g_pt; a.pt_idx = c->d_pt_idx; a.g_slot = c->d_g_slot;
+    a.g_face = c->d_g_face;
+    a.onface = c->onface && !c->force_general_iface ? 1 : 0;
+    for (int i = 0; i < Dp.n; ++i)
+      for (int j = 0; j < Dp.n; ++j) a.Dp[i][j] = T(Dp.basis->D[i * Dp.n + j]);
+    for (int i = 0; i < Dm.n; ++i)
+      for (int j = 0; j < Dm.n; ++j) a.Dm[i][j] = T(Dm.basis->D[i * Dm.n + j]);
     a.pdat = c->d_pdat;
     for (int i = 0; i < Dp.n; ++i) a.xip[i] = Dp.basis->x[i];
     for (int i = 0; i < Dm.n; ++i) a.xim[i] = Dm.basis->x[i];
@@ -1008,6 +1029,12 @@ int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
   return DGSEM_OK;
 }
 
+int dghex_set_interface_kernel(dghex_ctx* c, int general) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  c->force_general_iface = general != 0;
+  return DGSEM_OK;
+}
+
 int dghex_profile(dghex_ctx* c, int enable) {
   if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
   c->profiling = enable != 0;
@@ -1036,6 +1063,7 @@ void dghex_destroy(dghex_ctx* c) {
     D.basis = nullptr;
   }
   dfree(c->d_g_fe); dfree(c->d_g_ce); dfree(c->d_g_pt); dfree(c->d_pt_idx); dfree(c->d_g_slot); dfree(c->d_pdat);
+  dfree(c->d_g_face);
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
   dfree(c->d_node_ptr); dfree(c->d_node_slot);
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);

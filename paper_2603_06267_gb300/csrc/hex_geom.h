@@ -207,11 +207,14 @@ struct HexIfaceArgs {
   const int* g_pt;                    // [ng+1] CSR into pt_idx
   const int* pt_idx;                  // interface node ids (rows of pdat)
   const long long* g_slot;            // [ng] first slot of the group's block
+  const int* g_face;                  // [ng][2] local face of K+ and of K- (face kernel)
   const double* pdat;
   double xip[MAXN1], xim[MAXN1];
+  T Dp[MAXN1][MAXN1], Dm[MAXN1][MAXN1];   // derivative matrices of the two orders (face kernel)
   int np, nm;                         // GLL nodes per direction, fine / coarse
   double c2p, c2m;
   int ng, max_pts;
+  int onface;                         // every Gauss node lies on one face of each side's element
 };
 
 // Step: residual assembly (sum of a node's slots in ascending slot order)

@@ -265,22 +265,6 @@ constexpr bool packed2() { return std::is_same<T, float>::value && BB % 2 == 0; 
 
 __device__ __forceinline__ float2 sub2_(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
-// acc += d * (x - y)
-template <typename T, int BB>
-__device__ __forceinline__ void vfma_diff(Pack<T, BB>& acc, T d, const Pack<T, BB>& x, const Pack<T, BB>& y) {
-  if constexpr (packed2<T, BB>()) {
-    const float2 d2 = make_float2(d, d);
-#pragma unroll
-    for (int b = 0; b < BB; b += 2) {
-      float2& a = *reinterpret_cast<float2*>(&acc.v[b]);
-      a = __ffma2_rn(d2, sub2_(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b])), a);
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < BB; ++b) acc.v[b] = fma_(d, sub_(x.v[b], y.v[b]), acc.v[b]);
-  }
-}
-
 // acc += d * x
 template <typename T, int BB>
 __device__ __forceinline__ void vfma(Pack<T, BB>& acc, T d, const Pack<T, BB>& x) {
@@ -313,6 +297,22 @@ __device__ __forceinline__ Pack<T, BB> vmul(T d, const Pack<T, BB>& x) {
   return o;
 }
 
+// x - y
+template <typename T, int BB>
+__device__ __forceinline__ Pack<T, BB> vsub(const Pack<T, BB>& x, const Pack<T, BB>& y) {
+  Pack<T, BB> o;
+  if constexpr (packed2<T, BB>()) {
+#pragma unroll
+    for (int b = 0; b < BB; b += 2)
+      *reinterpret_cast<float2*>(&o.v[b]) =
+          sub2_(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b]));
+  } else {
+#pragma unroll
+    for (int b = 0; b < BB; ++b) o.v[b] = sub_(x.v[b], y.v[b]);
+  }
+  return o;
+}
+
 // x + y
 template <typename T, int BB>
 __device__ __forceinline__ Pack<T, BB> vadd(const Pack<T, BB>& x, const Pack<T, BB>& y) {
@@ -341,8 +341,10 @@ __device__ __forceinline__ Pack<T, BB> vzero() {
 // A CTA takes E elements and BB batch members at a time; each element has
 // n^2 threads, and thread q of an element owns the x-line (b, c), the y-line
 // (a, c) and the z-line (a, b) with (., .) = (q mod n, q div n):
-//   A: x- and y-lines: grad^_x u, grad^_y u of their line (difference form
-//      sum_m D_am (u_m - u_a), exact for constants in any precision) -> smem
+//   A: x- and y-lines: grad^_x u, grad^_y u of their line in difference form
+//      sum_m D_am (u_m - u_0) with the line's first node as reference (exact
+//      for constants in any precision; rounding scales with the variation
+//      along the line, not with u) -> smem
 //   B: z-line: grad^_z u in registers, then F = G grad^ u at its nodes with
 //      the geometric factors G; F_x, F_y -> smem, F_z stays in registers
 //   C: x-lines: D^T F_x -> R_x; y-lines: D^T F_y -> R_y (in place)
@@ -452,14 +454,18 @@ __global__ void __launch_bounds__(VolTeam<N>::threads) hex_vol_kernel(const __gr
         ly[m] = U.ld(o + qa + n * m + n * n * qb);
       }
 #pragma unroll
-      for (int a = 0; a < n; ++a) {
-        P ox = vzero<T, BB>(), oy = vzero<T, BB>();
+      for (int m = n - 1; m > 0; --m) {
+        lx[m] = vsub(lx[m], lx[0]);
+        ly[m] = vsub(ly[m], ly[0]);
+      }
 #pragma unroll
-        for (int m = 0; m < n; ++m) {
-          if (m == a) continue;
+      for (int a = 0; a < n; ++a) {
+        P ox = vmul(T(A.D[a][1]), lx[1]), oy = vmul(T(A.D[a][1]), ly[1]);
+#pragma unroll
+        for (int m = 2; m < n; ++m) {
           const T d = A.D[a][m];
-          vfma_diff(ox, d, lx[m], lx[a]);
-          vfma_diff(oy, d, ly[m], ly[a]);
+          vfma(ox, d, lx[m]);
+          vfma(oy, d, ly[m]);
         }
         G0.st(o + a + n * qa + n * n * qb, ox);
         G1.st(o + qa + n * a + n * n * qb, oy);
@@ -473,13 +479,12 @@ __global__ void __launch_bounds__(VolTeam<N>::threads) hex_vol_kernel(const __gr
 #pragma unroll
       for (int m = 0; m < n; ++m) lz[m] = U.ld(o + qa + n * qb + n * n * m);
 #pragma unroll
-      for (int c = 0; c < n; ++c) {
-        P gz = vzero<T, BB>();
+      for (int m = n - 1; m > 0; --m) lz[m] = vsub(lz[m], lz[0]);
 #pragma unroll
-        for (int m = 0; m < n; ++m) {
-          if (m == c) continue;
-          vfma_diff(gz, T(A.D[c][m]), lz[m], lz[c]);
-        }
+      for (int c = 0; c < n; ++c) {
+        P gz = vmul(T(A.D[c][1]), lz[1]);
+#pragma unroll
+        for (int m = 2; m < n; ++m) vfma(gz, T(A.D[c][m]), lz[m]);
         const int k = qa + n * qb + n * n * c;
         const T* gp = gsm + k;
         const T G00 = gp[0], G11 = gp[gs], G22 = gp[2 * gs], G01 = gp[3 * gs], G02 = gp[4 * gs], G12 = gp[5 * gs];
@@ -693,6 +698,161 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
   }
 }
 
+// Interface terms when every Gauss node of a group lies on one face of K+
+// and on one face of K- (a geometrically conforming interface): on a face,
+// psi_abc = delta_{c,face} l_a l_b and d psi / d xi_normal = l_a l_b l_c'(+-1),
+// so each side first collapses to two face arrays (the face layer u_f and the
+// normal derivative u_n = sum_c l_c'(+-1) u_abc), the Gauss-node values and
+// reference gradients cost O(n^2) each, and the projection back collapses the
+// same way: R_f (value and tangential terms) on the face layer and R_n (the
+// normal-derivative term) spread along each normal line by l_c'(+-1).
+template <typename T, int BB>
+__global__ void __launch_bounds__(128) hex_iface_face_kernel(const __grid_constant__ HexIfaceArgs<T> A) {
+  using P = Pack<T, BB>;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  const int g = blockIdx.x;
+  const int np = A.np, nm = A.nm;
+  const int nlp = np * np * np, nlm = nm * nm * nm;
+  const int p0 = A.g_pt[g], npts = A.g_pt[g + 1] - p0;
+  const int Q = A.max_pts;
+  P* up = reinterpret_cast<P*>(smem_raw);
+  P* um = up + nlp;
+  P* cf = um + nlm;                      // [np^2] u_f+, [np^2] u_n+, [nm^2] u_f-, [nm^2] u_n-
+  P* pv = cf + 2 * (np * np + nm * nm);  // [Q][4]: value and d/dn+ of each side
+  P* sv = pv + 4 * Q;                    // [Q]
+  P* sd = sv + Q;                        // [Q]
+  T* tb = reinterpret_cast<T*>(sd + Q);  // [Q][2 sides][2 axes][2][MAXN1]: l, l' along the face axes
+  T* av = tb + (long long)Q * 8 * MAXN1; // [Q][8]: c+^2 a+ (t0, t1, n), c-^2 a- (t0, t1, n), W, gamma
+  const int tid = threadIdx.x;
+  const int fp = A.g_face[2 * g], fm = A.g_face[2 * g + 1];
+  const T c2p = T(A.c2p), c2m = T(A.c2m);
+  for (int j = tid; j < npts; j += blockDim.x) {
+    const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
+    double l[MAXN1], dl[MAXN1];
+    for (int side = 0; side < 2; ++side) {
+      const int f = side ? fm : fp, n = side ? nm : np, ax = f >> 1;
+      const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+      const int ta[2] = {t0, t1};
+      const double* ref = d + 3 * side;
+      for (int k = 0; k < 2; ++k) {
+        lagrange(n, side ? A.xim : A.xip, ref[ta[k]], l, dl);
+        T* row = tb + ((j * 2 + side) * 2 + k) * 2 * MAXN1;
+        for (int i = 0; i < n; ++i) {
+          row[i] = T(l[i]);
+          row[MAXN1 + i] = T(dl[i]);
+        }
+      }
+      const double c2 = side ? A.c2m : A.c2p;
+      const double* a = d + 6 + 3 * side;
+      av[8 * j + 3 * side] = T(c2 * a[t0]);
+      av[8 * j + 3 * side + 1] = T(c2 * a[t1]);
+      av[8 * j + 3 * side + 2] = T(c2 * a[ax]);
+    }
+    av[8 * j + 6] = T(d[12]);
+    av[8 * j + 7] = T(d[13]);
+  }
+  const int fe = A.g_fe[g], ce = A.g_ce[g];
+  const long long slot = A.g_slot[g];
+  const int nch = A.Bp / BB;
+  for (int ch = 0; ch < nch; ++ch) {
+    for (int i = tid; i < nlp; i += blockDim.x)
+      up[i] = reinterpret_cast<const P*>(A.p + (long long)A.conn_p[(long long)fe * nlp + i] * A.Bp)[ch];
+    for (int i = tid; i < nlm; i += blockDim.x)
+      um[i] = reinterpret_cast<const P*>(A.p + (long long)A.conn_m[(long long)ce * nlm + i] * A.Bp)[ch];
+    __syncthreads();
+    // collapse each side to its face layer and normal derivative
+    for (int t = tid; t < np * np + nm * nm; t += blockDim.x) {
+      const bool plus = t < np * np;
+      const int n = plus ? np : nm, k = plus ? t : t - np * np;
+      const int f = plus ? fp : fm, ax = f >> 1;
+      const int s[3] = {1, n, n * n};
+      const int st0 = s[ax == 0 ? 1 : 0], st1 = s[ax == 2 ? 1 : 2], sn = s[ax];
+      const int fi = (f & 1) ? n - 1 : 0;
+      const int base = (k % n) * st0 + (k / n) * st1;
+      const P* u = plus ? up : um;
+      const T(*D)[MAXN1] = plus ? A.Dp : A.Dm;
+      P un = vmul(D[fi][0], u[base]);
+      for (int c = 1; c < n; ++c) vfma(un, D[fi][c], u[base + c * sn]);
+      P* dst = cf + (plus ? 0 : 2 * np * np);
+      dst[k] = u[base + fi * sn];
+      dst[n * n + k] = un;
+    }
+    __syncthreads();
+    // value and normal derivative (d/dn+) of each side at each Gauss node
+    for (int t = tid; t < 2 * npts; t += blockDim.x) {
+      const int side = t >= npts, j = side ? t - npts : t;
+      const int n = side ? nm : np;
+      const P* uf = cf + (side ? 2 * np * np : 0);
+      const P* un = uf + n * n;
+      const T* L0 = tb + ((j * 2 + side) * 2 + 0) * 2 * MAXN1;
+      const T* L1 = tb + ((j * 2 + side) * 2 + 1) * 2 * MAXN1;
+      P v = vzero<T, BB>(), d0 = vzero<T, BB>(), d1 = vzero<T, BB>(), dn = vzero<T, BB>();
+      for (int i1 = 0; i1 < n; ++i1) {
+        P s0 = vzero<T, BB>(), s1 = vzero<T, BB>(), sn = vzero<T, BB>();
+        for (int i0 = 0; i0 < n; ++i0) {
+          const P a = uf[i0 + n * i1], b = un[i0 + n * i1];
+          vfma(s0, L0[i0], a);
+          vfma(s1, L0[MAXN1 + i0], a);
+          vfma(sn, L0[i0], b);
+        }
+        vfma(v, L1[i1], s0);
+        vfma(d0, L1[i1], s1);
+        vfma(d1, L1[MAXN1 + i1], s0);
+        vfma(dn, L1[i1], sn);
+      }
+      // c^2 dp/dn+ = c^2 (a_t0 d0 + a_t1 d1 + a_n dn)
+      const T* a = av + 8 * j + 3 * side;
+      P w = vmul(a[0], d0);
+      vfma(w, a[1], d1);
+      vfma(w, a[2], dn);
+      pv[4 * j + 2 * side] = v;
+      pv[4 * j + 2 * side + 1] = w;
+    }
+    __syncthreads();
+    for (int j = tid; j < npts; j += blockDim.x) {
+      const T W = av[8 * j + 6], gam = av[8 * j + 7];
+      const P jump = vsub(pv[4 * j], pv[4 * j + 2]);
+      // A = 1/2 (c+^2 dp+/dn+ + c-^2 dp-/dn+)
+      const P avg = vmul(T(0.5), vadd(pv[4 * j + 1], pv[4 * j + 3]));
+      sv[j] = vmul(W, vsub(vmul(gam, jump), avg));
+      sd[j] = vmul(mul_(T(-0.5), W), jump);
+    }
+    __syncthreads();
+    // projection back onto each side's element: face arrays, then normal lines
+    for (int t = tid; t < np * np + nm * nm; t += blockDim.x) {
+      const bool plus = t < np * np;
+      const int side = plus ? 0 : 1;
+      const int n = plus ? np : nm, k = plus ? t : t - np * np;
+      const int i0 = k % n, i1 = k / n;
+      const T sgn = plus ? T(1) : T(-1);
+      P Rf = vzero<T, BB>(), Rn = vzero<T, BB>();
+      for (int j = 0; j < npts; ++j) {
+        const T* L0 = tb + ((j * 2 + side) * 2 + 0) * 2 * MAXN1;
+        const T* L1 = tb + ((j * 2 + side) * 2 + 1) * 2 * MAXN1;
+        const T* a = av + 8 * j + 3 * side;
+        const T psi = mul_(L0[i0], L1[i1]);
+        const T gt = fma_(a[1], mul_(L0[i0], L1[MAXN1 + i1]), mul_(a[0], mul_(L0[MAXN1 + i0], L1[i1])));
+        const T gn = mul_(a[2], psi);
+        vfma(Rf, mul_(sgn, psi), sv[j]);
+        vfma(Rf, gt, sd[j]);
+        vfma(Rn, gn, sd[j]);
+      }
+      const int f = plus ? fp : fm, ax = f >> 1;
+      const int s[3] = {1, n, n * n};
+      const int st0 = s[ax == 0 ? 1 : 0], st1 = s[ax == 2 ? 1 : 2], sn = s[ax];
+      const int fi = (f & 1) ? n - 1 : 0;
+      const T(*D)[MAXN1] = plus ? A.Dp : A.Dm;
+      const long long sb = slot + (plus ? 0 : nlp) + i0 * st0 + i1 * st1;
+      for (int c = 0; c < n; ++c) {
+        P r = vmul(D[fi][c], Rn);
+        if (c == fi) r = vadd(r, Rf);
+        reinterpret_cast<P*>(A.S + (sb + (long long)c * sn) * A.Bp)[ch] = r;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Residual assembly and leapfrog update, one thread per (node, BB members):
 // r = sum of the node's slots (ascending slot order, so the sum is the same
 // in every run and for every batch width), v += cv M^-1 r, p += cp v.
@@ -848,7 +1008,28 @@ size_t iface_smem(const HexIfaceArgs<T>& a) {
 }
 
 template <typename T, int BB>
+size_t iface_face_smem(const HexIfaceArgs<T>& a) {
+  const long long Q = a.max_pts;
+  const long long nlp = (long long)a.np * a.np * a.np, nlm = (long long)a.nm * a.nm * a.nm;
+  const long long nf = 2LL * (a.np * a.np + a.nm * a.nm);
+  return sizeof(T) * BB * (size_t)(nlp + nlm + nf + 6 * Q) + sizeof(T) * (size_t)(Q * 8 * MAXN1 + 8 * Q);
+}
+
+template <typename T, int BB>
+cudaError_t iface_face_bb(const HexIfaceArgs<T>& a, cudaStream_t s) {
+  const size_t sm = iface_face_smem<T, BB>(a);
+  if (sm > 48 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(hex_iface_face_kernel<T, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  hex_iface_face_kernel<T, BB><<<a.ng, 128, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int BB>
 cudaError_t iface_bb(const HexIfaceArgs<T>& a, cudaStream_t s) {
+  if (a.onface) return iface_face_bb<T, BB>(a, s);
   const size_t sm = iface_smem<T, BB>(a);
   if (sm > 48 * 1024) {
     const cudaError_t e =

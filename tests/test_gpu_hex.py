@@ -76,13 +76,16 @@ def test_nodes_mass_layout_and_pmut_weights(lib, two_dom):
     s.close()
 
 
+@pytest.mark.parametrize("general", [False, True])
 @pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
-def test_two_domain_pmut_parity(lib, two_dom, prec, tol):
+def test_two_domain_pmut_parity(lib, two_dom, prec, tol, general):
     """Distorted fine/coarse pair with a bent 2:1 interface, rotated element
-    frames and a driven PMUT array: traces and the final field."""
+    frames and a driven PMUT array: traces and the final field, with the
+    face-collapsed and with the full-evaluation interface kernel."""
     from paper_2603_06267_gb300 import dghex
     w, prob = two_dom
     s = dghex.HexSolver(w)
+    dghex.dghex_set_interface_kernel(s.ctx, general)
     tr = s.run(precision=prec)
     ref = prob.run(dt=s.dt)
     assert np.max(np.abs(ref)) > 0
@@ -126,11 +129,12 @@ def test_batch_members_are_independent(lib):
     w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=40, batch=9, steer=True)
     s = dghex.HexSolver(w)
     drive = w.drive(s.dt, w.nsteps, 9)
-    for prec, B in ((0, 3), (1, 3), (1, 9), (0, 5)):
+    for prec, B, general in ((0, 3, False), (1, 3, False), (1, 9, False), (0, 5, False), (1, 9, True)):
+        dghex.dghex_set_interface_kernel(s.ctx, general)
         tr = s.run(drive=np.ascontiguousarray(drive[:B]), precision=prec, batch=B)
         for b in range(B):
             one = s.run(drive=np.ascontiguousarray(drive[b:b + 1]), precision=prec, batch=1)
-            assert np.array_equal(one[0], tr[b]), (prec, B, b)
+            assert np.array_equal(one[0], tr[b]), (prec, B, b, general)
     s.close()
 
 
