@@ -143,6 +143,15 @@ int dghex_set_state(dghex_ctx* ctx, const double* p0, const double* v0);
 /* Pressure p^n of every batch member after the last run, [batch][ndof]. */
 int dghex_get_pressure(const dghex_ctx* ctx, double* p, size_t len);
 
+/* Power iteration for lambda_max(M^-1 K) on the device in FP64 (iters
+ * products, with the step's own stiffness and interface kernels, from a fixed
+ * pseudo-random start vector).  Returns DGSEM_EUNSTABLE if dt > 0.95 * 2 /
+ * sqrt(lambda_max) (the explicit scheme's limit; the CFL rule of
+ * dghex_mesh_create is a heuristic on distorted elements); *lambda_max (may
+ * be NULL) receives the estimate either way.  Uses the run state as scratch:
+ * the next dghex_run starts afresh. */
+int dghex_check_stability(dghex_ctx* ctx, int iters, double* lambda_max);
+
 /* Interface kernel.  When every Gauss node of a (fine face, coarse element)
  * group lies on one face of each side's element (a geometrically conforming
  * interface; checked at mesh creation to 1e-12 in the coarse reference

@@ -1029,6 +1029,49 @@ int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
   return DGSEM_OK;
 }
 
+int dghex_check_stability(dghex_ctx* c, int iters, double* lambda_max) {
+  if (!c || iters < 1) return hfail(DGSEM_EINVAL, "ctx is NULL or iters < 1");
+  int rc = ensure_run_state(c, DGSEM_FP64, 1);
+  if (rc) return rc;
+  c->state_valid = false;
+  double* P = static_cast<double*>(c->P);
+  double* V = static_cast<double*>(c->V);
+  double* d_n2 = nullptr;
+  if ((rc = dmalloc(&d_n2, 2 * sizeof(double)))) return rc;
+  // deterministic start vector in [-1, 1] (a 64-bit linear congruential sequence)
+  std::vector<double> x((size_t)c->ndof);
+  unsigned long long st = 0x9E3779B97F4A7C15ULL;
+  for (auto& v : x) {
+    st = st * 6364136223846793005ULL + 1442695040888963407ULL;
+    v = (double)(st >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+  cudaStream_t s = 0;
+  double lam = 0.0;
+  cudaError_t e = cudaMemcpy(P, x.data(), x.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->S, 0, sizeof(double) * c->nslot, s);
+  for (int it = 0; it < iters && e == cudaSuccess && rc == DGSEM_OK; ++it) {
+    // v = M^-1 K x through the step's own kernels (zero forcing slots, v = 0 first)
+    e = cudaMemsetAsync(V, 0, sizeof(double) * c->ndof, s);
+    if (e != cudaSuccess) break;
+    if ((rc = launch_residual<double>(c, s)) || (rc = launch_update<double>(c, s, 1.0, 0.0))) break;
+    if ((e = hex::launch_norm2(P, c->ndof, d_n2, s)) != cudaSuccess) break;
+    if ((e = hex::launch_norm2(V, c->ndof, d_n2 + 1, s)) != cudaSuccess) break;
+    double n2[2];
+    if ((e = cudaMemcpy(n2, d_n2, sizeof(n2), cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+    lam = std::sqrt(n2[1] / n2[0]);
+    if (!(n2[1] > 0.0) || !std::isfinite(lam)) break;
+    e = hex::launch_scale(P, V, d_n2 + 1, c->ndof, s);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  dfree(d_n2);
+  if (rc) return rc;
+  if (e != cudaSuccess) return hfail(DGSEM_ECUDA, "stability check: %s", cudaGetErrorString(e));
+  if (lambda_max) *lambda_max = lam;
+  if (lam > 0.0 && c->dt > 0.95 * 2.0 / std::sqrt(lam))
+    return hfail(DGSEM_EUNSTABLE, "dt %.4g above 0.95 * 2 / sqrt(lambda_max) = %.4g", c->dt, 0.95 * 2.0 / std::sqrt(lam));
+  return DGSEM_OK;
+}
+
 int dghex_set_interface_kernel(dghex_ctx* c, int general) {
   if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
   c->force_general_iface = general != 0;

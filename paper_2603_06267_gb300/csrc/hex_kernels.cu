@@ -926,6 +926,42 @@ __global__ void __launch_bounds__(256) hex_tail_kernel(const __grid_constant__ H
 }
 
 // ---------------------------------------------------------------------------
+// Power iteration helpers (FP64, one batch member): sum of squares, scaling
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) norm2_kernel(const double* x, long long n, double* out) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    s = fma(x[i], x[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double w[8];
+  if ((threadIdx.x & 31) == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += w[k];
+    atomicAdd(out, t);
+  }
+}
+
+__global__ void __launch_bounds__(256) scale_kernel(double* dst, const double* src, const double* norm2, long long n) {
+  const double s = 1.0 / sqrt(*norm2);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i] * s;
+}
+
+cudaError_t launch_norm2(const double* x, long long n, double* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  norm2_kernel<<<1216, 256, 0, s>>>(x, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(double* dst, const double* src, const double* norm2, long long n, cudaStream_t s) {
+  scale_kernel<<<1216, 256, 0, s>>>(dst, src, norm2, n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_geom(const GeomArgs& a, cudaStream_t s) {

@@ -17,7 +17,8 @@ from .dgsem import DGSEM_FP32_MIXED, DGSEM_FP64, DgsemError, _current_stream, _f
 
 EXPORTED = [
     "dghex_mesh_create", "dghex_get_dt", "dghex_nodes", "dghex_pmut_nodes", "dghex_pmut_set", "dghex_get_matches",
-    "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_set_interface_kernel", "dghex_profile",
+    "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_check_stability", "dghex_set_interface_kernel",
+    "dghex_profile",
     "dghex_kernel_stats", "dghex_destroy",
 ]
 DGHEX_K_PMUT, DGHEX_K_VOL, DGHEX_K_IFACE, DGHEX_K_UPDATE, DGHEX_K_TAIL = 0, 1, 2, 3, 4
@@ -55,6 +56,7 @@ def load_library():
     lib.dghex_run.argtypes = [vp, c_int, c_int, c_int, vp, c_int, vp, vp, c_int, vp]
     lib.dghex_set_state.argtypes = [vp, vp, vp]
     lib.dghex_get_pressure.argtypes = [vp, vp, c_size_t]
+    lib.dghex_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
     lib.dghex_set_interface_kernel.argtypes = [vp, c_int]
     lib.dghex_profile.argtypes = [vp, c_int]
     lib.dghex_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
@@ -186,6 +188,14 @@ def dghex_get_pressure(ctx, batch: int, ndof: int) -> np.ndarray:
     out = np.zeros((batch, ndof))
     _check(_lib.dghex_get_pressure(ctx, _ptr(out), out.size), "dghex_get_pressure")
     return out
+
+
+def dghex_check_stability(ctx, iters: int = 100):
+    """(status, lambda_max of M^-1 K): status DGSEM_EUNSTABLE when dt is above
+    0.95 * 2 / sqrt(lambda_max)."""
+    lam = c_double()
+    code = _lib.dghex_check_stability(ctx, iters, byref(lam))
+    return code, lam.value
 
 
 def dghex_set_interface_kernel(ctx, general: bool):

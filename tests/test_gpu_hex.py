@@ -184,3 +184,71 @@ def test_errors_inverted_element_and_unmatched_interface(lib):
     s = dghex.HexSolver(w)
     s.run(nsteps=3)
     s.close()
+
+
+@pytest.mark.parametrize("general", [False, True])
+@pytest.mark.parametrize("orders,dims", [((2, 3), (4, 1, 2, 2)), ((3, 5), (4, 1, 2, 2)), ((4, 8), (2, 1, 1, 1)),
+                                         ((1, 2), (4, 2, 2, 2))])
+def test_order_pairs_vector_and_scalar_paths(lib, orders, dims, general):
+    """Other order pairs across the bent interface, with a batch wide enough
+    for the 32-byte vector path (9 FP32 members, 5 FP64 members) and with one
+    member (scalar path), against the oracle."""
+    from paper_2603_06267_gb300 import dghex
+    nxp, nzp, nxs, nzs = dims
+    w = H.distorted_two_domain(nx_p=nxp, nz_p=nzp, nx_s=nxs, nz_s=nzs, order_p=orders[0], order_s=orders[1],
+                               n_pmut_side=1, nsteps=40, scramble=5, batch=9, steer=True)
+    prob = HO.HexOracleProblem(w)
+    s = dghex.HexSolver(w)
+    dghex.dghex_set_interface_kernel(s.ctx, general)
+    for prec, tol, B in ((0, FP64_TOL, 5), (1, FP32_TOL, 9), (0, FP64_TOL, 1)):
+        drive = w.drive(s.dt, w.nsteps, B)
+        tr = s.run(drive=drive, precision=prec, batch=B)
+        ref = prob.run(dt=s.dt, drive=drive, batch=B)
+        assert np.max(np.abs(ref)) > 0
+        assert _rel(tr, ref) < tol, (orders, prec, B, _rel(tr, ref))
+    s.close()
+
+
+@pytest.mark.parametrize("order", [1, 2, 7, 8])
+def test_single_domain_orders(lib, order):
+    """Distorted single box at the lowest and highest orders, from a smooth
+    initial state, FP64 and FP32 (scalar and vector paths)."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_one_domain(nel=(2, 2, 2), order=order, nsteps=40)
+    w.pmuts = None
+    prob = HO.HexOracleProblem(w)
+    s = dghex.HexSolver(w)
+    xyz, first = dghex.dghex_nodes(s.ctx)
+    idx = _node_map(prob, xyz, first)
+    X = prob.meshes[0].coords
+    p0 = W.seeded_field(8, X[:, 0], X[:, 1], X[:, 2])
+    g0 = np.zeros(s.ndof)
+    g0[idx] = p0
+    dghex.dghex_set_state(s.ctx, g0, None)
+    ref = prob.run(dt=s.dt, p0=p0, batch=1)
+    for prec, tol, B in ((0, FP64_TOL, 1), (0, FP64_TOL, 4), (1, FP32_TOL, 1), (1, FP32_TOL, 8)):
+        tr = s.run(precision=prec, batch=B)
+        for b in range(B):
+            assert _rel(tr[b], ref[0]) < tol, (order, prec, B, _rel(tr[b], ref[0]))
+    s.close()
+
+
+def test_stability_check_matches_the_largest_eigenvalue(lib, two_dom):
+    """Device power iteration for lambda_max(M^-1 K) against the oracle's
+    generalised eigenvalue, and the explicit-scheme limit it enforces."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import eigsh
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w, prob = two_dom
+    Mh = sp.diags(1.0 / np.sqrt(prob.M))
+    lam_ref = eigsh(Mh @ prob.K @ Mh, k=1, which="LA", return_eigenvectors=False)[0]
+    s = dghex.HexSolver(w)
+    code, lam = dghex.dghex_check_stability(s.ctx, 400)
+    assert code == 0
+    assert abs(lam / lam_ref - 1.0) < 2e-2, (lam, lam_ref)
+    assert s.dt < 0.95 * 2.0 / np.sqrt(lam_ref)
+    s.close()
+    big = dghex.HexSolver(w, dt=1.2 * 2.0 / np.sqrt(lam_ref))
+    code, lam2 = dghex.dghex_check_stability(big.ctx, 400)
+    assert code == dgsem.DGSEM_EUNSTABLE and abs(lam2 / lam_ref - 1.0) < 2e-2
+    big.close()
