@@ -31,7 +31,10 @@ are the extra ones for curved elements):
     (h_min,K / 2 * min GLL gap(N_K)) / c_max (the box reading for boxes);
   * the PMUT face weights W_j = sum_F w_a w_b |J_F| at the face's GLL nodes;
   * a receiver lies in the lowest-id element (primary first) whose Newton
-    reference position is inside [-1, 1]^3 up to 1e-10.
+    reference position is inside [-1, 1]^3 up to 1e-10;
+  * absorbing faces: C_jj = sum_F c w_a w_b |J_F| at the face's GLL nodes
+    (the box reading with the Nanson surface Jacobian), dt at most
+    1 / max_j C_jj / M_jj.
 Node numbering: nodes of one domain at the same physical position (within
 1e-9 of the domain size) are one node, numbered in order of first appearance
 over the elements (element order, then local index a + (N+1) b + (N+1)^2 c).
@@ -318,7 +321,7 @@ class HexOracleProblem(OracleProblem):
                 alpha, nq, workload.normal_tol)
             self.K = (self.K + KI).tocsr()
         self.Minv = 1.0 / self.M
-        self.C = np.zeros(self.nh)
+        self._absorbing_matrix()
         self.pml = None
         self._pmut_matrix()
 
@@ -336,6 +339,23 @@ class HexOracleProblem(OracleProblem):
         self.K = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                shape=(self.nh, self.nh)).tocsr()
         self.M = M
+
+    def _absorbing_matrix(self):
+        """Diagonal C of the damping form d of eq. (Wf_4) on the absorbing
+        faces: C_jj = sum_F c w_a w_b |J_F| at the face's GLL nodes (the
+        collocation of the box oracle, with the Nanson surface Jacobian)."""
+        C = np.zeros(self.nh)
+        faces = getattr(self.w, "absorbing_faces", None)
+        if faces:
+            for m, fl in zip(self.meshes, faces):
+                if fl is None:
+                    continue
+                for e, f in np.asarray(fl).reshape(-1, 2):
+                    sel, a, b = m.face_local_nodes(int(f))
+                    _, J = trilinear(m.elem_verts(int(e)), m.ref_nodes[sel])
+                    _, dS = face_normal_and_jac(J, int(f))
+                    np.add.at(C, m.conn[int(e), sel], m.c * m.w[a] * m.w[b] * dS)
+        self.C = C
 
     def pmut_face_nodes(self):
         """Unique node ids on the PMUT faces, their positions and the
@@ -396,11 +416,18 @@ class HexOracleProblem(OracleProblem):
                              shape=(len(points), self.nh)).tocsr()
 
     def stable_dt(self, cfl: Optional[float] = None):
+        """CFL on the shortest element edge (reading R24), and with absorbing
+        faces at most 1 / max_j (C_jj / M_jj) like the box oracle (the damping
+        of Algorithm 1 is explicit)."""
         cfl = self.w.cfl if cfl is None else cfl
         cmax = max(m.c for m in self.meshes)
         hmin = min(min(m.h_min(e) for e in range(m.ne)) / 2.0 * float(np.min(np.diff(m.xi)))
                    for m in self.meshes)
-        return cfl * hmin / cmax
+        dt = cfl * hmin / cmax
+        sigma = float(np.max(self.C * self.Minv))
+        if sigma > 0.0:
+            dt = min(dt, 1.0 / sigma)
+        return dt
 
     def all_coordinates(self):
         X = np.concatenate([m.coords for m in self.meshes])

@@ -231,3 +231,36 @@ def test_unmatched_interface_node_is_an_error():
     with pytest.raises(ValueError):
         HO.HexOracleProblem(w2)
     HO.HexOracleProblem(w)
+
+
+def test_absorbing_faces_on_the_affine_box_are_the_box_oracles():
+    """Absorbing sides given as face lists of the affine lattice give the box
+    oracle's C (and its damping-limited dt)."""
+    wb = W.small_one_domain(nel=(3, 2, 2), order=4, nsteps=5)
+    wb.domains[0].absorbing = (1, 0, 0, 1, 0, 1)
+    wh = H.hex_workload_from_box(wb)
+    lat = wh.domains[0].lattice
+    wh.absorbing_faces = [np.concatenate([H.lattice_side_faces(lat, s) for s in (0, 3, 5)])]
+    pb, ph = O.OracleProblem(wb), HO.HexOracleProblem(wh)
+    idx = _map_nodes(pb, ph, 1e-15)
+    np.testing.assert_allclose(ph.C[idx], pb.C, rtol=1e-13, atol=1e-30)
+    assert abs(ph.stable_dt() - pb.stable_dt()) < 1e-15 * pb.stable_dt()
+
+
+def test_absorbing_faces_dissipate_on_a_curved_mesh():
+    """With absorbing faces (curved mesh) the leapfrog energy of the free
+    acoustic field decreases monotonically and C sums to c times the
+    absorbing area."""
+    w = H.distorted_one_domain(nel=(3, 2, 2), order=4, nsteps=60)
+    w.pmuts = None
+    lat = w.domains[0].lattice
+    w.absorbing_faces = [np.concatenate([H.lattice_side_faces(lat, s) for s in (1, 5)])]
+    p = HO.HexOracleProblem(w)
+    ext = w.box_extent
+    area = ext[1] * ext[2] + ext[0] * ext[1]          # x+ and z+ walls (planar)
+    assert abs(p.C.sum() - p.meshes[0].c * area) < 1e-12 * p.meshes[0].c * area
+    X = _coords(p)
+    p0 = W.seeded_field(4, X[:, 0], X[:, 1], X[:, 2])
+    _, e = p.run(nsteps=80, p0=p0, energy=True, receivers=w.receivers[:1])
+    lf = e[:, 0, 0]
+    assert np.all(np.diff(lf) <= 1e-12 * lf[0]) and lf[-1] < 0.999 * lf[0]

@@ -49,6 +49,8 @@ class HexWorkload(Workload):
     fine_faces: Optional[np.ndarray] = None     # [nf, 2] (element, local face) of domain 0 on Gamma_I
     coarse_faces: Optional[np.ndarray] = None   # [nc, 2] of domain 1 on Gamma_I
     pmut_faces: Optional[np.ndarray] = None     # [np, 2] of domain 0 on Gamma_PMUT
+    # first-order absorbing faces (Gamma_ABC) per domain: [n, 2] (element, local face) or None
+    absorbing_faces: Optional[list] = None
     normal_tol: float = 0.5                     # Algorithm 3 |n+ + n-| < tol
     box_extent: Optional[tuple] = None          # the box the mesh fills (for receivers)
 
@@ -253,6 +255,22 @@ def distorted_one_domain(nel=(3, 3, 2), order=4, h=50e-6, amp=0.15, seed=41, nst
     a = a * rng.uniform(0.5, 1.5, size=a.shape)
     return HexWorkload("distorted_one_domain", [dom], nsteps, rec, pm, batch=batch, drive_delay=d, drive_amp=a,
                        pmut_faces=pmutf, box_extent=ext)
+
+
+def lattice_side_faces(lattice, side: int) -> np.ndarray:
+    """(element, local face) of every element face on one side of a
+    structured lattice (x-, x+, y-, y+, z-, z+ = 0..5), elements in lattice
+    order, before any re-listing of element frames."""
+    nx, ny, nz = lattice
+    ax, hi = side // 2, side % 2
+    out = []
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                ijk = (i, j, k)
+                if ijk[ax] == (lattice[ax] - 1 if hi else 0):
+                    out.append([_eid(i, j, k, nx, ny), side])
+    return np.array(out, dtype=np.int64).reshape(-1, 2)
 
 
 def hex_from_box(domain, offset_vertices=0) -> HexDomain:
