@@ -123,6 +123,29 @@ int dghex_pmut_set(dghex_ctx* ctx, int n_pmut, int n_modes, const int* foot_ptr,
                    const double* shape_un, const double* freq_hz, const double* damping, const double* eta,
                    const double* modal_mass);
 
+/* First-order absorbing faces (Gamma_ABC) of one domain (eq. Wf_4): the
+ * damping form d(w, v) = sum_F int_F c w v, collocated at the faces' GLL
+ * nodes with the Nanson surface Jacobian (C diagonal), acting on the
+ * predicted velocity as in Algorithm 1.  faces [n][2] (element, local face)
+ * must be boundary faces of that domain and not on Gamma_I or Gamma_PMUT;
+ * n = 0 removes the domain's absorbing faces.  dt is held to
+ * min(cfl dt, 1 / max_j C_jj / M_jj); a dt fixed at creation above that
+ * bound is refused (DGSEM_EUNSTABLE).  The state restarts from rest. */
+int dghex_set_absorbing_faces(dghex_ctx* ctx, int domain, int n, const int* faces);
+
+/* TX -> RX switch and the voltage record, as pmut_set_receive and
+ * dgsem_get_voltages in dgsem.h (steps counted since rest or the last
+ * dghex_set_state; DGSEM_RUN_CONTINUE and checkpoints keep counting). */
+int dghex_pmut_set_receive(dghex_ctx* ctx, long long n_switch, const double* capacitance, int sign);
+int dghex_get_voltages(const dghex_ctx* ctx, double* out, size_t n);
+
+/* Checkpoint of the time-stepping state (pressure, half-step velocity,
+ * PMUT forcing rows, q, q', q'', step count, precision, batch), as
+ * dgsem_state_save / dgsem_state_load.  A loaded state is continued by the
+ * next dghex_run with DGSEM_RUN_CONTINUE. */
+int dghex_state_save(const dghex_ctx* ctx, void* buf, size_t* len);
+int dghex_state_load(dghex_ctx* ctx, const void* buf, size_t len);
+
 /* Algorithm 3 result: for every fine face (list order) and every Gauss node
  * (s fastest, s and t the face's two other reference axes in increasing
  * order), the index of the matched coarse face in coarse_faces and the
@@ -137,7 +160,8 @@ int dghex_run(dghex_ctx* ctx, int precision, int batch, int nsteps, const double
               const double* recv_xyz, double* traces, int flags, void* stream);
 
 /* Initial state p^0, p'^0 ([ndof] FP64 host, node order above; NULL = 0)
- * for the next run without DGSEM_RUN_CONTINUE: p''^0 = M^-1 (-K p^0). */
+ * for the next run without DGSEM_RUN_CONTINUE: p''^0 = M^-1 (-K p^0 - C p'^0)
+ * (C: absorbing faces). */
 int dghex_set_state(dghex_ctx* ctx, const double* p0, const double* v0);
 
 /* Pressure p^n of every batch member after the last run, [batch][ndof]. */

@@ -223,6 +223,19 @@ struct dghex_ctx {
   long long ndof = 0, nvol = 0;
   std::vector<double> xyz;
   double dt = 0.0;
+  double dt_cfl = 0.0;                      // dt before the absorbing-face limit
+  bool dt_fixed = false;                    // dt given by the caller
+  std::vector<std::map<std::array<int, 4>, int>> fcount;   // element faces per domain (boundary test)
+  std::vector<double> Mh;                   // lumped mass (host copy)
+  // absorbing faces per domain, and C_jj / M_jj on the device (NULL: none)
+  std::vector<int> abs_faces[2];
+  double* d_damp64 = nullptr; float* d_damp32 = nullptr;
+  // TX -> RX switch of the PMUT array (off: rx_switch < 0)
+  long long rx_switch = -1;
+  double* d_rx_gain = nullptr;
+  long long* d_step_base = nullptr;        // steps done before the current run
+  long long steps_done = 0;                 // steps since rest or the last set state
+  double* d_volt = nullptr; size_t volt_cap = 0; long long volt_n = 0;
   // interface (Algorithm 3)
   int q = 0, nff = 0, ncf = 0;
   std::vector<int> ff, cf, match;
@@ -243,6 +256,7 @@ struct dghex_ctx {
   int K = 0, M = 0, nnz = 0;
   long long fslot0 = 0;
   std::vector<long long> ent_node;
+  std::vector<int> pmut_faces;
   int* d_fp_ptr = nullptr; long long* d_fp_off = nullptr; double* d_Bm = nullptr; int* d_ent_k = nullptr;
   double* d_modal = nullptr;
   double kappa = 0.0;
@@ -253,7 +267,9 @@ struct dghex_ctx {
   // run state: fields batch-innermost, row length Bp (the batch padded to a
   // multiple of the 32-byte vector width when it is at least that wide)
   int prec = -1, batch = 0, Bp = 0;
-  void* P = nullptr; void* V = nullptr; void* S = nullptr;
+  // X = p^n, Y = p^{n+1}, V = v^{n+1/2} (two-vector form of Algorithm 1;
+  // X and Y swap every step)
+  void* X = nullptr; void* Y = nullptr; void* V = nullptr; void* S = nullptr;
   long long* d_fp_offB = nullptr;          // footprint node offsets j * Bp for the PMUT kernel
   double* q_state = nullptr;
   bool state_valid = false;
@@ -306,7 +322,7 @@ void collect_timings(dghex_ctx* c) {
 }
 
 void free_run_state(dghex_ctx* c) {
-  dfree(c->P); dfree(c->V); dfree(c->S); dfree(c->q_state); dfree(c->d_fp_offB);
+  dfree(c->X); dfree(c->Y); dfree(c->V); dfree(c->S); dfree(c->q_state); dfree(c->d_fp_offB);
   c->prec = -1;
   c->batch = 0;
   c->Bp = 0;
@@ -314,13 +330,14 @@ void free_run_state(dghex_ctx* c) {
 }
 
 int ensure_run_state(dghex_ctx* c, int prec, int batch) {
-  if (c->prec == prec && c->batch == batch && c->P) return DGSEM_OK;
+  if (c->prec == prec && c->batch == batch && c->X) return DGSEM_OK;
   free_run_state(c);
   const size_t es = prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
   const int vw = (int)(32 / es);
   const int Bp = batch < vw ? batch : (batch + vw - 1) / vw * vw;
   int rc;
-  if ((rc = dmalloc(&c->P, es * Bp * c->ndof)) || (rc = dmalloc(&c->V, es * Bp * c->ndof)) ||
+  if ((rc = dmalloc(&c->X, es * Bp * c->ndof)) || (rc = dmalloc(&c->Y, es * Bp * c->ndof)) ||
+      (rc = dmalloc(&c->V, es * Bp * c->ndof)) ||
       (rc = dmalloc(&c->S, es * Bp * c->nslot)))
     return rc;
   if (c->K > 0) {
@@ -571,9 +588,10 @@ int setup_receivers(dghex_ctx* c, int R, const double* xyz) {
   return DGSEM_OK;
 }
 
+// element stiffness and interface terms of the pressure field p
 template <typename T>
-int launch_residual(dghex_ctx* c, cudaStream_t s) {
-  const T* p = static_cast<const T*>(c->P);
+int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
+  const T* p = static_cast<const T*>(pfield);
   T* S = static_cast<T*>(c->S);
   for (int d = 0; d < c->nd; ++d) {
     const HexDom& D = c->dom[d];
@@ -615,19 +633,51 @@ int launch_residual(dghex_ctx* c, cudaStream_t s) {
 }
 
 template <typename T>
-int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp) {
+int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void* p_in, void* p_out) {
   hex::HexUpdateArgs<T> a;
   std::memset(&a, 0, sizeof(a));
-  a.p = static_cast<T*>(c->P); a.v = static_cast<T*>(c->V); a.S = static_cast<const T*>(c->S);
+  a.p_in = static_cast<const T*>(p_in); a.p_out = static_cast<T*>(p_out);
+  a.v = static_cast<T*>(c->V); a.S = static_cast<const T*>(c->S);
   a.Bp = c->Bp;
   a.node_ptr = c->d_node_ptr; a.node_slot = c->d_node_slot;
   a.Minv = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_Minv32) : reinterpret_cast<const T*>(c->d_Minv64);
+  a.damp = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_damp32) : reinterpret_cast<const T*>(c->d_damp64);
   a.ndof = c->ndof; a.cv = T(cv); a.cp = T(cp);
   HexTimer t(c, s, DGHEX_K_UPDATE);
   HCUDA(hex::launch_hex_update<T>(a, s));
   return DGSEM_OK;
 }
 
+// PMUT forcing rows kappa sum_m q''_km B_jm (R = 0) or receivers of Y and the
+// step counter (forcing = false)
+template <typename T>
+int launch_tail(dghex_ctx* c, cudaStream_t s, bool forcing, int R, double* traces, long long tbs, long long trs) {
+  hex::HexTailArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.M = c->M; a.K = c->K; a.B = c->batch; a.Bp = c->Bp;
+  a.S = static_cast<T*>(c->S); a.fslot = c->fslot0;
+  if (forcing) {
+    a.nnz = c->nnz;
+    a.ent_k = c->d_ent_k; a.Bm = c->d_Bm;
+    a.qdd = c->q_state + 2 * (long long)c->batch * c->K * c->M;
+    a.kappa = c->kappa;
+    a.fblocks = (int)(((long long)c->nnz * c->batch + 255) / 256);
+    if (a.fblocks == 0) return DGSEM_OK;
+  } else {
+    a.R = R; a.rstride = c->rstride; a.rw = c->d_rw; a.roff = c->d_roff; a.rnn = c->d_rnn;
+    a.p = static_cast<const T*>(c->Y);
+    a.traces = traces; a.tbs = tbs; a.trs = trs;
+    a.n = 0; a.step = c->d_step; a.done = c->d_done;
+  }
+  HexTimer t(c, s, DGHEX_K_TAIL);
+  HCUDA(hex::launch_hex_tail<T>(a, s));
+  return DGSEM_OK;
+}
+
+// One step of Algorithm 1: PMUT (p^n, drive of step n) -> q''^{n+1}; forcing
+// rows of q''^{n+1}; K p^{n+1}; v^{n+3/2} = v^{n+1/2} + dt M^-1 (f - K p^{n+1}
+// - C v^{n+1/2}), p^{n+2} = p^{n+1} + dt v^{n+3/2} into X; receivers of
+// p^{n+1}; swap.
 template <typename T>
 int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs, long long dks, int R, double* traces,
                 long long tbs, long long trs) {
@@ -636,33 +686,26 @@ int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs
     std::memset(&a, 0, sizeof(a));
     a.B = c->batch; a.K = c->K; a.M = c->M;
     a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_offB; a.Bm = c->d_Bm;
-    a.p_prev = static_cast<const T*>(c->P);
+    a.p_prev = static_cast<const T*>(c->X);
     a.bsp = 1;
     const long long kmB = (long long)c->batch * c->K * c->M;
     a.q = c->q_state; a.qd = c->q_state + kmB; a.qdd = c->q_state + 2 * kmB;
     const long long km = (long long)c->K * c->M;
     a.omega2 = c->d_modal; a.twozw = c->d_modal + km; a.inv_mu = c->d_modal + 2 * km; a.eta = c->d_modal + 3 * km;
     a.drive = drive; a.dbs = dbs; a.dks = dks; a.n = 0; a.step = c->d_step; a.dt = c->dt;
+    if (c->rx_switch >= 0) {
+      a.rx_gain = c->d_rx_gain; a.rx_switch = c->rx_switch; a.step_base = c->d_step_base;
+      a.volt = c->d_volt; a.vbs = (long long)c->K * dks; a.vks = dks;
+    }
     HexTimer t(c, s, DGHEX_K_PMUT);
     HCUDA(launch_pmut_recv<T>(a, s));
   }
-  int rc = launch_residual<T>(c, s);
-  if (rc) return rc;
-  if ((rc = launch_update<T>(c, s, -c->dt, c->dt))) return rc;
-  hex::HexTailArgs<T> a;
-  std::memset(&a, 0, sizeof(a));
-  a.nnz = c->nnz; a.M = c->M; a.K = c->K; a.B = c->batch; a.Bp = c->Bp;
-  a.ent_k = c->d_ent_k; a.Bm = c->d_Bm;
-  a.qdd = c->q_state ? c->q_state + 2 * (long long)c->batch * c->K * c->M : nullptr;
-  a.kappa = c->kappa;
-  a.S = static_cast<T*>(c->S); a.fslot = c->fslot0;
-  a.R = R; a.rstride = c->rstride; a.rw = c->d_rw; a.roff = c->d_roff; a.rnn = c->d_rnn;
-  a.p = static_cast<const T*>(c->P);
-  a.traces = traces; a.tbs = tbs; a.trs = trs;
-  a.n = 0; a.step = c->d_step; a.done = c->d_done;
-  a.fblocks = (int)(((long long)c->nnz * c->batch + 255) / 256);
-  HexTimer t(c, s, DGHEX_K_TAIL);
-  HCUDA(hex::launch_hex_tail<T>(a, s));
+  int rc;
+  if (c->K > 0 && (rc = launch_tail<T>(c, s, true, 0, nullptr, 0, 0))) return rc;
+  if ((rc = launch_residual<T>(c, s, c->Y))) return rc;
+  if ((rc = launch_update<T>(c, s, -c->dt, c->dt, c->Y, c->X))) return rc;
+  if ((rc = launch_tail<T>(c, s, false, R, traces, tbs, trs))) return rc;
+  std::swap(c->X, c->Y);
   return DGSEM_OK;
 }
 
@@ -681,17 +724,33 @@ template <typename T>
 int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* traces_out, int flags, cudaStream_t s) {
   const bool fresh = !(flags & DGSEM_RUN_CONTINUE) || !c->state_valid;
   const size_t es = sizeof(T);
+  if (fresh) c->steps_done = 0;
+  HCUDA(cudaMemcpyAsync(c->d_step_base, &c->steps_done, sizeof(long long), cudaMemcpyHostToDevice, s));
+  c->volt_n = 0;
+  if (c->rx_switch >= 0 && c->K > 0) {
+    const size_t nv = (size_t)c->batch * c->K * nsteps;
+    if (nv > c->volt_cap) {
+      dfree(c->d_volt);
+      int rc = dmalloc(&c->d_volt, nv * sizeof(double));
+      if (rc) return rc;
+      c->volt_cap = nv;
+    }
+    c->volt_n = (long long)nv;
+  }
   if (fresh) {
-    HCUDA(cudaMemsetAsync(c->P, 0, es * c->Bp * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->X, 0, es * c->Bp * c->ndof, s));
+    HCUDA(cudaMemsetAsync(c->Y, 0, es * c->Bp * c->ndof, s));
     HCUDA(cudaMemsetAsync(c->V, 0, es * c->Bp * c->ndof, s));
     HCUDA(cudaMemsetAsync(c->S, 0, es * c->Bp * c->nslot, s));
     if (c->q_state) HCUDA(cudaMemsetAsync(c->q_state, 0, sizeof(double) * 3 * (size_t)c->batch * c->K * c->M, s));
     if (c->has_init) {
       int rc;
-      if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->P, c->batch, c->Bp, c->ndof, s))) return rc;
+      if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->X, c->batch, c->Bp, c->ndof, s))) return rc;
       if (!c->init_v.empty() && (rc = upload_field<T>(c->init_v, c->V, c->batch, c->Bp, c->ndof, s))) return rc;
-      // v^{-1/2} = p'^0 - dt/2 p''^0 with p''^0 = -M^-1 K p^0 (the forcing slots are zero at rest)
-      if ((rc = launch_residual<T>(c, s)) || (rc = launch_update<T>(c, s, 0.5 * c->dt, 0.0))) return rc;
+      // v^{1/2} = p'^0 + dt/2 p''^0 with p''^0 = M^-1 (-K p^0 - C p'^0) (no forcing at rest),
+      // p^1 = p^0 + dt v^{1/2}
+      if ((rc = launch_residual<T>(c, s, c->X)) || (rc = launch_update<T>(c, s, -0.5 * c->dt, c->dt, c->X, c->Y)))
+        return rc;
     }
   }
   const double* d_drive = drive;
@@ -735,6 +794,7 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
   if (c->profiling) collect_timings(c);
   else c->ev_used.clear();
   c->state_valid = true;
+  c->steps_done += nsteps;
   return DGSEM_OK;
 }
 
@@ -776,7 +836,8 @@ int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
   dghex_ctx* c = new dghex_ctx();
   cudaGetDevice(&c->device);
   c->nd = d->ndomains;
-  std::vector<std::map<std::array<int, 4>, int>> fcount(c->nd);
+  c->fcount.assign(c->nd, {});
+  auto& fcount = c->fcount;
   long long node0 = 0, vslot = 0;
   for (int k = 0; k < c->nd; ++k) {
     const dghex_domain_desc& S = d->domains[k];
@@ -882,12 +943,15 @@ int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
     }
     cmax = std::max(cmax, D.c);
   }
-  c->dt = d->dt > 0.0 ? d->dt : d->cfl * hmin_t / cmax;
+  c->dt_cfl = d->dt > 0.0 ? d->dt : d->cfl * hmin_t / cmax;
+  c->dt_fixed = d->dt > 0.0;
+  c->dt = c->dt_cfl;
   if (c->nd == 2 && (rc = setup_interface(c, d))) {
     dghex_destroy(c);
     return rc;
   }
   std::vector<int> pf(d->pmut_faces, d->pmut_faces + 2 * (size_t)std::max(0, d->n_pmut_faces));
+  c->pmut_faces = pf;
   setup_pmut_nodes(c, pf);
   if ((rc = build_slots(c)) || (rc = dmalloc(&c->d_M, sizeof(double) * c->ndof)) ||
       (rc = dmalloc(&c->d_Minv64, sizeof(double) * c->ndof)) || (rc = dmalloc(&c->d_Minv32, sizeof(float) * c->ndof)) ||
@@ -898,6 +962,11 @@ int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
   cudaError_t e = hex::launch_mass(c->d_Mloc, c->d_node_ptr, c->d_node_slot, c->nvol, c->ndof, c->d_Minv64, c->d_Minv32,
                                    c->d_M, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) {
+    c->Mh.resize((size_t)c->ndof);
+    e = cudaMemcpy(c->Mh.data(), c->d_M, sizeof(double) * c->ndof, cudaMemcpyDeviceToHost);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&c->d_step_base), sizeof(long long));
   if (e != cudaSuccess) {
     dghex_destroy(c);
     return hfail(DGSEM_ECUDA, "mass kernel: %s", cudaGetErrorString(e));
@@ -1019,13 +1088,188 @@ int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
   std::vector<double> t(nb);
   if (c->prec == DGSEM_FP32_MIXED) {
     std::vector<float> f(nb);
-    HCUDA(cudaMemcpy(f.data(), c->P, nb * sizeof(float), cudaMemcpyDeviceToHost));
+    HCUDA(cudaMemcpy(f.data(), c->X, nb * sizeof(float), cudaMemcpyDeviceToHost));
     std::copy(f.begin(), f.end(), t.begin());
   } else {
-    HCUDA(cudaMemcpy(t.data(), c->P, nb * sizeof(double), cudaMemcpyDeviceToHost));
+    HCUDA(cudaMemcpy(t.data(), c->X, nb * sizeof(double), cudaMemcpyDeviceToHost));
   }
   for (int b = 0; b < c->batch; ++b)
     for (long long j = 0; j < c->ndof; ++j) p[(size_t)b * c->ndof + j] = t[(size_t)j * c->Bp + b];
+  return DGSEM_OK;
+}
+
+namespace {
+// C_jj / M_jj of every domain's absorbing faces (Nanson-weighted GLL
+// collocation of the damping form of eq. Wf_4), uploaded in both precisions;
+// dt held to 1 / max of it.
+int apply_absorbing(dghex_ctx* c) {
+  dfree(c->d_damp64);
+  dfree(c->d_damp32);
+  std::vector<double> C((size_t)c->ndof, 0.0);
+  bool any = false;
+  for (int d = 0; d < c->nd; ++d) {
+    const HexDom& D = c->dom[d];
+    const auto& fl = c->abs_faces[d];
+    for (size_t k = 0; k < fl.size() / 2; ++k) {
+      const int e = fl[2 * k], f = fl[2 * k + 1];
+      double V[24];
+      elem_verts(D, e, V);
+      const int ax = f >> 1, fixed = (f & 1) ? D.N : 0;
+      const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+      for (int i = 0; i < D.nl; ++i) {
+        const int l[3] = {i % D.n, (i / D.n) % D.n, i / (D.n * D.n)};
+        if (l[ax] != fixed) continue;
+        const double r[3] = {D.basis->x[l[0]], D.basis->x[l[1]], D.basis->x[l[2]]};
+        double x[3], J[3][3], nrm[3];
+        hex::tri_map(V, r, x, J);
+        const double dS = hex::face_normal(f, J, nrm);
+        C[D.conn[(size_t)e * D.nl + i]] += D.c * D.basis->w[l[t0]] * D.basis->w[l[t1]] * dS;
+        any = true;
+      }
+    }
+  }
+  c->dt = c->dt_cfl;
+  c->state_valid = false;
+  if (!any) return DGSEM_OK;
+  double smax = 0.0;
+  std::vector<float> s32((size_t)c->ndof);
+  for (long long j = 0; j < c->ndof; ++j) {
+    C[j] /= c->Mh[j];
+    smax = std::max(smax, C[j]);
+    s32[j] = (float)C[j];
+  }
+  if (c->dt_fixed && c->dt > 1.0 / smax)
+    return hfail(DGSEM_EUNSTABLE, "dt %.4g above the absorbing-face limit 1 / max C/M = %.4g", c->dt, 1.0 / smax);
+  if (!c->dt_fixed) c->dt = std::min(c->dt, 1.0 / smax);
+  int rc;
+  if ((rc = upload(&c->d_damp64, C)) || (rc = upload(&c->d_damp32, s32))) return rc;
+  return DGSEM_OK;
+}
+
+bool face_in(const std::vector<int>& list, int e, int f) {
+  for (size_t k = 0; k < list.size() / 2; ++k)
+    if (list[2 * k] == e && list[2 * k + 1] == f) return true;
+  return false;
+}
+
+struct HexCkpt {
+  char magic[8];
+  int prec, batch, Bp, K, M, nnz;
+  long long ndof, steps;
+};
+}  // namespace
+
+int dghex_set_absorbing_faces(dghex_ctx* c, int domain, int n, const int* faces) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (domain < 0 || domain >= c->nd) return hfail(DGSEM_EINVAL, "domain %d out of range", domain);
+  if (n < 0 || (n > 0 && !faces)) return hfail(DGSEM_EINVAL, "bad face list");
+  const HexDom& D = c->dom[domain];
+  std::vector<int> fl(faces, faces + 2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const int e = fl[2 * i], f = fl[2 * i + 1];
+    if (e < 0 || e >= D.ne || f < 0 || f > 5) return hfail(DGSEM_EINVAL, "face entry %d out of range", i);
+    std::array<int, 4> key;
+    int k = 0;
+    for (int cc = 0; cc < 8; ++cc)
+      if (((cc >> (f >> 1)) & 1) == (f & 1)) key[k++] = D.elem[(size_t)e * 8 + cc];
+    std::sort(key.begin(), key.end());
+    auto it = c->fcount[domain].find(key);
+    if (it == c->fcount[domain].end() || it->second != 1) return hfail(DGSEM_EINVAL, "face entry %d is not a boundary face", i);
+    if ((domain == 0 && (face_in(c->ff, e, f) || face_in(c->pmut_faces, e, f))) || (domain == 1 && face_in(c->cf, e, f)))
+      return hfail(DGSEM_EINVAL, "face entry %d lies on the interface or on Gamma_PMUT", i);
+  }
+  c->abs_faces[domain] = fl;
+  return apply_absorbing(c);
+}
+
+int dghex_pmut_set_receive(dghex_ctx* c, long long n_switch, const double* capacitance, int sign) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (n_switch < 0) {
+    c->rx_switch = -1;
+    return DGSEM_OK;
+  }
+  if (c->K == 0) return hfail(DGSEM_ESTATE, "no PMUT array: call dghex_pmut_set first");
+  if (!capacitance) return hfail(DGSEM_EINVAL, "NULL capacitance");
+  if (sign != 1 && sign != -1) return hfail(DGSEM_EINVAL, "sign must be +1 or -1");
+  std::vector<double> gain(c->K);
+  for (int k = 0; k < c->K; ++k) {
+    if (!(capacitance[k] > 0.0) || !std::isfinite(capacitance[k]))
+      return hfail(DGSEM_EINVAL, "capacitance[%d] must be > 0", k);
+    gain[k] = sign / capacitance[k];
+  }
+  dfree(c->d_rx_gain);
+  int rc = upload(&c->d_rx_gain, gain);
+  if (rc) {
+    c->rx_switch = -1;
+    return rc;
+  }
+  c->rx_switch = n_switch;
+  return DGSEM_OK;
+}
+
+int dghex_get_voltages(const dghex_ctx* c, double* out, size_t n) {
+  if (!c || !out) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (c->volt_n == 0 || !c->d_volt) return hfail(DGSEM_ESTATE, "no voltage record: configure dghex_pmut_set_receive and run");
+  if (n < (size_t)c->volt_n) return hfail(DGSEM_EINVAL, "buffer of %zu doubles is smaller than %lld", n, c->volt_n);
+  HCUDA(cudaMemcpy(out, c->d_volt, (size_t)c->volt_n * sizeof(double), cudaMemcpyDeviceToHost));
+  return DGSEM_OK;
+}
+
+int dghex_state_save(const dghex_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (!c->state_valid) return hfail(DGSEM_ESTATE, "no state to save");
+  const size_t es = c->prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
+  const size_t field = (size_t)c->Bp * c->ndof * es;
+  const size_t qb = (size_t)3 * c->batch * c->K * c->M * sizeof(double);
+  const size_t need = sizeof(HexCkpt) + 3 * field + qb;
+  if (!buf) {
+    *len = need;
+    return DGSEM_OK;
+  }
+  if (*len < need) return hfail(DGSEM_EINVAL, "buffer too small (%zu < %zu)", *len, need);
+  HCUDA(cudaDeviceSynchronize());
+  HexCkpt h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "DGHEXCK2", 8);
+  h.prec = c->prec; h.batch = c->batch; h.Bp = c->Bp; h.K = c->K; h.M = c->M; h.nnz = c->nnz;
+  h.ndof = c->ndof; h.steps = c->steps_done;
+  unsigned char* o = static_cast<unsigned char*>(buf);
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  for (const void* src : {c->X, c->Y, c->V}) {
+    HCUDA(cudaMemcpy(o, src, field, cudaMemcpyDeviceToHost));
+    o += field;
+  }
+  if (qb) HCUDA(cudaMemcpy(o, c->q_state, qb, cudaMemcpyDeviceToHost));
+  *len = need;
+  return DGSEM_OK;
+}
+
+int dghex_state_load(dghex_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (len < sizeof(HexCkpt)) return hfail(DGSEM_EINVAL, "buffer too small");
+  HexCkpt h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, "DGHEXCK2", 8) != 0) return hfail(DGSEM_EINVAL, "not a checkpoint of this library");
+  if (h.ndof != c->ndof || h.K != c->K || h.M != c->M || h.nnz != c->nnz)
+    return hfail(DGSEM_EINVAL, "checkpoint of another mesh or PMUT array");
+  if (h.prec != DGSEM_FP64 && h.prec != DGSEM_FP32_MIXED) return hfail(DGSEM_EINVAL, "bad precision in checkpoint");
+  int rc = ensure_run_state(c, h.prec, h.batch);
+  if (rc) return rc;
+  if (c->Bp != h.Bp) return hfail(DGSEM_EINVAL, "checkpoint batch layout differs");
+  const size_t es = c->prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
+  const size_t field = (size_t)c->Bp * c->ndof * es;
+  const size_t qb = (size_t)3 * c->batch * c->K * c->M * sizeof(double);
+  if (len < sizeof(HexCkpt) + 3 * field + qb) return hfail(DGSEM_EINVAL, "truncated checkpoint");
+  const unsigned char* o = static_cast<const unsigned char*>(buf) + sizeof(HexCkpt);
+  HCUDA(cudaMemset(c->S, 0, (size_t)c->Bp * c->nslot * es));
+  for (void* dst : {c->X, c->Y, c->V}) {
+    HCUDA(cudaMemcpy(dst, o, field, cudaMemcpyHostToDevice));
+    o += field;
+  }
+  if (qb) HCUDA(cudaMemcpy(c->q_state, o, qb, cudaMemcpyHostToDevice));
+  c->steps_done = h.steps;
+  c->state_valid = true;
   return DGSEM_OK;
 }
 
@@ -1034,7 +1278,7 @@ int dghex_check_stability(dghex_ctx* c, int iters, double* lambda_max) {
   int rc = ensure_run_state(c, DGSEM_FP64, 1);
   if (rc) return rc;
   c->state_valid = false;
-  double* P = static_cast<double*>(c->P);
+  double* P = static_cast<double*>(c->Y);
   double* V = static_cast<double*>(c->V);
   double* d_n2 = nullptr;
   if ((rc = dmalloc(&d_n2, 2 * sizeof(double)))) return rc;
@@ -1053,7 +1297,7 @@ int dghex_check_stability(dghex_ctx* c, int iters, double* lambda_max) {
     // v = M^-1 K x through the step's own kernels (zero forcing slots, v = 0 first)
     e = cudaMemsetAsync(V, 0, sizeof(double) * c->ndof, s);
     if (e != cudaSuccess) break;
-    if ((rc = launch_residual<double>(c, s)) || (rc = launch_update<double>(c, s, 1.0, 0.0))) break;
+    if ((rc = launch_residual<double>(c, s, P)) || (rc = launch_update<double>(c, s, 1.0, 0.0, P, P))) break;
     if ((e = hex::launch_norm2(P, c->ndof, d_n2, s)) != cudaSuccess) break;
     if ((e = hex::launch_norm2(V, c->ndof, d_n2 + 1, s)) != cudaSuccess) break;
     double n2[2];
@@ -1111,6 +1355,7 @@ void dghex_destroy(dghex_ctx* c) {
   dfree(c->d_node_ptr); dfree(c->d_node_slot);
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);
   dfree(c->d_step); dfree(c->d_done);
+  dfree(c->d_damp64); dfree(c->d_damp32); dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rnn);
   dfree(c->d_drive); dfree(c->d_traces);
   for (auto ev : c->ev_pool) cudaEventDestroy(ev);

@@ -218,13 +218,14 @@ struct HexIfaceArgs {
 };
 
 // Step: residual assembly (sum of a node's slots in ascending slot order)
-// and the leapfrog update v += cv M^-1 r, p += cp v.
+// and the leapfrog update v += cv (damp v + M^-1 r), p_out = p_in + cp v.
 template <typename T>
 struct HexUpdateArgs {
-  T* p; T* v; const T* S;
+  const T* p_in; T* p_out; T* v; const T* S;
   int Bp;
   const int* node_ptr; const int* node_slot;
   const T* Minv;
+  const T* damp;             // C_jj / M_jj of absorbing faces, or NULL: v += cv (damp v + M^-1 r)
   long long ndof;
   T cv, cp;
 };

@@ -855,7 +855,8 @@ __global__ void __launch_bounds__(128) hex_iface_face_kernel(const __grid_consta
 
 // Residual assembly and leapfrog update, one thread per (node, BB members):
 // r = sum of the node's slots (ascending slot order, so the sum is the same
-// in every run and for every batch width), v += cv M^-1 r, p += cp v.
+// in every run and for every batch width), v += cv (damp v + M^-1 r),
+// p_out = p_in + cp v.
 template <typename T, int BB>
 __global__ void __launch_bounds__(256) hex_update_kernel(const __grid_constant__ HexUpdateArgs<T> A) {
   using P = Pack<T, BB>;
@@ -868,13 +869,14 @@ __global__ void __launch_bounds__(256) hex_update_kernel(const __grid_constant__
   const T mi = A.Minv[j];
   P r = vzero<T, BB>();
   for (int k = k0; k < k1; ++k) r = vadd(r, reinterpret_cast<const P*>(A.S + (long long)A.node_slot[k] * A.Bp)[ch]);
-  P* pp = reinterpret_cast<P*>(A.p + j * A.Bp) + ch;
   P* vp = reinterpret_cast<P*>(A.v + j * A.Bp) + ch;
-  P pv = *pp, vv = *vp;
+  P pv = reinterpret_cast<const P*>(A.p_in + j * A.Bp)[ch], vv = *vp;
+  // damping of absorbing faces on the predicted velocity (C p'_pred of Algorithm 1)
+  if (A.damp) vfma(vv, mul_(A.cv, A.damp[j]), P(vv));
   vfma(vv, mul_(A.cv, mi), r);
   vfma(pv, A.cp, vv);
   *vp = vv;
-  *pp = pv;
+  reinterpret_cast<P*>(A.p_out + j * A.Bp)[ch] = pv;
 }
 
 __device__ __forceinline__ double hex_warp_sum(double v) {

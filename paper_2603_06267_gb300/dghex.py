@@ -17,6 +17,8 @@ from .dgsem import DGSEM_FP32_MIXED, DGSEM_FP64, DgsemError, _current_stream, _f
 
 EXPORTED = [
     "dghex_mesh_create", "dghex_get_dt", "dghex_nodes", "dghex_pmut_nodes", "dghex_pmut_set", "dghex_get_matches",
+    "dghex_set_absorbing_faces", "dghex_pmut_set_receive", "dghex_get_voltages", "dghex_state_save",
+    "dghex_state_load",
     "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_check_stability", "dghex_set_interface_kernel",
     "dghex_profile",
     "dghex_kernel_stats", "dghex_destroy",
@@ -57,6 +59,11 @@ def load_library():
     lib.dghex_set_state.argtypes = [vp, vp, vp]
     lib.dghex_get_pressure.argtypes = [vp, vp, c_size_t]
     lib.dghex_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
+    lib.dghex_set_absorbing_faces.argtypes = [vp, c_int, c_int, vp]
+    lib.dghex_pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
+    lib.dghex_get_voltages.argtypes = [vp, vp, c_size_t]
+    lib.dghex_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
+    lib.dghex_state_load.argtypes = [vp, vp, c_size_t]
     lib.dghex_set_interface_kernel.argtypes = [vp, c_int]
     lib.dghex_profile.argtypes = [vp, c_int]
     lib.dghex_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
@@ -190,6 +197,37 @@ def dghex_get_pressure(ctx, batch: int, ndof: int) -> np.ndarray:
     return out
 
 
+def dghex_set_absorbing_faces(ctx, domain: int, faces):
+    """First-order absorbing faces ([n, 2] (element, local face)) of a domain."""
+    f = np.ascontiguousarray(faces if faces is not None else np.zeros((0, 2)), dtype=np.int32).reshape(-1, 2)
+    _check(_lib.dghex_set_absorbing_faces(ctx, domain, f.shape[0], _ptr(f) if f.size else None),
+           "dghex_set_absorbing_faces")
+
+
+def dghex_pmut_set_receive(ctx, n_switch: int, capacitance=None, sign: int = -1):
+    cap = None if capacitance is None else np.ascontiguousarray(capacitance, dtype=np.float64)
+    _check(_lib.dghex_pmut_set_receive(ctx, int(n_switch), _ptr(cap), int(sign)), "dghex_pmut_set_receive")
+
+
+def dghex_get_voltages(ctx, batch: int, n_pmut: int, nsteps: int):
+    out = np.zeros((batch, n_pmut, nsteps))
+    _check(_lib.dghex_get_voltages(ctx, _ptr(out), out.size), "dghex_get_voltages")
+    return out
+
+
+def dghex_state_save(ctx) -> bytes:
+    n = c_size_t(0)
+    _check(_lib.dghex_state_save(ctx, None, byref(n)), "dghex_state_save")
+    buf = ctypes.create_string_buffer(n.value)
+    _check(_lib.dghex_state_save(ctx, buf, byref(n)), "dghex_state_save")
+    return buf.raw[: n.value]
+
+
+def dghex_state_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(_lib.dghex_state_load(ctx, buf, len(blob)), "dghex_state_load")
+
+
 def dghex_check_stability(ctx, iters: int = 100):
     """(status, lambda_max of M^-1 K): status DGSEM_EUNSTABLE when dt is above
     0.95 * 2 / sqrt(lambda_max)."""
@@ -231,10 +269,16 @@ class HexSolver:
                                      penalty_alpha=workload.penalty_alpha,
                                      iface_quad_pts=getattr(workload, "quad_pts", 0) or 0,
                                      normal_tol=getattr(workload, "normal_tol", 0.5))
+        for d, faces in enumerate(getattr(workload, "absorbing_faces", None) or []):
+            if faces is not None and len(faces):
+                dghex_set_absorbing_faces(self.ctx, d, faces)
         self.dt, self.ndof = dghex_get_dt(self.ctx)
         self.K = 0
         if workload.pmuts is not None and workload.pmut_faces is not None:
             self.set_pmuts(workload.pmuts)
+            if getattr(workload, "rx_switch", None) is not None:
+                cap = np.broadcast_to(np.asarray(workload.rx_capacitance, dtype=np.float64), (self.K,))
+                dghex_pmut_set_receive(self.ctx, workload.rx_switch, cap, workload.rx_sign)
 
     def set_pmuts(self, pm):
         xyz, _ = dghex_pmut_nodes(self.ctx)

@@ -252,3 +252,94 @@ def test_stability_check_matches_the_largest_eigenvalue(lib, two_dom):
     code, lam2 = dghex.dghex_check_stability(big.ctx, 400)
     assert code == dgsem.DGSEM_EUNSTABLE and abs(lam2 / lam_ref - 1.0) < 2e-2
     big.close()
+
+
+def _absorbing_workload(nsteps=60):
+    w = H.distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=nsteps)
+    prim, sec = w.domains
+    w.absorbing_faces = [H.lattice_side_faces(prim.lattice, 0),
+                         np.concatenate([H.lattice_side_faces(sec.lattice, 3), H.lattice_side_faces(sec.lattice, 5)])]
+    return w
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_absorbing_faces_parity(lib, prec, tol):
+    """Absorbing faces on a curved two-domain mesh (primary x-, secondary y+
+    and top): driven traces and a run from a state with velocity."""
+    from paper_2603_06267_gb300 import dghex
+    w = _absorbing_workload()
+    prob = HO.HexOracleProblem(w)
+    s = dghex.HexSolver(w)
+    assert abs(s.dt - prob.stable_dt()) < 1e-15 * s.dt
+    tr = s.run(precision=prec)
+    ref = prob.run(dt=s.dt)
+    assert _rel(tr, ref) < tol, _rel(tr, ref)
+    xyz, first = dghex.dghex_nodes(s.ctx)
+    idx = _node_map(prob, xyz, first)
+    X = np.concatenate([m.coords for m in prob.meshes])
+    p0 = W.seeded_field(9, X[:, 0], X[:, 1], X[:, 2])
+    v0 = 2e6 * W.seeded_field(10, X[:, 0], X[:, 1], X[:, 2])
+    g0 = np.zeros(s.ndof); g0[idx] = p0
+    gv = np.zeros(s.ndof); gv[idx] = v0
+    dghex.dghex_set_state(s.ctx, g0, gv)
+    drive = np.zeros((1, w.pmuts.n_pmut, w.nsteps))
+    tr = s.run(drive=drive, precision=prec)
+    ref = prob.run(dt=s.dt, drive=drive, p0=p0, v0=v0)
+    assert _rel(tr, ref) < tol, _rel(tr, ref)
+    s.close()
+
+
+def test_absorbing_faces_refused_on_the_interface(lib):
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w = _absorbing_workload()
+    s = dghex.HexSolver(w)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_set_absorbing_faces(s.ctx, 0, w.fine_faces[:1])
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    dghex.dghex_set_absorbing_faces(s.ctx, 0, None)
+    dghex.dghex_set_absorbing_faces(s.ctx, 1, None)
+    dt, _ = dghex.dghex_get_dt(s.ctx)
+    assert dt >= s.dt
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_receive_switch_parity(lib, prec, tol):
+    """TX -> RX switch at step 25 on the curved mesh: traces and the recorded
+    voltages (drive, then open circuit) against the oracle."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=60)
+    w.rx_switch, w.rx_capacitance, w.rx_sign = 25, np.full(w.pmuts.n_pmut, 2e-12), -1
+    prob = HO.HexOracleProblem(w)
+    s = dghex.HexSolver(w)
+    tr = s.run(precision=prec)
+    ref = prob.run(dt=s.dt)
+    assert _rel(tr, ref) < tol
+    v = dghex.dghex_get_voltages(s.ctx, 1, w.pmuts.n_pmut, w.nsteps)
+    assert np.max(np.abs(prob.voltages[:, :, 25:])) > 0
+    assert _rel(v, prob.voltages) < tol
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_roundtrip_is_bitwise(lib, prec):
+    """30 steps, checkpoint, load into a fresh context, 20 more steps equals
+    50 steps in one run bit for bit (reception switching on after the
+    checkpoint, so the step count must survive it)."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=50, batch=3, steer=True)
+    w.rx_switch, w.rx_capacitance, w.rx_sign = 35, np.full(w.pmuts.n_pmut, 2e-12), -1
+    a = dghex.HexSolver(w)
+    drive = w.drive(a.dt, 50, 3)
+    full = a.run(drive=drive, precision=prec, nsteps=50)
+    vfull = dghex.dghex_get_voltages(a.ctx, 3, w.pmuts.n_pmut, 50)
+    a.run(drive=np.ascontiguousarray(drive[:, :, :30]), precision=prec, nsteps=30)
+    blob = dghex.dghex_state_save(a.ctx)
+    a.close()
+    b = dghex.HexSolver(w)
+    dghex.dghex_state_load(b.ctx, blob)
+    tail = b.run(drive=np.ascontiguousarray(drive[:, :, 30:]), precision=prec, nsteps=20, flags=1)
+    vtail = dghex.dghex_get_voltages(b.ctx, 3, w.pmuts.n_pmut, 20)
+    assert np.array_equal(tail, full[:, :, 30:])
+    assert np.array_equal(vtail, vfull[:, :, 30:])
+    b.close()
