@@ -34,7 +34,10 @@ are the extra ones for curved elements):
     reference position is inside [-1, 1]^3 up to 1e-10;
   * absorbing faces: C_jj = sum_F c w_a w_b |J_F| at the face's GLL nodes
     (the box reading with the Nanson surface Jacobian), dt at most
-    1 / max_j C_jj / M_jj.
+    1 / max_j (C_jj / M_jj + alpha_j);
+  * perfectly matched layers: the box reading (psi nodal, Phi element-local
+    at the GLL nodes, Crank-Nicolson damping of Phi, half steps), the layers
+    measured from the domain's bounding-box sides, gradients J^-T grad^.
 Node numbering: nodes of one domain at the same physical position (within
 1e-9 of the domain size) are one node, numbered in order of first appearance
 over the elements (element order, then local index a + (N+1) b + (N+1)^2 c).
@@ -322,7 +325,7 @@ class HexOracleProblem(OracleProblem):
             self.K = (self.K + KI).tocsr()
         self.Minv = 1.0 / self.M
         self._absorbing_matrix()
-        self.pml = None
+        self._hex_pml_setup()
         self._pmut_matrix()
 
     def _assemble_volume(self):
@@ -356,6 +359,45 @@ class HexOracleProblem(OracleProblem):
                     _, dS = face_normal_and_jac(J, int(f))
                     np.add.at(C, m.conn[int(e), sel], m.c * m.w[a] * m.w[b] * dS)
         self.C = C
+
+    def _hex_pml_setup(self):
+        """Perfectly matched layers (eq. full_problem rows 1-3, profile of
+        Sec. 2) on curved elements: zeta_d at every node from its coordinate's
+        depth into the layers of the domain's bounding box, and per layer
+        element its node ids, the physical gradients J^-T grad^ psi at its GLL
+        nodes, w |J| and c^2 -- the inputs of the box oracle's PML step."""
+        self.pml = None
+        layers = getattr(self.w, "pml", None)
+        if not layers:
+            return
+        R = float(getattr(self.w, "pml_R", 1e-4))
+        zeta = np.zeros((3, self.nh))
+        elems = []
+        for m, th in zip(self.meshes, layers):
+            if th is None or not any(t > 0 for t in th):
+                continue
+            lo, hi = m.verts.min(axis=0), m.verts.max(axis=0)
+            ids_all = np.arange(m.offset, m.offset + m.nnode)
+            for d in range(3):
+                for side, t in ((0, th[2 * d]), (1, th[2 * d + 1])):
+                    if t <= 0:
+                        continue
+                    zt = m.c / t * math.log(1.0 / R)
+                    x = m.coords[:, d]
+                    s = (lo[d] + t - x) / t if side == 0 else (x - (hi[d] - t)) / t
+                    s = np.clip(s, 0.0, 1.0)
+                    zeta[d, ids_all] += zt * (s - np.sin(2 * math.pi * s) / (2 * math.pi))
+            _, gref = reference_basis(m.N, m.xi, m.ref_nodes)
+            for e in range(m.ne):
+                ids = m.conn[e]
+                if np.any(zeta[:, ids] != 0.0):
+                    grad = np.einsum("qdx,qjd->qjx", np.linalg.inv(m.J[e]), gref)
+                    elems.append((ids, grad, m.wq * m.detJ[e], m.c ** 2))
+        if not elems:
+            return
+        z1, z2, z3 = zeta
+        self.pml = dict(zeta=zeta, alpha=z1 + z2 + z3, beta=z1 * z2 + z2 * z3 + z3 * z1, gamma=z1 * z2 * z3,
+                        elems=elems)
 
     def pmut_face_nodes(self):
         """Unique node ids on the PMUT faces, their positions and the
@@ -424,7 +466,10 @@ class HexOracleProblem(OracleProblem):
         hmin = min(min(m.h_min(e) for e in range(m.ne)) / 2.0 * float(np.min(np.diff(m.xi)))
                    for m in self.meshes)
         dt = cfl * hmin / cmax
-        sigma = float(np.max(self.C * self.Minv))
+        damp = self.C * self.Minv
+        if self.pml is not None:
+            damp = damp + self.pml["alpha"]
+        sigma = float(np.max(damp))
         if sigma > 0.0:
             dt = min(dt, 1.0 / sigma)
         return dt

@@ -264,3 +264,38 @@ def test_absorbing_faces_dissipate_on_a_curved_mesh():
     _, e = p.run(nsteps=80, p0=p0, energy=True, receivers=w.receivers[:1])
     lf = e[:, 0, 0]
     assert np.all(np.diff(lf) <= 1e-12 * lf[0]) and lf[-1] < 0.999 * lf[0]
+
+
+def test_pml_on_the_affine_box_is_the_box_oracles():
+    """Layers on an undistorted lattice give the box oracle's profiles, dt and
+    traces (its PML is pinned by the plane-pulse reflection)."""
+    wb = W.small_one_domain(nel=(4, 2, 2), order=3, nsteps=40)
+    wb.domains[0].pml = (75e-6, 0.0, 0.0, 75e-6, 0.0, 75e-6)
+    wh = H.hex_workload_from_box(wb)
+    wh.pml, wh.pml_R = [wb.domains[0].pml], wb.domains[0].pml_R
+    pb, ph = O.OracleProblem(wb), HO.HexOracleProblem(wh)
+    idx = _map_nodes(pb, ph, 1e-15)
+    np.testing.assert_allclose(ph.pml["zeta"][:, idx], pb.pml["zeta"], rtol=1e-12, atol=1e-6)
+    assert abs(ph.stable_dt() - pb.stable_dt()) < 1e-15 * pb.stable_dt()
+    dt = pb.stable_dt()
+    tb = pb.run(dt=dt)
+    th = ph.run(dt=dt)
+    assert np.linalg.norm(th - tb) < 1e-11 * np.linalg.norm(tb)
+
+
+def test_pml_on_a_curved_mesh_absorbs():
+    """A smooth field in a distorted box with layers on every side loses
+    most of its acoustic leapfrog energy, without late-time growth (the
+    acoustic part alone is not an invariant of the layer system, so the first
+    steps may exchange energy with Phi and psi)."""
+    w = H.distorted_one_domain(nel=(4, 4, 3), order=3, nsteps=5, h=50e-6)
+    w.pmuts = None
+    w.pml, w.pml_R = [(50e-6,) * 6], 1e-3
+    p = HO.HexOracleProblem(w)
+    X = _coords(p)
+    p0 = W.seeded_field(5, X[:, 0], X[:, 1], X[:, 2])
+    _, e = p.run(nsteps=400, p0=p0, energy=True, receivers=w.receivers[:1])
+    lf = e[:, 0, 0]
+    assert np.all(np.isfinite(lf)) and lf[-1] < 0.2 * lf[0]
+    assert np.max(lf) < 1.1 * lf[0]
+    assert np.all(np.diff(lf[200:]) <= 1e-9 * lf[0])

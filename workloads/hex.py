@@ -51,6 +51,10 @@ class HexWorkload(Workload):
     pmut_faces: Optional[np.ndarray] = None     # [np, 2] of domain 0 on Gamma_PMUT
     # first-order absorbing faces (Gamma_ABC) per domain: [n, 2] (element, local face) or None
     absorbing_faces: Optional[list] = None
+    # perfectly matched layers per domain: thickness (m) along the sides x-, x+, y-, y+, z-, z+
+    # of the domain's bounding box (None or zeros: none), design reflection pml_R
+    pml: Optional[list] = None
+    pml_R: float = 1.0e-4
     normal_tol: float = 0.5                     # Algorithm 3 |n+ + n-| < tol
     box_extent: Optional[tuple] = None          # the box the mesh fills (for receivers)
 
