@@ -296,6 +296,7 @@ def test_pml_on_a_curved_mesh_absorbs():
     p0 = W.seeded_field(5, X[:, 0], X[:, 1], X[:, 2])
     _, e = p.run(nsteps=400, p0=p0, energy=True, receivers=w.receivers[:1])
     lf = e[:, 0, 0]
-    assert np.all(np.isfinite(lf)) and lf[-1] < 0.2 * lf[0]
+    assert np.all(np.isfinite(lf)) and lf[-1] < 1e-3 * lf[0]
     assert np.max(lf) < 1.1 * lf[0]
-    assert np.all(np.diff(lf[200:]) <= 1e-9 * lf[0])
+    # no late-time growth: every later window stays below the energy at step 200
+    assert np.max(lf[240:]) < lf[200] and np.max(lf[320:]) < lf[280]
