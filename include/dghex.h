@@ -133,6 +133,19 @@ int dghex_pmut_set(dghex_ctx* ctx, int n_pmut, int n_modes, const int* foot_ptr,
  * bound is refused (DGSEM_EUNSTABLE).  The state restarts from rest. */
 int dghex_set_absorbing_faces(dghex_ctx* ctx, int domain, int n, const int* faces);
 
+/* Perfectly matched layers (Sec. 2, eq. full_problem rows 1-3) along the
+ * sides x-, x+, y-, y+, z-, z+ of a domain's bounding box, thickness[6] in m
+ * (0 = none), design reflection R in (0, 1) (one R per mesh), with the
+ * profile zeta~ (s - sin(2 pi s) / (2 pi)), zeta~ = c / l log(1/R), s the
+ * depth into the layer.  As on the box path (dgsem_set_pml): psi nodal, Phi
+ * element-local at the GLL nodes of the layer elements (any node with a
+ * non-zero profile), gradients J^-T grad^ on the curved elements,
+ * Crank-Nicolson damping of Phi, alpha p' on the predicted velocity; dt held
+ * to 1 / max (C/M + alpha).  All-zero thickness removes the domain's layers.
+ * The state restarts from rest; checkpoints of a state with a layer are
+ * refused (DGSEM_ESTATE). */
+int dghex_set_pml(dghex_ctx* ctx, int domain, const double* thickness, double R);
+
 /* TX -> RX switch and the voltage record, as pmut_set_receive and
  * dgsem_get_voltages in dgsem.h (steps counted since rest or the last
  * dghex_set_state; DGSEM_RUN_CONTINUE and checkpoints keep counting). */

@@ -94,6 +94,14 @@ struct HexDom {
   int* d_conn = nullptr;
   double* d_G64 = nullptr;
   float* d_G32 = nullptr;
+  // perfectly matched layer: thickness per bounding-box side, layer elements,
+  // their J^-1 and w |J| at the GLL nodes, first layer slot
+  double pml_th[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<int> pml_elem;
+  int* d_pml_elem = nullptr;
+  double* d_pml_geo64 = nullptr; float* d_pml_geo32 = nullptr;
+  long long pslot0 = 0;
+  void* Phi = nullptr;                 // run state [npml][3][nl][Bp]
 };
 
 // corner list position of the corner with bits (i, j, k)
@@ -229,7 +237,16 @@ struct dghex_ctx {
   std::vector<double> Mh;                   // lumped mass (host copy)
   // absorbing faces per domain, and C_jj / M_jj on the device (NULL: none)
   std::vector<int> abs_faces[2];
-  double* d_damp64 = nullptr; float* d_damp32 = nullptr;
+  double* d_damp64 = nullptr; float* d_damp32 = nullptr;   // C_jj/M_jj + alpha_j
+  // perfectly matched layers: design reflection, profiles zeta_d per node and
+  // the node coefficients beta, gamma (alpha is in the damping array)
+  bool has_pml = false;
+  double pml_R = 1e-4;
+  double *d_zeta64 = nullptr, *d_beta64 = nullptr, *d_gamma64 = nullptr;
+  float *d_zeta32 = nullptr, *d_beta32 = nullptr, *d_gamma32 = nullptr;
+  long long npslot = 0;                     // layer slots (after the forcing slots)
+  std::vector<double> pml_alpha;            // alpha_j per node (host)
+  void* Psi = nullptr;                      // run state [ndof][Bp]
   // TX -> RX switch of the PMUT array (off: rx_switch < 0)
   long long rx_switch = -1;
   double* d_rx_gain = nullptr;
@@ -323,6 +340,8 @@ void collect_timings(dghex_ctx* c) {
 
 void free_run_state(dghex_ctx* c) {
   dfree(c->X); dfree(c->Y); dfree(c->V); dfree(c->S); dfree(c->q_state); dfree(c->d_fp_offB);
+  dfree(c->Psi);
+  for (int d = 0; d < 2; ++d) dfree(c->dom[d].Phi);
   c->prec = -1;
   c->batch = 0;
   c->Bp = 0;
@@ -340,6 +359,11 @@ int ensure_run_state(dghex_ctx* c, int prec, int batch) {
       (rc = dmalloc(&c->V, es * Bp * c->ndof)) ||
       (rc = dmalloc(&c->S, es * Bp * c->nslot)))
     return rc;
+  if (c->has_pml) {
+    if ((rc = dmalloc(&c->Psi, es * Bp * c->ndof))) return rc;
+    for (int d = 0; d < c->nd; ++d)
+      if ((rc = dmalloc(&c->dom[d].Phi, es * Bp * 3 * c->dom[d].nl * c->dom[d].pml_elem.size()))) return rc;
+  }
   if (c->K > 0) {
     if ((rc = dmalloc(&c->q_state, sizeof(double) * 3 * (size_t)batch * c->K * c->M))) return rc;
     std::vector<long long> off(c->ent_node);
@@ -358,7 +382,13 @@ int ensure_run_state(dghex_ctx* c, int prec, int batch) {
 int build_slots(dghex_ctx* c) {
   c->islot0 = c->nvol;
   c->fslot0 = c->islot0 + c->nislot;
-  c->nslot = c->fslot0 + c->nnz;
+  long long ps = c->fslot0 + c->nnz;
+  for (int d = 0; d < c->nd; ++d) {
+    c->dom[d].pslot0 = ps;
+    ps += (long long)c->dom[d].pml_elem.size() * c->dom[d].nl;
+  }
+  c->npslot = ps - c->fslot0 - c->nnz;
+  c->nslot = ps;
   if (c->nslot >= (1LL << 31)) return hfail(DGSEM_EINVAL, "mesh too large: %lld residual slots", c->nslot);
   std::vector<int> node_of((size_t)c->nslot);
   for (int d = 0; d < c->nd; ++d) {
@@ -374,6 +404,11 @@ int build_slots(dghex_ctx* c) {
     }
   }
   for (int e = 0; e < c->nnz; ++e) node_of[(size_t)c->fslot0 + e] = (int)c->ent_node[e];
+  for (int d = 0; d < c->nd; ++d) {
+    const HexDom& D = c->dom[d];
+    for (size_t k = 0; k < D.pml_elem.size(); ++k)
+      for (int i = 0; i < D.nl; ++i) node_of[(size_t)D.pslot0 + k * D.nl + i] = D.conn[(size_t)D.pml_elem[k] * D.nl + i];
+  }
   std::vector<int> ptr((size_t)c->ndof + 1, 0), slot((size_t)c->nslot);
   for (long long s = 0; s < c->nslot; ++s) ptr[node_of[s] + 1] += 1;
   for (long long j = 0; j < c->ndof; ++j) ptr[j + 1] += ptr[j];
@@ -632,8 +667,9 @@ int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
   return DGSEM_OK;
 }
 
+// pml: 0 no layer terms, 1 set-state start (psi stays 0), 2 time step
 template <typename T>
-int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void* p_in, void* p_out) {
+int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void* p_in, void* p_out, int pml = 0) {
   hex::HexUpdateArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.p_in = static_cast<const T*>(p_in); a.p_out = static_cast<T*>(p_out);
@@ -642,6 +678,14 @@ int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void
   a.node_ptr = c->d_node_ptr; a.node_slot = c->d_node_slot;
   a.Minv = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_Minv32) : reinterpret_cast<const T*>(c->d_Minv64);
   a.damp = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_damp32) : reinterpret_cast<const T*>(c->d_damp64);
+  if (pml && c->has_pml) {
+    const bool f = std::is_same<T, float>::value;
+    a.beta = f ? reinterpret_cast<const T*>(c->d_beta32) : reinterpret_cast<const T*>(c->d_beta64);
+    a.gamma = f ? reinterpret_cast<const T*>(c->d_gamma32) : reinterpret_cast<const T*>(c->d_gamma64);
+    a.psi = static_cast<T*>(c->Psi);
+    a.hpsi = pml == 2 ? T(0.5 * c->dt) : T(0);
+    a.dpsi = pml == 2 ? T(c->dt) : T(0);
+  }
   a.ndof = c->ndof; a.cv = T(cv); a.cp = T(cp);
   HexTimer t(c, s, DGHEX_K_UPDATE);
   HCUDA(hex::launch_hex_update<T>(a, s));
@@ -703,7 +747,25 @@ int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs
   int rc;
   if (c->K > 0 && (rc = launch_tail<T>(c, s, true, 0, nullptr, 0, 0))) return rc;
   if ((rc = launch_residual<T>(c, s, c->Y))) return rc;
-  if ((rc = launch_update<T>(c, s, -c->dt, c->dt, c->Y, c->X))) return rc;
+  for (int d = 0; d < c->nd && c->has_pml; ++d) {
+    const HexDom& D = c->dom[d];
+    if (D.pml_elem.empty()) continue;
+    const bool f = std::is_same<T, float>::value;
+    hex::HexPmlArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.p = static_cast<const T*>(c->Y); a.psi = static_cast<const T*>(c->Psi); a.phi = static_cast<T*>(D.Phi);
+    a.S = static_cast<T*>(c->S); a.Bp = c->Bp;
+    a.elem = D.d_pml_elem; a.conn = D.d_conn;
+    a.geo = f ? reinterpret_cast<const T*>(D.d_pml_geo32) : reinterpret_cast<const T*>(D.d_pml_geo64);
+    a.zeta = f ? reinterpret_cast<const T*>(c->d_zeta32) : reinterpret_cast<const T*>(c->d_zeta64);
+    a.ndof = c->ndof; a.slot_base = D.pslot0; a.npml = (int)D.pml_elem.size();
+    a.c2 = T(D.c * D.c); a.dt = T(c->dt);
+    for (int i = 0; i < D.n; ++i)
+      for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
+    HexTimer t(c, s, DGHEX_K_VOL);
+    HCUDA(hex::launch_hex_pml<T>(a, D.n, s));
+  }
+  if ((rc = launch_update<T>(c, s, -c->dt, c->dt, c->Y, c->X, 2))) return rc;
   if ((rc = launch_tail<T>(c, s, false, R, traces, tbs, trs))) return rc;
   std::swap(c->X, c->Y);
   return DGSEM_OK;
@@ -743,13 +805,17 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
     HCUDA(cudaMemsetAsync(c->V, 0, es * c->Bp * c->ndof, s));
     HCUDA(cudaMemsetAsync(c->S, 0, es * c->Bp * c->nslot, s));
     if (c->q_state) HCUDA(cudaMemsetAsync(c->q_state, 0, sizeof(double) * 3 * (size_t)c->batch * c->K * c->M, s));
+    if (c->Psi) HCUDA(cudaMemsetAsync(c->Psi, 0, es * c->Bp * c->ndof, s));
+    for (int d = 0; d < c->nd; ++d)
+      if (c->dom[d].Phi)
+        HCUDA(cudaMemsetAsync(c->dom[d].Phi, 0, es * c->Bp * 3 * c->dom[d].nl * c->dom[d].pml_elem.size(), s));
     if (c->has_init) {
       int rc;
       if (!c->init_p.empty() && (rc = upload_field<T>(c->init_p, c->X, c->batch, c->Bp, c->ndof, s))) return rc;
       if (!c->init_v.empty() && (rc = upload_field<T>(c->init_v, c->V, c->batch, c->Bp, c->ndof, s))) return rc;
       // v^{1/2} = p'^0 + dt/2 p''^0 with p''^0 = M^-1 (-K p^0 - C p'^0) (no forcing at rest),
       // p^1 = p^0 + dt v^{1/2}
-      if ((rc = launch_residual<T>(c, s, c->X)) || (rc = launch_update<T>(c, s, -0.5 * c->dt, c->dt, c->X, c->Y)))
+      if ((rc = launch_residual<T>(c, s, c->X)) || (rc = launch_update<T>(c, s, -0.5 * c->dt, c->dt, c->X, c->Y, 1)))
         return rc;
     }
   }
@@ -1102,7 +1168,7 @@ namespace {
 // C_jj / M_jj of every domain's absorbing faces (Nanson-weighted GLL
 // collocation of the damping form of eq. Wf_4), uploaded in both precisions;
 // dt held to 1 / max of it.
-int apply_absorbing(dghex_ctx* c) {
+int apply_absorbing(dghex_ctx* c, const std::vector<double>* alpha) {
   dfree(c->d_damp64);
   dfree(c->d_damp32);
   std::vector<double> C((size_t)c->ndof, 0.0);
@@ -1130,20 +1196,109 @@ int apply_absorbing(dghex_ctx* c) {
   }
   c->dt = c->dt_cfl;
   c->state_valid = false;
+  if (alpha) any = true;
   if (!any) return DGSEM_OK;
   double smax = 0.0;
   std::vector<float> s32((size_t)c->ndof);
   for (long long j = 0; j < c->ndof; ++j) {
     C[j] /= c->Mh[j];
+    if (alpha) C[j] += (*alpha)[j];
     smax = std::max(smax, C[j]);
     s32[j] = (float)C[j];
   }
   if (c->dt_fixed && c->dt > 1.0 / smax)
-    return hfail(DGSEM_EUNSTABLE, "dt %.4g above the absorbing-face limit 1 / max C/M = %.4g", c->dt, 1.0 / smax);
+    return hfail(DGSEM_EUNSTABLE, "dt %.4g above the damping limit 1 / max (C/M + alpha) = %.4g", c->dt, 1.0 / smax);
   if (!c->dt_fixed) c->dt = std::min(c->dt, 1.0 / smax);
   int rc;
   if ((rc = upload(&c->d_damp64, C)) || (rc = upload(&c->d_damp32, s32))) return rc;
   return DGSEM_OK;
+}
+
+// Layer profiles zeta_d (Sec. 2: zeta~ (s - sin(2 pi s) / (2 pi)), zeta~ =
+// c / l log(1/R), s the depth into a layer of thickness l measured from the
+// side of the domain's bounding box), the layer elements (any node with a
+// non-zero profile), their J^-1 and w |J| at the GLL nodes, the node
+// coefficients, the layer slots and the damping limit of dt.
+int rebuild_pml(dghex_ctx* c) {
+  std::vector<double> zeta(3 * (size_t)c->ndof, 0.0);
+  for (int d = 0; d < c->nd; ++d) {
+    HexDom& D = c->dom[d];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int v = 0; v < D.nv; ++v)
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], D.vert[3 * (size_t)v + a]);
+        hi[a] = std::max(hi[a], D.vert[3 * (size_t)v + a]);
+      }
+    for (int side = 0; side < 6; ++side) {
+      const double t = D.pml_th[side];
+      if (!(t > 0.0)) continue;
+      const int ax = side >> 1;
+      const double zt = D.c / t * std::log(1.0 / c->pml_R);
+      for (long long j = D.node0; j < D.node0 + D.nnode; ++j) {
+        const double x = c->xyz[3 * j + ax];
+        double sd = (side & 1) ? (x - (hi[ax] - t)) / t : (lo[ax] + t - x) / t;
+        sd = std::min(1.0, std::max(0.0, sd));
+        zeta[(size_t)ax * c->ndof + j] += zt * (sd - std::sin(2.0 * M_PI * sd) / (2.0 * M_PI));
+      }
+    }
+  }
+  c->has_pml = false;
+  for (double z : zeta) c->has_pml = c->has_pml || z != 0.0;
+  dfree(c->d_zeta64); dfree(c->d_zeta32); dfree(c->d_beta64); dfree(c->d_beta32);
+  dfree(c->d_gamma64); dfree(c->d_gamma32);
+  c->pml_alpha.clear();
+  for (int d = 0; d < c->nd; ++d) {
+    HexDom& D = c->dom[d];
+    D.pml_elem.clear();
+    dfree(D.d_pml_elem); dfree(D.d_pml_geo64); dfree(D.d_pml_geo32);
+    if (!c->has_pml) continue;
+    for (int e = 0; e < D.ne; ++e) {
+      bool in = false;
+      for (int i = 0; i < D.nl && !in; ++i) {
+        const int j = D.conn[(size_t)e * D.nl + i];
+        in = zeta[j] != 0.0 || zeta[c->ndof + j] != 0.0 || zeta[2 * c->ndof + j] != 0.0;
+      }
+      if (in) D.pml_elem.push_back(e);
+    }
+    std::vector<double> geo(D.pml_elem.size() * 10 * (size_t)D.nl);
+    for (size_t k = 0; k < D.pml_elem.size(); ++k) {
+      double V[24];
+      elem_verts(D, D.pml_elem[k], V);
+      for (int i = 0; i < D.nl; ++i) {
+        const int l[3] = {i % D.n, (i / D.n) % D.n, i / (D.n * D.n)};
+        const double r[3] = {D.basis->x[l[0]], D.basis->x[l[1]], D.basis->x[l[2]]};
+        double x[3], J[3][3], Ji[3][3];
+        hex::tri_map(V, r, x, J);
+        const double det = hex::inv3(J, Ji);
+        double* g = &geo[k * 10 * D.nl + i];
+        for (int q = 0; q < 9; ++q) g[(size_t)q * D.nl] = Ji[q / 3][q % 3];
+        g[9 * (size_t)D.nl] = D.basis->w[l[0]] * D.basis->w[l[1]] * D.basis->w[l[2]] * det;
+      }
+    }
+    std::vector<float> g32(geo.begin(), geo.end());
+    int rc;
+    if ((rc = upload(&D.d_pml_elem, D.pml_elem)) || (rc = upload(&D.d_pml_geo64, geo)) || (rc = upload(&D.d_pml_geo32, g32)))
+      return rc;
+  }
+  if (c->has_pml) {
+    const size_t n = (size_t)c->ndof;
+    std::vector<double> beta(n), gamma(n);
+    c->pml_alpha.resize(n);
+    for (size_t j = 0; j < n; ++j) {
+      const double z1 = zeta[j], z2 = zeta[n + j], z3 = zeta[2 * n + j];
+      c->pml_alpha[j] = z1 + z2 + z3;
+      beta[j] = z1 * z2 + z2 * z3 + z3 * z1;
+      gamma[j] = z1 * z2 * z3;
+    }
+    std::vector<float> z32(zeta.begin(), zeta.end()), b32(beta.begin(), beta.end()), g32(gamma.begin(), gamma.end());
+    int rc;
+    if ((rc = upload(&c->d_zeta64, zeta)) || (rc = upload(&c->d_zeta32, z32)) || (rc = upload(&c->d_beta64, beta)) ||
+        (rc = upload(&c->d_beta32, b32)) || (rc = upload(&c->d_gamma64, gamma)) || (rc = upload(&c->d_gamma32, g32)))
+      return rc;
+  }
+  int rc = build_slots(c);
+  if (rc) return rc;
+  return apply_absorbing(c, c->has_pml ? &c->pml_alpha : nullptr);
 }
 
 bool face_in(const std::vector<int>& list, int e, int f) {
@@ -1179,7 +1334,18 @@ int dghex_set_absorbing_faces(dghex_ctx* c, int domain, int n, const int* faces)
       return hfail(DGSEM_EINVAL, "face entry %d lies on the interface or on Gamma_PMUT", i);
   }
   c->abs_faces[domain] = fl;
-  return apply_absorbing(c);
+  return apply_absorbing(c, c->has_pml ? &c->pml_alpha : nullptr);
+}
+
+int dghex_set_pml(dghex_ctx* c, int domain, const double* thickness, double R) {
+  if (!c || !thickness) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (domain < 0 || domain >= c->nd) return hfail(DGSEM_EINVAL, "domain %d out of range", domain);
+  if (!(R > 0.0 && R < 1.0)) return hfail(DGSEM_EINVAL, "R must lie in (0, 1)");
+  for (int k = 0; k < 6; ++k)
+    if (!(thickness[k] >= 0.0) || !std::isfinite(thickness[k])) return hfail(DGSEM_EINVAL, "thickness[%d] must be >= 0", k);
+  for (int k = 0; k < 6; ++k) c->dom[domain].pml_th[k] = thickness[k];
+  c->pml_R = R;
+  return rebuild_pml(c);
 }
 
 int dghex_pmut_set_receive(dghex_ctx* c, long long n_switch, const double* capacitance, int sign) {
@@ -1218,6 +1384,7 @@ int dghex_get_voltages(const dghex_ctx* c, double* out, size_t n) {
 int dghex_state_save(const dghex_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return hfail(DGSEM_EINVAL, "NULL argument");
   if (!c->state_valid) return hfail(DGSEM_ESTATE, "no state to save");
+  if (c->has_pml) return hfail(DGSEM_ESTATE, "checkpoints of a state with a layer are not supported");
   const size_t es = c->prec == DGSEM_FP32_MIXED ? sizeof(float) : sizeof(double);
   const size_t field = (size_t)c->Bp * c->ndof * es;
   const size_t qb = (size_t)3 * c->batch * c->K * c->M * sizeof(double);
@@ -1356,6 +1523,11 @@ void dghex_destroy(dghex_ctx* c) {
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);
   dfree(c->d_step); dfree(c->d_done);
   dfree(c->d_damp64); dfree(c->d_damp32); dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
+  dfree(c->d_zeta64); dfree(c->d_zeta32); dfree(c->d_beta64); dfree(c->d_beta32); dfree(c->d_gamma64);
+  dfree(c->d_gamma32);
+  for (int k = 0; k < 2; ++k) {
+    dfree(c->dom[k].d_pml_elem); dfree(c->dom[k].d_pml_geo64); dfree(c->dom[k].d_pml_geo32);
+  }
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rnn);
   dfree(c->d_drive); dfree(c->d_traces);
   for (auto ev : c->ev_pool) cudaEventDestroy(ev);

@@ -225,9 +225,34 @@ struct HexUpdateArgs {
   int Bp;
   const int* node_ptr; const int* node_slot;
   const T* Minv;
-  const T* damp;             // C_jj / M_jj of absorbing faces, or NULL: v += cv (damp v + M^-1 r)
+  const T* damp;             // C_jj / M_jj + alpha_j (absorbing faces, layers), or NULL
+  // perfectly matched layers (or NULL): v += cv (beta p + gamma psi_int) with
+  // psi_int = psi + hpsi p_in, then psi += dpsi p_in
+  const T* beta; const T* gamma; T* psi;
+  T hpsi, dpsi;
   long long ndof;
   T cv, cp;
+};
+
+// Step: one layer element per CTA (one node per thread): Phi^{n+1/2} ->
+// Phi^{n+3/2} by Crank-Nicolson and the residual G (Phi^{n+1/2} + Phi^{n+3/2})/2
+// into the element's layer slots.
+template <typename T>
+struct HexPmlArgs {
+  const T* p;                // p^{n+1}
+  const T* psi;              // psi^{n+1/2}
+  T* phi;                    // [npml][3][n^3][Bp]
+  T* S;
+  int Bp;
+  const int* elem;           // [npml] element ids
+  const int* conn;           // [ne][n^3]
+  const T* geo;              // [npml][10][n^3]: J^-1 (row-major), w |J|
+  const T* zeta;             // [3][ndof]
+  long long ndof;
+  long long slot_base;       // first layer slot of this domain (element-major)
+  int npml;
+  T c2, dt;
+  T D[MAXN1][MAXN1];
 };
 
 // Step tail: PMUT forcing slots kappa sum_m q''_km B_jm of every footprint
@@ -254,6 +279,7 @@ cudaError_t launch_match(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_ipoints(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_norm2(const double* x, long long n, double* out, cudaStream_t s);
 cudaError_t launch_scale(double* dst, const double* src, const double* norm2, long long n, cudaStream_t s);
+template <typename T> cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_update(const HexUpdateArgs<T>& a, cudaStream_t s);

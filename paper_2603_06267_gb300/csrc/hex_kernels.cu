@@ -256,6 +256,8 @@ __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float div_(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
 
 // Member-wise operations on a Pack.  FP32 packs of an even width use the
 // packed f32x2 instructions (two members per instruction); each lane rounds
@@ -870,9 +872,22 @@ __global__ void __launch_bounds__(256) hex_update_kernel(const __grid_constant__
   P r = vzero<T, BB>();
   for (int k = k0; k < k1; ++k) r = vadd(r, reinterpret_cast<const P*>(A.S + (long long)A.node_slot[k] * A.Bp)[ch]);
   P* vp = reinterpret_cast<P*>(A.v + j * A.Bp) + ch;
-  P pv = reinterpret_cast<const P*>(A.p_in + j * A.Bp)[ch], vv = *vp;
-  // damping of absorbing faces on the predicted velocity (C p'_pred of Algorithm 1)
+  const P pin = reinterpret_cast<const P*>(A.p_in + j * A.Bp)[ch];
+  P pv = pin, vv = *vp;
+  // damping on the predicted velocity: C p'_pred of Algorithm 1, alpha p'_pred of a layer
   if (A.damp) vfma(vv, mul_(A.cv, A.damp[j]), P(vv));
+  if (A.psi) {
+    // layer terms beta p^{n+1} + gamma psi^{n+1}, psi^{n+1} = psi^{n+1/2} + dt/2 p^{n+1}
+    P* sp = reinterpret_cast<P*>(A.psi + j * A.Bp) + ch;
+    const P ps = *sp;
+    P psi_int = ps;
+    vfma(psi_int, A.hpsi, pin);
+    vfma(vv, mul_(A.cv, A.beta[j]), pin);
+    vfma(vv, mul_(A.cv, A.gamma[j]), psi_int);
+    P pn = ps;
+    vfma(pn, A.dpsi, pin);
+    *sp = pn;
+  }
   vfma(vv, mul_(A.cv, mi), r);
   vfma(pv, A.cp, vv);
   *vp = vv;
@@ -924,6 +939,111 @@ __global__ void __launch_bounds__(256) hex_tail_kernel(const __grid_constant__ H
         __threadfence();
       }
     }
+  }
+}
+
+// Perfectly matched layer of eq. (full_problem) rows 1-3 on one element (the
+// reading of the box path): at every GLL node the physical gradients of
+// p^{n+1} and psi^{n+1} = psi^{n+1/2} + dt/2 p^{n+1} (J^-T grad^),
+//   Phi_d <- [(1 - dt z_d/2) Phi_d + dt c^2 ((alpha - 2 z_d) dp/dx_d
+//            + z_e z_f dpsi/dx_d)] / (1 + dt z_d/2),
+// and the element residual sum_q w |J| (Phi^{n+1/2} + Phi^{n+3/2})/2 . grad psi_j.
+template <typename T, int BB>
+__global__ void __launch_bounds__(1024) hex_pml_kernel(const __grid_constant__ HexPmlArgs<T> A, int n) {
+  using P = Pack<T, BB>;
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  const int nl = n * n * n;
+  P* u = reinterpret_cast<P*>(smem_raw);   // p^{n+1}
+  P* w = u + nl;                           // psi^{n+1}
+  P* F = w + nl;                           // [3][nl]
+  T* D = reinterpret_cast<T*>(F + 3 * nl); // [n][n]
+  const int i = threadIdx.x;
+  const int ep = blockIdx.x;
+  const int e = A.elem[ep];
+  if (i < n * n) D[i] = A.D[i / n][i % n];
+  const bool act = i < nl;
+  const int ia = i % n, ib = (i / n) % n, ic = i / (n * n);
+  long long node = 0;
+  T Ji[9], wJ = T(0), z[3] = {T(0), T(0), T(0)};
+  if (act) {
+    node = A.conn[(long long)e * nl + i];
+    const T* g = A.geo + (long long)ep * 10 * nl + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ji[k] = g[(long long)k * nl];
+    wJ = g[9LL * nl];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) z[d] = A.zeta[d * A.ndof + node];
+  }
+  const T alpha = add_(add_(z[0], z[1]), z[2]);
+  const T h = mul_(T(0.5), A.dt);
+  const int nch = A.Bp / BB;
+  for (int ch = 0; ch < nch; ++ch) {
+    if (act) {
+      const P pv = reinterpret_cast<const P*>(A.p + node * A.Bp)[ch];
+      P sv = reinterpret_cast<const P*>(A.psi + node * A.Bp)[ch];
+      vfma(sv, h, pv);
+      u[i] = pv;
+      w[i] = sv;
+    }
+    __syncthreads();
+    if (act) {
+      // reference gradients (difference form), then physical ones
+      P gp[3], gs[3];
+      for (int d = 0; d < 3; ++d) {
+        gp[d] = vzero<T, BB>();
+        gs[d] = vzero<T, BB>();
+      }
+      const P ui = u[i], wi = w[i];
+      for (int m = 0; m < n; ++m) {
+        const int k0 = ic * n * n + ib * n + m, k1 = ic * n * n + m * n + ia, k2 = m * n * n + ib * n + ia;
+        const T d0 = D[ia * n + m], d1 = D[ib * n + m], d2 = D[ic * n + m];
+        vfma(gp[0], d0, vsub(u[k0], ui));
+        vfma(gp[1], d1, vsub(u[k1], ui));
+        vfma(gp[2], d2, vsub(u[k2], ui));
+        vfma(gs[0], d0, vsub(w[k0], wi));
+        vfma(gs[1], d1, vsub(w[k1], wi));
+        vfma(gs[2], d2, vsub(w[k2], wi));
+      }
+      P favg[3];
+      for (int x = 0; x < 3; ++x) {
+        // d/dx_x = sum_d (J^-1)_{d x} d/dxi_d
+        P px = vmul(Ji[x], gp[0]), sx = vmul(Ji[x], gs[0]);
+        vfma(px, Ji[3 + x], gp[1]);
+        vfma(px, Ji[6 + x], gp[2]);
+        vfma(sx, Ji[3 + x], gs[1]);
+        vfma(sx, Ji[6 + x], gs[2]);
+        const T zx = z[x], z3 = mul_(z[(x + 1) % 3], z[(x + 2) % 3]);
+        const T a1 = sub_(T(1), mul_(h, zx)), den = add_(T(1), mul_(h, zx));
+        const T ca = mul_(mul_(A.dt, A.c2), sub_(alpha, mul_(T(2), zx))), cz = mul_(mul_(A.dt, A.c2), z3);
+        P* ph = reinterpret_cast<P*>(A.phi + (((long long)ep * 3 + x) * nl + i) * A.Bp) + ch;
+        const P old = *ph;
+        P nw = vmul(a1, old);
+        vfma(nw, ca, px);
+        vfma(nw, cz, sx);
+#pragma unroll
+        for (int b = 0; b < BB; ++b) nw.v[b] = div_(nw.v[b], den);
+        *ph = nw;
+        favg[x] = vmul(T(0.5), vadd(old, nw));
+      }
+      // F_d = w |J| sum_x (J^-1)_{d x} Phi_avg,x
+      for (int d = 0; d < 3; ++d) {
+        P f = vmul(Ji[3 * d], favg[0]);
+        vfma(f, Ji[3 * d + 1], favg[1]);
+        vfma(f, Ji[3 * d + 2], favg[2]);
+        F[d * nl + i] = vmul(wJ, f);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      P r = vzero<T, BB>();
+      for (int m = 0; m < n; ++m) {
+        vfma(r, D[m * n + ia], F[ic * n * n + ib * n + m]);
+        vfma(r, D[m * n + ib], F[nl + ic * n * n + m * n + ia]);
+        vfma(r, D[m * n + ic], F[2 * nl + m * n * n + ib * n + ia]);
+      }
+      reinterpret_cast<P*>(A.S + (A.slot_base + (long long)ep * nl + i) * A.Bp)[ch] = r;
+    }
+    __syncthreads();
   }
 }
 
@@ -1107,6 +1227,27 @@ cudaError_t launch_hex_tail(const HexTailArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T, int BB>
+cudaError_t pml_bb(const HexPmlArgs<T>& a, int n, cudaStream_t s) {
+  const int nl = n * n * n;
+  const size_t sm = sizeof(Pack<T, BB>) * 5 * (size_t)nl + sizeof(T) * n * n;
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(hex_pml_kernel<T, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  hex_pml_kernel<T, BB><<<a.npml, (nl + 31) / 32 * 32, sm, s>>>(a, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, cudaStream_t s) {
+  if (a.npml == 0 || a.Bp == 0) return cudaSuccess;
+  constexpr int V = vec_width<T>();
+  return (a.Bp % V == 0) ? pml_bb<T, V>(a, n, s) : pml_bb<T, 1>(a, n, s);
+}
+
+template cudaError_t launch_hex_pml<float>(const HexPmlArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_hex_pml<double>(const HexPmlArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_hex_vol<float>(const HexVolArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_hex_vol<double>(const HexVolArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_hex_iface<float>(const HexIfaceArgs<float>&, cudaStream_t);

@@ -17,7 +17,7 @@ from .dgsem import DGSEM_FP32_MIXED, DGSEM_FP64, DgsemError, _current_stream, _f
 
 EXPORTED = [
     "dghex_mesh_create", "dghex_get_dt", "dghex_nodes", "dghex_pmut_nodes", "dghex_pmut_set", "dghex_get_matches",
-    "dghex_set_absorbing_faces", "dghex_pmut_set_receive", "dghex_get_voltages", "dghex_state_save",
+    "dghex_set_absorbing_faces", "dghex_set_pml", "dghex_pmut_set_receive", "dghex_get_voltages", "dghex_state_save",
     "dghex_state_load",
     "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_check_stability", "dghex_set_interface_kernel",
     "dghex_profile",
@@ -60,6 +60,7 @@ def load_library():
     lib.dghex_get_pressure.argtypes = [vp, vp, c_size_t]
     lib.dghex_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
     lib.dghex_set_absorbing_faces.argtypes = [vp, c_int, c_int, vp]
+    lib.dghex_set_pml.argtypes = [vp, c_int, vp, c_double]
     lib.dghex_pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
     lib.dghex_get_voltages.argtypes = [vp, vp, c_size_t]
     lib.dghex_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
@@ -204,6 +205,14 @@ def dghex_set_absorbing_faces(ctx, domain: int, faces):
            "dghex_set_absorbing_faces")
 
 
+def dghex_set_pml(ctx, domain: int, thickness, R: float = 1e-4):
+    """Perfectly matched layers of the given thickness (m) along the sides
+    x-, x+, y-, y+, z-, z+ of a domain's bounding box, design reflection R."""
+    th = np.ascontiguousarray(thickness, dtype=np.float64)
+    assert th.shape == (6,)
+    _check(_lib.dghex_set_pml(ctx, domain, _ptr(th), float(R)), "dghex_set_pml")
+
+
 def dghex_pmut_set_receive(ctx, n_switch: int, capacitance=None, sign: int = -1):
     cap = None if capacitance is None else np.ascontiguousarray(capacitance, dtype=np.float64)
     _check(_lib.dghex_pmut_set_receive(ctx, int(n_switch), _ptr(cap), int(sign)), "dghex_pmut_set_receive")
@@ -272,6 +281,9 @@ class HexSolver:
         for d, faces in enumerate(getattr(workload, "absorbing_faces", None) or []):
             if faces is not None and len(faces):
                 dghex_set_absorbing_faces(self.ctx, d, faces)
+        for d, th in enumerate(getattr(workload, "pml", None) or []):
+            if th is not None and any(t > 0 for t in th):
+                dghex_set_pml(self.ctx, d, th, getattr(workload, "pml_R", 1e-4))
         self.dt, self.ndof = dghex_get_dt(self.ctx)
         self.K = 0
         if workload.pmuts is not None and workload.pmut_faces is not None:

@@ -343,3 +343,58 @@ def test_checkpoint_roundtrip_is_bitwise(lib, prec):
     assert np.array_equal(tail, full[:, :, 30:])
     assert np.array_equal(vtail, vfull[:, :, 30:])
     b.close()
+
+
+def _pml_workload(nsteps=60):
+    w = H.distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=nsteps)
+    w.pml = [(0.0, 25e-6, 0.0, 0.0, 0.0, 0.0), (50e-6, 0.0, 0.0, 50e-6, 0.0, 50e-6)]
+    w.pml_R = 1e-3
+    return w
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_pml_parity(lib, prec, tol):
+    """Layers on curved elements (primary x+, secondary x-, y+ and top):
+    driven traces and a run from a state with velocity, against the oracle."""
+    from paper_2603_06267_gb300 import dghex
+    w = _pml_workload()
+    prob = HO.HexOracleProblem(w)
+    assert prob.pml is not None and len(prob.pml["elems"]) > 0
+    s = dghex.HexSolver(w)
+    assert abs(s.dt - prob.stable_dt()) < 1e-15 * s.dt
+    tr = s.run(precision=prec)
+    ref = prob.run(dt=s.dt)
+    assert _rel(tr, ref) < tol, _rel(tr, ref)
+    xyz, first = dghex.dghex_nodes(s.ctx)
+    idx = _node_map(prob, xyz, first)
+    X = np.concatenate([m.coords for m in prob.meshes])
+    p0 = W.seeded_field(11, X[:, 0], X[:, 1], X[:, 2])
+    v0 = 2e6 * W.seeded_field(12, X[:, 0], X[:, 1], X[:, 2])
+    g0 = np.zeros(s.ndof); g0[idx] = p0
+    gv = np.zeros(s.ndof); gv[idx] = v0
+    dghex.dghex_set_state(s.ctx, g0, gv)
+    drive = np.zeros((1, w.pmuts.n_pmut, w.nsteps))
+    for B in (1, 9 if prec == 1 else 5):
+        tr = s.run(drive=np.zeros((B, w.pmuts.n_pmut, w.nsteps)), precision=prec, batch=B)
+        ref = prob.run(dt=s.dt, drive=drive, p0=p0, v0=v0)
+        for b in range(B):
+            assert _rel(tr[b], ref[0]) < tol, (B, b, _rel(tr[b], ref[0]))
+    s.close()
+
+
+def test_pml_checkpoint_refused_and_removal(lib):
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w = _pml_workload(nsteps=5)
+    s = dghex.HexSolver(w)
+    dt_layer = s.dt
+    s.run(precision=0)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_state_save(s.ctx)
+    assert e.value.code == dgsem.DGSEM_ESTATE
+    for d in range(2):
+        dghex.dghex_set_pml(s.ctx, d, np.zeros(6), 1e-3)
+    dt, _ = dghex.dghex_get_dt(s.ctx)
+    assert dt >= dt_layer
+    s.run(precision=0)
+    assert len(dghex.dghex_state_save(s.ctx)) > 0
+    s.close()
