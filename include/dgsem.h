@@ -237,7 +237,9 @@ int dgsem_get_voltages(const dgsem_ctx* ctx, double* out, size_t n);
  *   stream     cudaStream_t to order the work on (NULL = legacy default
  *              stream); the call returns after the stream has finished.
  * Without DGSEM_RUN_CONTINUE the state restarts from rest (or from the state
- * given by the last dgsem_set_state/dgsem_state_load) and n0 = 0. */
+ * given by the last dgsem_set_state/dgsem_state_load) and n0 = 0.
+ * Returns DGSEM_EUNSTABLE when the receiver traces or the PMUT state are not
+ * finite at the end of the run (the step diverged); the state is then invalid. */
 int dgsem_run(dgsem_ctx* ctx, int precision, int batch, int nsteps, const double* drive,
               int n_recv, const double* recv_xyz, double* traces, int flags, void* stream);
 

@@ -142,6 +142,7 @@ struct dgsem_ctx {
   bool has_tmap_v[2] = {false, false};
   int tile_pref[2][2] = {{0, 0}, {0, 0}};   // [fp64, fp32][box] tile-shape variant
   int* d_err = nullptr;
+  int* d_nf = nullptr;                        // non-finite flag of the divergence check
   int* d_step = nullptr;                      // step counter of the current run
   // CUDA graph of a block of steps, replayed by dgsem_run
   cudaStream_t cap_stream = nullptr;
@@ -927,14 +928,24 @@ int run_prepare(dgsem_ctx* c, int nsteps, const double* drive, int R, double* tr
 // Traces back to the host if needed, timings, device status word.
 int run_finish(dgsem_ctx* c, int nsteps, const RunIO& io, cudaStream_t s) {
   c->step += nsteps;
+  // divergence check: receiver traces (they sample p every step) and the PMUT state
+  if (!c->d_nf) CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&c->d_nf), sizeof(int)));
+  CUDA_TRY(cudaMemsetAsync(c->d_nf, 0, sizeof(int), s));
+  CUDA_TRY(launch_nonfinite(io.d_tr, io.tr_n, c->d_nf, s));
+  if (c->q_state) CUDA_TRY(launch_nonfinite(c->q_state, (size_t)3 * c->batch * c->K * c->M, c->d_nf, s));
   if (io.host_tr) CUDA_TRY(cudaMemcpyAsync(io.host_tr, io.d_tr, io.tr_n * sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
   collect_timings(c);
-  int err = 0;
+  int err = 0, nf = 0;
   CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&nf, c->d_nf, sizeof(int), cudaMemcpyDeviceToHost));
   if (err) {
     c->state_valid = false;
     return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up (status %d); the state is invalid", err);
+  }
+  if (nf) {
+    c->state_valid = false;
+    return fail(DGSEM_EUNSTABLE, "non-finite receiver traces or PMUT state: the time step diverged (dt above the stability limit?)");
   }
   return DGSEM_OK;
 }
@@ -1820,7 +1831,7 @@ void dgsem_destroy(dgsem_ctx* c) {
   dfree(c->d_ent_pmut); dfree(c->d_modal);
   dfree(c->d_drive); dfree(c->d_traces);
   dfree(c->d_rw); dfree(c->d_roff); dfree(c->d_rdom); dfree(c->d_rnn);
-  dfree(c->d_err);
+  dfree(c->d_err); dfree(c->d_nf);
   dfree(c->d_step);
   dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
   for (int d = 0; d < 2; ++d) {

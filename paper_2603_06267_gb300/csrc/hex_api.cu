@@ -291,6 +291,7 @@ struct dghex_ctx {
   double* q_state = nullptr;
   bool state_valid = false;
   int* d_step = nullptr; unsigned* d_done = nullptr;
+  int* d_nf = nullptr;                      // non-finite flag of the divergence check
   std::vector<double> init_p, init_v;
   bool has_init = false;
   // receivers and scratch for host-pointer runs
@@ -855,10 +856,20 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
     int rc = launch_step<T>(c, s, d_drive, (long long)c->K * nsteps, nsteps, R, d_traces, (long long)R * nsteps, nsteps);
     if (rc) return rc;
   }
+  // divergence check: receiver traces (they sample p every step) and the PMUT state
+  HCUDA(cudaMemsetAsync(c->d_nf, 0, sizeof(int), s));
+  if (R > 0) HCUDA(launch_nonfinite(d_traces, tn, c->d_nf, s));
+  if (c->q_state) HCUDA(launch_nonfinite(c->q_state, (size_t)3 * c->batch * c->K * c->M, c->d_nf, s));
   if (host_traces) HCUDA(cudaMemcpyAsync(traces_out, d_traces, tn * sizeof(double), cudaMemcpyDeviceToHost, s));
   HCUDA(cudaStreamSynchronize(s));
   if (c->profiling) collect_timings(c);
   else c->ev_used.clear();
+  int nf = 0;
+  HCUDA(cudaMemcpy(&nf, c->d_nf, sizeof(int), cudaMemcpyDeviceToHost));
+  if (nf) {
+    c->state_valid = false;
+    return hfail(DGSEM_EUNSTABLE, "non-finite receiver traces or PMUT state: the time step diverged (dt above the stability limit?)");
+  }
   c->state_valid = true;
   c->steps_done += nsteps;
   return DGSEM_OK;
@@ -1021,7 +1032,8 @@ int dghex_mesh_create(const dghex_mesh_desc* d, dghex_ctx** out) {
   setup_pmut_nodes(c, pf);
   if ((rc = build_slots(c)) || (rc = dmalloc(&c->d_M, sizeof(double) * c->ndof)) ||
       (rc = dmalloc(&c->d_Minv64, sizeof(double) * c->ndof)) || (rc = dmalloc(&c->d_Minv32, sizeof(float) * c->ndof)) ||
-      (rc = dmalloc(&c->d_step, sizeof(int))) || (rc = dmalloc(&c->d_done, sizeof(unsigned)))) {
+      (rc = dmalloc(&c->d_step, sizeof(int))) || (rc = dmalloc(&c->d_done, sizeof(unsigned))) ||
+      (rc = dmalloc(&c->d_nf, sizeof(int)))) {
     dghex_destroy(c);
     return rc;
   }
@@ -1521,7 +1533,7 @@ void dghex_destroy(dghex_ctx* c) {
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
   dfree(c->d_node_ptr); dfree(c->d_node_slot);
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);
-  dfree(c->d_step); dfree(c->d_done);
+  dfree(c->d_step); dfree(c->d_done); dfree(c->d_nf);
   dfree(c->d_damp64); dfree(c->d_damp32); dfree(c->d_rx_gain); dfree(c->d_step_base); dfree(c->d_volt);
   dfree(c->d_zeta64); dfree(c->d_zeta32); dfree(c->d_beta64); dfree(c->d_beta32); dfree(c->d_gamma64);
   dfree(c->d_gamma32);

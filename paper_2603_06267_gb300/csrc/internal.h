@@ -283,6 +283,9 @@ cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pml(const PmlArgs<T>& a, int batch, cudaStream_t s);
 // one warp waiting on an mbarrier nothing arrives at (bounded; sets *err = 3)
+// Sets *flag to 1 if any of x[0..n) is not finite (NaN or Inf); *flag is
+// left unchanged otherwise.
+cudaError_t launch_nonfinite(const double* x, size_t n, int* flag, cudaStream_t s);
 cudaError_t launch_wait_probe(int* err, long long budget, cudaStream_t s);
 template <typename T>
 cudaError_t launch_face_asm(const FaceAsmArgs<T>& a, int batch, cudaStream_t s);

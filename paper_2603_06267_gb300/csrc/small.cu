@@ -605,6 +605,20 @@ cudaError_t launch_iface(const IfaceArgs<T>& a, int batch, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(256) nonfinite_kernel(const double* x, size_t n, int* flag) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad = bad || !isfinite(x[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+cudaError_t launch_nonfinite(const double* x, size_t n, int* flag, cudaStream_t s) {
+  if (n == 0 || !x) return cudaSuccess;
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 1216);
+  nonfinite_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, flag);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_pmut_recv(const PmutArgs<T>& a, cudaStream_t s) {
   const long long warps = (long long)a.B * a.K + (long long)a.B * a.R;

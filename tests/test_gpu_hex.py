@@ -433,3 +433,15 @@ def test_full_size_distorted_mesh_properties(lib):
     t64 = s.run(drive=np.ascontiguousarray(d1[:1]), precision=0, batch=1)
     assert _rel(t1[0], t64[0]) < FP32_TOL
     s.close()
+
+
+def test_diverging_run_is_reported(lib):
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w = H.distorted_one_domain(nel=(3, 2, 2), order=4, nsteps=600)
+    dt = HO.HexOracleProblem(w).stable_dt()
+    bad = dghex.HexSolver(w, dt=4.0 * dt)
+    for prec in (0, 1):
+        with pytest.raises(dgsem.DgsemError) as e:
+            bad.run(precision=prec)
+        assert e.value.code == dgsem.DGSEM_EUNSTABLE
+    bad.close()

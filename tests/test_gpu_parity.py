@@ -381,3 +381,22 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
     tg = sol.run(drive=drive, precision=0)
     sol.close()
     assert rel_l2(tg, to) < FP64_TOL
+
+
+def test_diverging_run_is_reported():
+    """A time step far above the stability limit makes the run overflow; the
+    run returns DGSEM_EUNSTABLE instead of non-finite traces, and a stable
+    context is unaffected."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_one_domain(nel=(3, 2, 2), order=4, nsteps=600)
+    dt = oracle_problem(w).stable_dt()
+    bad = dgsem.Solver(w, dt=4.0 * dt)
+    for prec in (0, 1):
+        with pytest.raises(dgsem.DgsemError) as e:
+            bad.run(precision=prec)
+        assert e.value.code == dgsem.DGSEM_EUNSTABLE
+    bad.close()
+    ok = gpu_solver(w)
+    tr = ok.run(precision=0, nsteps=50)
+    assert np.all(np.isfinite(tr))
+    ok.close()
