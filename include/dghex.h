@@ -178,6 +178,13 @@ int dghex_run(dghex_ctx* ctx, int precision, int batch, int nsteps, const double
  * (C: absorbing faces). */
 int dghex_set_state(dghex_ctx* ctx, const double* p0, const double* v0);
 
+/* Leapfrog energy of the acoustic field of every batch member after the
+ * last run (FP64 state only; diagnostics): e[b] = 1/2 v^T M v + 1/2 p^n^T K
+ * p^{n+1} with v = v^{n+1/2}, K the stiffness with the interface terms (no
+ * PMUT coupling, absorbing or layer terms).  Algorithm 1 conserves it
+ * exactly without forcing and damping.  e holds n >= batch values. */
+int dghex_energy(dghex_ctx* ctx, double* e, int n);
+
 /* Pressure p^n of every batch member after the last run, [batch][ndof]. */
 int dghex_get_pressure(const dghex_ctx* ctx, double* p, size_t len);
 

@@ -261,6 +261,13 @@ int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* bat
  * pointer may be NULL (zero). */
 int dgsem_set_state(dgsem_ctx* ctx, const double* p0, const double* v0);
 
+/* Leapfrog energy of the acoustic field of every batch member after the
+ * last run (FP64 state only; diagnostics): e[b] = 1/2 v^T M v + 1/2
+ * p^n^T K p^{n+1} with v = v^{n+1/2} and K the stiffness with the interface
+ * terms (no PMUT coupling, absorbing or layer terms); Algorithm 1 conserves
+ * it exactly without forcing and damping.  e holds n >= batch values. */
+int dgsem_energy(dgsem_ctx* ctx, double* e, int n);
+
 /* Current pressure field p^n of every batch member after the last run, as
  * FP64 host array [batch][ndof] (node order above). */
 int dgsem_get_pressure(const dgsem_ctx* ctx, double* p, size_t len);

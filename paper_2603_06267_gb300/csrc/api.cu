@@ -1631,6 +1631,84 @@ int dgsem_state_load(dgsem_ctx* c, const void* buf, size_t len) {
   return DGSEM_OK;
 }
 
+int dgsem_energy(dgsem_ctx* c, double* e, int n) {
+  if (!c || !e) return fail(DGSEM_EINVAL, "NULL argument");
+  if (!c->state_valid) return fail(DGSEM_ESTATE, "no state: run first");
+  if (c->prec != DGSEM_FP64) return fail(DGSEM_ESTATE, "the energy diagnostic needs an FP64 state");
+  if (n < c->batch) return fail(DGSEM_EINVAL, "e holds %d values, %d needed", n, c->batch);
+  int rc = refresh_tmaps(c);
+  if (rc) return rc;
+  cudaStream_t s = 0;
+  std::vector<double*> tmp;
+  auto cleanup = [&]() { for (double* p : tmp) cudaFree(p); };
+  // W = -M^-1 K p^{n+1} (volume kernel on Y with v = 0, dtv = 1, dtp = 0, no
+  // forcing, absorbing or layer terms), P2 receives the unchanged p_out
+  double* W[2] = {nullptr, nullptr};
+  double* P2[2] = {nullptr, nullptr};
+  double* w1[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  double* d_red = nullptr;
+  if ((rc = dalloc(&d_red, 2 * sizeof(double) * c->batch))) return rc;
+  tmp.push_back(d_red);
+  for (int d = 0; d < c->nd; ++d) {
+    const size_t bytes = (size_t)c->batch * c->box[d].bstride * sizeof(double);
+    if ((rc = dalloc(&W[d], bytes)) || (rc = dalloc(&P2[d], bytes))) { cleanup(); return rc; }
+    tmp.push_back(W[d]);
+    tmp.push_back(P2[d]);
+    CUDA_TRY(cudaMemsetAsync(W[d], 0, bytes, s));
+    for (int k = 0; k < 3; ++k) {
+      std::vector<double> w(c->box[d].L[k]);
+      for (int i = 0; i < c->box[d].L[k]; ++i) w[i] = c->box[d].basis->assembled_weight(i, c->box[d].ne[k]);
+      if ((rc = upload(&w1[d][k], w))) { cleanup(); return rc; }
+      tmp.push_back(w1[d][k]);
+    }
+  }
+  CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+  if (c->has_iface) {
+    IfaceArgs<double> a = iface_args<double>(c);
+    a.pp = static_cast<const double*>(c->Y[0]);
+    a.ps = static_cast<const double*>(c->Y[1]);
+    CUDA_TRY(launch_iface<double>(a, c->batch, s));
+    if ((rc = launch_face_assembly<double>(c, s, c->batch, false))) { cleanup(); return rc; }
+  }
+  for (int d = 0; d < c->nd; ++d) {
+    VolSpec v = c->vspec[d];
+    v.has_abc = 0;
+    v.has_pml = 0;
+    v.has_pmut = 0;
+    v.tmap = &c->tmap_y[d];
+    v.tmap_v = nullptr;
+    v.err = c->d_err;
+    v.tile = c->tile_pref[0][d];
+    v.step = nullptr;
+    v.p_in = c->Y[d]; v.p_out = P2[d]; v.v = W[d];
+    v.dtv = 1.0; v.dtp = 0.0;
+    v.ga = c->Ga[d]; v.gb = c->Gb[d];
+    v.gbs = (long long)c->box[d].L[1] * c->box[d].py;
+    CUDA_TRY(launch_vol<double>(v, c->batch, s));
+  }
+  // e_b = 1/2 v.M v + 1/2 p^n.K p^{n+1} = 1/2 (v.M v - p^n.M W)
+  CUDA_TRY(cudaMemsetAsync(d_red, 0, 2 * sizeof(double) * c->batch, s));
+  for (int b = 0; b < c->batch; ++b)
+    for (int d = 0; d < c->nd; ++d) {
+      const Box& B = c->box[d];
+      const long long o = (long long)b * B.bstride;
+      const double scale = B.h[0] * B.h[1] * B.h[2] / 8.0;
+      const double* V = static_cast<const double*>(c->V[d]) + o;
+      const double* X = static_cast<const double*>(c->X[d]) + o;
+      CUDA_TRY(launch_mdot(V, V, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale, d_red + 2 * b, s));
+      CUDA_TRY(launch_mdot(X, W[d] + o, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
+                           d_red + 2 * b + 1, s));
+    }
+  std::vector<double> red(2 * (size_t)c->batch);
+  CUDA_TRY(cudaMemcpy(red.data(), d_red, red.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  int err = 0;
+  CUDA_TRY(cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  cleanup();
+  if (err) return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up during the energy diagnostic");
+  for (int b = 0; b < c->batch; ++b) e[b] = 0.5 * (red[2 * b] - red[2 * b + 1]);
+  return DGSEM_OK;
+}
+
 int dgsem_check_stability(dgsem_ctx* c, int iters, double* lambda_max) {
   if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
   if (iters < 1) return fail(DGSEM_EINVAL, "iters must be >= 1");

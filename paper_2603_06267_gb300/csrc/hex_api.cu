@@ -670,11 +670,12 @@ int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
 
 // pml: 0 no layer terms, 1 set-state start (psi stays 0), 2 time step
 template <typename T>
-int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void* p_in, void* p_out, int pml = 0) {
+int launch_update(dghex_ctx* c, cudaStream_t s, double cv, double cp, const void* p_in, void* p_out, int pml = 0,
+                  void* v = nullptr) {
   hex::HexUpdateArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   a.p_in = static_cast<const T*>(p_in); a.p_out = static_cast<T*>(p_out);
-  a.v = static_cast<T*>(c->V); a.S = static_cast<const T*>(c->S);
+  a.v = static_cast<T*>(v ? v : c->V); a.S = static_cast<const T*>(c->S);
   a.Bp = c->Bp;
   a.node_ptr = c->d_node_ptr; a.node_slot = c->d_node_slot;
   a.Minv = std::is_same<T, float>::value ? reinterpret_cast<const T*>(c->d_Minv32) : reinterpret_cast<const T*>(c->d_Minv64);
@@ -1449,6 +1450,43 @@ int dghex_state_load(dghex_ctx* c, const void* buf, size_t len) {
   if (qb) HCUDA(cudaMemcpy(c->q_state, o, qb, cudaMemcpyHostToDevice));
   c->steps_done = h.steps;
   c->state_valid = true;
+  return DGSEM_OK;
+}
+
+int dghex_energy(dghex_ctx* c, double* e, int n) {
+  if (!c || !e) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (!c->state_valid) return hfail(DGSEM_ESTATE, "no state: run first");
+  if (c->prec != DGSEM_FP64) return hfail(DGSEM_ESTATE, "the energy diagnostic needs an FP64 state");
+  if (n < c->batch) return hfail(DGSEM_EINVAL, "e holds %d values, %d needed", n, c->batch);
+  cudaStream_t s = 0;
+  const size_t field = sizeof(double) * (size_t)c->Bp * c->ndof;
+  double* w = nullptr;
+  double* d_e = nullptr;
+  int rc;
+  if ((rc = dmalloc(&w, field)) || (rc = dmalloc(&d_e, sizeof(double) * c->batch))) {
+    dfree(w);
+    return rc;
+  }
+  // w = M^-1 K p^{n+1}: the stiffness and interface slots of Y gathered by the
+  // update kernel into a zero field (forcing and layer slots cleared: K only)
+  cudaError_t err = cudaMemsetAsync(w, 0, field, s);
+  if (err == cudaSuccess && c->nslot > c->fslot0)
+    err = cudaMemsetAsync(static_cast<double*>(c->S) + (size_t)c->fslot0 * c->Bp, 0,
+                          sizeof(double) * (size_t)c->Bp * (c->nslot - c->fslot0), s);
+  if (err == cudaSuccess) {
+    const double* dsave = c->d_damp64;
+    c->d_damp64 = nullptr;                  // K only: no damping on the (zero) scratch velocity
+    rc = launch_residual<double>(c, s, c->Y);
+    if (!rc) rc = launch_update<double>(c, s, 1.0, 0.0, c->Y, c->Y, 0, w);
+    c->d_damp64 = const_cast<double*>(dsave);
+    if (!rc) err = hex::launch_energy(c->d_M, static_cast<const double*>(c->V), static_cast<const double*>(c->X), w,
+                                      c->ndof, c->batch, c->Bp, d_e, s);
+  }
+  if (!rc && err == cudaSuccess) err = cudaMemcpy(e, d_e, sizeof(double) * c->batch, cudaMemcpyDeviceToHost);
+  dfree(w);
+  dfree(d_e);
+  if (rc) return rc;
+  if (err != cudaSuccess) return hfail(DGSEM_ECUDA, "energy: %s", cudaGetErrorString(err));
   return DGSEM_OK;
 }
 

@@ -278,6 +278,8 @@ cudaError_t launch_faces(const FaceArgs& a, cudaStream_t s);
 cudaError_t launch_match(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_ipoints(const MatchArgs& a, cudaStream_t s);
 cudaError_t launch_norm2(const double* x, long long n, double* out, cudaStream_t s);
+cudaError_t launch_energy(const double* M, const double* v, const double* p, const double* w, long long ndof, int B,
+                          int Bp, double* e, cudaStream_t s);
 cudaError_t launch_scale(double* dst, const double* src, const double* norm2, long long n, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s);

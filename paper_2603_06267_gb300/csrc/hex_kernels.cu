@@ -1071,6 +1071,34 @@ __global__ void __launch_bounds__(256) scale_kernel(double* dst, const double* s
     dst[i] = src[i] * s;
 }
 
+// e[b] += 1/2 sum_j M_j (v_jb^2 + p_jb w_jb) over a field [ndof][Bp] (energy diagnostic)
+__global__ void __launch_bounds__(256) energy_kernel(const double* M, const double* v, const double* p, const double* w,
+                                                   long long ndof, int B, int Bp, double* e) {
+  const int b = blockIdx.y;
+  double s = 0.0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < ndof; j += (long long)gridDim.x * blockDim.x) {
+    const long long o = j * Bp + b;
+    s += M[j] * (v[o] * v[o] + p[o] * w[o]);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[8];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws[k];
+    atomicAdd(e + b, 0.5 * t);
+  }
+}
+
+cudaError_t launch_energy(const double* M, const double* v, const double* p, const double* w, long long ndof, int B,
+                          int Bp, double* e, cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(e, 0, sizeof(double) * B, s);
+  if (err != cudaSuccess || B == 0) return err;
+  energy_kernel<<<dim3(304, B), 256, 0, s>>>(M, v, p, w, ndof, B, Bp, e);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm2(const double* x, long long n, double* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
   if (e != cudaSuccess) return e;

@@ -19,7 +19,8 @@ EXPORTED = [
     "dghex_mesh_create", "dghex_get_dt", "dghex_nodes", "dghex_pmut_nodes", "dghex_pmut_set", "dghex_get_matches",
     "dghex_set_absorbing_faces", "dghex_set_pml", "dghex_pmut_set_receive", "dghex_get_voltages", "dghex_state_save",
     "dghex_state_load",
-    "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_check_stability", "dghex_set_interface_kernel",
+    "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_energy", "dghex_check_stability",
+    "dghex_set_interface_kernel",
     "dghex_profile",
     "dghex_kernel_stats", "dghex_destroy",
 ]
@@ -59,6 +60,7 @@ def load_library():
     lib.dghex_set_state.argtypes = [vp, vp, vp]
     lib.dghex_get_pressure.argtypes = [vp, vp, c_size_t]
     lib.dghex_check_stability.argtypes = [vp, c_int, POINTER(c_double)]
+    lib.dghex_energy.argtypes = [vp, vp, c_int]
     lib.dghex_set_absorbing_faces.argtypes = [vp, c_int, c_int, vp]
     lib.dghex_set_pml.argtypes = [vp, c_int, vp, c_double]
     lib.dghex_pmut_set_receive.argtypes = [vp, c_longlong, vp, c_int]
@@ -235,6 +237,13 @@ def dghex_state_save(ctx) -> bytes:
 def dghex_state_load(ctx, blob: bytes):
     buf = ctypes.create_string_buffer(blob, len(blob))
     _check(_lib.dghex_state_load(ctx, buf, len(blob)), "dghex_state_load")
+
+
+def dghex_energy(ctx, batch: int) -> np.ndarray:
+    """Leapfrog energy 1/2 v.M v + 1/2 p^n.K p^{n+1} of each batch member (FP64 state)."""
+    out = np.zeros(batch)
+    _check(_lib.dghex_energy(ctx, _ptr(out), batch), "dghex_energy")
+    return out
 
 
 def dghex_check_stability(ctx, iters: int = 100):

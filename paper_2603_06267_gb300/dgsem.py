@@ -32,7 +32,8 @@ DGSEM_RUN_CONTINUE = 1
 EXPORTED = [
     "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_set_pml", "dgsem_selftest_wait", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "pmut_set_receive", "dgsem_get_voltages",
-    "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_state_save", "dgsem_state_load",
+    "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_energy", "dgsem_state_save",
+    "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
     "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
 ]
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_run_multi.argtypes = [c_int, vp, c_int, vp, c_int, vp, vp, vp, vp, c_int, vp]
     lib.dgsem_set_state.argtypes = [vp, vp, vp]
     lib.dgsem_get_pressure.argtypes = [vp, vp, c_size_t]
+    lib.dgsem_energy.argtypes = [vp, vp, c_int]
     lib.dgsem_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
     lib.dgsem_state_load.argtypes = [vp, vp, c_size_t]
     lib.dgsem_num_tiles.argtypes = [vp, c_int, c_int, POINTER(c_int)]
@@ -293,6 +295,13 @@ def dgsem_set_state(ctx, p0=None, v0=None):
 def dgsem_get_pressure(ctx, batch: int, ndof: int) -> np.ndarray:
     out = np.zeros((batch, ndof))
     _check(_lib.dgsem_get_pressure(ctx, _ptr(out), out.size), "dgsem_get_pressure")
+    return out
+
+
+def dgsem_energy(ctx, batch: int) -> np.ndarray:
+    """Leapfrog energy 1/2 v.M v + 1/2 p^n.K p^{n+1} of each batch member (FP64 state)."""
+    out = np.zeros(batch)
+    _check(_lib.dgsem_energy(ctx, _ptr(out), batch), "dgsem_energy")
     return out
 
 

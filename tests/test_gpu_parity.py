@@ -400,3 +400,32 @@ def test_diverging_run_is_reported():
     tr = ok.run(precision=0, nsteps=50)
     assert np.all(np.isfinite(tr))
     ok.close()
+
+
+def test_energy_diagnostic_matches_oracle_and_is_conserved():
+    """dgsem_energy after a run equals the oracle's leapfrog energy
+    1/2 v.M v + 1/2 p^n.K p^{n+1}, and stays constant over a continued run
+    (acoustic field, 2:1 interface, no forcing)."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, nsteps=60)
+    w.pmuts = None
+    P = oracle_problem(w)
+    X = np.column_stack(P.all_coordinates())
+    p0 = W.seeded_field(3, X[:, 0], X[:, 1], X[:, 2])
+    v0 = 1e6 * W.seeded_field(4, X[:, 0], X[:, 1], X[:, 2])
+    sol = gpu_solver(w)
+    dgsem.dgsem_set_state(sol.ctx, p0, v0)
+    sol.run(precision=0, batch=2)
+    e1 = dgsem.dgsem_energy(sol.ctx, 2)
+    _, eo = P.run(dt=sol.dt, p0=p0, v0=v0, energy=True, batch=1)
+    ref = eo[-1, 0, 0]
+    # (the reduction adds with atomics: members agree to rounding, not bit for bit)
+    assert abs(e1[0] - ref) < 1e-10 * abs(ref) and abs(e1[1] - e1[0]) < 1e-14 * abs(e1[0])
+    sol.run(precision=0, batch=2, nsteps=150, flags=dgsem.DGSEM_RUN_CONTINUE)
+    e2 = dgsem.dgsem_energy(sol.ctx, 2)
+    assert abs(e2[0] - e1[0]) < 1e-12 * abs(e1[0])
+    sol.run(precision=1, batch=1, nsteps=5)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_energy(sol.ctx, 1)
+    assert e.value.code == dgsem.DGSEM_ESTATE
+    sol.close()
