@@ -437,11 +437,11 @@ def main_hex(args, torch, dist, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        launches = sum(dghex.dghex_kernel_stats(sol.ctx, k)[1] for k in range(5))
+        launches = sum(dghex.dghex_kernel_stats(sol.ctx, k)[1] for k in range(6))
         dghex.dghex_profile(sol.ctx, True)
         sol.run(drive=d_time, precision=prec, nsteps=args.steps, traces=tr_time, flags=dghex._dg.DGSEM_RUN_CONTINUE,
                 stream=stream.cuda_stream)
-        kstats = [dghex.dghex_kernel_stats(sol.ctx, k) for k in range(5)]
+        kstats = [dghex.dghex_kernel_stats(sol.ctx, k) for k in range(6)]
         dghex.dghex_profile(sol.ctx, False)
         e2e = None
         if not args.no_e2e:
@@ -456,7 +456,7 @@ def main_hex(args, torch, dist, rank, world, local):
                    "h2d_bytes_per_step": int(B * K_p * 8), "d2h_bytes_per_step": int(B * R * 8)}
     finite = bool(torch.isfinite(tr_time).all().item())
     value = whole_job_rate(ndof, B, args.steps, 1, ms / 1e3)
-    names = ["pmut", "vol", "iface", "update", "tail"]
+    names = ["pmut", "vol", "iface", "update", "tail", "pml"]
     es = 4 if prec == dghex.DGSEM_FP32_MIXED else 8
     # algorithmic bytes per launch (DRAM, the work each kernel must move)
     nl = [(d.order + 1) ** 3 for d in w.domains]
@@ -490,7 +490,7 @@ def main_hex(args, torch, dist, rank, world, local):
                    "parallelism": "single-gpu",
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cs.summary(local),
-        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(5) if kstats[k][1]},
+        "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(6) if kstats[k][1]},
         "finite": finite,
     }
     print(json.dumps(out), flush=True)

@@ -212,7 +212,8 @@ int dghex_set_interface_kernel(dghex_ctx* ctx, int general);
 #define DGHEX_K_IFACE 2      /* interface fluxes                                  */
 #define DGHEX_K_UPDATE 3     /* assembly of the element residuals + leapfrog update */
 #define DGHEX_K_TAIL 4       /* PMUT forcing rows + receiver sampling             */
-#define DGHEX_K_COUNT 5
+#define DGHEX_K_PML 5        /* perfectly matched layer elements                  */
+#define DGHEX_K_COUNT 6
 int dghex_profile(dghex_ctx* ctx, int enable);
 int dghex_kernel_stats(const dghex_ctx* ctx, int kind, double* total_ms, long long* launches);
 

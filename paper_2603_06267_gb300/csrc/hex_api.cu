@@ -764,7 +764,7 @@ int launch_step(dghex_ctx* c, cudaStream_t s, const double* drive, long long dbs
     a.c2 = T(D.c * D.c); a.dt = T(c->dt);
     for (int i = 0; i < D.n; ++i)
       for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
-    HexTimer t(c, s, DGHEX_K_VOL);
+    HexTimer t(c, s, DGHEX_K_PML);
     HCUDA(hex::launch_hex_pml<T>(a, D.n, s));
   }
   if ((rc = launch_update<T>(c, s, -c->dt, c->dt, c->Y, c->X, 2))) return rc;

@@ -24,7 +24,7 @@ EXPORTED = [
     "dghex_profile",
     "dghex_kernel_stats", "dghex_destroy",
 ]
-DGHEX_K_PMUT, DGHEX_K_VOL, DGHEX_K_IFACE, DGHEX_K_UPDATE, DGHEX_K_TAIL = 0, 1, 2, 3, 4
+DGHEX_K_PMUT, DGHEX_K_VOL, DGHEX_K_IFACE, DGHEX_K_UPDATE, DGHEX_K_TAIL, DGHEX_K_PML = 0, 1, 2, 3, 4, 5
 
 
 class HexDomainDesc(ctypes.Structure):
