@@ -850,9 +850,6 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
   }
   HCUDA(cudaMemsetAsync(c->d_step, 0, sizeof(int), s));
   HCUDA(cudaMemsetAsync(c->d_done, 0, sizeof(unsigned), s));
-  if (c->profiling) {
-    for (int k = 0; k < DGHEX_K_COUNT; ++k) c->kernel_ms[k] += 0.0;
-  }
   for (int n = 0; n < nsteps; ++n) {
     int rc = launch_step<T>(c, s, d_drive, (long long)c->K * nsteps, nsteps, R, d_traces, (long long)R * nsteps, nsteps);
     if (rc) return rc;
