@@ -472,3 +472,30 @@ def test_energy_diagnostic_matches_oracle_and_is_conserved(lib):
     e2 = dghex.dghex_energy(s.ctx, 5)
     assert abs(e2[0] - e1[0]) < 1e-12 * abs(e1[0])
     s.close()
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_unstructured_nonconforming_interface_parity(lib, general):
+    """3:2 flat interface between independently distorted tilings (fine faces
+    straddle coarse faces, so a fine face splits into several groups):
+    Algorithm 3 on the GPU equals the oracle's, and FP64 / FP32 traces match
+    with both interface kernels."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.distorted_two_domain(nx_p=6, nz_p=1, nx_s=4, nz_s=2, bump=0.0, n_pmut_side=2, order_p=3, order_s=4,
+                               nsteps=50, batch=9, steer=True)
+    prob = HO.HexOracleProblem(w)
+    s = dghex.HexSolver(w)
+    dghex.dghex_set_interface_kernel(s.ctx, general)
+    q, cf, ref = dghex.dghex_get_matches(s.ctx, len(w.fine_faces))
+    split = 0
+    for f, (F, refp, xq, per) in enumerate(prob.matches):
+        assert [gi for gi, _ in per] == list(cf[f])
+        assert np.max(np.abs(ref[f] - np.array([r for _, r in per]))) < 1e-12
+        split += len({w.coarse_faces[g][0] for g in cf[f]}) > 1
+    assert split > 0
+    for prec, tol, B in ((0, FP64_TOL, 1), (1, FP32_TOL, 9)):
+        drive = w.drive(s.dt, w.nsteps, B)
+        tr = s.run(drive=drive, precision=prec, batch=B)
+        ref_tr = prob.run(dt=s.dt, drive=drive, batch=B)
+        assert _rel(tr, ref_tr) < tol, (prec, _rel(tr, ref_tr))
+    s.close()

@@ -300,3 +300,34 @@ def test_pml_on_a_curved_mesh_absorbs():
     assert np.max(lf) < 1.1 * lf[0]
     # no late-time growth: every later window stays below the energy at step 200
     assert np.max(lf[240:]) < lf[200] and np.max(lf[320:]) < lf[280]
+
+
+def test_unstructured_nonconforming_interface_matching():
+    """A flat interface between a 6 x 6 fine tiling and an independently
+    distorted 4 x 4 coarse tiling (3:2, faces straddling coarse faces):
+    Algorithm 3 matches every fine Gauss node to the lowest-id coarse face
+    whose element contains it (checked by brute force over all coarse
+    elements), K is symmetric and annihilates constants."""
+    w = H.distorted_two_domain(nx_p=6, nz_p=1, nx_s=4, nz_s=2, bump=0.0, n_pmut_side=1, order_p=3, order_s=4)
+    p = HO.HexOracleProblem(w)
+    m1 = p.meshes[1]
+    straddled = 0
+    for F, refp, xq, per in p.matches:
+        elems = set()
+        for q, (gi, refm) in enumerate(per):
+            G = p.coarse_faces[gi]
+            elems.add(G.elem)
+            x, _ = HO.trilinear(m1.elem_verts(G.elem), refm[None, :])
+            assert np.linalg.norm(x[0] - xq[q]) < 1e-12 * 1e-4
+            # brute force: the lowest-id coarse face whose element contains the node
+            first = None
+            for gj, H2 in enumerate(p.coarse_faces):
+                r = HO.newton_reference(m1.elem_verts(H2.elem), xq[q])
+                if np.all(np.abs(r) <= 1.0 + 1e-10):
+                    first = gj
+                    break
+            assert first == gi
+        straddled += len(elems) > 1
+    assert straddled > 0
+    assert abs(p.K - p.K.T).max() < 1e-12 * abs(p.K).max()
+    assert np.max(np.abs(p.K @ np.ones(p.nh))) < 1e-12 * abs(p.K).sum(axis=1).max()

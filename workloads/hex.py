@@ -169,17 +169,24 @@ def distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, h_p=25e-6, order_p=4, o
                          batch=1, n_recv=12, penalty_alpha=0.5, scramble: Optional[int] = None,
                          steer=False, ny_p=None, ny_s=None) -> HexWorkload:
     """Fine primary box (nx_p x ny_p x nz_p, order_p) under a coarse secondary
-    box (nx_s x ny_s x nz_s with twice the lateral element size, order_s), both
-    distorted; the interface is bent into a bump of height bump * h_p.  PMUT
+    box (nx_s x ny_s x nz_s, order_s), both distorted.  With twice the lateral
+    element count on the fine side the interface is bent into a bump of height
+    bump * h_p and the fine interface vertices lie on the coarse faces'
+    bilinear patches (a nested 2:1 interface).  With any other ratio the
+    interface is the flat plane z = nz_p h_p (bump must be 0) and each side
+    keeps its own in-plane vertex displacement: the fine and coarse faces tile
+    the plane independently (an unstructured non-conforming interface).  PMUT
     membranes sit on the flat z = 0 face.  `scramble` re-lists every element in
     a random rotated local frame (seeded)."""
     rng = np.random.default_rng(seed)
     ny_p = nx_p if ny_p is None else ny_p
     ny_s = nx_s if ny_s is None else ny_s
-    assert nx_p == 2 * nx_s and ny_p == 2 * ny_s
+    nested = nx_p == 2 * nx_s and ny_p == 2 * ny_s
+    assert nested or bump == 0.0, "a non-nested interface is kept flat (bump = 0)"
     Lx, Ly = nx_p * h_p, ny_p * h_p
     Lz_p = nz_p * h_p
     hs = Lx / nx_s
+    assert abs(Ly / ny_s - hs) < 1e-12 * hs or not nested
     Lz_s = nz_s * hs
     zI = Lz_p
     ph = rng.uniform(0, 2 * math.pi, 12)
@@ -200,9 +207,9 @@ def distorted_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, h_p=25e-6, order_p=4, o
     basep = Pp.copy()
     Pp = _displace(Pp, np.zeros(3), np.array([Lx, Ly, Lz_p]), np.full(3, h_p), amp, ph[6:])
     Pp[:, 2] += basep[:, 2] / Lz_p * bump_z(basep[:, 0], basep[:, 1])
-    # interface vertices of the primary: on the coarse bilinear patches
+    # interface vertices of the primary: on the coarse bilinear patches (nested case)
     vs = lambda i, j, k: (k * (ny_s + 1) + j) * (nx_s + 1) + i
-    for j in range(ny_p + 1):
+    for j in range(ny_p + 1 if nested else 0):
         for i in range(nx_p + 1):
             I, u = min(i // 2, nx_s - 1), (i - 2 * min(i // 2, nx_s - 1)) / 2.0
             J, v = min(j // 2, ny_s - 1), (j - 2 * min(j // 2, ny_s - 1)) / 2.0
