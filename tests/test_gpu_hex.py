@@ -499,3 +499,17 @@ def test_unstructured_nonconforming_interface_parity(lib, general):
         ref_tr = prob.run(dt=s.dt, drive=drive, batch=B)
         assert _rel(tr, ref_tr) < tol, (prec, _rel(tr, ref_tr))
     s.close()
+
+
+def test_c2_size_long_run_fp32_vs_fp64(lib):
+    """The distorted config-2-class mesh (18.6M nodes, 256 PMUTs, 4000 steps,
+    the length of the config-2 runs): FP32-mixed traces stay within 1e-4 of
+    the FP64 path (oracle-validated on small meshes)."""
+    from paper_2603_06267_gb300 import dghex
+    w = H.hex_c2_like(nsteps=4000, batch=1, steer=False)
+    s = dghex.HexSolver(w)
+    t64 = s.run(precision=0)
+    t32 = s.run(precision=1)
+    assert np.abs(t64).max() > 0 and np.all(np.isfinite(t32))
+    assert _rel(t32, t64) < FP32_TOL, _rel(t32, t64)
+    s.close()
