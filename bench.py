@@ -62,7 +62,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--tiles", default=None,
-                    help="comma-separated volume-kernel tile variant per box (skips the autotuner)")
+                    help="comma-separated volume-kernel tile variant per box, or element-stiffness variant per "
+                         "domain on general hexahedra (skips the autotuner)")
     return ap.parse_args(argv)
 
 
@@ -413,6 +414,12 @@ def main_hex(args, torch, dist, rank, world, local):
     sol = dghex.HexSolver(w)
     setup_s = time.perf_counter() - t0
     ndof = sol.ndof
+    # untimed setup: pick the element-stiffness launch variant per domain for this batch
+    if args.tiles:
+        variants = [int(t) for t in args.tiles.split(",")]
+        dghex.dghex_set_volume_variant(sol.ctx, prec, variants)
+    else:
+        variants = dghex.dghex_autotune(sol.ctx, prec, B, len(w.domains), reps=2)
     K_p = w.pmuts.n_pmut
     R = w.receivers.shape[0]
     S_tot = args.warmup + args.steps
@@ -487,6 +494,7 @@ def main_hex(args, torch, dist, rank, world, local):
         "config": {"workload": name, "precision": "fp32-mixed" if prec == dghex.DGSEM_FP32_MIXED else "fp64",
                    "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
                    "elements": ne, "orders": [d.order for d in w.domains], "setup_s": setup_s,
+                   "vol_variants": variants,
                    "parallelism": "single-gpu",
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cs.summary(local),

@@ -206,6 +206,24 @@ int dghex_check_stability(dghex_ctx* ctx, int iters, double* lambda_max);
  * operator up to rounding. */
 int dghex_set_interface_kernel(dghex_ctx* ctx, int general);
 
+/* Launch variants of the element-stiffness kernel of eq. (Wf_2).  They do the
+ * same arithmetic in the same order (results agree bit for bit) and differ in
+ * batch members per thread, elements per CTA and what is kept in registers,
+ * shared memory or the read-only cache, i.e. in resident CTAs per SM.  They
+ * differ only for batches of at least the vector width (8 FP32, 4 FP64
+ * members) and orders >= 3; elsewhere every index runs the default kernel.
+ * dghex_num_volume_variants writes their count; dghex_set_volume_variant
+ * selects one per domain (variants[ndomains], 0 = default) for later runs at
+ * `precision`; dghex_autotune times every variant of each domain's kernel for
+ * `batch` patterns (one warm-up and `reps` timed launches, CUDA events on
+ * `stream`), keeps the fastest and writes it to chosen[ndomains] (may be
+ * NULL).  The autotuner uses the run state as scratch: the next dghex_run
+ * must not pass DGSEM_RUN_CONTINUE.  DGSEM_EINVAL for an index out of range,
+ * batch < 1 or reps < 1. */
+int dghex_num_volume_variants(const dghex_ctx* ctx, int* n);
+int dghex_set_volume_variant(dghex_ctx* ctx, int precision, const int* variants);
+int dghex_autotune(dghex_ctx* ctx, int precision, int batch, int reps, int* chosen, void* stream);
+
 /* Kernel instrumentation as dgsem_profile / dgsem_kernel_stats. */
 #define DGHEX_K_PMUT 0       /* PMUT modal step                                   */
 #define DGHEX_K_VOL 1        /* element stiffness (both domains)                  */

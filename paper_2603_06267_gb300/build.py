@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgsem.so")
 SOURCES = ["api.cu", "vol_f32.cu", "vol_f32_abc.cu", "vol_f64.cu", "vol_f64_abc.cu", "small.cu", "pml.cu", "surrogate.cu",
-           "hex_api.cu", "hex_kernels.cu"]
+           "hex_api.cu", "hex_kernels.cu", "hex_vol_f32.cu", "hex_vol_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,7 +39,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, "internal.h"), os.path.join(CSRC, "vol_impl.cuh"), os.path.join(CSRC, "tables.h"),
-               os.path.join(CSRC, "hex_geom.h"), os.path.join(INCLUDE, "dgsem.h"), os.path.join(INCLUDE, "dghex.h"),
+               os.path.join(CSRC, "hex_geom.h"), os.path.join(CSRC, "hex_step.cuh"),
+               os.path.join(CSRC, "hex_vol.cuh"), os.path.join(INCLUDE, "dgsem.h"), os.path.join(INCLUDE, "dghex.h"),
                os.path.join(INCLUDE, "surrogate.h")]
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                     "-I", CSRC, "-I", INCLUDE]

@@ -262,6 +262,7 @@ struct dghex_ctx {
   std::vector<int> g_fe, g_ce, g_pt, pt_idx, g_face;
   bool onface = false;                      // every group's Gauss nodes lie on one face per side
   bool force_general_iface = false;         // use the general interface kernel even when onface
+  int vol_variant[2][2] = {};               // element-stiffness launch variant [FP64, FP32][domain]
   int* d_g_face = nullptr;
   std::vector<long long> g_slot;
   int *d_g_fe = nullptr, *d_g_ce = nullptr, *d_g_pt = nullptr, *d_pt_idx = nullptr;
@@ -624,24 +625,34 @@ int setup_receivers(dghex_ctx* c, int R, const double* xyz) {
   return DGSEM_OK;
 }
 
+// element stiffness of domain d applied to the pressure field p
+template <typename T>
+hex::HexVolArgs<T> vol_args(const dghex_ctx* c, int d, const void* pfield) {
+  const HexDom& D = c->dom[d];
+  hex::HexVolArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.p = static_cast<const T*>(pfield); a.S = static_cast<T*>(c->S); a.Bp = c->Bp;
+  a.conn = D.d_conn;
+  a.G = std::is_same<T, float>::value ? reinterpret_cast<const T*>(D.d_G32) : reinterpret_cast<const T*>(D.d_G64);
+  a.slot_base = D.vslot0;
+  a.ne = D.ne;
+  for (int i = 0; i < D.n; ++i)
+    for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
+  return a;
+}
+
+template <typename T>
+int vol_variant_of(const dghex_ctx* c, int d) { return c->vol_variant[std::is_same<T, float>::value ? 1 : 0][d]; }
+
 // element stiffness and interface terms of the pressure field p
 template <typename T>
 int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
   const T* p = static_cast<const T*>(pfield);
   T* S = static_cast<T*>(c->S);
   for (int d = 0; d < c->nd; ++d) {
-    const HexDom& D = c->dom[d];
-    hex::HexVolArgs<T> a;
-    std::memset(&a, 0, sizeof(a));
-    a.p = p; a.S = S; a.Bp = c->Bp;
-    a.conn = D.d_conn;
-    a.G = std::is_same<T, float>::value ? reinterpret_cast<const T*>(D.d_G32) : reinterpret_cast<const T*>(D.d_G64);
-    a.slot_base = D.vslot0;
-    a.ne = D.ne;
-    for (int i = 0; i < D.n; ++i)
-      for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
+    const hex::HexVolArgs<T> a = vol_args<T>(c, d, pfield);
     HexTimer t(c, s, DGHEX_K_VOL);
-    HCUDA(hex::launch_hex_vol<T>(a, D.n, s));
+    HCUDA(hex::launch_hex_vol<T>(a, c->dom[d].n, vol_variant_of<T>(c, d), s));
   }
   if (c->nd == 2 && c->ng > 0) {
     const HexDom &Dp = c->dom[0], &Dm = c->dom[1];
@@ -871,6 +882,41 @@ int run_impl(dghex_ctx* c, int nsteps, const double* drive, int R, double* trace
   c->state_valid = true;
   c->steps_done += nsteps;
   return DGSEM_OK;
+}
+
+template <typename T>
+int autotune_impl(dghex_ctx* c, int reps, int* chosen, cudaStream_t s) {
+  const int pi = std::is_same<T, float>::value ? 1 : 0;
+  HCUDA(cudaMemsetAsync(c->Y, 0, sizeof(T) * (size_t)c->Bp * c->ndof, s));
+  cudaEvent_t e0, e1;
+  HCUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return hfail(DGSEM_ECUDA, "cudaEventCreate failed");
+  }
+  int rc = DGSEM_OK;
+  for (int d = 0; d < c->nd && rc == DGSEM_OK; ++d) {
+    const hex::HexVolArgs<T> a = vol_args<T>(c, d, c->Y);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < hex::kHexVolVariants; ++v) {
+      cudaError_t e = hex::launch_hex_vol<T>(a, c->dom[d].n, v, s);   // warm-up
+      if (e != cudaSuccess) { rc = hfail(DGSEM_ECUDA, "autotune, variant %d: %s", v, cudaGetErrorString(e)); break; }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = hex::launch_hex_vol<T>(a, c->dom[d].n, v, s);
+      cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) { rc = hfail(DGSEM_ECUDA, "autotune, variant %d: %s", v, cudaGetErrorString(e)); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) { best_ms = ms; best = v; }
+    }
+    c->vol_variant[pi][d] = best;
+    if (chosen) chosen[d] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 }  // namespace
@@ -1534,6 +1580,33 @@ int dghex_set_interface_kernel(dghex_ctx* c, int general) {
   if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
   c->force_general_iface = general != 0;
   return DGSEM_OK;
+}
+
+int dghex_num_volume_variants(const dghex_ctx* c, int* n) {
+  if (!c || !n) return hfail(DGSEM_EINVAL, "NULL argument");
+  *n = hex::kHexVolVariants;
+  return DGSEM_OK;
+}
+
+int dghex_set_volume_variant(dghex_ctx* c, int precision, const int* variants) {
+  if (!c || !variants) return hfail(DGSEM_EINVAL, "NULL argument");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return hfail(DGSEM_EINVAL, "bad precision");
+  for (int d = 0; d < c->nd; ++d)
+    if (variants[d] < 0 || variants[d] >= hex::kHexVolVariants)
+      return hfail(DGSEM_EINVAL, "domain %d: no element-stiffness variant %d", d, variants[d]);
+  for (int d = 0; d < c->nd; ++d) c->vol_variant[precision == DGSEM_FP32_MIXED ? 1 : 0][d] = variants[d];
+  return DGSEM_OK;
+}
+
+int dghex_autotune(dghex_ctx* c, int precision, int batch, int reps, int* chosen, void* stream) {
+  if (!c) return hfail(DGSEM_EINVAL, "ctx is NULL");
+  if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return hfail(DGSEM_EINVAL, "bad precision");
+  if (batch < 1 || reps < 1) return hfail(DGSEM_EINVAL, "batch and reps must be >= 1");
+  int rc = ensure_run_state(c, precision, batch);
+  if (rc) return rc;
+  c->state_valid = false;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return precision == DGSEM_FP32_MIXED ? autotune_impl<float>(c, reps, chosen, s) : autotune_impl<double>(c, reps, chosen, s);
 }
 
 int dghex_profile(dghex_ctx* c, int enable) {

@@ -282,7 +282,9 @@ cudaError_t launch_energy(const double* M, const double* v, const double* p, con
                           int Bp, double* e, cudaStream_t s);
 cudaError_t launch_scale(double* dst, const double* src, const double* norm2, long long n, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, cudaStream_t s);
-template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s);
+// element stiffness, launch variant 0 .. kHexVolVariants - 1 (same results)
+constexpr int kHexVolVariants = 5;
+template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, int variant, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_update(const HexUpdateArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_tail(const HexTailArgs<T>& a, cudaStream_t s);

@@ -13,44 +13,7 @@
 #include <type_traits>
 
 #include "hex_geom.h"
-
-namespace {
-
-// cp.async (sm_80+): asynchronous global -> shared copies, completed by
-// commit/wait groups; they keep no registers busy while in flight.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int K>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory"); }
-
-// copy of `bytes` (4, 8, 16 or 32; both addresses aligned to it)
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  if constexpr (BYTES == 32) {
-    cp_async16(smem, gmem);
-    cp_async16(static_cast<char*>(smem) + 16, static_cast<const char*>(gmem) + 16);
-  } else if constexpr (BYTES == 16) {
-    cp_async16(smem, gmem);
-  } else if constexpr (BYTES == 8) {
-    cp_async8(smem, gmem);
-  } else {
-    static_assert(BYTES == 4, "cp.async size");
-    cp_async4(smem, gmem);
-  }
-}
-
-}  // namespace
+#include "hex_step.cuh"
 
 namespace hex {
 
@@ -240,307 +203,6 @@ __global__ void ipoint_kernel(const __grid_constant__ MatchArgs a) {
 // ---------------------------------------------------------------------------
 // Step kernels
 // ---------------------------------------------------------------------------
-// BB consecutive batch members of one node, moved as one vector.
-template <typename T, int BB>
-struct alignas(sizeof(T) * BB) Pack {
-  T v[BB];
-};
-
-// Explicitly rounded arithmetic: the compiler may not contract or reorder
-// these, so a batch member's result is the same for every vector width BB.
-__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ float div_(float a, float b) { return __fdiv_rn(a, b); }
-__device__ __forceinline__ double div_(double a, double b) { return __ddiv_rn(a, b); }
-
-// Member-wise operations on a Pack.  FP32 packs of an even width use the
-// packed f32x2 instructions (two members per instruction); each lane rounds
-// exactly like the scalar form, so results do not depend on the width.
-template <typename T, int BB>
-constexpr bool packed2() { return std::is_same<T, float>::value && BB % 2 == 0; }
-
-__device__ __forceinline__ float2 sub2_(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-
-// acc += d * x
-template <typename T, int BB>
-__device__ __forceinline__ void vfma(Pack<T, BB>& acc, T d, const Pack<T, BB>& x) {
-  if constexpr (packed2<T, BB>()) {
-    const float2 d2 = make_float2(d, d);
-#pragma unroll
-    for (int b = 0; b < BB; b += 2) {
-      float2& a = *reinterpret_cast<float2*>(&acc.v[b]);
-      a = __ffma2_rn(d2, *reinterpret_cast<const float2*>(&x.v[b]), a);
-    }
-  } else {
-#pragma unroll
-    for (int b = 0; b < BB; ++b) acc.v[b] = fma_(d, x.v[b], acc.v[b]);
-  }
-}
-
-// d * x
-template <typename T, int BB>
-__device__ __forceinline__ Pack<T, BB> vmul(T d, const Pack<T, BB>& x) {
-  Pack<T, BB> o;
-  if constexpr (packed2<T, BB>()) {
-    const float2 d2 = make_float2(d, d);
-#pragma unroll
-    for (int b = 0; b < BB; b += 2)
-      *reinterpret_cast<float2*>(&o.v[b]) = __fmul2_rn(d2, *reinterpret_cast<const float2*>(&x.v[b]));
-  } else {
-#pragma unroll
-    for (int b = 0; b < BB; ++b) o.v[b] = mul_(d, x.v[b]);
-  }
-  return o;
-}
-
-// x - y
-template <typename T, int BB>
-__device__ __forceinline__ Pack<T, BB> vsub(const Pack<T, BB>& x, const Pack<T, BB>& y) {
-  Pack<T, BB> o;
-  if constexpr (packed2<T, BB>()) {
-#pragma unroll
-    for (int b = 0; b < BB; b += 2)
-      *reinterpret_cast<float2*>(&o.v[b]) =
-          sub2_(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b]));
-  } else {
-#pragma unroll
-    for (int b = 0; b < BB; ++b) o.v[b] = sub_(x.v[b], y.v[b]);
-  }
-  return o;
-}
-
-// x + y
-template <typename T, int BB>
-__device__ __forceinline__ Pack<T, BB> vadd(const Pack<T, BB>& x, const Pack<T, BB>& y) {
-  Pack<T, BB> o;
-  if constexpr (packed2<T, BB>()) {
-#pragma unroll
-    for (int b = 0; b < BB; b += 2)
-      *reinterpret_cast<float2*>(&o.v[b]) =
-          __fadd2_rn(*reinterpret_cast<const float2*>(&x.v[b]), *reinterpret_cast<const float2*>(&y.v[b]));
-  } else {
-#pragma unroll
-    for (int b = 0; b < BB; ++b) o.v[b] = add_(x.v[b], y.v[b]);
-  }
-  return o;
-}
-
-template <typename T, int BB>
-__device__ __forceinline__ Pack<T, BB> vzero() {
-  Pack<T, BB> o;
-#pragma unroll
-  for (int b = 0; b < BB; ++b) o.v[b] = T(0);
-  return o;
-}
-
-// Element stiffness of eq. (Wf_2), sum-factorised along element lines.
-// A CTA takes E elements and BB batch members at a time; each element has
-// n^2 threads, and thread q of an element owns the x-line (b, c), the y-line
-// (a, c) and the z-line (a, b) with (., .) = (q mod n, q div n):
-//   A: x- and y-lines: grad^_x u, grad^_y u of their line in difference form
-//      sum_m D_am (u_m - u_0) with the line's first node as reference (exact
-//      for constants in any precision; rounding scales with the variation
-//      along the line, not with u) -> smem
-//   B: z-line: grad^_z u in registers, then F = G grad^ u at its nodes with
-//      the geometric factors G; F_x, F_y -> smem, F_z stays in registers
-//   C: x-lines: D^T F_x -> R_x; y-lines: D^T F_y -> R_y (in place)
-//   D: z-line: r = R_x + R_y + D^T F_z -> the element's residual slots.
-// The derivative matrix is indexed by compile-time indices only (uniform
-// across the warp), and the per-member arithmetic is the same for every BB.
-template <int N>
-struct VolTeam {
-  static constexpr int n = N + 1, nl = n * n * n, line = n * n;
-  static constexpr int E = line >= 128 ? 1 : 128 / line;          // elements per CTA
-  static constexpr int threads = (E * line + 31) / 32 * 32;
-};
-
-// shared memory: u double buffer (the current one then holds R_x), the
-// x/y gradients (then F_x, F_y, R_y), and the CTA's geometric factors
-template <typename T, int BB, int N>
-constexpr size_t vol_smem() {
-  return 4 * sizeof(T) * BB * (size_t)VolTeam<N>::nl * VolTeam<N>::E +
-         sizeof(T) * 6 * (size_t)((VolTeam<N>::nl + 3) / 4 * 4) * VolTeam<N>::E;
-}
-
-// A shared array of packs stored as planes of 16-byte entries (members
-// [0, H), [H, 2H), ...): a warp's 16-byte accesses to consecutive entries are
-// then contiguous and free of bank conflicts.
-template <typename T, int BB>
-struct SPlanes {
-  static constexpr int H = (int)(sizeof(T) * BB > 16 ? 16 / sizeof(T) : BB);   // members per entry
-  static constexpr int NPL = BB / H;                                           // planes
-  using P = Pack<T, BB>;
-  using Half = Pack<T, H>;
-  T* base;
-  int count;
-  __device__ __forceinline__ T* ptr(int pl, int k) const { return base + ((long long)pl * count + k) * H; }
-  __device__ __forceinline__ P ld(int k) const {
-    P o;
-#pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) *reinterpret_cast<Half*>(&o.v[pl * H]) = *reinterpret_cast<const Half*>(ptr(pl, k));
-    return o;
-  }
-  __device__ __forceinline__ void st(int k, const P& x) const {
-#pragma unroll
-    for (int pl = 0; pl < NPL; ++pl) *reinterpret_cast<Half*>(ptr(pl, k)) = *reinterpret_cast<const Half*>(&x.v[pl * H]);
-  }
-};
-
-template <typename T, int N, int BB>
-__global__ void __launch_bounds__(VolTeam<N>::threads) hex_vol_kernel(const __grid_constant__ HexVolArgs<T> A) {
-  using TM = VolTeam<N>;
-  constexpr int n = TM::n, nl = TM::nl, E = TM::E, gs = (nl + 3) / 4 * 4;
-  constexpr int GPER = (E * nl + TM::threads - 1) / TM::threads;   // gather entries per thread
-  using P = Pack<T, BB>;
-  using SP = SPlanes<T, BB>;
-  extern __shared__ __align__(32) unsigned char smem_raw[];
-  T* sm = reinterpret_cast<T*>(smem_raw);
-  const SP Ub[2] = {{sm, E * nl}, {sm + (long long)E * nl * BB, E * nl}};   // u, then R_x
-  const SP G0 = {sm + 2LL * E * nl * BB, E * nl};   // grad^_x u, then F_x
-  const SP G1 = {sm + 3LL * E * nl * BB, E * nl};   // grad^_y u, then F_y, then R_y
-  T* Gs = sm + 4LL * E * nl * BB;                   // [E][6][gs] geometric factors
-  const int t = threadIdx.x;
-  const int el = t / TM::line, q = t - el * TM::line;
-  const int e0 = blockIdx.x * E;
-  const int e = e0 + el;
-  const int ne_cta = min(E, A.ne - e0);
-  const bool act = el < E && e < A.ne;
-  const int qa = q % n, qb = q / n;          // the two line coordinates
-  const int o = el * nl;                     // this element's entries in the shared arrays
-  const T* gsm = Gs + el * 6 * gs;
-  const int nch = A.Bp / BB;
-  // node ids of this thread's gather entries, reused by every chunk
-  int nd[GPER];
-#pragma unroll
-  for (int g = 0; g < GPER; ++g) {
-    const int i = t + g * TM::threads;
-    nd[g] = i < ne_cta * nl ? A.conn[(long long)e0 * nl + i] : 0;
-  }
-  auto gather = [&](int ch, const SP& dst) {
-#pragma unroll
-    for (int g = 0; g < GPER; ++g) {
-      const int i = t + g * TM::threads;
-      if (i < ne_cta * nl) {
-        const T* src = A.p + (long long)nd[g] * A.Bp + ch * BB;
-#pragma unroll
-        for (int pl = 0; pl < SP::NPL; ++pl)
-          cp_async<(int)(SP::H * sizeof(T))>(dst.ptr(pl, i), src + pl * SP::H);
-      }
-    }
-  };
-  {
-    constexpr int per16 = 16 / (int)sizeof(T);
-    const T* gsrc = A.G + 6LL * e0 * gs;
-    for (int i = t * per16; i < ne_cta * 6 * gs; i += blockDim.x * per16) cp_async16(Gs + i, gsrc + i);
-  }
-  gather(0, Ub[0]);
-  cp_commit();
-  for (int ch = 0; ch < nch; ++ch) {
-    const SP& U = Ub[ch & 1];
-    if (ch + 1 < nch) gather(ch + 1, Ub[(ch + 1) & 1]);
-    cp_commit();
-    cp_wait<1>();
-    __syncthreads();
-    if (act) {
-      // A: x-line (b, c) = (qa, qb) and y-line (a, c) = (qa, qb)
-      P lx[n], ly[n];
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        lx[m] = U.ld(o + m + n * qa + n * n * qb);
-        ly[m] = U.ld(o + qa + n * m + n * n * qb);
-      }
-#pragma unroll
-      for (int m = n - 1; m > 0; --m) {
-        lx[m] = vsub(lx[m], lx[0]);
-        ly[m] = vsub(ly[m], ly[0]);
-      }
-#pragma unroll
-      for (int a = 0; a < n; ++a) {
-        P ox = vmul(T(A.D[a][1]), lx[1]), oy = vmul(T(A.D[a][1]), ly[1]);
-#pragma unroll
-        for (int m = 2; m < n; ++m) {
-          const T d = A.D[a][m];
-          vfma(ox, d, lx[m]);
-          vfma(oy, d, ly[m]);
-        }
-        G0.st(o + a + n * qa + n * n * qb, ox);
-        G1.st(o + qa + n * a + n * n * qb, oy);
-      }
-    }
-    __syncthreads();
-    P fz[n];
-    if (act) {
-      // B: z-line (a, b) = (qa, qb): grad^_z u, then F = G grad^ u at its nodes
-      P lz[n];
-#pragma unroll
-      for (int m = 0; m < n; ++m) lz[m] = U.ld(o + qa + n * qb + n * n * m);
-#pragma unroll
-      for (int m = n - 1; m > 0; --m) lz[m] = vsub(lz[m], lz[0]);
-#pragma unroll
-      for (int c = 0; c < n; ++c) {
-        P gz = vmul(T(A.D[c][1]), lz[1]);
-#pragma unroll
-        for (int m = 2; m < n; ++m) vfma(gz, T(A.D[c][m]), lz[m]);
-        const int k = qa + n * qb + n * n * c;
-        const T* gp = gsm + k;
-        const T G00 = gp[0], G11 = gp[gs], G22 = gp[2 * gs], G01 = gp[3 * gs], G02 = gp[4 * gs], G12 = gp[5 * gs];
-        const P gx = G0.ld(o + k), gy = G1.ld(o + k);
-        P fx = vmul(G00, gx), fy = vmul(G01, gx);
-        fz[c] = vmul(G02, gx);
-        vfma(fx, G01, gy);
-        vfma(fy, G11, gy);
-        vfma(fz[c], G12, gy);
-        vfma(fx, G02, gz);
-        vfma(fy, G12, gz);
-        vfma(fz[c], G22, gz);
-        G0.st(o + k, fx);
-        G1.st(o + k, fy);
-      }
-    }
-    __syncthreads();
-    if (act) {
-      // C: x-line: R_x = D^T F_x -> U; y-line: R_y = D^T F_y -> G1 (in place)
-      P lx[n], ly[n];
-#pragma unroll
-      for (int m = 0; m < n; ++m) {
-        lx[m] = G0.ld(o + m + n * qa + n * n * qb);
-        ly[m] = G1.ld(o + qa + n * m + n * n * qb);
-      }
-#pragma unroll
-      for (int a = 0; a < n; ++a) {
-        P ox = vzero<T, BB>(), oy = vzero<T, BB>();
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          const T d = A.D[m][a];
-          vfma(ox, d, lx[m]);
-          vfma(oy, d, ly[m]);
-        }
-        U.st(o + a + n * qa + n * n * qb, ox);
-        G1.st(o + qa + n * a + n * n * qb, oy);
-      }
-    }
-    __syncthreads();
-    if (act) {
-      // D: z-line: r = R_x + R_y + D^T F_z
-      P* sout = reinterpret_cast<P*>(A.S + (A.slot_base + (long long)e * nl) * A.Bp) + ch;
-#pragma unroll
-      for (int c = 0; c < n; ++c) {
-        const int k = qa + n * qb + n * n * c;
-        P rz = vzero<T, BB>();
-#pragma unroll
-        for (int m = 0; m < n; ++m) vfma(rz, T(A.D[m][c]), fz[m]);
-        sout[(long long)k * (A.Bp / BB)] = vadd(vadd(U.ld(o + k), G1.ld(o + k)), rz);
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // SIPG interface terms of eq. (Wf_2) for one group of fine Gauss nodes that
 // share a fine element K+ and a coarse element K-.  With jump J = p+ - p-
@@ -1148,44 +810,6 @@ cudaError_t launch_ipoints(const MatchArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// vector width: 32 bytes of batch members when the padded batch allows it
-template <typename T>
-constexpr int vec_width() { return 32 / (int)sizeof(T); }
-
-template <typename T, int N, int BB>
-cudaError_t vol_n(const HexVolArgs<T>& a, cudaStream_t s) {
-  using TM = VolTeam<N>;
-  constexpr size_t sm = vol_smem<T, BB, N>();
-  if (sm > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(hex_vol_kernel<T, N, BB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-  }
-  hex_vol_kernel<T, N, BB><<<(a.ne + TM::E - 1) / TM::E, TM::threads, sm, s>>>(a);
-  return cudaGetLastError();
-}
-
-template <typename T, int BB>
-cudaError_t vol_bb(const HexVolArgs<T>& a, int n, cudaStream_t s) {
-  switch (n - 1) {
-    case 1: return vol_n<T, 1, BB>(a, s);
-    case 2: return vol_n<T, 2, BB>(a, s);
-    case 3: return vol_n<T, 3, BB>(a, s);
-    case 4: return vol_n<T, 4, BB>(a, s);
-    case 5: return vol_n<T, 5, BB>(a, s);
-    case 6: return vol_n<T, 6, BB>(a, s);
-    case 7: return vol_n<T, 7, BB>(a, s);
-    case 8: return vol_n<T, 8, BB>(a, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <typename T>
-cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, cudaStream_t s) {
-  if (a.ne == 0 || a.Bp == 0) return cudaSuccess;
-  constexpr int V = vec_width<T>();
-  return (a.Bp % V == 0) ? vol_bb<T, V>(a, n, s) : vol_bb<T, 1>(a, n, s);
-}
-
 template <typename T, int BB>
 size_t iface_smem(const HexIfaceArgs<T>& a) {
   const long long Q = a.max_pts;
@@ -1276,8 +900,6 @@ cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, cudaStream_t s) {
 
 template cudaError_t launch_hex_pml<float>(const HexPmlArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_hex_pml<double>(const HexPmlArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_hex_vol<float>(const HexVolArgs<float>&, int, cudaStream_t);
-template cudaError_t launch_hex_vol<double>(const HexVolArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_hex_iface<float>(const HexIfaceArgs<float>&, cudaStream_t);
 template cudaError_t launch_hex_iface<double>(const HexIfaceArgs<double>&, cudaStream_t);
 template cudaError_t launch_hex_update<float>(const HexUpdateArgs<float>&, cudaStream_t);

@@ -20,7 +20,7 @@ EXPORTED = [
     "dghex_set_absorbing_faces", "dghex_set_pml", "dghex_pmut_set_receive", "dghex_get_voltages", "dghex_state_save",
     "dghex_state_load",
     "dghex_run", "dghex_set_state", "dghex_get_pressure", "dghex_energy", "dghex_check_stability",
-    "dghex_set_interface_kernel",
+    "dghex_set_interface_kernel", "dghex_num_volume_variants", "dghex_set_volume_variant", "dghex_autotune",
     "dghex_profile",
     "dghex_kernel_stats", "dghex_destroy",
 ]
@@ -68,6 +68,9 @@ def load_library():
     lib.dghex_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
     lib.dghex_state_load.argtypes = [vp, vp, c_size_t]
     lib.dghex_set_interface_kernel.argtypes = [vp, c_int]
+    lib.dghex_num_volume_variants.argtypes = [vp, POINTER(c_int)]
+    lib.dghex_set_volume_variant.argtypes = [vp, c_int, vp]
+    lib.dghex_autotune.argtypes = [vp, c_int, c_int, c_int, vp, vp]
     lib.dghex_profile.argtypes = [vp, c_int]
     lib.dghex_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
     lib.dghex_destroy.argtypes = [vp]
@@ -258,6 +261,28 @@ def dghex_set_interface_kernel(ctx, general: bool):
     """Force the full-evaluation interface kernel (True) or restore the
     automatic choice (False)."""
     _check(_lib.dghex_set_interface_kernel(ctx, 1 if general else 0), "dghex_set_interface_kernel")
+
+
+def dghex_num_volume_variants(ctx) -> int:
+    n = c_int()
+    _check(_lib.dghex_num_volume_variants(ctx, byref(n)), "dghex_num_volume_variants")
+    return n.value
+
+
+def dghex_set_volume_variant(ctx, precision: int, variants):
+    """Element-stiffness launch variant per domain for later runs at `precision`."""
+    v = np.ascontiguousarray(variants, dtype=np.int32)
+    _check(_lib.dghex_set_volume_variant(ctx, precision, _ptr(v)), "dghex_set_volume_variant")
+
+
+def dghex_autotune(ctx, precision: int, batch: int, ndomains: int, reps: int = 3, stream=None):
+    """Time every element-stiffness variant of each domain for `batch`
+    patterns and keep the fastest; returns the chosen variant per domain."""
+    out = np.zeros(ndomains, dtype=np.int32)
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dghex_autotune(ctx, precision, batch, reps, _ptr(out), stream), "dghex_autotune")
+    return [int(x) for x in out]
 
 
 def dghex_profile(ctx, enable: bool = True):

@@ -138,6 +138,40 @@ def test_batch_members_are_independent(lib):
     s.close()
 
 
+@pytest.mark.parametrize("orders", [(4, 6), (5, 8), (3, 7)])
+def test_volume_variants_agree_bit_for_bit(lib, orders):
+    """Every element-stiffness launch variant, and the autotuner's choice,
+    gives the default kernel's traces and final field bit for bit: FP32 with
+    16 members (8 or 4 per thread, several chunks) and FP64 with 8 members,
+    on element counts that leave the last CTA partly filled for several
+    elements-per-CTA choices."""
+    from paper_2603_06267_gb300 import dghex, dgsem
+    w = H.distorted_two_domain(nx_p=6, nz_p=1, nx_s=3, nz_s=2, order_p=orders[0], order_s=orders[1],
+                               n_pmut_side=2, nsteps=25, scramble=3, batch=16, steer=True)
+    s = dghex.HexSolver(w)
+    nv = dghex.dghex_num_volume_variants(s.ctx)
+    assert nv >= 2
+    for prec, B in ((1, 16), (0, 8)):
+        drive = w.drive(s.dt, w.nsteps, B)
+        dghex.dghex_set_volume_variant(s.ctx, prec, [0, 0])
+        ref_tr = s.run(drive=drive, precision=prec, batch=B)
+        ref_p = dghex.dghex_get_pressure(s.ctx, B, s.ndof)
+        assert np.max(np.abs(ref_tr)) > 0 and np.all(np.isfinite(ref_p))
+        for v in range(1, nv):
+            dghex.dghex_set_volume_variant(s.ctx, prec, [v, nv - v])
+            tr = s.run(drive=drive, precision=prec, batch=B)
+            assert np.array_equal(tr, ref_tr), (orders, prec, v)
+            assert np.array_equal(dghex.dghex_get_pressure(s.ctx, B, s.ndof), ref_p), (orders, prec, v)
+        chosen = dghex.dghex_autotune(s.ctx, prec, B, 2, reps=1)
+        assert all(0 <= c < nv for c in chosen)
+        tr = s.run(drive=drive, precision=prec, batch=B)
+        assert np.array_equal(tr, ref_tr), (orders, prec, chosen)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dghex.dghex_set_volume_variant(s.ctx, 1, [0, nv])
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    s.close()
+
+
 def test_continued_run_equals_single_run(lib):
     from paper_2603_06267_gb300 import dghex
     w = H.distorted_two_domain(nx_p=4, nz_p=1, nx_s=2, nz_s=2, n_pmut_side=2, nsteps=50)
