@@ -399,14 +399,18 @@ template <typename T, int N, int BB, int E, int FL>
 cudaError_t vol_launch(const HexVolArgs<T>& a, cudaStream_t s) {
   using TM = VolTeam<N, E>;
   constexpr size_t sm = vol_smem<T, BB, N, E, FL>();
-  static_assert(sm <= 227 * 1024, "element-stiffness variant exceeds the shared memory of a CTA");
-  if (sm > 48 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(hex_vol_kernel<T, N, BB, E, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
+  if constexpr (sm > 227 * 1024) {
+    // this shape does not fit one CTA at this order: the default form instead
+    return vol_launch<T, N, BB, vol_e0<N>(), VOL_GSM | VOL_DB>(a, s);
+  } else {
+    if (sm > 48 * 1024) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(hex_vol_kernel<T, N, BB, E, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (e != cudaSuccess) return e;
+    }
+    hex_vol_kernel<T, N, BB, E, FL><<<(a.ne + E - 1) / E, TM::threads, sm, s>>>(a);
+    return cudaGetLastError();
   }
-  hex_vol_kernel<T, N, BB, E, FL><<<(a.ne + E - 1) / E, TM::threads, sm, s>>>(a);
-  return cudaGetLastError();
 }
 
 // Variant v of order N.  Batches not padded to the vector width V take the
@@ -415,6 +419,9 @@ cudaError_t vol_launch(const HexVolArgs<T>& a, cudaStream_t s) {
 // decided the set: the default (v 0) is fastest for order 4 at 64 FP32
 // members, v 4 for order 6 there, v 3 (five order-6 elements per CTA, 4%
 // idle lanes instead of 23%) for FP64, v 1, 2 and 4 for 8 FP32 members.
+// Measured and left out: 8 FP32 members in the register form with five
+// order-6 elements per CTA (one 220 KB CTA per SM), with the prefetch or with
+// staged geometry: 1.3 and 3.2 ms slower than v 0 at 64 members.
 template <typename T, int N>
 cudaError_t vol_variant(const HexVolArgs<T>& a, int v, cudaStream_t s) {
   constexpr int V = vec_width<T>(), H = V / 2, E0 = vol_e0<N>(), E1 = vol_e1<N>();
