@@ -636,8 +636,19 @@ hex::HexVolArgs<T> vol_args(const dghex_ctx* c, int d, const void* pfield) {
   a.G = std::is_same<T, float>::value ? reinterpret_cast<const T*>(D.d_G32) : reinterpret_cast<const T*>(D.d_G64);
   a.slot_base = D.vslot0;
   a.ne = D.ne;
-  for (int i = 0; i < D.n; ++i)
-    for (int j = 0; j < D.n; ++j) a.D[i][j] = T(D.basis->D[i * D.n + j]);
+  const int n = D.n, h = n / 2;
+  for (int t = 0; t < 2; ++t) {
+    auto C = [&](int i, int j) { return t == 0 ? D.basis->D[i * n + j] : D.basis->D[j * n + i]; };
+    for (int r = 0; r < h; ++r) {
+      for (int m = 0; m < h; ++m) {
+        a.ea[t][r][m] = T(0.5 * (C(r, m) - C(r, n - 1 - m)));
+        a.eb[t][r][m] = T(0.5 * (C(r, m) + C(r, n - 1 - m)));
+      }
+      if (n % 2 == 1) a.eb[t][r][h] = T(C(r, h));
+    }
+    if (n % 2 == 1)
+      for (int m = 0; m < h; ++m) a.em[t][m] = T(C(h, m));
+  }
   return a;
 }
 

@@ -193,7 +193,12 @@ struct HexVolArgs {
   const T* G;                // [ne][6][gstride(n)]
   long long slot_base;       // first volume slot of this domain
   int ne;
-  T D[MAXN1][MAXN1];         // D[i][j] = l_j'(xi_i)
+  // even-odd split of C = D ([0], D[i][j] = l_j'(xi_i)) and C = D^T ([1]),
+  // h = n / 2: ea[a][m] = (C[a][m] - C[a][n-1-m]) / 2, eb[a][m] = (C[a][m] +
+  // C[a][n-1-m]) / 2 (a, m < h), eb[a][h] = C[a][h], em[m] = C[h][m] (odd n)
+  T ea[2][MAXN1 / 2][MAXN1 / 2];
+  T eb[2][MAXN1 / 2][MAXN1 / 2 + 1];
+  T em[2][MAXN1 / 2];
 };
 
 // Step: SIPG interface terms of one group (fine face, coarse element) into

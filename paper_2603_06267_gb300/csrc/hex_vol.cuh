@@ -60,15 +60,15 @@ namespace hex {
 //      the geometric factors G; F_x, F_y -> smem, F_z kept for D
 //   C: x-lines: D^T F_x -> R_x; y-lines: D^T F_y -> R_y
 //   D: z-line: r = R_x + R_y + D^T F_z -> the element's residual slots.
-// The derivative matrix is indexed by compile-time indices only (uniform
-// across the warp), and the per-member arithmetic is the same for every BB.
+// Every line contraction uses the even-odd split of D (eo_line); its
+// coefficients are indexed by compile-time indices only (uniform across the
+// warp), and the per-member arithmetic is the same for every BB.
 //
 // Launch variants (flags FL) trade registers and shared memory for resident
 // CTAs; all of them do the same arithmetic in the same order, so their
 // results agree bit for bit:
-//   VOL_LEAN  x- and y-lines one after the other (half the live line
-//             registers); F_z goes to the z-line's own entries of the u
-//             buffer instead of registers, R_x replaces F_x in place
+//   VOL_LEAN  F_z goes to the z-line's own entries of the u buffer instead
+//             of registers, R_x replaces F_x in place
 //   VOL_GSM   geometric factors staged in shared memory once per CTA
 //             (otherwise read through the read-only cache at each chunk)
 //   VOL_DB    two u buffers: the next chunk's gather is in flight while the
@@ -153,32 +153,57 @@ struct SPlanes {
   }
 };
 
-// out[a] = sum_{m >= 1} D_am (l[m] - l[0]) along one line -> dst at
-// base + a * stride (l is overwritten by the differences)
-template <typename T, int BB, int n>
-__device__ __forceinline__ void vol_grad_line(const HexVolArgs<T>& A, Pack<T, BB> (&l)[n], const SPlanes<T, BB>& dst,
-                                              int base, int stride) {
+// One line contraction out_a = sum_m C_am l_m with C = D (TR false: the
+// reference gradient, in difference form: l_m - l_0 replaces l_m) or C = D^T
+// (TR true), by its even-odd split.  Both matrices are centro-antisymmetric
+// on GLL nodes (C_{n-1-a, n-1-m} = -C_am), so with h = n / 2,
+// s_m = l_m + l_{n-1-m} and d_m = l_m - l_{n-1-m} (m < h):
+//   P_a = sum_{m<h} ea_am d_m,  Q_a = sum_{m<h} eb_am s_m (+ eb_ah l_h, odd n)
+//   out_a = P_a + Q_a,  out_{n-1-a} = P_a - Q_a  (a < h)
+//   out_h = sum_{m<h} em_m d_m  (odd n; C_hh = 0)
+// with ea = (C_am - C_{a,n-1-m}) / 2, eb = (C_am + C_{a,n-1-m}) / 2,
+// eb_ah = C_ah, em_m = C_hm: about 3/4 of the direct n^2 multiply-adds.  In
+// the difference form l_0 = 0, so s_0 = l_{n-1}, d_0 = -l_{n-1}.  Outputs go
+// to emit(a, value) as they are formed (a compile-time index once unrolled).
+template <typename T, int BB, int n, bool TR, class F>
+__device__ __forceinline__ void eo_line(const HexVolArgs<T>& A, Pack<T, BB> (&l)[n], F&& emit) {
+  using P = Pack<T, BB>;
+  constexpr int h = n / 2, t = TR ? 1 : 0, m0 = TR ? 0 : 1;
+  if constexpr (!TR) {
 #pragma unroll
-  for (int m = n - 1; m > 0; --m) l[m] = vsub(l[m], l[0]);
-#pragma unroll
-  for (int a = 0; a < n; ++a) {
-    Pack<T, BB> o = vmul(T(A.D[a][1]), l[1]);
-#pragma unroll
-    for (int m = 2; m < n; ++m) vfma(o, T(A.D[a][m]), l[m]);
-    dst.st(base + a * stride, o);
+    for (int m = n - 1; m > 0; --m) l[m] = vsub(l[m], l[0]);
   }
-}
-
-// out[a] = sum_m D_ma l[m] along one line -> dst at base + a * stride
-template <typename T, int BB, int n>
-__device__ __forceinline__ void vol_divt_line(const HexVolArgs<T>& A, const Pack<T, BB> (&l)[n],
-                                              const SPlanes<T, BB>& dst, int base, int stride) {
+  P s[h], d[h];
 #pragma unroll
-  for (int a = 0; a < n; ++a) {
-    Pack<T, BB> o = vzero<T, BB>();
+  for (int m = m0; m < h; ++m) {
+    s[m] = vadd(l[m], l[n - 1 - m]);
+    d[m] = vsub(l[m], l[n - 1 - m]);
+  }
 #pragma unroll
-    for (int m = 0; m < n; ++m) vfma(o, T(A.D[m][a]), l[m]);
-    dst.st(base + a * stride, o);
+  for (int a = 0; a < h; ++a) {
+    P p, q;
+    if constexpr (TR) {
+      p = vmul(T(A.ea[t][a][0]), d[0]);
+      q = vmul(T(A.eb[t][a][0]), s[0]);
+    } else {
+      p = vmul(T(-A.ea[t][a][0]), l[n - 1]);
+      q = vmul(T(A.eb[t][a][0]), l[n - 1]);
+    }
+#pragma unroll
+    for (int m = 1; m < h; ++m) vfma(p, T(A.ea[t][a][m]), d[m]);
+#pragma unroll
+    for (int m = 1; m < h; ++m) vfma(q, T(A.eb[t][a][m]), s[m]);
+    if constexpr (n % 2 == 1) vfma(q, T(A.eb[t][a][h]), l[h]);
+    emit(a, vadd(p, q));
+    emit(n - 1 - a, vsub(p, q));
+  }
+  if constexpr (n % 2 == 1) {
+    P o;
+    if constexpr (TR) o = vmul(T(A.em[t][0]), d[0]);
+    else o = vmul(T(-A.em[t][0]), l[n - 1]);
+#pragma unroll
+    for (int m = 1; m < h; ++m) vfma(o, T(A.em[t][m]), d[m]);
+    emit(h, o);
   }
 }
 
@@ -206,6 +231,9 @@ __global__ void __launch_bounds__(VolTeam<N, E>::threads, vol_min_blocks<T, BB, 
   const bool act = el < E && e < A.ne;
   const int qa = q % n, qb = q / n;          // the two line coordinates
   const int o = el * nl;                     // this element's entries in the shared arrays
+  const int xb = o + n * qa + n * n * qb;    // x-line (b, c) = (qa, qb): entries xb + a
+  const int yb = o + qa + n * n * qb;        // y-line (a, c) = (qa, qb): entries yb + n a
+  const int zb = o + qa + n * qb;            // z-line (a, b) = (qa, qb): entries zb + n^2 c
   const T* gsm = GSM ? Gs + el * 6 * gs : (act ? A.G + 6LL * e * gs : A.G);
   const int nch = A.Bp / BB;
   // node ids of this thread's gather entries, reused by every chunk
@@ -249,62 +277,30 @@ __global__ void __launch_bounds__(VolTeam<N, E>::threads, vol_min_blocks<T, BB, 
     }
     __syncthreads();
     if (act) {
-      // A: x-line (b, c) = (qa, qb) and y-line (a, c) = (qa, qb)
-      if constexpr (LEAN) {
-        {
-          P l[n];
+      // A: grad^_x u along the x-line, grad^_y u along the y-line
+      {
+        P l[n];
 #pragma unroll
-          for (int m = 0; m < n; ++m) l[m] = U.ld(o + m + n * qa + n * n * qb);
-          vol_grad_line<T, BB, n>(A, l, G0, o + n * qa + n * n * qb, 1);
-        }
-        {
-          P l[n];
+        for (int m = 0; m < n; ++m) l[m] = U.ld(xb + m);
+        eo_line<T, BB, n, false>(A, l, [&](int a, const P& v) { G0.st(xb + a, v); });
+      }
+      {
+        P l[n];
 #pragma unroll
-          for (int m = 0; m < n; ++m) l[m] = U.ld(o + qa + n * m + n * n * qb);
-          vol_grad_line<T, BB, n>(A, l, G1, o + qa + n * n * qb, n);
-        }
-      } else {
-        P lx[n], ly[n];
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          lx[m] = U.ld(o + m + n * qa + n * n * qb);
-          ly[m] = U.ld(o + qa + n * m + n * n * qb);
-        }
-#pragma unroll
-        for (int m = n - 1; m > 0; --m) {
-          lx[m] = vsub(lx[m], lx[0]);
-          ly[m] = vsub(ly[m], ly[0]);
-        }
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-          P ox = vmul(T(A.D[a][1]), lx[1]), oy = vmul(T(A.D[a][1]), ly[1]);
-#pragma unroll
-          for (int m = 2; m < n; ++m) {
-            const T d = A.D[a][m];
-            vfma(ox, d, lx[m]);
-            vfma(oy, d, ly[m]);
-          }
-          G0.st(o + a + n * qa + n * n * qb, ox);
-          G1.st(o + qa + n * a + n * n * qb, oy);
-        }
+        for (int m = 0; m < n; ++m) l[m] = U.ld(yb + n * m);
+        eo_line<T, BB, n, false>(A, l, [&](int a, const P& v) { G1.st(yb + n * a, v); });
       }
     }
     __syncthreads();
     P fz[LEAN ? 1 : n];
     if (act) {
-      // B: z-line (a, b) = (qa, qb): grad^_z u, then F = G grad^ u at its nodes
-      P lz[n];
+      // B: z-line: grad^_z u, then F = G grad^ u at its nodes
+      P l[n];
 #pragma unroll
-      for (int m = 0; m < n; ++m) lz[m] = U.ld(o + qa + n * qb + n * n * m);
-#pragma unroll
-      for (int m = n - 1; m > 0; --m) lz[m] = vsub(lz[m], lz[0]);
-#pragma unroll
-      for (int c = 0; c < n; ++c) {
-        P gz = vmul(T(A.D[c][1]), lz[1]);
-#pragma unroll
-        for (int m = 2; m < n; ++m) vfma(gz, T(A.D[c][m]), lz[m]);
-        const int k = qa + n * qb + n * n * c;
-        const T* gp = gsm + k;
+      for (int m = 0; m < n; ++m) l[m] = U.ld(zb + n * n * m);
+      eo_line<T, BB, n, false>(A, l, [&](int c, const P& gz) {
+        const int k = zb + n * n * c;
+        const T* gp = gsm + (k - o);
         T G00, G11, G22, G01, G02, G12;
         if constexpr (GSM) {
           G00 = gp[0]; G11 = gp[gs]; G22 = gp[2 * gs]; G01 = gp[3 * gs]; G02 = gp[4 * gs]; G12 = gp[5 * gs];
@@ -312,7 +308,7 @@ __global__ void __launch_bounds__(VolTeam<N, E>::threads, vol_min_blocks<T, BB, 
           G00 = __ldg(gp); G11 = __ldg(gp + gs); G22 = __ldg(gp + 2 * gs);
           G01 = __ldg(gp + 3 * gs); G02 = __ldg(gp + 4 * gs); G12 = __ldg(gp + 5 * gs);
         }
-        const P gx = G0.ld(o + k), gy = G1.ld(o + k);
+        const P gx = G0.ld(k), gy = G1.ld(k);
         P fx = vmul(G00, gx), fy = vmul(G01, gx), fzc = vmul(G02, gx);
         vfma(fx, G01, gy);
         vfma(fy, G11, gy);
@@ -320,75 +316,47 @@ __global__ void __launch_bounds__(VolTeam<N, E>::threads, vol_min_blocks<T, BB, 
         vfma(fx, G02, gz);
         vfma(fy, G12, gz);
         vfma(fzc, G22, gz);
-        G0.st(o + k, fx);
-        G1.st(o + k, fy);
-        if constexpr (LEAN) U.st(o + k, fzc);   // the thread's own z-line entries, already read
+        G0.st(k, fx);
+        G1.st(k, fy);
+        if constexpr (LEAN) U.st(k, fzc);   // the thread's own z-line entries, already read
         else fz[c] = fzc;
+      });
+    }
+    __syncthreads();
+    if (act) {
+      // C: R_x = D^T F_x along the x-line (to U, or in place: LEAN); R_y = D^T F_y in place
+      {
+        P l[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) l[m] = G0.ld(xb + m);
+        eo_line<T, BB, n, true>(A, l, [&](int a, const P& v) {
+          if constexpr (LEAN) G0.st(xb + a, v);
+          else U.st(xb + a, v);
+        });
+      }
+      {
+        P l[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) l[m] = G1.ld(yb + n * m);
+        eo_line<T, BB, n, true>(A, l, [&](int a, const P& v) { G1.st(yb + n * a, v); });
       }
     }
     __syncthreads();
     if (act) {
-      // C: x-line: R_x = D^T F_x; y-line: R_y = D^T F_y -> G1 (in place)
-      if constexpr (LEAN) {
-        {
-          P l[n];
-#pragma unroll
-          for (int m = 0; m < n; ++m) l[m] = G0.ld(o + m + n * qa + n * n * qb);
-          vol_divt_line<T, BB, n>(A, l, G0, o + n * qa + n * n * qb, 1);
-        }
-        {
-          P l[n];
-#pragma unroll
-          for (int m = 0; m < n; ++m) l[m] = G1.ld(o + qa + n * m + n * n * qb);
-          vol_divt_line<T, BB, n>(A, l, G1, o + qa + n * n * qb, n);
-        }
-      } else {
-        P lx[n], ly[n];
-#pragma unroll
-        for (int m = 0; m < n; ++m) {
-          lx[m] = G0.ld(o + m + n * qa + n * n * qb);
-          ly[m] = G1.ld(o + qa + n * m + n * n * qb);
-        }
-#pragma unroll
-        for (int a = 0; a < n; ++a) {
-          P ox = vzero<T, BB>(), oy = vzero<T, BB>();
-#pragma unroll
-          for (int m = 0; m < n; ++m) {
-            const T d = A.D[m][a];
-            vfma(ox, d, lx[m]);
-            vfma(oy, d, ly[m]);
-          }
-          U.st(o + a + n * qa + n * n * qb, ox);
-          G1.st(o + qa + n * a + n * n * qb, oy);
-        }
-      }
-    }
-    __syncthreads();
-    if (act) {
-      // D: z-line: r = R_x + R_y + D^T F_z
+      // D: z-line: r = R_x + R_y + D^T F_z -> the element's residual slots
       P* sout = reinterpret_cast<P*>(A.S + (A.slot_base + (long long)e * nl) * A.Bp) + ch;
       const SP& RX = LEAN ? G0 : U;
+      auto out = [&](int c, const P& rz) {
+        const int k = zb + n * n * c;
+        sout[(long long)(k - o) * (A.Bp / BB)] = vadd(vadd(RX.ld(k), G1.ld(k)), rz);
+      };
       if constexpr (LEAN) {
         P l[n];
 #pragma unroll
-        for (int m = 0; m < n; ++m) l[m] = U.ld(o + qa + n * qb + n * n * m);
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const int k = qa + n * qb + n * n * c;
-          P rz = vzero<T, BB>();
-#pragma unroll
-          for (int m = 0; m < n; ++m) vfma(rz, T(A.D[m][c]), l[m]);
-          sout[(long long)k * (A.Bp / BB)] = vadd(vadd(RX.ld(o + k), G1.ld(o + k)), rz);
-        }
+        for (int m = 0; m < n; ++m) l[m] = U.ld(zb + n * n * m);
+        eo_line<T, BB, n, true>(A, l, out);
       } else {
-#pragma unroll
-        for (int c = 0; c < n; ++c) {
-          const int k = qa + n * qb + n * n * c;
-          P rz = vzero<T, BB>();
-#pragma unroll
-          for (int m = 0; m < n; ++m) vfma(rz, T(A.D[m][c]), fz[m]);
-          sout[(long long)k * (A.Bp / BB)] = vadd(vadd(RX.ld(o + k), G1.ld(o + k)), rz);
-        }
+        eo_line<T, BB, n, true>(A, fz, out);
       }
     }
     __syncthreads();
