@@ -407,6 +407,49 @@ def main():
         dist.destroy_process_group()
 
 
+HEX_KERNELS = ["pmut", "vol", "iface", "update", "tail", "pml"]
+
+
+def hex_roofline(kstats, orders, nelem, ndof, B, fp32, hbm_gbs):
+    """Roofline block of the general-hexahedron step for its dominant kernel
+    (element stiffness or update), from per-kind (total ms, launches).
+
+    Algorithmic bytes per launch: stiffness (per launch averaged over the
+    domains) p once per node, the element-local residual slots written, the
+    geometric factors and node ids once; update: p in, p out, v in and out,
+    the slots read, M^-1 and the node's slot list.  Algorithmic flops of the
+    stiffness per element and member: 12 n^4 + 18 n^3 (reference gradient and
+    transposed derivative along three directions, 2 x 3 n^4 FMA; geometric-
+    factor product, 9 n^3 FMA).  Above the ridge point the arithmetic pipe
+    bounds the kernel and the block reports TFLOP/s against it."""
+    es = 4 if fp32 else 8
+    peak = hbm_gbs if hbm_gbs else 6800.0
+    nl = [(o + 1) ** 3 for o in orders]
+    ploc = sum(a * b for a, b in zip(nl, nelem))              # element-local nodes = volume slots
+    vol_bytes = (ndof * B * es + ploc * B * es + ploc * (6 * es + 4)) / len(orders)
+    upd_bytes = ndof * B * 4 * es + ploc * B * es + ndof * (es + 4) + ploc * 4
+    alg = {"vol": vol_bytes, "update": upd_bytes}
+    kdom = max((1, 3), key=lambda k: kstats[k][0])
+    name = HEX_KERNELS[kdom]
+    avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
+    achieved = alg[name] / avg_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": name, "peak_source": "measured" if hbm_gbs else "fallback",
+            "alg_bytes_per_launch": alg[name]}
+    if name == "vol":
+        vol_flops = sum(e * B * (12 * (o + 1) ** 4 + 18 * (o + 1) ** 3) for e, o in zip(nelem, orders)) / len(orders)
+        alu_peak = FP32_TFLOPS if fp32 else FP64_TFLOPS
+        achieved_f = vol_flops / avg_s / 1e12
+        if vol_flops / vol_bytes > alu_peak * 1e12 / (peak * 1e9):
+            roof = {"bound": "alu", "achieved": achieved_f, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved_f / alu_peak, "traffic": None, "kernel": "vol",
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                    if fp32 else "nominal FP64 (no measured FP64 peak)",
+                    "alg_flops_per_launch": vol_flops, "alg_bytes_per_launch": vol_bytes,
+                    "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
+    return roof
+
+
 def main_hex(args, torch, dist, rank, world, local):
     """General hexahedra (include/dghex.h): the same step on distorted
     trilinear meshes with a bent 2:1 interface."""
@@ -469,42 +512,11 @@ def main_hex(args, torch, dist, rank, world, local):
                    "h2d_bytes_per_step": int(B * K_p * 8), "d2h_bytes_per_step": int(B * R * 8)}
     finite = bool(torch.isfinite(tr_time).all().item())
     value = whole_job_rate(ndof, B, args.steps, 1, ms / 1e3)
-    names = ["pmut", "vol", "iface", "update", "tail", "pml"]
-    es = 4 if prec == dghex.DGSEM_FP32_MIXED else 8
-    # algorithmic bytes per launch (DRAM, the work each kernel must move)
-    nl = [(d.order + 1) ** 3 for d in w.domains]
-    ne = [d.elements.shape[0] for d in w.domains]
-    ploc = sum(a * b for a, b in zip(nl, ne))                 # element-local nodes = volume slots
-    # vol (both domains, per launch averaged over the two launches): p read once per node,
-    # the element-local residual written, geometric factors and node ids read once
-    vol_bytes = (ndof * B * es + ploc * B * es + ploc * (6 * es + 4)) / len(w.domains)
-    upd_bytes = ndof * B * 4 * es + ploc * B * es + ndof * (es + 4) + ploc * 4
-    alg = {"vol": vol_bytes, "update": upd_bytes}
-    kdom = max((1, 3), key=lambda k: kstats[k][0])
     peaks = measured_peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
-    achieved = alg[names[kdom]] / avg_s / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": names[kdom], "peak_source": "measured" if peaks else "fallback",
-            "alg_bytes_per_launch": alg[names[kdom]]}
-    if names[kdom] == "vol":
-        # algorithmic flops of the general-map sum factorisation per element and member:
-        # the reference gradient and the transposed derivative along three directions
-        # (2 x 3 n^4 FMA) and the geometric-factor product (9 n^3 FMA); per launch averaged
-        # over the domains like the bytes
-        vol_flops = sum(e * B * (12 * n1 ** 4 + 18 * n1 ** 3)
-                        for e, n1 in zip(ne, [d.order + 1 for d in w.domains])) / len(w.domains)
-        alu_peak = FP32_TFLOPS if prec == dghex.DGSEM_FP32_MIXED else FP64_TFLOPS
-        achieved_f = vol_flops / avg_s / 1e12
-        if vol_flops / alg["vol"] > alu_peak * 1e12 / (peak * 1e9):
-            # above the ridge point: the arithmetic pipe bounds the kernel
-            roof = {"bound": "alu", "achieved": achieved_f, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved_f / alu_peak, "traffic": None, "kernel": "vol",
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
-                    if prec == dghex.DGSEM_FP32_MIXED else "nominal FP64 (no measured FP64 peak)",
-                    "alg_flops_per_launch": vol_flops, "alg_bytes_per_launch": alg["vol"],
-                    "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
+    roof = hex_roofline(kstats, [d.order for d in w.domains], [d.elements.shape[0] for d in w.domains], ndof, B,
+                        prec == dghex.DGSEM_FP32_MIXED, peaks["hbm_gbs"] if peaks else None)
+    names = HEX_KERNELS
+    es = 4 if prec == dghex.DGSEM_FP32_MIXED else 8
     cpu = None
     if not args.no_cpu_baseline:
         v, sample, _, _, _ = time_oracle(name, seconds=15.0)
@@ -516,7 +528,8 @@ def main_hex(args, torch, dist, rank, world, local):
         "data": "synthetic",
         "config": {"workload": name, "precision": "fp32-mixed" if prec == dghex.DGSEM_FP32_MIXED else "fp64",
                    "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
-                   "elements": ne, "orders": [d.order for d in w.domains], "setup_s": setup_s,
+                   "elements": [int(d.elements.shape[0]) for d in w.domains],
+                   "orders": [d.order for d in w.domains], "setup_s": setup_s,
                    "vol_variants": variants,
                    "parallelism": "single-gpu",
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
