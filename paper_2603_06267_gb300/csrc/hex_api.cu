@@ -264,6 +264,7 @@ struct dghex_ctx {
   bool force_general_iface = false;         // use the general interface kernel even when onface
   int vol_variant[2][2] = {};               // element-stiffness launch variant [FP64, FP32][domain]
   int* d_g_face = nullptr;
+  void* d_ftab[2] = {nullptr, nullptr};     // face-kernel per-point tables [FP64, FP32] (built on first use)
   std::vector<long long> g_slot;
   int *d_g_fe = nullptr, *d_g_ce = nullptr, *d_g_pt = nullptr, *d_pt_idx = nullptr;
   long long* d_g_slot = nullptr;
@@ -684,6 +685,15 @@ int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
     a.np = Dp.n; a.nm = Dm.n;
     a.c2p = Dp.c * Dp.c; a.c2m = Dm.c * Dm.c;
     a.ng = c->ng; a.max_pts = c->max_pts;
+    if (a.onface) {
+      void*& tab = c->d_ftab[std::is_same<T, float>::value ? 1 : 0];
+      if (!tab) {
+        int rc = dmalloc(&tab, sizeof(T) * (size_t)hex::kFaceTab * (size_t)c->g_pt[c->ng]);
+        if (rc) return rc;
+        HCUDA(hex::launch_hex_iface_table<T>(a, static_cast<T*>(tab), s));
+      }
+      a.ftab = static_cast<const T*>(tab);
+    }
     HexTimer t(c, s, DGHEX_K_IFACE);
     HCUDA(hex::launch_hex_iface<T>(a, s));
   }
@@ -1649,6 +1659,7 @@ void dghex_destroy(dghex_ctx* c) {
   }
   dfree(c->d_g_fe); dfree(c->d_g_ce); dfree(c->d_g_pt); dfree(c->d_pt_idx); dfree(c->d_g_slot); dfree(c->d_pdat);
   dfree(c->d_g_face);
+  dfree(c->d_ftab[0]); dfree(c->d_ftab[1]);
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
   dfree(c->d_node_ptr); dfree(c->d_node_slot);
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);

@@ -16,6 +16,10 @@ namespace hex {
 constexpr int MAXN1 = 9;     // GLL nodes per direction (order <= 8)
 constexpr int MAXQ = 9;      // Gauss points per direction on a fine face
 constexpr int PDAT = 14;     // doubles per interface quadrature node
+// per-point table of the face-collapsed interface kernel: l and l' along the
+// two face axes of each side ([2 sides][2 axes][2][MAXN1]), then c+^2 a+
+// (t0, t1, n), c-^2 a- (t0, t1, n), W, gamma
+constexpr int kFaceTab = 8 * MAXN1 + 8;
 
 // Trilinear map of an element with corner vertices V (corner (i, j, k) at
 // index i + 2 j + 4 k, reference corner (2i-1, 2j-1, 2k-1)): X(r) and
@@ -220,6 +224,7 @@ struct HexIfaceArgs {
   double c2p, c2m;
   int ng, max_pts;
   int onface;                         // every Gauss node lies on one face of each side's element
+  const T* ftab;                      // [g_pt[ng]][kFaceTab] per-point tables of the face kernel
 };
 
 // Step: residual assembly (sum of a node's slots in ascending slot order)
@@ -291,6 +296,8 @@ template <typename T> cudaError_t launch_hex_pml(const HexPmlArgs<T>& a, int n, 
 constexpr int kHexVolVariants = 5;
 template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, int variant, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s);
+// setup: the face kernel's per-point tables in the working precision (once per precision)
+template <typename T> cudaError_t launch_hex_iface_table(const HexIfaceArgs<T>& a, T* tab, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_update(const HexUpdateArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_tail(const HexTailArgs<T>& a, cudaStream_t s);
 

@@ -370,6 +370,45 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
 // reference gradients cost O(n^2) each, and the projection back collapses the
 // same way: R_f (value and tangential terms) on the face layer and R_n (the
 // normal-derivative term) spread along each normal line by l_c'(+-1).
+// Per-point tables of the face-collapsed interface kernel (setup, once per
+// precision): for each side, the 1-D Lagrange values and derivatives along
+// the two axes of its face at the node's reference coordinate, c^2 times the
+// normal's reference components, then W and gamma; row p0 + j of group g.
+template <typename T>
+__global__ void __launch_bounds__(128) iface_table_kernel(const __grid_constant__ HexIfaceArgs<T> A, T* tab) {
+  const int g = blockIdx.x;
+  const int np = A.np, nm = A.nm;
+  const int p0 = A.g_pt[g], npts = A.g_pt[g + 1] - p0;
+  const int fp = A.g_face[2 * g], fm = A.g_face[2 * g + 1];
+  for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+    T* tb = tab + (long long)(p0 + j) * kFaceTab;
+    T* av = tb + 8 * MAXN1;
+    const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
+    double l[MAXN1], dl[MAXN1];
+    for (int side = 0; side < 2; ++side) {
+      const int f = side ? fm : fp, n = side ? nm : np, ax = f >> 1;
+      const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
+      const int ta[2] = {t0, t1};
+      const double* ref = d + 3 * side;
+      for (int k = 0; k < 2; ++k) {
+        lagrange(n, side ? A.xim : A.xip, ref[ta[k]], l, dl);
+        T* row = tb + (side * 2 + k) * 2 * MAXN1;
+        for (int i = 0; i < MAXN1; ++i) {
+          row[i] = i < n ? T(l[i]) : T(0);
+          row[MAXN1 + i] = i < n ? T(dl[i]) : T(0);
+        }
+      }
+      const double c2 = side ? A.c2m : A.c2p;
+      const double* a = d + 6 + 3 * side;
+      av[3 * side] = T(c2 * a[t0]);
+      av[3 * side + 1] = T(c2 * a[t1]);
+      av[3 * side + 2] = T(c2 * a[ax]);
+    }
+    av[6] = T(d[12]);
+    av[7] = T(d[13]);
+  }
+}
+
 template <typename T, int BB>
 __global__ void __launch_bounds__(128) hex_iface_face_kernel(const __grid_constant__ HexIfaceArgs<T> A) {
   using P = Pack<T, BB>;
@@ -389,31 +428,15 @@ __global__ void __launch_bounds__(128) hex_iface_face_kernel(const __grid_consta
   T* av = tb + (long long)Q * 8 * MAXN1; // [Q][8]: c+^2 a+ (t0, t1, n), c-^2 a- (t0, t1, n), W, gamma
   const int tid = threadIdx.x;
   const int fp = A.g_face[2 * g], fm = A.g_face[2 * g + 1];
-  const T c2p = T(A.c2p), c2m = T(A.c2m);
-  for (int j = tid; j < npts; j += blockDim.x) {
-    const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
-    double l[MAXN1], dl[MAXN1];
-    for (int side = 0; side < 2; ++side) {
-      const int f = side ? fm : fp, n = side ? nm : np, ax = f >> 1;
-      const int t0 = ax == 0 ? 1 : 0, t1 = ax == 2 ? 1 : 2;
-      const int ta[2] = {t0, t1};
-      const double* ref = d + 3 * side;
-      for (int k = 0; k < 2; ++k) {
-        lagrange(n, side ? A.xim : A.xip, ref[ta[k]], l, dl);
-        T* row = tb + ((j * 2 + side) * 2 + k) * 2 * MAXN1;
-        for (int i = 0; i < n; ++i) {
-          row[i] = T(l[i]);
-          row[MAXN1 + i] = T(dl[i]);
-        }
-      }
-      const double c2 = side ? A.c2m : A.c2p;
-      const double* a = d + 6 + 3 * side;
-      av[8 * j + 3 * side] = T(c2 * a[t0]);
-      av[8 * j + 3 * side + 1] = T(c2 * a[t1]);
-      av[8 * j + 3 * side + 2] = T(c2 * a[ax]);
+  {
+    // the group's rows of the per-point tables (built once at setup)
+    const T* trow = A.ftab + (long long)p0 * kFaceTab;
+    for (int i = tid; i < npts * kFaceTab; i += blockDim.x) {
+      const int r = i / kFaceTab, c = i - r * kFaceTab;
+      const T v = trow[i];
+      if (c < 8 * MAXN1) tb[r * 8 * MAXN1 + c] = v;
+      else av[r * 8 + c - 8 * MAXN1] = v;
     }
-    av[8 * j + 6] = T(d[12]);
-    av[8 * j + 7] = T(d[13]);
   }
   const int fe = A.g_fe[g], ce = A.g_ce[g];
   const long long slot = A.g_slot[g];
@@ -851,6 +874,13 @@ cudaError_t iface_bb(const HexIfaceArgs<T>& a, cudaStream_t s) {
 }
 
 template <typename T>
+cudaError_t launch_hex_iface_table(const HexIfaceArgs<T>& a, T* tab, cudaStream_t s) {
+  if (a.ng == 0) return cudaSuccess;
+  iface_table_kernel<T><<<a.ng, 128, 0, s>>>(a, tab);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s) {
   if (a.ng == 0 || a.Bp == 0) return cudaSuccess;
   constexpr int V = vec_width<T>();
@@ -902,6 +932,8 @@ template cudaError_t launch_hex_pml<float>(const HexPmlArgs<float>&, int, cudaSt
 template cudaError_t launch_hex_pml<double>(const HexPmlArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_hex_iface<float>(const HexIfaceArgs<float>&, cudaStream_t);
 template cudaError_t launch_hex_iface<double>(const HexIfaceArgs<double>&, cudaStream_t);
+template cudaError_t launch_hex_iface_table<float>(const HexIfaceArgs<float>&, float*, cudaStream_t);
+template cudaError_t launch_hex_iface_table<double>(const HexIfaceArgs<double>&, double*, cudaStream_t);
 template cudaError_t launch_hex_update<float>(const HexUpdateArgs<float>&, cudaStream_t);
 template cudaError_t launch_hex_update<double>(const HexUpdateArgs<double>&, cudaStream_t);
 template cudaError_t launch_hex_tail<float>(const HexTailArgs<float>&, cudaStream_t);
