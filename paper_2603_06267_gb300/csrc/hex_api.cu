@@ -265,6 +265,7 @@ struct dghex_ctx {
   int vol_variant[2][2] = {};               // element-stiffness launch variant [FP64, FP32][domain]
   int* d_g_face = nullptr;
   void* d_ftab[2] = {nullptr, nullptr};     // face-kernel per-point tables [FP64, FP32] (built on first use)
+  void* d_gtab[2] = {nullptr, nullptr};     // general-kernel per-point tables [FP64, FP32] (built on first use)
   std::vector<long long> g_slot;
   int *d_g_fe = nullptr, *d_g_ce = nullptr, *d_g_pt = nullptr, *d_pt_idx = nullptr;
   long long* d_g_slot = nullptr;
@@ -693,6 +694,14 @@ int launch_residual(dghex_ctx* c, cudaStream_t s, const void* pfield) {
         HCUDA(hex::launch_hex_iface_table<T>(a, static_cast<T*>(tab), s));
       }
       a.ftab = static_cast<const T*>(tab);
+    } else {
+      void*& tab = c->d_gtab[std::is_same<T, float>::value ? 1 : 0];
+      if (!tab) {
+        int rc = dmalloc(&tab, sizeof(T) * (size_t)hex::kGenTab * (size_t)c->g_pt[c->ng]);
+        if (rc) return rc;
+        HCUDA(hex::launch_hex_iface_gtable<T>(a, static_cast<T*>(tab), s));
+      }
+      a.gtab = static_cast<const T*>(tab);
     }
     HexTimer t(c, s, DGHEX_K_IFACE);
     HCUDA(hex::launch_hex_iface<T>(a, s));
@@ -1659,7 +1668,7 @@ void dghex_destroy(dghex_ctx* c) {
   }
   dfree(c->d_g_fe); dfree(c->d_g_ce); dfree(c->d_g_pt); dfree(c->d_pt_idx); dfree(c->d_g_slot); dfree(c->d_pdat);
   dfree(c->d_g_face);
-  dfree(c->d_ftab[0]); dfree(c->d_ftab[1]);
+  dfree(c->d_ftab[0]); dfree(c->d_ftab[1]); dfree(c->d_gtab[0]); dfree(c->d_gtab[1]);
   dfree(c->d_fp_ptr); dfree(c->d_fp_off); dfree(c->d_Bm); dfree(c->d_ent_k); dfree(c->d_modal);
   dfree(c->d_node_ptr); dfree(c->d_node_slot);
   dfree(c->d_Mloc); dfree(c->d_M); dfree(c->d_Minv64); dfree(c->d_Minv32);

@@ -20,6 +20,10 @@ constexpr int PDAT = 14;     // doubles per interface quadrature node
 // two face axes of each side ([2 sides][2 axes][2][MAXN1]), then c+^2 a+
 // (t0, t1, n), c-^2 a- (t0, t1, n), W, gamma
 constexpr int kFaceTab = 8 * MAXN1 + 8;
+// per-point table of the general interface kernel: l and l' along the three
+// reference axes of each side ([2 sides][3 axes][2][MAXN1]), then a+ (3),
+// a- (3), W, gamma
+constexpr int kGenTab = 12 * MAXN1 + 8;
 
 // Trilinear map of an element with corner vertices V (corner (i, j, k) at
 // index i + 2 j + 4 k, reference corner (2i-1, 2j-1, 2k-1)): X(r) and
@@ -225,6 +229,7 @@ struct HexIfaceArgs {
   int ng, max_pts;
   int onface;                         // every Gauss node lies on one face of each side's element
   const T* ftab;                      // [g_pt[ng]][kFaceTab] per-point tables of the face kernel
+  const T* gtab;                      // [g_pt[ng]][kGenTab] per-point tables of the general kernel
 };
 
 // Step: residual assembly (sum of a node's slots in ascending slot order)
@@ -298,6 +303,7 @@ template <typename T> cudaError_t launch_hex_vol(const HexVolArgs<T>& a, int n, 
 template <typename T> cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s);
 // setup: the face kernel's per-point tables in the working precision (once per precision)
 template <typename T> cudaError_t launch_hex_iface_table(const HexIfaceArgs<T>& a, T* tab, cudaStream_t s);
+template <typename T> cudaError_t launch_hex_iface_gtable(const HexIfaceArgs<T>& a, T* tab, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_update(const HexUpdateArgs<T>& a, cudaStream_t s);
 template <typename T> cudaError_t launch_hex_tail(const HexTailArgs<T>& a, cudaStream_t s);
 

@@ -226,22 +226,21 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
   T* tm = tp + (long long)Q * 6 * np;     // [Q][3][2][nm]
   T* av = tm + (long long)Q * 6 * nm;     // [Q][8]: a+(3) a-(3) W gamma
   const int tid = threadIdx.x;
-  for (int j = tid; j < npts; j += blockDim.x) {
-    const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
-    double l[MAXN1], dl[MAXN1];
-    for (int ax = 0; ax < 3; ++ax) {
-      lagrange(np, A.xip, d[ax], l, dl);
-      for (int k = 0; k < np; ++k) {
-        tp[((j * 3 + ax) * 2) * np + k] = T(l[k]);
-        tp[((j * 3 + ax) * 2 + 1) * np + k] = T(dl[k]);
-      }
-      lagrange(nm, A.xim, d[3 + ax], l, dl);
-      for (int k = 0; k < nm; ++k) {
-        tm[((j * 3 + ax) * 2) * nm + k] = T(l[k]);
-        tm[((j * 3 + ax) * 2 + 1) * nm + k] = T(dl[k]);
+  {
+    // the group's rows of the per-point tables (built once at setup), into
+    // the per-order strides of the shared arrays
+    const T* trow = A.gtab + (long long)p0 * kGenTab;
+    for (int i = tid; i < npts * kGenTab; i += blockDim.x) {
+      const int j = i / kGenTab, c = i - j * kGenTab;
+      const T v = trow[i];
+      if (c < 12 * MAXN1) {
+        const int side = c / (6 * MAXN1), r = (c / MAXN1) % 6, k = c % MAXN1;   // r = 2 axis + (0: l, 1: l')
+        if (side == 0 && k < np) tp[(j * 6 + r) * np + k] = v;
+        else if (side == 1 && k < nm) tm[(j * 6 + r) * nm + k] = v;
+      } else {
+        av[8 * j + c - 12 * MAXN1] = v;
       }
     }
-    for (int k = 0; k < 8; ++k) av[8 * j + k] = T(d[6 + k]);
   }
   const int fe = A.g_fe[g], ce = A.g_ce[g];
   const long long slot = A.g_slot[g];
@@ -370,6 +369,33 @@ __global__ void __launch_bounds__(128) hex_iface_kernel(const __grid_constant__ 
 // reference gradients cost O(n^2) each, and the projection back collapses the
 // same way: R_f (value and tangential terms) on the face layer and R_n (the
 // normal-derivative term) spread along each normal line by l_c'(+-1).
+// Per-point tables of the general interface kernel (setup, once per
+// precision): for each side, the 1-D Lagrange values and derivatives along
+// its three reference axes at the node's reference coordinates, then the
+// normal's reference components a+ and a-, W and gamma; row p0 + j of group g.
+template <typename T>
+__global__ void __launch_bounds__(128) iface_gtable_kernel(const __grid_constant__ HexIfaceArgs<T> A, T* tab) {
+  const int g = blockIdx.x;
+  const int p0 = A.g_pt[g], npts = A.g_pt[g + 1] - p0;
+  for (int j = threadIdx.x; j < npts; j += blockDim.x) {
+    T* row = tab + (long long)(p0 + j) * kGenTab;
+    const double* d = A.pdat + (long long)PDAT * A.pt_idx[p0 + j];
+    double l[MAXN1], dl[MAXN1];
+    for (int side = 0; side < 2; ++side) {
+      const int n = side ? A.nm : A.np;
+      for (int ax = 0; ax < 3; ++ax) {
+        lagrange(n, side ? A.xim : A.xip, d[3 * side + ax], l, dl);
+        T* r = row + (side * 6 + ax * 2) * MAXN1;
+        for (int k = 0; k < MAXN1; ++k) {
+          r[k] = k < n ? T(l[k]) : T(0);
+          r[MAXN1 + k] = k < n ? T(dl[k]) : T(0);
+        }
+      }
+    }
+    for (int k = 0; k < 8; ++k) row[12 * MAXN1 + k] = T(d[6 + k]);
+  }
+}
+
 // Per-point tables of the face-collapsed interface kernel (setup, once per
 // precision): for each side, the 1-D Lagrange values and derivatives along
 // the two axes of its face at the node's reference coordinate, c^2 times the
@@ -881,6 +907,13 @@ cudaError_t launch_hex_iface_table(const HexIfaceArgs<T>& a, T* tab, cudaStream_
 }
 
 template <typename T>
+cudaError_t launch_hex_iface_gtable(const HexIfaceArgs<T>& a, T* tab, cudaStream_t s) {
+  if (a.ng == 0) return cudaSuccess;
+  iface_gtable_kernel<T><<<a.ng, 128, 0, s>>>(a, tab);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_hex_iface(const HexIfaceArgs<T>& a, cudaStream_t s) {
   if (a.ng == 0 || a.Bp == 0) return cudaSuccess;
   constexpr int V = vec_width<T>();
@@ -934,6 +967,8 @@ template cudaError_t launch_hex_iface<float>(const HexIfaceArgs<float>&, cudaStr
 template cudaError_t launch_hex_iface<double>(const HexIfaceArgs<double>&, cudaStream_t);
 template cudaError_t launch_hex_iface_table<float>(const HexIfaceArgs<float>&, float*, cudaStream_t);
 template cudaError_t launch_hex_iface_table<double>(const HexIfaceArgs<double>&, double*, cudaStream_t);
+template cudaError_t launch_hex_iface_gtable<float>(const HexIfaceArgs<float>&, float*, cudaStream_t);
+template cudaError_t launch_hex_iface_gtable<double>(const HexIfaceArgs<double>&, double*, cudaStream_t);
 template cudaError_t launch_hex_update<float>(const HexUpdateArgs<float>&, cudaStream_t);
 template cudaError_t launch_hex_update<double>(const HexUpdateArgs<double>&, cudaStream_t);
 template cudaError_t launch_hex_tail<float>(const HexTailArgs<float>&, cudaStream_t);
