@@ -92,6 +92,31 @@ def test_sign_error_between_forcing_and_projection_fails_the_coupled_energy_pin(
         box_pins.test_coupled_energy_first_order_drift()
 
 
+@pytest.mark.parametrize("mistake", ["kappa_rho", "kappa_sign", "b_sign", "weights_doubled"])
+def test_forcing_scale_and_sign_mistakes_fail_the_rayleigh_pin(monkeypatch, mistake):
+    """kappa = rho instead of rho c^2, kappa or B with the wrong sign as a
+    whole (consistent between f and g, so the energy pin cannot see it), or
+    face weights doubled: the radiated pressure of a prescribed membrane
+    motion is then wrong in scale or sign."""
+    orig = O.OracleProblem._pmut_matrix
+
+    def mutant(self):
+        orig(self)
+        if self.B is None:
+            return
+        if mistake == "kappa_rho":
+            self.kappa = self.meshes[0].rho
+        elif mistake == "kappa_sign":
+            self.kappa = -self.kappa
+        elif mistake == "b_sign":
+            self.B = -self.B
+        else:
+            self.B = 2.0 * self.B
+    monkeypatch.setattr(O.OracleProblem, "_pmut_matrix", mutant)
+    with pytest.raises(AssertionError):
+        box_pins.test_rayleigh_integral_of_a_baffled_membrane()
+
+
 # ---------------------------------------------------------------- hex oracle
 def test_gradient_with_j_inverse_untransposed_fails_the_linear_patch(monkeypatch):
     """grad psi = J^-1 grad^ psi instead of J^-T grad^ psi in the element

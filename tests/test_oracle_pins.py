@@ -287,7 +287,8 @@ def test_coupled_energy_first_order_drift():
     """Coupled, zeta = 0, after the burst: the semi-discrete energy of
     eqs. (semi_SEM)-(semi_PMUT) is conserved up to the one-step lag of
     g(p^n) in Algorithm 1, so its drift halves when dt halves.  A sign error
-    between f and g, or a wrong kappa, breaks this."""
+    between f and g breaks this (kappa's value and the overall sign of the
+    coupling are pinned by the Rayleigh-integral test)."""
     drifts = []
     for scale in (1.0, 0.5):
         w = W.config1_single_pmut(nsteps=int(700 / scale))
@@ -302,6 +303,55 @@ def test_coupled_energy_first_order_drift():
         drifts.append((e.max() - e.min()) / e.mean())
     assert drifts[0] < 0.2
     assert 1.7 < drifts[0] / drifts[1] < 2.3
+
+
+def _rayleigh_case(N):
+    """A 0.3 mm membrane (mode (1,1), unit peak) in the rigid z = 0 face of a
+    0.6 mm water cube, moved with a prescribed acceleration: a huge modal mass
+    makes the fluid's reaction negligible and no stiffness, so Algorithm 1
+    gives q''^{n+1} = (eta / mu) phi^n exactly.  Returns the oracle's on-axis
+    trace at z0 = 0.15 mm and the Rayleigh integral of the same motion."""
+    L, a, z0, f = 0.6e-3, 0.3e-3, 0.15e-3, 8.0e6
+    dom = W.Domain((0, 0, 0), (L, L, L), (8, 8, 8), N)
+    pm = W.PmutArray(centers=np.array([[0.3e-3, 0.3e-3]]), side=a, freq_hz=np.array([[1.0]]),
+                     damping=np.array([[0.0]]), eta=np.array([[1.0e6]]), modal_mass=np.array([[1.0e6]]))
+    rec = np.array([[0.3e-3, 0.3e-3, z0]])
+    w = W.Workload("rayleigh", [dom], 10, rec, pm, drive_delay=np.zeros((1, 1)), drive_amp=np.ones((1, 1)),
+                   burst_freq=f, burst_cycles=1.0)
+    P = O.OracleProblem(w)
+    dt = P.stable_dt()
+    # before the first echo: the membrane edge's image in the x = 0 wall is
+    # 0.474 mm from the receiver (0.316 us)
+    S = int(0.31e-6 / dt)
+    tr = P.run(nsteps=S, dt=dt)[0, 0]                      # sample n = p^{n+1}
+    Tb = 1.0 / f
+
+    def qdd(s):                                             # eta / mu = 1 m/s^2 per volt
+        on = (s >= 0) & (s <= Tb)
+        return np.where(on, np.sin(2 * math.pi * f * s) * 0.5 * (1 - np.cos(2 * math.pi * s / Tb)), 0.0)
+    g, gw = np.polynomial.legendre.leggauss(80)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    wts = np.outer(gw, gw) * (a / 2) ** 2
+    phi = (1 - X ** 2) ** 2 * (1 - Y ** 2) ** 2
+    R = np.sqrt((X * a / 2) ** 2 + (Y * a / 2) ** 2 + z0 ** 2)
+    t = (np.arange(S) + 1) * dt
+    # p(x, t) = rho / (2 pi) int a_n(y, t - R / c) / R dA for a baffled surface
+    ref = np.array([dom.rho / (2 * math.pi) * np.sum(wts * qdd(tt - dt - R / dom.c) * phi / R) for tt in t])
+    return tr, ref
+
+
+def test_rayleigh_integral_of_a_baffled_membrane():
+    """Prescribed membrane motion radiating into the half space before any
+    wall echo: the pressure is the Rayleigh integral (rigid baffle), which
+    fixes kappa = rho c^2, the sign and face weights of B and the forcing, and
+    the wave speed; the error falls spectrally from N = 4 to N = 6."""
+    errs = []
+    for N in (4, 6):
+        tr, ref = _rayleigh_case(N)
+        assert np.abs(ref).max() > 0
+        errs.append(np.linalg.norm(tr - ref) / np.linalg.norm(ref))
+    assert errs[0] < 0.05 and errs[1] < 0.006, errs
+    assert errs[0] / errs[1] > 5, errs
 
 
 def test_symmetry_centred_pmut():
