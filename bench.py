@@ -356,33 +356,11 @@ def main():
         return
     value = whole_job_rate(ndof, B, args.steps, world, ms / 1e3)
     # roofline of the dominant kernel
-    names = ["pmut_recv", "iface", "vol_primary", "vol_secondary", "pml"]
-    kdom = max(range(4), key=lambda k: kstats[k][0])
+    names = BOX_KERNELS
     es = 4 if prec == dgsem.DGSEM_FP32_MIXED else 8
     peaks = measured_peaks()
-    roof = None
-    if kdom >= 2 and kstats[kdom][1] > 0:
-        d = w.domains[kdom - 2]
-        nodes = int(np.prod([d.nelem[i] * d.order + 1 for i in range(3)]))
-        alg_bytes = nodes * B * 4 * es          # read p, read v, write v, write p_next
-        avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
-        achieved = alg_bytes / avg_s / 1e9
-        if prec == dgsem.DGSEM_FP32_MIXED:
-            peak = peaks["hbm_gbs"] if peaks else 6800.0
-            roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": (NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])) if B in (1, 64) else None),
-                    "kernel": names[kdom], "peak_source": "measured" if peaks else "fallback",
-                    "alg_bytes_per_launch": alg_bytes}
-        else:
-            # FP64 path: bound by the FP64 pipe; peak derived from the nominal
-            # 1.25 TFLOP/s FP64 rate of GB300 at the 2070 MHz maximum SM clock
-            N = d.order
-            flop_per_node = 2 * (3 * (N + 2) + 4)
-            achieved_f = nodes * B * flop_per_node / avg_s / 1e12
-            roof = {"bound": "alu", "achieved": achieved_f, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved_f / FP64_TFLOPS, "traffic": NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, names[kdom])),
-                    "kernel": names[kdom], "peak_source": "nominal FP64 (no measured FP64 peak)",
-                    "hbm_achieved_gbs": nodes * B * 4 * es / avg_s / 1e9}
+    roof = box_roofline(kstats, w.domains, B, prec == dgsem.DGSEM_FP32_MIXED, peaks["hbm_gbs"] if peaks else None,
+                        lambda kernel: NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, kernel)))
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         v, sample, _, _, _ = time_oracle(name, seconds=15.0)
@@ -405,6 +383,39 @@ def main():
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+BOX_KERNELS = ["pmut_recv", "iface", "vol_primary", "vol_secondary", "pml"]
+
+
+def box_roofline(kstats, domains, B, fp32, hbm_gbs, traffic_of):
+    """Roofline block of the box path for its dominant volume kernel, from
+    per-kind (total ms, launches).  Algorithmic bytes per launch: p read, v
+    read and written, p_next written once per node of the box and pattern
+    (4 words); FP32 reports against the copy bandwidth, FP64 against the FP64
+    rate with 2 (3 (N + 2) + 4) flops per node (the three assembled 1-D
+    stencils and the update).  traffic_of(kernel) gives the ncu DRAM bytes
+    per launch where a capture of this kernel exists (None otherwise)."""
+    kdom = max(range(4), key=lambda k: kstats[k][0])
+    if kdom < 2 or kstats[kdom][1] == 0:
+        return None
+    es = 4 if fp32 else 8
+    name = BOX_KERNELS[kdom]
+    d = domains[kdom - 2]
+    nodes = int(np.prod([d.nelem[i] * d.order + 1 for i in range(3)]))
+    alg_bytes = nodes * B * 4 * es
+    avg_s = kstats[kdom][0] / kstats[kdom][1] / 1e3
+    achieved = alg_bytes / avg_s / 1e9
+    if fp32:
+        peak = hbm_gbs if hbm_gbs else 6800.0
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_of(name) if B in (1, 64) else None, "kernel": name,
+                "peak_source": "measured" if hbm_gbs else "fallback", "alg_bytes_per_launch": alg_bytes}
+    flop_per_node = 2 * (3 * (d.order + 2) + 4)
+    achieved_f = nodes * B * flop_per_node / avg_s / 1e12
+    return {"bound": "alu", "achieved": achieved_f, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved_f / FP64_TFLOPS, "traffic": traffic_of(name), "kernel": name,
+            "peak_source": "nominal FP64 (no measured FP64 peak)", "hbm_achieved_gbs": achieved}
 
 
 HEX_KERNELS = ["pmut", "vol", "iface", "update", "tail", "pml"]
