@@ -125,3 +125,16 @@ def test_invalid_hex_mesh_rejected_without_gpu(lib):
     with pytest.raises(dgsem.DgsemError) as e:
         dghex.dghex_mesh_create([prim], pmut_faces=inner)
     assert e.value.code == dgsem.DGSEM_EINVAL and "boundary" in str(e.value)
+
+
+def test_volume_variant_calls_refuse_a_null_context_without_gpu(lib):
+    """The element-stiffness variant calls check their arguments on the host
+    before any device work: a NULL context is DGSEM_EINVAL."""
+    import ctypes
+    from paper_2603_06267_gb300 import dgsem
+    n = ctypes.c_int(-1)
+    assert lib.dghex_num_volume_variants(None, ctypes.byref(n)) == dgsem.DGSEM_EINVAL
+    v = (ctypes.c_int * 2)(0, 0)
+    assert lib.dghex_set_volume_variant(None, dgsem.DGSEM_FP32_MIXED, v) == dgsem.DGSEM_EINVAL
+    out = (ctypes.c_int * 2)()
+    assert lib.dghex_autotune(None, dgsem.DGSEM_FP32_MIXED, 8, 1, out, None) == dgsem.DGSEM_EINVAL
