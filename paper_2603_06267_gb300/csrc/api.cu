@@ -1499,8 +1499,11 @@ int dgsem_run(dgsem_ctx* c, int precision, int batch, int nsteps, const double* 
   if (rc) return rc;
   if ((rc = setup_receivers(c, n_recv, recv_xyz))) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == DGSEM_FP64) return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
-  return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
+  // a run that fails part-way leaves no state to continue from
+  rc = precision == DGSEM_FP64 ? run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s)
+                               : run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
+  if (rc != DGSEM_OK) c->state_valid = false;
+  return rc;
 }
 
 int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* batch, int nsteps,
@@ -1529,8 +1532,11 @@ int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* bat
     if ((rc = setup_receivers(c, R, R > 0 ? recv_xyz[i] : nullptr))) return rc;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (precision == DGSEM_FP64) return run_multi_impl<double>(n, ctxs, nsteps, drive, n_recv, traces, flags, s);
-  return run_multi_impl<float>(n, ctxs, nsteps, drive, n_recv, traces, flags, s);
+  const int rc = precision == DGSEM_FP64 ? run_multi_impl<double>(n, ctxs, nsteps, drive, n_recv, traces, flags, s)
+                                         : run_multi_impl<float>(n, ctxs, nsteps, drive, n_recv, traces, flags, s);
+  if (rc != DGSEM_OK)
+    for (int i = 0; i < n; ++i) ctxs[i]->state_valid = false;
+  return rc;
 }
 
 int dgsem_get_pressure(const dgsem_ctx* c, double* p, size_t len) {

@@ -1228,8 +1228,11 @@ int dghex_run(dghex_ctx* c, int precision, int batch, int nsteps, const double* 
   int rc = ensure_run_state(c, precision, batch);
   if (rc) return rc;
   if ((rc = setup_receivers(c, n_recv, recv_xyz))) return rc;
-  if (precision == DGSEM_FP32_MIXED) return run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s);
-  return run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
+  // a run that fails part-way leaves no state to continue from
+  rc = precision == DGSEM_FP32_MIXED ? run_impl<float>(c, nsteps, drive, n_recv, traces, flags, s)
+                                     : run_impl<double>(c, nsteps, drive, n_recv, traces, flags, s);
+  if (rc != DGSEM_OK) c->state_valid = false;
+  return rc;
 }
 
 int dghex_get_pressure(const dghex_ctx* c, double* p, size_t len) {
