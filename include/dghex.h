@@ -168,8 +168,8 @@ int dghex_state_load(dghex_ctx* ctx, const void* buf, size_t len);
 int dghex_get_matches(const dghex_ctx* ctx, int* q, int* coarse_face, double* ref, long long n);
 
 /* Run nsteps steps of Algorithm 1 for `batch` drive patterns (arguments,
- * flags, trace convention and the DGSEM_EUNSTABLE divergence report as
- * dgsem_run in dgsem.h). */
+ * flags, trace convention, the DGSEM_EUNSTABLE divergence report and the
+ * invalid state after a failed run as dgsem_run in dgsem.h). */
 int dghex_run(dghex_ctx* ctx, int precision, int batch, int nsteps, const double* drive, int n_recv,
               const double* recv_xyz, double* traces, int flags, void* stream);
 

@@ -239,7 +239,11 @@ int dgsem_get_voltages(const dgsem_ctx* ctx, double* out, size_t n);
  * Without DGSEM_RUN_CONTINUE the state restarts from rest (or from the state
  * given by the last dgsem_set_state/dgsem_state_load) and n0 = 0.
  * Returns DGSEM_EUNSTABLE when the receiver traces or the PMUT state are not
- * finite at the end of the run (the step diverged); the state is then invalid. */
+ * finite at the end of the run (the step diverged); the state is then invalid.
+ * Any other failure once the run has started (DGSEM_ECUDA, DGSEM_ETIMEOUT,
+ * DGSEM_ENOMEM) leaves the state invalid too, so a later DGSEM_RUN_CONTINUE
+ * is refused (DGSEM_ESTATE); argument errors found before the run starts
+ * leave it as it was. */
 int dgsem_run(dgsem_ctx* ctx, int precision, int batch, int nsteps, const double* drive,
               int n_recv, const double* recv_xyz, double* traces, int flags, void* stream);
 
