@@ -331,3 +331,43 @@ def test_unstructured_nonconforming_interface_matching():
     assert straddled > 0
     assert abs(p.K - p.K.T).max() < 1e-12 * abs(p.K).max()
     assert np.max(np.abs(p.K @ np.ones(p.nh))) < 1e-12 * abs(p.K).sum(axis=1).max()
+
+
+def test_rayleigh_integral_on_a_distorted_mesh():
+    """A 0.3 mm membrane moved with a prescribed acceleration (huge modal
+    mass, no stiffness) in the flat z = 0 face of a distorted 0.6 mm cube:
+    before the first wall echo the on-axis pressure is the Rayleigh integral
+    of a baffled surface, p = rho / (2 pi) int a_n(y, t - R / c) / R dA.  Pins
+    the Nanson-weighted PMUT matrix, kappa and the curved-element stiffness
+    together; the error falls spectrally from N = 4 to N = 5."""
+    a, z0, f = 0.3e-3, 0.15e-3, 8.0e6
+    errs = []
+    for N in (4, 5):
+        w = H.distorted_one_domain(nel=(8, 8, 8), order=N, h=75e-6, amp=0.15, nsteps=10)
+        w.pmuts = W.PmutArray(centers=np.array([[0.3e-3, 0.3e-3]]), side=a, freq_hz=np.array([[1.0]]),
+                              damping=np.array([[0.0]]), eta=np.array([[1.0e6]]),
+                              modal_mass=np.array([[1.0e6]]))
+        w.receivers = np.array([[0.3e-3, 0.3e-3, z0]])
+        w.drive_delay, w.drive_amp = np.zeros((1, 1)), np.ones((1, 1))
+        w.burst_freq, w.burst_cycles = f, 1.0
+        P = HO.HexOracleProblem(w)
+        dt = P.stable_dt()
+        S = int(0.31e-6 / dt)          # the x = 0 wall's first echo arrives at 0.316 us
+        tr = P.run(nsteps=S, dt=dt)[0, 0]
+        Tb = 1.0 / f
+
+        def qdd(s):
+            on = (s >= 0) & (s <= Tb)
+            return np.where(on, np.sin(2 * math.pi * f * s) * 0.5 * (1 - np.cos(2 * math.pi * s / Tb)), 0.0)
+        g, gw = np.polynomial.legendre.leggauss(80)
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        wts = np.outer(gw, gw) * (a / 2) ** 2
+        phi = (1 - X ** 2) ** 2 * (1 - Y ** 2) ** 2
+        R = np.sqrt((X * a / 2) ** 2 + (Y * a / 2) ** 2 + z0 ** 2)
+        rho, c = w.domains[0].rho, w.domains[0].c
+        t = (np.arange(S) + 1) * dt
+        ref = np.array([rho / (2 * math.pi) * np.sum(wts * qdd(tt - dt - R / c) * phi / R) for tt in t])
+        assert np.abs(ref).max() > 0
+        errs.append(np.linalg.norm(tr - ref) / np.linalg.norm(ref))
+    assert errs[0] < 0.06 and errs[1] < 0.012, errs
+    assert errs[0] / errs[1] > 3, errs
