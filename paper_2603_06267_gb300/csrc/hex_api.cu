@@ -1222,8 +1222,9 @@ int dghex_run(dghex_ctx* c, int precision, int batch, int nsteps, const double* 
   if (precision != DGSEM_FP64 && precision != DGSEM_FP32_MIXED) return hfail(DGSEM_EINVAL, "bad precision");
   if (batch < 1 || nsteps < 0 || n_recv < 0) return hfail(DGSEM_EINVAL, "batch >= 1, nsteps >= 0, n_recv >= 0");
   if (n_recv > 0 && (!recv_xyz || !traces)) return hfail(DGSEM_EINVAL, "receivers without positions or traces");
-  if ((flags & DGSEM_RUN_CONTINUE) && c->state_valid && (c->prec != precision || c->batch != batch))
-    return hfail(DGSEM_ESTATE, "continuing run with a different precision or batch");
+  if ((flags & DGSEM_RUN_CONTINUE) && (!c->state_valid || c->prec != precision || c->batch != batch))
+    return hfail(DGSEM_ESTATE, "DGSEM_RUN_CONTINUE needs a valid state from a run (or a loaded checkpoint) "
+                               "with the same precision and batch");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = ensure_run_state(c, precision, batch);
   if (rc) return rc;
