@@ -55,12 +55,14 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config4_batched",
-                    choices=["config4_batched", "config3_array32", "config2_array16", "config1_single_pmut",
-                             "hex_c3_like", "hex_c2_like"])
+                    choices=["config4_batched", "config4b_uneven", "config3_array32", "config2_array16",
+                             "config1_single_pmut", "hex_c3_like", "hex_c2_like"])
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64"])
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the FP32-vs-FP64 check of the benchmarked configuration (FP32 lines)")
     ap.add_argument("--tiles", default=None,
                     help="comma-separated volume-kernel tile variant per box, or element-stiffness variant per "
                          "domain on general hexahedra (skips the autotuner)")
@@ -110,7 +112,8 @@ def whole_job_rate(ndof, batch, steps, world, seconds):
 
 
 def default_precision(name):
-    return "fp32" if name in ("config4_batched", "config3_array32", "hex_c3_like", "hex_c2_like") else "fp64"
+    return "fp32" if name in ("config4_batched", "config4b_uneven", "config3_array32", "hex_c3_like",
+                              "hex_c2_like") else "fp64"
 
 
 def is_hex(name):
@@ -135,29 +138,77 @@ def oracle_sample(name):
     return W.small_two_domain(nx_p=8, nz_p=4, nx_s=4, nz_s=8, n_pmut_side=2, nsteps=1)
 
 
-def time_oracle(name, seconds=15.0, chunk=None):
-    """Oracle Gdof-steps/s on the bounded sample (single host thread: scipy's
-    sparse mat-vec and numpy's element-wise kernels run on one core)."""
+def _loop_seconds(P, nsteps, dt):
+    """Wall time of the oracle's time loop alone: the run's per-step callback
+    marks the end of step 0 and of the last step, so setup inside run() (the
+    receiver matrix, the drive array, the initial state) stays outside; the
+    first step's share is added back from the per-step mean."""
+    marks = {}
+
+    def cb(n, **_):
+        if n == 0 or n == nsteps - 1:
+            marks[n] = time.perf_counter()
+
+    P.run(nsteps=nsteps, dt=dt, batch=1, callback=cb)
+    return (marks[nsteps - 1] - marks[0]) * nsteps / (nsteps - 1)
+
+
+def _oracle_worker_init(name):
+    global _WORKER
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    w = oracle_sample(name)
+    P = _oracle_problem(w)
+    _WORKER = (P, P.stable_dt())
+
+
+def _oracle_worker_run(nsteps):
+    P, dt = _WORKER
+    return _loop_seconds(P, nsteps, dt)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(name, seconds=15.0, chunk=None, parallel=True):
+    """Oracle Gdof-steps/s on the bounded sample, time loop only: on one host
+    thread (scipy's sparse mat-vec and numpy's element-wise kernels run on one
+    core), and on every host core as independent processes, one drive pattern
+    each (the patterns of a batch are independent problems).  Returns the
+    all-core figure (and the one-thread figure inside the sample text)."""
     w = oracle_sample(name)
     P = _oracle_problem(w)
     dt = P.stable_dt()
     n = 8
     while True:
-        t0 = time.perf_counter()
-        P.run(nsteps=n, dt=dt, batch=1)
-        el = time.perf_counter() - t0
+        el = _loop_seconds(P, n, dt)
         if el > 0.5 or n >= 1 << 20:
             break
         n *= 4
     per_step = el / n
-    S = max(1, int(seconds / per_step)) if chunk is None else chunk
-    t0 = time.perf_counter()
-    P.run(nsteps=S, dt=dt, batch=1)
-    el = time.perf_counter() - t0
+    S = max(2, int(seconds / 2 / per_step)) if chunk is None else max(2, chunk)
+    el = _loop_seconds(P, S, dt)
+    one = P.nh * S / el / 1e9
     sample = (f"{w.name}: primary {_nelem(w.domains[0])} N={w.domains[0].order}"
               + (f" + secondary {_nelem(w.domains[1])} N={w.domains[1].order}" if len(w.domains) > 1 else "")
-              + f", {P.nh} nodes, {S} steps, batch 1")
-    return P.nh * S / el / 1e9, sample, P, w, dt
+              + f", {P.nh} nodes, {S} steps per pattern, time loop only")
+    cores = host_cores()
+    if not parallel or cores < 2:
+        return one, sample + f"; 1 thread: {one:.4g} Gdof-steps/s", 1, one
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")           # no fork after the GPU is in use
+    with ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(name,)) as pool:
+        pool.map(_oracle_worker_run, [2] * cores, chunksize=1)      # every worker built and warm
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker_run, [S] * cores, chunksize=1)
+        wall = time.perf_counter() - t0
+    allc = P.nh * S * cores / wall / 1e9
+    sample += (f"; {cores} processes x 1 pattern each (wall time of the pool, loops only); "
+               f"1 thread: {one:.4g} Gdof-steps/s")
+    return allc, sample, cores, one
 
 
 def _oracle_problem(w):
@@ -234,35 +285,37 @@ def measured_peaks():
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle on a bounded sample of the workload."""
+    """Reference arm: the CPU oracle as it stands on a bounded sample of the
+    workload, on every host core (one process and one drive pattern per core;
+    time loops only, setup outside), K timed steps of about 0.5 s each."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     name = args.workload
-    prec = args.precision or default_precision(name)
     w = oracle_sample(name)
     P = _oracle_problem(w)
     dt = P.stable_dt()
-    # chunk of oracle time steps per bench step: about 0.5 s each
-    n = 4
-    t0 = time.perf_counter()
-    P.run(nsteps=n, dt=dt, batch=1)
-    per = (time.perf_counter() - t0) / n
-    chunk = max(1, int(0.5 / per))
-    for _ in range(args.warmup):
-        P.run(nsteps=chunk, dt=dt, batch=1)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        P.run(nsteps=chunk, dt=dt, batch=1)
-    el = time.perf_counter() - t0
-    value = P.nh * chunk * args.steps / el / 1e9
-    sample = (f"{w.name}: {P.nh} nodes, {chunk} oracle time steps per bench step, batch 1 "
-              f"(same element sizes/orders/PMUT model as {name})")
+    per = _loop_seconds(P, 8, dt) / 8
+    chunk = max(2, int(0.5 / per))
+    cores = host_cores()
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_oracle_worker_init, initargs=(name,)) as pool:
+        for _ in range(max(1, args.warmup)):
+            pool.map(_oracle_worker_run, [chunk] * cores, chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_worker_run, [chunk] * cores, chunksize=1)
+        el = time.perf_counter() - t0
+    value = P.nh * chunk * cores * args.steps / el / 1e9
+    sample = (f"{w.name}: {P.nh} nodes, {chunk} oracle time steps per bench step on each of {cores} processes "
+              f"(one drive pattern each; same element sizes/orders/PMUT model as {name}; time loops only)")
     out = {"impl": "reference", "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": name, "precision": "fp64 (oracle)", "sample": sample},
-           "cpu_baseline": {"value": value, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "Gdof-steps/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": value, "unit": "Gdof-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -286,6 +339,9 @@ def main():
     name = args.workload
     if is_hex(name):
         main_hex(args, torch, dist, rank, world, local)
+        return
+    if name == "config4b_uneven":
+        main_multi(args, torch, dist, rank, world, local)
         return
     prec_name = args.precision or default_precision(name)
     prec = dgsem.DGSEM_FP32_MIXED if prec_name == "fp32" else dgsem.DGSEM_FP64
@@ -359,12 +415,18 @@ def main():
     names = BOX_KERNELS
     es = 4 if prec == dgsem.DGSEM_FP32_MIXED else 8
     peaks = measured_peaks()
+    alu = alu_peaks(dgsem, stream)
     roof = box_roofline(kstats, w.domains, B, prec == dgsem.DGSEM_FP32_MIXED, peaks["hbm_gbs"] if peaks else None,
-                        lambda kernel: NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, kernel)))
+                        lambda kernel: NCU_TRAFFIC_PER_LAUNCH.get((name, prec_name, kernel)),
+                        fp64_peak=alu.get("fp64_tflops"))
+    parity = None
+    if not args.no_parity and prec == dgsem.DGSEM_FP32_MIXED and w.pmuts is not None:
+        parity = live_parity(dgsem, sol, w, torch)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, sample, _, _, _ = time_oracle(name, seconds=15.0)
-        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+        v, sample, cores, one = time_oracle(name, seconds=15.0)
+        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": one}
     clocks = cs.summary(local)
     out = {
         "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s", "n_gpus": world,
@@ -378,6 +440,7 @@ def main():
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(5) if kstats[k][1]},
+        "alu_peaks": alu, "parity": parity,
         "finite": finite,
     }
     print(json.dumps(out), flush=True)
@@ -387,8 +450,54 @@ def main():
 
 BOX_KERNELS = ["pmut_recv", "iface", "vol_primary", "vol_secondary", "pml"]
 
+# oracle-parity tests of the benchmarked kernels and configuration (run by
+# `pytest -m gpu`); their measured errors are printed by the tests
+PARITY_TESTS = [
+    "tests/test_gpu_fullsize_sampled.py: config-4 mesh, 64 patterns FP32 / 8 FP64, every tile variant, "
+    "sampled receivers vs the oracle on local crops",
+    "tests/test_gpu_launch_shape.py: every CTA through all layers of its box, 64 patterns, every tile "
+    "variant, each pattern vs its own oracle column",
+    "tests/test_gpu_config3_crop.py: cropped config 3 (6.5M nodes), 8000 steps vs the stored oracle run; "
+    "traces, q(t), energy",
+    "tests/test_gpu_precision_scale.py: config 3 (8000 steps) and config 4 (8 patterns) FP32 vs FP64",
+]
 
-def box_roofline(kstats, domains, B, fp32, hbm_gbs, traffic_of):
+
+def alu_peaks(dgsem, stream):
+    """FP64 and packed-FP32 FMA rates of this GPU, measured now (untimed)."""
+    out = {}
+    for key, prec in (("fp64_tflops", dgsem.DGSEM_FP64), ("fp32_tflops", dgsem.DGSEM_FP32_MIXED)):
+        try:
+            out[key] = dgsem.dgsem_measure_peak(prec, stream.cuda_stream)
+        except Exception as e:  # the line still reports, against nominal figures
+            out[key + "_error"] = str(e)
+    return out
+
+
+def live_parity(dgsem, sol32, w, torch, nsteps=400, nb=8):
+    """FP32 (the benchmarked batch) against FP64 (its first nb patterns) on
+    the benchmarked mesh from rest over nsteps steps, at 64 receivers 0.15 mm
+    above the array (the 2 mm receivers see nothing that early): relative L2
+    per pattern."""
+    pm = w.pmuts
+    lo, hi = pm.centers.min(axis=0), pm.centers.max(axis=0)
+    gx = np.linspace(lo[0], hi[0], 8)
+    gy = np.linspace(lo[1], hi[1], 8)
+    X, Y = np.meshgrid(gx, gy, indexing="ij")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(64, 0.15e-3)], axis=1)
+    drive = w.drive(sol32.dt, nsteps, w.batch)
+    t32 = sol32.run(drive=drive, precision=dgsem.DGSEM_FP32_MIXED, nsteps=nsteps, receivers=rec)
+    sol64 = dgsem.Solver(w)
+    t64 = sol64.run(drive=np.ascontiguousarray(drive[:nb]), precision=dgsem.DGSEM_FP64, batch=nb, nsteps=nsteps,
+                    receivers=rec)
+    sol64.close()
+    errs = [float(np.linalg.norm(t32[b] - t64[b]) / np.linalg.norm(t64[b])) for b in range(nb)]
+    return {"fp32_vs_fp64_gpu": {"patterns": nb, "steps": nsteps, "receivers": "8x8 over the array at z = 0.15 mm",
+                                 "rel_l2_max": max(errs), "rel_l2_median": float(np.median(errs))},
+            "oracle_parity_tests": PARITY_TESTS}
+
+
+def box_roofline(kstats, domains, B, fp32, hbm_gbs, traffic_of, fp64_peak=None):
     """Roofline block of the box path for its dominant volume kernel, from
     per-kind (total ms, launches).  Algorithmic bytes per launch: p read, v
     read and written, p_next written once per node of the box and pattern
@@ -413,15 +522,17 @@ def box_roofline(kstats, domains, B, fp32, hbm_gbs, traffic_of):
                 "peak_source": "measured" if hbm_gbs else "fallback", "alg_bytes_per_launch": alg_bytes}
     flop_per_node = 2 * (3 * (d.order + 2) + 4)
     achieved_f = nodes * B * flop_per_node / avg_s / 1e12
-    return {"bound": "alu", "achieved": achieved_f, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved_f / FP64_TFLOPS, "traffic": traffic_of(name), "kernel": name,
-            "peak_source": "nominal FP64 (no measured FP64 peak)", "hbm_achieved_gbs": achieved}
+    peak = fp64_peak if fp64_peak else FP64_TFLOPS
+    return {"bound": "alu", "achieved": achieved_f, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved_f / peak, "traffic": traffic_of(name), "kernel": name,
+            "peak_source": "measured in this run: DFMA probe (dgsem_measure_peak)" if fp64_peak
+            else "nominal FP64 (no measured FP64 peak)", "hbm_achieved_gbs": achieved}
 
 
 HEX_KERNELS = ["pmut", "vol", "iface", "update", "tail", "pml"]
 
 
-def hex_roofline(kstats, orders, nelem, ndof, B, fp32, hbm_gbs):
+def hex_roofline(kstats, orders, nelem, ndof, B, fp32, hbm_gbs, alu_peaks=None):
     """Roofline block of the general-hexahedron step for its dominant kernel
     (element stiffness or update), from per-kind (total ms, launches).
 
@@ -449,16 +560,137 @@ def hex_roofline(kstats, orders, nelem, ndof, B, fp32, hbm_gbs):
             "alg_bytes_per_launch": alg[name]}
     if name == "vol":
         vol_flops = sum(e * B * (12 * (o + 1) ** 4 + 18 * (o + 1) ** 3) for e, o in zip(nelem, orders)) / len(orders)
-        alu_peak = FP32_TFLOPS if fp32 else FP64_TFLOPS
+        measured = (alu_peaks or {}).get("fp32_tflops" if fp32 else "fp64_tflops")
+        alu_peak = measured or (FP32_TFLOPS if fp32 else FP64_TFLOPS)
         achieved_f = vol_flops / avg_s / 1e12
         if vol_flops / vol_bytes > alu_peak * 1e12 / (peak * 1e9):
             roof = {"bound": "alu", "achieved": achieved_f, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved_f / alu_peak, "traffic": None, "kernel": "vol",
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
-                    if fp32 else "nominal FP64 (no measured FP64 peak)",
+                    "peak_source": ("measured in this run: packed FP32 FMA probe (dgsem_measure_peak)"
+                                    if fp32 else "measured in this run: DFMA probe (dgsem_measure_peak)")
+                    if measured else ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                                      if fp32 else "nominal FP64 (no measured FP64 peak)"),
                     "alg_flops_per_launch": vol_flops, "alg_bytes_per_launch": vol_bytes,
                     "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
     return roof
+
+
+def multi_roofline(ndofs, B, fp32, ms_per_step, hbm_gbs):
+    """Roofline block of a several-mesh launch: the algorithmic bytes of one
+    step of every mesh (p read, v read and written, p_next written: 4 words
+    per node and pattern) over the measured step time, against the copy
+    bandwidth (FP32).  The meshes' volume launches run as parallel graph
+    branches, so the step, not one kernel, is the unit."""
+    es = 4 if fp32 else 8
+    alg = sum(ndofs) * B * 4 * es
+    achieved = alg / (ms_per_step / 1e3) / 1e9
+    peak = hbm_gbs if hbm_gbs else 6800.0
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "whole step (volume, interface and PMUT launches of every mesh)",
+            "peak_source": "measured" if hbm_gbs else "fallback", "alg_bytes_per_step": alg}
+
+
+def main_multi(args, torch, dist, rank, world, local):
+    """Uneven PMUT arrays (8x8, 16x16, 24x24, 32x32, primary N=4 + secondary
+    N=6 boxes) advanced together: dgsem_run_multi captures every mesh's step
+    as a parallel branch of one CUDA graph; tile shapes from the autotuner."""
+    from paper_2603_06267_gb300 import dgsem
+    name = args.workload
+    prec_name = args.precision or default_precision(name)
+    prec = dgsem.DGSEM_FP32_MIXED if prec_name == "fp32" else dgsem.DGSEM_FP64
+    B = args.batch or 64
+    ws = W.config4b_uneven(nsteps=1, batch=B)
+    if world > 1:
+        for w in ws:
+            w.drive_delay, w.drive_amp, _ = W.steering_patterns(w.pmuts.centers, B, seed=4 + 1000 * rank)
+    sols = [dgsem.Solver(w) for w in ws]
+    ctxs = [s_.ctx for s_ in sols]
+    ndofs = [s_.ndof for s_ in sols]
+    tiles = []
+    for s_, w in zip(sols, ws):
+        if args.tiles:
+            t = [int(v) for v in args.tiles.split(",")]
+            dgsem.dgsem_set_tiles(s_.ctx, prec, t)
+        else:
+            t = dgsem.dgsem_autotune(s_.ctx, prec, B, len(w.domains), reps=2)
+        tiles.append([int(v) for v in t])
+    S_tot = args.warmup + args.steps
+    drives = [w.drive(s_.dt, S_tot + args.steps, B) for s_, w in zip(sols, ws)]
+    recvs = [w.receivers for w in ws]
+    R = [r.shape[0] for r in recvs]
+    stream = torch.cuda.current_stream()
+    d_warm = [torch.tensor(np.ascontiguousarray(d[:, :, :args.warmup]), device="cuda") for d in drives]
+    d_time = [torch.tensor(np.ascontiguousarray(d[:, :, args.warmup:S_tot]), device="cuda") for d in drives]
+    tr_warm = [torch.zeros((B, r, args.warmup), dtype=torch.float64, device="cuda") for r in R]
+    tr_time = [torch.zeros((B, r, args.steps), dtype=torch.float64, device="cuda") for r in R]
+    Bs = [B] * len(ws)
+    dgsem.dgsem_run_multi(ctxs, prec, Bs, args.warmup, d_warm, recvs, traces=tr_warm, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks_dir = os.environ.get("DGSEM_BENCH_CLOCKS_DIR", tempfile.gettempdir())
+    clocks_path = os.path.join(clocks_dir, f".bench_clocks_{rank}.csv")
+    for c in ctxs:
+        dgsem.dgsem_profile(c, False)
+    with ClockSampler(clocks_path) as cs:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dgsem.dgsem_run_multi(ctxs, prec, Bs, args.steps, d_time, recvs, traces=tr_time,
+                              flags=dgsem.DGSEM_RUN_CONTINUE, stream=stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        launches = sum(dgsem.dgsem_kernel_stats(c, k)[1] for c in ctxs for k in range(5))
+        e2e = None
+        if not args.no_e2e:
+            h_drive = [torch.from_numpy(np.ascontiguousarray(d[:, :, S_tot:S_tot + args.steps])).pin_memory()
+                       for d in drives]
+            h_tr = [torch.zeros((B, r, args.steps), dtype=torch.float64).pin_memory() for r in R]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dgsem.dgsem_run_multi(ctxs, prec, Bs, args.steps, h_drive, recvs, traces=h_tr,
+                                  flags=dgsem.DGSEM_RUN_CONTINUE, stream=stream.cuda_stream)
+            e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+            e2e = {"value": whole_job_rate(sum(ndofs), B, args.steps, world, e2e_s), "unit": "Gdof-steps/s",
+                   "h2d_bytes_per_step": int(sum(B * w.pmuts.n_pmut * 8 for w in ws)),
+                   "d2h_bytes_per_step": int(sum(B * r * 8 for r in R))}
+    finite = all(bool(torch.isfinite(t).all().item()) for t in tr_time)
+    ms = max_over_ranks(ms, dist)
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    value = whole_job_rate(sum(ndofs), B, args.steps, world, ms / 1e3)
+    peaks = measured_peaks()
+    es = 4 if prec == dgsem.DGSEM_FP32_MIXED else 8
+    roof = multi_roofline(ndofs, B, prec == dgsem.DGSEM_FP32_MIXED, ms / args.steps,
+                          peaks["hbm_gbs"] if peaks else None)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample, cores, one = time_oracle("config4_batched", seconds=15.0)
+        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": one}
+    out = {
+        "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == dgsem.DGSEM_FP32_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": name, "precision": "fp32-mixed" if prec == dgsem.DGSEM_FP32_MIXED else "fp64",
+                   "meshes": [w.name for w in ws], "ndof": ndofs, "ndof_total": sum(ndofs), "batch_per_mesh": B,
+                   "n_pmut": [w.pmuts.n_pmut for w in ws], "receivers": R,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single-gpu, one graph, 4 branches",
+                   "tiles": tiles,
+                   "l2": "state larger than L2" if sum(ndofs) * B * 3 * es > 129e6 else "state fits in L2"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cs.summary(local),
+        "finite": finite,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main_hex(args, torch, dist, rank, world, local):
@@ -524,14 +756,17 @@ def main_hex(args, torch, dist, rank, world, local):
     finite = bool(torch.isfinite(tr_time).all().item())
     value = whole_job_rate(ndof, B, args.steps, 1, ms / 1e3)
     peaks = measured_peaks()
+    from paper_2603_06267_gb300 import dgsem as _dgsem
+    alu = alu_peaks(_dgsem, stream)
     roof = hex_roofline(kstats, [d.order for d in w.domains], [d.elements.shape[0] for d in w.domains], ndof, B,
-                        prec == dghex.DGSEM_FP32_MIXED, peaks["hbm_gbs"] if peaks else None)
+                        prec == dghex.DGSEM_FP32_MIXED, peaks["hbm_gbs"] if peaks else None, alu_peaks=alu)
     names = HEX_KERNELS
     es = 4 if prec == dghex.DGSEM_FP32_MIXED else 8
     cpu = None
     if not args.no_cpu_baseline:
-        v, sample, _, _, _ = time_oracle(name, seconds=15.0)
-        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+        v, sample, cores, one = time_oracle(name, seconds=15.0)
+        cpu = {"value": v, "unit": "Gdof-steps/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": one}
     out = {
         "metric": "DG-SEM Gdof-steps/s", "value": value, "unit": "Gdof-steps/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -546,6 +781,7 @@ def main_hex(args, torch, dist, rank, world, local):
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cs.summary(local),
         "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(6) if kstats[k][1]},
+        "alu_peaks": alu,
         "finite": finite,
     }
     print(json.dumps(out), flush=True)

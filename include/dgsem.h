@@ -266,11 +266,20 @@ int dgsem_run_multi(int n, dgsem_ctx* const* ctxs, int precision, const int* bat
 int dgsem_set_state(dgsem_ctx* ctx, const double* p0, const double* v0);
 
 /* Leapfrog energy of the acoustic field of every batch member after the
- * last run (FP64 state only; diagnostics): e[b] = 1/2 v^T M v + 1/2
- * p^n^T K p^{n+1} with v = v^{n+1/2} and K the stiffness with the interface
- * terms (no PMUT coupling, absorbing or layer terms); Algorithm 1 conserves
- * it exactly without forcing and damping.  e holds n >= batch values. */
+ * last run (diagnostics, computed in FP64 for either state precision): e[b]
+ * = 1/2 v^T M v + 1/2 p^n^T K p^{n+1} with v = v^{n+1/2} and K the stiffness
+ * with the interface terms (no PMUT coupling, absorbing or layer terms);
+ * Algorithm 1 conserves it exactly without forcing and damping.  An FP32
+ * state is widened to FP64 copies first (about three state-sized FP64
+ * buffers per box, allocated for the call; DGSEM_ENOMEM if they do not fit).
+ * e holds n >= batch values. */
 int dgsem_energy(dgsem_ctx* ctx, double* e, int n);
+
+/* Modal state of the PMUT array after the last run: q^n, q'^n, q''^n of
+ * every batch member, PMUT and mode, each a host array [batch][n_pmut]
+ * [n_modes] of n >= batch * n_pmut * n_modes doubles (any pointer may be
+ * NULL).  DGSEM_ESTATE without a PMUT array or a state. */
+int dgsem_get_pmut_state(const dgsem_ctx* ctx, double* q, double* qd, double* qdd, size_t n);
 
 /* Current pressure field p^n of every batch member after the last run, as
  * FP64 host array [batch][ndof] (node order above). */
@@ -295,6 +304,20 @@ int dgsem_num_tiles(const dgsem_ctx* ctx, int precision, int box, int* n);
 int dgsem_set_tiles(dgsem_ctx* ctx, int precision, const int* tiles);
 int dgsem_autotune(dgsem_ctx* ctx, int precision, int batch, int reps, int* chosen, void* stream);
 
+/* Launch shape of the fused volume kernels (no counterpart in the paper).
+ * A CTA owns an x-y tile of a box and marches through a chunk of its
+ * element layers in z, streaming one layer after another through a ring of
+ * shared-memory stages.  dgsem_set_layers sets, per box, the layers one CTA
+ * marches through ([ndomains] values; 0 = automatic, the default: all of the
+ * box's layers, halved while the grid would have fewer than 4 x 152 CTAs;
+ * values above the box's layer count are clamped to it).  The value applies to
+ * every later launch at either precision.  dgsem_vol_launch reports the shape
+ * of box `box`'s volume launch in the last dgsem_run: shape[8] = grid x, y, z,
+ * block x, y, z, layers per CTA, z chunks (grid z = z chunks x batch).
+ * DGSEM_ESTATE before the first run. */
+int dgsem_set_layers(dgsem_ctx* ctx, const int* layers_per_cta);
+int dgsem_vol_launch(const dgsem_ctx* ctx, int box, int* shape);
+
 /* Kernel instrumentation.  dgsem_profile(ctx, 1) makes later runs bracket
  * every kernel launch with CUDA events on the run's stream; statistics are
  * accumulated per kernel kind (DGSEM_K_*) until dgsem_profile(ctx, 1) is
@@ -317,21 +340,40 @@ int dgsem_kernel_stats(const dgsem_ctx* ctx, int kind, double* total_ms, long lo
  * and tensor Lagrange interpolation as dgsem_run's traces.
  *   recv_xyz  [n_recv][3] positions, host or device memory.
  *   out       [batch][n_recv] FP64, device memory (written on `stream`).
- * Why: some callers cannot call cudaMalloc at the moment they want a sample
- * -- code running while a CUDA stream capture is open (an allocation would
- * break the capture), processes whose device memory is handed out entirely
- * by another allocator, or real-time loops that cannot afford the device
- * synchronisation an allocation implies.  This call allocates nothing: the
- * receiver table lives in a fixed array of about 0.75 MiB that every device
- * loading the library holds until the process exits.
- * Limits: at most 64 receivers per call (larger n_recv returns
- * DGSEM_EINVAL with a message); needs a previous dgsem_run (DGSEM_ESTATE
- * otherwise).  The first call on a device looks up the array's device
- * address; make that first call before any stream capture begins.  All calls
- * share the one array and it keeps the last call's contents, so calls whose
- * work overlaps on the GPU (other host threads, other streams) race: issue
- * them one at a time.  Returns after `stream` has finished the work. */
-int dgsem_sample_noalloc(dgsem_ctx* ctx, int n_recv, const double* recv_xyz, double* out, void* stream);
+ *   out_len   number of doubles `out` holds; less than batch * n_recv is
+ *             refused (DGSEM_EINVAL) before anything is written.
+ * Why: some callers cannot call cudaMalloc when they want a sample -- a
+ * process whose device memory has been handed out entirely to another
+ * allocator (for instance a framework's caching pool that reserved the GPU),
+ * or code running under a fixed device-memory budget that a new buffer would
+ * exceed.  This call allocates nothing: its receiver table lives in one
+ * fixed array of about 0.75 MiB that every device loading the library holds
+ * until the process exits.
+ * Limits and behaviour:
+ *   - at most 64 receivers per call (larger n_recv returns DGSEM_EINVAL with
+ *     a message); a receiver outside the mesh returns DGSEM_EINVAL and leaves
+ *     the context usable; needs a previous dgsem_run (DGSEM_ESTATE otherwise).
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and keeps it; make that first call before any
+ *     stream capture begins.  The kept address is not refreshed after
+ *     cudaDeviceReset.
+ *   - the call reads a status word back and waits for `stream` (it returns
+ *     after the stream has finished the work).
+ *   - all calls share the one array and it keeps the last call's contents
+ *     (the status word is cleared at every call, the table is overwritten),
+ *     so calls whose work overlaps on the GPU (other host threads, other
+ *     streams) race: issue them one at a time. */
+int dgsem_sample_noalloc(dgsem_ctx* ctx, int n_recv, const double* recv_xyz, double* out, size_t out_len,
+                         void* stream);
+
+/* Arithmetic-rate probe (no counterpart in the paper; measurement support).
+ * Runs long chains of independent fused multiply-adds on every SM of the
+ * current device -- plain FP64 DFMA for DGSEM_FP64, packed f32x2 FMA for
+ * DGSEM_FP32_MIXED -- in launches of about 0.2 s timed with CUDA events on
+ * `stream`, and writes the best of three rates in TFLOP/s (2 flops per FMA)
+ * to *tflops.  It reads the clocks the GPU runs at and changes no setting.
+ * Allocates a small output buffer for the call. */
+int dgsem_measure_peak(int precision, double* tflops, void* stream);
 
 /* Message of the calling thread's last error ("" if none). */
 const char* dgsem_last_error(void);

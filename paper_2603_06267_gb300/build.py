@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdgsem.so")
-SOURCES = ["api.cu", "vol_f32.cu", "vol_f32_abc.cu", "vol_f64.cu", "vol_f64_abc.cu", "small.cu", "pml.cu", "surrogate.cu",
+SOURCES = ["api.cu", "vol_f32.cu", "vol_f32_abc.cu", "vol_f64.cu", "vol_f64_abc.cu", "small.cu", "pml.cu", "surrogate.cu", "peak.cu",
            "hex_api.cu", "hex_kernels.cu", "hex_vol_f32.cu", "hex_vol_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

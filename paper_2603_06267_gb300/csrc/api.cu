@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -76,6 +77,7 @@ struct dgsem_ctx {
   bool dt_fixed = false;                   // dt given by the caller (not from cfl)
   long long ndof = 0;
   VolSpec vspec[2];
+  int vol_shape[2][8] = {{0}};   // launch shape of each box's volume kernel in the last run
   // interface
   bool has_iface = false;
   int q = 0, nsub = 0;
@@ -730,6 +732,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
       v.has_pmut = 1;
       v.fpm = c->Fpm;
     }
+    v.shape_out = c->vol_shape[d];
     LaunchTimer lt(c, s, DGSEM_K_VOL0 + d);
     CUDA_TRY(launch_vol<T>(v, c->batch, s));
   }
@@ -1640,30 +1643,67 @@ int dgsem_state_load(dgsem_ctx* c, const void* buf, size_t len) {
 int dgsem_energy(dgsem_ctx* c, double* e, int n) {
   if (!c || !e) return fail(DGSEM_EINVAL, "NULL argument");
   if (!c->state_valid) return fail(DGSEM_ESTATE, "no state: run first");
-  if (c->prec != DGSEM_FP64) return fail(DGSEM_ESTATE, "the energy diagnostic needs an FP64 state");
   if (n < c->batch) return fail(DGSEM_EINVAL, "e holds %d values, %d needed", n, c->batch);
+  const bool f32 = c->prec == DGSEM_FP32_MIXED;
   int rc = refresh_tmaps(c);
   if (rc) return rc;
   cudaStream_t s = 0;
-  std::vector<double*> tmp;
-  auto cleanup = [&]() { for (double* p : tmp) cudaFree(p); };
-  // W = -M^-1 K p^{n+1} (volume kernel on Y with v = 0, dtv = 1, dtp = 0, no
-  // forcing, absorbing or layer terms), P2 receives the unchanged p_out
+  std::vector<void*> tmp;
+  auto cleanup = [&]() { for (void* p : tmp) cudaFree(p); };
+  // The operator is applied in FP64 to p^{n+1}: the state's own buffer in
+  // FP64, an FP64 copy of it (with its own tensor map and FP64 interface
+  // buffers) for an FP32 state.  W = -M^-1 K p^{n+1} (volume kernel with
+  // v = 0, dtv = 1, dtp = 0, no forcing, absorbing or layer terms); P2
+  // receives the unchanged p_out.
   double* W[2] = {nullptr, nullptr};
   double* P2[2] = {nullptr, nullptr};
+  double* Y64[2] = {nullptr, nullptr};
+  double* Ra64[2] = {nullptr, nullptr};
+  double* Rb64[2] = {nullptr, nullptr};
+  double* Ga64[2] = {nullptr, nullptr};
+  double* Gb64[2] = {nullptr, nullptr};
+  CUtensorMap tm64[2];
   double* w1[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
   double* d_red = nullptr;
   if ((rc = dalloc(&d_red, 2 * sizeof(double) * c->batch))) return rc;
   tmp.push_back(d_red);
   for (int d = 0; d < c->nd; ++d) {
-    const size_t bytes = (size_t)c->batch * c->box[d].bstride * sizeof(double);
+    const Box& B = c->box[d];
+    const size_t cnt = (size_t)c->batch * B.bstride;
+    const size_t bytes = cnt * sizeof(double);
     if ((rc = dalloc(&W[d], bytes)) || (rc = dalloc(&P2[d], bytes))) { cleanup(); return rc; }
     tmp.push_back(W[d]);
     tmp.push_back(P2[d]);
     CUDA_TRY(cudaMemsetAsync(W[d], 0, bytes, s));
+    if (f32) {
+      if ((rc = dalloc(&Y64[d], bytes))) { cleanup(); return rc; }
+      tmp.push_back(Y64[d]);
+      CUDA_TRY(launch_widen(static_cast<const float*>(c->Y[d]), Y64[d], (long long)cnt, s));
+      unsigned box[3], vbox[3];
+      if (!vol_tma_box_f64(B.N, c->tile_pref[0][d], box, vbox)) { cleanup(); return fail(DGSEM_EINVAL, "no FP64 tile variant"); }
+      if ((rc = make_tmap(&tm64[d], Y64[d], B, c->batch, DGSEM_FP64, box))) { cleanup(); return rc; }
+      if (c->has_iface) {
+        const size_t rb = (size_t)c->batch * B.ne[0] * B.ne[1] * (B.N + 1) * (B.N + 1) * sizeof(double);
+        const size_t gb = (size_t)c->batch * B.L[1] * B.py * sizeof(double);
+        if ((rc = dalloc(&Ra64[d], rb)) || (rc = dalloc(&Rb64[d], rb)) || (rc = dalloc(&Ga64[d], gb)) ||
+            (rc = dalloc(&Gb64[d], gb))) {
+          for (double* q : {Ra64[d], Rb64[d], Ga64[d], Gb64[d]}) if (q) tmp.push_back(q);
+          cleanup();
+          return rc;
+        }
+        for (double* q : {Ra64[d], Rb64[d], Ga64[d], Gb64[d]}) tmp.push_back(q);
+        CUDA_TRY(cudaMemsetAsync(Ga64[d], 0, gb, s));
+        CUDA_TRY(cudaMemsetAsync(Gb64[d], 0, gb, s));
+      }
+    } else {
+      Y64[d] = static_cast<double*>(c->Y[d]);
+      tm64[d] = c->tmap_y[d];
+      Ra64[d] = static_cast<double*>(c->Ra[d]); Rb64[d] = static_cast<double*>(c->Rb[d]);
+      Ga64[d] = static_cast<double*>(c->Ga[d]); Gb64[d] = static_cast<double*>(c->Gb[d]);
+    }
     for (int k = 0; k < 3; ++k) {
-      std::vector<double> w(c->box[d].L[k]);
-      for (int i = 0; i < c->box[d].L[k]; ++i) w[i] = c->box[d].basis->assembled_weight(i, c->box[d].ne[k]);
+      std::vector<double> w(B.L[k]);
+      for (int i = 0; i < B.L[k]; ++i) w[i] = B.basis->assembled_weight(i, B.ne[k]);
       if ((rc = upload(&w1[d][k], w))) { cleanup(); return rc; }
       tmp.push_back(w1[d][k]);
     }
@@ -1671,24 +1711,34 @@ int dgsem_energy(dgsem_ctx* c, double* e, int n) {
   CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
   if (c->has_iface) {
     IfaceArgs<double> a = iface_args<double>(c);
-    a.pp = static_cast<const double*>(c->Y[0]);
-    a.ps = static_cast<const double*>(c->Y[1]);
+    a.pp = Y64[0];
+    a.ps = Y64[1];
+    a.Rap = Ra64[0]; a.Rbp = Rb64[0]; a.Ras = Ra64[1]; a.Rbs = Rb64[1];
     CUDA_TRY(launch_iface<double>(a, c->batch, s));
-    if ((rc = launch_face_assembly<double>(c, s, c->batch, false))) { cleanup(); return rc; }
+    for (int d = 0; d < c->nd; ++d) {
+      const Box& B = c->box[d];
+      FaceAsmArgs<double> f;
+      f.Ra = Ra64[d]; f.Rb = Rb64[d]; f.ga = Ga64[d]; f.gb = Gb64[d];
+      f.N = B.N; f.ne0 = B.ne[0]; f.ne1 = B.ne[1]; f.L0 = B.L[0]; f.L1 = B.L[1]; f.py = B.py;
+      f.rbs = (long long)B.ne[0] * B.ne[1] * (B.N + 1) * (B.N + 1);
+      f.gbs = (long long)B.L[1] * B.py;
+      CUDA_TRY(launch_face_asm<double>(f, c->batch, s));
+    }
   }
   for (int d = 0; d < c->nd; ++d) {
     VolSpec v = c->vspec[d];
     v.has_abc = 0;
     v.has_pml = 0;
     v.has_pmut = 0;
-    v.tmap = &c->tmap_y[d];
+    v.tmap = &tm64[d];
     v.tmap_v = nullptr;
     v.err = c->d_err;
     v.tile = c->tile_pref[0][d];
     v.step = nullptr;
-    v.p_in = c->Y[d]; v.p_out = P2[d]; v.v = W[d];
+    v.shape_out = nullptr;
+    v.p_in = Y64[d]; v.p_out = P2[d]; v.v = W[d];
     v.dtv = 1.0; v.dtp = 0.0;
-    v.ga = c->Ga[d]; v.gb = c->Gb[d];
+    v.ga = Ga64[d]; v.gb = Gb64[d];
     v.gbs = (long long)c->box[d].L[1] * c->box[d].py;
     CUDA_TRY(launch_vol<double>(v, c->batch, s));
   }
@@ -1699,11 +1749,23 @@ int dgsem_energy(dgsem_ctx* c, double* e, int n) {
       const Box& B = c->box[d];
       const long long o = (long long)b * B.bstride;
       const double scale = B.h[0] * B.h[1] * B.h[2] / 8.0;
-      const double* V = static_cast<const double*>(c->V[d]) + o;
-      const double* X = static_cast<const double*>(c->X[d]) + o;
-      CUDA_TRY(launch_mdot(V, V, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale, d_red + 2 * b, s));
-      CUDA_TRY(launch_mdot(X, W[d] + o, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
-                           d_red + 2 * b + 1, s));
+      if (f32) {
+        const float* V = static_cast<const float*>(c->V[d]) + o;
+        const float* X = static_cast<const float*>(c->X[d]) + o;
+        // v.M v: v widened into P2, which the volume launch no longer needs
+        CUDA_TRY(launch_widen(V, P2[d] + o, B.bstride, s));
+        CUDA_TRY(launch_mdot(V, P2[d] + o, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
+                             d_red + 2 * b, s));
+        CUDA_TRY(launch_mdot(X, W[d] + o, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
+                             d_red + 2 * b + 1, s));
+      } else {
+        const double* V = static_cast<const double*>(c->V[d]) + o;
+        const double* X = static_cast<const double*>(c->X[d]) + o;
+        CUDA_TRY(launch_mdot(V, V, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
+                             d_red + 2 * b, s));
+        CUDA_TRY(launch_mdot(X, W[d] + o, w1[d][0], w1[d][1], w1[d][2], B.L[0], B.L[1], B.L[2], B.py, B.pz, scale,
+                             d_red + 2 * b + 1, s));
+      }
     }
   std::vector<double> red(2 * (size_t)c->batch);
   CUDA_TRY(cudaMemcpy(red.data(), d_red, red.size() * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1712,6 +1774,19 @@ int dgsem_energy(dgsem_ctx* c, double* e, int n) {
   cleanup();
   if (err) return fail(DGSEM_ETIMEOUT, "a bounded device-side wait gave up during the energy diagnostic");
   for (int b = 0; b < c->batch; ++b) e[b] = 0.5 * (red[2 * b] - red[2 * b + 1]);
+  return DGSEM_OK;
+}
+
+int dgsem_get_pmut_state(const dgsem_ctx* c, double* q, double* qd, double* qdd, size_t n) {
+  if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
+  if (!c->state_valid) return fail(DGSEM_ESTATE, "no state: run first");
+  if (c->K == 0 || !c->q_state) return fail(DGSEM_ESTATE, "no PMUT array");
+  const size_t km = (size_t)c->batch * c->K * c->M;
+  if (n < km) return fail(DGSEM_EINVAL, "arrays hold %zu values, [batch][n_pmut][n_modes] = %zu needed", n, km);
+  CUDA_TRY(cudaDeviceSynchronize());
+  double* dst[3] = {q, qd, qdd};
+  for (int i = 0; i < 3; ++i)
+    if (dst[i]) CUDA_TRY(cudaMemcpy(dst[i], c->q_state + i * km, km * sizeof(double), cudaMemcpyDeviceToHost));
   return DGSEM_OK;
 }
 
@@ -1822,6 +1897,23 @@ int dgsem_set_tiles(dgsem_ctx* c, int precision, const int* tiles) {
     if (!nv) return fail(DGSEM_EINVAL, "box %d: no tile variant %d for order %d", d, tiles[d], c->box[d].N);
   }
   for (int d = 0; d < c->nd; ++d) c->tile_pref[precision == DGSEM_FP32_MIXED ? 1 : 0][d] = tiles[d];
+  return DGSEM_OK;
+}
+
+int dgsem_set_layers(dgsem_ctx* c, const int* layers_per_cta) {
+  if (!c || !layers_per_cta) return fail(DGSEM_EINVAL, "NULL argument");
+  for (int d = 0; d < c->nd; ++d)
+    if (layers_per_cta[d] < 0) return fail(DGSEM_EINVAL, "box %d: layers_per_cta %d < 0", d, layers_per_cta[d]);
+  for (int d = 0; d < c->nd; ++d) c->vspec[d].layers_per_cta = std::min(layers_per_cta[d], c->box[d].ne[2]);
+  drop_graph(c);   // the captured launches hold the old grid
+  return DGSEM_OK;
+}
+
+int dgsem_vol_launch(const dgsem_ctx* c, int box, int* shape) {
+  if (!c || !shape) return fail(DGSEM_EINVAL, "NULL argument");
+  if (box < 0 || box >= c->nd) return fail(DGSEM_EINVAL, "box %d out of range", box);
+  if (c->vol_shape[box][0] == 0) return fail(DGSEM_ESTATE, "no volume launch of box %d yet", box);
+  for (int i = 0; i < 8; ++i) shape[i] = c->vol_shape[box][i];
   return DGSEM_OK;
 }
 
@@ -1957,9 +2049,12 @@ constexpr size_t NA_BYTES = NA_OFF_NN + (size_t)NA_MAX_RECV * sizeof(int);   // 
 
 static __device__ __align__(256) unsigned char g_sample_scratch[NA_BYTES];
 
-// device address of g_sample_scratch, looked up once per device
+// device address of g_sample_scratch, looked up once per device (under the
+// mutex: host threads may make their first calls concurrently).  The address
+// is not refreshed after cudaDeviceReset.
 constexpr int NA_MAX_DEVICES = 64;
 unsigned char* g_sample_scratch_addr[NA_MAX_DEVICES] = {nullptr};
+std::mutex g_sample_scratch_mu;
 
 struct NaBox {
   double o[3], h[3], ext[3];
@@ -2039,7 +2134,8 @@ __global__ void na_receiver_table(const __grid_constant__ NaArgs A) {
 
 }  // namespace
 
-extern "C" int dgsem_sample_noalloc(dgsem_ctx* c, int n_recv, const double* recv_xyz, double* out, void* stream) {
+extern "C" int dgsem_sample_noalloc(dgsem_ctx* c, int n_recv, const double* recv_xyz, double* out, size_t out_len,
+                                    void* stream) {
   if (!c) return fail(DGSEM_EINVAL, "ctx is NULL");
   if (n_recv < 0 || n_recv > NA_MAX_RECV)
     return fail(DGSEM_EINVAL, "dgsem_sample_noalloc: n_recv = %d outside [0, %d] (its receiver table holds at most %d points)",
@@ -2047,6 +2143,9 @@ extern "C" int dgsem_sample_noalloc(dgsem_ctx* c, int n_recv, const double* recv
   if (n_recv == 0) return DGSEM_OK;
   if (!recv_xyz || !out) return fail(DGSEM_EINVAL, "recv_xyz and out are required");
   if (!c->state_valid || !c->X[0]) return fail(DGSEM_ESTATE, "no pressure state: call dgsem_run first");
+  if (out_len < (size_t)c->batch * (size_t)n_recv)
+    return fail(DGSEM_EINVAL, "out holds %zu doubles, [batch = %d][n_recv = %d] needs %zu", out_len, c->batch, n_recv,
+                (size_t)c->batch * (size_t)n_recv);
   if (!is_device_ptr(out)) return fail(DGSEM_EINVAL, "out must be device memory ([batch][n_recv] doubles)");
   int dev = -1;
   CUDA_TRY(cudaGetDevice(&dev));
@@ -2054,14 +2153,18 @@ extern "C" int dgsem_sample_noalloc(dgsem_ctx* c, int n_recv, const double* recv
   if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(DGSEM_EINVAL, "device %d beyond the supported %d", dev, NA_MAX_DEVICES);
   // set-up, once per device: the device address of the scratch array (the
   // host-side symbol is only a stand-in and must never reach a kernel)
-  if (!g_sample_scratch_addr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_sample_scratch);
-    if (e != cudaSuccess || !ptr)
-      return fail(DGSEM_ECUDA, "cudaGetSymbolAddress(g_sample_scratch): %s", cudaGetErrorString(e));
-    g_sample_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+  unsigned char* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_sample_scratch_mu);
+    if (!g_sample_scratch_addr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_sample_scratch);
+      if (e != cudaSuccess || !ptr)
+        return fail(DGSEM_ECUDA, "cudaGetSymbolAddress(g_sample_scratch): %s", cudaGetErrorString(e));
+      g_sample_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    scratch = g_sample_scratch_addr[dev];
   }
-  unsigned char* scratch = g_sample_scratch_addr[dev];
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the status word must start at zero; the table entries are overwritten
   CUDA_TRY(cudaMemsetAsync(scratch + NA_OFF_STATUS, 0, sizeof(int), s));

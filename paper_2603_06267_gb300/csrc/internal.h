@@ -256,6 +256,7 @@ struct VolSpec {
   int pml_lo[3], pml_hi[3];
   int layers_per_cta;              // 0: choose automatically
   int tile;                        // tile-shape variant (see vol_impl.cuh)
+  int* shape_out;                  // if not NULL: [8] grid xyz, block xyz, layers per CTA, z chunks of the launch
 };
 
 // Box shapes (x, y, z) of the TMA staging loads of one element layer (p)
@@ -294,4 +295,8 @@ cudaError_t launch_pmut_force(const PmutForceArgs& a, int batch, cudaStream_t s)
 // power-iteration helpers (FP64)
 cudaError_t launch_mdot(const double* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
                         int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s);
+cudaError_t launch_mdot(const float* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
+                        int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s);
 cudaError_t launch_scale(double* x, const double* y, double a, long long n, cudaStream_t s);
+// y[0..n) = x[0..n) widened to FP64
+cudaError_t launch_widen(const float* x, double* y, long long n, cudaStream_t s);

@@ -548,7 +548,8 @@ __global__ void __launch_bounds__(256) pmut_force_kernel(const __grid_constant__
 // Power-iteration helpers (setup only): M-weighted dot product over a box
 // lattice with the lumped mass M = scale * w_x(i) w_y(j) w_z(k), and scaling.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) mdot_kernel(const double* __restrict__ x, const double* __restrict__ y,
+template <typename TX>
+__global__ void __launch_bounds__(256) mdot_kernel(const TX* __restrict__ x, const double* __restrict__ y,
                                                    const double* __restrict__ wx, const double* __restrict__ wy,
                                                    const double* __restrict__ wz, int L0, int L1, int L2, int py,
                                                    long long pz, double scale, double* out) {
@@ -560,7 +561,7 @@ __global__ void __launch_bounds__(256) mdot_kernel(const double* __restrict__ x,
     const long long r = t / L0;
     const int j = (int)(r % L1), k = (int)(r / L1);
     const long long g = (long long)k * pz + (long long)j * py + i;
-    s += wx[i] * wy[j] * wz[k] * x[g] * y[g];
+    s += wx[i] * wy[j] * wz[k] * (double)x[g] * y[g];
   }
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -572,6 +573,12 @@ __global__ void __launch_bounds__(256) mdot_kernel(const double* __restrict__ x,
   }
 }
 
+// y = x, FP32 -> FP64 (exact)
+__global__ void widen_kernel(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (double)x[t];
+}
+
 __global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ y, double a, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
     x[t] = a * y[t];
@@ -581,7 +588,19 @@ __global__ void scale_kernel(double* __restrict__ x, const double* __restrict__ 
 
 cudaError_t launch_mdot(const double* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
                         int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s) {
-  mdot_kernel<<<4 * 152, 256, 0, s>>>(x, y, wx, wy, wz, L0, L1, L2, py, pz, scale, out);
+  mdot_kernel<double><<<4 * 152, 256, 0, s>>>(x, y, wx, wy, wz, L0, L1, L2, py, pz, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mdot(const float* x, const double* y, const double* wx, const double* wy, const double* wz, int L0,
+                        int L1, int L2, int py, long long pz, double scale, double* out, cudaStream_t s) {
+  mdot_kernel<float><<<4 * 152, 256, 0, s>>>(x, y, wx, wy, wz, L0, L1, L2, py, pz, scale, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  widen_kernel<<<4 * 152, 256, 0, s>>>(x, y, n);
   return cudaGetLastError();
 }
 

@@ -1057,6 +1057,10 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
   dim3 block(TXE, G::TYR, PG);
+  if (s.shape_out) {
+    const int sh[8] = {(int)grid.x, (int)grid.y, (int)grid.z, (int)block.x, (int)block.y, (int)block.z, layers, a.nchunks};
+    for (int i = 0; i < 8; ++i) s.shape_out[i] = sh[i];
+  }
   kern<<<grid, block, G::SMEM, st>>>(a);
   return cudaGetLastError();
 }

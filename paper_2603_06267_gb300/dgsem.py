@@ -32,10 +32,11 @@ DGSEM_RUN_CONTINUE = 1
 EXPORTED = [
     "dgsem_mesh_create", "dgsem_set_absorbing", "dgsem_set_pml", "dgsem_selftest_wait", "dgsem_get_dt", "dgsem_check_stability", "dgsem_pmut_nodes", "pmut_array_set",
     "pmut_set_receive", "dgsem_get_voltages",
-    "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_energy", "dgsem_state_save",
+    "dgsem_run", "dgsem_run_multi", "dgsem_set_state", "dgsem_get_pressure", "dgsem_get_pmut_state", "dgsem_energy", "dgsem_state_save",
     "dgsem_state_load",
     "dgsem_num_tiles", "dgsem_set_tiles", "dgsem_autotune",
-    "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_last_error", "dgsem_destroy",
+    "dgsem_set_layers", "dgsem_vol_launch", "dgsem_profile", "dgsem_kernel_stats", "dgsem_sample_noalloc", "dgsem_measure_peak", "dgsem_last_error",
+    "dgsem_destroy",
 ]
 DGSEM_K_PMUT_RECV, DGSEM_K_IFACE, DGSEM_K_VOL0, DGSEM_K_VOL1, DGSEM_K_PML = 0, 1, 2, 3, 4
 
@@ -86,13 +87,17 @@ def load_library(path: str = LIB_PATH):
     lib.dgsem_run_multi.argtypes = [c_int, vp, c_int, vp, c_int, vp, vp, vp, vp, c_int, vp]
     lib.dgsem_set_state.argtypes = [vp, vp, vp]
     lib.dgsem_get_pressure.argtypes = [vp, vp, c_size_t]
+    lib.dgsem_get_pmut_state.argtypes = [vp, vp, vp, vp, c_size_t]
     lib.dgsem_energy.argtypes = [vp, vp, c_int]
     lib.dgsem_state_save.argtypes = [vp, vp, POINTER(c_size_t)]
     lib.dgsem_state_load.argtypes = [vp, vp, c_size_t]
     lib.dgsem_num_tiles.argtypes = [vp, c_int, c_int, POINTER(c_int)]
     lib.dgsem_set_tiles.argtypes = [vp, c_int, vp]
     lib.dgsem_autotune.argtypes = [vp, c_int, c_int, c_int, vp, vp]
-    lib.dgsem_sample_noalloc.argtypes = [vp, c_int, vp, vp, vp]
+    lib.dgsem_set_layers.argtypes = [vp, vp]
+    lib.dgsem_measure_peak.argtypes = [c_int, POINTER(c_double), vp]
+    lib.dgsem_vol_launch.argtypes = [vp, c_int, vp]
+    lib.dgsem_sample_noalloc.argtypes = [vp, c_int, vp, vp, c_size_t, vp]
     lib.dgsem_profile.argtypes = [vp, c_int]
     lib.dgsem_kernel_stats.argtypes = [vp, c_int, POINTER(c_double), POINTER(c_longlong)]
     lib.dgsem_last_error.restype = ctypes.c_char_p
@@ -298,8 +303,16 @@ def dgsem_get_pressure(ctx, batch: int, ndof: int) -> np.ndarray:
     return out
 
 
+def dgsem_get_pmut_state(ctx, batch: int, n_pmut: int, n_modes: int):
+    """(q, q', q'') of the PMUT array after the last run, each [batch][n_pmut][n_modes]."""
+    out = [np.zeros((batch, n_pmut, n_modes)) for _ in range(3)]
+    _check(_lib.dgsem_get_pmut_state(ctx, _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), out[0].size),
+           "dgsem_get_pmut_state")
+    return tuple(out)
+
+
 def dgsem_energy(ctx, batch: int) -> np.ndarray:
-    """Leapfrog energy 1/2 v.M v + 1/2 p^n.K p^{n+1} of each batch member (FP64 state)."""
+    """Leapfrog energy 1/2 v.M v + 1/2 p^n.K p^{n+1} of each batch member, in FP64 (either state precision)."""
     out = np.zeros(batch)
     _check(_lib.dgsem_energy(ctx, _ptr(out), batch), "dgsem_energy")
     return out
@@ -339,15 +352,45 @@ def dgsem_autotune(ctx, precision: int, batch: int, ndomains: int, reps: int = 3
     return out
 
 
+def dgsem_set_layers(ctx, layers_per_cta: Sequence[int]):
+    """Element layers per CTA of each box's volume kernel (0 = automatic)."""
+    arr = np.ascontiguousarray(layers_per_cta, dtype=np.int32)
+    _check(_lib.dgsem_set_layers(ctx, _ptr(arr)), "dgsem_set_layers")
+
+
+def dgsem_vol_launch(ctx, box: int) -> dict:
+    """Shape of box `box`'s volume launch in the last run."""
+    out = np.zeros(8, dtype=np.int32)
+    _check(_lib.dgsem_vol_launch(ctx, box, _ptr(out)), "dgsem_vol_launch")
+    return dict(grid=tuple(int(v) for v in out[:3]), block=tuple(int(v) for v in out[3:6]),
+                layers_per_cta=int(out[6]), nchunks=int(out[7]))
+
+
 def dgsem_sample_noalloc(ctx, recv_xyz, out, stream=None):
     """Sample the current pressure field at recv_xyz ([R][3], R <= 64) into the
-    device tensor `out` ([batch][R] float64) without any device allocation
-    (for callers inside a stream capture or with a fixed memory budget)."""
+    device tensor `out` ([batch][R] float64, contiguous) without any device
+    allocation, for callers whose device memory belongs to another allocator
+    or to a fixed budget.  Returns after the stream has finished."""
+    import torch
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64 \
+            or not out.is_contiguous():
+        raise TypeError("out must be a contiguous float64 CUDA tensor of [batch][R] values")
     recv = np.ascontiguousarray(recv_xyz, dtype=np.float64).reshape(-1, 3)
     if stream is None:
         stream = _current_stream()
-    _check(_lib.dgsem_sample_noalloc(ctx, recv.shape[0], _ptr(recv), _ptr(out), stream), "dgsem_sample_noalloc")
+    _check(_lib.dgsem_sample_noalloc(ctx, recv.shape[0], _ptr(recv), _ptr(out), out.numel(), stream),
+           "dgsem_sample_noalloc")
     return out
+
+
+def dgsem_measure_peak(precision: int, stream=None) -> float:
+    """FMA rate of the current device in TFLOP/s (FP64 DFMA or packed FP32)."""
+    load_library()
+    v = c_double()
+    if stream is None:
+        stream = _current_stream()
+    _check(_lib.dgsem_measure_peak(precision, byref(v), stream), "dgsem_measure_peak")
+    return v.value
 
 
 def dgsem_profile(ctx, enable: bool = True):

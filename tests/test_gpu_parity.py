@@ -424,8 +424,31 @@ def test_energy_diagnostic_matches_oracle_and_is_conserved():
     sol.run(precision=0, batch=2, nsteps=150, flags=dgsem.DGSEM_RUN_CONTINUE)
     e2 = dgsem.dgsem_energy(sol.ctx, 2)
     assert abs(e2[0] - e1[0]) < 1e-12 * abs(e1[0])
-    sol.run(precision=1, batch=1, nsteps=5)
+    # an FP32 state: the diagnostic widens it and applies the FP64 operator
+    sol.run(precision=1, batch=2)
+    e3 = dgsem.dgsem_energy(sol.ctx, 2)
+    assert abs(e3[0] - ref) < 1e-4 * abs(ref) and abs(e3[1] - e3[0]) < 1e-12 * abs(e3[0])
     with pytest.raises(dgsem.DgsemError) as e:
         dgsem.dgsem_energy(sol.ctx, 1)
-    assert e.value.code == dgsem.DGSEM_ESTATE
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    sol.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(0, FP64_TOL), (1, FP32_TOL)])
+def test_pmut_state_getter_matches_oracle(prec, tol):
+    """dgsem_get_pmut_state returns q^S, q'^S, q''^S of every pattern, PMUT
+    and mode after an S-step run; they equal the oracle's modal state."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=150, batch=3, steer=True)
+    P = oracle_problem(w)
+    sol = gpu_solver(w)
+    drive = w.drive(sol.dt, w.nsteps, w.batch)
+    sol.run(drive=drive, precision=prec)
+    q, qd, qdd = dgsem.dgsem_get_pmut_state(sol.ctx, 3, w.pmuts.n_pmut, w.pmuts.n_modes)
+    P.run(dt=sol.dt, drive=drive)
+    fs = P.final_state
+    for got, key in ((q, "q"), (qd, "qd"), (qdd, "qdd")):
+        ref = fs[key].T.reshape(3, w.pmuts.n_pmut, w.pmuts.n_modes)
+        assert np.abs(ref).max() > 0
+        assert rel_l2(got, ref) < tol, key
     sol.close()

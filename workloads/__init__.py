@@ -274,6 +274,28 @@ def config3_array32(nsteps: int = 8000, batch: int = 1, seed: int = 3) -> Worklo
     return Workload("config3_array32", doms, nsteps, rec, pm, batch=batch, drive_delay=d, drive_amp=a)
 
 
+def config3_crop(nsteps: int = 8000, batch: int = 1) -> Workload:
+    """The config-3 problem cropped to its first 8x8 block of PMUTs: a 32x32x16
+    N=4 primary box (0.8 x 0.8 x 0.4 mm) below a 16x16x96 N=6 secondary box
+    (0.8 x 0.8 x 4.8 mm), 6,510,658 nodes.  Element sizes, orders, heights,
+    time step and horizon are config 3's; the 64 PMUTs are config 3's
+    membranes (i, j) < 8 with their seeded frequency factors.  64 receivers on
+    an 8x8 grid (pitch 100 um) at z = 2 mm.  The crop's x/y walls are rigid,
+    so this is its own problem, small enough for the oracle."""
+    full = config3_array32(nsteps=nsteps, batch=batch)
+    doms = _stacked(32, 16, 0.8e-3, 0.4e-3, 16, 96, 4.8e-3)
+    c = full.pmuts.centers
+    keep = np.nonzero((c[:, 0] < 0.8e-3) & (c[:, 1] < 0.8e-3))[0]
+    pm = PmutArray(centers=c[keep].copy(), side=full.pmuts.side, freq_hz=full.pmuts.freq_hz[keep].copy(),
+                   damping=full.pmuts.damping[keep].copy(), eta=full.pmuts.eta[keep].copy(),
+                   modal_mass=full.pmuts.modal_mass[keep].copy())
+    g = 50e-6 + 100e-6 * np.arange(8)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(64, 2.0e-3)], axis=1)
+    d, a = _uniform_drive(keep.size, batch)
+    return Workload("config3_crop", doms, nsteps, rec, pm, batch=batch, drive_delay=d, drive_amp=a)
+
+
 def steering_patterns(centers: np.ndarray, batch: int, seed: int, c: float = WATER_C,
                       jitter: float = 5e-9, max_angle_deg: float = 30.0, amp=(0.8, 1.2),
                       base_amp: float = 10.0):
@@ -295,6 +317,30 @@ def config4_batched(nsteps: int = 8000, batch: int = 64) -> Workload:
     w.name = "config4_batched"
     w.drive_delay, w.drive_amp, _ = steering_patterns(w.pmuts.centers, batch, seed=4)
     return w
+
+
+def config4b_uneven(nsteps: int = 8000, batch: int = 64, sides=(8, 16, 24, 32)) -> List[Workload]:
+    """Uneven arrays in one launch: for each side a in `sides`, an a x a PMUT
+    array (pitch 100 um, 5 modes, +-3 % spread) on a 4a x 4a x 16 N=4 primary
+    box (h = 25 um, 0.4 mm high) below a 2a x 2a x 96 N=6 secondary box
+    (4.8 mm high), 64 receivers on an 8x8 grid at z = 2 mm, `batch`
+    beam-steering drive patterns per array (seed 40 + a).  The 32 x 32 member
+    is the config-3 mesh."""
+    out = []
+    for a in sides:
+        rng = np.random.default_rng(1000 + a)
+        L = a * 100e-6
+        doms = _stacked(4 * a, 16, L, 0.4e-3, 2 * a, 96, 4.8e-3)
+        centers = _grid_centers(a, 100e-6)
+        pm = make_pmut_array(centers, 60e-6, MODE_FREQS_5, 0.01,
+                             freq_scale=rng.uniform(0.97, 1.03, size=centers.shape[0]))
+        g = (np.arange(8) + 0.5) * L / 8
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        rec = np.stack([X.ravel(), Y.ravel(), np.full(64, 2.0e-3)], axis=1)
+        d, amp, _ = steering_patterns(centers, batch, seed=40 + a)
+        out.append(Workload(f"config4b_array{a}", doms, nsteps, rec, pm, batch=batch, drive_delay=d,
+                            drive_amp=amp))
+    return out
 
 
 def small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=4, n_pmut_side=2, nsteps=200, batch=1,
