@@ -12,7 +12,7 @@
 
 #include "../../include/dgsem.h"
 
-extern "C" int dg_fail_msg(int code, const char* msg);
+int dg_fail_msg(int code, const char* msg);   // api.cu: sets the thread's last-error message
 
 namespace {
 
