@@ -141,6 +141,7 @@ struct dgsem_ctx {
   // TMA descriptors of the pressure buffers (X and Y of each box) and the
   // device status word written by bounded waits
   CUtensorMap tmap_x[2], tmap_y[2], tmap_v[2];
+  CUtensorMap tmap_px[2], tmap_py[2];   // X / Y with the v box: p_out of the TMA-store tile variants
   bool has_tmap_v[2] = {false, false};
   int tile_pref[2][2] = {{0, 0}, {0, 0}};   // [fp64, fp32][box] tile-shape variant
   int* d_err = nullptr;
@@ -312,7 +313,10 @@ int refresh_tmaps(dgsem_ctx* c) {
         (rc = make_tmap(&c->tmap_y[d], c->Y[d], c->box[d], c->batch, c->prec, box)))
       return rc;
     c->has_tmap_v[d] = vbox[0] != 0;
-    if (c->has_tmap_v[d] && (rc = make_tmap(&c->tmap_v[d], c->V[d], c->box[d], c->batch, c->prec, vbox))) return rc;
+    if (c->has_tmap_v[d] && ((rc = make_tmap(&c->tmap_v[d], c->V[d], c->box[d], c->batch, c->prec, vbox)) ||
+                             (rc = make_tmap(&c->tmap_px[d], c->X[d], c->box[d], c->batch, c->prec, vbox)) ||
+                             (rc = make_tmap(&c->tmap_py[d], c->Y[d], c->box[d], c->batch, c->prec, vbox))))
+      return rc;
   }
   return DGSEM_OK;
 }
@@ -706,6 +710,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     VolSpec v = c->vspec[d];
     v.tmap = init ? &c->tmap_x[d] : &c->tmap_y[d];
     v.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
+    v.tmap_pst = c->has_tmap_v[d] ? (init ? &c->tmap_py[d] : &c->tmap_px[d]) : nullptr;
     v.err = c->d_err;
     v.tile = c->tile_pref[c->prec == DGSEM_FP32_MIXED ? 1 : 0][d];
     v.step = (!init && d == c->nd - 1) ? c->d_step : nullptr;
@@ -740,6 +745,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     for (int d = 0; d < c->nd; ++d) {
       std::swap(c->X[d], c->Y[d]);
       std::swap(c->tmap_x[d], c->tmap_y[d]);
+      std::swap(c->tmap_px[d], c->tmap_py[d]);
     }
   }
   return DGSEM_OK;
@@ -1950,6 +1956,7 @@ int dgsem_autotune(dgsem_ctx* c, int precision, int batch, int reps, int* chosen
       VolSpec sp = c->vspec[d];
       sp.tmap = &c->tmap_y[d];
       sp.tmap_v = c->has_tmap_v[d] ? &c->tmap_v[d] : nullptr;
+      sp.tmap_pst = c->has_tmap_v[d] ? &c->tmap_px[d] : nullptr;
       sp.err = c->d_err;
       sp.tile = v;
       sp.p_in = c->Y[d]; sp.p_out = c->X[d]; sp.v = c->V[d];

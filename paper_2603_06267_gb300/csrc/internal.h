@@ -24,7 +24,8 @@
 template <typename T, int N>
 struct VolArgs {
   CUtensorMap tmap;    // 4D (x, y, z, batch) tiled view of p_in for the TMA staging loads
-  CUtensorMap tmap_v;  // same view of v (used when v is staged too)
+  CUtensorMap tmap_v;  // same view of v (used when v is staged too; also the v store box)
+  CUtensorMap tmap_pst;  // view of p_out with the v box (TMA-store tile variants)
   int* err;            // device status word: set to 1 if a bounded wait gives up
   int* step;           // if not NULL, block (0,0,0) advances the run's step counter
   const T* p_in;       // p^{n+1}: stencil source
@@ -224,6 +225,7 @@ struct PmutArgs {
 struct VolSpec {
   const CUtensorMap* tmap;         // tensor map of p_in
   const CUtensorMap* tmap_v;       // tensor map of v (NULL when the variant does not stage v)
+  const CUtensorMap* tmap_pst;     // tensor map of p_out with the v box (TMA-store variants), else NULL
   int* err;
   int* step;                       // step counter to advance (last launch of a step), or NULL
   const void* p_in; void* p_out; void* v;

@@ -79,6 +79,22 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// TMA tensor store shared -> global of a 4-D box (elements outside the
+// tensor are not written), and the bulk-group bookkeeping of the issuing thread
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int x, int y, int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z), "r"(w)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory sources of every committed group have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed group has completed (its global writes done)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // vector loads / stores of runs of consecutive elements
 // ---------------------------------------------------------------------------
@@ -136,16 +152,19 @@ constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
 // read that copy instead of shared memory (FP32 only); MINB: CTAs per SM;
 // RING 3: the p layers in a three-deep ring (v stays two deep), so a p load
 // has two layers of work to hide behind
-template <int A, int B, int C, int Z = 0, int M = 1, int R = 0> struct Shape {
+// TS: the layer's new v and p_next go to shared memory (v in place in its
+// stage, p_next into one of two output tiles) and leave by TMA tensor stores,
+// one per array and layer, instead of per-thread global stores
+template <int A, int B, int C, int Z = 0, int M = 1, int R = 0, int TSV = 0> struct Shape {
   static constexpr int TXE = A, TYE = B, PG = C, MINB = M, RING = R;
-  static constexpr bool ZR = Z != 0;
+  static constexpr bool ZR = Z != 0, TS = TSV != 0;
 };
 template <typename T, int N, int V> struct TileShape {
   using S = Shape<(N <= 4) ? 32 : 16,
                   (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1))), 1>;
 };
 template <typename T, int N> struct NumShapes {
-  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? (N == 6 ? 7 : 6) : 4) : 1;
+  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? (N == 6 ? 9 : 6) : 4) : 1;
 };
 // FP32 N=4: 512 / 512 / 512 / 256 threads, register-column 512 / 256 (two CTAs
 // per SM); FP64 N=4: 256 / 256 / 128 / 512
@@ -169,12 +188,15 @@ template <> struct TileShape<float, 6, 3> { using S = Shape<32, 1, 2>; };
 template <> struct TileShape<float, 6, 4> { using S = Shape<16, 2, 2, 1>; };
 template <> struct TileShape<float, 6, 5> { using S = Shape<16, 2, 1, 1>; };
 template <> struct TileShape<float, 6, 6> { using S = Shape<16, 2, 2, 1, 1, 3>; };
+// FP32 N=6 with TMA stores of the outputs: register column, 384 / 576 threads
+template <> struct TileShape<float, 6, 7> { using S = Shape<16, 2, 2, 1, 1, 0, 1>; };
+template <> struct TileShape<float, 6, 8> { using S = Shape<16, 2, 3, 1, 1, 0, 1>; };
 template <> struct TileShape<double, 6, 0> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<double, 6, 1> { using S = Shape<16, 1, 1>; };
 template <> struct TileShape<double, 6, 2> { using S = Shape<8, 4, 1>; };
 template <> struct TileShape<double, 6, 3> { using S = Shape<16, 2, 2>; };
 
-template <typename T, int N, int TXE, int TYE, int PG, int RING = 0>
+template <typename T, int N, int TXE, int TYE, int PG, int RING = 0, bool TS = false>
 struct Geo {
   static constexpr int AL = 16 / (int)sizeof(T);                // elements per 16 bytes
   static constexpr int NAL = (N + AL - 1) / AL * AL;            // low x halo rounded up to 16 B
@@ -185,8 +207,10 @@ struct Geo {
   static constexpr int BZ = N + 1;                              // staged p planes (one layer)
   static constexpr int PLANE = BX * BY;
   static constexpr size_t P_BYTES = sizeof(T) * (size_t)BZ * PLANE;
-  // v of the owned nodes (+ the box's last x column), N planes, staged in FP32
-  static constexpr int BXV = (TXE * N + 1 + AL - 1) / AL * AL;
+  // v of the owned nodes (+ the box's last x column unless the outputs leave
+  // by TMA stores, whose box must hold the owned columns only), N planes,
+  // staged in FP32
+  static constexpr int BXV = TS ? TXE * N : (TXE * N + 1 + AL - 1) / AL * AL;
   static constexpr int VPLANE = BXV * TYR;
   static constexpr size_t V_BYTES_RAW = sizeof(T) * (size_t)N * VPLANE;
   static constexpr size_t PB = r128(P_BYTES), VBR = r128(V_BYTES_RAW);
@@ -198,7 +222,10 @@ struct Geo {
   static constexpr int PST = (PDEPTH * PB + (VTMA ? 2 * VB : 0) + 128 <= 227 * 1024) ? PDEPTH : 1;
   static constexpr int VST = VTMA ? 2 : 0;
   static constexpr size_t VBASE = PST * PB;
-  static constexpr size_t SMEM = PST * PB + VST * VB + 128;   // + barriers and counters
+  // p_next output tiles (two, alternating by layer) of the TMA-store form
+  static constexpr size_t OBASE = VBASE + VST * VB;
+  static constexpr size_t OB = TS ? VB : 0;
+  static constexpr size_t SMEM = PST * PB + VST * VB + 2 * OB + 128;   // + barriers and counters
   static constexpr int NT = TXE * TYR * PG;
   // vector widths: shared-memory runs start at column NAL + tx*N, global runs at ex*N
   static constexpr int VS = cmin(cmin(AL, pow2_div(N)), pow2_div(gcd_c(N, NAL)));
@@ -211,6 +238,8 @@ struct Geo {
   static_assert((BX * sizeof(T)) % 16 == 0 && (BXV * sizeof(T)) % 16 == 0, "TMA box row not a multiple of 16 B");
   static_assert(BX <= 256 && BY <= 256 && BZ <= 256 && BXV <= 256 && TYR <= 256, "TMA box dimension above 256");
   static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
+  static_assert(!TS || (VTMA && PST == 2 && VST == 2), "TMA stores need the staged v ring");
+  static_assert(!TS || (TXE * N * sizeof(T)) % 16 == 0, "TMA store box row not a multiple of 16 B");
 };
 
 // z stencil of the N owned nodes: sum_q coef[q] * (staged plane q, own column)
@@ -502,9 +531,9 @@ __device__ __forceinline__ int tile_row(int ty) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN, int RING>
+template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN, int RING, bool TS>
 __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
-  using G = Geo<T, N, TXE, TYE, PG, RING>;
+  using G = Geo<T, N, TXE, TYE, PG, RING, TS>;
   static_assert(RING == 0 || G::VTMA, "the three-deep p ring is for kernels that stage v");
   static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
   constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
@@ -634,6 +663,9 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
     const int sp = it % PST, sv = VST ? it % VST : 0;
     const T* S0 = reinterpret_cast<const T*>(smem_raw + sp * G::PB);
     const T* V0 = reinterpret_cast<const T*>(smem_raw + G::VBASE + sv * G::VB);
+    // TMA-store form: new v in place in its stage, p_next into this layer's output tile
+    T* V0w = reinterpret_cast<T*>(smem_raw + G::VBASE + sv * G::VB);
+    T* PO = reinterpret_cast<T*>(smem_raw + G::OBASE + (it & 1) * G::OB);
     const bool last_layer = (ez == A.ne2 - 1);
     const int nplanes = last_layer ? N + 1 : N;
     bool ok = mbar_wait_bounded(&pbar[sp], (uint32_t)((it / PST) & 1));
@@ -643,6 +675,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       // give the copies in flight a bounded chance to land before leaving
       for (int q = 0; q < PST; ++q) (void)mbar_wait_bounded(&pbar[q], (uint32_t)((it / PST) & 1));
       for (int q = 0; q < VST; ++q) (void)mbar_wait_bounded(&vbar[q], (uint32_t)((it / VST) & 1));
+      if constexpr (TS) bulk_wait_all();
       return;
     }
     if (active) {
@@ -872,8 +905,13 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
             pn[a] = xr[N + a] + A.dtp * vn[a];
           }
         }
-        vst<T, VG, N>(vv + (long long)k * A.pz + grow, vn);
-        vst<T, VG, N>(pout + (long long)k * A.pz + grow, pn);
+        if constexpr (TS && ZM != 2) {
+          vst<T, VV, N>(V0w + c * VPLANE + vown, vn);
+          vst<T, VV, N>(PO + c * VPLANE + vown, pn);
+        } else {
+          vst<T, VG, N>(vv + (long long)k * A.pz + grow, vn);
+          vst<T, VG, N>(pout + (long long)k * A.pz + grow, pn);
+        }
       };
       // the box's last x node (column cb+N), owned by the last element column
       auto plane_last_x = [&](int c) {
@@ -921,16 +959,25 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
         T accum = -(x + y + z);
         if (extras_layer && plane_extras(k)) accum += last_extra_val(k, iw_z);
         T* vp = vv + (long long)k * A.pz + grow + N;
+        // TMA-store form: the column lies in the tile's store box only when the
+        // tile is ragged (an inactive column follows); otherwise it is the box's
+        // right neighbour and goes to global memory directly
+        const bool in_box = TS && c < N && tx < TXE - 1;
         T vo;
-        if constexpr (VTMA) vo = (c < N) ? V0[c * VPLANE + vown + N] : *vp;
+        if constexpr (VTMA) vo = (c < N && (!TS || tx < TXE - 1)) ? V0[c * VPLANE + vown + N] : *vp;
         else vo = *vp;
         if constexpr (OPEN) {
           accum -= (abc_plane(k) + A.abc[1]) * vo;
           if (A.has_pml) accum -= pml_terms<T, N>(A, ex * N + N, j, k, b, P[col], vo, mscale * A.iwb * iw_y * iw_z);
         }
         const T vn = vo + A.dtv * accum;
-        *vp = vn;
-        pout[(long long)k * A.pz + grow + N] = P[col] + A.dtp * vn;
+        if (in_box) {
+          V0w[c * VPLANE + vown + N] = vn;
+          PO[c * VPLANE + vown + N] = P[col] + A.dtp * vn;
+        } else {
+          *vp = vn;
+          pout[(long long)k * A.pz + grow + N] = P[col] + A.dtp * vn;
+        }
       };
       for (int c = pg; c < nplanes; c += PG) {
         if (c == 0) plane(std::integral_constant<int, 0>(), 0);
@@ -954,6 +1001,9 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
     // release the layer's stages: the last warp to finish reading them issues their next
     // load, so warps with more work in this layer (vertex rows, the z carry)
     // hold up the others only when the ring runs dry
+    // TMA-store form: the outputs this thread wrote to shared memory become
+    // visible to the async proxy before the counter hands them to the store
+    if constexpr (TS) fence_proxy_async_smem();
     __syncwarp();
     if ((tid & 31) == 0) {
       __threadfence_block();
@@ -961,11 +1011,21 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
         cnt[sp] = 0;
         __threadfence_block();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if constexpr (TS) {
+          // the layer's planes ez*N .. ez*N+N-1 of v (in place in its stage) and
+          // p_next; the stage is refilled only once the stores have read it
+          tma_store_4d(&A.tmap_v, V0w, x0, y0, ez * N, b);
+          tma_store_4d(&A.tmap_pst, PO, x0, y0, ez * N, b);
+          bulk_commit();
+          bulk_wait_read_all();
+        }
         if (ez + PST < ez1) issue_p(ez + PST, sp);
         if (ez + VST < ez1) issue_v(ez + VST, sv);
       }
     }
   }
+  // stores issued by this thread have completed before the CTA leaves
+  if constexpr (TS) bulk_wait_all();
 }
 
 template <typename T, int N>
@@ -973,6 +1033,7 @@ VolArgs<T, N> make_args(const VolSpec& s) {
   VolArgs<T, N> a;
   a.tmap = *s.tmap;
   if (s.tmap_v) a.tmap_v = *s.tmap_v;
+  if (s.tmap_pst) a.tmap_pst = *s.tmap_pst;
   a.err = s.err;
   a.step = s.step;
   a.p_in = static_cast<const T*>(s.p_in);
@@ -1037,9 +1098,10 @@ template <typename T, int N, int V, bool OPEN>
 cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   using SH = typename TileShape<T, N, V>::S;
   constexpr int TXE = SH::TXE, TYE = SH::TYE, PG = SH::PG;
-  using G = Geo<T, N, TXE, TYE, PG, SH::RING>;
+  using G = Geo<T, N, TXE, TYE, PG, SH::RING, SH::TS>;
   if (!s.tmap || !s.err) return cudaErrorInvalidValue;
   if (G::VTMA && !s.tmap_v) return cudaErrorInvalidValue;
+  if (SH::TS && !s.tmap_pst) return cudaErrorInvalidValue;
   VolArgs<T, N> a = make_args<T, N>(s);
   int layers = s.layers_per_cta;
   const int gx = (s.ne[0] + TXE - 1) / TXE;
@@ -1052,7 +1114,7 @@ cudaError_t launch_v(const VolSpec& s, int batch, cudaStream_t st) {
   }
   a.layers_per_cta = layers;
   a.nchunks = (s.ne[2] + layers - 1) / layers;
-  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, OPEN, SH::RING>;
+  auto kern = vol_kernel<T, N, TXE, TYE, PG, SH::ZR, SH::MINB, OPEN, SH::RING, SH::TS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
   if (e != cudaSuccess) return e;
   dim3 grid(gx, gy, a.nchunks * batch);
@@ -1076,6 +1138,8 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
       case 4: if constexpr (NumShapes<T, N>::value > 4) return launch_v<T, N, 4, OPEN>(s, batch, st); break;
       case 5: if constexpr (NumShapes<T, N>::value > 5) return launch_v<T, N, 5, OPEN>(s, batch, st); break;
       case 6: if constexpr (NumShapes<T, N>::value > 6) return launch_v<T, N, 6, OPEN>(s, batch, st); break;
+      case 7: if constexpr (NumShapes<T, N>::value > 7) return launch_v<T, N, 7, OPEN>(s, batch, st); break;
+      case 8: if constexpr (NumShapes<T, N>::value > 8) return launch_v<T, N, 8, OPEN>(s, batch, st); break;
       default: break;
     }
     return cudaErrorInvalidValue;
@@ -1088,7 +1152,7 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
 template <typename T, int N, int V>
 void box_v(unsigned box[3], unsigned vbox[3]) {
   using SH = typename TileShape<T, N, V>::S;
-  using G = Geo<T, N, SH::TXE, SH::TYE, SH::PG, SH::RING>;
+  using G = Geo<T, N, SH::TXE, SH::TYE, SH::PG, SH::RING, SH::TS>;
   box[0] = G::BX;
   box[1] = G::BY;
   box[2] = G::BZ;
@@ -1110,7 +1174,9 @@ int box_n(int tile, unsigned box[3], unsigned vbox[3]) {
       case 3: box_v<T, N, 3>(box, vbox); break;
       case 4: if constexpr (NumShapes<T, N>::value > 4) box_v<T, N, 4>(box, vbox); break;
       case 5: if constexpr (NumShapes<T, N>::value > 5) box_v<T, N, 5>(box, vbox); break;
-      default: if constexpr (NumShapes<T, N>::value > 6) box_v<T, N, 6>(box, vbox); break;
+      case 6: if constexpr (NumShapes<T, N>::value > 6) box_v<T, N, 6>(box, vbox); break;
+      case 7: if constexpr (NumShapes<T, N>::value > 7) box_v<T, N, 7>(box, vbox); break;
+      default: if constexpr (NumShapes<T, N>::value > 8) box_v<T, N, 8>(box, vbox); break;
     }
   } else {
     box_v<T, N, 0>(box, vbox);
