@@ -65,6 +65,12 @@ int srg_adam_step(srg_net* net, float lr, float beta1, float beta2, float eps, v
 int srg_train_step(srg_net* net, const float* x, const float* target, int batch, float lr, double* loss,
                    void* stream);
 
+/* Throughput of the dense-layer product on the tensor cores: C = A B^T with
+ * A [M][K], B [N][K] BF16 (constant fill), FP32 C, reps launches after one
+ * warm-up, timed with CUDA events on `stream`; *tflops = 2 M N K reps / time.
+ * N and K multiples of 64.  Allocates its operands for the call. */
+int srg_gemm_bench(int M, int N, int K, int reps, double* tflops, void* stream);
+
 const char* srg_last_error(void);
 void srg_destroy(srg_net* net);
 

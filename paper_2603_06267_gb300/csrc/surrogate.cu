@@ -2,14 +2,15 @@
 // paper): MLP + transposed-convolution decoder, BF16 weights/activations with
 // FP32 accumulation, MSE loss, Adam.  See include/surrogate.h.
 //
-// Dense layers run on the tensor cores (BF16 WMMA 16x16x16 fragments, FP32
-// accumulators) with a fused epilogue (bias, GELU, BF16 copy); the three
-// product shapes of a layer are  Z = A W^T (forward), dW = dZ^T A and
-// dA = dZ W (backward).  The transposed convolutions are small and run on
-// the CUDA cores.
+// Dense layers run on the tcgen05 tensor cores (tc_gemm.cuh: TMA-fed shared-
+// memory operands, FP32 accumulators in tensor memory) with a fused epilogue
+// (bias, GELU, BF16 copy).  Every product is taken in the form C = A B^T with
+// both operands K-contiguous: the forward Z = A W^T directly; the backward
+// dW = dZ^T A and dA = dZ W after BF16 transposes of dZ, A and W.  The
+// transposed convolutions are small and run on the CUDA cores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <mma.h>
+#include <cuda.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -20,6 +21,7 @@
 
 #include "../../include/dgsem.h"
 #include "../../include/surrogate.h"
+#include "tc_gemm.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -57,75 +59,112 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 }
 
 // ---------------------------------------------------------------------------
-// C[M x N] = op(A) op(B) on the tensor cores.  TA = 0: A is [M][K] row-major;
-// TA = 1: A is stored [K][M].  TB = 0: B is [K][N]; TB = 1: B is stored
-// [N][K].  M, N multiples of 64, K a multiple of 16.  Epilogue: + bias[n],
-// FP32 copy to C (ldc), BF16 copy of gelu(.) (act = 1) or of the value
-// (act = 0) to Cb (ldcb).
+// Dense products on the tcgen05 tensor cores: C[M x N] = A B^T, A [M][K] and
+// B [N][K] BF16 row-major (K contiguous), K a multiple of 64, N a multiple of
+// 64.  Rows of A beyond M are read as zeros (TMA fill) and not written.
 // ---------------------------------------------------------------------------
-struct Epi {
-  const float* bias;
-  float* C; int ldc;
-  bf16* Cb; int ldcb; int act;
+using tcg::Epi;
+
+struct DenseEpi {
+  Epi e;
+  __device__ __forceinline__ void operator()(int m, int n, const uint32_t* r) const {
+    float v[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + (e.bias ? e.bias[n + j] : 0.f);
+    if (e.C) {
+      float4* dst = reinterpret_cast<float4*>(e.C + (size_t)m * e.ldc + n);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    }
+    if (e.Cb) {
+      uint4* dst = reinterpret_cast<uint4*>(e.Cb + (size_t)m * e.ldcb + n);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const float a = e.act ? gelu_f(v[8 * q + 2 * h]) : v[8 * q + 2 * h];
+          const float b = e.act ? gelu_f(v[8 * q + 2 * h + 1]) : v[8 * q + 2 * h + 1];
+          const __nv_bfloat162 p2 = __floats2bfloat162_rn(a, b);
+          w[h] = *reinterpret_cast<const uint32_t*>(&p2);
+        }
+        dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+  }
 };
 
-template <int TA, int TB>
-__global__ void __launch_bounds__(128) gemm_bf16(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
-                                                 int ldb, int M, int N, int K, Epi ep) {
-  using namespace nvcuda;
-  using LA = typename std::conditional<TA == 0, wmma::row_major, wmma::col_major>::type;
-  using LB = typename std::conditional<TB == 0, wmma::row_major, wmma::col_major>::type;
-  __shared__ float tile[64][64 + 4];
-  const int warp = threadIdx.x >> 5;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int wm = m0 + (warp >> 1) * 32, wn = n0 + (warp & 1) * 32;
-  wmma::fragment<wmma::accumulator, 16, 16, 16, float> acc[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) wmma::fill_fragment(acc[i][j], 0.f);
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    wmma::fragment<wmma::matrix_a, 16, 16, 16, bf16, LA> fa[2];
-    wmma::fragment<wmma::matrix_b, 16, 16, 16, bf16, LB> fb[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-      const int m = wm + 16 * i;
-      const bf16* pa = (TA == 0) ? A + (size_t)m * lda + k0 : A + (size_t)k0 * lda + m;
-      wmma::load_matrix_sync(fa[i], pa, lda);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int n = wn + 16 * j;
-      const bf16* pb = (TB == 0) ? B + (size_t)k0 * ldb + n : B + (size_t)n * ldb + k0;
-      wmma::load_matrix_sync(fb[j], pb, ldb);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) wmma::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 2-D tensor map of a BF16 [rows][ld] matrix (cols = K used) for box_rows x 64
+// tiles with 128-byte swizzle
+int tmap_bf16(CUtensorMap* map, const bf16* base, int rows, int cols, int ld, int box_rows) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
   }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      wmma::store_matrix_sync(&tile[(warp >> 1) * 32 + 16 * i][(warp & 1) * 32 + 16 * j], acc[i][j], 64 + 4,
-                              wmma::mem_row_major);
+  if (reinterpret_cast<uintptr_t>(base) % 16 || (ld * 2) % 16) return sfail(DGSEM_EINVAL, "gemm operand misaligned");
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)tcg::BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DGSEM_OK;
+}
+
+template <int BN, int STAGES>
+int tc_launch(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& ep, int* err,
+              cudaStream_t s) {
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = tmap_bf16(&ta, A, M, K, lda, tcg::BM)) || (rc = tmap_bf16(&tb, B, N, K, ldb, BN))) return rc;
+  auto kern = tcg::gemm_kernel<BN, STAGES, DenseEpi>;
+  constexpr int smem = tcg::Geo<BN, STAGES>::SMEM;
+  S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  dim3 grid(N / BN, (M + tcg::BM - 1) / tcg::BM);
+  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, K, DenseEpi{ep}, err);
+  S_TRY(cudaGetLastError());
+  return DGSEM_OK;
+}
+
+// C = A B^T with the tile width that gives the most CTAs up to one wave
+int gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& ep, int* err,
+            cudaStream_t s) {
+  if (M < 1 || N % 64 || K % 64 || K < 64) return sfail(DGSEM_EINVAL, "gemm shape %d x %d x %d not tileable", M, N, K);
+  const int mt = (M + tcg::BM - 1) / tcg::BM;
+  if (N % 128 == 0 && mt * (N / 128) >= 148) return tc_launch<128, 4>(A, lda, B, ldb, M, N, K, ep, err, s);
+  return tc_launch<64, 6>(A, lda, B, ldb, M, N, K, ep, err, s);
+}
+
+// out[c][r] = in[r][c] for a BF16 [R][C] matrix
+__global__ void transpose_bf16(const bf16* __restrict__ in, int R, int C, bf16* __restrict__ out) {
+  __shared__ bf16 t[32][34];
+  const int c = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i;
+    if (r < R && c < C) t[i][threadIdx.x] = in[(size_t)r * C + c];
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < 64 * 64; t += 128) {
-    const int r = t >> 6, c = t & 63;
-    const int m = m0 + r, n = n0 + c;
-    float v = tile[r][c];
-    if (ep.bias) v += ep.bias[n];
-    if (ep.C) ep.C[(size_t)m * ep.ldc + n] = v;
-    if (ep.Cb) ep.Cb[(size_t)m * ep.ldcb + n] = __float2bfloat16(ep.act ? gelu_f(v) : v);
+  const int r = r0 + threadIdx.x;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int cc = blockIdx.x * 32 + i;
+    if (cc < C && r < R) out[(size_t)cc * R + r] = t[threadIdx.x][i];
   }
 }
 
-template <int TA, int TB>
-int gemm(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, const Epi& ep, cudaStream_t s) {
-  if (M % 64 || N % 64 || K % 16) return sfail(DGSEM_EINVAL, "gemm shape %d x %d x %d not tileable", M, N, K);
-  dim3 grid(N / 64, M / 64);
-  gemm_bf16<TA, TB><<<grid, 128, 0, s>>>(A, lda, B, ldb, M, N, K, ep);
+int transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t s) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32);
+  transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(in, R, C, out);
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
@@ -294,6 +333,9 @@ struct srg_net {
   // gradients
   float *gv = nullptr, *gu = nullptr, *ga = nullptr, *gz = nullptr;
   bf16* gzb = nullptr;
+  // BF16 transposes feeding the backward products (K-contiguous operands)
+  bf16 *tA = nullptr, *tB = nullptr, *tW = nullptr;
+  int* d_err = nullptr;               // set by a tensor-core product whose bounded wait gave up
   double* d_loss = nullptr;
   long long t = 0;                    // Adam step counter
   std::vector<void*> allocs;
@@ -319,14 +361,14 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
   int fan = c.d_in;
   for (int l = 0; l < c.n_hidden; ++l) {
     Epi ep{n->P + n->offB[l], n->z[l], c.hidden, n->a[l + 1], c.hidden, 1};
-    int rc = gemm<0, 1>(n->a[l], fan, n->Pb + n->offW[l], fan, B, c.hidden, fan, ep, s);
+    int rc = gemm_nt(n->a[l], fan, n->Pb + n->offW[l], fan, B, c.hidden, fan, ep, n->d_err, s);
     if (rc) return rc;
     fan = c.hidden;
   }
   const int L = c.n_hidden;
   const int nd = c.c0 * c.t0;
   Epi ep{n->P + n->offB[L], n->zd, nd, n->u[0], nd, 0};
-  int rc = gemm<0, 1>(n->a[L], fan, n->Pb + n->offW[L], fan, B, nd, fan, ep, s);
+  int rc = gemm_nt(n->a[L], fan, n->Pb + n->offW[L], fan, B, nd, fan, ep, n->d_err, s);
   if (rc) return rc;
   for (int j = 0; j < c.n_conv; ++j) {
     const int last = j == c.n_conv - 1;
@@ -334,6 +376,17 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
                                                conv_cin(c, j), c.conv_ch[j], conv_len(c, j), n->v[j],
                                                last ? nullptr : n->u[j + 1], 1);
     S_TRY(cudaGetLastError());
+  }
+  return DGSEM_OK;
+}
+
+// a bounded wait of a tensor-core product gave up (the flag is cleared)
+int check_err(srg_net* n) {
+  int err = 0;
+  S_TRY(cudaMemcpy(&err, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    S_TRY(cudaMemset(n->d_err, 0, sizeof(int)));
+    return sfail(DGSEM_ETIMEOUT, "a bounded wait of a tensor-core product gave up");
   }
   return DGSEM_OK;
 }
@@ -427,10 +480,14 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
   const size_t maxw = std::max((size_t)c.hidden, (size_t)c.d_in);
   if ((rc = A((void**)&n->gv, B * maxc * 4)) || (rc = A((void**)&n->gu, B * maxc * 4)) ||
       (rc = A((void**)&n->ga, B * std::max(maxw, nd) * 4)) || (rc = A((void**)&n->gz, B * std::max(maxw, nd) * 4)) ||
-      (rc = A((void**)&n->gzb, B * std::max(maxw, nd) * 2))) {
+      (rc = A((void**)&n->gzb, B * std::max(maxw, nd) * 2)) ||
+      (rc = A((void**)&n->tA, B * std::max((size_t)c.hidden, nd) * 2)) || (rc = A((void**)&n->tB, B * maxw * 2)) ||
+      (rc = A((void**)&n->tW, std::max(nd * c.hidden, (size_t)c.hidden * maxw) * 2)) ||
+      (rc = A((void**)&n->d_err, sizeof(int)))) {
     srg_destroy(n);
     return rc;
   }
+  S_TRY(cudaMemset(n->d_err, 0, sizeof(int)));
   if ((rc = srg_set_params(n, h.data(), o))) { srg_destroy(n); return rc; }
   S_TRY(cudaMemset(n->M1, 0, o * 4));
   S_TRY(cudaMemset(n->M2, 0, o * 4));
@@ -472,7 +529,7 @@ int srg_forward(srg_net* n, const float* x, int B, float* y, void* stream) {
   const size_t outn = (size_t)B * c.conv_ch[c.n_conv - 1] * conv_len(c, c.n_conv);
   S_TRY(cudaMemcpyAsync(y, n->v[c.n_conv - 1], outn * 4, cudaMemcpyDeviceToDevice, s));
   S_TRY(cudaStreamSynchronize(s));
-  return DGSEM_OK;
+  return check_err(n);
 }
 
 int srg_backward(srg_net* n, const float* x, const float* target, int B, double* loss, void* stream) {
@@ -505,28 +562,40 @@ int srg_backward(srg_net* n, const float* x, const float* target, int B, double*
   to_bf16<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gu, n->gzb, (size_t)B * nd);
   col_sum<<<(nd + 127) / 128, 128, 0, s>>>(n->gu, B, nd, n->G + n->offB[L]);
   S_TRY(cudaGetLastError());
+  // dW_dec [nd][hidden] = dZ^T a_L: operands dZ^T [nd][B] and a_L^T [hidden][B]
   Epi ew{nullptr, n->G + n->offW[L], c.hidden, nullptr, 0, 0};
-  if ((rc = gemm<1, 0>(n->gzb, nd, n->a[L], c.hidden, nd, c.hidden, B, ew, s))) return rc;
+  if ((rc = transpose(n->gzb, B, nd, n->tA, s)) || (rc = transpose(n->a[L], B, c.hidden, n->tB, s)) ||
+      (rc = gemm_nt(n->tA, B, n->tB, B, nd, c.hidden, B, ew, n->d_err, s)))
+    return rc;
+  // da_L [B][hidden] = dZ W_dec: operands dZ [B][nd] and W_dec^T [hidden][nd]
   Epi ea{nullptr, n->ga, c.hidden, nullptr, 0, 0};
-  if ((rc = gemm<0, 0>(n->gzb, nd, n->Pb + n->offW[L], c.hidden, B, c.hidden, nd, ea, s))) return rc;
+  if ((rc = transpose(n->Pb + n->offW[L], nd, c.hidden, n->tW, s)) ||
+      (rc = gemm_nt(n->gzb, nd, n->tW, nd, B, c.hidden, nd, ea, n->d_err, s)))
+    return rc;
   // hidden layers, last to first
   for (int l = L - 1; l >= 0; --l) {
     const int fan = l == 0 ? c.d_in : c.hidden;
     gelu_bwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->ga, n->z[l], n->gz, n->gzb, (size_t)B * c.hidden);
     col_sum<<<(c.hidden + 127) / 128, 128, 0, s>>>(n->gz, B, c.hidden, n->G + n->offB[l]);
     S_TRY(cudaGetLastError());
+    // dW_l [hidden][fan] = dZ^T a_l: operands dZ^T [hidden][B] and a_l^T [fan][B]
     Epi eW{nullptr, n->G + n->offW[l], fan, nullptr, 0, 0};
-    if ((rc = gemm<1, 0>(n->gzb, c.hidden, n->a[l], fan, c.hidden, fan, B, eW, s))) return rc;
+    if ((rc = transpose(n->gzb, B, c.hidden, n->tA, s)) || (rc = transpose(n->a[l], B, fan, n->tB, s)) ||
+        (rc = gemm_nt(n->tA, B, n->tB, B, c.hidden, fan, B, eW, n->d_err, s)))
+      return rc;
     if (l > 0) {
+      // da_l [B][fan] = dZ W_l: operands dZ [B][hidden] and W_l^T [fan][hidden]
       Epi eA{nullptr, n->ga, c.hidden, nullptr, 0, 0};
-      if ((rc = gemm<0, 0>(n->gzb, c.hidden, n->Pb + n->offW[l], fan, B, fan, c.hidden, eA, s))) return rc;
+      if ((rc = transpose(n->Pb + n->offW[l], c.hidden, fan, n->tW, s)) ||
+          (rc = gemm_nt(n->gzb, c.hidden, n->tW, c.hidden, B, fan, c.hidden, eA, n->d_err, s)))
+        return rc;
     }
   }
   double l_host = 0.0;
   S_TRY(cudaMemcpyAsync(&l_host, n->d_loss, 8, cudaMemcpyDeviceToHost, s));
   S_TRY(cudaStreamSynchronize(s));
   if (loss) *loss = l_host;
-  return DGSEM_OK;
+  return check_err(n);
 }
 
 int srg_adam_step(srg_net* n, float lr, float b1, float b2, float eps, void* stream) {
@@ -543,6 +612,51 @@ int srg_train_step(srg_net* n, const float* x, const float* target, int B, float
   int rc = srg_backward(n, x, target, B, loss, stream);
   if (rc) return rc;
   return srg_adam_step(n, lr, 0.9f, 0.999f, 1e-8f, stream);
+}
+
+int srg_gemm_bench(int M, int N, int K, int reps, double* tflops, void* stream) {
+  if (!tflops || reps < 1 || M < 1 || N < 64 || K < 64) return sfail(DGSEM_EINVAL, "bad arguments");
+  *tflops = 0.0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bf16 *A = nullptr, *B = nullptr;
+  float* C = nullptr;
+  int* err = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = DGSEM_OK;
+  auto cleanup = [&]() {
+    cudaFree(A); cudaFree(B); cudaFree(C); cudaFree(err);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  if (cudaMalloc(&A, (size_t)M * K * 2) != cudaSuccess || cudaMalloc(&B, (size_t)N * K * 2) != cudaSuccess ||
+      cudaMalloc(&C, (size_t)M * N * 4) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    cleanup();
+    return sfail(DGSEM_ENOMEM, "gemm bench buffers");
+  }
+  do {
+    if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess || cudaMemset(A, 0x3c, (size_t)M * K * 2) != cudaSuccess ||
+        cudaMemset(B, 0x3c, (size_t)N * K * 2) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+      rc = sfail(DGSEM_ECUDA, "gemm bench set-up");
+      break;
+    }
+    Epi ep{nullptr, C, N, nullptr, 0, 0};
+    if ((rc = gemm_nt(A, K, B, K, M, N, K, ep, err, s))) break;     // warm-up
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && !rc; ++r) rc = gemm_nt(A, K, B, K, M, N, K, ep, err, s);
+    cudaEventRecord(e1, s);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { rc = sfail(DGSEM_ECUDA, "gemm bench launch"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    int h_err = 0;
+    cudaMemcpy(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (h_err) { rc = sfail(DGSEM_ETIMEOUT, "a bounded wait of the tensor-core product gave up"); break; }
+    *tflops = 2.0 * M * N * (double)K * reps / (ms * 1e-3) / 1e12;
+  } while (false);
+  cleanup();
+  return rc;
 }
 
 void srg_destroy(srg_net* n) {

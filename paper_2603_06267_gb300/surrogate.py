@@ -13,8 +13,8 @@ import numpy as np
 from . import dgsem
 
 SRG_EXPORTED = ["srg_create", "srg_num_params", "srg_get_params", "srg_set_params", "srg_get_grads",
-                "srg_forward", "srg_backward", "srg_adam_step", "srg_train_step", "srg_last_error",
-                "srg_destroy"]
+                "srg_forward", "srg_backward", "srg_adam_step", "srg_train_step", "srg_gemm_bench",
+                "srg_last_error", "srg_destroy"]
 
 
 class SrgConfig(ctypes.Structure):
@@ -40,11 +40,12 @@ def load():
     lib.srg_backward.argtypes = [vp, vp, vp, c_int, POINTER(c_double), vp]
     lib.srg_adam_step.argtypes = [vp, c_float, c_float, c_float, c_float, vp]
     lib.srg_train_step.argtypes = [vp, vp, vp, c_int, c_float, POINTER(c_double), vp]
+    lib.srg_gemm_bench.argtypes = [c_int, c_int, c_int, c_int, POINTER(c_double), vp]
     lib.srg_last_error.restype = ctypes.c_char_p
     lib.srg_destroy.argtypes = [vp]
     lib.srg_destroy.restype = None
     for n in ("srg_create", "srg_get_params", "srg_set_params", "srg_get_grads", "srg_forward", "srg_backward",
-              "srg_adam_step", "srg_train_step"):
+              "srg_adam_step", "srg_train_step", "srg_gemm_bench"):
         getattr(lib, n).restype = c_int
     _lib = lib
     return lib
@@ -53,6 +54,17 @@ def load():
 def _check(code, where):
     if code != 0:
         raise dgsem.DgsemError(code, where, _lib.srg_last_error().decode())
+
+
+def gemm_tflops(M, N, K, reps=20, stream=None):
+    """TFLOP/s of the dense-layer product C = A B^T (A [M][K], B [N][K]) on the
+    tensor cores, timed with CUDA events."""
+    lib = load()
+    v = c_double()
+    if stream is None:
+        stream = dgsem._current_stream()
+    _check(lib.srg_gemm_bench(M, N, K, reps, byref(v), stream), "srg_gemm_bench")
+    return v.value
 
 
 class Surrogate:

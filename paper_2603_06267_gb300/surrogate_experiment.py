@@ -3,8 +3,13 @@ solver, train the surrogate with the project's kernels, and report its
 held-out error against the solver and its speed in patterns per second.
 
     python -m paper_2603_06267_gb300.surrogate_experiment [--train 4096 --test 512 --epochs 60]
+    python -m paper_2603_06267_gb300.surrogate_experiment --timing [--d-in 2048 --batch 512]
+    python -m paper_2603_06267_gb300.surrogate_experiment --gemm 512 2048 2048
 
-Prints one JSON line.  Everything runs on cuda:0.
+--timing measures the forward pass and one training step of the network at
+the given width on random inputs (no solver data); --gemm the rate of one
+dense-layer product C = A B^T on the tensor cores.  Prints one JSON line.
+Everything runs on cuda:0.
 """
 from __future__ import annotations
 
@@ -30,12 +35,23 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--n-out", type=int, default=512)
     ap.add_argument("--hidden", type=int, default=2048)
+    ap.add_argument("--d-in", type=int, default=2048)
+    ap.add_argument("--timing", action="store_true")
+    ap.add_argument("--gemm", type=int, nargs=3, default=None, metavar=("M", "N", "K"))
     args = ap.parse_args()
     import torch
     import workloads as W
     from paper_2603_06267_gb300 import surrogate as S
 
     torch.cuda.set_device(0)
+    if args.gemm:
+        M, N, K = args.gemm
+        tf = S.gemm_tflops(M, N, K, reps=20)
+        print(json.dumps({"experiment": "dense_product_rate", "M": M, "N": N, "K": K, "tflops": tf}), flush=True)
+        return
+    if args.timing:
+        timing(args, torch, S)
+        return
     n = args.train + args.test
     t0 = time.perf_counter()
     X, Y, t_solve = S.generate_dataset(W.surrogate_array, n, batch=64, seed=11, n_out=args.n_out)
@@ -80,6 +96,48 @@ def main():
         "speedup": (nt / t_inf) / (n / t_solve),
         "seconds": {"data": t_data, "solver": t_solve, "train": t_train, "inference_per_batch": t_inf},
     }
+    print(json.dumps(out), flush=True)
+    net.close()
+
+
+def timing(args, torch, S):
+    """Forward and training-step time of the experiment-width network on
+    random inputs, with the flop counts of its dense and convolution parts."""
+    B = args.batch
+    conv = (128, 128, 64, 64)
+    net = S.Surrogate(d_in=args.d_in, hidden=args.hidden, n_hidden=3, c0=256, t0=32, conv_ch=conv, max_batch=B,
+                      seed=13)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.randn((B, args.d_in), device="cuda", generator=g)
+    t = torch.randn((B, net.c_out, net.t_out), device="cuda", generator=g)
+    y = torch.zeros((B, net.c_out, net.t_out), device="cuda")
+    for _ in range(3):
+        net.forward(x, y)
+        net.backward(x, t)
+    torch.cuda.synchronize()
+    reps = 20
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.forward(x, y)
+    torch.cuda.synchronize()
+    t_fwd = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.backward(x, t)
+        net.adam(1e-4)
+    torch.cuda.synchronize()
+    t_step = (time.perf_counter() - t0) / reps
+    H, nd = args.hidden, 256 * 32
+    dense = 2.0 * B * (args.d_in * H + 2 * H * H + H * nd)
+    ci, ti, convf = 256, 32, 0.0
+    for co in conv:
+        convf += 2.0 * B * co * (2 * ti) * ci * 2          # two of the four taps reach each output sample
+        ci, ti = co, 2 * ti
+    out = {"experiment": "surrogate_timing", "batch": B, "d_in": args.d_in, "hidden": H, "params": net.n,
+           "forward_ms": t_fwd * 1e3, "train_step_ms": t_step * 1e3,
+           "forward_gflop": {"dense": dense / 1e9, "transposed_conv": convf / 1e9},
+           "forward_tflops": (dense + convf) / t_fwd / 1e12,
+           "patterns_per_s": B / t_fwd}
     print(json.dumps(out), flush=True)
     net.close()
 

@@ -75,6 +75,59 @@ def test_adam_step_matches_reference():
     net.close()
 
 
+FULL = dict(d_in=2048, hidden=2048, n_hidden=3, c0=256, t0=32, conv_ch=(128, 128, 64, 64))
+
+
+def test_forward_and_gradients_at_experiment_widths():
+    """The experiment's network (1024 PMUTs x 2 features, three hidden layers
+    of 2048, decoder 2048 -> 256 x 32, four transposed convolutions to 64 x
+    512): forward, loss and every gradient block against the CPU reference
+    at 64 patterns."""
+    import torch
+    from paper_2603_06267_gb300 import surrogate as S
+    net = S.Surrogate(max_batch=64, seed=11, **FULL)
+    cfg = R.SurrogateConfig(d_in=FULL["d_in"], hidden=FULL["hidden"], n_hidden=FULL["n_hidden"], c0=FULL["c0"],
+                            t0=FULL["t0"], conv_ch=list(FULL["conv_ch"]))
+    assert net.n == cfg.num_params()
+    ref = R.SurrogateRef(cfg, quant=True)
+    rng = np.random.default_rng(12)
+    x = rng.normal(size=(64, cfg.d_in)).astype(np.float32)
+    t = rng.normal(size=(64, cfg.c_out, cfg.t_out)).astype(np.float32)
+    y = torch.zeros((64, cfg.c_out, cfg.t_out), dtype=torch.float32, device="cuda")
+    net.forward(torch.tensor(x, device="cuda"), y)
+    p = net.params().astype(np.float64)
+    assert _rel(y.cpu().numpy(), ref.forward(p, x)) < 5e-3
+    loss = net.backward(torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda"))
+    lr_, gr = ref.loss_and_grad(p, x, t.astype(np.float64))
+    assert abs(loss - lr_) <= 1e-3 * lr_
+    g = net.grads()
+    o = 0
+    for name, shp in cfg.shapes():
+        n = int(np.prod(shp))
+        assert _rel(g[o:o + n], gr[o:o + n]) < 2e-2, name
+        o += n
+    net.close()
+
+
+@pytest.mark.parametrize("M,N,K,what", [(512, 2048, 2048, "hidden layer forward / dA"),
+                                        (512, 8192, 2048, "decoder forward"),
+                                        (2048, 2048, 512, "hidden layer dW")])
+def test_dense_product_rate(M, N, K, what):
+    """Tensor-core rate of the dense-layer products at the experiment's
+    shapes (512 patterns), against the measured BF16 peak."""
+    import json
+    import os
+    from paper_2603_06267_gb300 import surrogate as S
+    tf = S.gemm_tflops(M, N, K, reps=50)
+    peak = None
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        peak = json.load(open(path)).get("bf16_tflops")
+    frac = f" = {tf / peak:.3f} of the measured {peak:.0f} TFLOP/s" if peak else ""
+    print(f"{what}: {M} x {N} x {K}: {tf:.1f} TFLOP/s{frac}")
+    assert tf > 50.0
+
+
 def test_training_reduces_loss():
     import torch
     from paper_2603_06267_gb300 import surrogate as S
