@@ -132,7 +132,7 @@ int tc_launch(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int 
   constexpr int smem = tcg::Geo<BN, STAGES>::SMEM;
   S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   dim3 grid(N / BN, (M + tcg::BM - 1) / tcg::BM);
-  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, K, DenseEpi{ep}, err);
+  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, K, DenseEpi{ep}, err, tcg::DenseA());
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
@@ -146,9 +146,11 @@ int gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
   return tc_launch<64, 6>(A, lda, B, ldb, M, N, K, ep, err, s);
 }
 
-// out[c][r] = in[r][c] for a BF16 [R][C] matrix
+// out[c][r] = in[r][c] for a BF16 [R][C] matrix (blockIdx.z: one of a batch of them)
 __global__ void transpose_bf16(const bf16* __restrict__ in, int R, int C, bf16* __restrict__ out) {
   __shared__ bf16 t[32][34];
+  in += (size_t)blockIdx.z * R * C;
+  out += (size_t)blockIdx.z * R * C;
   const int c = blockIdx.x * 32 + threadIdx.x, r0 = blockIdx.y * 32;
   for (int i = threadIdx.y; i < 32; i += 8) {
     const int r = r0 + i;
@@ -162,9 +164,90 @@ __global__ void transpose_bf16(const bf16* __restrict__ in, int R, int C, bf16* 
   }
 }
 
-int transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t s) {
-  dim3 grid((C + 31) / 32, (R + 31) / 32);
+int transpose(const bf16* in, int R, int C, bf16* out, cudaStream_t s, int nbatch = 1) {
+  dim3 grid((C + 31) / 32, (R + 31) / 32, nbatch);
   transpose_bf16<<<grid, dim3(32, 8), 0, s>>>(in, R, C, out);
+  S_TRY(cudaGetLastError());
+  return DGSEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Transposed convolution (kernel 4, stride 2, padding 1) on the tensor cores.
+// Output sample t = 2m + par of channel co takes two taps of every input
+// channel:  even (par 0): W[.][co][1] u[m] + W[.][co][3] u[m - 1];  odd
+// (par 1): W[.][co][0] u[m + 1] + W[.][co][2] u[m].  With u in time-major
+// layout [b][t][ci] each parity is one product C[(b, m)][co] = A B^T, K = 2 Ci:
+// A's first Ci columns are u at time m + sh0, the next Ci at m + sh1 (zeros
+// past either end), B = [W_k0 | W_k1]^T per output channel.
+// ---------------------------------------------------------------------------
+// Be / Bo [Co][2 Ci]: the even and odd tap pairs of W [Ci][Co][4]
+__global__ void convt_taps(const bf16* __restrict__ W, int Ci, int Co, bf16* __restrict__ Be, bf16* __restrict__ Bo) {
+  const size_t n = (size_t)Ci * Co;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(idx % Co), ci = (int)(idx / Co);
+    const bf16* w = W + ((size_t)ci * Co + co) * 4;
+    Be[(size_t)co * 2 * Ci + ci] = w[1];
+    Be[(size_t)co * 2 * Ci + Ci + ci] = w[3];
+    Bo[(size_t)co * 2 * Ci + ci] = w[0];
+    Bo[(size_t)co * 2 * Ci + Ci + ci] = w[2];
+  }
+}
+
+// v[b][co][2m + par] = acc + bias[co]; u_next = bf16(gelu(v)) (channel-major)
+struct ConvEpi {
+  float* v; bf16* un; const float* bias; int T, Co, par;
+  __device__ __forceinline__ void operator()(int r, int n, const uint32_t* acc) const {
+    const int b = r / T, m = r % T, To = 2 * T;
+    const size_t o = ((size_t)b * Co + n) * To + 2 * m + par;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float val = __uint_as_float(acc[j]) + bias[n + j];
+      v[o + (size_t)j * To] = val;
+      if (un) un[o + (size_t)j * To] = __float2bfloat16(gelu_f(val));
+    }
+  }
+};
+
+// 3-D tensor map of a BF16 [B][T][C] array for 128-row tiles of (b, t) pairs
+int tmap_btc(CUtensorMap* map, const bf16* base, int B, int T, int C) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  if (!((T >= tcg::BM && T % tcg::BM == 0) || (T < tcg::BM && tcg::BM % T == 0)))
+    return sfail(DGSEM_EINVAL, "time length %d neither divides nor is a multiple of 128", T);
+  const cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)T, (cuuint64_t)B};
+  const cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)T * C * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)tcg::BK, (cuuint32_t)std::min(T, tcg::BM),
+                             (cuuint32_t)std::max(1, tcg::BM / T)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DGSEM_OK;
+}
+
+// one parity of a transposed convolution: u_tm [B][T][Ci] (time-major), taps
+// Bw [Co][2 Ci]; rows (b, m) of C go to v / u_next at time 2m + par
+int convt_parity(const bf16* u_tm, int B, int T, int Ci, const bf16* Bw, int Co, int par, const float* bias, float* v,
+                 bf16* un, int* err, cudaStream_t s) {
+  if (Ci % tcg::BK || Co % 64) return sfail(DGSEM_EINVAL, "convolution channels %d -> %d not tileable", Ci, Co);
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = tmap_btc(&ta, u_tm, B, T, Ci)) || (rc = tmap_bf16(&tb, Bw, Co, 2 * Ci, 2 * Ci, 64))) return rc;
+  auto kern = tcg::gemm_kernel<64, 6, ConvEpi, tcg::ShiftA>;
+  constexpr int smem = tcg::Geo<64, 6>::SMEM;
+  S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int M = B * T;
+  dim3 grid(Co / 64, M / tcg::BM);
+  const tcg::ShiftA al{Ci / tcg::BK, T, par == 0 ? 0 : 1, par == 0 ? -1 : 0};
+  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, 2 * Ci, ConvEpi{v, un, bias, T, Co, par}, err, al);
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
@@ -335,6 +418,10 @@ struct srg_net {
   bf16* gzb = nullptr;
   // BF16 transposes feeding the backward products (K-contiguous operands)
   bf16 *tA = nullptr, *tB = nullptr, *tW = nullptr;
+  // tensor-core transposed convolutions: time-major input copy and tap pairs;
+  // layers whose channel counts are not multiples of 64 run on the CUDA cores
+  bf16 *utm = nullptr, *Bev = nullptr;
+  std::vector<int> conv_tc;
   int* d_err = nullptr;               // set by a tensor-core product whose bounded wait gave up
   double* d_loss = nullptr;
   long long t = 0;                    // Adam step counter
@@ -372,10 +459,21 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
   if (rc) return rc;
   for (int j = 0; j < c.n_conv; ++j) {
     const int last = j == c.n_conv - 1;
-    convt_fwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->Pb + n->offW[L + 1 + j], n->P + n->offB[L + 1 + j], B,
-                                               conv_cin(c, j), c.conv_ch[j], conv_len(c, j), n->v[j],
-                                               last ? nullptr : n->u[j + 1], 1);
-    S_TRY(cudaGetLastError());
+    const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
+    if (n->conv_tc[j]) {
+      // time-major copy of the input, the tap pairs, then the two parities
+      if ((rc = transpose(n->u[j], ci, ti, n->utm, s, B))) return rc;
+      convt_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev, n->Bev + (size_t)co * 2 * ci);
+      S_TRY(cudaGetLastError());
+      for (int par = 0; par < 2; ++par)
+        if ((rc = convt_parity(n->utm, B, ti, ci, n->Bev + (size_t)par * co * 2 * ci, co, par, n->P + n->offB[L + 1 + j],
+                               n->v[j], last ? nullptr : n->u[j + 1], n->d_err, s)))
+          return rc;
+    } else {
+      convt_fwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->Pb + n->offW[L + 1 + j], n->P + n->offB[L + 1 + j], B,
+                                                 ci, co, ti, n->v[j], last ? nullptr : n->u[j + 1], 1);
+      S_TRY(cudaGetLastError());
+    }
   }
   return DGSEM_OK;
 }
@@ -488,6 +586,23 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
     return rc;
   }
   S_TRY(cudaMemset(n->d_err, 0, sizeof(int)));
+  // which transposed convolutions take the tensor-core path (channel counts
+  // multiples of 64; time lengths that tile 128 rows), and their scratch
+  size_t utm_n = 0, bev_n = 0;
+  n->conv_tc.assign(c.n_conv, 0);
+  for (int j = 0; j < c.n_conv; ++j) {
+    const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
+    const bool tiles_t = (ti >= 128 && ti % 128 == 0) || (ti < 128 && 128 % ti == 0);
+    if (ci % 64 == 0 && co % 64 == 0 && tiles_t && ((size_t)max_batch * ti) % 128 == 0) {
+      n->conv_tc[j] = 1;
+      utm_n = std::max(utm_n, B * ci * ti);
+      bev_n = std::max(bev_n, (size_t)4 * ci * co);
+    }
+  }
+  if (utm_n && ((rc = A((void**)&n->utm, utm_n * 2)) || (rc = A((void**)&n->Bev, bev_n * 2)))) {
+    srg_destroy(n);
+    return rc;
+  }
   if ((rc = srg_set_params(n, h.data(), o))) { srg_destroy(n); return rc; }
   S_TRY(cudaMemset(n->M1, 0, o * 4));
   S_TRY(cudaMemset(n->M2, 0, o * 4));

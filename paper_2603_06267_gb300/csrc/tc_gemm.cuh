@@ -4,7 +4,9 @@
 //     C[m][n] = sum_k A[m][k] B[n][k]        (A [M][K], B [N][K], both K-contiguous)
 //
 // One CTA computes a 128 x BN tile of C.  Thread 0 streams 128 x 64 tiles of A
-// and BN x 64 tiles of B into a ring of shared-memory stages with TMA
+// (rows of a matrix, or time-shifted rows of a [batch][time][channel] array
+// for the transposed convolutions) and BN x 64 tiles of B into a ring of
+// shared-memory stages with TMA
 // (cp.async.bulk.tensor, 128-byte swizzle); thread 32 issues tcgen05.mma
 // (kind::f16, BF16 inputs, M = 128, N = BN, K = 16 per instruction) into a
 // 128-lane x BN-column FP32 accumulator in tensor memory, and releases each
@@ -60,6 +62,36 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Where the 128 x 64 A tile of k-tile kt and row tile mt comes from.
+// DenseA: rows mt*128 .. of a 2-D [M][K] matrix.
+struct DenseA {
+  __device__ __forceinline__ void operator()(void* dst, const CUtensorMap* map, uint64_t* bar, int kt, int mt) const {
+    tma_load_2d(dst, map, bar, kt * BK, mt * BM);
+  }
+};
+// ShiftA: the rows of a 3-D [B][T][C] array taken as (b, t) pairs, t fastest
+// (T divides 128 or 128 divides T); the first kh k-tiles read channels
+// 64 kt .. at time t + sh0, the others channels 64 (kt - kh) .. at time
+// t + sh1.  Rows shifted past either end of the time axis read zeros.
+struct ShiftA {
+  int kh, T, sh0, sh1;
+  __device__ __forceinline__ void operator()(void* dst, const CUtensorMap* map, uint64_t* bar, int kt, int mt) const {
+    const bool second = kt >= kh;
+    const int c0 = (second ? kt - kh : kt) * BK;
+    const int sh = second ? sh1 : sh0;
+    const int r0 = mt * BM;
+    tma_load_3d(dst, map, bar, c0, (r0 % T) + sh, r0 / T);
+  }
+};
 
 // Shared-memory matrix descriptor of a K-major operand tile written by TMA
 // with 128-byte swizzle: rows of 128 bytes, 8-row (1024-byte) swizzle atoms
@@ -134,10 +166,10 @@ struct Epi {
   __nv_bfloat16* Cb; int ldcb; int act;
 };
 
-template <int BN, int STAGES, typename EpiFn>
+template <int BN, int STAGES, typename EpiFn, typename ALoad = DenseA>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int K,
-                EpiFn epi, int* err) {
+                EpiFn epi, int* err, ALoad aload) {
   using G = Geo<BN, STAGES>;
   extern __shared__ unsigned char raw[];
   // 1024-byte aligned base of the stages (128-byte swizzle atoms)
@@ -183,7 +215,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       unsigned char* st = base + s * G::STAGE;
       mbar_expect_tx(&full[s], (uint32_t)G::STAGE);
-      tma_load_2d(st, &tmA, &full[s], kt * BK, m0);
+      aload(st, &tmA, &full[s], kt, blockIdx.y);
       tma_load_2d(st + G::A_BYTES, &tmB, &full[s], kt * BK, n0);
       issued = kt + 1;
     }
