@@ -167,8 +167,10 @@ class SurrogateRef:
         G = {}
         dv = 2.0 * (y - target) / nel
         for j in range(len(cfg.conv_ch) - 1, -1, -1):
-            du, dW, db = convt_bwd(us[j], q(P[f"Wc{j}"]), dv)
-            G[f"Wc{j}"], G[f"bc{j}"] = dW, db
+            # the products read dv rounded like the other pre-activation
+            # gradients; the bias gradient sums it as it is
+            du, dW, _ = convt_bwd(us[j], q(P[f"Wc{j}"]), q(dv))
+            G[f"Wc{j}"], G[f"bc{j}"] = dW, dv.sum(axis=(0, 2))
             if j > 0:
                 dv = du * gelu_grad(vs[j - 1])
         dzd = q(du.reshape(du.shape[0], -1))

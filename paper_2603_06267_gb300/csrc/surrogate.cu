@@ -253,6 +253,166 @@ int convt_parity(const bf16* u_tm, int B, int T, int Ci, const bf16* Bw, int Co,
 }
 
 // ---------------------------------------------------------------------------
+// Gradients of a transposed convolution on the tensor cores (dv = dL/dv in
+// FP32 [B][Co][To], To = 2 Ti; the products read it rounded to BF16):
+//   du[b][ci][i] = sum_co sum_k W[ci][co][k] dv[b][co][2i - 1 + k]:
+//     one product over rows (b, i), K = 4 Co in four segments (k = 0..3)
+//     read from the parity-split, time-major dvp[par][b][m][co] at time
+//     m = i - 1, i, i, i + 1 of parity 1, 0, 1, 0;  B = Bd[ci][k Co + co];
+//   dW[ci][co][k] = sum_{b,i} u[b][ci][i] dv[b][co][2i - 1 + k]:
+//     four products (one per k) over K = (b, i) with K-contiguous copies
+//     uK[ci][b Ti + i] and dvK[k][co][b Ti + i], split over S parts of K
+//     whose partial sums a fixed-order reduction adds;
+//   db[co] = sum_{b,t} dv[b][co][t] in FP32 (no rounding).
+// ---------------------------------------------------------------------------
+// dvp[par][b][m][co] = bf16(dv[b][co][2m + par])
+__global__ void convt_dv_split(const float* __restrict__ dv, int B, int Co, int Ti, bf16* __restrict__ dvp) {
+  __shared__ float t[32][65];
+  const int To = 2 * Ti;
+  const int b = blockIdx.z, co0 = blockIdx.y * 32, t0 = blockIdx.x * 64;
+  for (int r = threadIdx.y; r < 32; r += 8)
+    for (int c = threadIdx.x; c < 64; c += 32) {
+      const int co = co0 + r, tt = t0 + c;
+      t[r][c] = (co < Co && tt < To) ? dv[((size_t)b * Co + co) * To + tt] : 0.f;
+    }
+  __syncthreads();
+  const size_t plane = (size_t)B * Ti * Co;
+  for (int c = threadIdx.y; c < 64; c += 8) {
+    const int tt = t0 + c, co = co0 + threadIdx.x;
+    if (tt < To && co < Co) dvp[(size_t)(tt & 1) * plane + ((size_t)b * Ti + (tt >> 1)) * Co + co] = __float2bfloat16(t[threadIdx.x][c]);
+  }
+}
+
+// Bd[ci][k Co + co] = W[ci][co][k]
+__global__ void convt_taps_data(const bf16* __restrict__ W, int Ci, int Co, bf16* __restrict__ Bd) {
+  const size_t n = (size_t)Ci * Co * 4;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % 4), co = (int)((idx / 4) % Co), ci = (int)(idx / ((size_t)4 * Co));
+    Bd[((size_t)ci * 4 + k) * Co + co] = W[idx];
+  }
+}
+
+// uK[ci][b Ti + i] = u[b][ci][i]
+__global__ void convt_u_kmajor(const bf16* __restrict__ u, int B, int Ci, int Ti, bf16* __restrict__ uK) {
+  const size_t n = (size_t)B * Ci * Ti;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % Ti), ci = (int)((idx / Ti) % Ci), b = (int)(idx / ((size_t)Ti * Ci));
+    uK[((size_t)ci * B + b) * Ti + i] = u[idx];
+  }
+}
+
+// dvK[k][co][b Ti + i] = bf16(dv[b][co][2i - 1 + k]), zero where the time is outside [0, To)
+__global__ void convt_dv_taps(const float* __restrict__ dv, int B, int Co, int Ti, bf16* __restrict__ dvK) {
+  const int To = 2 * Ti;
+  const size_t n = (size_t)B * Co * Ti;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx % Ti), co = (int)((idx / Ti) % Co), b = (int)(idx / ((size_t)Ti * Co));
+    const float* row = dv + ((size_t)b * Co + co) * To;
+    const size_t o = ((size_t)co * B + b) * Ti + i;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int t = 2 * i - 1 + k;
+      dvK[(size_t)k * Co * B * Ti + o] = __float2bfloat16((t >= 0 && t < To) ? row[t] : 0.f);
+    }
+  }
+}
+
+// dW[ci][co][k] = sum_z part[k][z][ci][co] (fixed order)
+__global__ void convt_dw_reduce(const float* __restrict__ part, int S, int Ci, int Co, float* __restrict__ dW) {
+  const size_t n = (size_t)Ci * Co * 4;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(idx % 4), co = (int)((idx / 4) % Co), ci = (int)(idx / ((size_t)4 * Co));
+    const float* p = part + (size_t)k * S * Ci * Co + (size_t)ci * Co + co;
+    float acc = 0.f;
+    for (int z = 0; z < S; ++z) acc += p[(size_t)z * Ci * Co];
+    dW[idx] = acc;
+  }
+}
+
+// db[co] = sum_{b,t} dv[b][co][t]: one block per channel, fixed-order tree
+__global__ void __launch_bounds__(256) convt_bias_grad(const float* __restrict__ dv, int B, int Co, int To,
+                                                       float* __restrict__ db) {
+  __shared__ float red[256];
+  const int co = blockIdx.x;
+  float acc = 0.f;
+  for (int idx = threadIdx.x; idx < B * To; idx += 256) {
+    const int b = idx / To, t = idx % To;
+    acc += dv[((size_t)b * Co + co) * To + t];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[co] = red[0];
+}
+
+// round FP32 values to BF16 precision in place (the CUDA-core gradient path
+// reads dv at the precision the tensor-core path reads it)
+__global__ void round_bf16_inplace(float* __restrict__ x, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] = __bfloat162float(__float2bfloat16(x[i]));
+}
+
+// du rows (b, i), 32 consecutive ci: gu[b][ci][i] (channel-major FP32)
+struct DuEpi {
+  float* du; int T, Ci;
+  __device__ __forceinline__ void operator()(int r, int n, const uint32_t* acc) const {
+    const int b = r / T, i = r % T;
+    const size_t o = ((size_t)b * Ci + n) * T + i;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) du[o + (size_t)j * T] = __uint_as_float(acc[j]);
+  }
+};
+
+// partial dW_k rows ci, 32 consecutive co: part[z][ci][co] for K part z = blockIdx.z
+struct PartEpi {
+  float* part; int Ci, Co;
+  __device__ __forceinline__ void operator()(int r, int n, const uint32_t* acc) const {
+    float4* dst = reinterpret_cast<float4*>(part + ((size_t)blockIdx.z * Ci + r) * Co + n);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      dst[q] = make_float4(__uint_as_float(acc[4 * q]), __uint_as_float(acc[4 * q + 1]), __uint_as_float(acc[4 * q + 2]),
+                           __uint_as_float(acc[4 * q + 3]));
+  }
+};
+
+// 4-D tensor map of a BF16 [P][B][T][C] array for 128-row tiles of (b, t) pairs
+int tmap_pbtc(CUtensorMap* map, const bf16* base, int P, int B, int T, int C) {
+  static EncodeTiledFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled is not available");
+    encode = reinterpret_cast<EncodeTiledFn>(fn);
+  }
+  if (!((T >= tcg::BM && T % tcg::BM == 0) || (T < tcg::BM && tcg::BM % T == 0)))
+    return sfail(DGSEM_EINVAL, "time length %d neither divides nor is a multiple of 128", T);
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)T, (cuuint64_t)B, (cuuint64_t)P};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)T * C * 2, (cuuint64_t)B * T * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)tcg::BK, (cuuint32_t)std::min(T, tcg::BM),
+                             (cuuint32_t)std::max(1, tcg::BM / T), 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(base), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return sfail(DGSEM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return DGSEM_OK;
+}
+
+// K parts of the weight-gradient products: the largest divisor of the k-tile
+// count that keeps the grid within about one wave
+int dw_parts(int tiles, int ktiles) {
+  int best = 1;
+  for (int s = 1; s <= ktiles && s <= 64; ++s)
+    if (ktiles % s == 0 && tiles * s <= 160) best = s;
+  return best;
+}
+
+// ---------------------------------------------------------------------------
 // element-wise and small kernels
 // ---------------------------------------------------------------------------
 __global__ void to_bf16(const float* __restrict__ x, bf16* __restrict__ y, size_t n) {
@@ -348,16 +508,6 @@ __global__ void convt_bwd_weight(const bf16* __restrict__ u, const float* __rest
   }
 }
 
-// db[co] = sum_{b, t} dv[b][co][t]
-__global__ void convt_bwd_bias(const float* __restrict__ dv, int B, int Co, int To, float* __restrict__ db) {
-  const int co = blockIdx.x * blockDim.x + threadIdx.x;
-  if (co >= Co) return;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b)
-    for (int t = 0; t < To; ++t) s += dv[((size_t)b * Co + co) * To + t];
-  db[co] = s;
-}
-
 // dv = du * gelu'(v)
 __global__ void act_bwd(const float* __restrict__ du, const float* __restrict__ v, float* __restrict__ dv, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -422,6 +572,11 @@ struct srg_net {
   // layers whose channel counts are not multiples of 64 run on the CUDA cores
   bf16 *utm = nullptr, *Bev = nullptr;
   std::vector<int> conv_tc;
+  // their gradients: parity-split dv, K-contiguous u and tap-shifted dv, and
+  // the partial sums of the split weight-gradient products
+  bf16 *dvp = nullptr, *uK = nullptr, *dvK = nullptr;
+  float* part = nullptr;
+  size_t part_n = 0;
   int* d_err = nullptr;               // set by a tensor-core product whose bounded wait gave up
   double* d_loss = nullptr;
   long long t = 0;                    // Adam step counter
@@ -475,6 +630,52 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
       S_TRY(cudaGetLastError());
     }
   }
+  return DGSEM_OK;
+}
+
+// data and weight gradients of transposed convolution j on the tensor cores
+// (dv in n->gv; du into n->gu, dW into the gradient vector)
+int convt_backward_tc(srg_net* n, int j, int B, cudaStream_t s) {
+  const srg_config& c = n->cfg;
+  const int L = c.n_hidden;
+  const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j), to = 2 * ti;
+  int rc;
+  // du: rows (b, i), N = Ci, K = 4 Co from the parity-split time-major dv
+  convt_dv_split<<<dim3((to + 63) / 64, (co + 31) / 32, B), dim3(32, 8), 0, s>>>(n->gv, B, co, ti, n->dvp);
+  convt_taps_data<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev);
+  S_TRY(cudaGetLastError());
+  {
+    CUtensorMap ta, tb;
+    if ((rc = tmap_pbtc(&ta, n->dvp, 2, B, ti, co)) || (rc = tmap_bf16(&tb, n->Bev, ci, 4 * co, 4 * co, 64))) return rc;
+    auto kern = tcg::gemm_kernel<64, 6, DuEpi, tcg::SegA>;
+    constexpr int smem = tcg::Geo<64, 6>::SMEM;
+    S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int M = B * ti;
+    const tcg::SegA al{co / tcg::BK, ti, {-1, 0, 0, 1}, {1, 0, 1, 0}};
+    kern<<<dim3(ci / 64, M / tcg::BM, 1), tcg::THREADS, smem, s>>>(ta, tb, M, 4 * co, DuEpi{n->gu, ti, ci}, n->d_err, al);
+    S_TRY(cudaGetLastError());
+  }
+  // dW_k: rows ci, N = Co, K = (b, i), split into S parts
+  convt_u_kmajor<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], B, ci, ti, n->uK);
+  convt_dv_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gv, B, co, ti, n->dvK);
+  S_TRY(cudaGetLastError());
+  const int K = B * ti;
+  const int mt = (ci + tcg::BM - 1) / tcg::BM;
+  const int S = dw_parts(mt * (co / 64), K / tcg::BK);
+  if ((size_t)4 * S * ci * co > n->part_n) return sfail(DGSEM_EINVAL, "weight-gradient partial buffer too small");
+  for (int k = 0; k < 4; ++k) {
+    CUtensorMap ta, tb;
+    const bf16* dk = n->dvK + (size_t)k * co * K;
+    if ((rc = tmap_bf16(&ta, n->uK, ci, K, K, tcg::BM)) || (rc = tmap_bf16(&tb, dk, co, K, K, 64))) return rc;
+    auto kern = tcg::gemm_kernel<64, 6, PartEpi, tcg::DenseA>;
+    constexpr int smem = tcg::Geo<64, 6>::SMEM;
+    S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    kern<<<dim3(co / 64, mt, S), tcg::THREADS, smem, s>>>(ta, tb, ci, K, PartEpi{n->part + (size_t)k * S * ci * co, ci, co},
+                                                         n->d_err, tcg::DenseA());
+    S_TRY(cudaGetLastError());
+  }
+  convt_dw_reduce<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->part, S, ci, co, n->G + n->offW[L + 1 + j]);
+  S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
 
@@ -588,7 +789,7 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
   S_TRY(cudaMemset(n->d_err, 0, sizeof(int)));
   // which transposed convolutions take the tensor-core path (channel counts
   // multiples of 64; time lengths that tile 128 rows), and their scratch
-  size_t utm_n = 0, bev_n = 0;
+  size_t utm_n = 0, bev_n = 0, dvp_n = 0, uk_n = 0, dvk_n = 0;
   n->conv_tc.assign(c.n_conv, 0);
   for (int j = 0; j < c.n_conv; ++j) {
     const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
@@ -597,9 +798,16 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
       n->conv_tc[j] = 1;
       utm_n = std::max(utm_n, B * ci * ti);
       bev_n = std::max(bev_n, (size_t)4 * ci * co);
+      dvp_n = std::max(dvp_n, B * 2 * ti * co);
+      uk_n = std::max(uk_n, B * ci * ti);
+      dvk_n = std::max(dvk_n, (size_t)4 * co * B * ti);
+      // the weight-gradient parts for the smallest batch (64) the network takes, the most parts
+      n->part_n = std::max(n->part_n, (size_t)4 * 64 * ci * co);
     }
   }
-  if (utm_n && ((rc = A((void**)&n->utm, utm_n * 2)) || (rc = A((void**)&n->Bev, bev_n * 2)))) {
+  if (utm_n && ((rc = A((void**)&n->utm, utm_n * 2)) || (rc = A((void**)&n->Bev, bev_n * 2)) ||
+                (rc = A((void**)&n->dvp, dvp_n * 2)) || (rc = A((void**)&n->uK, uk_n * 2)) ||
+                (rc = A((void**)&n->dvK, dvk_n * 2)) || (rc = A((void**)&n->part, n->part_n * 4)))) {
     srg_destroy(n);
     return rc;
   }
@@ -663,9 +871,16 @@ int srg_backward(srg_net* n, const float* x, const float* target, int B, double*
   // transposed convolutions, last to first: gv holds dv_j, gu receives du_j
   for (int j = J - 1; j >= 0; --j) {
     const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
-    convt_bwd_weight<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->gv, B, ci, co, ti, n->G + n->offW[L + 1 + j]);
-    convt_bwd_bias<<<(co + 127) / 128, 128, 0, s>>>(n->gv, B, co, 2 * ti, n->G + n->offB[L + 1 + j]);
-    convt_bwd_data<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gv, n->Pb + n->offW[L + 1 + j], B, ci, co, ti, n->gu);
+    // the bias gradient from dv itself; the products read dv rounded to BF16
+    convt_bias_grad<<<co, 256, 0, s>>>(n->gv, B, co, 2 * ti, n->G + n->offB[L + 1 + j]);
+    S_TRY(cudaGetLastError());
+    if (n->conv_tc[j]) {
+      if ((rc = convt_backward_tc(n, j, B, s))) return rc;
+    } else {
+      round_bf16_inplace<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gv, (size_t)B * co * 2 * ti);
+      convt_bwd_weight<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->gv, B, ci, co, ti, n->G + n->offW[L + 1 + j]);
+      convt_bwd_data<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gv, n->Pb + n->offW[L + 1 + j], B, ci, co, ti, n->gu);
+    }
     S_TRY(cudaGetLastError());
     if (j > 0) {
       act_bwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gu, n->v[j - 1], n->gv, (size_t)B * ci * ti);

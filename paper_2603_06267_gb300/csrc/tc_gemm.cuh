@@ -71,6 +71,15 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                            int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Where the 128 x 64 A tile of k-tile kt and row tile mt comes from.
 // DenseA: rows mt*128 .. of a 2-D [M][K] matrix.
 struct DenseA {
@@ -90,6 +99,21 @@ struct ShiftA {
     const int sh = second ? sh1 : sh0;
     const int r0 = mt * BM;
     tma_load_3d(dst, map, bar, c0, (r0 % T) + sh, r0 / T);
+  }
+};
+
+// SegA: rows (b, t) of a 4-D [P][B][T][C] array, t fastest (T divides 128
+// or 128 divides T); the K axis is nseg segments of C channels each, segment
+// g read at time t + sh[g] from plane pl[g].  Rows shifted past either end of
+// the time axis read zeros.
+struct SegA {
+  int kseg, T;
+  int sh[4], pl[4];
+  __device__ __forceinline__ void operator()(void* dst, const CUtensorMap* map, uint64_t* bar, int kt, int mt) const {
+    const int g = kt / kseg;
+    const int c0 = (kt - g * kseg) * BK;
+    const int r0 = mt * BM;
+    tma_load_4d(dst, map, bar, c0, (r0 % T) + sh[g], r0 / T, pl[g]);
   }
 };
 
@@ -181,7 +205,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int KT = K / BK;
+  // split K: CTA z of gridDim.z takes k-tiles kt0 .. kt0 + KT - 1 (the
+  // epilogue sees blockIdx.z and writes that part's partial sum)
+  const int KT = K / BK / gridDim.z;
+  const int kt0 = blockIdx.z * KT;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -215,8 +242,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       unsigned char* st = base + s * G::STAGE;
       mbar_expect_tx(&full[s], (uint32_t)G::STAGE);
-      aload(st, &tmA, &full[s], kt, blockIdx.y);
-      tma_load_2d(st + G::A_BYTES, &tmB, &full[s], kt * BK, n0);
+      aload(st, &tmA, &full[s], kt0 + kt, blockIdx.y);
+      tma_load_2d(st + G::A_BYTES, &tmB, &full[s], (kt0 + kt) * BK, n0);
       issued = kt + 1;
     }
     // every fill issued has landed before the CTA can leave
