@@ -40,11 +40,12 @@ import workloads as W  # noqa: E402
 # (workload, precision, kernel kind); see profiles/.  None: not measured for
 # the current kernel.
 NCU_TRAFFIC_PER_LAUNCH = {
-    # profiles/vol_kernel_f32_N6_config3.md: 1.347 GB per launch at batch 1 on the
-    # config-3 mesh (secondary box, register-column tile variant); traffic scales
-    # with the number of patterns (independent state)
-    ("config4_batched", "fp32", "vol_secondary"): 1.3474e9 * 64,
-    ("config3_array32", "fp32", "vol_secondary"): 1.3474e9,
+    # profiles/vol_kernel_f32_N6_tma_store_config3.md (variant 6, the one the
+    # autotuner picks): 706.8 MB read + 640.4 MB written per launch at batch 1 on
+    # the config-3 mesh (secondary box); the traffic scales with the number of
+    # patterns (each has its own state, the operator lives in the parameter block)
+    ("config4_batched", "fp32", "vol_secondary"): 1.3472e9 * 64,
+    ("config3_array32", "fp32", "vol_secondary"): 1.3472e9,
 }
 
 
