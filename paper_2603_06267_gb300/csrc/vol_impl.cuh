@@ -151,7 +151,8 @@ constexpr size_t r128(size_t b) { return (b + 127) / 128 * 128; }
 // registers once per layer, and the z stencils of its planes and the z carry
 // read that copy instead of shared memory (FP32 only); MINB: CTAs per SM;
 // RING 3: the p layers in a three-deep ring (v stays two deep), so a p load
-// has two layers of work to hide behind
+// has two layers of work to hide behind; RING 4: the v planes three deep (p
+// two), so the v fill of a layer is issued two layers ahead
 // TS: the layer's new v and p_next go to shared memory (v in place in its
 // stage, p_next into one of two output tiles) and leave by TMA tensor stores,
 // one per array and layer, instead of per-thread global stores
@@ -164,7 +165,7 @@ template <typename T, int N, int V> struct TileShape {
                   (sizeof(T) == 8 && N == 4) ? 2 : ((N <= 2) ? 16 / N : ((N <= 4) ? 4 : (N <= 7 ? 2 : 1))), 1>;
 };
 template <typename T, int N> struct NumShapes {
-  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? (N == 6 ? 9 : 6) : 4) : 1;
+  static constexpr int value = (N == 4 || N == 6) ? (sizeof(T) == 4 ? (N == 6 ? 10 : 6) : 4) : 1;
 };
 // FP32 N=4: 512 / 512 / 512 / 256 threads, register-column 512 / 256 (two CTAs
 // per SM); FP64 N=4: 256 / 256 / 128 / 512
@@ -191,6 +192,8 @@ template <> struct TileShape<float, 6, 6> { using S = Shape<16, 2, 2, 1, 1, 3>; 
 // FP32 N=6 with TMA stores of the outputs: register column, 384 / 576 threads
 template <> struct TileShape<float, 6, 7> { using S = Shape<16, 2, 2, 1, 1, 0, 1>; };
 template <> struct TileShape<float, 6, 8> { using S = Shape<16, 2, 3, 1, 1, 0, 1>; };
+// FP32 N=6, register column, v planes three deep (p two deep): 201 KB
+template <> struct TileShape<float, 6, 9> { using S = Shape<16, 2, 2, 1, 1, 4>; };
 template <> struct TileShape<double, 6, 0> { using S = Shape<16, 2, 1>; };
 template <> struct TileShape<double, 6, 1> { using S = Shape<16, 1, 1>; };
 template <> struct TileShape<double, 6, 2> { using S = Shape<8, 4, 1>; };
@@ -215,12 +218,13 @@ struct Geo {
   static constexpr size_t V_BYTES_RAW = sizeof(T) * (size_t)N * VPLANE;
   static constexpr size_t PB = r128(P_BYTES), VBR = r128(V_BYTES_RAW);
   static constexpr int PDEPTH = RING == 3 ? 3 : 2;
-  static constexpr bool VTMA = sizeof(T) == 4 && PDEPTH * PB + 2 * VBR + 128 <= 227 * 1024;
+  static constexpr int VDEPTH = RING == 4 ? 3 : 2;
+  static constexpr bool VTMA = sizeof(T) == 4 && PDEPTH * PB + VDEPTH * VBR + 128 <= 227 * 1024;
   static constexpr size_t V_BYTES = VTMA ? V_BYTES_RAW : 0;
   static constexpr size_t VB = r128(V_BYTES);
   // ring depths: p layers (PST) and v planes (VST, 0 when v is not staged)
-  static constexpr int PST = (PDEPTH * PB + (VTMA ? 2 * VB : 0) + 128 <= 227 * 1024) ? PDEPTH : 1;
-  static constexpr int VST = VTMA ? 2 : 0;
+  static constexpr int PST = (PDEPTH * PB + (VTMA ? VDEPTH * VB : 0) + 128 <= 227 * 1024) ? PDEPTH : 1;
+  static constexpr int VST = VTMA ? VDEPTH : 0;
   static constexpr size_t VBASE = PST * PB;
   // p_next output tiles (two, alternating by layer) of the TMA-store form
   static constexpr size_t OBASE = VBASE + VST * VB;
@@ -239,6 +243,7 @@ struct Geo {
   static_assert(BX <= 256 && BY <= 256 && BZ <= 256 && BXV <= 256 && TYR <= 256, "TMA box dimension above 256");
   static_assert(SMEM <= 227 * 1024, "tile exceeds shared memory");
   static_assert(!TS || (VTMA && PST == 2 && VST == 2), "TMA stores need the staged v ring");
+  static_assert(PST + VST <= 8, "the stage barriers and counters share 128 bytes");
   static_assert(!TS || (TXE * N * sizeof(T)) % 16 == 0, "TMA store box row not a multiple of 16 B");
 };
 
@@ -534,7 +539,7 @@ __device__ __forceinline__ int tile_row(int ty) {
 template <typename T, int N, int TXE, int TYE, int PG, bool ZR, int MINB, bool OPEN, int RING, bool TS>
 __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __grid_constant__ VolArgs<T, N> A) {
   using G = Geo<T, N, TXE, TYE, PG, RING, TS>;
-  static_assert(RING == 0 || G::VTMA, "the three-deep p ring is for kernels that stage v");
+  static_assert(RING == 0 || G::VTMA, "the three-deep rings are for kernels that stage v");
   static_assert(!ZR || sizeof(T) == 4, "register columns: FP32 only");
   constexpr int BX = G::BX, PLANE = G::PLANE, TYR = G::TYR, NAL = G::NAL, VS = G::VS, VG = G::VG;
   constexpr int BXV = G::BXV, VPLANE = G::VPLANE, VV = G::VV;
@@ -1140,6 +1145,7 @@ cudaError_t launch_n(const VolSpec& s, int batch, cudaStream_t st) {
       case 6: if constexpr (NumShapes<T, N>::value > 6) return launch_v<T, N, 6, OPEN>(s, batch, st); break;
       case 7: if constexpr (NumShapes<T, N>::value > 7) return launch_v<T, N, 7, OPEN>(s, batch, st); break;
       case 8: if constexpr (NumShapes<T, N>::value > 8) return launch_v<T, N, 8, OPEN>(s, batch, st); break;
+      case 9: if constexpr (NumShapes<T, N>::value > 9) return launch_v<T, N, 9, OPEN>(s, batch, st); break;
       default: break;
     }
     return cudaErrorInvalidValue;
@@ -1176,7 +1182,8 @@ int box_n(int tile, unsigned box[3], unsigned vbox[3]) {
       case 5: if constexpr (NumShapes<T, N>::value > 5) box_v<T, N, 5>(box, vbox); break;
       case 6: if constexpr (NumShapes<T, N>::value > 6) box_v<T, N, 6>(box, vbox); break;
       case 7: if constexpr (NumShapes<T, N>::value > 7) box_v<T, N, 7>(box, vbox); break;
-      default: if constexpr (NumShapes<T, N>::value > 8) box_v<T, N, 8>(box, vbox); break;
+      case 8: if constexpr (NumShapes<T, N>::value > 8) box_v<T, N, 8>(box, vbox); break;
+      default: if constexpr (NumShapes<T, N>::value > 9) box_v<T, N, 9>(box, vbox); break;
     }
   } else {
     box_v<T, N, 0>(box, vbox);
