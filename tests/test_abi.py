@@ -75,6 +75,27 @@ def test_null_context_calls_fail_cleanly(lib):
     assert b"NULL" in lib.dgsem_last_error()
 
 
+def test_new_entry_points_reject_bad_arguments_before_cuda(lib):
+    """The rate probes, the layer setter, the launch-shape getter and the PMUT
+    state getter check their arguments before any CUDA call."""
+    from ctypes import byref, c_double
+    from paper_2603_06267_gb300 import dgsem
+    from paper_2603_06267_gb300 import surrogate as S
+    S.load()
+    v = c_double(-1.0)
+    assert lib.dgsem_measure_peak(7, byref(v), None) == dgsem.DGSEM_EINVAL
+    assert lib.dgsem_measure_peak(0, None, None) == dgsem.DGSEM_EINVAL
+    assert lib.srg_gemm_bench(512, 32, 2048, 1, byref(v), None) == dgsem.DGSEM_EINVAL
+    assert lib.srg_gemm_bench(512, 2048, 2048, 0, byref(v), None) == dgsem.DGSEM_EINVAL
+    assert lib.srg_gemm_bench(512, 2048, 2048, 1, None, None) == dgsem.DGSEM_EINVAL
+    layers = np.zeros(2, dtype=np.int32)
+    shape = np.zeros(8, dtype=np.int32)
+    assert lib.dgsem_set_layers(None, layers.ctypes.data) == dgsem.DGSEM_EINVAL
+    assert lib.dgsem_vol_launch(None, 0, shape.ctypes.data) == dgsem.DGSEM_EINVAL
+    assert lib.dgsem_get_pmut_state(None, None, None, None, 0) == dgsem.DGSEM_EINVAL
+    assert lib.dgsem_sample_noalloc(None, 1, None, None, 0, None) == dgsem.DGSEM_EINVAL
+
+
 def test_surrogate_symbols_exported(lib):
     src = open(os.path.join(ROOT, "include", "surrogate.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)

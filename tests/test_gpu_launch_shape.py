@@ -92,3 +92,50 @@ def test_automatic_shape_takes_every_layer_when_the_grid_is_full(case):
         assert sh["layers_per_cta"] == layers
         assert sh["nchunks"] == (nz + layers - 1) // layers
     sol.close()
+
+
+def test_layer_setter_and_launch_report_edge_cases():
+    """Negative layer counts are refused, counts above a box's layers are
+    clamped to them, 0 restores the automatic shape, and the launch report
+    is refused before the first run."""
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=3, nx_s=2, nz_s=5, n_pmut_side=2, nsteps=6, batch=2, steer=True)
+    sol = dgsem.Solver(w)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_vol_launch(sol.ctx, 0)
+    assert e.value.code == dgsem.DGSEM_ESTATE
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_set_layers(sol.ctx, [-1, 0])
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    ref = sol.run(precision=1)
+    dgsem.dgsem_set_layers(sol.ctx, [1000, 1000])
+    tr = sol.run(precision=1)
+    for d in range(2):
+        sh = dgsem.dgsem_vol_launch(sol.ctx, d)
+        assert sh["layers_per_cta"] == w.domains[d].nelem[2] and sh["nchunks"] == 1
+    # a different launch shape changes the result by rounding at most
+    assert rel_l2(tr, ref) < 1e-6
+    dgsem.dgsem_set_layers(sol.ctx, [1, 2])
+    tr2 = sol.run(precision=1)
+    assert dgsem.dgsem_vol_launch(sol.ctx, 1)["layers_per_cta"] == 2
+    assert rel_l2(tr2, ref) < 1e-6
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_vol_launch(sol.ctx, 2)
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    sol.close()
+
+
+def test_pmut_state_getter_refusals():
+    from paper_2603_06267_gb300 import dgsem
+    w = W.small_two_domain(nx_p=4, nz_p=2, nx_s=2, nz_s=3, n_pmut_side=2, nsteps=4)
+    sol = dgsem.Solver(w)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_get_pmut_state(sol.ctx, 1, w.pmuts.n_pmut, w.pmuts.n_modes)
+    assert e.value.code == dgsem.DGSEM_ESTATE
+    sol.run(precision=0)
+    with pytest.raises(dgsem.DgsemError) as e:
+        dgsem.dgsem_get_pmut_state(sol.ctx, 1, w.pmuts.n_pmut, w.pmuts.n_modes - 1)
+    assert e.value.code == dgsem.DGSEM_EINVAL
+    q, qd, qdd = dgsem.dgsem_get_pmut_state(sol.ctx, 1, w.pmuts.n_pmut, w.pmuts.n_modes)
+    assert np.all(np.isfinite(q)) and np.abs(qdd).max() > 0
+    sol.close()
