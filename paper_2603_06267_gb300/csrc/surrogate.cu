@@ -193,6 +193,41 @@ __global__ void convt_taps(const bf16* __restrict__ W, int Ci, int Co, bf16* __r
   }
 }
 
+// Both parities in one product: K = 3 Ci over the input at times m - 1, m,
+// m + 1, N = 2 Co with B3[co] = [W_3 | W_1 | 0] (even output) and
+// B3[Co + co] = [0 | W_2 | W_0] (odd); the accumulator's column halves hold
+// the even and odd samples of a channel, written as adjacent pairs.
+__global__ void convt_taps3(const bf16* __restrict__ W, int Ci, int Co, bf16* __restrict__ B3) {
+  const size_t n = (size_t)Ci * Co;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(idx % Co), ci = (int)(idx / Co);
+    const bf16* w = W + ((size_t)ci * Co + co) * 4;
+    bf16* ev = B3 + (size_t)co * 3 * Ci;
+    bf16* od = B3 + (size_t)(Co + co) * 3 * Ci;
+    ev[ci] = w[3]; ev[Ci + ci] = w[1]; ev[2 * Ci + ci] = zero;
+    od[ci] = zero; od[Ci + ci] = w[2]; od[2 * Ci + ci] = w[0];
+  }
+}
+
+// rows (b, m), channels n .. n + 31: v[b][co][2m], v[b][co][2m + 1] (+ bias)
+// and u_next = bf16(gelu(v)) as adjacent pairs (channel-major)
+struct PairConvEpi {
+  static constexpr bool paired = true;
+  float* v; bf16* un; const float* bias; int T, Co;
+  __device__ __forceinline__ void operator()(int r, int n, const uint32_t* ev, const uint32_t* od) const {
+    const int b = r / T, m = r % T, To = 2 * T;
+    const size_t o = ((size_t)b * Co + n) * To + 2 * m;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float bj = bias[n + j];
+      const float e = __uint_as_float(ev[j]) + bj, d = __uint_as_float(od[j]) + bj;
+      *reinterpret_cast<float2*>(v + o + (size_t)j * To) = make_float2(e, d);
+      if (un) *reinterpret_cast<__nv_bfloat162*>(un + o + (size_t)j * To) = __floats2bfloat162_rn(gelu_f(e), gelu_f(d));
+    }
+  }
+};
+
 // v[b][co][2m + par] = acc + bias[co]; u_next = bf16(gelu(v)) (channel-major)
 struct ConvEpi {
   float* v; bf16* un; const float* bias; int T, Co, par;
@@ -329,15 +364,18 @@ __global__ void convt_dw_reduce(const float* __restrict__ part, int S, int Ci, i
   }
 }
 
-// db[co] = sum_{b,t} dv[b][co][t]: one block per channel, fixed-order tree
-__global__ void __launch_bounds__(256) convt_bias_grad(const float* __restrict__ dv, int B, int Co, int To,
-                                                       float* __restrict__ db) {
+// db[co] = sum_{b,t} dv[b][co][t] in a fixed order: block (co, c) sums the
+// rows of batch members c*BIAS_BPB .. (c+1)*BIAS_BPB - 1 into part[co][c]
+// (tree over its threads), then convt_bias_sum adds the parts in order
+constexpr int BIAS_BPB = 4;
+__global__ void __launch_bounds__(256) convt_bias_part(const float* __restrict__ dv, int B, int Co, int To,
+                                                       float* __restrict__ part) {
   __shared__ float red[256];
-  const int co = blockIdx.x;
+  const int co = blockIdx.x, c = blockIdx.y, nch = gridDim.y;
   float acc = 0.f;
-  for (int idx = threadIdx.x; idx < B * To; idx += 256) {
-    const int b = idx / To, t = idx % To;
-    acc += dv[((size_t)b * Co + co) * To + t];
+  for (int b = c * BIAS_BPB; b < min(B, (c + 1) * BIAS_BPB); ++b) {
+    const float* row = dv + ((size_t)b * Co + co) * To;
+    for (int t = threadIdx.x; t < To; t += 256) acc += row[t];
   }
   red[threadIdx.x] = acc;
   __syncthreads();
@@ -345,7 +383,15 @@ __global__ void __launch_bounds__(256) convt_bias_grad(const float* __restrict__
     if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
     __syncthreads();
   }
-  if (threadIdx.x == 0) db[co] = red[0];
+  if (threadIdx.x == 0) part[(size_t)co * nch + c] = red[0];
+}
+
+__global__ void convt_bias_sum(const float* __restrict__ part, int Co, int nch, float* __restrict__ db) {
+  const int co = blockIdx.x * blockDim.x + threadIdx.x;
+  if (co >= Co) return;
+  float acc = 0.f;
+  for (int c = 0; c < nch; ++c) acc += part[(size_t)co * nch + c];
+  db[co] = acc;
 }
 
 // round FP32 values to BF16 precision in place (the CUDA-core gradient path
@@ -410,6 +456,32 @@ int dw_parts(int tiles, int ktiles) {
   for (int s = 1; s <= ktiles && s <= 64; ++s)
     if (ktiles % s == 0 && tiles * s <= 160) best = s;
   return best;
+}
+
+// a transposed convolution, both parities in one product (see convt_taps3):
+// u_tm [B][T][Ci] time-major, B3 [2 Co][3 Ci]; v and u_next channel-major
+template <int BN, int STAGES>
+int convt_pair_launch(const bf16* u_tm, int B, int T, int Ci, const bf16* B3, int Co, const float* bias, float* v,
+                      bf16* un, int* err, cudaStream_t s) {
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = tmap_pbtc(&ta, u_tm, 1, B, T, Ci)) || (rc = tmap_bf16(&tb, B3, 2 * Co, 3 * Ci, 3 * Ci, BN))) return rc;
+  auto kern = tcg::gemm_kernel<BN, STAGES, PairConvEpi, tcg::SegA>;
+  constexpr int smem = tcg::Geo<BN, STAGES>::SMEM;
+  S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  const int M = B * T;
+  const tcg::SegA al{Ci / tcg::BK, T, {-1, 0, 1, 0}, {0, 0, 0, 0}};
+  kern<<<dim3(1, M / tcg::BM, 1), tcg::THREADS, smem, s>>>(ta, tb, M, 3 * Ci, PairConvEpi{v, un, bias, T, Co}, err, al);
+  S_TRY(cudaGetLastError());
+  return DGSEM_OK;
+}
+
+int convt_pair(const bf16* u_tm, int B, int T, int Ci, const bf16* B3, int Co, const float* bias, float* v, bf16* un,
+               int* err, cudaStream_t s) {
+  if (Ci % tcg::BK) return sfail(DGSEM_EINVAL, "convolution input channels %d not tileable", Ci);
+  if (Co == 64) return convt_pair_launch<128, 6>(u_tm, B, T, Ci, B3, Co, bias, v, un, err, s);
+  if (Co == 128) return convt_pair_launch<256, 4>(u_tm, B, T, Ci, B3, Co, bias, v, un, err, s);
+  return sfail(DGSEM_EINVAL, "paired convolution product needs 64 or 128 output channels, not %d", Co);
 }
 
 // ---------------------------------------------------------------------------
@@ -577,6 +649,7 @@ struct srg_net {
   bf16 *dvp = nullptr, *uK = nullptr, *dvK = nullptr;
   float* part = nullptr;
   size_t part_n = 0;
+  float* bias_part = nullptr;         // [Co][batch / 4] partial sums of the bias gradients
   int* d_err = nullptr;               // set by a tensor-core product whose bounded wait gave up
   double* d_loss = nullptr;
   long long t = 0;                    // Adam step counter
@@ -618,12 +691,22 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
     if (n->conv_tc[j]) {
       // time-major copy of the input, the tap pairs, then the two parities
       if ((rc = transpose(n->u[j], ci, ti, n->utm, s, B))) return rc;
-      convt_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev, n->Bev + (size_t)co * 2 * ci);
-      S_TRY(cudaGetLastError());
-      for (int par = 0; par < 2; ++par)
-        if ((rc = convt_parity(n->utm, B, ti, ci, n->Bev + (size_t)par * co * 2 * ci, co, par, n->P + n->offB[L + 1 + j],
-                               n->v[j], last ? nullptr : n->u[j + 1], n->d_err, s)))
+      if (co == 64 || co == 128) {
+        // both output parities in one product, written as adjacent samples
+        convt_taps3<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev);
+        S_TRY(cudaGetLastError());
+        if ((rc = convt_pair(n->utm, B, ti, ci, n->Bev, co, n->P + n->offB[L + 1 + j], n->v[j],
+                             last ? nullptr : n->u[j + 1], n->d_err, s)))
           return rc;
+      } else {
+        convt_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev,
+                                                    n->Bev + (size_t)co * 2 * ci);
+        S_TRY(cudaGetLastError());
+        for (int par = 0; par < 2; ++par)
+          if ((rc = convt_parity(n->utm, B, ti, ci, n->Bev + (size_t)par * co * 2 * ci, co, par,
+                                 n->P + n->offB[L + 1 + j], n->v[j], last ? nullptr : n->u[j + 1], n->d_err, s)))
+            return rc;
+      }
     } else {
       convt_fwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->Pb + n->offW[L + 1 + j], n->P + n->offB[L + 1 + j], B,
                                                  ci, co, ti, n->v[j], last ? nullptr : n->u[j + 1], 1);
@@ -797,7 +880,7 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
     if (ci % 64 == 0 && co % 64 == 0 && tiles_t && ((size_t)max_batch * ti) % 128 == 0) {
       n->conv_tc[j] = 1;
       utm_n = std::max(utm_n, B * ci * ti);
-      bev_n = std::max(bev_n, (size_t)4 * ci * co);
+      bev_n = std::max(bev_n, (size_t)6 * ci * co);
       dvp_n = std::max(dvp_n, B * 2 * ti * co);
       uk_n = std::max(uk_n, B * ci * ti);
       dvk_n = std::max(dvk_n, (size_t)4 * co * B * ti);
@@ -810,6 +893,14 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
                 (rc = A((void**)&n->dvK, dvk_n * 2)) || (rc = A((void**)&n->part, n->part_n * 4)))) {
     srg_destroy(n);
     return rc;
+  }
+  {
+    int maxco = 0;
+    for (int j = 0; j < c.n_conv; ++j) maxco = std::max(maxco, c.conv_ch[j]);
+    if ((rc = A((void**)&n->bias_part, (size_t)maxco * ((max_batch + BIAS_BPB - 1) / BIAS_BPB) * 4))) {
+      srg_destroy(n);
+      return rc;
+    }
   }
   if ((rc = srg_set_params(n, h.data(), o))) { srg_destroy(n); return rc; }
   S_TRY(cudaMemset(n->M1, 0, o * 4));
@@ -872,7 +963,11 @@ int srg_backward(srg_net* n, const float* x, const float* target, int B, double*
   for (int j = J - 1; j >= 0; --j) {
     const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
     // the bias gradient from dv itself; the products read dv rounded to BF16
-    convt_bias_grad<<<co, 256, 0, s>>>(n->gv, B, co, 2 * ti, n->G + n->offB[L + 1 + j]);
+    {
+      const int nch = (B + BIAS_BPB - 1) / BIAS_BPB;
+      convt_bias_part<<<dim3(co, nch), 256, 0, s>>>(n->gv, B, co, 2 * ti, n->bias_part);
+      convt_bias_sum<<<(co + 127) / 128, 128, 0, s>>>(n->bias_part, co, nch, n->G + n->offB[L + 1 + j]);
+    }
     S_TRY(cudaGetLastError());
     if (n->conv_tc[j]) {
       if ((rc = convt_backward_tc(n, j, B, s))) return rc;

@@ -182,6 +182,11 @@ struct Geo {
   static_assert(SMEM <= 227 * 1024, "stages exceed shared memory");
 };
 
+// An epilogue functor with `static constexpr bool paired = true` receives the
+// accumulator columns c and c + BN/2 of a row together.
+template <typename E, typename = void> struct PairedEpilogue { static constexpr bool value = false; };
+template <typename E> struct PairedEpilogue<E, decltype(void(E::paired))> { static constexpr bool value = E::paired; };
+
 // Epilogue of the surrogate's dense layers: + bias[n]; FP32 copy to C (ldc);
 // BF16 copy of gelu(.) (act = 1) or of the value (act = 0) to Cb (ldcb).
 struct Epi {
@@ -274,11 +279,23 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_after_sync();
   if (ready && *reinterpret_cast<volatile int*>(err) == 0) {
     const int row = m0 + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    if constexpr (PairedEpilogue<EpiFn>::value) {
+      // the tile's two column halves belong together (column c and c + BN/2)
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) epi(row, n0 + c0, r);
+      for (int c0 = 0; c0 < BN / 2; c0 += 32) {
+        uint32_t r[32], q[32];
+        tmem_ld32(tl + (uint32_t)c0, r);
+        tmem_ld32(tl + (uint32_t)(c0 + BN / 2), q);
+        if (row < M) epi(row, n0 + c0, r, q);
+      }
+    } else {
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tl + (uint32_t)c0, r);
+        if (row < M) epi(row, n0 + c0, r);
+      }
     }
   }
   fence_before_sync();

@@ -78,19 +78,15 @@ def test_adam_step_matches_reference():
 FULL = dict(d_in=2048, hidden=2048, n_hidden=3, c0=256, t0=32, conv_ch=(128, 128, 64, 64))
 
 
-def test_forward_and_gradients_at_experiment_widths():
-    """The experiment's network (1024 PMUTs x 2 features, three hidden layers
-    of 2048, decoder 2048 -> 256 x 32, four transposed convolutions to 64 x
-    512): forward, loss and every gradient block against the CPU reference
-    at 64 patterns."""
+def _check_widths(widths, seed):
     import torch
     from paper_2603_06267_gb300 import surrogate as S
-    net = S.Surrogate(max_batch=64, seed=11, **FULL)
-    cfg = R.SurrogateConfig(d_in=FULL["d_in"], hidden=FULL["hidden"], n_hidden=FULL["n_hidden"], c0=FULL["c0"],
-                            t0=FULL["t0"], conv_ch=list(FULL["conv_ch"]))
+    net = S.Surrogate(max_batch=64, seed=seed, **widths)
+    cfg = R.SurrogateConfig(d_in=widths["d_in"], hidden=widths["hidden"], n_hidden=widths["n_hidden"],
+                            c0=widths["c0"], t0=widths["t0"], conv_ch=list(widths["conv_ch"]))
     assert net.n == cfg.num_params()
     ref = R.SurrogateRef(cfg, quant=True)
-    rng = np.random.default_rng(12)
+    rng = np.random.default_rng(seed + 1)
     x = rng.normal(size=(64, cfg.d_in)).astype(np.float32)
     t = rng.normal(size=(64, cfg.c_out, cfg.t_out)).astype(np.float32)
     y = torch.zeros((64, cfg.c_out, cfg.t_out), dtype=torch.float32, device="cuda")
@@ -107,6 +103,22 @@ def test_forward_and_gradients_at_experiment_widths():
         assert _rel(g[o:o + n], gr[o:o + n]) < 2e-2, name
         o += n
     net.close()
+
+
+def test_forward_and_gradients_at_experiment_widths():
+    """The experiment's network (1024 PMUTs x 2 features, three hidden layers
+    of 2048, decoder 2048 -> 256 x 32, four transposed convolutions to 64 x
+    512): forward, loss and every gradient block against the CPU reference
+    at 64 patterns.  Every convolution has 64 or 128 output channels and
+    takes both output parities in one tensor-core product."""
+    _check_widths(FULL, 11)
+
+
+def test_convolution_with_192_output_channels():
+    """A convolution with 192 output channels takes the two-product form (one
+    product per output parity) on the tensor cores; the next one, 192 -> 64,
+    the paired form."""
+    _check_widths(dict(d_in=128, hidden=256, n_hidden=1, c0=64, t0=32, conv_ch=(192, 64)), 21)
 
 
 @pytest.mark.parametrize("M,N,K,what", [(512, 2048, 2048, "hidden layer forward / dA"),
