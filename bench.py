@@ -67,6 +67,9 @@ def parse(argv=None):
     ap.add_argument("--tiles", default=None,
                     help="comma-separated volume-kernel tile variant per box, or element-stiffness variant per "
                          "domain on general hexahedra (skips the autotuner)")
+    ap.add_argument("--layers", default=None,
+                    help="comma-separated element layers per CTA of the volume kernel, per box (0 = automatic): "
+                         "profiles a one-pattern case in the launch shape of a many-pattern run")
     return ap.parse_args(argv)
 
 
@@ -356,6 +359,8 @@ def main():
         dgsem.dgsem_set_tiles(sol.ctx, prec, tiles)
     else:
         tiles = dgsem.dgsem_autotune(sol.ctx, prec, B, len(w.domains), reps=2)
+    if args.layers:
+        dgsem.dgsem_set_layers(sol.ctx, [int(t) for t in args.layers.split(",")])
     K_p = w.pmuts.n_pmut if w.pmuts is not None else 0
     R = w.receivers.shape[0]
     S_tot = args.warmup + args.steps
@@ -438,6 +443,7 @@ def main():
                    "ndof": ndof, "batch_per_gpu": B, "n_pmut": K_p, "receivers": R,
                    "parallelism": f"replicas x{world}" if world > 1 else "single-gpu",
                    "tiles": [int(t) for t in tiles],
+                   **({"layers_per_cta": [int(t) for t in args.layers.split(",")]} if args.layers else {}),
                    "l2": "state larger than L2" if ndof * B * 3 * es > 129e6 else "state fits in L2"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "kernels": {names[k]: {"ms_total": kstats[k][0], "launches": kstats[k][1]} for k in range(5) if kstats[k][1]},
