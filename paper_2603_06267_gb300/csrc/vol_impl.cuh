@@ -393,34 +393,53 @@ __device__ __forceinline__ void zstencil_smem_f32(const VolArgs<float, N>& A, co
   }
 }
 
-// acc += c2 * (col - self) over the owned run, all in registers
+// The register column holds differences to the layer's middle plane R:
+// dcol[q] = p_q - p_R of the owned run (dcol[R] = 0, never read).  A full z
+// row of the stiffness sums to zero, so sum_q c_q p_q = sum_{q != R} c_q
+// dcol[q] exactly; the differences are formed once per layer and shared by
+// the thread's planes and the carry, and they have the size of the variation
+// of p across one element, as the per-plane differences did.
+template <int N> struct ColRef { static constexpr int R = N / 2; };
+
+// the owned run's column differences to plane R, in place
 template <int N>
-__device__ __forceinline__ void reg_term(const float* col, float2 c2, const float* self, float2* acc, float& accT) {
+__device__ __forceinline__ void col_to_diff(float (*col)[N]) {
+  constexpr int R = ColRef<N>::R;
 #pragma unroll
-  for (int i = 0; i < N / 2; ++i)
-    acc[i] = __ffma2_rn(c2, sub2(f2(col[2 * i], col[2 * i + 1]), f2(self[2 * i], self[2 * i + 1])), acc[i]);
-  if constexpr (N % 2 == 1) accT = fmaf(c2.x, col[N - 1] - self[N - 1], accT);
+  for (int q = 0; q <= N; ++q) {
+    if (q == R) continue;
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float2 d = sub2(f2(col[q][2 * i], col[q][2 * i + 1]), f2(col[R][2 * i], col[R][2 * i + 1]));
+      col[q][2 * i] = d.x;
+      col[q][2 * i + 1] = d.y;
+    }
+    if constexpr (N % 2 == 1) col[q][N - 1] -= col[R][N - 1];
+  }
 }
 
-// z part from the thread's column of the layer in registers, runtime plane c
-// (the term q = c is zero)
+// acc += c2 * dcol over the owned run, all in registers
+template <int N>
+__device__ __forceinline__ void reg_term(const float* dcol, float2 c2, float2* acc, float& accT) {
+#pragma unroll
+  for (int i = 0; i < N / 2; ++i) acc[i] = __ffma2_rn(c2, f2(dcol[2 * i], dcol[2 * i + 1]), acc[i]);
+  if constexpr (N % 2 == 1) accT = fmaf(c2.x, dcol[N - 1], accT);
+}
+
+// z part from the thread's column differences of the layer, runtime plane c
 template <int N, int ZM>
-__device__ __forceinline__ void zstencil_col_f32(const VolArgs<float, N>& A, const float (*col)[N], int c,
-                                                 const float* self, const float* carry, float iw_z, float2* zs,
-                                                 float& zsT) {
-  constexpr int NP = N / 2;
+__device__ __forceinline__ void zstencil_col_f32(const VolArgs<float, N>& A, const float (*dcol)[N], int c,
+                                                 const float* carry, float iw_z, float2* zs, float& zsT) {
+  constexpr int NP = N / 2, R = ColRef<N>::R;
   zsT = 0.f;
 #pragma unroll
   for (int i = 0; i < NP; ++i) zs[i] = f2(0.f, 0.f);
-  if constexpr (ZM == 0) {
 #pragma unroll
-    for (int q = 1; q <= N; ++q) reg_term<N>(col[q], A.rz2[q], self, zs, zsT);
-  } else if constexpr (ZM == 1) {
-#pragma unroll
-    for (int q = 0; q <= N; ++q) reg_term<N>(col[q], A.cz2[c][q], self, zs, zsT);
-  } else {
-#pragma unroll
-    for (int q = 0; q < N; ++q) reg_term<N>(col[q], A.lz2[q], self, zs, zsT);
+  for (int q = 0; q <= N; ++q) {
+    if (q == R) continue;
+    if constexpr (ZM == 0) reg_term<N>(dcol[q], A.rz2[q], zs, zsT);
+    else if constexpr (ZM == 1) reg_term<N>(dcol[q], A.cz2[c][q], zs, zsT);
+    else reg_term<N>(dcol[q], A.lz2[q], zs, zsT);
   }
   if constexpr (ZM != 1) {
     const float2 w2 = f2(iw_z, iw_z);
@@ -464,16 +483,19 @@ __device__ __forceinline__ void carry_f32(const VolArgs<float, N>& A, const floa
   if constexpr (N % 2 == 1) carry[N - 1] = cT;
 }
 
-// the same from the column in registers
+// the same from the column differences in registers
 template <int N>
-__device__ __forceinline__ void carry_reg_f32(const VolArgs<float, N>& A, const float (*col)[N], float* carry) {
-  constexpr int NP = N / 2;
+__device__ __forceinline__ void carry_reg_f32(const VolArgs<float, N>& A, const float (*dcol)[N], float* carry) {
+  constexpr int NP = N / 2, R = ColRef<N>::R;
   float2 cs[NP > 0 ? NP : 1];
   float cT = 0.f;
 #pragma unroll
   for (int i = 0; i < NP; ++i) cs[i] = f2(0.f, 0.f);
 #pragma unroll
-  for (int q = 0; q < N; ++q) reg_term<N>(col[q], A.lz2[q], col[N], cs, cT);
+  for (int q = 0; q <= N; ++q) {
+    if (q == R) continue;
+    reg_term<N>(dcol[q], A.lz2[q], cs, cT);
+  }
 #pragma unroll
   for (int i = 0; i < NP; ++i) { carry[2 * i] = cs[i].x; carry[2 * i + 1] = cs[i].y; }
   if constexpr (N % 2 == 1) carry[N - 1] = cT;
@@ -755,6 +777,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
       if constexpr (ZR) {
 #pragma unroll
         for (int q = 0; q <= N; ++q) vld<T, VS, N>(S0 + q * PLANE + own, col[q]);
+        col_to_diff<N>(col);
       }
       // FP32 update of the N owned nodes of plane k from sm = M^-1 K p:
       // a = -sm (+ PMUT / interface terms), v += dtv a, p_out = p + dtp v
@@ -826,7 +849,7 @@ __global__ void __launch_bounds__(TXE * TYE * N * PG, MINB) vol_kernel(const __g
           float ysT, zsT;
           xstencil_f32<N>(A, xr, xl, xiw, acc);
           ystencil_f32<N, VS, BX>(A, P, own, xr + N, yvert, yl, yr, yiw, yb, cyi2, ys, ysT);
-          if constexpr (ZR) zstencil_col_f32<N, ZM>(A, col, c, xr + N, carry, iw_z, zs, zsT);
+          if constexpr (ZR) zstencil_col_f32<N, ZM>(A, col, c, carry, iw_z, zs, zsT);
           else zstencil_smem_f32<N, ZM, VS, PLANE>(A, S0, own, c, xr + N, carry, iw_z, zs, zsT);
           combine_f32<N>(acc, ys, ysT, zs, zsT, sm);
           commit_f32(k, vcur, xr + N, sm, iw_z, vn, pn);
