@@ -40,12 +40,12 @@ import workloads as W  # noqa: E402
 # (workload, precision, kernel kind); see profiles/.  None: not measured for
 # the current kernel.
 NCU_TRAFFIC_PER_LAUNCH = {
-    # profiles/vol_kernel_f32_N6_vring3_config3.md (variant 9, the one the
-    # autotuner picks): 708.1 MB read + 642.3 MB written per launch at batch 1 on
-    # the config-3 mesh (secondary box); the traffic scales with the number of
+    # profiles/vol_kernel_f32_N6_dram_traffic_config3.md (variant 9, the one
+    # the autotuner picks): 707.3 MB read + 640.8 MB written per launch at batch 1
+    # on the config-3 mesh (secondary box); the traffic scales with the number of
     # patterns (each has its own state, the operator lives in the parameter block)
-    ("config4_batched", "fp32", "vol_secondary"): 1.3504e9 * 64,
-    ("config3_array32", "fp32", "vol_secondary"): 1.3504e9,
+    ("config4_batched", "fp32", "vol_secondary"): 1.3481e9 * 64,
+    ("config3_array32", "fp32", "vol_secondary"): 1.3481e9,
 }
 
 

@@ -337,8 +337,26 @@ def dgsem_num_tiles(ctx, precision: int, box: int) -> int:
     return n.value
 
 
+def _num_boxes(ctx) -> int:
+    """Boxes of the context (the C calls that take one value per box read
+    exactly this many from their array)."""
+    n = c_int()
+    nb = 0
+    while nb < 64 and _lib.dgsem_num_tiles(ctx, 0, nb, byref(n)) == DGSEM_OK:
+        nb += 1
+    return nb
+
+
+def _per_box(ctx, values, where):
+    arr = np.ascontiguousarray(values, dtype=np.int32).ravel()
+    nb = _num_boxes(ctx)
+    if arr.size != nb:
+        raise ValueError(f"{where}: one value per box ({nb}), got {arr.size}")
+    return arr
+
+
 def dgsem_set_tiles(ctx, precision: int, tiles):
-    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    t = _per_box(ctx, tiles, "dgsem_set_tiles")
     _check(_lib.dgsem_set_tiles(ctx, precision, _ptr(t)), "dgsem_set_tiles")
 
 
@@ -354,7 +372,7 @@ def dgsem_autotune(ctx, precision: int, batch: int, ndomains: int, reps: int = 3
 
 def dgsem_set_layers(ctx, layers_per_cta: Sequence[int]):
     """Element layers per CTA of each box's volume kernel (0 = automatic)."""
-    arr = np.ascontiguousarray(layers_per_cta, dtype=np.int32)
+    arr = _per_box(ctx, layers_per_cta, "dgsem_set_layers")
     _check(_lib.dgsem_set_layers(ctx, _ptr(arr)), "dgsem_set_layers")
 
 

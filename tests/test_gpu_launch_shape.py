@@ -107,6 +107,12 @@ def test_layer_setter_and_launch_report_edge_cases():
     with pytest.raises(dgsem.DgsemError) as e:
         dgsem.dgsem_set_layers(sol.ctx, [-1, 0])
     assert e.value.code == dgsem.DGSEM_EINVAL
+    # one value per box: the binding refuses other lengths before the library
+    # would read past the array
+    with pytest.raises(ValueError):
+        dgsem.dgsem_set_layers(sol.ctx, [1])
+    with pytest.raises(ValueError):
+        dgsem.dgsem_set_tiles(sol.ctx, 1, [0, 0, 0])
     ref = sol.run(precision=1)
     dgsem.dgsem_set_layers(sol.ctx, [1000, 1000])
     tr = sol.run(precision=1)
