@@ -632,6 +632,7 @@ int launch_step(dgsem_ctx* c, cudaStream_t s, const double* drive, long long dbs
     a.B = c->batch; a.K = c->K; a.M = c->M;
     a.fp_ptr = c->d_fp_ptr; a.fp_off = c->d_fp_off; a.Bm = c->d_Bm;
     a.qdd32 = std::is_same<T, float>::value ? c->d_qdd32 : nullptr;
+    a.Bm32 = std::is_same<T, float>::value ? c->d_Bm32 : nullptr;
     a.p_prev = static_cast<const T*>(c->X[0]);
     a.bsp = c->box[0].bstride;
     const long long kmB = (long long)c->batch * c->K * c->M;

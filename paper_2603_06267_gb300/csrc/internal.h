@@ -187,6 +187,7 @@ struct PmutArgs {
   const int* fp_ptr;               // [K+1] footprint entries of PMUT k
   const long long* fp_off;         // [nnz] offset of the face node in the primary array
   const double* Bm;                // [nnz][M]
+  const float* Bm32;               // FP32 copy of Bm: FP32 state, projection sums in FP32; or NULL
   const T* p_prev;                 // p^n of the primary box
   long long bsp;
   double* q; double* qd; double* qdd;   // [B][K][M]

@@ -1,5 +1,7 @@
 // Interface fluxes on Gamma_I (Sec. 5, eq. Wf_2 interface terms) and the
 // PMUT modal step with receiver sampling (Algorithm 1 PMUT rows, eqs. g_m).
+#include <type_traits>
+
 #include "internal.h"
 
 namespace {
@@ -395,6 +397,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ PmutArgs<T> A) {
@@ -416,24 +423,48 @@ __global__ void __launch_bounds__(256) pmut_recv_kernel(const __grid_constant__ 
       qd = A.qd[kb + lane];
       qdd = A.qdd[kb + lane];
     }
-    double g[DG_MAXM];
-#pragma unroll
-    for (int m = 0; m < DG_MAXM; ++m) g[m] = 0.0;
     const T* p = A.p_prev + (long long)b * A.bsp;
     const int e1 = A.fp_ptr[k + 1];
-    for (int e = A.fp_ptr[k] + lane; e < e1; e += 32) {
-      const double pv = (double)p[A.fp_off[e]];
-      const double* Bv = A.Bm + (long long)e * M;
-#pragma unroll
-      for (int m = 0; m < DG_MAXM; ++m)
-        if (m < M) g[m] += Bv[m] * pv;
-    }
     double gm = 0.0;
+    if (std::is_same<T, float>::value && A.Bm32) {
+      // FP32 state: products and sums in FP32 (a footprint sums ~10^2 terms,
+      // rounding ~1e-7 relative, the size of the FP32 field's own error);
+      // GB300's FP64 pipe made the FP64 sums most of this kernel's time.  The
+      // modal state below stays FP64.
+      float g[DG_MAXM];
 #pragma unroll
-    for (int m = 0; m < DG_MAXM; ++m) {
-      if (m < M) {
-        const double s = warp_sum(g[m]);
-        if (lane == m) gm = s;
+      for (int m = 0; m < DG_MAXM; ++m) g[m] = 0.f;
+      for (int e = A.fp_ptr[k] + lane; e < e1; e += 32) {
+        const float pv = (float)p[A.fp_off[e]];
+        const float* Bv = A.Bm32 + (long long)e * M;
+#pragma unroll
+        for (int m = 0; m < DG_MAXM; ++m)
+          if (m < M) g[m] = fmaf(Bv[m], pv, g[m]);
+      }
+#pragma unroll
+      for (int m = 0; m < DG_MAXM; ++m) {
+        if (m < M) {
+          const float s = warp_sum(g[m]);
+          if (lane == m) gm = (double)s;
+        }
+      }
+    } else {
+      double g[DG_MAXM];
+#pragma unroll
+      for (int m = 0; m < DG_MAXM; ++m) g[m] = 0.0;
+      for (int e = A.fp_ptr[k] + lane; e < e1; e += 32) {
+        const double pv = (double)p[A.fp_off[e]];
+        const double* Bv = A.Bm + (long long)e * M;
+#pragma unroll
+        for (int m = 0; m < DG_MAXM; ++m)
+          if (m < M) g[m] += Bv[m] * pv;
+      }
+#pragma unroll
+      for (int m = 0; m < DG_MAXM; ++m) {
+        if (m < M) {
+          const double s = warp_sum(g[m]);
+          if (lane == m) gm = s;
+        }
       }
     }
     // voltage of membrane k at t^n: the drive (TX) or, from step rx_switch on,
