@@ -211,13 +211,40 @@ __global__ void convt_taps3(const bf16* __restrict__ W, int Ci, int Co, bf16* __
 }
 
 // rows (b, m), channels n .. n + 31: v[b][co][2m], v[b][co][2m + 1] (+ bias)
-// and u_next = bf16(gelu(v)) as adjacent pairs (channel-major)
+// as adjacent pairs (channel-major), and u_next = bf16(gelu(v)): channel-major
+// [b][co][t] like v, or (tm) time-major [b][t][co], the layout the next
+// transposed convolution reads, 32 consecutive channels per sample
 struct PairConvEpi {
   static constexpr bool paired = true;
-  float* v; bf16* un; const float* bias; int T, Co;
+  float* v; bf16* un; const float* bias; int T, Co, tm;
   __device__ __forceinline__ void operator()(int r, int n, const uint32_t* ev, const uint32_t* od) const {
     const int b = r / T, m = r % T, To = 2 * T;
     const size_t o = ((size_t)b * Co + n) * To + 2 * m;
+    if (un && tm) {
+      bf16* ue = un + ((size_t)b * To + 2 * m) * Co + n;
+      bf16* uo = ue + Co;
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) {
+        uint4 we, wo;
+        uint32_t* pe = &we.x;
+        uint32_t* po = &wo.x;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int q = j + 2 * h;
+          const float e0 = __uint_as_float(ev[q]) + bias[n + q], e1 = __uint_as_float(ev[q + 1]) + bias[n + q + 1];
+          const float d0 = __uint_as_float(od[q]) + bias[n + q], d1 = __uint_as_float(od[q + 1]) + bias[n + q + 1];
+          *reinterpret_cast<float2*>(v + o + (size_t)q * To) = make_float2(e0, d0);
+          *reinterpret_cast<float2*>(v + o + (size_t)(q + 1) * To) = make_float2(e1, d1);
+          const __nv_bfloat162 ue2 = __floats2bfloat162_rn(gelu_f(e0), gelu_f(e1));
+          const __nv_bfloat162 uo2 = __floats2bfloat162_rn(gelu_f(d0), gelu_f(d1));
+          pe[h] = *reinterpret_cast<const uint32_t*>(&ue2);
+          po[h] = *reinterpret_cast<const uint32_t*>(&uo2);
+        }
+        *reinterpret_cast<uint4*>(ue + j) = we;
+        *reinterpret_cast<uint4*>(uo + j) = wo;
+      }
+      return;
+    }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const float bj = bias[n + j];
@@ -228,17 +255,22 @@ struct PairConvEpi {
   }
 };
 
-// v[b][co][2m + par] = acc + bias[co]; u_next = bf16(gelu(v)) (channel-major)
+// v[b][co][2m + par] = acc + bias[co]; u_next = bf16(gelu(v)), channel-major
+// or (tm) time-major [b][t][co]
 struct ConvEpi {
-  float* v; bf16* un; const float* bias; int T, Co, par;
+  float* v; bf16* un; const float* bias; int T, Co, par, tm;
   __device__ __forceinline__ void operator()(int r, int n, const uint32_t* acc) const {
     const int b = r / T, m = r % T, To = 2 * T;
     const size_t o = ((size_t)b * Co + n) * To + 2 * m + par;
+    bf16* ut = un + ((size_t)b * To + 2 * m + par) * Co + n;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const float val = __uint_as_float(acc[j]) + bias[n + j];
       v[o + (size_t)j * To] = val;
-      if (un) un[o + (size_t)j * To] = __float2bfloat16(gelu_f(val));
+      if (un) {
+        if (tm) ut[j] = __float2bfloat16(gelu_f(val));
+        else un[o + (size_t)j * To] = __float2bfloat16(gelu_f(val));
+      }
     }
   }
 };
@@ -270,21 +302,31 @@ int tmap_btc(CUtensorMap* map, const bf16* base, int B, int T, int C) {
 
 // one parity of a transposed convolution: u_tm [B][T][Ci] (time-major), taps
 // Bw [Co][2 Ci]; rows (b, m) of C go to v / u_next at time 2m + par
-int convt_parity(const bf16* u_tm, int B, int T, int Ci, const bf16* Bw, int Co, int par, const float* bias, float* v,
-                 bf16* un, int* err, cudaStream_t s) {
-  if (Ci % tcg::BK || Co % 64) return sfail(DGSEM_EINVAL, "convolution channels %d -> %d not tileable", Ci, Co);
-  CUtensorMap ta, tb;
-  int rc;
-  if ((rc = tmap_btc(&ta, u_tm, B, T, Ci)) || (rc = tmap_bf16(&tb, Bw, Co, 2 * Ci, 2 * Ci, 64))) return rc;
-  auto kern = tcg::gemm_kernel<64, 6, ConvEpi, tcg::ShiftA>;
-  constexpr int smem = tcg::Geo<64, 6>::SMEM;
+template <int STAGES>
+int convt_parity_launch(const CUtensorMap& ta, const CUtensorMap& tb, int B, int T, int Ci, int Co, int par,
+                        const ConvEpi& ep, int* err, cudaStream_t s) {
+  auto kern = tcg::gemm_kernel<64, STAGES, ConvEpi, tcg::ShiftA>;
+  constexpr int smem = tcg::Geo<64, STAGES>::SMEM;
   S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int M = B * T;
   dim3 grid(Co / 64, M / tcg::BM);
   const tcg::ShiftA al{Ci / tcg::BK, T, par == 0 ? 0 : 1, par == 0 ? -1 : 0};
-  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, 2 * Ci, ConvEpi{v, un, bias, T, Co, par}, err, al);
+  kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, 2 * Ci, ep, err, al);
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
+}
+
+int convt_parity(const bf16* u_tm, int B, int T, int Ci, const bf16* Bw, int Co, int par, const float* bias, float* v,
+                 bf16* un, int tm, int* err, cudaStream_t s) {
+  if (Ci % tcg::BK || Co % 64) return sfail(DGSEM_EINVAL, "convolution channels %d -> %d not tileable", Ci, Co);
+  CUtensorMap ta, tb;
+  int rc;
+  if ((rc = tmap_btc(&ta, u_tm, B, T, Ci)) || (rc = tmap_bf16(&tb, Bw, Co, 2 * Ci, 2 * Ci, 64))) return rc;
+  const ConvEpi ep{v, un, bias, T, Co, par, tm};
+  // a short K (few k-tiles) takes a shallow ring, so that several CTAs share an
+  // SM and one's epilogue overlaps another's products
+  if (2 * Ci / tcg::BK <= 6) return convt_parity_launch<3>(ta, tb, B, T, Ci, Co, par, ep, err, s);
+  return convt_parity_launch<6>(ta, tb, B, T, Ci, Co, par, ep, err, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +504,7 @@ int dw_parts(int tiles, int ktiles) {
 // u_tm [B][T][Ci] time-major, B3 [2 Co][3 Ci]; v and u_next channel-major
 template <int BN, int STAGES>
 int convt_pair_launch(const bf16* u_tm, int B, int T, int Ci, const bf16* B3, int Co, const float* bias, float* v,
-                      bf16* un, int* err, cudaStream_t s) {
+                      bf16* un, int tm, int* err, cudaStream_t s) {
   CUtensorMap ta, tb;
   int rc;
   if ((rc = tmap_pbtc(&ta, u_tm, 1, B, T, Ci)) || (rc = tmap_bf16(&tb, B3, 2 * Co, 3 * Ci, 3 * Ci, BN))) return rc;
@@ -471,16 +513,24 @@ int convt_pair_launch(const bf16* u_tm, int B, int T, int Ci, const bf16* B3, in
   S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   const int M = B * T;
   const tcg::SegA al{Ci / tcg::BK, T, {-1, 0, 1, 0}, {0, 0, 0, 0}};
-  kern<<<dim3(1, M / tcg::BM, 1), tcg::THREADS, smem, s>>>(ta, tb, M, 3 * Ci, PairConvEpi{v, un, bias, T, Co}, err, al);
+  kern<<<dim3(1, M / tcg::BM, 1), tcg::THREADS, smem, s>>>(ta, tb, M, 3 * Ci, PairConvEpi{v, un, bias, T, Co, tm}, err,
+                                                          al);
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
 
 int convt_pair(const bf16* u_tm, int B, int T, int Ci, const bf16* B3, int Co, const float* bias, float* v, bf16* un,
-               int* err, cudaStream_t s) {
+               int tm, int* err, cudaStream_t s) {
   if (Ci % tcg::BK) return sfail(DGSEM_EINVAL, "convolution input channels %d not tileable", Ci);
-  if (Co == 64) return convt_pair_launch<128, 6>(u_tm, B, T, Ci, B3, Co, bias, v, un, err, s);
-  if (Co == 128) return convt_pair_launch<256, 4>(u_tm, B, T, Ci, B3, Co, bias, v, un, err, s);
+  // a short K (few k-tiles) takes a shallow ring (96 KB of shared memory), so
+  // that two CTAs share an SM and one's epilogue overlaps the other's products
+  const bool shallow = 3 * Ci / tcg::BK <= 6;
+  if (Co == 64)
+    return shallow ? convt_pair_launch<128, 3>(u_tm, B, T, Ci, B3, Co, bias, v, un, tm, err, s)
+                   : convt_pair_launch<128, 6>(u_tm, B, T, Ci, B3, Co, bias, v, un, tm, err, s);
+  if (Co == 128)
+    return shallow ? convt_pair_launch<256, 2>(u_tm, B, T, Ci, B3, Co, bias, v, un, tm, err, s)
+                   : convt_pair_launch<256, 4>(u_tm, B, T, Ci, B3, Co, bias, v, un, tm, err, s);
   return sfail(DGSEM_EINVAL, "paired convolution product needs 64 or 128 output channels, not %d", Co);
 }
 
@@ -644,6 +694,14 @@ struct srg_net {
   // layers whose channel counts are not multiples of 64 run on the CUDA cores
   bf16 *utm = nullptr, *Bev = nullptr;
   std::vector<int> conv_tc;
+  // tm_u[j]: u[j] is stored time-major [b][t][ci] (written so by the epilogue of
+  // tensor-core layer j - 1 and read so by tensor-core layer j, no transpose)
+  std::vector<int> tm_u;
+  // forward tap matrices of each tensor-core layer, rebuilt only when the
+  // BF16 weights have changed since (pb_ver counts their updates)
+  std::vector<bf16*> b3;
+  std::vector<unsigned long long> b3_ver;
+  unsigned long long pb_ver = 1;
   // their gradients: parity-split dv, K-contiguous u and tap-shifted dv, and
   // the partial sums of the split weight-gradient products
   bf16 *dvp = nullptr, *uK = nullptr, *dvK = nullptr;
@@ -668,8 +726,9 @@ int salloc(srg_net* n, void** p, size_t bytes) {
 int conv_len(const srg_config& c, int j) { return c.t0 << j; }        // input length of conv j
 int conv_cin(const srg_config& c, int j) { return j == 0 ? c.c0 : c.conv_ch[j - 1]; }
 
-// forward pass keeping every activation; returns the output buffer
-int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
+// forward pass keeping every activation; the last layer's output goes to
+// yout when given (inference), else to v[n_conv - 1]
+int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s, float* yout = nullptr) {
   const srg_config& c = n->cfg;
   to_bf16<<<EW_BLOCKS, EW_THREADS, 0, s>>>(x, n->a[0], (size_t)B * c.d_in);
   S_TRY(cudaGetLastError());
@@ -688,28 +747,42 @@ int forward_impl(srg_net* n, const float* x, int B, cudaStream_t s) {
   for (int j = 0; j < c.n_conv; ++j) {
     const int last = j == c.n_conv - 1;
     const int ci = conv_cin(c, j), co = c.conv_ch[j], ti = conv_len(c, j);
+    float* vj = (last && yout) ? yout : n->v[j];
+    bf16* un = last ? nullptr : n->u[j + 1];
+    const int tm_next = last ? 0 : n->tm_u[j + 1];
     if (n->conv_tc[j]) {
-      // time-major copy of the input, the tap pairs, then the two parities
-      if ((rc = transpose(n->u[j], ci, ti, n->utm, s, B))) return rc;
-      if (co == 64 || co == 128) {
-        // both output parities in one product, written as adjacent samples
-        convt_taps3<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev);
+      // the input in time-major layout (a transposed copy unless the previous
+      // layer wrote it so), the tap matrix (cached per weight update), then
+      // both parities in one product (64 or 128 output channels) or one
+      // product per parity
+      const bf16* uin = n->u[j];
+      if (!n->tm_u[j]) {
+        if ((rc = transpose(n->u[j], ci, ti, n->utm, s, B))) return rc;
+        uin = n->utm;
+      }
+      const bool paired = co == 64 || co == 128;
+      if (n->b3_ver[j] != n->pb_ver) {
+        if (paired) {
+          convt_taps3<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->b3[j]);
+        } else {
+          convt_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->b3[j],
+                                                      n->b3[j] + (size_t)co * 2 * ci);
+        }
         S_TRY(cudaGetLastError());
-        if ((rc = convt_pair(n->utm, B, ti, ci, n->Bev, co, n->P + n->offB[L + 1 + j], n->v[j],
-                             last ? nullptr : n->u[j + 1], n->d_err, s)))
+        n->b3_ver[j] = n->pb_ver;
+      }
+      if (paired) {
+        if ((rc = convt_pair(uin, B, ti, ci, n->b3[j], co, n->P + n->offB[L + 1 + j], vj, un, tm_next, n->d_err, s)))
           return rc;
       } else {
-        convt_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->Pb + n->offW[L + 1 + j], ci, co, n->Bev,
-                                                    n->Bev + (size_t)co * 2 * ci);
-        S_TRY(cudaGetLastError());
         for (int par = 0; par < 2; ++par)
-          if ((rc = convt_parity(n->utm, B, ti, ci, n->Bev + (size_t)par * co * 2 * ci, co, par,
-                                 n->P + n->offB[L + 1 + j], n->v[j], last ? nullptr : n->u[j + 1], n->d_err, s)))
+          if ((rc = convt_parity(uin, B, ti, ci, n->b3[j] + (size_t)par * co * 2 * ci, co, par,
+                                 n->P + n->offB[L + 1 + j], vj, un, tm_next, n->d_err, s)))
             return rc;
       }
     } else {
       convt_fwd<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], n->Pb + n->offW[L + 1 + j], n->P + n->offB[L + 1 + j], B,
-                                                 ci, co, ti, n->v[j], last ? nullptr : n->u[j + 1], 1);
+                                                 ci, co, ti, vj, un, 1);
       S_TRY(cudaGetLastError());
     }
   }
@@ -730,16 +803,31 @@ int convt_backward_tc(srg_net* n, int j, int B, cudaStream_t s) {
   {
     CUtensorMap ta, tb;
     if ((rc = tmap_pbtc(&ta, n->dvp, 2, B, ti, co)) || (rc = tmap_bf16(&tb, n->Bev, ci, 4 * co, 4 * co, 64))) return rc;
-    auto kern = tcg::gemm_kernel<64, 6, DuEpi, tcg::SegA>;
-    constexpr int smem = tcg::Geo<64, 6>::SMEM;
-    S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int M = B * ti;
     const tcg::SegA al{co / tcg::BK, ti, {-1, 0, 0, 1}, {1, 0, 1, 0}};
-    kern<<<dim3(ci / 64, M / tcg::BM, 1), tcg::THREADS, smem, s>>>(ta, tb, M, 4 * co, DuEpi{n->gu, ti, ci}, n->d_err, al);
+    const dim3 grid(ci / 64, M / tcg::BM, 1);
+    const DuEpi ep{n->gu, ti, ci};
+    // a short K takes a shallow ring (several CTAs per SM)
+    if (4 * co / tcg::BK <= 6) {
+      auto kern = tcg::gemm_kernel<64, 3, DuEpi, tcg::SegA>;
+      constexpr int smem = tcg::Geo<64, 3>::SMEM;
+      S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, 4 * co, ep, n->d_err, al);
+    } else {
+      auto kern = tcg::gemm_kernel<64, 6, DuEpi, tcg::SegA>;
+      constexpr int smem = tcg::Geo<64, 6>::SMEM;
+      S_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      kern<<<grid, tcg::THREADS, smem, s>>>(ta, tb, M, 4 * co, ep, n->d_err, al);
+    }
     S_TRY(cudaGetLastError());
   }
   // dW_k: rows ci, N = Co, K = (b, i), split into S parts
-  convt_u_kmajor<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], B, ci, ti, n->uK);
+  if (n->tm_u[j]) {
+    // time-major u[j] is [(b, i)][ci]: its transpose is the K-contiguous copy
+    if ((rc = transpose(n->u[j], B * ti, ci, n->uK, s))) return rc;
+  } else {
+    convt_u_kmajor<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->u[j], B, ci, ti, n->uK);
+  }
   convt_dv_taps<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->gv, B, co, ti, n->dvK);
   S_TRY(cudaGetLastError());
   const int K = B * ti;
@@ -880,13 +968,23 @@ int srg_create(const srg_config* cfg, int max_batch, unsigned long long seed, sr
     if (ci % 64 == 0 && co % 64 == 0 && tiles_t && ((size_t)max_batch * ti) % 128 == 0) {
       n->conv_tc[j] = 1;
       utm_n = std::max(utm_n, B * ci * ti);
-      bev_n = std::max(bev_n, (size_t)6 * ci * co);
+      bev_n = std::max(bev_n, (size_t)4 * ci * co);   // the data-gradient taps
       dvp_n = std::max(dvp_n, B * 2 * ti * co);
       uk_n = std::max(uk_n, B * ci * ti);
       dvk_n = std::max(dvk_n, (size_t)4 * co * B * ti);
       // the weight-gradient parts for the smallest batch (64) the network takes, the most parts
       n->part_n = std::max(n->part_n, (size_t)4 * 64 * ci * co);
     }
+  }
+  n->tm_u.assign(c.n_conv, 0);
+  n->b3.assign(c.n_conv, nullptr);
+  n->b3_ver.assign(c.n_conv, 0);
+  for (int j = 0; j < c.n_conv; ++j) {
+    if (!n->conv_tc[j]) continue;
+    n->tm_u[j] = j > 0 && n->conv_tc[j - 1];
+    const int ci = conv_cin(c, j), co = c.conv_ch[j];
+    const size_t nb3 = (size_t)((co == 64 || co == 128) ? 6 : 4) * ci * co;
+    if ((rc = A((void**)&n->b3[j], nb3 * 2))) { srg_destroy(n); return rc; }
   }
   if (utm_n && ((rc = A((void**)&n->utm, utm_n * 2)) || (rc = A((void**)&n->Bev, bev_n * 2)) ||
                 (rc = A((void**)&n->dvp, dvp_n * 2)) || (rc = A((void**)&n->uK, uk_n * 2)) ||
@@ -928,6 +1026,7 @@ int srg_set_params(srg_net* n, const float* host, size_t len) {
   if (!n || !host || len < n->np) return sfail(DGSEM_EINVAL, "bad arguments");
   S_TRY(cudaMemcpy(n->P, host, n->np * 4, cudaMemcpyHostToDevice));
   to_bf16<<<EW_BLOCKS, EW_THREADS>>>(n->P, n->Pb, n->np);
+  ++n->pb_ver;
   S_TRY(cudaGetLastError());
   S_TRY(cudaDeviceSynchronize());
   return DGSEM_OK;
@@ -938,10 +1037,7 @@ int srg_forward(srg_net* n, const float* x, int B, float* y, void* stream) {
   int rc = check_batch(n, B);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((rc = forward_impl(n, x, B, s))) return rc;
-  const srg_config& c = n->cfg;
-  const size_t outn = (size_t)B * c.conv_ch[c.n_conv - 1] * conv_len(c, c.n_conv);
-  S_TRY(cudaMemcpyAsync(y, n->v[c.n_conv - 1], outn * 4, cudaMemcpyDeviceToDevice, s));
+  if ((rc = forward_impl(n, x, B, s, y))) return rc;
   S_TRY(cudaStreamSynchronize(s));
   return check_err(n);
 }
@@ -1029,6 +1125,7 @@ int srg_adam_step(srg_net* n, float lr, float b1, float b2, float eps, void* str
   const float c1 = 1.f - std::pow(b1, (float)n->t), c2 = 1.f - std::pow(b2, (float)n->t);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   adam<<<EW_BLOCKS, EW_THREADS, 0, s>>>(n->P, n->Pb, n->G, n->M1, n->M2, n->np, lr, b1, b2, eps, c1, c2);
+  ++n->pb_ver;
   S_TRY(cudaGetLastError());
   return DGSEM_OK;
 }
