@@ -1037,7 +1037,15 @@ int srg_forward(srg_net* n, const float* x, int B, float* y, void* stream) {
   int rc = check_batch(n, B);
   if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((rc = forward_impl(n, x, B, s, y))) return rc;
+  // the last layer writes straight into y (its epilogue stores pairs of floats);
+  // a y that is not 16-byte aligned gets the network's own buffer and a copy
+  const bool direct = reinterpret_cast<uintptr_t>(y) % 16 == 0;
+  if ((rc = forward_impl(n, x, B, s, direct ? y : nullptr))) return rc;
+  if (!direct) {
+    const srg_config& c = n->cfg;
+    const size_t outn = (size_t)B * c.conv_ch[c.n_conv - 1] * conv_len(c, c.n_conv);
+    S_TRY(cudaMemcpyAsync(y, n->v[c.n_conv - 1], outn * 4, cudaMemcpyDeviceToDevice, s));
+  }
   S_TRY(cudaStreamSynchronize(s));
   return check_err(n);
 }

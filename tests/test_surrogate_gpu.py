@@ -187,3 +187,25 @@ def test_screening_gain_over_solver():
     assert err < 0.8 * err_const
     assert surr_pps > 100 * solver_pps
     net.close()
+
+
+def test_forward_into_unaligned_output_buffer():
+    """The forward writes the last layer straight into an aligned output
+    buffer; a buffer that starts one float off 16 bytes gets the same values
+    through the network's own buffer."""
+    import torch
+    from paper_2603_06267_gb300 import surrogate as S
+    w = dict(d_in=128, hidden=256, n_hidden=1, c0=64, t0=32, conv_ch=(128, 64))
+    net = S.Surrogate(max_batch=64, seed=5, **w)
+    x = torch.randn((64, 128), device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    shape = (64, net.c_out, net.t_out)
+    n = 64 * net.c_out * net.t_out
+    y0 = torch.zeros(shape, device="cuda")
+    net.forward(x, y0)
+    big = torch.full((n + 1,), float("nan"), device="cuda")
+    y1 = big[1:].view(shape)
+    assert y1.data_ptr() % 16 == 4
+    net.forward(x, y1)
+    assert torch.equal(y0, y1)
+    assert torch.isnan(big[0])
+    net.close()
