@@ -142,7 +142,9 @@ int gemm_nt(const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K,
             cudaStream_t s) {
   if (M < 1 || N % 64 || K % 64 || K < 64) return sfail(DGSEM_EINVAL, "gemm shape %d x %d x %d not tileable", M, N, K);
   const int mt = (M + tcg::BM - 1) / tcg::BM;
-  if (N % 128 == 0 && mt * (N / 128) >= 148) return tc_launch<128, 4>(A, lda, B, ldb, M, N, K, ep, err, s);
+  // enough 128-wide tiles to fill the GPU: a three-stage ring (100 KB), so two CTAs
+  // share an SM and a grid of up to 2 x 152 tiles runs in one wave
+  if (N % 128 == 0 && mt * (N / 128) >= 148) return tc_launch<128, 3>(A, lda, B, ldb, M, N, K, ep, err, s);
   return tc_launch<64, 6>(A, lda, B, ldb, M, N, K, ep, err, s);
 }
 
